@@ -1,0 +1,296 @@
+"""Pins for the CPU oracle: each test checks it against something other than itself.
+
+* the worked example of Section 4.3 (every intermediate matrix T_0..T_5, the loop
+  count k = 6 and the relations R_A), read from ``tests/golden/worked_example.txt``;
+* brute force over walks with CYK (Section 2's definition of R_A, directly);
+* closed forms (two cycles sharing a node; S -> S S | a is transitive closure;
+  S -> A B is one Boolean matrix product; the sc-only query on a tree hierarchy);
+* Lemma 3 (derivation height <= k after k iterations) on the two-cycle family, where
+  the largest minimal height is known in closed form;
+* agreement between the worklist oracle and Algorithm 1 written literally;
+* planted mistakes: wrong variants of the C oracle must fail these pins.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import cfpq_synth as synth
+import oracle
+
+
+def read_golden(path):
+    g = {"edges": [], "T": {}, "R": {}, "k": None, "n": None}
+    with open(path) as f:
+        for ln in f:
+            ln = ln.split("#", 1)[0].strip()
+            if not ln:
+                continue
+            t = ln.split()
+            if t[0] == "n":
+                g["n"] = int(t[1])
+            elif t[0] == "edge":
+                g["edges"].append((int(t[1]), t[2], int(t[3])))
+            elif t[0] == "k":
+                g["k"] = int(t[1])
+            elif t[0] == "R":
+                g["R"].setdefault(t[1], set()).add((int(t[2]), int(t[3])))
+            elif t[0].startswith("T"):
+                g["T"].setdefault(int(t[0][1:]), set()).add((int(t[1]), int(t[2]), t[3]))
+    return g
+
+
+@pytest.fixture(scope="module")
+def worked(golden_dir):
+    return read_golden(os.path.join(golden_dir, "worked_example.txt"))
+
+
+def test_worked_example_graph_matches_fixture(worked):
+    g = synth.worked_example_graph()
+    got = sorted((int(s), g.labels[int(l)], int(d)) for s, l, d in g.edges)
+    assert got == sorted(worked["edges"])
+    assert g.n == worked["n"]
+
+
+def test_worked_example_relations(worked):
+    g = synth.worked_example_graph()
+    res = oracle.hellings(g, synth.GRAMMAR_WORKED).as_sets()
+    for name in ["S", "S1", "S2", "S3", "S4", "S5", "S6"]:
+        assert res[name] == worked["R"].get(name, set()), name
+
+
+def test_worked_example_every_iteration(worked):
+    g = synth.worked_example_graph()
+    cnf, snaps, k = oracle.matrix_closure(g, synth.GRAMMAR_WORKED)
+    assert k == worked["k"] == 6
+    assert len(snaps) == 6  # T_0 .. T_5
+    for i, T in enumerate(snaps):
+        got = {(int(a), int(b), cnf.names[A]) for A, M in T.items() for a, b in zip(*np.nonzero(M))}
+        assert got == worked["T"][i], f"T{i}"
+
+
+def _as_sets_from_snap(cnf, T):
+    return {cnf.names[a]: set(zip(*map(lambda v: v.tolist(), np.nonzero(M)))) for a, M in T.items()}
+
+
+# ----------------------------------------------------------------------------- brute force
+
+def _dag_graph(n, m, L, seed):
+    k = synth.key(seed, 99)
+    i = np.arange(m)
+    a = synth.uniform_int(k, 3 * i, n)
+    b = synth.uniform_int(k, 3 * i + 1, n)
+    lab = synth.uniform_int(k, 3 * i + 2, L)
+    src, dst = np.minimum(a, b), np.maximum(a, b)
+    keep = src < dst
+    e = np.stack([src[keep], lab[keep], dst[keep]], axis=1)
+    return synth.Graph(n=n, edges=e, labels=[f"t{j}" for j in range(L)])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_brute_force_dag_exact(seed):
+    # On a DAG every walk has < n edges, so walks up to n-1 edges are all walks.
+    n = 5
+    g = _dag_graph(n, 9, 2, seed)
+    gram = synth.random_grammar_text(n_nt=3, n_terms=2, n_binary=5, n_unary=4,
+                                     n_eps=seed % 2, seed=seed)
+    res = oracle.hellings(g, gram).as_sets()
+    bf = oracle.brute_force(g, gram, max_len=n - 1)
+    assert res == bf
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_brute_force_cyclic_bounded(seed):
+    # On cyclic graphs every bounded enumeration is a subset, and a large enough bound
+    # reaches the oracle's result exactly.
+    g = synth.random_graph(4, 7, 2, seed=seed)
+    gram = synth.random_grammar_text(n_nt=3, n_terms=2, n_binary=4, n_unary=3,
+                                     n_eps=(seed + 1) % 2, seed=100 + seed)
+    res = oracle.hellings(g, gram).as_sets()
+    prev = None
+    for L in (3, 6, 9):
+        bf = oracle.brute_force(g, gram, max_len=L)
+        for name in res:
+            assert bf[name] <= res[name]
+        prev = bf
+    assert prev == res
+
+
+def test_brute_force_worked_example(worked):
+    g = synth.worked_example_graph()
+    bf = oracle.brute_force(g, synth.GRAMMAR_WORKED, max_len=8)
+    for name, pairs in worked["R"].items():
+        assert bf[name] == pairs
+
+
+# ----------------------------------------------------------------------------- closed forms
+
+def _two_cycle_expected(p, q):
+    """R_S for S -> a S b | a b on two cycles sharing node 0: (i, j) is in R_S iff some
+    m >= 1 has i + m = 0 (mod p) on the a-cycle and m b-steps from 0 reach j, i.e.
+    d_i = e_j (mod gcd(p, q)) with d_i = (p - i) mod p and e_j = position of j."""
+    g = math.gcd(p, q)
+    pos = {0: 0}
+    for t in range(q - 1):
+        pos[p + t] = t + 1
+    out = set()
+    for i in range(p):
+        d = (p - i) % p
+        for j, e in pos.items():
+            if (d - e) % g == 0:
+                out.add((i, j))
+    return out
+
+
+@pytest.mark.parametrize("p,q", [(6, 4), (9, 6), (8, 7), (5, 5), (3, 2), (1, 1), (4, 1)])
+def test_two_cycles_closed_form(p, q):
+    g = synth.two_cycles(p, q)
+    res = oracle.hellings(g, synth.GRAMMAR_C3)
+    exp = _two_cycle_expected(p, q)
+    assert set(map(tuple, res.pairs("S").tolist())) == exp
+    # S1 -> S B: one b-step after every S pair
+    nxt = {int(s): int(d) for s, l, d in g.edges if l == 1}
+    assert set(map(tuple, res.pairs("S1").tolist())) == {(i, nxt[j]) for i, j in exp}
+    assert res.count("A") == p and res.count("B") == q
+
+
+@pytest.mark.parametrize("p,q", [(2, 1), (3, 2), (4, 3), (5, 3), (5, 4)])
+def test_two_cycles_iteration_count(p, q):
+    # Lemma 3: after k loop executions T holds exactly the pairs with a derivation of
+    # height <= k. With gcd(p, q) = 1 the largest minimal m with a^m b^m is pq, whose
+    # derivation has height 2pq for S and 2pq + 1 for S1 -> S B, so the loop runs
+    # 2pq + 1 times before an execution changes nothing.
+    g = synth.two_cycles(p, q)
+    cnf, snaps, k = oracle.matrix_closure(g, synth.GRAMMAR_C3)
+    assert k == 2 * p * q + 1
+
+
+def _warshall(adj):
+    n = adj.shape[0]
+    r = adj.copy()
+    for k in range(n):
+        r = r | (r[:, [k]] & r[[k], :])
+    return r
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_transitive_closure_closed_form(seed):
+    g = synth.random_graph(40, 60, 1, seed=seed)
+    res = oracle.hellings(g, "S S S\nS t0\n")
+    adj = np.zeros((g.n, g.n), dtype=bool)
+    adj[g.edges[:, 0], g.edges[:, 2]] = True
+    tc = _warshall(adj)
+    assert set(map(tuple, res.pairs("S").tolist())) == set(zip(*map(lambda v: v.tolist(), np.nonzero(tc))))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_single_product_closed_form(seed):
+    g = synth.random_graph(50, 300, 2, seed=seed)
+    res = oracle.hellings(g, "S A B\nA t0\nB t1\n")
+    A = np.zeros((g.n, g.n), dtype=np.int64)
+    B = np.zeros((g.n, g.n), dtype=np.int64)
+    for s, l, d in g.edges:
+        (A if l == 0 else B)[s, d] = 1
+    exp = (A @ B) > 0
+    assert set(map(tuple, res.pairs("S").tolist())) == set(zip(*map(lambda v: v.tolist(), np.nonzero(exp))))
+
+
+@pytest.mark.parametrize("n,C,seed", [(200, 60, 0), (1024, 300, 1), (500, 500, 2)])
+def test_sc_only_hierarchy_closed_form(n, C, seed):
+    g = synth.hierarchy(n, C, seed=seed)
+    res = oracle.hellings(g, synth.GRAMMAR_QSC)
+    parent = {int(s): int(d) for s, l, d in g.edges if l == 0}
+    has_child = set(parent.values())
+    assert set(map(tuple, res.pairs("S").tolist())) == {(p, p) for p in has_child}
+    assert set(map(tuple, res.pairs("X").tolist())) == {(c, parent[c]) for c in has_child if c in parent}
+
+
+def test_q1_hierarchy_y_empty():
+    g = synth.hierarchy(1024, 300, seed=0)
+    res = oracle.hellings(g, synth.GRAMMAR_Q1)
+    assert res.count("Y") == 0
+    assert res.count("S") > 0
+
+
+# ----------------------------------------------------------------------------- cross-checks
+
+@pytest.mark.parametrize("seed", range(6))
+def test_worklist_equals_algorithm1(seed):
+    g = synth.random_graph(24, 60, 3, seed=seed)
+    gram = synth.random_grammar_text(n_nt=5, n_terms=3, n_binary=9, n_unary=6,
+                                     n_eps=seed % 3, seed=seed)
+    res = oracle.hellings(g, gram).as_sets()
+    cnf, snaps, k = oracle.matrix_closure(g, gram)
+    final = _as_sets_from_snap(cnf, snaps[-1])
+    assert res == final
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_monotone_iterations(seed):
+    g = synth.random_graph(20, 50, 2, seed=seed)
+    gram = synth.random_grammar_text(4, 2, 7, 4, 0, seed=seed)
+    cnf, snaps, k = oracle.matrix_closure(g, gram)
+    for a, b in zip(snaps, snaps[1:]):
+        for A in a:
+            assert (b[A] >= a[A]).all()  # a^(i) contains a^(i-1)
+    # Theorem 3: at most |V|^2 |N| changing iterations
+    assert k - 1 <= g.n * g.n * len(cnf.names)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_properties_hold_on_oracle(seed):
+    g = synth.hierarchy(300, 90, seed=seed)
+    cnf = oracle.parse_grammar(synth.GRAMMAR_Q1, g.labels)
+    res = oracle.hellings(g, synth.GRAMMAR_Q1)
+    sets = {nm: res.pairs(nm) for nm in cnf.names}
+    assert oracle.check_seed_included(cnf, g.n, g.edges, sets)
+    assert oracle.check_closed(cnf, g.n, sets)
+    assert oracle.check_witnessed(cnf, g.n, g.edges, sets)
+
+
+# ----------------------------------------------------------------------------- grammar reader
+
+def test_grammar_reader_q1_normal_form():
+    cnf = oracle.parse_grammar(synth.GRAMMAR_Q1, synth.HIERARCHY_LABELS)
+    assert cnf.names == ["S", "X", "Y", "SC", "TY", "<sc_r>", "<ty_r>"]
+    assert len(cnf.binary) == 6 and len(cnf.unary) == 4 and cnf.eps == []
+
+
+def test_grammar_reader_rejects_bad_input():
+    with pytest.raises(ValueError):
+        oracle.parse_grammar("S A\nA a\n", ["a"])        # chain rule
+    with pytest.raises(ValueError):
+        oracle.parse_grammar("S zz\n", ["a"])            # unknown terminal
+    with pytest.raises(ValueError):
+        oracle.parse_grammar("S a b c\n", ["a", "b", "c"])
+
+
+def test_oracle_rejects_out_of_range_edges():
+    g = synth.Graph(n=3, edges=np.array([[0, 0, 5]]), labels=["a"])
+    with pytest.raises(ValueError):
+        oracle.hellings(g, "S a\n")
+
+
+def test_empty_graph_and_isolated_nodes():
+    g = synth.Graph(n=4, edges=np.zeros((0, 3), dtype=np.int64), labels=["a"])
+    res = oracle.hellings(g, "S S S\nS a\nE eps\n")
+    assert res.count("S") == 0
+    assert set(map(tuple, res.pairs("E").tolist())) == {(i, i) for i in range(4)}
+
+
+# ----------------------------------------------------------------------------- planted mistakes
+
+@pytest.mark.parametrize("plant", [1, 2, 3])
+def test_planted_mistakes_are_caught(plant, worked):
+    """Each deliberately wrong build of the C oracle must fail at least one pin."""
+    failures = 0
+    g = synth.worked_example_graph()
+    res = oracle.hellings(g, synth.GRAMMAR_WORKED, plant=plant).as_sets()
+    failures += any(res[nm] != worked["R"].get(nm, set()) for nm in res)
+    for seed in range(4):
+        gg = synth.random_graph(4, 7, 2, seed=seed)
+        gram = synth.random_grammar_text(3, 2, 4, 3, 1, seed=100 + seed)
+        r = oracle.hellings(gg, gram, plant=plant).as_sets()
+        failures += r != oracle.brute_force(gg, gram, max_len=9)
+    assert failures > 0
