@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the CFPQ closure engine on B300.
+
+Workload (one GPU): the same-generation hierarchy of n = 16384 nodes (5000 classes,
+11384 instances, seed 0) with both same-generation grammars on the same graph (Query 1
+and the subClassOf-only query). One step = one pass of the whole path for both queries:
+matrix initialisation, the closure loop to the fixpoint, and extraction of every R_A
+into device memory.
+
+metric: Boolean GOPS. The work of a step is the work of Algorithm 1 on the workload:
+sum over queries of (loop executions of Algorithm 1) x (binary productions) x 2 n^3, a
+fixed number for the workload (both arms count it the same way), divided by the step
+time. `value` is device-timed (CUDA events on the launching stream, inputs resident in
+HBM); `e2e` is the same metric through the C ABI with host buffers (edge upload, solve,
+triples copied back) inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--path auto|tensor|gather]
+    python bench.py --impl reference ...      # the CPU oracle on the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cfpq_synth as synth  # noqa: E402
+
+N_NODES, N_CLASSES, SEED = 16384, 5000, 0
+WORKLOAD = "hierarchy n=16384 (5000 classes), Query 1 + sc-only query on one graph, closure + extraction"
+METRIC = "Boolean GOPS (2n^3 per product of Algorithm 1) over the closure"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--path", default="auto", choices=["auto", "tensor", "gather"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload():
+    g = synth.hierarchy(N_NODES, N_CLASSES, seed=SEED)
+    return g, [("Q1", synth.GRAMMAR_Q1), ("QSC", synth.GRAMMAR_QSC)]
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx, self.proc, self.lines = gpu_index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------ CPU arm
+
+def oracle_step(graph, grammars):
+    import oracle
+
+    return [oracle.hellings(graph, text) for _, text in grammars]
+
+
+def oracle_work(graph, grammars):
+    """Products of Algorithm 1 on the workload, counted by the oracle's own sparse form of
+    Algorithm 1 (loop executions x binary productions)."""
+    import oracle
+
+    total = 0
+    for _, text in grammars:
+        cnf, _, k = oracle.matrix_closure_sparse(graph, text)
+        total += k * len(set(map(tuple, cnf.binary)))
+    return total
+
+
+def reference_arm(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    graph, grammars = workload()
+    products = oracle_work(graph, grammars)
+    ops = products * 2.0 * float(N_NODES) ** 3
+    for _ in range(args.warmup):
+        oracle_step(graph, grammars)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(graph, grammars)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = ops / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64 bitsets (CPU worklist)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_NODES, "classes": N_CLASSES, "seed": SEED,
+                   "grammars": [nm for nm, _ in grammars], "products_per_step": products},
+        "cpu_baseline": {"value": value, "unit": "GOPS", "cores": 1, "kind": "oracle",
+                         "sample": f"full workload, {args.steps} timed steps, one host thread"},
+        "e2e": {"value": value, "unit": "GOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------------ GPU arm
+
+def roofline(eng, graph, gs, path, stream):
+    """Average duration of the dominant product kernel over a profiled solve (CUDA events
+    around every product launch on the launching stream), against its algorithmic work."""
+    peaks, kind = load_peaks()
+    prod_ms = prod_l = tens_ms = tens_l = 0
+    flops = bytes_ = 0.0
+    for g in gs:
+        q = eng.Query(g, graph.n, graph.edges, path=path, profile=True)
+        q.solve(stream)
+        s = q.stats()
+        prod_ms += s["product_ms"]
+        prod_l += s["product_launches"]
+        tens_ms += s["tensor_ms"]
+        tens_l += s["tensor_launches"]
+        flops += s["dense_ops"]
+        bytes_ += s["product_bytes"]
+        q.close()
+    if tens_l > 0 and tens_ms >= 0.5 * prod_ms:
+        achieved = flops / (tens_ms / 1e3) / 1e12
+        peak = 2.0 * peaks["bf16_tflops_sustained"]
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_tc_bool_gemm", "launch_ms": tens_ms / tens_l,
+                "peak_note": f"{kind} sustained bf16 dense x 2 (fp8 e4m3 nominal ratio)"}
+    gather_ms = prod_ms - tens_ms
+    launches = max(1, prod_l - tens_l)
+    achieved = bytes_ / (gather_ms / 1e3) / 1e9 if gather_ms > 0 else None
+    peak = peaks["hbm_gbs"]
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None, "kernel": "k_gather",
+            "launch_ms": gather_ms / launches, "bytes_per_launch": bytes_ / launches,
+            "peak_note": f"{kind} HBM copy bandwidth"}
+
+
+def engine_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1707_01007_b300 as eng
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    path = {"tensor": eng.PATH_TENSOR, "gather": eng.PATH_GATHER, "auto": eng.PATH_AUTO}[args.path]
+
+    graph, grammars = workload()
+    gs = [eng.Grammar(t, graph.labels) for _, t in grammars]
+    stream = torch.cuda.current_stream()
+    # work of Algorithm 1 on this workload: its loop count from a Jacobi-schedule solve
+    products = 0
+    for g in gs:
+        qj = eng.Query(g, graph.n, graph.edges, schedule=eng.SCHED_JACOBI, path=eng.PATH_GATHER)
+        qj.solve(stream)
+        products += qj.stats()["iterations"] * len({(r.lhs, r.b, r.c) for r in
+                                                    (g.cnf.contents.binary[i] for i in range(g.cnf.contents.n_binary))})
+        qj.close()
+    ops_per_step = products * 2.0 * float(N_NODES) ** 3
+
+    qs = [eng.Query(g, graph.n, graph.edges, path=path) for g in gs]
+    caps = []
+    for q, g in zip(qs, gs):
+        q.solve(stream)
+        caps.append([max(1, q.count(nm)) for nm in g.names])
+    bufs = [[torch.empty(c * 3, dtype=torch.int32, device="cuda") for c in cl] for cl in caps]
+
+    def step():
+        for q, g, bl in zip(qs, gs, bufs):
+            q.solve(stream)
+            for nm, b in zip(g.names, bl):
+                q.get_device(nm, b.data_ptr(), b.numel() // 3)
+
+    for _ in range(args.warmup):
+        step()
+    st = [q.stats() for q in qs]
+    launches_per_step = sum(s["kernel_launches"] + 3 * len(g.names) for s, g in zip(st, gs))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * ops_per_step / (ms / 1e3) / 1e9
+
+    # e2e through the C ABI with host buffers: create (edge upload), solve, copy triples back
+    h2d = graph.n_edges * 12 * len(grammars)
+    d2h = 0
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d2h = 0
+        for g in gs:
+            q = eng.Query(g, graph.n, graph.edges, path=path)
+            q.solve()
+            for nm in g.names:
+                d2h += q.triples(nm).shape[0] * 12
+            q.close()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * ops_per_step / e2e_s / 1e9
+
+    roof = roofline(eng, graph, gs, path, stream)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32 bit-packed (gather); fp8 e4m3 0/1 operands, f32 accumulate (tensor)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_NODES, "classes": N_CLASSES, "seed": SEED,
+                   "grammars": [nm for nm, _ in grammars], "path": args.path,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (bit planes 3 x 7 x 32 MiB per query)",
+                   "products_per_step": products,
+                   "iterations_inplace": [s["iterations"] for s in st],
+                   "tensor_products": sum(s["tensor_products"] for s in st),
+                   "gather_products": sum(s["gather_products"] for s in st),
+                   "results_S": [q.count("S") for q in qs]},
+        "e2e": {"value": e2e_val, "unit": "GOPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            oracle_step(graph, grammars)
+            reps += 1
+            if time.perf_counter() - t0 >= args.cpu_seconds:
+                break
+        per = (time.perf_counter() - t0) / reps
+        line["cpu_baseline"] = {"value": ops_per_step / per / 1e9, "unit": "GOPS", "cores": 1, "kind": "oracle",
+                                "sample": f"full workload x{reps} ({per * 1e3:.0f} ms per step), one host thread"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return engine_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

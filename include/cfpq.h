@@ -1,0 +1,205 @@
+/*
+ * cfpq.h -- C ABI of the B300 (sm_103a) engine for relational-semantics context-free
+ * path querying (CFPQ) by matrix transitive closure.
+ *
+ * The method (Azimov & Grigorev, "Context-Free Path Querying by Matrix
+ * Multiplication"):
+ *   - input: an edge-labelled directed graph D = (V, E), V = {0..n-1}, and a grammar
+ *     G = (N, Sigma, P) whose productions are A -> B C and A -> x (Section 2); this ABI
+ *     also accepts A -> eps, which adds the empty walk (m, m);
+ *   - output: the context-free relations R_A = {(m, n) | some walk m -> n has a label
+ *     string derived from A} for every A in N (Section 2), returned as (A, m, n) triples;
+ *   - computation: Algorithm 1 (Section 4.2). One Boolean n x n matrix T_A is kept per
+ *     non-terminal, seeded from the terminal edges (matrix initialisation), and
+ *     T_A |= T_B x T_C over the Boolean semiring is applied for every production
+ *     A -> B C until no bit changes (the closure a^cf, whose result is R_A by Theorem 2).
+ *
+ * Conventions for every entry point:
+ *   - return value: CFPQ_OK (0) or one of the CFPQ_ERR_* codes below; no entry point
+ *     aborts the process; cfpq_strerror() names a code;
+ *   - the library copies every input array during the call; the caller keeps ownership
+ *     of everything it passes and of every output buffer;
+ *   - all device memory belongs to a context and is released by cfpq_destroy();
+ *   - a context is not thread-safe; distinct contexts may be used from distinct threads.
+ *
+ * Limits: 1 <= n <= CFPQ_MAX_NODES, 1 <= |N| <= CFPQ_MAX_NONTERM.
+ */
+#ifndef CFPQ_H_
+#define CFPQ_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CFPQ_MAX_NODES 131072
+#define CFPQ_MAX_NONTERM 64
+
+enum cfpq_status {
+    CFPQ_OK = 0,
+    CFPQ_ERR_INVALID = 1,     /* an id out of range, n out of range, NULL where data is required */
+    CFPQ_ERR_NOMEM = 2,       /* device or host allocation failed (or admission refused) */
+    CFPQ_ERR_NOT_SOLVED = 3,  /* results asked for before a successful cfpq_solve */
+    CFPQ_ERR_ITER_LIMIT = 4,  /* the iteration cap was reached before the fixpoint */
+    CFPQ_ERR_TIMEOUT = 5,     /* the wall-clock limit was reached before the fixpoint */
+    CFPQ_ERR_CUDA = 6,        /* a CUDA runtime call failed (no device, launch error, ...) */
+    CFPQ_ERR_BUFFER = 7,      /* output capacity smaller than the result */
+    CFPQ_ERR_UNSUPPORTED = 8  /* option combination not available (e.g. tensor path on a non-sm_103 device) */
+};
+
+/* A -> x : lhs is a non-terminal id in [0, n_nonterm), term a terminal id in [0, n_term). */
+typedef struct { int32_t lhs, term; } cfpq_rule1;
+/* A -> B C : all three are non-terminal ids. */
+typedef struct { int32_t lhs, b, c; } cfpq_rule2;
+
+/* A grammar in the normal form of Section 2 (plus A -> eps). Duplicate productions are
+ * allowed and mean the same production (set semantics). */
+typedef struct {
+    int32_t n_nonterm, n_term;
+    const cfpq_rule1 *unary;  int32_t n_unary;
+    const cfpq_rule2 *binary; int32_t n_binary;
+    const int32_t *eps_lhs;   int32_t n_eps;   /* non-terminals with A -> eps */
+} cfpq_grammar_cnf;
+
+/* Edge (src, label, dst) of E: src, dst in [0, n), label a terminal id. Multiple edges
+ * between the same nodes add the union of their heads (Section 4.2, after Algorithm 1). */
+typedef struct { uint32_t src; int32_t label; uint32_t dst; } cfpq_edge;
+
+/* Result element: (A, m, n) with (m, n) in R_A. */
+typedef struct { int32_t A; uint32_t m, n; } cfpq_triple;
+
+enum cfpq_schedule {
+    CFPQ_SCHED_INPLACE = 0,   /* products update T_A as soon as they finish (same least fixpoint) */
+    CFPQ_SCHED_JACOBI = 1     /* T_{k+1} = T_k u (T_k x T_k) exactly as Algorithm 1's loop body */
+};
+
+enum cfpq_path {
+    CFPQ_PATH_AUTO = 0,       /* per production group and iteration, the cheaper of the two below */
+    CFPQ_PATH_TENSOR = 1,     /* dense tcgen05 product of every production, every iteration */
+    CFPQ_PATH_GATHER = 2      /* CUDA-core bit-gather over changed bits only (semi-naive) */
+};
+
+typedef struct {
+    int32_t schedule;         /* enum cfpq_schedule; default INPLACE */
+    int32_t path;             /* enum cfpq_path; default AUTO */
+    int32_t use_graph;        /* 1: fixpoint loop in a CUDA graph with a conditional while node
+                                 and a device-side convergence flag (default); 0: host-driven loop */
+    int32_t profile;          /* 1: host-driven loop that times every product launch with CUDA
+                                 events (cfpq_stats.product_ms / product_launches); default 0 */
+    int64_t max_iter;         /* iteration cap; 0 = |V|^2 |N| + 1 (Theorem 3's bound on changes) */
+    double timeout_s;         /* wall-clock limit checked on the device; <= 0 = none */
+} cfpq_options;
+
+typedef struct {
+    int64_t iterations;       /* loop executions, the last being the one that changed nothing */
+    int64_t new_bits;         /* pairs added by products (excludes the seed) */
+    int64_t seed_bits;        /* pairs set by the matrix initialisation */
+    int64_t tensor_products;  /* (production, iteration) pairs computed by the tensor path */
+    int64_t gather_products;  /* (production, iteration) pairs computed by the gather path */
+    double dense_ops;         /* 2 * n_pad^3 * tensor_products: Boolean ops the tensor path executed */
+    double solve_ms;          /* device time of the last cfpq_solve (CUDA events) */
+    uint32_t n_pad;           /* padded matrix side (multiple of 256) */
+    int32_t status;           /* status of the last cfpq_solve */
+    int64_t kernel_launches;  /* kernels the last cfpq_solve ran (a graph's body counted per execution) */
+    int64_t product_launches; /* profile mode: product kernel launches timed */
+    double product_ms;        /* profile mode: summed device time of those launches */
+    double tensor_ms;         /* profile mode: the part of product_ms spent in tensor-core launches */
+    int64_t tensor_launches;  /* profile mode: tensor-core product launches timed */
+    double product_bytes;     /* profile mode: bytes the gather products read or wrote (rows
+                                 scanned, rows gathered, result rows merged) */
+} cfpq_stats;
+
+typedef struct cfpq_ctx cfpq_ctx;
+
+/* Fills *opt with the defaults. Errors: INVALID if opt is NULL. */
+int cfpq_options_default(cfpq_options *opt);
+
+/*
+ * Creates a context for one query: validates and copies the grammar and the edge list,
+ * allocates the bit-packed matrices in device memory (row-major, n_pad = n rounded up to
+ * a multiple of 256, bit j of row i in 32-bit word i * n_pad/32 + j/32 at bit j % 32),
+ * and uploads the edges. Uses the current CUDA device.
+ *   g       grammar; every id must be in range (INVALID otherwise)
+ *   n       number of nodes, 1..CFPQ_MAX_NODES
+ *   edges   host array of n_edges edges (may be NULL iff n_edges == 0)
+ *   opt     options, NULL for defaults
+ *   out     receives the context; untouched on error
+ * Errors: INVALID, NOMEM, CUDA, UNSUPPORTED.
+ */
+int cfpq_create(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
+                const cfpq_options *opt, cfpq_ctx **out);
+
+/*
+ * Runs Algorithm 1 on the device: matrix initialisation from the edges, then the
+ * closure loop until an iteration adds no pair. May be called again; each call starts
+ * from the edges. Blocks until the fixpoint is reached (or a limit hits).
+ *   stream  a cudaStream_t to run on, or NULL for the context's own stream
+ * Errors: ITER_LIMIT, TIMEOUT, CUDA, UNSUPPORTED. After ITER_LIMIT or TIMEOUT the partial
+ * closure is still readable with cfpq_get (it is a subset of the result).
+ */
+int cfpq_solve(cfpq_ctx *ctx, void *stream);
+
+/*
+ * Copies R_A as triples (A, m, n), sorted by (m, n), into buf (host memory). With
+ * buf == NULL only *count is set (the size query). Runs on the stream of the last
+ * cfpq_solve. Errors: INVALID (A out of range, count NULL), NOT_SOLVED, BUFFER (cap <
+ * count; *count still set), NOMEM, CUDA.
+ */
+int cfpq_get(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, size_t cap, size_t *count);
+
+/* As cfpq_get, but buf is device memory (cap triples) and nothing is copied to the host
+ * except the count. Errors: as cfpq_get. */
+int cfpq_get_device(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, size_t cap, size_t *count);
+
+/* |R_A| without copying pairs. Errors: as cfpq_get. */
+int cfpq_count(cfpq_ctx *ctx, int32_t A, size_t *count);
+
+/* Statistics of the last cfpq_solve. Errors: INVALID. */
+int cfpq_stats_get(const cfpq_ctx *ctx, cfpq_stats *out);
+
+/* Releases the context and its device memory; NULL is ignored. */
+void cfpq_destroy(cfpq_ctx *ctx);
+
+/* Static string naming a status code. */
+const char *cfpq_strerror(int code);
+
+/*
+ * Reads grammar text into the normal form: one production per line, "A B C", "A x" or
+ * "A eps", '#' starts a comment. A symbol is a non-terminal iff it is some line's
+ * left-hand side; every other symbol must be one of the n_labels terminal names
+ * (terminal id = position in labels). A terminal inside a binary production gets a
+ * preterminal named "<x>" with the production <x> -> x, as the paper rewrites its
+ * same-generation grammar into normal form (Section 4.3). Non-terminal ids: left-hand
+ * sides in order of first appearance, then preterminals in order of first use.
+ * On success *out owns its arrays; release it with cfpq_grammar_free.
+ * Errors: INVALID (syntax, unknown terminal, chain production A -> B, too many
+ * non-terminals); err (may be NULL, size errlen) receives a message.
+ */
+typedef struct cfpq_parsed_grammar cfpq_parsed_grammar;
+int cfpq_grammar_parse(const char *text, const char *const *labels, int32_t n_labels,
+                       cfpq_parsed_grammar **out, char *err, size_t errlen);
+/* The normal form inside a parsed grammar (valid until cfpq_grammar_free). */
+const cfpq_grammar_cnf *cfpq_grammar_cnf_of(const cfpq_parsed_grammar *pg);
+/* Name of non-terminal id (NULL if out of range). */
+const char *cfpq_grammar_name(const cfpq_parsed_grammar *pg, int32_t id);
+void cfpq_grammar_free(cfpq_parsed_grammar *pg);
+
+/*
+ * Batched solve (many independent queries, one persistent grouped launch): every
+ * context advances one loop iteration per round; a context whose iteration added no
+ * pair is retired (per-query convergence) while the others continue. Results are
+ * identical to solving each context alone. Each context keeps its own schedule and
+ * iteration cap; products always take the gather path inside the grouped launch, and
+ * timeouts are not applied. Errors: INVALID, NOMEM, CUDA, UNSUPPORTED (no cooperative
+ * launch), TIMEOUT (a bounded grid barrier gave up), ITER_LIMIT (some context hit its
+ * cap; the others are still complete).
+ */
+int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFPQ_H_ */

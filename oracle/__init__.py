@@ -260,6 +260,53 @@ def matrix_closure(graph, grammar_text: str, max_iter: int | None = None):
     return cnf, snaps, k
 
 
+def matrix_closure_sparse(graph, grammar_text: str, max_iter: int | None = None):
+    """Algorithm 1 as in ``matrix_closure`` but with sparse Boolean matrices (scipy CSR
+    products as the library primitive, the representation of the paper's sCPU variant),
+    for sizes where dense n x n products are too slow. Returns (cnf, T, k) with T the
+    final matrices and k the loop count."""
+    import scipy.sparse as sp
+
+    cnf = parse_grammar(grammar_text, graph.labels)
+    n = graph.n
+    heads = {}
+    for a, t in cnf.unary:
+        heads.setdefault(t, []).append(a)
+    rows = {a: [] for a in range(len(cnf.names))}
+    cols = {a: [] for a in range(len(cnf.names))}
+    for src, lab, dst in np.asarray(graph.edges, dtype=np.int64).reshape(-1, 3):
+        for a in heads.get(int(lab), []):
+            rows[a].append(int(src))
+            cols[a].append(int(dst))
+    for a in cnf.eps:
+        rows[a].extend(range(n))
+        cols[a].extend(range(n))
+
+    def mat(r, c):
+        m = sp.csr_matrix((np.ones(len(r), dtype=np.int64), (np.asarray(r, dtype=np.int64),
+                                                              np.asarray(c, dtype=np.int64))), shape=(n, n))
+        m.data[:] = 1
+        return m
+
+    T = {a: mat(rows[a], cols[a]) for a in rows}
+    k = 0
+    while True:
+        k += 1
+        new = {a: T[a].copy() for a in T}
+        for a, b, c in cnf.binary:
+            new[a] = new[a] + (T[b] @ T[c])
+        changed = False
+        for a in T:
+            new[a].data[:] = 1
+            new[a].eliminate_zeros()
+            if new[a].nnz != T[a].nnz:
+                changed = True
+        T = new
+        if not changed or (max_iter is not None and k >= max_iter):
+            break
+    return cnf, T, k
+
+
 # --------------------------------------------------------------------------------------
 # Brute force: walks + CYK (tiny inputs)
 # --------------------------------------------------------------------------------------

@@ -1,0 +1,250 @@
+"""B300 (sm_103a) engine for relational-semantics context-free path querying.
+
+Thin Python binding over the C ABI in ``include/cfpq.h`` (``libcfpq.so``): argument
+marshalling only; every step of the closure runs in the library's CUDA kernels. There is
+no CPU fallback: if the library is missing or has no device to run on, calls raise.
+
+    g = Grammar(text, labels)                 # normal form with preterminals (Section 4.3)
+    q = Query(g, n, edges)                    # edges: (E, 3) ints (src, label, dst)
+    q.solve()                                 # Algorithm 1 on the GPU
+    q.get("S")                                # R_S as a sorted (k, 2) uint32 array
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcfpq.so")
+
+OK, ERR_INVALID, ERR_NOMEM, ERR_NOT_SOLVED, ERR_ITER_LIMIT, ERR_TIMEOUT, ERR_CUDA, ERR_BUFFER, \
+    ERR_UNSUPPORTED = range(9)
+SCHED_INPLACE, SCHED_JACOBI = 0, 1
+PATH_AUTO, PATH_TENSOR, PATH_GATHER = 0, 1, 2
+
+
+class CfpqError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_lib().cfpq_strerror(code).decode()} (status {code})")
+        self.code = code
+
+
+class Rule1(ctypes.Structure):
+    _fields_ = [("lhs", ctypes.c_int32), ("term", ctypes.c_int32)]
+
+
+class Rule2(ctypes.Structure):
+    _fields_ = [("lhs", ctypes.c_int32), ("b", ctypes.c_int32), ("c", ctypes.c_int32)]
+
+
+class GrammarCNF(ctypes.Structure):
+    _fields_ = [("n_nonterm", ctypes.c_int32), ("n_term", ctypes.c_int32),
+                ("unary", ctypes.POINTER(Rule1)), ("n_unary", ctypes.c_int32),
+                ("binary", ctypes.POINTER(Rule2)), ("n_binary", ctypes.c_int32),
+                ("eps_lhs", ctypes.POINTER(ctypes.c_int32)), ("n_eps", ctypes.c_int32)]
+
+
+class Edge(ctypes.Structure):
+    _fields_ = [("src", ctypes.c_uint32), ("label", ctypes.c_int32), ("dst", ctypes.c_uint32)]
+
+
+class Triple(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_int32), ("m", ctypes.c_uint32), ("n", ctypes.c_uint32)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("path", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("timeout_s", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("new_bits", ctypes.c_int64), ("seed_bits", ctypes.c_int64),
+                ("tensor_products", ctypes.c_int64), ("gather_products", ctypes.c_int64),
+                ("dense_ops", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("n_pad", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64), ("product_launches", ctypes.c_int64),
+                ("product_ms", ctypes.c_double), ("tensor_ms", ctypes.c_double),
+                ("tensor_launches", ctypes.c_int64), ("product_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+
+_P, _VP = ctypes.POINTER, ctypes.c_void_p
+#: signature of every function ``include/cfpq.h`` declares
+SIGNATURES = {
+    "cfpq_options_default": (ctypes.c_int, [_P(Options)]),
+    "cfpq_create": (ctypes.c_int, [_P(GrammarCNF), ctypes.c_uint32, _P(Edge), ctypes.c_size_t, _P(Options),
+                                   _P(_VP)]),
+    "cfpq_solve": (ctypes.c_int, [_VP, _VP]),
+    "cfpq_get": (ctypes.c_int, [_VP, ctypes.c_int32, _P(Triple), ctypes.c_size_t, _P(ctypes.c_size_t)]),
+    "cfpq_get_device": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_size_t, _P(ctypes.c_size_t)]),
+    "cfpq_count": (ctypes.c_int, [_VP, ctypes.c_int32, _P(ctypes.c_size_t)]),
+    "cfpq_stats_get": (ctypes.c_int, [_VP, _P(Stats)]),
+    "cfpq_destroy": (None, [_VP]),
+    "cfpq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "cfpq_grammar_parse": (ctypes.c_int, [ctypes.c_char_p, _P(ctypes.c_char_p), ctypes.c_int32, _P(_VP),
+                                          ctypes.c_char_p, ctypes.c_size_t]),
+    "cfpq_grammar_cnf_of": (_P(GrammarCNF), [_VP]),
+    "cfpq_grammar_name": (ctypes.c_char_p, [_VP, ctypes.c_int32]),
+    "cfpq_grammar_free": (None, [_VP]),
+    "cfpq_solve_batch": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP]),
+}
+EXPORTS = sorted(SIGNATURES)
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA engine library not built: {LIB_PATH} "
+                               "(run `python -m paper_1707_01007_b300.build`)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype, f.argtypes = res, args
+        _LIB = lib
+    return _LIB
+
+
+def library():
+    """The loaded ``libcfpq.so`` (ctypes handle)."""
+    return _lib()
+
+
+def _check(code, what):
+    if code != OK:
+        raise CfpqError(code, what)
+
+
+class Grammar:
+    """A grammar read by the library's own reader (``cfpq_grammar_parse``)."""
+
+    def __init__(self, text: str, labels):
+        self.labels = list(labels)
+        arr = (ctypes.c_char_p * max(1, len(self.labels)))(*[s.encode() for s in self.labels])
+        h = ctypes.c_void_p()
+        err = ctypes.create_string_buffer(256)
+        code = _lib().cfpq_grammar_parse(text.encode(), arr, len(self.labels), ctypes.byref(h), err, 256)
+        if code != OK:
+            raise ValueError(f"grammar rejected: {err.value.decode()}")
+        self._h = h
+        self.cnf = _lib().cfpq_grammar_cnf_of(h)
+        self.names = [_lib().cfpq_grammar_name(h, i).decode() for i in range(self.cnf.contents.n_nonterm)]
+
+    def id(self, name: str) -> int:
+        return self.names.index(name)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _LIB is not None:
+            _LIB.cfpq_grammar_free(h)
+            self._h = None
+
+
+def _edges_struct(edges):
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int64).reshape(-1, 3))
+    rec = np.empty(e.shape[0], dtype=[("src", "<u4"), ("label", "<i4"), ("dst", "<u4")])
+    rec["src"], rec["label"], rec["dst"] = e[:, 0], e[:, 1], e[:, 2]
+    return rec
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(int(stream.cuda_stream))  # torch.cuda.Stream
+
+
+class Query:
+    """One CFPQ query (graph + grammar) resident on the device (``cfpq_create``)."""
+
+    def __init__(self, grammar: Grammar, n: int, edges, schedule: int = SCHED_INPLACE, path: int = PATH_AUTO,
+                 use_graph: bool = True, max_iter: int = 0, timeout_s: float = 0.0, profile: bool = False):
+        self.grammar = grammar
+        self.n = int(n)
+        self._h = None
+        opt = Options()
+        _lib().cfpq_options_default(ctypes.byref(opt))
+        opt.schedule, opt.path, opt.use_graph = schedule, path, int(bool(use_graph))
+        opt.profile = int(bool(profile))
+        opt.max_iter, opt.timeout_s = int(max_iter), float(timeout_s)
+        rec = _edges_struct(edges)
+        h = ctypes.c_void_p()
+        ptr = rec.ctypes.data_as(ctypes.POINTER(Edge)) if rec.size else None
+        code = _lib().cfpq_create(grammar.cnf, self.n, ptr, rec.size, ctypes.byref(opt), ctypes.byref(h))
+        _check(code, "cfpq_create")
+        self._h = h
+        self.status = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def solve(self, stream=None, check: bool = True) -> int:
+        code = _lib().cfpq_solve(self._h, _stream_handle(stream))
+        self.status = code
+        if check:
+            _check(code, "cfpq_solve")
+        return code
+
+    def _aid(self, A):
+        return self.grammar.id(A) if isinstance(A, str) else int(A)
+
+    def count(self, A) -> int:
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_count(self._h, self._aid(A), ctypes.byref(c)), "cfpq_count")
+        return int(c.value)
+
+    def triples(self, A) -> np.ndarray:
+        """R_A as an (k, 3) int64 array of (A, m, n) triples, sorted by (m, n)."""
+        a = self._aid(A)
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_get(self._h, a, None, 0, ctypes.byref(c)), "cfpq_get")
+        k = int(c.value)
+        buf = np.zeros(max(k, 1), dtype=[("A", "<i4"), ("m", "<u4"), ("n", "<u4")])
+        _check(_lib().cfpq_get(self._h, a, buf.ctypes.data_as(ctypes.POINTER(Triple)), k, ctypes.byref(c)),
+               "cfpq_get")
+        buf = buf[:k]
+        return np.stack([buf["A"].astype(np.int64), buf["m"].astype(np.int64), buf["n"].astype(np.int64)], axis=1)
+
+    def get(self, A) -> np.ndarray:
+        """R_A as a sorted (k, 2) uint32 array of (m, n)."""
+        return self.triples(A)[:, 1:].astype(np.uint32)
+
+    def get_device(self, A, dev_ptr: int, cap: int) -> int:
+        """Writes R_A as triples into device memory at dev_ptr (cap triples); returns |R_A|."""
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_get_device(self._h, self._aid(A), ctypes.c_void_p(dev_ptr), cap, ctypes.byref(c)),
+               "cfpq_get_device")
+        return int(c.value)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(_lib().cfpq_stats_get(self._h, ctypes.byref(s)), "cfpq_stats_get")
+        return s.as_dict()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and _LIB is not None:
+            _LIB.cfpq_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def solve_batch(queries, stream=None, check: bool = True) -> int:
+    """Solves many queries in one grouped persistent launch (``cfpq_solve_batch``)."""
+    arr = (ctypes.c_void_p * len(queries))(*[q.handle.value for q in queries])
+    code = _lib().cfpq_solve_batch(arr, len(queries), _stream_handle(stream))
+    for q in queries:
+        q.status = code
+    if check:
+        _check(code, "cfpq_solve_batch")
+    return code

@@ -1,0 +1,629 @@
+// C ABI of the CFPQ engine: contexts, the fixpoint loop of Algorithm 1 (Section 4.2) as a
+// CUDA graph with a conditional while node, and result extraction (R_A, Section 2).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "cfpq_device.cuh"
+#include "cfpq_internal.h"
+
+namespace cfpq {
+
+// ------------------------------------------------------------------------------------
+// Kernels (thin wrappers over the device functions of cfpq_device.cuh)
+// ------------------------------------------------------------------------------------
+
+__global__ void k_seed(const QDesc *qd) {
+    const QDesc q = *qd;
+    seed_query(q, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+}
+
+template <int CPL>
+__global__ void __launch_bounds__(256) k_gather(const QDesc *qd, int g, uint32_t n_chunks) {
+    const QDesc &q = *qd;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint64_t total = (uint64_t)q.n * n_chunks;
+    if (warp == 0 && lane == 0 && q.st->use_tensor[g] == 0)
+        atomicAdd(&q.st->gather_products, (unsigned long long)(q.gstart[g + 1] - q.gstart[g]));
+    if (warp >= total || q.st->use_tensor[g]) return;
+    const uint32_t i = (uint32_t)(warp / n_chunks);
+    const uint32_t ch = (uint32_t)(warp % n_chunks);
+    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
+    gather_row_chunk<CPL>(q, g, i, ch, lane, parity);
+}
+
+__global__ void k_merge(const QDesc *qd) {
+    const QDesc &q = *qd;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= (uint64_t)q.n_nt * q.n) return;
+    merge_row(q, (int)(warp / q.n), (uint32_t)(warp % q.n), lane, (uint32_t)(q.st->iter & 1ull));
+}
+
+__global__ void k_clear(const QDesc *qd) {
+    const QDesc &q = *qd;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= (uint64_t)q.n_nt * q.n) return;
+    clear_row(q, (int)(warp / q.n), (uint32_t)(warp % q.n), lane, (uint32_t)(q.st->iter & 1ull));
+}
+
+__global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle) {
+    const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, cont);
+}
+
+__global__ void k_arm_deadline(DevState *st, unsigned long long dt_ns) { st->deadline_ns = globaltimer_ns() + dt_ns; }
+
+// --- extraction: popc per row -> exclusive scan -> emit (A, m, n) in row-major order ---
+
+__global__ void k_count_rows(const QDesc *qd, int a, uint32_t *counts) {
+    const QDesc &q = *qd;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= q.n_pad) return;
+    const uint32_t *row = q.T + (uint64_t)a * q.plane + warp * q.W;
+    uint32_t c = 0;
+    if (test_bit(q.Trow + (uint64_t)a * q.W, (uint32_t)warp))
+        for (uint32_t w = lane; w < q.W; w += 32) c += __popc(row[w]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) counts[warp] = c;
+}
+
+// one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t *counts, uint64_t *offsets, uint32_t n,
+                                               unsigned long long *total) {
+    __shared__ unsigned long long part[1024];
+    const uint32_t per = (n + 1023) / 1024;
+    const uint32_t lo = threadIdx.x * per, hi = min(n, lo + per);
+    unsigned long long s = 0;
+    for (uint32_t i = lo; i < hi; i++) s += counts[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned long long v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = part[threadIdx.x] - s;  // exclusive prefix of this segment
+    for (uint32_t i = lo; i < hi; i++) {
+        offsets[i] = run;
+        run += counts[i];
+    }
+    if (threadIdx.x == 1023) *total = part[1023];
+}
+
+__global__ void k_emit(const QDesc *qd, int a, const uint64_t *offsets, const uint32_t *counts,
+                       cfpq_triple *out) {
+    const QDesc &q = *qd;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= q.n_pad || counts[warp] == 0) return;
+    const uint32_t *row = q.T + (uint64_t)a * q.plane + warp * q.W;
+    uint64_t off = offsets[warp];
+    for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
+        uint32_t x = (w0 + lane < q.W) ? row[w0 + lane] : 0u;
+        const uint32_t c = __popc(x);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        uint64_t pos = off + incl - c;
+        while (x) {
+            const uint32_t j = (w0 + lane) * 32u + (uint32_t)(__ffs(x) - 1);
+            x &= x - 1;
+            out[pos++] = cfpq_triple{a, (uint32_t)warp, j};
+        }
+        off += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
+}  // namespace cfpq
+
+using namespace cfpq;
+
+// ------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------
+
+static void note_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    if (getenv("CFPQ_VERBOSE")) fprintf(stderr, "cfpq: %s failed: %s (%s:%d)\n", what, cudaGetErrorString(e), file, line);
+}
+
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) {                               \
+            note_cuda_error(e_, #call, __FILE__, __LINE__);    \
+            return CFPQ_ERR_CUDA;                              \
+        }                                                      \
+    } while (0)
+
+extern "C" const char *cfpq_strerror(int code) {
+    switch (code) {
+        case CFPQ_OK: return "ok";
+        case CFPQ_ERR_INVALID: return "invalid argument";
+        case CFPQ_ERR_NOMEM: return "out of memory";
+        case CFPQ_ERR_NOT_SOLVED: return "not solved";
+        case CFPQ_ERR_ITER_LIMIT: return "iteration limit reached";
+        case CFPQ_ERR_TIMEOUT: return "timeout";
+        case CFPQ_ERR_CUDA: return "CUDA error";
+        case CFPQ_ERR_BUFFER: return "buffer too small";
+        case CFPQ_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int cfpq_options_default(cfpq_options *opt) {
+    if (!opt) return CFPQ_ERR_INVALID;
+    memset(opt, 0, sizeof(*opt));
+    opt->schedule = CFPQ_SCHED_INPLACE;
+    opt->path = CFPQ_PATH_AUTO;
+    opt->use_graph = 1;
+    opt->profile = 0;
+    opt->max_iter = 0;
+    opt->timeout_s = 0.0;
+    return CFPQ_OK;
+}
+
+namespace cfpq {
+
+uint32_t gather_chunks(uint32_t W, int *cpl) {
+    if (W <= 32) { *cpl = 1; return 1; }
+    if (W <= 64) { *cpl = 2; return 1; }
+    if (W <= 128) { *cpl = 4; return 1; }
+    *cpl = 8;
+    return (W + 255) / 256;
+}
+
+void launch_gather(cfpq_ctx *c, int g, cudaStream_t s) {
+    int cpl;
+    const uint32_t nch = gather_chunks(c->W, &cpl);
+    const uint64_t warps = (uint64_t)c->n * nch;
+    const uint32_t blocks = (uint32_t)((warps * 32 + 255) / 256);
+    switch (cpl) {
+        case 1: k_gather<1><<<blocks, 256, 0, s>>>(c->d_q, g, nch); break;
+        case 2: k_gather<2><<<blocks, 256, 0, s>>>(c->d_q, g, nch); break;
+        case 4: k_gather<4><<<blocks, 256, 0, s>>>(c->d_q, g, nch); break;
+        default: k_gather<8><<<blocks, 256, 0, s>>>(c->d_q, g, nch); break;
+    }
+}
+
+static uint32_t row_warp_blocks(uint64_t rows) { return (uint32_t)((rows * 32 + 255) / 256); }
+
+// One loop execution (the body of Algorithm 1's while loop).
+int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
+    c->iter_launches = 0;
+    const bool prof = c->profile && !use_handle;
+    for (int g = 0; g < c->n_groups; g++) {
+        if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
+        if (c->group_tensor[g]) {
+            const int rc = enqueue_tensor_group(c, g, s);
+            if (rc != CFPQ_OK) return rc;
+        } else {
+            launch_gather(c, g, s);
+            c->iter_launches++;
+        }
+        if (prof) CK(cudaEventRecord(c->prof_ev[2 * g + 1], s));
+    }
+    if (c->schedule == CFPQ_SCHED_JACOBI) {
+        k_merge<<<row_warp_blocks((uint64_t)c->n_nt * c->n), 256, 0, s>>>(c->d_q);
+        c->iter_launches++;
+    }
+    k_clear<<<row_warp_blocks((uint64_t)c->n_nt * c->n), 256, 0, s>>>(c->d_q);
+    k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle);
+    c->iter_launches += 2;
+    CK(cudaGetLastError());
+    return CFPQ_OK;
+}
+
+// profile mode: adds the product launches of the iteration just synchronised
+static int collect_profile(cfpq_ctx *c) {
+    for (int g = 0; g < c->n_groups; g++) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * g], c->prof_ev[2 * g + 1]));
+        c->stats.product_ms += ms;
+        c->stats.product_launches++;
+        if (c->group_tensor[g]) {
+            c->stats.tensor_ms += ms;
+            c->stats.tensor_launches++;
+        }
+    }
+    return CFPQ_OK;
+}
+
+static int build_graph(cfpq_ctx *c) {
+    if (c->graph_exec) return CFPQ_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "handle", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "addnode", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "capture", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
+    const int rc = enqueue_iteration(c, c->stream, h, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(c->stream, &captured);
+    if (rc != CFPQ_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) note_cuda_error(e, "endcapture", __FILE__, __LINE__);
+        return rc != CFPQ_OK ? rc : CFPQ_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { c->graph_exec = nullptr; note_cuda_error(e, "instantiate", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
+    return CFPQ_OK;
+}
+
+void free_ctx_device(cfpq_ctx *c) {
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+    void *ptrs[] = {c->d_T, c->d_TT, c->d_X0, c->d_X1, c->d_R0, c->d_R1, c->d_Trow, c->d_rules, c->d_gstart,
+                    c->d_unary, c->d_eps, c->d_edges, c->d_state, c->d_q, c->d_counts, c->d_offsets,
+                    c->d_total, c->d_triples, c->d_tc_work};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto e : c->prof_ev)
+        if (e) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);
+}
+
+void arm_deadline(cfpq_ctx *c, cudaStream_t s) {
+    k_arm_deadline<<<1, 1, 0, s>>>(c->d_state, (unsigned long long)(c->timeout_s * 1e9));
+}
+
+// Clears the matrices and seeds them from the edges (Algorithm 1's initialisation).
+int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
+    const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
+    const size_t rows = (size_t)c->n_nt * c->W * sizeof(uint32_t);
+    CK(cudaMemsetAsync(c->d_T, 0, planes, s));
+    CK(cudaMemsetAsync(c->d_X0, 0, planes, s));
+    CK(cudaMemsetAsync(c->d_X1, 0, planes, s));
+    CK(cudaMemsetAsync(c->d_R0, 0, rows, s));
+    CK(cudaMemsetAsync(c->d_R1, 0, rows, s));
+    CK(cudaMemsetAsync(c->d_Trow, 0, rows, s));
+    DevState st0;
+    memset(&st0, 0, sizeof(st0));
+    st0.max_iter = c->max_iter;
+    for (int a = 0; a < c->n_nt; a++) st0.dirty[a] = 1u;
+    for (int g = 0; g < c->n_groups && g < kMaxNT; g++) st0.use_tensor[g] = c->group_tensor[g] ? 1u : 0u;
+    CK(cudaMemcpyAsync(c->d_state, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+    c->fixed_launches = 1;
+    if (c->timeout_s > 0) {
+        arm_deadline(c, s);
+        c->fixed_launches++;
+    }
+    const uint64_t work = std::max<uint64_t>(c->n_edges, (uint64_t)c->n_eps_rules * c->n);
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (work + 255) / 256), 148ull * 16);
+    k_seed<<<blocks, 256, 0, s>>>(c->d_q);
+    CK(cudaGetLastError());
+    return CFPQ_OK;
+}
+
+int read_status(cfpq_ctx *c, cudaStream_t s) {
+    DevState st;
+    CK(cudaMemcpyAsync(&st, c->d_state, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->stats.iterations = (int64_t)st.iter;
+    c->stats.new_bits = (int64_t)st.new_bits;
+    c->stats.seed_bits = (int64_t)st.seed_bits;
+    c->stats.tensor_products = (int64_t)st.tensor_products;
+    c->stats.gather_products = (int64_t)st.gather_products;
+    c->stats.dense_ops = 2.0 * (double)c->n_pad * (double)c->n_pad * (double)c->n_pad * (double)st.tensor_products;
+    c->stats.n_pad = c->n_pad;
+    c->stats.kernel_launches = c->fixed_launches + (int64_t)st.iter * c->iter_launches;
+    c->stats.product_bytes = 4.0 * (double)st.prof_words;
+    int rc = CFPQ_OK;
+    if (st.error == kErrIterLimit) rc = CFPQ_ERR_ITER_LIMIT;
+    else if (st.error == kErrTimeout) rc = CFPQ_ERR_TIMEOUT;
+    c->stats.status = rc;
+    return rc;
+}
+
+int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
+             const cfpq_options &o) {
+    c->n = n;
+    c->n_pad = (n + 255u) / 256u * 256u;
+    c->W = c->n_pad / 32u;
+    c->plane = (uint64_t)c->n_pad * c->W;
+    c->n_nt = g->n_nonterm;
+    c->n_term = g->n_term;
+    c->schedule = o.schedule;
+    c->path = o.path;
+    c->use_graph = o.use_graph;
+    c->profile = o.profile;
+    c->timeout_s = o.timeout_s;
+    const double bound = (double)n * (double)n * (double)g->n_nonterm + 1.0;
+    c->max_iter = o.max_iter > 0 ? (uint64_t)o.max_iter : (bound > 1.8e19 ? ~0ull : (uint64_t)bound);
+    // productions: dedupe, group by left-hand side
+    std::vector<Rule> rules;
+    for (int i = 0; i < g->n_binary; i++) rules.push_back({g->binary[i].lhs, g->binary[i].b, g->binary[i].c, 0});
+    std::sort(rules.begin(), rules.end(), [](const Rule &x, const Rule &y) {
+        if (x.lhs != y.lhs) return x.lhs < y.lhs;
+        if (x.b != y.b) return x.b < y.b;
+        return x.c < y.c;
+    });
+    rules.erase(std::unique(rules.begin(), rules.end(),
+                            [](const Rule &x, const Rule &y) { return x.lhs == y.lhs && x.b == y.b && x.c == y.c; }),
+                rules.end());
+    std::vector<int32_t> gstart;
+    for (size_t i = 0; i < rules.size(); i++)
+        if (i == 0 || rules[i].lhs != rules[i - 1].lhs) gstart.push_back((int32_t)i);
+    gstart.push_back((int32_t)rules.size());
+    c->n_groups = (int)gstart.size() - 1;
+    c->rules = rules;
+    c->gstart = gstart;
+    std::vector<int2> unary;
+    for (int i = 0; i < g->n_unary; i++) unary.push_back(make_int2(g->unary[i].lhs, g->unary[i].term));
+    std::vector<int32_t> eps(g->eps_lhs, g->eps_lhs + g->n_eps);
+    std::sort(eps.begin(), eps.end());
+    eps.erase(std::unique(eps.begin(), eps.end()), eps.end());
+    c->n_unary = (int)unary.size();
+    c->n_eps_rules = (int)eps.size();
+    c->n_edges = n_edges;
+    c->group_tensor.assign(std::max(1, c->n_groups), 0);
+    if (c->path == CFPQ_PATH_TENSOR) {
+        if (!tensor_path_available()) return CFPQ_ERR_UNSUPPORTED;
+        c->group_tensor.assign(std::max(1, c->n_groups), 1);
+    }
+
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+    c->last_stream = c->stream;
+    CK(cudaEventCreate(&c->ev0));
+    CK(cudaEventCreate(&c->ev1));
+    if (c->profile) {
+        c->prof_ev.assign(2 * std::max(1, c->n_groups), nullptr);
+        for (auto &e : c->prof_ev) CK(cudaEventCreate(&e));
+    }
+    const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
+    const size_t rowsz = (size_t)c->n_nt * c->W * sizeof(uint32_t);
+    auto alloc = [&](void **p, size_t bytes) -> int {
+        const cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); *p = nullptr; return CFPQ_ERR_NOMEM; }
+        if (e != cudaSuccess) { *p = nullptr; return CFPQ_ERR_CUDA; }
+        return CFPQ_OK;
+    };
+    int rc;
+    if ((rc = alloc((void **)&c->d_T, planes))) return rc;
+    if ((rc = alloc((void **)&c->d_X0, planes))) return rc;
+    if ((rc = alloc((void **)&c->d_X1, planes))) return rc;
+    if ((rc = alloc((void **)&c->d_R0, rowsz))) return rc;
+    if ((rc = alloc((void **)&c->d_R1, rowsz))) return rc;
+    if ((rc = alloc((void **)&c->d_Trow, rowsz))) return rc;
+    if (c->path != CFPQ_PATH_GATHER && tensor_path_available()) {
+        if ((rc = alloc((void **)&c->d_TT, planes))) return rc;
+    }
+    if ((rc = alloc((void **)&c->d_rules, rules.size() * sizeof(Rule)))) return rc;
+    if ((rc = alloc((void **)&c->d_gstart, gstart.size() * sizeof(int32_t)))) return rc;
+    if ((rc = alloc((void **)&c->d_unary, unary.size() * sizeof(int2)))) return rc;
+    if ((rc = alloc((void **)&c->d_eps, eps.size() * sizeof(int32_t)))) return rc;
+    if ((rc = alloc((void **)&c->d_edges, n_edges * sizeof(cfpq_edge)))) return rc;
+    if ((rc = alloc((void **)&c->d_state, sizeof(DevState)))) return rc;
+    if ((rc = alloc((void **)&c->d_q, sizeof(QDesc)))) return rc;
+    if ((rc = alloc((void **)&c->d_counts, c->n_pad * sizeof(uint32_t)))) return rc;
+    if ((rc = alloc((void **)&c->d_offsets, c->n_pad * sizeof(uint64_t)))) return rc;
+    if ((rc = alloc((void **)&c->d_total, sizeof(unsigned long long)))) return rc;
+    if (!rules.empty()) CK(cudaMemcpy(c->d_rules, rules.data(), rules.size() * sizeof(Rule), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_gstart, gstart.data(), gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!unary.empty()) CK(cudaMemcpy(c->d_unary, unary.data(), unary.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    if (!eps.empty()) CK(cudaMemcpy(c->d_eps, eps.data(), eps.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (n_edges) CK(cudaMemcpy(c->d_edges, edges, n_edges * sizeof(cfpq_edge), cudaMemcpyHostToDevice));
+    QDesc q;
+    memset(&q, 0, sizeof(q));
+    q.n = n;
+    q.n_pad = c->n_pad;
+    q.W = c->W;
+    q.n_nt = c->n_nt;
+    q.n_rules = (int32_t)rules.size();
+    q.n_groups = c->n_groups;
+    q.schedule = c->schedule;
+    q.profile = c->profile;
+    q.n_unary = c->n_unary;
+    q.n_eps = c->n_eps_rules;
+    q.plane = c->plane;
+    q.n_edges = n_edges;
+    q.T = c->d_T;
+    q.TT = c->d_TT;
+    q.X0 = c->d_X0;
+    q.X1 = c->d_X1;
+    q.R0 = c->d_R0;
+    q.R1 = c->d_R1;
+    q.Trow = c->d_Trow;
+    q.rules = c->d_rules;
+    q.gstart = c->d_gstart;
+    q.unary = c->d_unary;
+    q.eps = c->d_eps;
+    q.edges = c->d_edges;
+    q.st = c->d_state;
+    c->hq = q;
+    CK(cudaMemcpy(c->d_q, &q, sizeof(q), cudaMemcpyHostToDevice));
+    return CFPQ_OK;
+}
+
+int run_loop(cfpq_ctx *c, cudaStream_t s) {
+    if (c->n_groups == 0) {
+        // no binary productions: one execution of the loop body finds nothing new
+        k_tail<<<1, 1024, 0, s>>>(c->d_q, 0, 0);
+        c->iter_launches = 1;
+        CK(cudaGetLastError());
+        return CFPQ_OK;
+    }
+    if (c->use_graph && !c->profile) {
+        const int rc = build_graph(c);
+        if (rc != CFPQ_OK) return rc;
+        CK(cudaGraphLaunch(c->graph_exec, s));
+        return CFPQ_OK;
+    }
+    for (;;) {
+        int rc = enqueue_iteration(c, s, 0, 0);
+        if (rc != CFPQ_OK) return rc;
+        unsigned cont = 0;
+        CK(cudaMemcpyAsync(&cont, &c->d_state->cont, sizeof(cont), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (c->profile && (rc = collect_profile(c)) != CFPQ_OK) return rc;
+        if (!cont) break;
+    }
+    return CFPQ_OK;
+}
+
+static int count_rows_and_scan(cfpq_ctx *c, int32_t A, cudaStream_t s, unsigned long long *total) {
+    k_count_rows<<<row_warp_blocks(c->n_pad), 256, 0, s>>>(c->d_q, A, c->d_counts);
+    k_scan<<<1, 1024, 0, s>>>(c->d_counts, c->d_offsets, c->n_pad, c->d_total);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(total, c->d_total, sizeof(*total), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return CFPQ_OK;
+}
+
+static int emit(cfpq_ctx *c, int32_t A, cfpq_triple *dev_out, cudaStream_t s) {
+    k_emit<<<row_warp_blocks(c->n_pad), 256, 0, s>>>(c->d_q, A, c->d_offsets, c->d_counts, dev_out);
+    CK(cudaGetLastError());
+    return CFPQ_OK;
+}
+
+}  // namespace cfpq
+
+extern "C" int cfpq_create(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
+                           const cfpq_options *opt, cfpq_ctx **out) {
+    if (!g || !out || n == 0 || n > CFPQ_MAX_NODES) return CFPQ_ERR_INVALID;
+    if (g->n_nonterm <= 0 || g->n_nonterm > CFPQ_MAX_NONTERM || g->n_term < 0) return CFPQ_ERR_INVALID;
+    if (g->n_unary < 0 || g->n_binary < 0 || g->n_eps < 0) return CFPQ_ERR_INVALID;
+    if ((g->n_unary > 0 && !g->unary) || (g->n_binary > 0 && !g->binary) || (g->n_eps > 0 && !g->eps_lhs))
+        return CFPQ_ERR_INVALID;
+    if (n_edges > 0 && !edges) return CFPQ_ERR_INVALID;
+    for (int i = 0; i < g->n_unary; i++)
+        if (g->unary[i].lhs < 0 || g->unary[i].lhs >= g->n_nonterm || g->unary[i].term < 0 ||
+            g->unary[i].term >= g->n_term)
+            return CFPQ_ERR_INVALID;
+    for (int i = 0; i < g->n_binary; i++) {
+        const cfpq_rule2 r = g->binary[i];
+        if (r.lhs < 0 || r.lhs >= g->n_nonterm || r.b < 0 || r.b >= g->n_nonterm || r.c < 0 || r.c >= g->n_nonterm)
+            return CFPQ_ERR_INVALID;
+    }
+    for (int i = 0; i < g->n_eps; i++)
+        if (g->eps_lhs[i] < 0 || g->eps_lhs[i] >= g->n_nonterm) return CFPQ_ERR_INVALID;
+    for (size_t e = 0; e < n_edges; e++)
+        if (edges[e].src >= n || edges[e].dst >= n || edges[e].label < 0 || edges[e].label >= g->n_term)
+            return CFPQ_ERR_INVALID;
+    cfpq_options o;
+    cfpq_options_default(&o);
+    if (opt) o = *opt;
+    if (o.schedule != CFPQ_SCHED_INPLACE && o.schedule != CFPQ_SCHED_JACOBI) return CFPQ_ERR_INVALID;
+    if (o.path < CFPQ_PATH_AUTO || o.path > CFPQ_PATH_GATHER) return CFPQ_ERR_INVALID;
+
+    cfpq_ctx *c = new (std::nothrow) cfpq_ctx();
+    if (!c) return CFPQ_ERR_NOMEM;
+    const int rc = ctx_init(c, g, n, edges, n_edges, o);
+    if (rc != CFPQ_OK) {
+        free_ctx_device(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
+    if (!c) return CFPQ_ERR_INVALID;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    c->solved = false;
+    c->last_stream = s;
+    c->stats.product_ms = c->stats.tensor_ms = 0.0;
+    c->stats.product_launches = c->stats.tensor_launches = 0;
+    CK(cudaEventRecord(c->ev0, s));
+    int rc = enqueue_reset_and_seed(c, s);
+    if (rc != CFPQ_OK) return rc;
+    rc = run_loop(c, s);
+    if (rc != CFPQ_OK) return rc;
+    CK(cudaEventRecord(c->ev1, s));
+    rc = read_status(c, s);
+    if (rc == CFPQ_ERR_CUDA) return rc;
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    c->stats.solve_ms = ms;
+    c->solved = true;
+    return rc;
+}
+
+extern "C" int cfpq_count(cfpq_ctx *c, int32_t A, size_t *count) {
+    if (!c || !count || A < 0 || A >= c->n_nt) return CFPQ_ERR_INVALID;
+    if (!c->solved) return CFPQ_ERR_NOT_SOLVED;
+    unsigned long long total = 0;
+    const int rc = count_rows_and_scan(c, A, c->last_stream, &total);
+    if (rc != CFPQ_OK) return rc;
+    *count = (size_t)total;
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_get_device(cfpq_ctx *c, int32_t A, cfpq_triple *buf, size_t cap, size_t *count) {
+    if (!c || !count || A < 0 || A >= c->n_nt) return CFPQ_ERR_INVALID;
+    if (!c->solved) return CFPQ_ERR_NOT_SOLVED;
+    cudaStream_t s = c->last_stream;
+    unsigned long long total = 0;
+    const int rc = count_rows_and_scan(c, A, s, &total);
+    if (rc != CFPQ_OK) return rc;
+    *count = (size_t)total;
+    if (!buf) return CFPQ_OK;
+    if (cap < total) return CFPQ_ERR_BUFFER;
+    if (total == 0) return CFPQ_OK;
+    return emit(c, A, buf, s);
+}
+
+extern "C" int cfpq_get(cfpq_ctx *c, int32_t A, cfpq_triple *buf, size_t cap, size_t *count) {
+    if (!c || !count || A < 0 || A >= c->n_nt) return CFPQ_ERR_INVALID;
+    if (!c->solved) return CFPQ_ERR_NOT_SOLVED;
+    cudaStream_t s = c->last_stream;
+    unsigned long long total = 0;
+    int rc = count_rows_and_scan(c, A, s, &total);
+    if (rc != CFPQ_OK) return rc;
+    *count = (size_t)total;
+    if (!buf) return CFPQ_OK;
+    if (cap < total) return CFPQ_ERR_BUFFER;
+    if (total == 0) return CFPQ_OK;
+    if (c->triples_cap < total) {
+        if (c->d_triples) cudaFree(c->d_triples);
+        c->d_triples = nullptr;
+        c->triples_cap = 0;
+        const cudaError_t e = cudaMalloc(&c->d_triples, total * sizeof(cfpq_triple));
+        if (e != cudaSuccess) { cudaGetLastError(); c->d_triples = nullptr; return CFPQ_ERR_NOMEM; }
+        c->triples_cap = total;
+    }
+    if ((rc = emit(c, A, c->d_triples, s)) != CFPQ_OK) return rc;
+    CK(cudaMemcpyAsync(buf, c->d_triples, total * sizeof(cfpq_triple), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_stats_get(const cfpq_ctx *c, cfpq_stats *out) {
+    if (!c || !out) return CFPQ_ERR_INVALID;
+    *out = c->stats;
+    return CFPQ_OK;
+}
+
+extern "C" void cfpq_destroy(cfpq_ctx *c) {
+    if (!c) return;
+    free_ctx_device(c);
+    delete c;
+}

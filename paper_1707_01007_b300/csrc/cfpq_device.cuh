@@ -1,0 +1,285 @@
+// Device-side state and CUDA-core kernels of the CFPQ closure (Algorithm 1, Section 4.2).
+//
+// Layout in HBM (one query): for every non-terminal A, a bit-packed n_pad x n_pad matrix,
+// row-major, 32-bit words, bit j of row i at word i*W + j/32, bit j%32 (W = n_pad/32):
+//   T[A]      the current closure T_A
+//   X[p][A]   p = 0, 1: the two delta planes; in iteration `it`, X[it&1] holds the pairs
+//             added by the previous iteration (D, read by the semi-naive products) and
+//             X[(it+1)&1] collects the pairs added now (N)
+//   R[p][A]   row bitmaps of X[p][A] (bit i set iff row i of X[p][A] may be non-zero)
+//   Trow[A]   row bitmap of T[A] (bit i set iff row i of T[A] is non-empty)
+//   TT[A]     T_A transposed, refreshed before tensor-core products that read it
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cfpq.h"
+
+namespace cfpq {
+
+constexpr int kMaxNT = CFPQ_MAX_NONTERM;
+
+enum : uint32_t { kErrNone = 0, kErrIterLimit = 1, kErrTimeout = 2 };
+
+// Per-query device state; one instance in device memory per context.
+struct DevState {
+    unsigned long long iter;            // loop executions completed
+    unsigned long long max_iter;
+    unsigned long long deadline_ns;     // %globaltimer deadline, 0 = none
+    unsigned long long new_bits;
+    unsigned long long seed_bits;
+    unsigned long long tensor_products;
+    unsigned long long gather_products;
+    unsigned int changed;               // set by any product that added a pair this iteration
+    unsigned int error;
+    unsigned int done;                  // loop ended (converged or error)
+    unsigned int cont;                  // loop condition written by the tail
+    unsigned int dirty[kMaxNT];         // T[A] changed since TT[A] was rebuilt
+    unsigned long long dcount[2][kMaxNT];  // pairs in X[p][A]
+    unsigned int use_tensor[kMaxNT];    // AUTO path: per group, 1 = tensor product this iteration
+    unsigned long long prof_words;      // profile mode: 32-bit words the gather products read or wrote
+};
+
+struct Rule {
+    int32_t lhs, b, c, pad;
+};
+
+// Everything a kernel needs about one query; lives in device memory.
+struct QDesc {
+    uint32_t n, n_pad, W;
+    int32_t n_nt, n_rules, n_groups, schedule, n_unary, n_eps;
+    int32_t profile, pad0;
+    uint64_t plane;                     // words per matrix = n_pad * W
+    uint64_t n_edges;
+    uint32_t *T, *TT, *X0, *X1, *R0, *R1, *Trow;
+    const Rule *rules;                  // sorted by lhs; group g = rules[gstart[g] .. gstart[g+1])
+    const int32_t *gstart;
+    const int2 *unary;                  // (lhs, term)
+    const int32_t *eps;
+    const cfpq_edge *edges;
+    DevState *st;
+};
+
+// Mutable state is read with ld.global.cg (L2, not L1): the persistent batched kernel
+// reads, after a grid barrier, words that other SMs wrote in an earlier phase.
+__device__ __forceinline__ bool test_bit(const uint32_t *bm, uint32_t i) {
+    return (__ldcg(bm + (i >> 5)) >> (i & 31)) & 1u;
+}
+
+__device__ __forceinline__ unsigned long long ld_u64(const unsigned long long *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned ld_u32(const unsigned *p) { return __ldcg(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------------------------------
+// Matrix initialisation (Algorithm 1, before the loop): T_ij gets {A | A -> x} for each
+// edge (i, x, j); A -> eps adds (m, m). Every seeded pair is also a delta pair of
+// iteration 0 so that the first semi-naive iteration joins everything with everything.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void seed_pair(const QDesc &q, int a, uint32_t i, uint32_t j,
+                                          unsigned long long *cnt) {
+    const uint64_t w = (uint64_t)a * q.plane + (uint64_t)i * q.W + (j >> 5);
+    const uint32_t bit = 1u << (j & 31);
+    const uint32_t old = atomicOr(&q.T[w], bit);
+    if (!(old & bit)) {
+        atomicOr(&q.X0[w], bit);
+        atomicOr(&q.R0[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
+        atomicOr(&q.Trow[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
+        atomicAdd(&q.st->dcount[0][a], 1ull);
+        (*cnt)++;
+    }
+}
+
+__device__ inline void seed_query(const QDesc &q, uint64_t tid, uint64_t nthreads) {
+    unsigned long long cnt = 0;
+    for (uint64_t e = tid; e < q.n_edges; e += nthreads) {
+        const cfpq_edge ed = q.edges[e];
+        for (int u = 0; u < q.n_unary; u++)
+            if (q.unary[u].y == ed.label) seed_pair(q, q.unary[u].x, ed.src, ed.dst, &cnt);
+    }
+    for (uint64_t t = tid; t < (uint64_t)q.n_eps * q.n; t += nthreads) {
+        const int a = q.eps[t / q.n];
+        const uint32_t m = (uint32_t)(t % q.n);
+        seed_pair(q, a, m, m, &cnt);
+    }
+    if (cnt) atomicAdd(&q.st->seed_bits, cnt);
+}
+
+// ------------------------------------------------------------------------------------
+// Semi-naive bit-gather product for all productions with one left-hand side A:
+//   N_A |= (D_B x T_C  u  T_B x D_C) \ T_A      for every A -> B C
+// where D = pairs added by the previous iteration. One warp owns row i of A and a chunk
+// of 32*CPL words of that row; it ORs whole rows of the right operand selected by the set
+// bits of the left operand's row ("AND" = the bit test, "OR" = the accumulation). The
+// OR-merge into T_A and the change detection are fused at the end.
+// ------------------------------------------------------------------------------------
+template <int CPL>
+__device__ __forceinline__ void or_rows_for_bits(uint32_t (&acc)[CPL], uint32_t bw, uint32_t w0,
+                                                 const uint32_t *__restrict__ rhs_plane, uint32_t W,
+                                                 uint32_t base, int lane, unsigned &rows) {
+    unsigned nz = __ballot_sync(0xffffffffu, bw != 0);
+    rows += __popc(bw);
+    while (nz) {
+        const int src = __ffs(nz) - 1;
+        nz &= nz - 1;
+        uint32_t bits = __shfl_sync(0xffffffffu, bw, src);
+        while (bits) {
+            const uint32_t k = (w0 + src) * 32u + (uint32_t)(__ffs(bits) - 1);
+            bits &= bits - 1;
+            const uint32_t *row = rhs_plane + (uint64_t)k * W + base;
+#pragma unroll
+            for (int c = 0; c < CPL; c++) {
+                const uint32_t col = base + lane + 32 * c;
+                if (col < W) acc[c] |= __ldcg(row + lane + 32 * c);
+            }
+        }
+    }
+}
+
+template <int CPL>
+__device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint32_t ch, int lane,
+                                        uint32_t parity) {
+    const uint32_t W = q.W;
+    const uint64_t plane = q.plane;
+    const uint32_t *D = parity ? q.X1 : q.X0;
+    uint32_t *N = parity ? q.X0 : q.X1;
+    const uint32_t *DR = parity ? q.R1 : q.R0;
+    uint32_t *NR = parity ? q.R0 : q.R1;
+    const DevState *st = q.st;
+    const uint32_t base = ch * 32u * CPL;
+    const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
+    const int A = q.rules[r0].lhs;
+
+    uint32_t acc[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; c++) acc[c] = 0;
+    bool touched = false;
+    unsigned rows = 0, scans = 0;  // gathered rows (this lane's share), scanned row words
+
+    for (int r = r0; r < r1; r++) {
+        const int B = q.rules[r].b, C = q.rules[r].c;
+        // D_B x T_C: row i of the left delta selects rows of the full right operand
+        if (test_bit(DR + (uint64_t)B * W, i)) {
+            touched = true;
+            scans += W;
+            const uint32_t *rowB = D + (uint64_t)B * plane + (uint64_t)i * W;
+            for (uint32_t w0 = 0; w0 < W; w0 += 32) {
+                const uint32_t bw = (w0 + lane < W) ? __ldcg(rowB + w0 + lane) : 0u;
+                or_rows_for_bits<CPL>(acc, bw, w0, q.T + (uint64_t)C * plane, W, base, lane, rows);
+            }
+        }
+        // T_B x D_C: only rows k of the right delta that may be non-zero
+        if (ld_u64(&st->dcount[parity][C]) != 0 && test_bit(q.Trow + (uint64_t)B * W, i)) {
+            touched = true;
+            scans += 2 * W;
+            const uint32_t *rowB = q.T + (uint64_t)B * plane + (uint64_t)i * W;
+            const uint32_t *rC = DR + (uint64_t)C * W;
+            for (uint32_t w0 = 0; w0 < W; w0 += 32) {
+                const uint32_t bw = (w0 + lane < W) ? (__ldcg(rowB + w0 + lane) & __ldcg(rC + w0 + lane)) : 0u;
+                or_rows_for_bits<CPL>(acc, bw, w0, D + (uint64_t)C * plane, W, base, lane, rows);
+            }
+        }
+    }
+    if (!touched) return;
+
+    // fused epilogue: new = acc & ~T_A; merge (in place) and record the delta
+    uint32_t *TA = q.T + (uint64_t)A * plane + (uint64_t)i * W;
+    uint32_t *NA = N + (uint64_t)A * plane + (uint64_t)i * W;
+    const bool inplace = q.schedule == CFPQ_SCHED_INPLACE;
+    unsigned cnt = 0;
+#pragma unroll
+    for (int c = 0; c < CPL; c++) {
+        const uint32_t col = base + lane + 32 * c;
+        if (col < W && acc[c]) {
+            const uint32_t old = __ldcg(TA + col);
+            const uint32_t nw = acc[c] & ~old;
+            if (nw) {
+                cnt += __popc(nw);
+                if (inplace) TA[col] = old | nw;
+                NA[col] = __ldcg(NA + col) | nw;
+            }
+        }
+    }
+    const unsigned any = __ballot_sync(0xffffffffu, cnt != 0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (q.profile) {
+        // words of this chunk: scanned operand rows, gathered row chunks, T_A chunk read
+        // and (when pairs were added) T_A and N_A chunks written
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rows += __shfl_xor_sync(0xffffffffu, rows, o);
+        const uint32_t cw = min(32u * CPL, W - base);
+        if (lane == 0)
+            atomicAdd(&q.st->prof_words, (unsigned long long)scans + (unsigned long long)rows * cw +
+                                             (unsigned long long)cw * (any ? 3ull : 1ull));
+    }
+    if (any && lane == 0) {
+        atomicOr(&NR[(uint64_t)A * W + (i >> 5)], 1u << (i & 31));
+        if (inplace) atomicOr(&q.Trow[(uint64_t)A * W + (i >> 5)], 1u << (i & 31));
+        atomicAdd(&q.st->dcount[parity ^ 1u][A], (unsigned long long)cnt);
+        atomicAdd(&q.st->new_bits, (unsigned long long)cnt);
+        q.st->changed = 1u;
+        q.st->dirty[A] = 1u;
+    }
+}
+
+// Jacobi schedule: T |= N after all products of the iteration (T_{k+1} = T_k u T_k x T_k).
+__device__ inline void merge_row(const QDesc &q, int a, uint32_t i, int lane, uint32_t parity) {
+    const uint32_t *N = parity ? q.X0 : q.X1;
+    const uint32_t *NR = parity ? q.R0 : q.R1;
+    const uint32_t W = q.W;
+    if (!test_bit(NR + (uint64_t)a * W, i)) return;
+    uint32_t *TA = q.T + (uint64_t)a * q.plane + (uint64_t)i * W;
+    const uint32_t *NA = N + (uint64_t)a * q.plane + (uint64_t)i * W;
+    for (uint32_t w = lane; w < W; w += 32) TA[w] = __ldcg(TA + w) | __ldcg(NA + w);
+    if (lane == 0) atomicOr(&q.Trow[(uint64_t)a * W + (i >> 5)], 1u << (i & 31));
+}
+
+// Zeroes the rows of the delta plane that was read this iteration (it becomes N next).
+__device__ inline void clear_row(const QDesc &q, int a, uint32_t i, int lane, uint32_t parity) {
+    uint32_t *D = parity ? q.X1 : q.X0;
+    const uint32_t *DR = parity ? q.R1 : q.R0;
+    const uint32_t W = q.W;
+    if (!test_bit(DR + (uint64_t)a * W, i)) return;
+    uint32_t *row = D + (uint64_t)a * q.plane + (uint64_t)i * W;
+    for (uint32_t w = lane; w < W; w += 32) row[w] = 0u;
+}
+
+// End of one loop execution (one block): clears the old delta's row bitmaps, counts the
+// iteration and decides whether the loop continues. Returns the loop condition (valid
+// in thread 0).
+__device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads) {
+    DevState *st = q.st;
+    const unsigned long long it = ld_u64(&st->iter);
+    const uint32_t old = (uint32_t)(it & 1ull);
+    uint32_t *DR = old ? q.R1 : q.R0;
+    for (uint64_t w = tid; w < (uint64_t)q.n_nt * q.W; w += nthreads) DR[w] = 0u;
+    __syncthreads();
+    unsigned cont = 0;
+    if (tid == 0) {
+        for (int a = 0; a < q.n_nt; a++) st->dcount[old][a] = 0ull;
+        const unsigned changed = ld_u32(&st->changed);
+        st->changed = 0u;
+        st->iter = it + 1;
+        cont = changed ? 1u : 0u;
+        if (cont && it + 1 >= ld_u64(&st->max_iter)) {
+            st->error = kErrIterLimit;
+            cont = 0;
+        }
+        const unsigned long long dl = ld_u64(&st->deadline_ns);
+        if (cont && dl && globaltimer_ns() > dl) {
+            st->error = kErrTimeout;
+            cont = 0;
+        }
+        st->cont = cont;
+        if (!cont) st->done = 1u;
+    }
+    __syncthreads();
+    return cont;
+}
+
+}  // namespace cfpq

@@ -1,0 +1,70 @@
+// Host-side context of one query and the declarations shared by the engine's files.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/cfpq.h"
+#include "cfpq_device.cuh"
+
+struct cfpq_ctx {
+    // problem
+    uint32_t n = 0, n_pad = 0, W = 0;
+    uint64_t plane = 0;
+    int n_nt = 0, n_term = 0, n_groups = 0, n_unary = 0, n_eps_rules = 0;
+    size_t n_edges = 0;
+    int schedule = 0, path = 0, use_graph = 1, profile = 0;
+    double timeout_s = 0.0;
+    uint64_t max_iter = 0;
+    std::vector<cfpq::Rule> rules;
+    std::vector<int32_t> gstart;
+    std::vector<char> group_tensor;   // per group: 1 = tensor-core product
+    // device memory
+    uint32_t *d_T = nullptr, *d_TT = nullptr, *d_X0 = nullptr, *d_X1 = nullptr;
+    uint32_t *d_R0 = nullptr, *d_R1 = nullptr, *d_Trow = nullptr;
+    cfpq::Rule *d_rules = nullptr;
+    int32_t *d_gstart = nullptr;
+    int2 *d_unary = nullptr;
+    int32_t *d_eps = nullptr;
+    cfpq_edge *d_edges = nullptr;
+    cfpq::DevState *d_state = nullptr;
+    cfpq::QDesc *d_q = nullptr;
+    cfpq::QDesc hq{};
+    uint32_t *d_counts = nullptr;
+    uint64_t *d_offsets = nullptr;
+    unsigned long long *d_total = nullptr;
+    cfpq_triple *d_triples = nullptr;
+    size_t triples_cap = 0;
+    void *d_tc_work = nullptr;
+    // execution
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t last_stream = nullptr;      // stream of the last cfpq_solve (results are read on it)
+    int64_t iter_launches = 0;               // kernels one loop execution launches
+    int64_t fixed_launches = 0;              // kernels a solve launches outside the loop
+    std::vector<cudaEvent_t> prof_ev;        // profile mode: a start/stop pair per group
+    bool solved = false;
+    cfpq_stats stats{};
+};
+
+namespace cfpq {
+
+int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
+             const cfpq_options &o);
+void free_ctx_device(cfpq_ctx *c);
+int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s);
+int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle);
+void launch_gather(cfpq_ctx *c, int g, cudaStream_t s);
+void arm_deadline(cfpq_ctx *c, cudaStream_t s);
+int read_status(cfpq_ctx *c, cudaStream_t s);
+int run_loop(cfpq_ctx *c, cudaStream_t s);
+uint32_t gather_chunks(uint32_t W, int *cpl);
+
+// tensor-core product path (cfpq_tensor.cu)
+bool tensor_path_available();
+int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s);
+
+}  // namespace cfpq

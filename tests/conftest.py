@@ -11,6 +11,10 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
     config.addinivalue_line("markers", "slow: longer-running case")
+    # the engine library is built in-tree (nvcc cross-compiles without a GPU)
+    from paper_1707_01007_b300 import build as engine_build
+
+    engine_build.build()
 
 
 @pytest.fixture(scope="session")

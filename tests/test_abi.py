@@ -1,0 +1,111 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every entry
+point ``include/cfpq.h`` declares, rejects invalid input before touching the device, and
+its grammar reader produces the same normal form as the oracle's independent reader."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import cfpq_synth as synth
+import oracle
+import paper_1707_01007_b300 as eng
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for path in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names |= set(re.findall(r"\b(cfpq_[a-z_]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = eng.library()
+    decl = declared_functions()
+    assert len(decl) >= 14
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(eng.EXPORTS) == decl
+
+
+def test_strerror_names_every_status():
+    lib = eng.library()
+    names = {lib.cfpq_strerror(c).decode() for c in range(9)}
+    assert len(names) == 9
+    assert lib.cfpq_strerror(99).decode() == "unknown status"
+
+
+@pytest.mark.parametrize("text,labels", [
+    (synth.GRAMMAR_Q1, synth.HIERARCHY_LABELS),
+    (synth.GRAMMAR_QSC, synth.HIERARCHY_LABELS),
+    (synth.GRAMMAR_C3, ["a", "b"]),
+    (synth.GRAMMAR_WORKED, synth.HIERARCHY_LABELS),
+    (synth.GRAMMAR_Q2, synth.HIERARCHY_LABELS),
+    (synth.random_grammar_text(6, 3, 12, 8, 2, seed=5), ["t0", "t1", "t2"]),
+    ("S a S1\nS1 S b\nS a b\n", ["a", "b"]),
+])
+def test_grammar_reader_matches_oracle_reader(text, labels):
+    g = eng.Grammar(text, labels)
+    c = oracle.parse_grammar(text, labels)
+    assert g.names == c.names
+    cn = g.cnf.contents
+    assert [(cn.unary[i].lhs, cn.unary[i].term) for i in range(cn.n_unary)] == list(map(tuple, c.unary))
+    assert [(cn.binary[i].lhs, cn.binary[i].b, cn.binary[i].c) for i in range(cn.n_binary)] == \
+        list(map(tuple, c.binary))
+    assert [cn.eps_lhs[i] for i in range(cn.n_eps)] == list(c.eps)
+
+
+@pytest.mark.parametrize("text", ["S A\nA a\n", "S zz\n", "S a b c\n", "eps a\n", "S <a>\n"])
+def test_grammar_reader_rejects(text):
+    with pytest.raises(ValueError):
+        eng.Grammar(text, ["a", "b", "c"])
+
+
+def _create(cnf, n, edges, opt=None):
+    rec = np.zeros(len(edges), dtype=[("src", "<u4"), ("label", "<i4"), ("dst", "<u4")])
+    for i, (s, l, d) in enumerate(edges):
+        rec[i] = (s, l, d)
+    h = ctypes.c_void_p()
+    ptr = rec.ctypes.data_as(ctypes.POINTER(eng.Edge)) if len(edges) else None
+    return eng.library().cfpq_create(cnf, n, ptr, len(edges), opt, ctypes.byref(h)), h
+
+
+def test_create_rejects_invalid_input_before_device_use():
+    g = eng.Grammar("S S S\nS a\n", ["a"])
+    assert _create(g.cnf, 0, [])[0] == eng.ERR_INVALID                  # n = 0
+    assert _create(g.cnf, 4, [(0, 0, 9)])[0] == eng.ERR_INVALID         # dst >= n
+    assert _create(g.cnf, 4, [(0, 3, 1)])[0] == eng.ERR_INVALID         # label out of range
+    assert _create(g.cnf, 200000, [])[0] == eng.ERR_INVALID             # n > CFPQ_MAX_NODES
+    bad = eng.GrammarCNF()
+    bad.n_nonterm, bad.n_term = 1, 1
+    r1 = (eng.Rule1 * 1)(eng.Rule1(3, 0))                               # lhs out of range
+    bad.unary, bad.n_unary = r1, 1
+    assert _create(ctypes.pointer(bad), 4, [])[0] == eng.ERR_INVALID
+    opt = eng.Options()
+    eng.library().cfpq_options_default(ctypes.byref(opt))
+    opt.schedule = 7
+    assert _create(g.cnf, 4, [], ctypes.byref(opt))[0] == eng.ERR_INVALID
+
+
+def test_null_arguments():
+    lib = eng.library()
+    assert lib.cfpq_solve(None, None) == eng.ERR_INVALID
+    assert lib.cfpq_get(None, 0, None, 0, None) == eng.ERR_INVALID
+    assert lib.cfpq_get_device(None, 0, None, 0, None) == eng.ERR_INVALID
+    assert lib.cfpq_count(None, 0, None) == eng.ERR_INVALID
+    assert lib.cfpq_stats_get(None, None) == eng.ERR_INVALID
+    assert lib.cfpq_options_default(None) == eng.ERR_INVALID
+    assert lib.cfpq_solve_batch(None, 0, None) == eng.ERR_INVALID
+    lib.cfpq_destroy(None)
+
+
+def test_options_defaults():
+    opt = eng.Options()
+    assert eng.library().cfpq_options_default(ctypes.byref(opt)) == eng.OK
+    assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter) == \
+        (eng.SCHED_INPLACE, eng.PATH_AUTO, 1, 0, 0)

@@ -294,3 +294,30 @@ def test_planted_mistakes_are_caught(plant, worked):
         r = oracle.hellings(gg, gram, plant=plant).as_sets()
         failures += r != oracle.brute_force(gg, gram, max_len=9)
     assert failures > 0
+
+
+# ----------------------------------------------------------------------------- sparse Algorithm 1
+
+def test_sparse_algorithm1_worked_example(worked):
+    cnf, T, k = oracle.matrix_closure_sparse(synth.worked_example_graph(), synth.GRAMMAR_WORKED)
+    assert k == worked["k"] == 6
+    for a, nm in enumerate(cnf.names):
+        coo = T[a].tocoo()
+        assert set(zip(coo.row.tolist(), coo.col.tolist())) == worked["R"].get(nm, set())
+
+
+@pytest.mark.parametrize("p,q", [(3, 2), (5, 4), (7, 3)])
+def test_sparse_algorithm1_two_cycle_count(p, q):
+    _, _, k = oracle.matrix_closure_sparse(synth.two_cycles(p, q), synth.GRAMMAR_C3)
+    assert k == 2 * p * q + 1
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sparse_algorithm1_equals_dense(seed):
+    g = synth.random_graph(30, 70, 3, seed=seed)
+    gram = synth.random_grammar_text(5, 3, 9, 6, seed % 2, seed=seed)
+    cnf, snaps, k = oracle.matrix_closure(g, gram)
+    cnf2, T, k2 = oracle.matrix_closure_sparse(g, gram)
+    assert k == k2
+    for a in range(len(cnf.names)):
+        assert (T[a].toarray() != 0).tolist() == snaps[-1][a].tolist()
