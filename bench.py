@@ -223,7 +223,7 @@ def engine_arm(args):
         qj.close()
     ops_per_step = products * 2.0 * float(N_NODES) ** 3
 
-    qs = [eng.Query(g, graph.n, graph.edges, path=path) for g in gs]
+    qs = [eng.Query(g, graph.n, graph.edges, path=path, timeout_s=300.0) for g in gs]
     caps = []
     for q, g in zip(qs, gs):
         q.solve(stream)

@@ -274,6 +274,7 @@ static int build_graph(cfpq_ctx *c) {
 }
 
 void free_ctx_device(cfpq_ctx *c) {
+    tensor_release(c);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
     void *ptrs[] = {c->d_T, c->d_TT, c->d_X0, c->d_X1, c->d_R0, c->d_R1, c->d_Trow, c->d_rules, c->d_gstart,
@@ -318,6 +319,9 @@ int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
     const uint32_t blocks = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (work + 255) / 256), 148ull * 16);
     k_seed<<<blocks, 256, 0, s>>>(c->d_q);
     CK(cudaGetLastError());
+    bool any_tensor = false;
+    for (int g = 0; g < c->n_groups; g++) any_tensor |= c->group_tensor[g] != 0;
+    if (any_tensor) return enqueue_tensor_seed_transposes(c, s, &c->fixed_launches);
     return CFPQ_OK;
 }
 
@@ -372,6 +376,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         if (i == 0 || rules[i].lhs != rules[i - 1].lhs) gstart.push_back((int32_t)i);
     gstart.push_back((int32_t)rules.size());
     c->n_groups = (int)gstart.size() - 1;
+    c->nt_dynamic.assign(g->n_nonterm, 0);
+    for (const Rule &r : rules) c->nt_dynamic[r.lhs] = 1;
     c->rules = rules;
     c->gstart = gstart;
     std::vector<int2> unary;

@@ -16,35 +16,45 @@
 
 namespace cfpq {
 
-constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
+constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;    // 20 s
+constexpr unsigned long long kLaunchLimitNs = 600ull * 1000 * 1000 * 1000;     // 10 min per launch
 
-// Returns false if the barrier timed out (recorded in ctl->error).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier on one counter: block 0 adds 2^31 - (G - 1), every other block adds
+// 1, so the counter's top bit flips exactly when all G blocks have arrived (no reset, no
+// separate generation word). Arrival is a release (fence + atomic), polling an acquire
+// load. The wait is bounded; returns false (the same value in every thread of the block)
+// once any block has recorded an error.
 __device__ bool grid_barrier(BatchCtl *ctl) {
+    __shared__ unsigned s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &ctl->bar_gen;
-        const unsigned g = *gen;
+        const unsigned nb = blockIdx.x == 0 ? (0x80000000u - (gridDim.x - 1u)) : 1u;
         __threadfence();
-        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            ctl->bar_count = 0u;
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const unsigned long long t0 = globaltimer_ns();
-            while (*gen == g) {
-                __nanosleep(64);
-                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
-                    atomicExch(&ctl->error, 1u);
-                    break;
-                }
-                if (*(volatile unsigned *)&ctl->error) break;
+        const unsigned old = atomicAdd(&ctl->bar_count, nb);
+        unsigned ok = 1;
+        const unsigned long long t0 = globaltimer_ns();
+        for (;;) {
+            const unsigned cur = ld_acquire_u32(&ctl->bar_count);
+            if ((old ^ cur) & 0x80000000u) break;
+            if (ld_acquire_u32(&ctl->error)) { ok = 0; break; }
+            if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                atomicExch(&ctl->error, 1u);
+                ok = 0;
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
+        s_ok = ok && ld_acquire_u32(&ctl->error) == 0u;
     }
     __syncthreads();
-    return *(volatile unsigned *)&ctl->error == 0u;
+    return s_ok != 0u;
 }
 
 // index of the slot containing item x in offsets[0..n] (offsets[0] = 0, increasing)
@@ -111,6 +121,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
     const uint64_t gwarp = gtid >> 5, gwarps = gthreads >> 5;
     const int lane = threadIdx.x & 31;
     const int k = ctl->k;
+    if (gtid == 0) ctl->start_ns = globaltimer_ns();
 
     // 1) queries starting in this launch: clear their matrices and state
     for (int j = 0; j < k; j++) {
@@ -143,18 +154,22 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
     if (!grid_barrier(ctl)) return;
 
     for (int round = 0; round < ctl->max_rounds; round++) {
-        const int na = (int)ld_u32(&ctl->n_active);
-        if (na == 0) break;
+        const int na = min((int)ld_u32(&ctl->n_active), k);
+        if (na <= 0) break;
         // 3) products of every active query
         const unsigned long long np = __ldcg(ctl->prod_off + na);
         for (unsigned long long it = gwarp; it < np; it += gwarps) {
             const int s = find_slot(ctl->prod_off, na, it);
-            const BatchQuery &b = bq[__ldcg(ctl->act + s)];
+            const int j = __ldcg(ctl->act + s);
+            if (j < 0 || j >= k) continue;
+            const BatchQuery &b = bq[j];
             const unsigned long long loc = it - __ldcg(ctl->prod_off + s);
             const unsigned long long per_group = (unsigned long long)b.q.n * b.nch;
-            const int g = (int)(loc / per_group);
+            const unsigned long long g64 = loc / per_group;
             const unsigned long long r = loc % per_group;
             const uint32_t i = (uint32_t)(r / b.nch), ch = (uint32_t)(r % b.nch);
+            if (g64 >= (unsigned long long)b.q.n_groups || i >= b.q.n) continue;
+            const int g = (int)g64;
             const uint32_t parity = (uint32_t)(ld_u64(&b.q.st->iter) & 1ull);
             switch (b.cpl) {
                 case 1: gather_row_chunk<1>(b.q, g, i, ch, lane, parity); break;
@@ -169,9 +184,12 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
         if (ctl->any_jacobi) {
             for (unsigned long long it = gwarp; it < nr; it += gwarps) {
                 const int s = find_slot(ctl->row_off, na, it);
-                const BatchQuery &b = bq[__ldcg(ctl->act + s)];
+                const int j = __ldcg(ctl->act + s);
+                if (j < 0 || j >= k) continue;
+                const BatchQuery &b = bq[j];
                 if (b.q.schedule != CFPQ_SCHED_JACOBI) continue;
                 const unsigned long long loc = it - __ldcg(ctl->row_off + s);
+                if (loc >= b.row_items) continue;
                 merge_row(b.q, (int)(loc / b.q.n), (uint32_t)(loc % b.q.n), lane,
                           (uint32_t)(ld_u64(&b.q.st->iter) & 1ull));
             }
@@ -180,14 +198,18 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
         // 5) clear the delta plane that was read
         for (unsigned long long it = gwarp; it < nr; it += gwarps) {
             const int s = find_slot(ctl->row_off, na, it);
-            const BatchQuery &b = bq[__ldcg(ctl->act + s)];
+            const int j = __ldcg(ctl->act + s);
+            if (j < 0 || j >= k) continue;
+            const BatchQuery &b = bq[j];
             const unsigned long long loc = it - __ldcg(ctl->row_off + s);
+            if (loc >= b.row_items) continue;
             clear_row(b.q, (int)(loc / b.q.n), (uint32_t)(loc % b.q.n), lane, (uint32_t)(ld_u64(&b.q.st->iter) & 1ull));
         }
         if (!grid_barrier(ctl)) return;
         // 6) per-query end of iteration; a converged query is retired
         for (int s = blockIdx.x; s < na; s += gridDim.x) {
             const int j = __ldcg(ctl->act + s);
+            if (j < 0 || j >= k) continue;  // uniform across the block
             const unsigned cont = tail_query(bq[j].q, threadIdx.x, blockDim.x);
             if (threadIdx.x == 0) {
                 bq[j].q.st->gather_products += (unsigned long long)bq[j].q.n_rules;
@@ -195,8 +217,14 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
             }
             __syncthreads();
         }
+        // every tail must be done (it reads act[] and writes active[]) before the tables change
         if (!grid_barrier(ctl)) return;
-        if (blockIdx.x == 0) build_tables(ctl, bq);
+        if (blockIdx.x == 0) {
+            build_tables(ctl, bq);
+            if (threadIdx.x == 0 && ctl->limit_ns && globaltimer_ns() - ctl->start_ns > ctl->limit_ns)
+                atomicExch(&ctl->error, 2u);
+            __syncthreads();
+        }
         if (!grid_barrier(ctl)) return;
     }
 }
@@ -252,6 +280,7 @@ int batch_buffers_upload(BatchBuffers *b, const BatchQuery *hb, const int *activ
     ctl.k = k;
     ctl.max_rounds = max_rounds;
     ctl.any_jacobi = any_jacobi ? 1 : 0;
+    ctl.limit_ns = kLaunchLimitNs;
     ctl.active = b->active;
     ctl.act = b->act;
     ctl.prod_off = b->prod_off;

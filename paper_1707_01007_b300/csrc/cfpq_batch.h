@@ -15,8 +15,10 @@ struct BatchQuery {
 };
 
 struct BatchCtl {
-    unsigned bar_count, bar_gen, error, n_active;
+    unsigned bar_count, bar_spare, error, n_active;   // bar_count: grid barrier (top bit flips per barrier)
     int k, max_rounds, any_jacobi, pad;
+    unsigned long long limit_ns;      // whole-launch wall-clock limit (0 = none)
+    unsigned long long start_ns;      // %globaltimer at launch start (set by the kernel)
     int *active;                      // [k] 1 while the query has not converged
     int *act;                         // [k] compacted active query ids of the current round
     unsigned long long *prod_off;     // [k+1] prefix sums of prod_items over act

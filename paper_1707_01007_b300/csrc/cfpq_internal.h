@@ -20,6 +20,7 @@ struct cfpq_ctx {
     std::vector<cfpq::Rule> rules;
     std::vector<int32_t> gstart;
     std::vector<char> group_tensor;   // per group: 1 = tensor-core product
+    std::vector<char> nt_dynamic;     // per non-terminal: 1 = left-hand side of a binary production
     // device memory
     uint32_t *d_T = nullptr, *d_TT = nullptr, *d_X0 = nullptr, *d_X1 = nullptr;
     uint32_t *d_R0 = nullptr, *d_R1 = nullptr, *d_Trow = nullptr;
@@ -37,6 +38,7 @@ struct cfpq_ctx {
     cfpq_triple *d_triples = nullptr;
     size_t triples_cap = 0;
     void *d_tc_work = nullptr;
+    void *h_tc_work = nullptr;               // tensor path: tensor maps (host side)
     // execution
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -66,5 +68,7 @@ uint32_t gather_chunks(uint32_t W, int *cpl);
 // tensor-core product path (cfpq_tensor.cu)
 bool tensor_path_available();
 int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s);
+int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launches);
+void tensor_release(cfpq_ctx *c);
 
 }  // namespace cfpq

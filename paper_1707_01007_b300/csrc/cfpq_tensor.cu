@@ -1,10 +1,464 @@
-// Tensor-core (tcgen05) Boolean product path.
+// Tensor-core (tcgen05) Boolean product path for sm_103a.
+//
+// One launch computes, for one left-hand side A with productions A -> B_r C_r,
+//     P = sum_r T_{B_r} x T_{C_r}      (K-concatenated over the productions)
+// on the 5th-generation tensor cores and merges it into T_A: the Boolean product of
+// Section 2 (one Boolean matrix product per production, Valiant's |N|^2 reduction) with
+// the union T <- T u (T x T) of Algorithm 1 fused into the epilogue.
+//
+// Exactness: operands are 0/1 in FP8 E4M3 (the encoding 0x08 = 2^-6), products are
+// 0 or 2^-12 and are accumulated in F32: a sum of at most K <= 4 * 131072 such terms is
+// exact, and it is non-zero iff some term is, so "accumulator != 0" is the Boolean OR
+// of ANDs. (tcgen05 has no 8-bit integer kind on sm_103a.)
+//
+// Data flow per CTA (one 128 x 256 output tile):
+//   warp 0     TMA: bit-packed 128 x 128-bit tile of T_B and 256 x 128-bit tile of T_C^T
+//              (the transposed copy, so both operands are K-major) into a packed ring
+//   warps 2-5  unpack: 1 bit -> 1 byte, written in the 128-byte-swizzled K-major layout;
+//              within each 32-bit word, bit q + 8r goes to byte 4q' + r of the word's 32
+//              bytes (q' = q): the same permutation of K for both operands, so the
+//              contraction is unchanged and each 4 output bytes cost a shift and a mask
+//   warp 1     one thread issues tcgen05.mma (M=128, N=256, K=32) into TMEM (256 columns)
+//   warps 2-5  epilogue: tcgen05.ld, threshold, pack 32 columns per word, OR-merge into
+//              T_A, record the new pairs (delta plane, row bitmap), set the change flag
+// Every mbarrier wait is bounded (%globaltimer); on expiry the CTA records an error,
+// drains what it started and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstring>
+
 #include "cfpq_internal.h"
 
 namespace cfpq {
+namespace tc {
 
-bool tensor_path_available() { return false; }
+constexpr int BM = 128, BN = 256;
+constexpr int KW = 4;                 // 32-bit words of K per stage
+constexpr int BK = 32 * KW;           // 128 K elements per stage
+constexpr int PST = 4, UST = 3;       // packed / unpacked ring depths
+constexpr int A_PACK = BM * KW * 4, B_PACK = BN * KW * 4;
+constexpr int A_TILE = BM * BK, B_TILE = BN * BK;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr unsigned long long WAIT_LIMIT_NS = 2ull * 1000 * 1000 * 1000;  // 2 s per wait
 
-int enqueue_tensor_group(cfpq_ctx *, int, cudaStream_t) { return CFPQ_ERR_UNSUPPORTED; }
+struct __align__(1024) Smem {
+    uint8_t a_tile[UST][A_TILE];
+    uint8_t b_tile[UST][B_TILE];
+    uint32_t a_pack[PST][BM * KW];
+    uint32_t b_pack[PST][BN * KW];
+    unsigned long long full_p[PST], empty_p[PST], full_u[UST], empty_u[UST], acc_full;
+    uint32_t tmem_base;
+    int err;
+};
+
+constexpr size_t SMEM_BYTES = sizeof(Smem) + 1024;
+
+__device__ __forceinline__ uint32_t sa(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(sa(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false (and the CTA's error flag set) if the phase did not complete in time
+// or another role of the CTA already gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, volatile int *err) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try(b, parity)) return true;
+        if (*err) return false;
+        if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
+            *err = 1;
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, unsigned long long *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            sa(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(sa(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;            // leading-dimension byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride-dimension byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f8f6f4, A = B = E4M3, D = F32, both K-major, M x N.
+constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem_d),
+        "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 4 bytes of the unpacked K-row: byte r = bit (q + 8r) of w, as FP8 E4M3 0x08 (2^-6) or 0.
+__device__ __forceinline__ uint32_t spread(uint32_t w, int q) {
+    return (q <= 3 ? (w << (3 - q)) : (w >> (q - 3))) & 0x08080808u;
+}
+
+// Unpacks one 128-bit K slice of a row into the 128-byte swizzled row r of a tile.
+__device__ __forceinline__ void unpack_row(uint8_t *tile, int r, uint4 p) {
+    const uint32_t w[4] = {p.x, p.y, p.z, p.w};
+    uint8_t *row = tile + r * 128;
+#pragma unroll
+    for (int wi = 0; wi < 4; wi++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int c = wi * 2 + h;
+            uint4 o;
+            o.x = spread(w[wi], 4 * h + 0);
+            o.y = spread(w[wi], 4 * h + 1);
+            o.z = spread(w[wi], 4 * h + 2);
+            o.w = spread(w[wi], 4 * h + 3);
+            *reinterpret_cast<uint4 *>(row + ((c ^ (r & 7)) << 4)) = o;
+        }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_bool_gemm(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmTT, const QDesc *qd,
+                   int g) {
+    extern __shared__ uint8_t smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const QDesc &q = *qd;
+    DevState *st = q.st;
+    if (st->use_tensor[g] == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
+    const int A = q.rules[r0].lhs;
+    const uint32_t kpr = q.n_pad / BK;  // stages per production
+    const uint32_t total = (uint32_t)(r1 - r0) * kpr;
+    volatile int *err = &S.err;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < PST; i++) {
+            mbar_init(&S.full_p[i], 1);
+            mbar_init(&S.empty_p[i], 128);
+        }
+        for (int i = 0; i < UST; i++) {
+            mbar_init(&S.full_u[i], 128);
+            mbar_init(&S.empty_u[i], 1);
+        }
+        mbar_init(&S.acc_full, 1);
+        S.err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- producer: TMA of the bit-packed tiles
+            uint32_t issued = 0;
+            for (uint32_t s = 0; s < total; s++) {
+                const uint32_t slot = s % PST, ph = (s / PST) & 1u;
+                if (!mbar_wait(&S.empty_p[slot], ph ^ 1u, err)) break;
+                const int r = r0 + (int)(s / kpr);
+                const uint32_t kb = s % kpr;
+                const int B = q.rules[r].b, C = q.rules[r].c;
+                mbar_expect_tx(&S.full_p[slot], A_PACK + B_PACK);
+                tma_load_2d(S.a_pack[slot], &tmT, &S.full_p[slot], (int)(kb * KW), (int)((uint32_t)B * q.n_pad + m0));
+                tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * KW), (int)((uint32_t)C * q.n_pad + n0));
+                issued = s + 1;
+            }
+            if (*err) {
+                // drain: the last load issued into each slot must land before the CTA exits
+                volatile int drain_err = 0;
+                for (uint32_t s = (issued > PST ? issued - PST : 0); s < issued; s++)
+                    mbar_wait(&S.full_p[s % PST], (s / PST) & 1u, &drain_err);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            const uint32_t a0 = sa(S.a_tile[0]), b0 = sa(S.b_tile[0]);
+            for (uint32_t s = 0; s < total; s++) {
+                const uint32_t slot = s % UST, ph = (s / UST) & 1u;
+                if (!mbar_wait(&S.full_u[slot], ph, err)) break;
+                tc_fence_after();
+                const uint32_t at = a0 + slot * A_TILE, bt = b0 + slot * B_TILE;
+#pragma unroll
+                for (int kk = 0; kk < BK / 32; kk++)
+                    mma_f8(tmem, sdesc(at + kk * 32), sdesc(bt + kk * 32), (s > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&S.empty_u[slot]);
+            }
+            mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
+        }
+    } else {
+        // ---------------- unpack (128 threads), then epilogue
+        const int t = threadIdx.x - 64;
+        for (uint32_t s = 0; s < total; s++) {
+            const uint32_t ps = s % PST, pph = (s / PST) & 1u;
+            const uint32_t us = s % UST, uph = (s / UST) & 1u;
+            if (!mbar_wait(&S.full_p[ps], pph, err)) break;
+            if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) break;
+            const uint4 pa = reinterpret_cast<const uint4 *>(S.a_pack[ps])[t];
+            const uint4 pb0 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
+            const uint4 pb1 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t + 128];
+            unpack_row(S.a_tile[us], t, pa);
+            unpack_row(S.b_tile[us], t, pb0);
+            unpack_row(S.b_tile[us], t + 128, pb1);
+            mbar_arrive(&S.empty_p[ps]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&S.full_u[us]);
+        }
+        const bool ok = mbar_wait(&S.acc_full, 0, err);
+        tc_fence_after();
+        const int quad = warp & 3;
+        const uint32_t row = m0 + quad * 32 + lane;
+        const uint32_t W = q.W;
+        const bool inplace = q.schedule == CFPQ_SCHED_INPLACE;
+        const uint32_t parity = (uint32_t)(st->iter & 1ull);
+        uint32_t *NA = (parity ? q.X0 : q.X1) + (uint64_t)A * q.plane;
+        uint32_t *NR = (parity ? q.R0 : q.R1) + (uint64_t)A * W;
+        uint32_t *TA = q.T + (uint64_t)A * q.plane;
+        unsigned cnt = 0;
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; c++) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
+            uint32_t word = 0;
+#pragma unroll
+            for (int j = 0; j < 32; j++) word |= (v[j] != 0u ? 1u : 0u) << j;
+            if (!ok || *err || row >= q.n || word == 0) continue;
+            const uint64_t idx = (uint64_t)row * W + n0 / 32 + c;
+            const uint32_t old = __ldcg(TA + idx);
+            const uint32_t nw = word & ~old;
+            if (nw) {
+                cnt += __popc(nw);
+                if (inplace) TA[idx] = old | nw;
+                NA[idx] = __ldcg(NA + idx) | nw;
+            }
+        }
+        if (cnt) {
+            atomicOr(&NR[row >> 5], 1u << (row & 31));
+            if (inplace) atomicOr(&q.Trow[(uint64_t)A * W + (row >> 5)], 1u << (row & 31));
+        }
+        const unsigned any = __ballot_sync(0xffffffffu, cnt != 0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (any && lane == 0) {
+            atomicAdd(&st->dcount[parity ^ 1u][A], (unsigned long long)cnt);
+            atomicAdd(&st->new_bits, (unsigned long long)cnt);
+            st->changed = 1u;
+            st->dirty[A] = 1u;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (S.err) atomicExch(&st->error, 3u);
+        if (blockIdx.x == 0 && blockIdx.y == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// Bit-matrix transpose of plane a: TT[a] = T[a]^T. One CTA: 256 rows x 8 words (256 x 256 bits).
+__global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a) {
+    __shared__ uint32_t in[256][9];
+    __shared__ uint32_t out[256][9];
+    const QDesc &q = *qd;
+    const uint32_t W = q.W;
+    const uint32_t r0 = blockIdx.y * 256, wc0 = blockIdx.x * 8;
+    const uint32_t *src = q.T + (uint64_t)a * q.plane;
+    uint32_t *dst = q.TT + (uint64_t)a * q.plane;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    for (int idx = t; idx < 2048; idx += 256) {
+        const int row = idx >> 3, w = idx & 7;
+        in[row][w] = __ldcg(src + (uint64_t)(r0 + row) * W + wc0 + w);
+    }
+    __syncthreads();
+    // warp `warp` owns input rows warp*32 .. +31 (one output word per output row)
+    for (int wc = 0; wc < 8; wc++) {
+        const uint32_t x = in[warp * 32 + lane][wc];
+        uint32_t mine = 0;
+#pragma unroll
+        for (int b = 0; b < 32; b++) {
+            const uint32_t tb = __ballot_sync(0xffffffffu, (x >> b) & 1u);
+            if (lane == b) mine = tb;
+        }
+        out[wc * 32 + lane][warp] = mine;
+    }
+    __syncthreads();
+    for (int idx = t; idx < 2048; idx += 256) {
+        const int j = idx >> 3, ib = idx & 7;
+        dst[(uint64_t)(wc0 * 32 + j) * W + r0 / 32 + ib] = out[j][ib];
+    }
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------------------ host
+
+static int g_tc_available = -1;
+
+bool tensor_path_available() {
+    if (g_tc_available < 0) {
+        int dev = 0;
+        cudaDeviceProp p;
+        g_tc_available = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&p, dev) == cudaSuccess)
+            g_tc_available = (p.major == 10 && p.minor == 3) ? 1 : 0;
+        cudaGetLastError();
+    }
+    return g_tc_available == 1;
+}
+
+struct TensorWork {
+    CUtensorMap tmT, tmTT;
+    bool attr_set;
+};
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) ==
+                cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static bool encode_map(CUtensorMap *m, uint32_t *base, const cfpq_ctx *c, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {c->W, (cuuint64_t)c->n_nt * c->n_pad};
+    const cuuint64_t strides[1] = {(cuuint64_t)c->W * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::KW, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+static int tensor_setup(cfpq_ctx *c) {
+    if (c->d_tc_work) return CFPQ_OK;
+    if (!c->d_TT) return CFPQ_ERR_UNSUPPORTED;
+    TensorWork *w = new TensorWork();
+    memset(w, 0, sizeof(*w));
+    if (!encode_map(&w->tmT, c->d_T, c, tc::BM) || !encode_map(&w->tmTT, c->d_TT, c, tc::BN)) {
+        delete w;
+        return CFPQ_ERR_CUDA;
+    }
+    if (cudaFuncSetAttribute(tc::k_tc_bool_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES) !=
+        cudaSuccess) {
+        delete w;
+        return CFPQ_ERR_CUDA;
+    }
+    c->h_tc_work = w;
+    c->d_tc_work = nullptr;
+    return CFPQ_OK;
+}
+
+void tensor_release(cfpq_ctx *c) {
+    delete static_cast<TensorWork *>(c->h_tc_work);
+    c->h_tc_work = nullptr;
+}
+
+static void launch_transpose(cfpq_ctx *c, int a, cudaStream_t s, int64_t *launches) {
+    const dim3 grid(c->W / 8, c->n_pad / 256);
+    tc::k_transpose<<<grid, 256, 0, s>>>(c->d_q, a);
+    (*launches)++;
+}
+
+// After the matrix initialisation: transposes of every right operand of a tensor group.
+int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launches) {
+    int rc = tensor_setup(c);
+    if (rc != CFPQ_OK) return rc;
+    std::vector<char> done(c->n_nt, 0);
+    for (int g = 0; g < c->n_groups; g++) {
+        if (!c->group_tensor[g]) continue;
+        for (int r = c->gstart[g]; r < c->gstart[g + 1]; r++) {
+            const int C = c->rules[r].c;
+            if (done[C]) continue;
+            done[C] = 1;
+            launch_transpose(c, C, s, launches);
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
+
+// Refreshes the transposes of right operands that may have changed, then the product.
+int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
+    int rc = tensor_setup(c);
+    if (rc != CFPQ_OK) return rc;
+    std::vector<char> done(c->n_nt, 0);
+    for (int r = c->gstart[g]; r < c->gstart[g + 1]; r++) {
+        const int C = c->rules[r].c;
+        if (done[C] || !c->nt_dynamic[C]) continue;
+        done[C] = 1;
+        launch_transpose(c, C, s, &c->iter_launches);
+    }
+    TensorWork *w = static_cast<TensorWork *>(c->h_tc_work);
+    const dim3 grid(c->n_pad / tc::BN, c->n_pad / tc::BM);
+    tc::k_tc_bool_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(w->tmT, w->tmTT, c->d_q, g);
+    c->iter_launches++;
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
 
 }  // namespace cfpq

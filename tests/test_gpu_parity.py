@@ -18,6 +18,7 @@ def engine_sets(q, names):
 
 
 def solve_engine(graph, text, **kw):
+    kw.setdefault("timeout_s", 120.0)  # device-side bound on any runaway loop
     g = eng.Grammar(text, graph.labels)
     q = eng.Query(g, graph.n, graph.edges, **kw)
     q.solve()

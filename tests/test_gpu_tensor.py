@@ -1,0 +1,66 @@
+"""Tensor-core (tcgen05) product path against the CPU oracle, bit-exact."""
+import numpy as np
+import pytest
+
+import cfpq_synth as synth
+import oracle
+import paper_1707_01007_b300 as eng
+
+pytestmark = pytest.mark.gpu
+
+
+def tensor_parity(graph, text, **kw):
+    kw.setdefault("timeout_s", 120.0)
+    g = eng.Grammar(text, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_TENSOR, **kw)
+    q.solve()
+    ref = oracle.hellings(graph, text)
+    for nm in g.names:
+        got, exp = q.get(nm), ref.pairs(nm)
+        assert got.shape == exp.shape and np.array_equal(got, exp), \
+            f"{nm}: engine {got.shape[0]} pairs, oracle {exp.shape[0]}"
+    s = q.stats()
+    assert s["tensor_products"] > 0 or s["iterations"] <= 1
+    return g, q
+
+
+@pytest.mark.parametrize("n,m", [(200, 3000), (256, 20000), (700, 30000)])
+def test_single_product(n, m):
+    # S -> A B is one Boolean matrix product: exercises the GEMM, its K loop and epilogue
+    tensor_parity(synth.random_graph(n, m, 2, seed=n), "S A B\nA t0\nB t1\n")
+
+
+def test_worked_example():
+    tensor_parity(synth.worked_example_graph(), synth.GRAMMAR_WORKED)
+
+
+def test_worked_example_jacobi_iterations():
+    g, q = tensor_parity(synth.worked_example_graph(), synth.GRAMMAR_WORKED, schedule=eng.SCHED_JACOBI)
+    assert q.stats()["iterations"] == 6
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("schedule", [eng.SCHED_INPLACE, eng.SCHED_JACOBI])
+def test_random(seed, schedule):
+    graph = synth.random_graph(90 + 61 * seed, 200 + 40 * seed, 3, seed=seed)
+    text = synth.random_grammar_text(5, 3, 9, 6, seed % 3, seed=seed)
+    tensor_parity(graph, text, schedule=schedule)
+
+
+@pytest.mark.parametrize("n", [1100, 2600])
+def test_dense_closure(n):
+    tensor_parity(synth.random_graph(n, int(1.6 * n), 1, seed=n), "S S S\nS t0\n")
+
+
+def test_two_cycles():
+    tensor_parity(synth.two_cycles(17, 12), synth.GRAMMAR_C3)
+
+
+@pytest.mark.parametrize("n,c", [(1024, 300), (4096, 1200)])
+def test_hierarchy_q1(n, c):
+    tensor_parity(synth.hierarchy(n, c, seed=1), synth.GRAMMAR_Q1)
+
+
+@pytest.mark.parametrize("text", [synth.GRAMMAR_Q1, synth.GRAMMAR_QSC])
+def test_hierarchy_n16384(text):
+    tensor_parity(synth.hierarchy(16384, 5000, seed=0), text)
