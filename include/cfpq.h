@@ -36,6 +36,7 @@ extern "C" {
 
 #define CFPQ_MAX_NODES 131072
 #define CFPQ_MAX_NONTERM 64
+#define CFPQ_NOALLOC_MAX_ROWS 65536   /* row limit of cfpq_extract_pairs_noalloc */
 
 enum cfpq_status {
     CFPQ_OK = 0,
@@ -197,6 +198,27 @@ void cfpq_grammar_free(cfpq_parsed_grammar *pg);
  * cap; the others are still complete).
  */
 int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream);
+
+/*
+ * Allocation-free pair extraction (the paper has no counterpart; it is an interface for
+ * callers that cannot allocate device memory, e.g. code under an external allocator that
+ * owns the device heap, or paths where cudaMalloc is forbidden after start-up).
+ * Reads a bit-packed relation matrix that the caller owns in device memory -- n_rows rows
+ * of row_words 32-bit words, bit j of row i at word i * row_words + j / 32, bit j % 32
+ * (the layout of the engine's matrices) -- and writes its pairs (m, n), n < n_cols, as
+ * triples (A, m, n) sorted by (m, n) into the caller's device buffer out (cap triples).
+ * With out == NULL only *count (host) is set. Runs on `stream` (NULL = legacy default
+ * stream) and returns after the work is complete.
+ * The library allocates nothing for this call: its scratch is one fixed device array
+ * that every GPU loading the library holds until the process exits (~768 KiB). The
+ * first call on a device looks up that array's device address (with the device
+ * current); make this first call before any stream capture. All calls share the array:
+ * calls whose work overlaps on the GPU race and must be serialised by the caller.
+ * Errors: INVALID (count NULL, bits NULL with n_rows > 0, n_rows > CFPQ_NOALLOC_MAX_ROWS,
+ * n_cols > 32 * row_words), BUFFER (cap < count; *count still set), CUDA.
+ */
+int cfpq_extract_pairs_noalloc(const uint32_t *bits, uint32_t n_rows, uint32_t n_cols, uint32_t row_words,
+                               int32_t A, cfpq_triple *out, size_t cap, size_t *count, void *stream);
 
 #ifdef __cplusplus
 }

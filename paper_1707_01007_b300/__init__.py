@@ -93,6 +93,8 @@ SIGNATURES = {
     "cfpq_grammar_name": (ctypes.c_char_p, [_VP, ctypes.c_int32]),
     "cfpq_grammar_free": (None, [_VP]),
     "cfpq_solve_batch": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP]),
+    "cfpq_extract_pairs_noalloc": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                  ctypes.c_int32, _VP, ctypes.c_size_t, _P(ctypes.c_size_t), _VP]),
 }
 EXPORTS = sorted(SIGNATURES)
 
@@ -237,6 +239,19 @@ class Query:
 
     def __del__(self):
         self.close()
+
+
+def extract_pairs_noalloc(bits_ptr: int, n_rows: int, n_cols: int, row_words: int, A: int, out_ptr: int,
+                          cap: int, stream=None) -> int:
+    """Pairs of a caller-owned bit-packed device matrix written as (A, m, n) triples into a
+    caller-owned device buffer, without any allocation by the library
+    (``cfpq_extract_pairs_noalloc``); returns the number of pairs."""
+    c = ctypes.c_size_t()
+    code = _lib().cfpq_extract_pairs_noalloc(ctypes.c_void_p(bits_ptr), n_rows, n_cols, row_words, A,
+                                             ctypes.c_void_p(out_ptr) if out_ptr else None, cap, ctypes.byref(c),
+                                             _stream_handle(stream))
+    _check(code, "cfpq_extract_pairs_noalloc")
+    return int(c.value)
 
 
 def solve_batch(queries, stream=None, check: bool = True) -> int:
