@@ -5,7 +5,10 @@ Workload (one GPU): the same-generation hierarchy of n = 16384 nodes (5000 class
 11384 instances, seed 0) with both same-generation grammars on the same graph (Query 1
 and the subClassOf-only query). One step = one pass of the whole path for both queries:
 matrix initialisation, the closure loop to the fixpoint, and extraction of every R_A
-into device memory.
+into device memory. The timed path is, by default, Algorithm 1 itself (Jacobi schedule,
+T <- T u T x T) with every Boolean product on the tcgen05 tensor cores; the in-place
+tensor schedule and the automatic path (sparse bit-gather products) are timed on the same
+workload and reported beside it.
 
 metric: Boolean GOPS. The work of a step is the work of Algorithm 1 on the workload:
 sum over queries of (loop executions of Algorithm 1) x (binary productions) x 2 n^3, a
@@ -14,7 +17,8 @@ time. `value` is device-timed (CUDA events on the launching stream, inputs resid
 HBM); `e2e` is the same metric through the C ABI with host buffers (edge upload, solve,
 triples copied back) inside the timed region.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--path auto|tensor|gather]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--path tensor|auto|gather]
+                    [--schedule jacobi|inplace]
     python bench.py --impl reference ...      # the CPU oracle on the same workload
 """
 from __future__ import annotations
@@ -45,10 +49,20 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--path", default="auto", choices=["auto", "tensor", "gather"])
+    ap.add_argument("--path", default="tensor", choices=["auto", "tensor", "gather"])
+    ap.add_argument("--schedule", default="jacobi", choices=["jacobi", "inplace"])
+    ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    return ap.parse_args()
+    ap.add_argument("--n", type=int, default=None, help="smaller hierarchy for profiling captures")
+    ap.add_argument("--classes", type=int, default=None)
+    a = ap.parse_args()
+    global N_NODES, N_CLASSES, WORKLOAD
+    if a.n:
+        N_NODES = a.n
+        N_CLASSES = a.classes or max(1, round(N_NODES * 5000 / 16384))
+        WORKLOAD = WORKLOAD.replace("n=16384 (5000 classes)", f"n={N_NODES} ({N_CLASSES} classes)")
+    return a
 
 
 def workload():
@@ -163,14 +177,38 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------------------------ GPU arm
 
-def roofline(eng, graph, gs, path, stream):
-    """Average duration of the dominant product kernel over a profiled solve (CUDA events
-    around every product launch on the launching stream), against its algorithmic work."""
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tc_bool_gemm_hier16k_dram.txt")
+TC_SOURCE = os.path.join(ROOT, "paper_1707_01007_b300", "csrc", "cfpq_tensor.cu")
+
+
+def tc_traffic_per_launch():
+    """DRAM bytes per k_tc_bool_gemm launch from the committed ncu summary, or None when the
+    summary is missing or the kernel source changed since the counters were taken."""
+    import hashlib
+
+    try:
+        vals = {}
+        for ln in open(TRAFFIC_FILE):
+            if ":" in ln:
+                k, v = ln.split(":", 1)
+                vals[k.strip()] = v.strip()
+        src = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
+        if vals.get("source_sha256") != src:
+            return None
+        return float(vals["dram_bytes_per_launch_S_group"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def roofline(eng, graph, gs, path, schedule, stream):
+    """Dominant product kernel: every product launch of a solve with the timed options is
+    bracketed by CUDA events on the launching stream (profile mode); algorithmic work per
+    launch is 2 n^3 per production of the group (tensor) or the counted words (gather)."""
     peaks, kind = load_peaks()
     prod_ms = prod_l = tens_ms = tens_l = 0
     flops = bytes_ = 0.0
     for g in gs:
-        q = eng.Query(g, graph.n, graph.edges, path=path, profile=True)
+        q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, profile=True, timeout_s=300.0)
         q.solve(stream)
         s = q.stats()
         prod_ms += s["product_ms"]
@@ -182,18 +220,55 @@ def roofline(eng, graph, gs, path, stream):
         q.close()
     if tens_l > 0 and tens_ms >= 0.5 * prod_ms:
         achieved = flops / (tens_ms / 1e3) / 1e12
-        peak = 2.0 * peaks["bf16_tflops_sustained"]
+        peak = 2.0 * peaks["bf16_tflops"]
+        sustained = 2.0 * peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_tc_bool_gemm", "launch_ms": tens_ms / tens_l,
-                "peak_note": f"{kind} sustained bf16 dense x 2 (fp8 e4m3 nominal ratio)"}
+                "traffic": tc_traffic_per_launch(), "kernel": "k_tc_bool_gemm", "launches": tens_l,
+                "launch_ms": tens_ms / tens_l, "flops_per_launch": flops / tens_l,
+                "peak_note": f"{kind} bf16 dense burst x 2 (fp8 e4m3 : bf16 nominal ratio); "
+                             f"frac against the sustained figure x 2: {achieved / sustained:.3f}"}
     gather_ms = prod_ms - tens_ms
     launches = max(1, prod_l - tens_l)
     achieved = bytes_ / (gather_ms / 1e3) / 1e9 if gather_ms > 0 else None
     peak = peaks["hbm_gbs"]
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None, "kernel": "k_gather",
-            "launch_ms": gather_ms / launches, "bytes_per_launch": bytes_ / launches,
+            "launches": launches, "launch_ms": gather_ms / launches, "bytes_per_launch": bytes_ / launches,
             "peak_note": f"{kind} HBM copy bandwidth"}
+
+
+class Leg:
+    """The queries of the workload resident on the device with one set of options."""
+
+    def __init__(self, eng, torch, graph, gs, path, schedule, stream):
+        self.eng, self.torch, self.gs, self.stream = eng, torch, gs, stream
+        self.qs = [eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0) for g in gs]
+        caps = []
+        for q, g in zip(self.qs, gs):
+            q.solve(stream)
+            caps.append([max(1, q.count(nm)) for nm in g.names])
+        self.bufs = [[torch.empty(c * 3, dtype=torch.int32, device="cuda") for c in cl] for cl in caps]
+
+    def step(self):
+        for q, g, bl in zip(self.qs, self.gs, self.bufs):
+            q.solve(self.stream)
+            for nm, b in zip(g.names, bl):
+                q.get_device(nm, b.data_ptr(), b.numel() // 3)
+
+    def time(self, steps):
+        torch = self.torch
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(steps):
+            self.step()
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def close(self):
+        for q in self.qs:
+            q.close()
 
 
 def engine_arm(args):
@@ -208,59 +283,62 @@ def engine_arm(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    path = {"tensor": eng.PATH_TENSOR, "gather": eng.PATH_GATHER, "auto": eng.PATH_AUTO}[args.path]
+    paths = {"tensor": eng.PATH_TENSOR, "gather": eng.PATH_GATHER, "auto": eng.PATH_AUTO}
+    path = paths[args.path]
+    schedule = eng.SCHED_JACOBI if args.schedule == "jacobi" else eng.SCHED_INPLACE
 
     graph, grammars = workload()
     gs = [eng.Grammar(t, graph.labels) for _, t in grammars]
     stream = torch.cuda.current_stream()
-    # work of Algorithm 1 on this workload: its loop count from a Jacobi-schedule solve
+    # work of Algorithm 1 on this workload: loop executions x productions, from a Jacobi solve
     products = 0
     for g in gs:
-        qj = eng.Query(g, graph.n, graph.edges, schedule=eng.SCHED_JACOBI, path=eng.PATH_GATHER)
+        qj = eng.Query(g, graph.n, graph.edges, schedule=eng.SCHED_JACOBI, path=eng.PATH_GATHER, timeout_s=300.0)
         qj.solve(stream)
-        products += qj.stats()["iterations"] * len({(r.lhs, r.b, r.c) for r in
-                                                    (g.cnf.contents.binary[i] for i in range(g.cnf.contents.n_binary))})
+        nprod = len({(g.cnf.contents.binary[i].lhs, g.cnf.contents.binary[i].b, g.cnf.contents.binary[i].c)
+                     for i in range(g.cnf.contents.n_binary)})
+        products += qj.stats()["iterations"] * nprod
         qj.close()
     ops_per_step = products * 2.0 * float(N_NODES) ** 3
 
-    qs = [eng.Query(g, graph.n, graph.edges, path=path, timeout_s=300.0) for g in gs]
-    caps = []
-    for q, g in zip(qs, gs):
-        q.solve(stream)
-        caps.append([max(1, q.count(nm)) for nm in g.names])
-    bufs = [[torch.empty(c * 3, dtype=torch.int32, device="cuda") for c in cl] for cl in caps]
-
-    def step():
-        for q, g, bl in zip(qs, gs, bufs):
-            q.solve(stream)
-            for nm, b in zip(g.names, bl):
-                q.get_device(nm, b.data_ptr(), b.numel() // 3)
-
+    main = Leg(eng, torch, graph, gs, path, schedule, stream)
     for _ in range(args.warmup):
-        step()
-    st = [q.stats() for q in qs]
+        main.step()
+    st = [q.stats() for q in main.qs]
     launches_per_step = sum(s["kernel_launches"] + 3 * len(g.names) for s, g in zip(st, gs))
 
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms = main.time(args.steps)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * ops_per_step / (ms / 1e3) / 1e9
+    executed_dense = sum(s["dense_ops"] for s in st)
+    results = {g.names[0]: q.count(g.names[0]) for g, q in zip(gs, main.qs)}
+    main.close()
+
+    # the same closure with the other schedules / product paths (exact results in all)
+    alternatives = {}
+    if not args.no_alternatives:
+        for name, (pth, sch) in {"tensor_inplace": (eng.PATH_TENSOR, eng.SCHED_INPLACE),
+                                 "auto_inplace": (eng.PATH_AUTO, eng.SCHED_INPLACE)}.items():
+            if pth == path and sch == schedule:
+                continue
+            leg = Leg(eng, torch, graph, gs, pth, sch, stream)
+            leg.step()
+            ams = leg.time(max(2, min(args.steps, 5)))
+            alternatives[name] = {"ms_per_step": ams, "value": world * ops_per_step / (ams / 1e3) / 1e9,
+                                  "iterations": [q.stats()["iterations"] for q in leg.qs],
+                                  "tensor_products": sum(q.stats()["tensor_products"] for q in leg.qs),
+                                  "gather_products": sum(q.stats()["gather_products"] for q in leg.qs)}
+            leg.close()
 
     # e2e through the C ABI with host buffers: create (edge upload), solve, copy triples back
     h2d = graph.n_edges * 12 * len(grammars)
@@ -271,7 +349,7 @@ def engine_arm(args):
     for _ in range(e2e_steps):
         d2h = 0
         for g in gs:
-            q = eng.Query(g, graph.n, graph.edges, path=path)
+            q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0)
             q.solve()
             for nm in g.names:
                 d2h += q.triples(nm).shape[0] * 12
@@ -283,27 +361,25 @@ def engine_arm(args):
         e2e_s = float(t.item())
     e2e_val = world * ops_per_step / e2e_s / 1e9
 
-    roof = roofline(eng, graph, gs, path, stream)
+    roof = roofline(eng, graph, gs, path, schedule, stream)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "u32 bit-packed (gather); fp8 e4m3 0/1 operands, f32 accumulate (tensor)",
+        "dtype": "fp8e4m3 0/1 operands, f32 accumulate (tensor path); u32 bit-packed storage",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_NODES, "classes": N_CLASSES, "seed": SEED,
-                   "grammars": [nm for nm, _ in grammars], "path": args.path,
+                   "grammars": [nm for nm, _ in grammars], "path": args.path, "schedule": args.schedule,
                    "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (bit planes 3 x 7 x 32 MiB per query)",
-                   "products_per_step": products,
-                   "iterations_inplace": [s["iterations"] for s in st],
-                   "tensor_products": sum(s["tensor_products"] for s in st),
-                   "gather_products": sum(s["gather_products"] for s in st),
-                   "results_S": [q.count("S") for q in qs]},
+                   "l2": "inputs larger than L2 (per query 3 x 7 x 32 MiB bit planes + 7 x 32 MiB transposes)",
+                   "products_per_step": products, "dense_ops_executed_per_step": executed_dense,
+                   "iterations": [s["iterations"] for s in st], "results_start_symbol": results},
         "e2e": {"value": e2e_val, "unit": "GOPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "roofline": roof,
+        "alternatives": alternatives,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()

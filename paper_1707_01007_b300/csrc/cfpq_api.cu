@@ -205,6 +205,10 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
     c->iter_launches = 0;
     const bool prof = c->profile && !use_handle;
     for (int g = 0; g < c->n_groups; g++) {
+        if (c->group_tensor[g]) {
+            const int rc = enqueue_tensor_transposes(c, g, s);
+            if (rc != CFPQ_OK) return rc;
+        }
         if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
         if (c->group_tensor[g]) {
             const int rc = enqueue_tensor_group(c, g, s);

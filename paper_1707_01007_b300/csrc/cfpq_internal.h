@@ -67,6 +67,7 @@ uint32_t gather_chunks(uint32_t W, int *cpl);
 
 // tensor-core product path (cfpq_tensor.cu)
 bool tensor_path_available();
+int enqueue_tensor_transposes(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launches);
 void tensor_release(cfpq_ctx *c);

@@ -443,9 +443,9 @@ int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launche
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 
-// Refreshes the transposes of right operands that may have changed, then the product.
-int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
-    int rc = tensor_setup(c);
+// Refreshes the transposes of the group's right operands that may have changed.
+int enqueue_tensor_transposes(cfpq_ctx *c, int g, cudaStream_t s) {
+    const int rc = tensor_setup(c);
     if (rc != CFPQ_OK) return rc;
     std::vector<char> done(c->n_nt, 0);
     for (int r = c->gstart[g]; r < c->gstart[g + 1]; r++) {
@@ -454,6 +454,13 @@ int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
         done[C] = 1;
         launch_transpose(c, C, s, &c->iter_launches);
     }
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
+
+// The tensor-core product of group g (after enqueue_tensor_transposes).
+int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
+    const int rc = tensor_setup(c);
+    if (rc != CFPQ_OK) return rc;
     TensorWork *w = static_cast<TensorWork *>(c->h_tc_work);
     const dim3 grid(c->n_pad / tc::BN, c->n_pad / tc::BM);
     tc::k_tc_bool_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(w->tmT, w->tmTT, c->d_q, g);

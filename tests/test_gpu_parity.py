@@ -202,3 +202,14 @@ def test_resolve_is_repeatable_and_profile_mode():
     assert engine_sets(qp, g.names) == first
     s = qp.stats()
     assert s["product_launches"] == s["iterations"] * 3 and s["product_ms"] > 0
+
+
+@pytest.mark.parametrize("text", [synth.GRAMMAR_Q1, synth.GRAMMAR_QSC])
+def test_algorithm1_loop_count_matches_oracle(text):
+    # the benchmark's work per step is Algorithm 1's loop count x productions: the engine's
+    # Jacobi count and the oracle's own sparse Algorithm 1 must agree on it
+    graph = synth.hierarchy(16384, 5000, seed=0)
+    _, _, k = oracle.matrix_closure_sparse(graph, text)
+    for path in (eng.PATH_GATHER, eng.PATH_TENSOR):
+        g, q = solve_engine(graph, text, schedule=eng.SCHED_JACOBI, path=path)
+        assert q.stats()["iterations"] == k
