@@ -321,7 +321,7 @@ def engine_arm(args):
         ms = float(t.item())
     value = world * ops_per_step / (ms / 1e3) / 1e9
     executed_dense = sum(s["dense_ops"] for s in st)
-    results = {g.names[0]: q.count(g.names[0]) for g, q in zip(gs, main.qs)}
+    results = {f"{label}:{g.names[0]}": q.count(g.names[0]) for (label, _), g, q in zip(grammars, gs, main.qs)}
     main.close()
 
     # the same closure with the other schedules / product paths (exact results in all)
