@@ -14,12 +14,15 @@
 // Data flow per CTA (one 128 x 256 output tile):
 //   warp 0     TMA: bit-packed 128 x 128-bit tile of T_B and 256 x 128-bit tile of T_C^T
 //              (the transposed copy, so both operands are K-major) into a packed ring
-//   warps 2-5  unpack: 1 bit -> 1 byte, written in the 128-byte-swizzled K-major layout;
-//              within each 32-bit word, bit q + 8r goes to byte 4q' + r of the word's 32
-//              bytes (q' = q): the same permutation of K for both operands, so the
-//              contraction is unchanged and each 4 output bytes cost a shift and a mask
-//   warp 1     one thread issues tcgen05.mma (M=128, N=256, K=32) into TMEM (256 columns)
-//   warps 2-5  epilogue: tcgen05.ld, threshold, pack 32 columns per word, OR-merge into
+//   warps 2-9  unpack: 1 bit -> 1 byte. The T_B tile goes straight into tensor memory
+//              (tcgen05.st, half a 128-byte K slice per row, lane and warp), the T_C^T tile into
+//              shared memory in the 128-byte-swizzled K-major layout. Within each 32-bit
+//              word, bit q + 8r becomes byte 4q + r of the word's 32 bytes: the same
+//              permutation of K for both operands, so the contraction is unchanged, and
+//              each 4 output bytes cost a shift and a mask
+//   warp 1     one thread issues tcgen05.mma (M=128, N=256, K=32, A from tensor memory,
+//              B from shared memory) into the TMEM accumulator (256 columns)
+//   warps 2-9  epilogue: tcgen05.ld, threshold, pack 32 columns per word, OR-merge into
 //              T_A, record the new pairs (delta plane, row bitmap), set the change flag
 // Every mbarrier wait is bounded (%globaltimer); on expiry the CTA records an error,
 // drains what it started and returns.
@@ -37,15 +40,19 @@ namespace tc {
 constexpr int BM = 128, BN = 256;
 constexpr int KW = 4;                 // 32-bit words of K per stage
 constexpr int BK = 32 * KW;           // 128 K elements per stage
-constexpr int PST = 4, UST = 3;       // packed / unpacked ring depths
+constexpr int PST = 8, UST = 5;       // packed / unpacked ring depths
 constexpr int A_PACK = BM * KW * 4, B_PACK = BN * KW * 4;
 constexpr int A_TILE = BM * BK, B_TILE = BN * BK;
-constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int UNPACK_WARPS = 8;      // two per SM sub-partition
+constexpr int UNPACK_THREADS = 32 * UNPACK_WARPS;
+constexpr int THREADS = 64 + UNPACK_THREADS;
+constexpr uint32_t ACC_COLS = 256;                 // F32 accumulator, 128 lanes x 256 columns
+constexpr uint32_t A_COLS = BK / 4;                // one stage of A: 128 FP8 per lane = 32 columns
+constexpr uint32_t TMEM_COLS = 512;                // accumulator + UST stages of A, power of two
+static_assert(ACC_COLS + UST * A_COLS <= TMEM_COLS, "tensor memory budget");
 constexpr unsigned long long WAIT_LIMIT_NS = 2ull * 1000 * 1000 * 1000;  // 2 s per wait
 
 struct __align__(1024) Smem {
-    uint8_t a_tile[UST][A_TILE];
     uint8_t b_tile[UST][B_TILE];
     uint32_t a_pack[PST][BM * KW];
     uint32_t b_pack[PST][BN * KW];
@@ -113,11 +120,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 // Instruction descriptor: kind::f8f6f4, A = B = E4M3, D = F32, both K-major, M x N.
 constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
-__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+// D[tmem] (+)= A[tmem] x B[smem]^T
+__device__ __forceinline__ void mma_f8_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t accumulate) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}" ::"r"(
             tmem_d),
-        "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate)
+        "r"(tmem_a), "l"(bd), "r"(IDESC), "r"(accumulate)
         : "memory");
 }
 
@@ -139,6 +147,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
           "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
 }
 
 // 4 bytes of the unpacked K-row: byte r = bit (q + 8r) of w, as FP8 E4M3 0x08 (2^-6) or 0.
@@ -164,6 +192,19 @@ __device__ __forceinline__ void unpack_row(uint8_t *tile, int r, uint4 p) {
         }
 }
 
+// Half (64 bytes, words 2h and 2h+1) of the same 128-byte K slice as unpack_row, as 16 TMEM
+// columns of one lane: column j of the slice holds logical bytes 4j .. 4j+3, i.e.
+// spread(word j/8, j%8); this half is columns 16h .. 16h+15.
+__device__ __forceinline__ void unpack_half_row_tmem(uint32_t taddr, uint2 p) {
+    uint32_t v[16];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        v[j] = spread(p.x, j);
+        v[8 + j] = spread(p.y, j);
+    }
+    tmem_st16(taddr, v);
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_bool_gemm(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmTT, const QDesc *qd,
                    int g) {
@@ -183,10 +224,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < PST; i++) {
             mbar_init(&S.full_p[i], 1);
-            mbar_init(&S.empty_p[i], 128);
+            mbar_init(&S.empty_p[i], UNPACK_THREADS);
         }
         for (int i = 0; i < UST; i++) {
-            mbar_init(&S.full_u[i], 128);
+            mbar_init(&S.full_u[i], UNPACK_THREADS);
             mbar_init(&S.empty_u[i], 1);
         }
         mbar_init(&S.acc_full, 1);
@@ -230,40 +271,44 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            const uint32_t a0 = sa(S.a_tile[0]), b0 = sa(S.b_tile[0]);
+            const uint32_t b0 = sa(S.b_tile[0]);
             for (uint32_t s = 0; s < total; s++) {
                 const uint32_t slot = s % UST, ph = (s / UST) & 1u;
                 if (!mbar_wait(&S.full_u[slot], ph, err)) break;
                 tc_fence_after();
-                const uint32_t at = a0 + slot * A_TILE, bt = b0 + slot * B_TILE;
+                const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + slot * B_TILE;
 #pragma unroll
                 for (int kk = 0; kk < BK / 32; kk++)
-                    mma_f8(tmem, sdesc(at + kk * 32), sdesc(bt + kk * 32), (s > 0 || kk > 0) ? 1u : 0u);
+                    mma_f8_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), (s > 0 || kk > 0) ? 1u : 0u);
                 mma_commit(&S.empty_u[slot]);
             }
             mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
         }
     } else {
-        // ---------------- unpack (128 threads), then epilogue
-        const int t = threadIdx.x - 64;
+        // ---------------- unpack (8 warps), then epilogue
+        const int t = threadIdx.x - 64;             // 0 .. 255: the B row of this thread
+        const int quad = warp & 3;                  // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;           // which half of the A slice / of the columns
+        const int arow = quad * 32 + lane;
+        const uint32_t a_lane = tmem + ((uint32_t)(quad * 32) << 16) + ACC_COLS + (uint32_t)(16 * half);
         for (uint32_t s = 0; s < total; s++) {
             const uint32_t ps = s % PST, pph = (s / PST) & 1u;
             const uint32_t us = s % UST, uph = (s / UST) & 1u;
             if (!mbar_wait(&S.full_p[ps], pph, err)) break;
             if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) break;
-            const uint4 pa = reinterpret_cast<const uint4 *>(S.a_pack[ps])[t];
-            const uint4 pb0 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
-            const uint4 pb1 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t + 128];
-            unpack_row(S.a_tile[us], t, pa);
-            unpack_row(S.b_tile[us], t, pb0);
-            unpack_row(S.b_tile[us], t + 128, pb1);
+            tc_fence_after();
+            const uint2 pa = reinterpret_cast<const uint2 *>(S.a_pack[ps])[2 * arow + half];
+            const uint4 pb = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
             mbar_arrive(&S.empty_p[ps]);
+            unpack_half_row_tmem(a_lane + us * A_COLS, pa);
+            unpack_row(S.b_tile[us], t, pb);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
             mbar_arrive(&S.full_u[us]);
         }
         const bool ok = mbar_wait(&S.acc_full, 0, err);
         tc_fence_after();
-        const int quad = warp & 3;
         const uint32_t row = m0 + quad * 32 + lane;
         const uint32_t W = q.W;
         const bool inplace = q.schedule == CFPQ_SCHED_INPLACE;
@@ -273,7 +318,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t *TA = q.T + (uint64_t)A * q.plane;
         unsigned cnt = 0;
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; c++) {
+        for (int c = half * (BN / 64); c < (half + 1) * (BN / 64); c++) {
             uint32_t v[32];
             tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
             uint32_t word = 0;
