@@ -321,3 +321,30 @@ def test_sparse_algorithm1_equals_dense(seed):
     assert k == k2
     for a in range(len(cnf.names)):
         assert (T[a].toarray() != 0).tolist() == snaps[-1][a].tolist()
+
+
+def test_property_checks_detect_broken_results():
+    """The property checks must reject results with a pair removed or a seed missing."""
+    g = synth.hierarchy(300, 90, seed=7)
+    cnf = oracle.parse_grammar(synth.GRAMMAR_Q1, g.labels)
+    res = oracle.hellings(g, synth.GRAMMAR_Q1)
+    good = {nm: res.pairs(nm) for nm in cnf.names}
+    assert oracle.check_closed(cnf, g.n, good) and oracle.check_seed_included(cnf, g.n, g.edges, good)
+    # drop a derived pair of S: the closure check fails (some product now points outside R_S)
+    broken = dict(good)
+    x_pairs = good["X"]
+    # an S pair that is produced from SCR x X: remove it
+    scr = set(map(tuple, good["<sc_r>"].tolist()))
+    xs = set(map(tuple, x_pairs.tolist()))
+    produced = {(i, j) for (i, k) in scr for (k2, j) in xs if k == k2}
+    victim = sorted(produced)[0]
+    broken["S"] = np.array([p for p in good["S"].tolist() if tuple(p) != victim], dtype=np.uint32)
+    assert not oracle.check_closed(cnf, g.n, broken)
+    # drop a seed pair
+    broken2 = dict(good)
+    broken2["SC"] = good["SC"][1:]
+    assert not oracle.check_seed_included(cnf, g.n, g.edges, broken2)
+    # add a pair with no derivation: the witness check fails
+    broken3 = dict(good)
+    broken3["S"] = np.concatenate([good["S"], np.array([[g.n - 1, g.n - 1]], dtype=np.uint32)])
+    assert not oracle.check_witnessed(cnf, g.n, g.edges, broken3)
