@@ -35,6 +35,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import cfpq_synth as synth  # noqa: E402
 
 N_NODES, N_CLASSES, SEED = 16384, 5000, 0
@@ -54,6 +56,8 @@ def parse():
     ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="hier16k", choices=["hier16k", "batch256", "serve"],
+                    help="hier16k: the default line; batch256 / serve: the batched and served workloads")
     ap.add_argument("--n", type=int, default=None, help="smaller hierarchy for profiling captures")
     ap.add_argument("--classes", type=int, default=None)
     a = ap.parse_args()
@@ -399,10 +403,101 @@ def engine_arm(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------ batched / served
+
+def batch_arm(args):
+    """256 independent hierarchy queries (n log-uniform in [64, 4096], class fraction 0.3,
+    grammar Q1 or sc-only uniformly, seed 0): one grouped persistent launch vs the same
+    queries solved one at a time with the single-query path."""
+    import torch
+
+    import paper_1707_01007_b300 as eng
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    work = synth.batch_queries(256, 64, 4096, 0.3, seed=0)
+    gs = [eng.Grammar(t, g.labels) for g, t in work]
+    qs = [eng.Query(gr, g.n, g.edges, path=eng.PATH_GATHER) for (g, _), gr in zip(work, gs)]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for _ in range(args.warmup):
+        eng.solve_batch(qs, stream)
+    ms_batch = timed(lambda: eng.solve_batch(qs, stream), args.steps)
+
+    def serial():
+        for q in qs:
+            q.solve(stream)
+    serial()
+    ms_serial = timed(serial, max(1, min(args.steps, 3)))
+    line = {"metric": "queries/s, 256 batched hierarchy queries (closure to fixpoint)",
+            "value": 256 / (ms_batch / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
+            "config": {"workload": "256 hierarchy queries, n log-uniform [64, 4096], class fraction 0.3, "
+                                   "Q1 or sc-only uniformly, seed 0", "path": "gather (grouped launch)"},
+            "serial_ms": ms_serial, "serial_queries_per_s": 256 / (ms_serial / 1e3),
+            "speedup_vs_serial": ms_serial / ms_batch}
+    print(json.dumps(line))
+    return 0
+
+
+def serve_arm(args):
+    """Poisson stream of 2000 hierarchy queries (n log-uniform in [128, 32768], both grammars)
+    plus one n = 65536 Query 1 query, at 0.7x and 1.5x the measured serial throughput: the
+    continuous-batching server against serial FIFO solves of the same stream."""
+    import torch
+
+    import paper_1707_01007_b300 as eng
+    from paper_1707_01007_b300 import serve
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    count = 2000 if args.n is None else args.n
+    work = synth.batch_queries(count, 128, 32768, 0.3, seed=5)
+    big = synth.hierarchy(65536, round(65536 * 0.3), seed=5)
+    work = work[: count // 2] + [(big, synth.GRAMMAR_Q1)] + work[count // 2:]
+    queries = [(eng.Grammar(t, g.labels), g.n, g.edges) for g, t in work]
+    # serial throughput on the stream's first 200 queries, all available at time 0
+    probe = queries[:200]
+    sp = serve.run_serial(probe, np.zeros(len(probe)))
+    thr = sp["queries_per_s"]
+    out = {"serial_probe_queries_per_s": thr}
+    for load in (0.7, 1.5):
+        arr = synth.poisson_arrivals(len(queries), rate_per_s=load * thr, seed=17)
+        srv = eng.Server(rounds_per_step=4)
+        s_sum, _ = serve.run_server(srv, queries, arr)
+        stats = srv.stats()
+        srv.close()
+        f_sum = serve.run_serial(queries, arr)
+        out[f"load_{load}"] = {"server": s_sum, "serial_fifo": f_sum, "server_launches": stats["launches"],
+                               "peak_hbm_bytes": stats["peak_used_bytes"], "budget_bytes": stats["budget_bytes"]}
+    top = out["load_1.5"]["server"]
+    line = {"metric": "queries/s and p50/p99 latency, served Poisson stream", "value": top["queries_per_s"],
+            "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
+            "config": {"workload": f"{len(queries)} hierarchy queries, n log-uniform [128, 32768] + one n=65536 Q1, "
+                                   "Poisson arrivals at 0.7x and 1.5x serial throughput", "rounds_per_step": 4},
+            "detail": out}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batch256":
+        return batch_arm(args)
+    if args.workload == "serve":
+        return serve_arm(args)
     return engine_arm(args)
 
 

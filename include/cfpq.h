@@ -200,6 +200,67 @@ void cfpq_grammar_free(cfpq_parsed_grammar *pg);
 int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream);
 
 /*
+ * Serving (continuous batching). A server takes independent queries (grammar + graph) at
+ * any time, admits them in arrival order while their device footprint fits in an HBM
+ * budget, and advances all resident queries together: each cfpq_server_step is one
+ * persistent grouped launch that seeds the newly admitted queries and runs up to
+ * rounds_per_step executions of Algorithm 1's loop body (Section 4.2) for every resident
+ * query. A query whose loop stopped is retired: its R_A are copied to host memory and its
+ * device memory is returned to a stream-ordered pool at once. Each query's result equals
+ * solving it alone (its own least fixpoint).
+ */
+typedef struct cfpq_server cfpq_server;
+
+enum cfpq_query_state { CFPQ_QUERY_QUEUED = 0, CFPQ_QUERY_RUNNING = 1, CFPQ_QUERY_DONE = 2, CFPQ_QUERY_FAILED = 3 };
+
+typedef struct {
+    uint64_t hbm_budget_bytes;  /* device bytes resident queries may hold; 0 = 90 % of free memory at creation */
+    int32_t rounds_per_step;    /* loop executions per step for every resident query; 0 = 4 */
+    int32_t max_resident;       /* upper bound on resident queries; 0 = 4096 */
+} cfpq_server_options;
+
+typedef struct {
+    int32_t state;              /* enum cfpq_query_state */
+    int32_t status;             /* CFPQ_OK, NOMEM (larger than the whole budget), ITER_LIMIT, ... */
+    int64_t iterations;         /* loop executions (when finished) */
+    int32_t n_nonterm;          /* number of relations available (when finished) */
+    int32_t reserved;
+} cfpq_query_info;
+
+typedef struct {
+    int64_t queued, resident, completed, failed, launches, steps;
+    uint64_t budget_bytes, used_bytes, peak_used_bytes;
+} cfpq_server_stats;
+
+/* Fills *opt with the defaults. Errors: INVALID. */
+int cfpq_server_options_default(cfpq_server_options *opt);
+/* Creates a server on the current device. Errors: INVALID, NOMEM, CUDA. */
+int cfpq_server_create(const cfpq_server_options *opt, cfpq_server **out);
+/* Queues a query (inputs copied; schedule = enum cfpq_schedule) and returns its ticket.
+ * Nothing runs until cfpq_server_step. Errors: INVALID (as cfpq_create). */
+int cfpq_server_submit(cfpq_server *s, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges,
+                       size_t n_edges, int32_t schedule, int64_t *ticket);
+/* Admission, one grouped launch, retirement; *n_completed (may be NULL) receives the number
+ * of queries that finished or failed in this step. Errors: CUDA, TIMEOUT (a bounded device
+ * wait gave up). */
+int cfpq_server_step(cfpq_server *s, int32_t *n_completed);
+/* Tickets that finished or failed since the previous call (then forgotten by this list);
+ * tickets == NULL: only *count. Errors: INVALID, BUFFER (cap < count). */
+int cfpq_server_completed(cfpq_server *s, int64_t *tickets, size_t cap, size_t *count);
+/* State of a ticket. Errors: INVALID (unknown or released ticket). */
+int cfpq_server_query_info(const cfpq_server *s, int64_t ticket, cfpq_query_info *out);
+/* R_A of a finished query as triples sorted by (m, n), host memory, two-call size query.
+ * Errors: INVALID, NOT_SOLVED (still queued or running), BUFFER, the query's own failure status. */
+int cfpq_server_result(const cfpq_server *s, int64_t ticket, int32_t A, cfpq_triple *buf, size_t cap,
+                       size_t *count);
+/* Forgets a finished query's host results. Errors: INVALID (unknown or unfinished ticket). */
+int cfpq_server_release(cfpq_server *s, int64_t ticket);
+/* Counters of the server. Errors: INVALID. */
+int cfpq_server_stats_get(const cfpq_server *s, cfpq_server_stats *out);
+/* Waits for the server's device work, frees everything; NULL is ignored. */
+void cfpq_server_destroy(cfpq_server *s);
+
+/*
  * Allocation-free pair extraction (the paper has no counterpart; it is an interface for
  * callers that cannot allocate device memory, e.g. code under an external allocator that
  * owns the device heap, or paths where cudaMalloc is forbidden after start-up).

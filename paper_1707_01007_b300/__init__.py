@@ -72,6 +72,28 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("rounds_per_step", ctypes.c_int32),
+                ("max_resident", ctypes.c_int32)]
+
+
+class QueryInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("iterations", ctypes.c_int64),
+                ("n_nonterm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("launches", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_uint64), ("used_bytes", ctypes.c_uint64),
+                ("peak_used_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+QUERY_QUEUED, QUERY_RUNNING, QUERY_DONE, QUERY_FAILED = range(4)
+
 _LIB = None
 
 _P, _VP = ctypes.POINTER, ctypes.c_void_p
@@ -93,6 +115,18 @@ SIGNATURES = {
     "cfpq_grammar_name": (ctypes.c_char_p, [_VP, ctypes.c_int32]),
     "cfpq_grammar_free": (None, [_VP]),
     "cfpq_solve_batch": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP]),
+    "cfpq_server_options_default": (ctypes.c_int, [_P(ServerOptions)]),
+    "cfpq_server_create": (ctypes.c_int, [_P(ServerOptions), _P(_VP)]),
+    "cfpq_server_submit": (ctypes.c_int, [_VP, _P(GrammarCNF), ctypes.c_uint32, _P(Edge), ctypes.c_size_t,
+                                          ctypes.c_int32, _P(ctypes.c_int64)]),
+    "cfpq_server_step": (ctypes.c_int, [_VP, _P(ctypes.c_int32)]),
+    "cfpq_server_completed": (ctypes.c_int, [_VP, _P(ctypes.c_int64), ctypes.c_size_t, _P(ctypes.c_size_t)]),
+    "cfpq_server_query_info": (ctypes.c_int, [_VP, ctypes.c_int64, _P(QueryInfo)]),
+    "cfpq_server_result": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int32, _P(Triple), ctypes.c_size_t,
+                                          _P(ctypes.c_size_t)]),
+    "cfpq_server_release": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "cfpq_server_stats_get": (ctypes.c_int, [_VP, _P(ServerStats)]),
+    "cfpq_server_destroy": (None, [_VP]),
     "cfpq_extract_pairs_noalloc": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                   ctypes.c_int32, _VP, ctypes.c_size_t, _P(ctypes.c_size_t), _VP]),
 }
@@ -252,6 +286,73 @@ def extract_pairs_noalloc(bits_ptr: int, n_rows: int, n_cols: int, row_words: in
                                              _stream_handle(stream))
     _check(code, "cfpq_extract_pairs_noalloc")
     return int(c.value)
+
+
+class Server:
+    """Continuous-batching server (``cfpq_server_*``): submit queries at any time, call
+    ``step()`` to admit, advance and retire; results of finished queries stay on the host."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, rounds_per_step: int = 4, max_resident: int = 0):
+        o = ServerOptions()
+        _lib().cfpq_server_options_default(ctypes.byref(o))
+        o.hbm_budget_bytes, o.rounds_per_step, o.max_resident = int(hbm_budget_bytes), int(rounds_per_step), \
+            int(max_resident)
+        h = ctypes.c_void_p()
+        _check(_lib().cfpq_server_create(ctypes.byref(o), ctypes.byref(h)), "cfpq_server_create")
+        self._h = h
+
+    def submit(self, grammar: Grammar, n: int, edges, schedule: int = SCHED_INPLACE) -> int:
+        rec = _edges_struct(edges)
+        t = ctypes.c_int64()
+        ptr = rec.ctypes.data_as(ctypes.POINTER(Edge)) if rec.size else None
+        _check(_lib().cfpq_server_submit(self._h, grammar.cnf, int(n), ptr, rec.size, schedule, ctypes.byref(t)),
+               "cfpq_server_submit")
+        return int(t.value)
+
+    def step(self) -> int:
+        c = ctypes.c_int32()
+        _check(_lib().cfpq_server_step(self._h, ctypes.byref(c)), "cfpq_server_step")
+        return int(c.value)
+
+    def completed(self) -> list:
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_server_completed(self._h, None, 0, ctypes.byref(c)), "cfpq_server_completed")
+        buf = (ctypes.c_int64 * max(1, c.value))()
+        _check(_lib().cfpq_server_completed(self._h, buf, c.value, ctypes.byref(c)), "cfpq_server_completed")
+        return [int(buf[i]) for i in range(c.value)]
+
+    def info(self, ticket: int) -> dict:
+        q = QueryInfo()
+        _check(_lib().cfpq_server_query_info(self._h, ticket, ctypes.byref(q)), "cfpq_server_query_info")
+        return {"state": q.state, "status": q.status, "iterations": q.iterations, "n_nonterm": q.n_nonterm}
+
+    def result(self, ticket: int, A: int) -> np.ndarray:
+        """R_A of a finished query as a sorted (k, 2) uint32 array of (m, n)."""
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_server_result(self._h, ticket, A, None, 0, ctypes.byref(c)), "cfpq_server_result")
+        k = int(c.value)
+        buf = np.zeros(max(k, 1), dtype=[("A", "<i4"), ("m", "<u4"), ("n", "<u4")])
+        _check(_lib().cfpq_server_result(self._h, ticket, A, buf.ctypes.data_as(ctypes.POINTER(Triple)), k,
+                                         ctypes.byref(c)), "cfpq_server_result")
+        buf = buf[:k]
+        return np.stack([buf["m"], buf["n"]], axis=1).astype(np.uint32)
+
+    def release(self, ticket: int):
+        _check(_lib().cfpq_server_release(self._h, ticket), "cfpq_server_release")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib().cfpq_server_stats_get(self._h, ctypes.byref(st)), "cfpq_server_stats_get")
+        return st.as_dict()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h and _LIB is not None:
+            _LIB.cfpq_server_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def solve_batch(queries, stream=None, check: bool = True) -> int:

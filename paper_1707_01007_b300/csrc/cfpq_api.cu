@@ -285,7 +285,10 @@ void free_ctx_device(cfpq_ctx *c) {
                     c->d_unary, c->d_eps, c->d_edges, c->d_state, c->d_q, c->d_counts, c->d_offsets,
                     c->d_total, c->d_triples, c->d_tc_work};
     for (void *p : ptrs)
-        if (p) cudaFree(p);
+        if (p) {
+            if (c->pooled) cudaFreeAsync(p, c->stream);
+            else cudaFree(p);
+        }
     for (auto e : c->prof_ev)
         if (e) cudaEventDestroy(e);
     c->prof_ev.clear();
@@ -398,8 +401,10 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         c->group_tensor.assign(std::max(1, c->n_groups), 1);
     }
 
-    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-    c->own_stream = true;
+    if (!c->pooled) {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
     c->last_stream = c->stream;
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
@@ -410,7 +415,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
     const size_t rowsz = (size_t)c->n_nt * c->W * sizeof(uint32_t);
     auto alloc = [&](void **p, size_t bytes) -> int {
-        const cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        const cudaError_t e = c->pooled ? cudaMallocAsync(p, std::max<size_t>(bytes, 16), c->stream)
+                                        : cudaMalloc(p, std::max<size_t>(bytes, 16));
         if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); *p = nullptr; return CFPQ_ERR_NOMEM; }
         if (e != cudaSuccess) { *p = nullptr; return CFPQ_ERR_CUDA; }
         return CFPQ_OK;
@@ -435,11 +441,16 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     if ((rc = alloc((void **)&c->d_counts, c->n_pad * sizeof(uint32_t)))) return rc;
     if ((rc = alloc((void **)&c->d_offsets, c->n_pad * sizeof(uint64_t)))) return rc;
     if ((rc = alloc((void **)&c->d_total, sizeof(unsigned long long)))) return rc;
-    if (!rules.empty()) CK(cudaMemcpy(c->d_rules, rules.data(), rules.size() * sizeof(Rule), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->d_gstart, gstart.data(), gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    if (!unary.empty()) CK(cudaMemcpy(c->d_unary, unary.data(), unary.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    if (!eps.empty()) CK(cudaMemcpy(c->d_eps, eps.data(), eps.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    if (n_edges) CK(cudaMemcpy(c->d_edges, edges, n_edges * sizeof(cfpq_edge), cudaMemcpyHostToDevice));
+    // copies are stream-ordered after the (possibly stream-ordered) allocations; the host
+    // sources are pageable, so each call returns once its source has been staged
+    cudaStream_t cs = c->stream;
+    if (!rules.empty())
+        CK(cudaMemcpyAsync(c->d_rules, rules.data(), rules.size() * sizeof(Rule), cudaMemcpyHostToDevice, cs));
+    CK(cudaMemcpyAsync(c->d_gstart, gstart.data(), gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, cs));
+    if (!unary.empty())
+        CK(cudaMemcpyAsync(c->d_unary, unary.data(), unary.size() * sizeof(int2), cudaMemcpyHostToDevice, cs));
+    if (!eps.empty()) CK(cudaMemcpyAsync(c->d_eps, eps.data(), eps.size() * sizeof(int32_t), cudaMemcpyHostToDevice, cs));
+    if (n_edges) CK(cudaMemcpyAsync(c->d_edges, edges, n_edges * sizeof(cfpq_edge), cudaMemcpyHostToDevice, cs));
     QDesc q;
     memset(&q, 0, sizeof(q));
     q.n = n;
@@ -468,8 +479,70 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.edges = c->d_edges;
     q.st = c->d_state;
     c->hq = q;
-    CK(cudaMemcpy(c->d_q, &q, sizeof(q), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(c->d_q, &q, sizeof(q), cudaMemcpyHostToDevice, cs));
+    CK(cudaStreamSynchronize(cs));  // host vectors above go out of scope
     return CFPQ_OK;
+}
+
+size_t query_footprint(uint32_t n, int n_nt, size_t n_edges, int n_rules, bool tensor) {
+    const size_t n_pad = (n + 255u) / 256u * 256u;
+    const size_t plane = n_pad * (n_pad / 32) * 4;
+    const size_t planes = (tensor ? 4 : 3) * (size_t)n_nt * plane;
+    const size_t rows = 3 * (size_t)n_nt * (n_pad / 8);
+    const size_t misc = n_edges * sizeof(cfpq_edge) + n_pad * 12 + (size_t)n_rules * 32 + 64 * 1024;
+    return planes + rows + misc;
+}
+
+int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
+                    const cfpq_options *opt) {
+    if (!g || n == 0 || n > CFPQ_MAX_NODES) return CFPQ_ERR_INVALID;
+    if (g->n_nonterm <= 0 || g->n_nonterm > CFPQ_MAX_NONTERM || g->n_term < 0) return CFPQ_ERR_INVALID;
+    if (g->n_unary < 0 || g->n_binary < 0 || g->n_eps < 0) return CFPQ_ERR_INVALID;
+    if ((g->n_unary > 0 && !g->unary) || (g->n_binary > 0 && !g->binary) || (g->n_eps > 0 && !g->eps_lhs))
+        return CFPQ_ERR_INVALID;
+    if (n_edges > 0 && !edges) return CFPQ_ERR_INVALID;
+    for (int i = 0; i < g->n_unary; i++)
+        if (g->unary[i].lhs < 0 || g->unary[i].lhs >= g->n_nonterm || g->unary[i].term < 0 ||
+            g->unary[i].term >= g->n_term)
+            return CFPQ_ERR_INVALID;
+    for (int i = 0; i < g->n_binary; i++) {
+        const cfpq_rule2 r = g->binary[i];
+        if (r.lhs < 0 || r.lhs >= g->n_nonterm || r.b < 0 || r.b >= g->n_nonterm || r.c < 0 || r.c >= g->n_nonterm)
+            return CFPQ_ERR_INVALID;
+    }
+    for (int i = 0; i < g->n_eps; i++)
+        if (g->eps_lhs[i] < 0 || g->eps_lhs[i] >= g->n_nonterm) return CFPQ_ERR_INVALID;
+    for (size_t e = 0; e < n_edges; e++)
+        if (edges[e].src >= n || edges[e].dst >= n || edges[e].label < 0 || edges[e].label >= g->n_term)
+            return CFPQ_ERR_INVALID;
+    if (opt) {
+        if (opt->schedule != CFPQ_SCHED_INPLACE && opt->schedule != CFPQ_SCHED_JACOBI) return CFPQ_ERR_INVALID;
+        if (opt->path < CFPQ_PATH_AUTO || opt->path > CFPQ_PATH_GATHER) return CFPQ_ERR_INVALID;
+    }
+    return CFPQ_OK;
+}
+
+int ctx_create_pooled(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
+                      const cfpq_options &o, cudaStream_t pool_stream, cfpq_ctx **out) {
+    cfpq_ctx *c = new (std::nothrow) cfpq_ctx();
+    if (!c) return CFPQ_ERR_NOMEM;
+    c->pooled = true;
+    c->stream = pool_stream;
+    c->own_stream = false;
+    const int rc = ctx_init(c, g, n, edges, n_edges, o);
+    if (rc != CFPQ_OK) {
+        free_ctx_device(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return CFPQ_OK;
+}
+
+void ctx_destroy(cfpq_ctx *c) {
+    if (!c) return;
+    free_ctx_device(c);
+    delete c;
 }
 
 int run_loop(cfpq_ctx *c, cudaStream_t s) {
@@ -517,31 +590,12 @@ static int emit(cfpq_ctx *c, int32_t A, cfpq_triple *dev_out, cudaStream_t s) {
 
 extern "C" int cfpq_create(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
                            const cfpq_options *opt, cfpq_ctx **out) {
-    if (!g || !out || n == 0 || n > CFPQ_MAX_NODES) return CFPQ_ERR_INVALID;
-    if (g->n_nonterm <= 0 || g->n_nonterm > CFPQ_MAX_NONTERM || g->n_term < 0) return CFPQ_ERR_INVALID;
-    if (g->n_unary < 0 || g->n_binary < 0 || g->n_eps < 0) return CFPQ_ERR_INVALID;
-    if ((g->n_unary > 0 && !g->unary) || (g->n_binary > 0 && !g->binary) || (g->n_eps > 0 && !g->eps_lhs))
-        return CFPQ_ERR_INVALID;
-    if (n_edges > 0 && !edges) return CFPQ_ERR_INVALID;
-    for (int i = 0; i < g->n_unary; i++)
-        if (g->unary[i].lhs < 0 || g->unary[i].lhs >= g->n_nonterm || g->unary[i].term < 0 ||
-            g->unary[i].term >= g->n_term)
-            return CFPQ_ERR_INVALID;
-    for (int i = 0; i < g->n_binary; i++) {
-        const cfpq_rule2 r = g->binary[i];
-        if (r.lhs < 0 || r.lhs >= g->n_nonterm || r.b < 0 || r.b >= g->n_nonterm || r.c < 0 || r.c >= g->n_nonterm)
-            return CFPQ_ERR_INVALID;
-    }
-    for (int i = 0; i < g->n_eps; i++)
-        if (g->eps_lhs[i] < 0 || g->eps_lhs[i] >= g->n_nonterm) return CFPQ_ERR_INVALID;
-    for (size_t e = 0; e < n_edges; e++)
-        if (edges[e].src >= n || edges[e].dst >= n || edges[e].label < 0 || edges[e].label >= g->n_term)
-            return CFPQ_ERR_INVALID;
+    if (!out) return CFPQ_ERR_INVALID;
+    const int vrc = validate_inputs(g, n, edges, n_edges, opt);
+    if (vrc != CFPQ_OK) return vrc;
     cfpq_options o;
     cfpq_options_default(&o);
     if (opt) o = *opt;
-    if (o.schedule != CFPQ_SCHED_INPLACE && o.schedule != CFPQ_SCHED_JACOBI) return CFPQ_ERR_INVALID;
-    if (o.path < CFPQ_PATH_AUTO || o.path > CFPQ_PATH_GATHER) return CFPQ_ERR_INVALID;
 
     cfpq_ctx *c = new (std::nothrow) cfpq_ctx();
     if (!c) return CFPQ_ERR_NOMEM;
@@ -613,10 +667,14 @@ extern "C" int cfpq_get(cfpq_ctx *c, int32_t A, cfpq_triple *buf, size_t cap, si
     if (cap < total) return CFPQ_ERR_BUFFER;
     if (total == 0) return CFPQ_OK;
     if (c->triples_cap < total) {
-        if (c->d_triples) cudaFree(c->d_triples);
+        if (c->d_triples) {
+            if (c->pooled) cudaFreeAsync(c->d_triples, s);
+            else cudaFree(c->d_triples);
+        }
         c->d_triples = nullptr;
         c->triples_cap = 0;
-        const cudaError_t e = cudaMalloc(&c->d_triples, total * sizeof(cfpq_triple));
+        const cudaError_t e = c->pooled ? cudaMallocAsync(&c->d_triples, total * sizeof(cfpq_triple), s)
+                                        : cudaMalloc(&c->d_triples, total * sizeof(cfpq_triple));
         if (e != cudaSuccess) { cudaGetLastError(); c->d_triples = nullptr; return CFPQ_ERR_NOMEM; }
         c->triples_cap = total;
     }

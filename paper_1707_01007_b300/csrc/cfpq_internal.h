@@ -42,6 +42,7 @@ struct cfpq_ctx {
     // execution
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    bool pooled = false;                     // device memory from the stream-ordered pool of `stream`
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t last_stream = nullptr;      // stream of the last cfpq_solve (results are read on it)
@@ -56,6 +57,15 @@ namespace cfpq {
 
 int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
              const cfpq_options &o);
+int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
+                    const cfpq_options *opt);
+// Creates a context whose device memory comes from the stream-ordered pool of `pool_stream`
+// and which runs on that stream (used by the server); inputs must be validated already.
+int ctx_create_pooled(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
+                      const cfpq_options &o, cudaStream_t pool_stream, cfpq_ctx **out);
+void ctx_destroy(cfpq_ctx *c);
+// Bytes of device memory a context for this query holds (path GATHER unless tensor).
+size_t query_footprint(uint32_t n, int n_nt, size_t n_edges, int n_rules, bool tensor);
 void free_ctx_device(cfpq_ctx *c);
 int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s);
 int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle);

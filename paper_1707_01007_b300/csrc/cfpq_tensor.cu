@@ -41,8 +41,8 @@ constexpr int BM = 128, BN = 256;
 constexpr int KW = 4;                 // 32-bit words of K per stage
 constexpr int BK = 32 * KW;           // 128 K elements per stage
 constexpr int PST = 8, UST = 5;       // packed / unpacked ring depths
-constexpr int A_PACK = BM * KW * 4, B_PACK = BN * KW * 4;
-constexpr int A_TILE = BM * BK, B_TILE = BN * BK;
+constexpr int A_PACK = BM * KW * 4, B_PACK = BN * KW * 4;  // bytes of one packed stage
+constexpr int B_TILE = BN * BK;       // bytes of one unpacked B stage (FP8)
 constexpr int UNPACK_WARPS = 8;      // two per SM sub-partition
 constexpr int UNPACK_THREADS = 32 * UNPACK_WARPS;
 constexpr int THREADS = 64 + UNPACK_THREADS;
