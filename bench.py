@@ -472,7 +472,7 @@ def serve_arm(args):
     out = {"serial_probe_queries_per_s": thr}
     for load in (0.7, 1.5):
         arr = synth.poisson_arrivals(len(queries), rate_per_s=load * thr, seed=17)
-        srv = eng.Server(rounds_per_step=4)
+        srv = eng.Server(rounds_per_step=8)
         s_sum, _ = serve.run_server(srv, queries, arr)
         stats = srv.stats()
         srv.close()
@@ -484,7 +484,7 @@ def serve_arm(args):
             "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
             "config": {"workload": f"{len(queries)} hierarchy queries, n log-uniform [128, 32768] + one n=65536 Q1, "
-                                   "Poisson arrivals at 0.7x and 1.5x serial throughput", "rounds_per_step": 4},
+                                   "Poisson arrivals at 0.7x and 1.5x serial throughput", "rounds_per_step": 8},
             "detail": out}
     print(json.dumps(line))
     return 0

@@ -154,6 +154,10 @@ int cfpq_get(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, size_t cap, size_t *cou
  * except the count. Errors: as cfpq_get. */
 int cfpq_get_device(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, size_t cap, size_t *count);
 
+/* Every relation at once: triples (A, m, n) sorted by (A, m, n) into buf (host memory, cap
+ * triples); buf == NULL: only *count. Errors: INVALID, NOT_SOLVED, BUFFER, NOMEM, CUDA. */
+int cfpq_get_all(cfpq_ctx *ctx, cfpq_triple *buf, size_t cap, size_t *count);
+
 /* |R_A| without copying pairs. Errors: as cfpq_get. */
 int cfpq_count(cfpq_ctx *ctx, int32_t A, size_t *count);
 
@@ -205,7 +209,7 @@ int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream);
  * budget, and advances all resident queries together: each cfpq_server_step is one
  * persistent grouped launch that seeds the newly admitted queries and runs up to
  * rounds_per_step executions of Algorithm 1's loop body (Section 4.2) for every resident
- * query. A query whose loop stopped is retired: its R_A are copied to host memory and its
+ * query (fewer for large queries, so small ones are not held to their pace). A query whose loop stopped is retired: its R_A are copied to host memory and its
  * device memory is returned to a stream-ordered pool at once. Each query's result equals
  * solving it alone (its own least fixpoint).
  */
@@ -215,7 +219,8 @@ enum cfpq_query_state { CFPQ_QUERY_QUEUED = 0, CFPQ_QUERY_RUNNING = 1, CFPQ_QUER
 
 typedef struct {
     uint64_t hbm_budget_bytes;  /* device bytes resident queries may hold; 0 = 90 % of free memory at creation */
-    int32_t rounds_per_step;    /* loop executions per step for every resident query; 0 = 4 */
+    int32_t rounds_per_step;    /* most loop executions per step of a query (queries with n above
+                                   4096 get proportionally fewer, at least one); 0 = 8 */
     int32_t max_resident;       /* upper bound on resident queries; 0 = 4096 */
 } cfpq_server_options;
 

@@ -104,6 +104,7 @@ SIGNATURES = {
                                    _P(_VP)]),
     "cfpq_solve": (ctypes.c_int, [_VP, _VP]),
     "cfpq_get": (ctypes.c_int, [_VP, ctypes.c_int32, _P(Triple), ctypes.c_size_t, _P(ctypes.c_size_t)]),
+    "cfpq_get_all": (ctypes.c_int, [_VP, _P(Triple), ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_get_device": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_count": (ctypes.c_int, [_VP, ctypes.c_int32, _P(ctypes.c_size_t)]),
     "cfpq_stats_get": (ctypes.c_int, [_VP, _P(Stats)]),
@@ -249,6 +250,17 @@ class Query:
         buf = buf[:k]
         return np.stack([buf["A"].astype(np.int64), buf["m"].astype(np.int64), buf["n"].astype(np.int64)], axis=1)
 
+    def triples_all(self) -> np.ndarray:
+        """Every relation as an (k, 3) int64 array of (A, m, n), sorted (``cfpq_get_all``)."""
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_get_all(self._h, None, 0, ctypes.byref(c)), "cfpq_get_all")
+        k = int(c.value)
+        buf = np.zeros(max(k, 1), dtype=[("A", "<i4"), ("m", "<u4"), ("n", "<u4")])
+        _check(_lib().cfpq_get_all(self._h, buf.ctypes.data_as(ctypes.POINTER(Triple)), k, ctypes.byref(c)),
+               "cfpq_get_all")
+        buf = buf[:k]
+        return np.stack([buf["A"].astype(np.int64), buf["m"].astype(np.int64), buf["n"].astype(np.int64)], axis=1)
+
     def get(self, A) -> np.ndarray:
         """R_A as a sorted (k, 2) uint32 array of (m, n)."""
         return self.triples(A)[:, 1:].astype(np.uint32)
@@ -292,7 +304,7 @@ class Server:
     """Continuous-batching server (``cfpq_server_*``): submit queries at any time, call
     ``step()`` to admit, advance and retire; results of finished queries stay on the host."""
 
-    def __init__(self, hbm_budget_bytes: int = 0, rounds_per_step: int = 4, max_resident: int = 0):
+    def __init__(self, hbm_budget_bytes: int = 0, rounds_per_step: int = 8, max_resident: int = 0):
         o = ServerOptions()
         _lib().cfpq_server_options_default(ctypes.byref(o))
         o.hbm_budget_bytes, o.rounds_per_step, o.max_resident = int(hbm_budget_bytes), int(rounds_per_step), \

@@ -127,6 +127,123 @@ __global__ void k_emit(const QDesc *qd, int a, const uint64_t *offsets, const ui
     }
 }
 
+// --- extraction of every relation at once: counts over (non-terminal, row) cells, a
+// device-wide three-pass scan, then emission sorted by (A, m, n) ---
+
+__global__ void k_count_all(const QDesc *qd, uint32_t *counts) {
+    const QDesc &q = *qd;
+    const uint64_t cell = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= (uint64_t)q.n_nt * q.n_pad) return;
+    const uint32_t a = (uint32_t)(cell / q.n_pad), i = (uint32_t)(cell % q.n_pad);
+    uint32_t c = 0;
+    if (i < q.n && test_bit(q.Trow + (uint64_t)a * q.W, i)) {
+        const uint32_t *row = q.T + (uint64_t)a * q.plane + (uint64_t)i * q.W;
+        for (uint32_t w = lane; w < q.W; w += 32) c += __popc(row[w]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) counts[cell] = c;
+}
+
+// pass 1: per-block sums of kScanSeg cells
+__global__ void __launch_bounds__(1024) k_scan_blocks(const uint32_t *counts, uint64_t n, unsigned long long *bsum) {
+    __shared__ unsigned long long red[32];
+    const uint64_t lo = (uint64_t)blockIdx.x * kScanSeg;
+    unsigned long long s = 0;
+    for (uint64_t i = lo + threadIdx.x; i < min(n, lo + kScanSeg); i += blockDim.x) s += counts[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = red[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = s;
+    }
+}
+
+// pass 2 (one block): exclusive scan of the block sums; bsum[nb] = total
+__global__ void __launch_bounds__(1024) k_scan_bsums(unsigned long long *bsum, int nb, unsigned long long *total) {
+    __shared__ unsigned long long v[1024];
+    const int t = threadIdx.x;
+    const unsigned long long mine = t < nb ? bsum[t] : 0ull;
+    v[t] = mine;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned long long x = t >= off ? v[t - off] : 0ull;
+        __syncthreads();
+        v[t] += x;
+        __syncthreads();
+    }
+    if (t < nb) bsum[t] = v[t] - mine;
+    if (t == 1023) {
+        bsum[nb] = v[1023];
+        *total = v[1023];
+    }
+}
+
+// pass 3: offsets inside each block's segment (each thread a contiguous run of 8 cells)
+__global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t *counts, uint64_t n, const unsigned long long *bsum,
+                                                     uint64_t *offsets) {
+    __shared__ unsigned long long v[1024];
+    const int t = threadIdx.x;
+    const uint64_t lo = (uint64_t)blockIdx.x * kScanSeg + (uint64_t)t * (kScanSeg / 1024);
+    unsigned long long s = 0;
+    for (uint64_t i = lo; i < min(n, lo + kScanSeg / 1024); i++) s += counts[i];
+    v[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned long long x = t >= off ? v[t - off] : 0ull;
+        __syncthreads();
+        v[t] += x;
+        __syncthreads();
+    }
+    unsigned long long run = bsum[blockIdx.x] + v[t] - s;
+    for (uint64_t i = lo; i < min(n, lo + kScanSeg / 1024); i++) {
+        offsets[i] = run;
+        run += counts[i];
+    }
+}
+
+// first triple of each non-terminal; nt_off[n_nt] = total
+__global__ void k_nt_offsets(const QDesc *qd, const uint64_t *offsets, const unsigned long long *total,
+                             unsigned long long *nt_off) {
+    const QDesc &q = *qd;
+    const int a = threadIdx.x;
+    if (a < q.n_nt) nt_off[a] = offsets[(uint64_t)a * q.n_pad];
+    if (a == q.n_nt) nt_off[a] = *total;
+}
+
+__global__ void k_emit_all(const QDesc *qd, const uint64_t *offsets, const uint32_t *counts, cfpq_triple *out) {
+    const QDesc &q = *qd;
+    const uint64_t cell = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= (uint64_t)q.n_nt * q.n_pad || counts[cell] == 0) return;
+    const int a = (int)(cell / q.n_pad);
+    const uint32_t i = (uint32_t)(cell % q.n_pad);
+    const uint32_t *row = q.T + (uint64_t)a * q.plane + (uint64_t)i * q.W;
+    uint64_t off = offsets[cell];
+    for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
+        uint32_t x = (w0 + lane < q.W) ? row[w0 + lane] : 0u;
+        const uint32_t c = __popc(x);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        uint64_t pos = off + incl - c;
+        while (x) {
+            const uint32_t j = (w0 + lane) * 32u + (uint32_t)(__ffs(x) - 1);
+            x &= x - 1;
+            out[pos++] = cfpq_triple{a, i, j};
+        }
+        off += __shfl_sync(0xffffffffu, incl, 31);
+    }
+}
+
 }  // namespace cfpq
 
 using namespace cfpq;
@@ -281,9 +398,7 @@ void free_ctx_device(cfpq_ctx *c) {
     tensor_release(c);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
-    void *ptrs[] = {c->d_T, c->d_TT, c->d_X0, c->d_X1, c->d_R0, c->d_R1, c->d_Trow, c->d_rules, c->d_gstart,
-                    c->d_unary, c->d_eps, c->d_edges, c->d_state, c->d_q, c->d_counts, c->d_offsets,
-                    c->d_total, c->d_triples, c->d_tc_work};
+    void *ptrs[] = {c->d_arena, c->d_triples, c->d_tc_work};
     for (void *p : ptrs)
         if (p) {
             if (c->pooled) cudaFreeAsync(p, c->stream);
@@ -412,35 +527,37 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         c->prof_ev.assign(2 * std::max(1, c->n_groups), nullptr);
         for (auto &e : c->prof_ev) CK(cudaEventCreate(&e));
     }
+    // one arena for every buffer of the query (one allocation, one free)
     const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
     const size_t rowsz = (size_t)c->n_nt * c->W * sizeof(uint32_t);
-    auto alloc = [&](void **p, size_t bytes) -> int {
-        const cudaError_t e = c->pooled ? cudaMallocAsync(p, std::max<size_t>(bytes, 16), c->stream)
-                                        : cudaMalloc(p, std::max<size_t>(bytes, 16));
-        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); *p = nullptr; return CFPQ_ERR_NOMEM; }
-        if (e != cudaSuccess) { *p = nullptr; return CFPQ_ERR_CUDA; }
-        return CFPQ_OK;
-    };
-    int rc;
-    if ((rc = alloc((void **)&c->d_T, planes))) return rc;
-    if ((rc = alloc((void **)&c->d_X0, planes))) return rc;
-    if ((rc = alloc((void **)&c->d_X1, planes))) return rc;
-    if ((rc = alloc((void **)&c->d_R0, rowsz))) return rc;
-    if ((rc = alloc((void **)&c->d_R1, rowsz))) return rc;
-    if ((rc = alloc((void **)&c->d_Trow, rowsz))) return rc;
-    if (c->path != CFPQ_PATH_GATHER && tensor_path_available()) {
-        if ((rc = alloc((void **)&c->d_TT, planes))) return rc;
+    const size_t cells = (size_t)c->n_nt * c->n_pad;  // (non-terminal, row) extraction cells
+    const bool want_tt = c->path != CFPQ_PATH_GATHER && tensor_path_available();
+    struct Part { void **dst; size_t bytes; };
+    const Part parts[] = {
+        {(void **)&c->d_T, planes}, {(void **)&c->d_X0, planes}, {(void **)&c->d_X1, planes},
+        {(void **)&c->d_TT, want_tt ? planes : 0}, {(void **)&c->d_R0, rowsz}, {(void **)&c->d_R1, rowsz},
+        {(void **)&c->d_Trow, rowsz}, {(void **)&c->d_rules, rules.size() * sizeof(Rule)},
+        {(void **)&c->d_gstart, gstart.size() * sizeof(int32_t)}, {(void **)&c->d_unary, unary.size() * sizeof(int2)},
+        {(void **)&c->d_eps, eps.size() * sizeof(int32_t)}, {(void **)&c->d_edges, n_edges * sizeof(cfpq_edge)},
+        {(void **)&c->d_state, sizeof(DevState)}, {(void **)&c->d_q, sizeof(QDesc)},
+        {(void **)&c->d_counts, cells * sizeof(uint32_t)}, {(void **)&c->d_offsets, cells * sizeof(uint64_t)},
+        {(void **)&c->d_block_sums, (kScanMaxBlocks + 1) * sizeof(unsigned long long)},
+        {(void **)&c->d_nt_off, (size_t)(c->n_nt + 1) * sizeof(unsigned long long)},
+        {(void **)&c->d_total, sizeof(unsigned long long)}};
+    size_t arena = 0;
+    for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
+    {
+        const cudaError_t e = c->pooled ? cudaMallocAsync(&c->d_arena, arena, c->stream) : cudaMalloc(&c->d_arena, arena);
+        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); c->d_arena = nullptr; return CFPQ_ERR_NOMEM; }
+        if (e != cudaSuccess) { c->d_arena = nullptr; return CFPQ_ERR_CUDA; }
     }
-    if ((rc = alloc((void **)&c->d_rules, rules.size() * sizeof(Rule)))) return rc;
-    if ((rc = alloc((void **)&c->d_gstart, gstart.size() * sizeof(int32_t)))) return rc;
-    if ((rc = alloc((void **)&c->d_unary, unary.size() * sizeof(int2)))) return rc;
-    if ((rc = alloc((void **)&c->d_eps, eps.size() * sizeof(int32_t)))) return rc;
-    if ((rc = alloc((void **)&c->d_edges, n_edges * sizeof(cfpq_edge)))) return rc;
-    if ((rc = alloc((void **)&c->d_state, sizeof(DevState)))) return rc;
-    if ((rc = alloc((void **)&c->d_q, sizeof(QDesc)))) return rc;
-    if ((rc = alloc((void **)&c->d_counts, c->n_pad * sizeof(uint32_t)))) return rc;
-    if ((rc = alloc((void **)&c->d_offsets, c->n_pad * sizeof(uint64_t)))) return rc;
-    if ((rc = alloc((void **)&c->d_total, sizeof(unsigned long long)))) return rc;
+    {
+        char *p = static_cast<char *>(c->d_arena);
+        for (const Part &pt : parts) {
+            *pt.dst = pt.bytes ? p : nullptr;
+            p += (pt.bytes + 255) / 256 * 256;
+        }
+    }
     // copies are stream-ordered after the (possibly stream-ordered) allocations; the host
     // sources are pageable, so each call returns once its source has been staged
     cudaStream_t cs = c->stream;
@@ -480,7 +597,6 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.st = c->d_state;
     c->hq = q;
     CK(cudaMemcpyAsync(c->d_q, &q, sizeof(q), cudaMemcpyHostToDevice, cs));
-    CK(cudaStreamSynchronize(cs));  // host vectors above go out of scope
     return CFPQ_OK;
 }
 
@@ -655,6 +771,30 @@ extern "C" int cfpq_get_device(cfpq_ctx *c, int32_t A, cfpq_triple *buf, size_t 
     return emit(c, A, buf, s);
 }
 
+namespace cfpq {
+
+// Grows the context's device triples buffer to hold `total` triples.
+int ensure_triples(cfpq_ctx *c, size_t total, cudaStream_t s) {
+    if (c->triples_cap >= total) return CFPQ_OK;
+    if (c->d_triples) {
+        if (c->pooled) cudaFreeAsync(c->d_triples, s);
+        else cudaFree(c->d_triples);
+    }
+    c->d_triples = nullptr;
+    c->triples_cap = 0;
+    const cudaError_t e = c->pooled ? cudaMallocAsync(&c->d_triples, total * sizeof(cfpq_triple), s)
+                                    : cudaMalloc(&c->d_triples, total * sizeof(cfpq_triple));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->d_triples = nullptr;
+        return CFPQ_ERR_NOMEM;
+    }
+    c->triples_cap = total;
+    return CFPQ_OK;
+}
+
+}  // namespace cfpq
+
 extern "C" int cfpq_get(cfpq_ctx *c, int32_t A, cfpq_triple *buf, size_t cap, size_t *count) {
     if (!c || !count || A < 0 || A >= c->n_nt) return CFPQ_ERR_INVALID;
     if (!c->solved) return CFPQ_ERR_NOT_SOLVED;
@@ -666,19 +806,74 @@ extern "C" int cfpq_get(cfpq_ctx *c, int32_t A, cfpq_triple *buf, size_t cap, si
     if (!buf) return CFPQ_OK;
     if (cap < total) return CFPQ_ERR_BUFFER;
     if (total == 0) return CFPQ_OK;
-    if (c->triples_cap < total) {
-        if (c->d_triples) {
-            if (c->pooled) cudaFreeAsync(c->d_triples, s);
-            else cudaFree(c->d_triples);
-        }
-        c->d_triples = nullptr;
-        c->triples_cap = 0;
-        const cudaError_t e = c->pooled ? cudaMallocAsync(&c->d_triples, total * sizeof(cfpq_triple), s)
-                                        : cudaMalloc(&c->d_triples, total * sizeof(cfpq_triple));
-        if (e != cudaSuccess) { cudaGetLastError(); c->d_triples = nullptr; return CFPQ_ERR_NOMEM; }
-        c->triples_cap = total;
-    }
+    if ((rc = ensure_triples(c, total, s)) != CFPQ_OK) return rc;
     if ((rc = emit(c, A, c->d_triples, s)) != CFPQ_OK) return rc;
+    CK(cudaMemcpyAsync(buf, c->d_triples, total * sizeof(cfpq_triple), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return CFPQ_OK;
+}
+
+namespace cfpq {
+
+// Counts every relation and returns the first triple of each non-terminal (n_nt + 1
+// entries, the last = total). One synchronisation.
+int count_all(cfpq_ctx *c, cudaStream_t s, std::vector<unsigned long long> &nt_off) {
+    const uint64_t cells = (uint64_t)c->n_nt * c->n_pad;
+    const int nb = (int)((cells + kScanSeg - 1) / kScanSeg);
+    k_count_all<<<row_warp_blocks(cells), 256, 0, s>>>(c->d_q, c->d_counts);
+    k_scan_blocks<<<nb, 1024, 0, s>>>(c->d_counts, cells, c->d_block_sums);
+    k_scan_bsums<<<1, 1024, 0, s>>>(c->d_block_sums, nb, c->d_total);
+    k_scan_apply<<<nb, 1024, 0, s>>>(c->d_counts, cells, c->d_block_sums, c->d_offsets);
+    k_nt_offsets<<<1, 96, 0, s>>>(c->d_q, c->d_offsets, c->d_total, c->d_nt_off);
+    CK(cudaGetLastError());
+    nt_off.assign(c->n_nt + 1, 0);
+    CK(cudaMemcpyAsync(nt_off.data(), c->d_nt_off, (c->n_nt + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return CFPQ_OK;
+}
+
+// Emits every relation (after count_all) into device memory `out`.
+int emit_all(cfpq_ctx *c, cfpq_triple *out, cudaStream_t s) {
+    const uint64_t cells = (uint64_t)c->n_nt * c->n_pad;
+    k_emit_all<<<row_warp_blocks(cells), 256, 0, s>>>(c->d_q, c->d_offsets, c->d_counts, out);
+    CK(cudaGetLastError());
+    return CFPQ_OK;
+}
+
+// Every relation copied to host memory, one vector per non-terminal. Two synchronisations.
+int extract_all_host(cfpq_ctx *c, std::vector<std::vector<cfpq_triple>> &out) {
+    cudaStream_t s = c->last_stream;
+    std::vector<unsigned long long> nt_off;
+    int rc = count_all(c, s, nt_off);
+    if (rc != CFPQ_OK) return rc;
+    const size_t total = (size_t)nt_off[c->n_nt];
+    out.assign(c->n_nt, {});
+    if (total == 0) return CFPQ_OK;
+    if ((rc = ensure_triples(c, total, s)) != CFPQ_OK) return rc;
+    if ((rc = emit_all(c, c->d_triples, s)) != CFPQ_OK) return rc;
+    std::vector<cfpq_triple> all(total);
+    CK(cudaMemcpyAsync(all.data(), c->d_triples, total * sizeof(cfpq_triple), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int a = 0; a < c->n_nt; a++) out[a].assign(all.begin() + nt_off[a], all.begin() + nt_off[a + 1]);
+    return CFPQ_OK;
+}
+
+}  // namespace cfpq
+
+extern "C" int cfpq_get_all(cfpq_ctx *c, cfpq_triple *buf, size_t cap, size_t *count) {
+    if (!c || !count) return CFPQ_ERR_INVALID;
+    if (!c->solved) return CFPQ_ERR_NOT_SOLVED;
+    cudaStream_t s = c->last_stream;
+    std::vector<unsigned long long> nt_off;
+    int rc = count_all(c, s, nt_off);
+    if (rc != CFPQ_OK) return rc;
+    const size_t total = (size_t)nt_off[c->n_nt];
+    *count = total;
+    if (!buf) return CFPQ_OK;
+    if (cap < total) return CFPQ_ERR_BUFFER;
+    if (total == 0) return CFPQ_OK;
+    if ((rc = ensure_triples(c, total, s)) != CFPQ_OK) return rc;
+    if ((rc = emit_all(c, c->d_triples, s)) != CFPQ_OK) return rc;
     CK(cudaMemcpyAsync(buf, c->d_triples, total * sizeof(cfpq_triple), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return CFPQ_OK;

@@ -67,8 +67,9 @@ __device__ __forceinline__ int find_slot(const unsigned long long *off, int n, u
     return lo;
 }
 
-// Rebuilds the per-round tables over the active queries (one block of <= 1024 threads).
-__device__ void build_tables(BatchCtl *ctl, const BatchQuery *bq) {
+// Rebuilds the per-round tables over the queries that take part in round `round`: not
+// converged and still within their own round budget (one block of <= 1024 threads).
+__device__ void build_tables(BatchCtl *ctl, const BatchQuery *bq, int round) {
     __shared__ unsigned long long sp[1024], sr[1024];
     __shared__ int sa[1024];
     const int k = ctl->k;
@@ -77,7 +78,7 @@ __device__ void build_tables(BatchCtl *ctl, const BatchQuery *bq) {
     unsigned long long p = 0, r = 0;
     int a = 0;
     for (int j = lo; j < hi; j++)
-        if (__ldcg(ctl->active + j)) {
+        if (__ldcg(ctl->active + j) && round < bq[j].max_rounds) {
             a++;
             p += bq[j].prod_items;
             r += bq[j].row_items;
@@ -99,7 +100,7 @@ __device__ void build_tables(BatchCtl *ctl, const BatchQuery *bq) {
     unsigned long long P = sp[threadIdx.x] - p, R = sr[threadIdx.x] - r;
     int A = sa[threadIdx.x] - a;
     for (int j = lo; j < hi; j++)
-        if (__ldcg(ctl->active + j)) {
+        if (__ldcg(ctl->active + j) && round < bq[j].max_rounds) {
             ctl->act[A] = j;
             ctl->prod_off[A] = P;
             ctl->row_off[A] = R;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
     for (int j = 0; j < k; j++)
         if (bq[j].init) seed_query(bq[j].q, gtid, gthreads);
     if (!grid_barrier(ctl)) return;
-    if (blockIdx.x == 0) build_tables(ctl, bq);
+    if (blockIdx.x == 0) build_tables(ctl, bq, 0);
     if (!grid_barrier(ctl)) return;
 
     for (int round = 0; round < ctl->max_rounds; round++) {
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
         // every tail must be done (it reads act[] and writes active[]) before the tables change
         if (!grid_barrier(ctl)) return;
         if (blockIdx.x == 0) {
-            build_tables(ctl, bq);
+            build_tables(ctl, bq, round + 1);
             if (threadIdx.x == 0 && ctl->limit_ns && globaltimer_ns() - ctl->start_ns > ctl->limit_ns)
                 atomicExch(&ctl->error, 2u);
             __syncthreads();
@@ -255,6 +256,7 @@ void fill_batch_query(const cfpq_ctx *c, BatchQuery *b, int init) {
     b->prod_items = (unsigned long long)c->n_groups * c->n * nch;
     b->row_items = (unsigned long long)c->n_nt * c->n;
     b->init = init;
+    b->max_rounds = 1 << 30;
 }
 
 int batch_buffers_alloc(BatchBuffers *b, int k) {

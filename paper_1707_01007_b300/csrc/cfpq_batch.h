@@ -11,7 +11,7 @@ struct BatchQuery {
     int cpl;                          // words per lane of the gather accumulator
     uint32_t nch;                     // column chunks per row
     int init;                         // 1: clear and seed this query at the start of the launch
-    int pad;
+    int max_rounds;                   // loop executions this query may run in this launch
 };
 
 struct BatchCtl {

@@ -32,8 +32,11 @@ struct cfpq_ctx {
     cfpq::DevState *d_state = nullptr;
     cfpq::QDesc *d_q = nullptr;
     cfpq::QDesc hq{};
-    uint32_t *d_counts = nullptr;
-    uint64_t *d_offsets = nullptr;
+    void *d_arena = nullptr;                 // every buffer below lives in this one allocation
+    uint32_t *d_counts = nullptr;            // [n_nt * n_pad] pairs per (non-terminal, row)
+    uint64_t *d_offsets = nullptr;           // [n_nt * n_pad] exclusive prefix of d_counts
+    unsigned long long *d_block_sums = nullptr;
+    unsigned long long *d_nt_off = nullptr;  // [n_nt + 1] first triple of each non-terminal
     unsigned long long *d_total = nullptr;
     cfpq_triple *d_triples = nullptr;
     size_t triples_cap = 0;
@@ -55,6 +58,9 @@ struct cfpq_ctx {
 
 namespace cfpq {
 
+constexpr int kScanSeg = 8192;                                  // cells per block of the wide scan
+constexpr int kScanMaxBlocks = (CFPQ_MAX_NONTERM * CFPQ_MAX_NODES) / kScanSeg;
+
 int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
              const cfpq_options &o);
 int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
@@ -64,6 +70,8 @@ int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edge
 int ctx_create_pooled(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
                       const cfpq_options &o, cudaStream_t pool_stream, cfpq_ctx **out);
 void ctx_destroy(cfpq_ctx *c);
+int ensure_triples(cfpq_ctx *c, size_t total, cudaStream_t s);
+int extract_all_host(cfpq_ctx *c, std::vector<std::vector<cfpq_triple>> &out);
 // Bytes of device memory a context for this query holds (path GATHER unless tensor).
 size_t query_footprint(uint32_t n, int n_nt, size_t n_edges, int n_rules, bool tensor);
 void free_ctx_device(cfpq_ctx *c);

@@ -55,7 +55,7 @@ struct Served {
 
 struct cfpq_server {
     size_t budget = 0, used = 0, peak_used = 0;
-    int rounds = 4, max_resident = 4096;
+    int rounds = 8, max_resident = 4096;
     cudaStream_t stream = nullptr;
     cudaMemPool_t pool = nullptr;
     std::deque<Pending> waiting;
@@ -82,7 +82,7 @@ extern "C" int cfpq_server_options_default(cfpq_server_options *o) {
     if (!o) return CFPQ_ERR_INVALID;
     memset(o, 0, sizeof(*o));
     o->hbm_budget_bytes = 0;
-    o->rounds_per_step = 4;
+    o->rounds_per_step = 8;
     o->max_resident = 4096;
     return CFPQ_OK;
 }
@@ -95,7 +95,7 @@ extern "C" int cfpq_server_create(const cfpq_server_options *opt, cfpq_server **
     if (o.rounds_per_step < 0 || o.max_resident < 0) return CFPQ_ERR_INVALID;
     cfpq_server *s = new (std::nothrow) cfpq_server();
     if (!s) return CFPQ_ERR_NOMEM;
-    s->rounds = o.rounds_per_step ? o.rounds_per_step : 4;
+    s->rounds = o.rounds_per_step ? o.rounds_per_step : 8;
     s->max_resident = o.max_resident ? o.max_resident : 4096;
     int dev = 0;
     size_t free_b = 0, total_b = 0;
@@ -145,17 +145,11 @@ static int retire(cfpq_server *s, Served *q) {
     cfpq_ctx *c = q->ctx;
     int rc = read_status(c, s->stream);
     q->status = rc;
+    c->last_stream = s->stream;
     q->iterations = c->stats.iterations;
     c->solved = true;
     if (rc == CFPQ_ERR_CUDA) return rc;
-    q->results.assign(c->n_nt, {});
-    for (int a = 0; a < c->n_nt; a++) {
-        size_t cnt = 0;
-        int r = cfpq_get(c, a, nullptr, 0, &cnt);
-        if (r != CFPQ_OK) return r;
-        q->results[a].resize(cnt);
-        if (cnt && (r = cfpq_get(c, a, q->results[a].data(), cnt, &cnt)) != CFPQ_OK) return r;
-    }
+    if ((rc = extract_all_host(c, q->results)) != CFPQ_OK) return rc;
     ctx_destroy(c);
     q->ctx = nullptr;
     s->used -= q->footprint;
@@ -230,6 +224,10 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
     bool any_jacobi = false;
     for (int j = 0; j < k; j++) {
         fill_batch_query(s->resident[j]->ctx, &hb[j], s->resident[j]->init);
+        // round budget: cheap queries run up to `rounds` executions per launch, expensive ones
+        // fewer, so small queries are not held to the pace of a large one
+        const double scale = 4096.0 / (double)s->resident[j]->ctx->n_pad;
+        hb[j].max_rounds = std::max(1, std::min(s->rounds, (int)(s->rounds * scale * scale)));
         any_jacobi |= s->resident[j]->ctx->schedule == CFPQ_SCHED_JACOBI;
     }
     rc = batch_buffers_upload(&s->bufs, hb.data(), active.data(), k, s->rounds, any_jacobi, s->stream);

@@ -62,7 +62,8 @@ def run_server(server: Server, queries, arrivals, keep_results: bool = False):
 
 
 def run_serial(queries, arrivals):
-    """One query at a time in arrival order (create, solve, copy every R_A back, destroy)."""
+    """One query at a time in arrival order (create, solve, copy every R_A back with one
+    call, destroy)."""
     n_q = len(queries)
     order = np.argsort(arrivals, kind="stable")
     arrivals = np.asarray(arrivals, dtype=np.float64)
@@ -75,8 +76,7 @@ def run_serial(queries, arrivals):
         g, n, e = queries[j]
         q = Query(g, n, e, path=PATH_GATHER)
         q.solve()
-        for nm in g.names:
-            q.triples(nm)
+        q.triples_all()
         q.close()
         done_at[j] = time.perf_counter() - t0
     return _summary(arrivals, done_at, time.perf_counter() - t0)

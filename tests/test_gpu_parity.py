@@ -213,3 +213,12 @@ def test_algorithm1_loop_count_matches_oracle(text):
     for path in (eng.PATH_GATHER, eng.PATH_TENSOR):
         g, q = solve_engine(graph, text, schedule=eng.SCHED_JACOBI, path=path)
         assert q.stats()["iterations"] == k
+
+
+@pytest.mark.parametrize("n,c", [(700, 200), (5000, 1500)])
+def test_get_all_equals_per_relation(n, c):
+    graph = synth.hierarchy(n, c, seed=3)
+    g, q = solve_engine(graph, synth.GRAMMAR_Q1)
+    allt = q.triples_all()
+    per = np.concatenate([q.triples(nm) for nm in g.names], axis=0)
+    assert np.array_equal(allt, per)
