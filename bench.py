@@ -199,7 +199,7 @@ def tc_traffic_per_launch():
         src = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
         if vals.get("source_sha256") != src:
             return None
-        return float(vals["dram_bytes_per_launch_S_group"])
+        return float(vals["dram_bytes_per_launch_avg"])
     except (OSError, KeyError, ValueError):
         return None
 

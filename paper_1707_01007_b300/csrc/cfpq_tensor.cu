@@ -44,6 +44,7 @@ constexpr int PST = 8, UST = 5;       // packed / unpacked ring depths
 constexpr int A_PACK = BM * KW * 4, B_PACK = BN * KW * 4;  // bytes of one packed stage
 constexpr int B_TILE = BN * BK;       // bytes of one unpacked B stage (FP8)
 constexpr int UNPACK_WARPS = 8;      // two per SM sub-partition
+constexpr uint32_t RASTER_N = 8;      // N tiles per rasterisation band
 constexpr int UNPACK_THREADS = 32 * UNPACK_WARPS;
 constexpr int THREADS = 64 + UNPACK_THREADS;
 constexpr uint32_t ACC_COLS = 256;                 // F32 accumulator, 128 lanes x 256 columns
@@ -214,7 +215,19 @@ __global__ void __launch_bounds__(THREADS, 1)
     DevState *st = q.st;
     if (st->use_tensor[g] == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    // grouped rasterisation: consecutive CTAs sweep the M tiles of a band of RASTER_N N tiles,
+    // so one wave of CTAs touches about RASTER_N right-operand tile columns (L2-resident)
+    uint32_t n0, m0;
+    {
+        const uint32_t n_tiles = q.n_pad / BN, m_tiles = q.n_pad / BM;
+        const uint32_t t = blockIdx.x;
+        const uint32_t band = t / (RASTER_N * m_tiles);
+        const uint32_t first_n = band * RASTER_N;
+        const uint32_t width = min((uint32_t)RASTER_N, n_tiles - first_n);
+        const uint32_t local = t - band * RASTER_N * m_tiles;
+        n0 = (first_n + local % width) * BN;
+        m0 = (local / width) * BM;
+    }
     const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
     const int A = q.rules[r0].lhs;
     const uint32_t kpr = q.n_pad / BK;  // stages per production
@@ -352,7 +365,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     if (threadIdx.x == 0) {
         if (S.err) atomicExch(&st->error, 3u);
-        if (blockIdx.x == 0 && blockIdx.y == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
+        if (blockIdx.x == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
     }
     if (warp == 1) {
         tc_fence_after();
@@ -507,7 +520,7 @@ int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
     const int rc = tensor_setup(c);
     if (rc != CFPQ_OK) return rc;
     TensorWork *w = static_cast<TensorWork *>(c->h_tc_work);
-    const dim3 grid(c->n_pad / tc::BN, c->n_pad / tc::BM);
+    const dim3 grid((c->n_pad / tc::BN) * (c->n_pad / tc::BM));
     tc::k_tc_bool_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(w->tmT, w->tmTT, c->d_q, g);
     c->iter_launches++;
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
