@@ -79,7 +79,10 @@ enum cfpq_schedule {
 enum cfpq_path {
     CFPQ_PATH_AUTO = 0,       /* per production group and iteration, the cheaper of the two below */
     CFPQ_PATH_TENSOR = 1,     /* dense tcgen05 product of every production, every iteration */
-    CFPQ_PATH_GATHER = 2      /* CUDA-core bit-gather over changed bits only (semi-naive) */
+    CFPQ_PATH_GATHER = 2,     /* CUDA-core bit-gather over changed bits only (semi-naive) */
+    CFPQ_PATH_WORKLIST = 3    /* one warp joins each new pair with its partners (semi-naive at the
+                                 grain of single pairs): for long chains of tiny deltas; the loop
+                                 count is not defined (reported as 1) */
 };
 
 typedef struct {
@@ -110,6 +113,7 @@ typedef struct {
     int64_t tensor_launches;  /* profile mode: tensor-core product launches timed */
     double product_bytes;     /* profile mode: bytes the gather products read or wrote (rows
                                  scanned, rows gathered, result rows merged) */
+    int64_t worklist_items;   /* worklist path: pairs joined with their partners */
 } cfpq_stats;
 
 typedef struct cfpq_ctx cfpq_ctx;

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcfpq.so")
 OK, ERR_INVALID, ERR_NOMEM, ERR_NOT_SOLVED, ERR_ITER_LIMIT, ERR_TIMEOUT, ERR_CUDA, ERR_BUFFER, \
     ERR_UNSUPPORTED = range(9)
 SCHED_INPLACE, SCHED_JACOBI = 0, 1
-PATH_AUTO, PATH_TENSOR, PATH_GATHER = 0, 1, 2
+PATH_AUTO, PATH_TENSOR, PATH_GATHER, PATH_WORKLIST = 0, 1, 2, 3
 
 
 class CfpqError(RuntimeError):
@@ -66,7 +66,8 @@ class Stats(ctypes.Structure):
                 ("n_pad", ctypes.c_uint32), ("status", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("product_launches", ctypes.c_int64),
                 ("product_ms", ctypes.c_double), ("tensor_ms", ctypes.c_double),
-                ("tensor_launches", ctypes.c_int64), ("product_bytes", ctypes.c_double)]
+                ("tensor_launches", ctypes.c_int64), ("product_bytes", ctypes.c_double),
+                ("worklist_items", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -396,6 +396,7 @@ static int build_graph(cfpq_ctx *c) {
 
 void free_ctx_device(cfpq_ctx *c) {
     tensor_release(c);
+    worklist_release(c);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
     void *ptrs[] = {c->d_arena, c->d_triples, c->d_tc_work};
@@ -509,6 +510,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     eps.erase(std::unique(eps.begin(), eps.end()), eps.end());
     c->n_unary = (int)unary.size();
     c->n_eps_rules = (int)eps.size();
+    c->h_unary = unary;
+    c->h_eps = eps;
     c->n_edges = n_edges;
     c->group_tensor.assign(std::max(1, c->n_groups), 0);
     if (c->path == CFPQ_PATH_TENSOR) {
@@ -531,7 +534,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
     const size_t rowsz = (size_t)c->n_nt * c->W * sizeof(uint32_t);
     const size_t cells = (size_t)c->n_nt * c->n_pad;  // (non-terminal, row) extraction cells
-    const bool want_tt = c->path != CFPQ_PATH_GATHER && tensor_path_available();
+    const bool want_tt = (c->path == CFPQ_PATH_WORKLIST) ||
+                         ((c->path == CFPQ_PATH_AUTO || c->path == CFPQ_PATH_TENSOR) && tensor_path_available());
     struct Part { void **dst; size_t bytes; };
     const Part parts[] = {
         {(void **)&c->d_T, planes}, {(void **)&c->d_X0, planes}, {(void **)&c->d_X1, planes},
@@ -597,6 +601,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.st = c->d_state;
     c->hq = q;
     CK(cudaMemcpyAsync(c->d_q, &q, sizeof(q), cudaMemcpyHostToDevice, cs));
+    if (c->path == CFPQ_PATH_WORKLIST) return worklist_setup(c, edges, n_edges);
     return CFPQ_OK;
 }
 
@@ -633,7 +638,7 @@ int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edge
             return CFPQ_ERR_INVALID;
     if (opt) {
         if (opt->schedule != CFPQ_SCHED_INPLACE && opt->schedule != CFPQ_SCHED_JACOBI) return CFPQ_ERR_INVALID;
-        if (opt->path < CFPQ_PATH_AUTO || opt->path > CFPQ_PATH_GATHER) return CFPQ_ERR_INVALID;
+        if (opt->path < CFPQ_PATH_AUTO || opt->path > CFPQ_PATH_WORKLIST) return CFPQ_ERR_INVALID;
     }
     return CFPQ_OK;
 }
@@ -735,7 +740,7 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
     CK(cudaEventRecord(c->ev0, s));
     int rc = enqueue_reset_and_seed(c, s);
     if (rc != CFPQ_OK) return rc;
-    rc = run_loop(c, s);
+    rc = c->path == CFPQ_PATH_WORKLIST ? worklist_run(c, s) : run_loop(c, s);
     if (rc != CFPQ_OK) return rc;
     CK(cudaEventRecord(c->ev1, s));
     rc = read_status(c, s);

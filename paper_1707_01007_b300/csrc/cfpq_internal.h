@@ -42,6 +42,9 @@ struct cfpq_ctx {
     size_t triples_cap = 0;
     void *d_tc_work = nullptr;
     void *h_tc_work = nullptr;               // tensor path: tensor maps (host side)
+    void *h_wl = nullptr;                    // worklist path state
+    std::vector<int2> h_unary;               // (lhs, terminal) productions, host copy
+    std::vector<int32_t> h_eps;
     // execution
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -89,5 +92,10 @@ int enqueue_tensor_transposes(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launches);
 void tensor_release(cfpq_ctx *c);
+
+// worklist path (cfpq_worklist.cu)
+int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges);
+int worklist_run(cfpq_ctx *c, cudaStream_t s);
+void worklist_release(cfpq_ctx *c);
 
 }  // namespace cfpq

@@ -1,0 +1,358 @@
+// Worklist path (CFPQ_PATH_WORKLIST): the closure of Algorithm 1 (Section 4.2) evaluated
+// semi-naively at the finest grain, one new pair at a time, by a single warp on the GPU.
+//
+// Algorithm 1 joins the whole matrix with itself each iteration. When every iteration adds
+// only a pair or two (long derivation chains, e.g. two cycles sharing a node, where the loop
+// runs ~pq times), every loop execution costs kernel launches and full-matrix scans for one
+// new bit. Here each newly set pair (A, i, j) is instead joined once with its partners:
+//   as the left operand of X -> A C:  every (C, j, k) gives (X, i, k)
+//   as the right operand of X -> B A: every (B, k, i) gives (X, k, j)
+// A derived pair is set with an atomic OR in T_X; if it was new it is pushed on the stack
+// (or, when it is the only new pair, handed to the next step in registers). When the stack
+// is empty, T is closed under every production: the same least fixpoint as the matrix loop.
+// Partners of non-terminals that no production derives (their relation is exactly the seed)
+// come from CSR adjacency built on the host; partners of the others from the bit matrices:
+// row j of T_C, and row i of T_B^T (T^T is maintained for them as pairs are set).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "cfpq_internal.h"
+
+namespace cfpq {
+
+struct WLDesc {
+    const int2 *occ;              // per non-terminal a: (production index, side 0 = left / 1 = right)
+    const int32_t *occ_start;     // [n_nt + 1]
+    const int32_t *is_static;     // [n_nt]
+    const uint64_t *out_base;     // [n_nt] start of a's out-CSR offsets in csr_off (static a only)
+    const uint64_t *in_base;      // [n_nt] start of a's in-CSR offsets in csr_off
+    const uint32_t *csr_off;      // offsets into csr_col (n + 1 per CSR)
+    const uint32_t *csr_col;
+    const int32_t *needs_tt;      // [n_nt] keep T^T of a (a dynamic and a left operand somewhere)
+    uint32_t *stack;              // triples (a, i, j)
+    uint64_t cap;                 // stack capacity in triples
+    unsigned long long *items;    // pairs processed
+    unsigned int *overflow;
+};
+
+__device__ __forceinline__ bool wl_set(const QDesc &q, const WLDesc &w, int x, uint32_t a, uint32_t b) {
+    const uint32_t bit = 1u << (b & 31);
+    const uint32_t old = atomicOr(&q.T[(uint64_t)x * q.plane + (uint64_t)a * q.W + (b >> 5)], bit);
+    if (old & bit) return false;
+    if (w.needs_tt[x]) atomicOr(&q.TT[(uint64_t)x * q.plane + (uint64_t)b * q.W + (a >> 5)], 1u << (a & 31));
+    return true;
+}
+
+// One warp. Processes the stack until it is empty, the deadline passes or it overflows.
+__global__ void __launch_bounds__(32) k_worklist(const QDesc *qd, WLDesc w, unsigned long long top0) {
+    const QDesc &q = *qd;
+    const int lane = threadIdx.x;
+    unsigned long long top = top0, processed = 0;
+    uint32_t ca = 0, ci = 0, cj = 0;  // item handed over in registers
+    bool have = false;
+    const unsigned long long deadline = ld_u64(&q.st->deadline_ns);
+    for (;;) {
+        if (!have) {
+            if (top == 0) break;
+            __syncwarp();  // stack entries written by other lanes of this warp
+            top--;
+            ca = w.stack[3 * top];
+            ci = w.stack[3 * top + 1];
+            cj = w.stack[3 * top + 2];
+        }
+        have = false;
+        processed++;
+        if ((processed & 4095u) == 0 && deadline && globaltimer_ns() > deadline) {
+            if (lane == 0) q.st->error = kErrTimeout;
+            break;
+        }
+        uint32_t n_new = 0, ha = 0, hi = 0, hj = 0;
+        for (int o = w.occ_start[ca]; o < w.occ_start[ca + 1]; o++) {
+            const int2 oc = w.occ[o];
+            const Rule r = q.rules[oc.x];
+            const int x = r.lhs;
+            const bool left = oc.y == 0;
+            const int p = left ? r.c : r.b;        // partner non-terminal
+            const uint32_t key = left ? cj : ci;   // row of T_p (left) or of T_p^T (right)
+            if (w.is_static[p]) {
+                const uint64_t base = left ? w.out_base[p] : w.in_base[p];
+                const uint32_t lo = __ldg(w.csr_off + base + key), hi_ = __ldg(w.csr_off + base + key + 1);
+                for (uint32_t e0 = lo; e0 < hi_; e0 += 32) {
+                    const uint32_t e = e0 + lane;
+                    bool nw = false;
+                    uint32_t a = 0, b = 0;
+                    if (e < hi_) {
+                        const uint32_t k = __ldg(w.csr_col + e);
+                        a = left ? ci : k;
+                        b = left ? k : cj;
+                        nw = wl_set(q, w, x, a, b);
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, nw);
+                    if (m) {
+                        const int first = __ffs(m) - 1;
+                        if (n_new == 0 && __popc(m) >= 1) {
+                            ha = (uint32_t)x;
+                            hi = __shfl_sync(0xffffffffu, a, first);
+                            hj = __shfl_sync(0xffffffffu, b, first);
+                        }
+                        // every new pair but the one kept in registers goes on the stack
+                        const unsigned push = (n_new == 0) ? (m & (m - 1)) : m;
+                        if (push) {
+                            const unsigned before = __popc(push & ((1u << lane) - 1u));
+                            if ((push >> lane) & 1u) {
+                                const unsigned long long pos = top + before;
+                                if (pos < w.cap) {
+                                    w.stack[3 * pos] = (uint32_t)x;
+                                    w.stack[3 * pos + 1] = a;
+                                    w.stack[3 * pos + 2] = b;
+                                }
+                            }
+                            top += __popc(push);
+                        }
+                        n_new += __popc(m);
+                    }
+                }
+            } else {
+                const uint32_t *row = left ? q.T + (uint64_t)p * q.plane + (uint64_t)key * q.W
+                                           : q.TT + (uint64_t)p * q.plane + (uint64_t)key * q.W;
+                for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
+                    uint32_t bits = (w0 + lane < q.W) ? __ldcg(row + w0 + lane) : 0u;
+                    while (__any_sync(0xffffffffu, bits != 0)) {
+                        bool nw = false;
+                        uint32_t a = 0, b = 0;
+                        if (bits) {
+                            const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(bits) - 1);
+                            bits &= bits - 1;
+                            a = left ? ci : k;
+                            b = left ? k : cj;
+                            nw = wl_set(q, w, x, a, b);
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, nw);
+                        if (m) {
+                            const int first = __ffs(m) - 1;
+                            if (n_new == 0) {
+                                ha = (uint32_t)x;
+                                hi = __shfl_sync(0xffffffffu, a, first);
+                                hj = __shfl_sync(0xffffffffu, b, first);
+                            }
+                            const unsigned push = (n_new == 0) ? (m & (m - 1)) : m;
+                            if (push) {
+                                const unsigned before = __popc(push & ((1u << lane) - 1u));
+                                if ((push >> lane) & 1u) {
+                                    const unsigned long long pos = top + before;
+                                    if (pos < w.cap) {
+                                        w.stack[3 * pos] = (uint32_t)x;
+                                        w.stack[3 * pos + 1] = a;
+                                        w.stack[3 * pos + 2] = b;
+                                    }
+                                }
+                                top += __popc(push);
+                            }
+                            n_new += __popc(m);
+                        }
+                    }
+                }
+            }
+        }
+        if (top > w.cap) {
+            if (lane == 0) atomicExch(w.overflow, 1u);
+            break;
+        }
+        if (n_new) {
+            ca = ha;
+            ci = hi;
+            cj = hj;
+            have = true;
+            if (lane == 0) atomicAdd(&q.st->new_bits, (unsigned long long)n_new);
+        }
+    }
+    if (lane == 0) {
+        *w.items = processed;
+        q.st->iter = 1;
+    }
+}
+
+// Every seeded pair goes on the stack (and into T^T where kept).
+__global__ void k_worklist_init(const QDesc *qd, WLDesc w, unsigned long long *top) {
+    const QDesc &q = *qd;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= (uint64_t)q.n_nt * q.n) return;
+    const uint32_t a = (uint32_t)(warp / q.n), i = (uint32_t)(warp % q.n);
+    if (!test_bit(q.Trow + (uint64_t)a * q.W, i)) return;
+    const uint32_t *row = q.T + (uint64_t)a * q.plane + (uint64_t)i * q.W;
+    for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
+        uint32_t bits = (w0 + lane < q.W) ? row[w0 + lane] : 0u;
+        while (bits) {
+            const uint32_t j = (w0 + lane) * 32u + (uint32_t)(__ffs(bits) - 1);
+            bits &= bits - 1;
+            if (w.needs_tt[a]) atomicOr(&q.TT[(uint64_t)a * q.plane + (uint64_t)j * q.W + (i >> 5)], 1u << (i & 31));
+            const unsigned long long pos = atomicAdd(top, 1ull);
+            if (pos < w.cap) {
+                w.stack[3 * pos] = a;
+                w.stack[3 * pos + 1] = i;
+                w.stack[3 * pos + 2] = j;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------ host
+
+struct WorklistState {
+    WLDesc d;
+    void *arena = nullptr;
+    unsigned long long *d_top = nullptr;
+};
+
+int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
+    const int n_nt = c->n_nt;
+    const uint32_t n = c->n;
+    std::vector<int32_t> is_static(n_nt, 1), needs_tt(n_nt, 0);
+    for (const Rule &r : c->rules) is_static[r.lhs] = 0;
+    for (const Rule &r : c->rules)
+        if (!is_static[r.b]) needs_tt[r.b] = 1;
+    // occurrences of each non-terminal as an operand
+    std::vector<std::vector<int2>> occ(n_nt);
+    for (size_t k = 0; k < c->rules.size(); k++) {
+        occ[c->rules[k].b].push_back(make_int2((int)k, 0));
+        occ[c->rules[k].c].push_back(make_int2((int)k, 1));
+    }
+    std::vector<int2> occ_flat;
+    std::vector<int32_t> occ_start(n_nt + 1, 0);
+    for (int a = 0; a < n_nt; a++) {
+        occ_start[a] = (int32_t)occ_flat.size();
+        occ_flat.insert(occ_flat.end(), occ[a].begin(), occ[a].end());
+    }
+    occ_start[n_nt] = (int32_t)occ_flat.size();
+    // CSR of static non-terminals (their relation is exactly the seed: edges and eps)
+    std::vector<std::vector<int32_t>> heads(c->n_term);
+    for (const int2 &u : c->h_unary) heads[u.y].push_back(u.x);
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> pairs(n_nt);
+    for (size_t e = 0; e < n_edges; e++)
+        for (int a : heads[edges[e].label])
+            if (is_static[a]) pairs[a].push_back({edges[e].src, edges[e].dst});
+    for (int a : c->h_eps)
+        if (is_static[a])
+            for (uint32_t m = 0; m < n; m++) pairs[a].push_back({m, m});
+    std::vector<uint64_t> out_base(n_nt, 0), in_base(n_nt, 0);
+    std::vector<uint32_t> csr_off, csr_col;
+    auto build = [&](std::vector<std::pair<uint32_t, uint32_t>> &pr, bool by_src) {
+        const uint64_t base = csr_off.size();
+        std::sort(pr.begin(), pr.end(), [&](const auto &x, const auto &y) {
+            return by_src ? (x.first != y.first ? x.first < y.first : x.second < y.second)
+                          : (x.second != y.second ? x.second < y.second : x.first < y.first);
+        });
+        pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
+        std::vector<uint32_t> off(n + 1, 0);
+        for (const auto &e : pr) off[(by_src ? e.first : e.second) + 1]++;
+        for (uint32_t i = 0; i < n; i++) off[i + 1] += off[i];
+        const uint32_t col0 = (uint32_t)csr_col.size();
+        for (uint32_t i = 0; i <= n; i++) csr_off.push_back(col0 + off[i]);
+        for (const auto &e : pr) csr_col.push_back(by_src ? e.second : e.first);
+        return base;
+    };
+    for (int a = 0; a < n_nt; a++)
+        if (is_static[a]) {
+            out_base[a] = build(pairs[a], true);
+            in_base[a] = build(pairs[a], false);
+        }
+    // device arena
+    const uint64_t cap_full = (uint64_t)n_nt * (uint64_t)n * (uint64_t)n;
+    const uint64_t cap = std::max<uint64_t>(1024, std::min<uint64_t>(cap_full, 1ull << 27));
+    struct Part { void **dst; size_t bytes; };
+    WorklistState *ws = new WorklistState();
+    WLDesc &d = ws->d;
+    memset(&d, 0, sizeof(d));
+    const Part parts[] = {{(void **)&d.occ, occ_flat.size() * sizeof(int2) + 8},
+                          {(void **)&d.occ_start, occ_start.size() * 4},
+                          {(void **)&d.is_static, (size_t)n_nt * 4},
+                          {(void **)&d.out_base, (size_t)n_nt * 8},
+                          {(void **)&d.in_base, (size_t)n_nt * 8},
+                          {(void **)&d.csr_off, csr_off.size() * 4 + 8},
+                          {(void **)&d.csr_col, csr_col.size() * 4 + 8},
+                          {(void **)&d.needs_tt, (size_t)n_nt * 4},
+                          {(void **)&d.stack, cap * 12},
+                          {(void **)&d.items, 8},
+                          {(void **)&d.overflow, 8},
+                          {(void **)&ws->d_top, 8}};
+    size_t total = 0;
+    for (const Part &p : parts) total += (p.bytes + 255) / 256 * 256;
+    cudaError_t e = c->pooled ? cudaMallocAsync(&ws->arena, total, c->stream) : cudaMalloc(&ws->arena, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ws;
+        return e == cudaErrorMemoryAllocation ? CFPQ_ERR_NOMEM : CFPQ_ERR_CUDA;
+    }
+    char *ptr = static_cast<char *>(ws->arena);
+    for (const Part &p : parts) {
+        *p.dst = ptr;
+        ptr += (p.bytes + 255) / 256 * 256;
+    }
+    d.cap = cap;
+    cudaStream_t s = c->stream;
+    bool ok = true;
+    auto up = [&](const void *dst, const void *src, size_t bytes) {
+        if (bytes && cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            ok = false;
+    };
+    up(d.occ, occ_flat.data(), occ_flat.size() * sizeof(int2));
+    up(d.occ_start, occ_start.data(), occ_start.size() * 4);
+    up(d.is_static, is_static.data(), (size_t)n_nt * 4);
+    up(d.out_base, out_base.data(), (size_t)n_nt * 8);
+    up(d.in_base, in_base.data(), (size_t)n_nt * 8);
+    up(d.csr_off, csr_off.data(), csr_off.size() * 4);
+    up(d.csr_col, csr_col.data(), csr_col.size() * 4);
+    up(d.needs_tt, needs_tt.data(), (size_t)n_nt * 4);
+    if (!ok) {
+        if (c->pooled) cudaFreeAsync(ws->arena, s);
+        else cudaFree(ws->arena);
+        delete ws;
+        return CFPQ_ERR_CUDA;
+    }
+    c->h_wl = ws;
+    return CFPQ_OK;
+}
+
+void worklist_release(cfpq_ctx *c) {
+    WorklistState *ws = static_cast<WorklistState *>(c->h_wl);
+    if (!ws) return;
+    if (ws->arena) {
+        if (c->pooled) cudaFreeAsync(ws->arena, c->stream);
+        else cudaFree(ws->arena);
+    }
+    delete ws;
+    c->h_wl = nullptr;
+}
+
+// After enqueue_reset_and_seed: stack the seeds, run the warp, read its counters.
+int worklist_run(cfpq_ctx *c, cudaStream_t s) {
+    WorklistState *ws = static_cast<WorklistState *>(c->h_wl);
+    if (!ws) return CFPQ_ERR_UNSUPPORTED;
+    WLDesc &d = ws->d;
+    if (cudaMemsetAsync(ws->d_top, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d.overflow, 0, 8, s) != cudaSuccess ||
+        cudaMemsetAsync(c->d_TT, 0, (size_t)c->n_nt * c->plane * 4, s) != cudaSuccess)
+        return CFPQ_ERR_CUDA;
+    const uint64_t rows = (uint64_t)c->n_nt * c->n;
+    k_worklist_init<<<(uint32_t)((rows * 32 + 255) / 256), 256, 0, s>>>(c->d_q, d, ws->d_top);
+    unsigned long long top = 0;
+    if (cudaMemcpyAsync(&top, ws->d_top, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CFPQ_ERR_CUDA;
+    if (top > d.cap) return CFPQ_ERR_NOMEM;
+    k_worklist<<<1, 32, 0, s>>>(c->d_q, d, top);
+    c->iter_launches = 1;
+    c->fixed_launches += 2;
+    unsigned overflow = 0;
+    unsigned long long items = 0;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&overflow, d.overflow, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&items, d.items, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CFPQ_ERR_CUDA;
+    c->stats.worklist_items = (int64_t)items;
+    return overflow ? CFPQ_ERR_NOMEM : CFPQ_OK;
+}
+
+}  // namespace cfpq

@@ -1,0 +1,67 @@
+"""Worklist path (semi-naive at the grain of single pairs, one warp): the same least
+fixpoint as Algorithm 1, against the oracle and the two-cycle closed form at full size."""
+import numpy as np
+import pytest
+
+import cfpq_synth as synth
+import oracle
+import paper_1707_01007_b300 as eng
+
+pytestmark = pytest.mark.gpu
+
+
+def wl(graph, text, **kw):
+    kw.setdefault("timeout_s", 300.0)
+    g = eng.Grammar(text, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_WORKLIST, **kw)
+    q.solve()
+    return g, q
+
+
+def parity(graph, text):
+    g, q = wl(graph, text)
+    ref = oracle.hellings(graph, text)
+    for nm in g.names:
+        assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+    return g, q
+
+
+def test_worked_example():
+    parity(synth.worked_example_graph(), synth.GRAMMAR_WORKED)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random(seed):
+    graph = synth.random_graph(40 + 9 * seed, 100 + 15 * seed, 3, seed=seed)
+    parity(graph, synth.random_grammar_text(5, 3, 9, 6, seed % 3, seed=seed))
+
+
+@pytest.mark.parametrize("n", [1, 33, 257, 600])
+def test_ragged_and_dense(n):
+    parity(synth.random_graph(n, 3 * n, 2, seed=n), "S S S\nS A B\nA t0\nB t1\nE eps\nF E S\n")
+
+
+@pytest.mark.parametrize("text", [synth.GRAMMAR_Q1, synth.GRAMMAR_QSC, synth.GRAMMAR_Q2])
+def test_hierarchy(text):
+    parity(synth.hierarchy(3000, 900, seed=6), text)
+
+
+@pytest.mark.parametrize("p,q", [(6, 4), (9, 6), (33, 32), (128, 127)])
+def test_two_cycles(p, q):
+    parity(synth.two_cycles(p, q), synth.GRAMMAR_C3)
+
+
+def test_two_cycles_full_size_closed_form():
+    """Two directed cycles of 4096 and 4095 nodes sharing node 0, S -> a S b | a b: since
+    gcd = 1, R_S = R_S1 = (a-cycle nodes) x (b-cycle nodes), 16,773,120 pairs each."""
+    p, qq = 4096, 4095
+    graph = synth.two_cycles(p, qq)
+    g, q = wl(graph, synth.GRAMMAR_C3, timeout_s=600.0)
+    a_nodes = np.arange(p, dtype=np.uint32)
+    b_nodes = np.sort(np.concatenate([[0], np.arange(p, p + qq - 1)]).astype(np.uint32))
+    exp = np.stack([np.repeat(a_nodes, qq), np.tile(b_nodes, p)], axis=1)
+    for nm in ("S", "S1"):
+        got = q.get(nm)
+        assert got.shape == (p * qq, 2)
+        assert np.array_equal(got, exp), nm
+    assert q.count("A") == p and q.count("B") == qq
