@@ -40,6 +40,7 @@ __device__ __forceinline__ bool wl_set(const QDesc &q, const WLDesc &w, int x, u
     const uint32_t bit = 1u << (b & 31);
     const uint32_t old = atomicOr(&q.T[(uint64_t)x * q.plane + (uint64_t)a * q.W + (b >> 5)], bit);
     if (old & bit) return false;
+    atomicOr(&q.Trow[(uint64_t)x * q.W + (a >> 5)], 1u << (a & 31));  // extraction skips empty rows
     if (w.needs_tt[x]) atomicOr(&q.TT[(uint64_t)x * q.plane + (uint64_t)b * q.W + (a >> 5)], 1u << (a & 31));
     return true;
 }
