@@ -45,7 +45,39 @@ __device__ __forceinline__ bool wl_set(const QDesc &q, const WLDesc &w, int x, u
     return true;
 }
 
+// The only candidate pair derived from (a, i, j), if all of a's partners are static and
+// they yield exactly one candidate in total. Uniform across the warp (broadcast loads).
+__device__ __forceinline__ bool single_successor(const QDesc &q, const WLDesc &w, uint32_t a, uint32_t i, uint32_t j,
+                                                 uint32_t &na, uint32_t &ni, uint32_t &nj) {
+    uint32_t cnt = 0;
+    for (int o = __ldg(w.occ_start + a); o < __ldg(w.occ_start + a + 1); o++) {
+        const int2 oc = w.occ[o];
+        const Rule r = q.rules[oc.x];
+        const bool left = oc.y == 0;
+        const int p = left ? r.c : r.b;
+        if (!__ldg(w.is_static + p)) return false;
+        const uint64_t base = left ? __ldg(w.out_base + p) : __ldg(w.in_base + p);
+        const uint32_t key = left ? j : i;
+        const uint32_t lo = __ldg(w.csr_off + base + key), hi = __ldg(w.csr_off + base + key + 1);
+        cnt += hi - lo;
+        if (cnt > 1) return false;
+        if (hi - lo == 1) {
+            const uint32_t k = __ldg(w.csr_col + lo);
+            na = (uint32_t)r.lhs;
+            ni = left ? i : k;
+            nj = left ? k : j;
+        }
+    }
+    return cnt == 1;
+}
+
 // One warp. Processes the stack until it is empty, the deadline passes or it overflows.
+// Chain lookahead: when the current pair has a single successor through static operands,
+// the warp follows the chain up to 31 steps ahead (lane l holds step l + 1) and sets all of
+// them with one round of atomics. Every pair set in the batch has its successor set in the
+// same batch except the last one, so the chain continues from the last pair if it was new
+// and stops otherwise: the pairs processed are exactly those the one-at-a-time loop would
+// process, and the result is the same least fixpoint.
 __global__ void __launch_bounds__(32) k_worklist(const QDesc *qd, WLDesc w, unsigned long long top0) {
     const QDesc &q = *qd;
     const int lane = threadIdx.x;
@@ -67,6 +99,30 @@ __global__ void __launch_bounds__(32) k_worklist(const QDesc *qd, WLDesc w, unsi
         if ((processed & 4095u) == 0 && deadline && globaltimer_ns() > deadline) {
             if (lane == 0) q.st->error = kErrTimeout;
             break;
+        }
+        {
+            // chain lookahead
+            uint32_t xa = ca, xi = ci, xj = cj, ma = 0, mi = 0, mj = 0;
+            int len = 0;
+            for (; len < 31; len++) {
+                uint32_t na, ni, nj;
+                if (!single_successor(q, w, xa, xi, xj, na, ni, nj)) break;
+                xa = na; xi = ni; xj = nj;
+                if (lane == len) { ma = na; mi = ni; mj = nj; }
+            }
+            if (len > 0) {
+                const bool nw = lane < len ? wl_set(q, w, (int)ma, mi, mj) : false;
+                const unsigned m = __ballot_sync(0xffffffffu, nw);
+                processed += (unsigned)len - 1u;
+                if (m && lane == 0) atomicAdd(&q.st->new_bits, (unsigned long long)__popc(m));
+                if ((m >> (len - 1)) & 1u) {  // the last pair was new: continue from it
+                    ca = __shfl_sync(0xffffffffu, ma, len - 1);
+                    ci = __shfl_sync(0xffffffffu, mi, len - 1);
+                    cj = __shfl_sync(0xffffffffu, mj, len - 1);
+                    have = true;
+                }
+                continue;
+            }
         }
         uint32_t n_new = 0, ha = 0, hi = 0, hj = 0;
         for (int o = w.occ_start[ca]; o < w.occ_start[ca + 1]; o++) {
