@@ -56,8 +56,9 @@ def parse():
     ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="hier16k", choices=["hier16k", "batch256", "serve"],
-                    help="hier16k: the default line; batch256 / serve: the batched and served workloads")
+    ap.add_argument("--workload", default="hier16k", choices=["hier16k", "batch256", "serve", "cycles"],
+                    help="hier16k: the default line; batch256 / serve / cycles: the batched, served and "
+                         "two-cycle workloads")
     ap.add_argument("--n", type=int, default=None, help="smaller hierarchy for profiling captures")
     ap.add_argument("--classes", type=int, default=None)
     a = ap.parse_args()
@@ -490,6 +491,45 @@ def serve_arm(args):
     return 0
 
 
+def cycles_arm(args):
+    """Two directed cycles of 4096 and 4095 nodes sharing node 0, S -> a S b | a b: closure
+    by the worklist path (one warp, on-device), timed with CUDA events; the result is checked
+    against the closed form R_S = R_S1 = (a-cycle) x (b-cycle)."""
+    import torch
+
+    import paper_1707_01007_b300 as eng
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    p, q = 4096, 4095
+    graph = synth.two_cycles(p, q)
+    g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
+    qy = eng.Query(g, graph.n, graph.edges, path=eng.PATH_WORKLIST, timeout_s=600.0)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, min(args.warmup, 1))):
+        qy.solve(stream)
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        qy.solve(stream)
+        times.append(qy.stats()["solve_ms"])
+    ok = qy.count("S") == p * q and qy.count("S1") == p * q
+    st = qy.stats()
+    ms = float(np.median(times))
+    line = {"metric": "two-cycle closure time (worklist path)", "value": ms / 1e3, "unit": "s", "n_gpus": 1,
+            "steps": len(times), "warmup": 1, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
+            "config": {"workload": "two cycles 4096 / 4095 sharing node 0, S -> a S b | a b (n = 8190)"},
+            "pairs_S": qy.count("S"), "closed_form_count_ok": bool(ok), "worklist_items": st["worklist_items"],
+            "ns_per_item": ms * 1e6 / max(1, st["worklist_items"])}
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.hellings(graph, synth.GRAMMAR_C3)
+        line["cpu_baseline"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": "full workload once, one host thread"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -498,6 +538,8 @@ def main():
         return batch_arm(args)
     if args.workload == "serve":
         return serve_arm(args)
+    if args.workload == "cycles":
+        return cycles_arm(args)
     return engine_arm(args)
 
 

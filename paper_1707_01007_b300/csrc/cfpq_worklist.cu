@@ -30,6 +30,10 @@ struct WLDesc {
     const uint32_t *csr_off;      // offsets into csr_col (n + 1 per CSR)
     const uint32_t *csr_col;
     const int32_t *needs_tt;      // [n_nt] keep T^T of a (a dynamic and a left operand somewhere)
+    const int4 *chain;            // [n_nt] (1, lhs, left, partner) when a has exactly one operand
+                                  // occurrence and its partner is static, else (0, ...)
+    const uint64_t *chain_base;   // [n_nt] start of the partner's unique-successor table
+    const uint32_t *uniq;         // per static partner and direction: the only k, or 0xFFFFFFFF
     uint32_t *stack;              // triples (a, i, j)
     uint64_t cap;                 // stack capacity in triples
     unsigned long long *items;    // pairs processed
@@ -45,30 +49,20 @@ __device__ __forceinline__ bool wl_set(const QDesc &q, const WLDesc &w, int x, u
     return true;
 }
 
-// The only candidate pair derived from (a, i, j), if all of a's partners are static and
-// they yield exactly one candidate in total. Uniform across the warp (broadcast loads).
-__device__ __forceinline__ bool single_successor(const QDesc &q, const WLDesc &w, uint32_t a, uint32_t i, uint32_t j,
-                                                 uint32_t &na, uint32_t &ni, uint32_t &nj) {
-    uint32_t cnt = 0;
-    for (int o = __ldg(w.occ_start + a); o < __ldg(w.occ_start + a + 1); o++) {
-        const int2 oc = w.occ[o];
-        const Rule r = q.rules[oc.x];
-        const bool left = oc.y == 0;
-        const int p = left ? r.c : r.b;
-        if (!__ldg(w.is_static + p)) return false;
-        const uint64_t base = left ? __ldg(w.out_base + p) : __ldg(w.in_base + p);
-        const uint32_t key = left ? j : i;
-        const uint32_t lo = __ldg(w.csr_off + base + key), hi = __ldg(w.csr_off + base + key + 1);
-        cnt += hi - lo;
-        if (cnt > 1) return false;
-        if (hi - lo == 1) {
-            const uint32_t k = __ldg(w.csr_col + lo);
-            na = (uint32_t)r.lhs;
-            ni = left ? i : k;
-            nj = left ? k : j;
-        }
-    }
-    return cnt == 1;
+// The only candidate pair derived from (a, i, j) when a has one operand occurrence whose
+// partner is static and has exactly one partner pair there (precomputed tables).
+__device__ __forceinline__ bool single_successor(const int4 *chain, const uint64_t *cbase, const uint32_t *uniq,
+                                                 uint32_t a, uint32_t i, uint32_t j, uint32_t &na, uint32_t &ni,
+                                                 uint32_t &nj) {
+    const int4 d = chain[a];
+    if (!d.x) return false;
+    const bool left = d.z != 0;
+    const uint32_t k = __ldg(uniq + cbase[a] + (left ? j : i));
+    if (k == 0xFFFFFFFFu) return false;
+    na = (uint32_t)d.y;
+    ni = left ? i : k;
+    nj = left ? k : j;
+    return true;
 }
 
 // One warp. Processes the stack until it is empty, the deadline passes or it overflows.
@@ -85,6 +79,13 @@ __global__ void __launch_bounds__(32) k_worklist(const QDesc *qd, WLDesc w, unsi
     uint32_t ca = 0, ci = 0, cj = 0;  // item handed over in registers
     bool have = false;
     const unsigned long long deadline = ld_u64(&q.st->deadline_ns);
+    __shared__ int4 s_chain[kMaxNT];
+    __shared__ uint64_t s_cbase[kMaxNT];
+    for (int a = lane; a < q.n_nt; a += 32) {
+        s_chain[a] = w.chain[a];
+        s_cbase[a] = w.chain_base[a];
+    }
+    __syncwarp();
     for (;;) {
         if (!have) {
             if (top == 0) break;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(32) k_worklist(const QDesc *qd, WLDesc w, unsi
             int len = 0;
             for (; len < 31; len++) {
                 uint32_t na, ni, nj;
-                if (!single_successor(q, w, xa, xi, xj, na, ni, nj)) break;
+                if (!single_successor(s_chain, s_cbase, w.uniq, xa, xi, xj, na, ni, nj)) break;
                 xa = na; xi = ni; xj = nj;
                 if (lane == len) { ma = na; mi = ni; mj = nj; }
             }
@@ -310,11 +311,33 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
         for (const auto &e : pr) csr_col.push_back(by_src ? e.second : e.first);
         return base;
     };
+    std::vector<uint64_t> uniq_out_base(n_nt, 0), uniq_in_base(n_nt, 0);
+    std::vector<uint32_t> uniq;
     for (int a = 0; a < n_nt; a++)
         if (is_static[a]) {
             out_base[a] = build(pairs[a], true);
             in_base[a] = build(pairs[a], false);
+            // unique successor tables from the two CSRs just built
+            for (int dir = 0; dir < 2; dir++) {
+                const uint64_t b = dir == 0 ? out_base[a] : in_base[a];
+                (dir == 0 ? uniq_out_base : uniq_in_base)[a] = uniq.size();
+                for (uint32_t key = 0; key < n; key++) {
+                    const uint32_t lo = csr_off[b + key], hi = csr_off[b + key + 1];
+                    uniq.push_back(hi - lo == 1 ? csr_col[lo] : 0xFFFFFFFFu);
+                }
+            }
         }
+    std::vector<int4> chain(n_nt, make_int4(0, 0, 0, 0));
+    std::vector<uint64_t> chain_base(n_nt, 0);
+    for (int a = 0; a < n_nt; a++) {
+        if (occ[a].size() != 1) continue;
+        const Rule &r = c->rules[occ[a][0].x];
+        const bool left = occ[a][0].y == 0;
+        const int p = left ? r.c : r.b;
+        if (!is_static[p]) continue;
+        chain[a] = make_int4(1, r.lhs, left ? 1 : 0, p);
+        chain_base[a] = left ? uniq_out_base[p] : uniq_in_base[p];
+    }
     // device arena
     const uint64_t cap_full = (uint64_t)n_nt * (uint64_t)n * (uint64_t)n;
     const uint64_t cap = std::max<uint64_t>(1024, std::min<uint64_t>(cap_full, 1ull << 27));
@@ -330,6 +353,9 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
                           {(void **)&d.csr_off, csr_off.size() * 4 + 8},
                           {(void **)&d.csr_col, csr_col.size() * 4 + 8},
                           {(void **)&d.needs_tt, (size_t)n_nt * 4},
+                          {(void **)&d.chain, (size_t)n_nt * sizeof(int4)},
+                          {(void **)&d.chain_base, (size_t)n_nt * 8},
+                          {(void **)&d.uniq, uniq.size() * 4 + 8},
                           {(void **)&d.stack, cap * 12},
                           {(void **)&d.items, 8},
                           {(void **)&d.overflow, 8},
@@ -362,6 +388,9 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
     up(d.csr_off, csr_off.data(), csr_off.size() * 4);
     up(d.csr_col, csr_col.data(), csr_col.size() * 4);
     up(d.needs_tt, needs_tt.data(), (size_t)n_nt * 4);
+    up(d.chain, chain.data(), (size_t)n_nt * sizeof(int4));
+    up(d.chain_base, chain_base.data(), (size_t)n_nt * 8);
+    up(d.uniq, uniq.data(), uniq.size() * 4);
     if (!ok) {
         if (c->pooled) cudaFreeAsync(ws->arena, s);
         else cudaFree(ws->arena);
