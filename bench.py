@@ -417,7 +417,7 @@ def batch_arm(args):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     work = synth.batch_queries(256, 64, 4096, 0.3, seed=0)
     gs = [eng.Grammar(t, g.labels) for g, t in work]
-    qs = [eng.Query(gr, g.n, g.edges, path=eng.PATH_GATHER) for (g, _), gr in zip(work, gs)]
+    qs = [eng.Query(gr, g.n, g.edges, path=eng.PATH_GATHER, schedule=eng.SCHED_AUTO) for (g, _), gr in zip(work, gs)]
     stream = torch.cuda.current_stream()
 
     def timed(fn, reps):
@@ -430,9 +430,16 @@ def batch_arm(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    default = eng.batch_tuning_default()
+    for _ in range(args.warmup):
+        eng.solve_batch(qs, stream, tuning=default)
+    ms_default = timed(lambda: eng.solve_batch(qs, stream, tuning=default), args.steps)
+    # the autotuner times candidate launch configurations on this batch and installs the best
+    best, report = eng.autotune_batch(qs, stream)
     for _ in range(args.warmup):
         eng.solve_batch(qs, stream)
     ms_batch = timed(lambda: eng.solve_batch(qs, stream), args.steps)
+    phases = eng.batch_last_profile()
 
     def serial():
         for q in qs:
@@ -444,9 +451,12 @@ def batch_arm(args):
             "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
             "config": {"workload": "256 hierarchy queries, n log-uniform [64, 4096], class fraction 0.3, "
-                                   "Q1 or sc-only uniformly, seed 0", "path": "gather (grouped launch)"},
+                                   "Q1 or sc-only uniformly, seed 0", "path": "gather (grouped launch)",
+                       "launch_config": "autotuned on this batch (grid, tile width per size class, schedule)"},
             "serial_ms": ms_serial, "serial_queries_per_s": 256 / (ms_serial / 1e3),
-            "speedup_vs_serial": ms_serial / ms_batch}
+            "speedup_vs_serial": ms_serial / ms_batch,
+            "built_in_config_ms": ms_default, "tuned_config": best.as_dict(), "tuner": report,
+            "phase_ms": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in phases.items()}}
     print(json.dumps(line))
     return 0
 

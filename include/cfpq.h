@@ -73,7 +73,11 @@ typedef struct { int32_t A; uint32_t m, n; } cfpq_triple;
 
 enum cfpq_schedule {
     CFPQ_SCHED_INPLACE = 0,   /* products update T_A as soon as they finish (same least fixpoint) */
-    CFPQ_SCHED_JACOBI = 1     /* T_{k+1} = T_k u (T_k x T_k) exactly as Algorithm 1's loop body */
+    CFPQ_SCHED_JACOBI = 1,    /* T_{k+1} = T_k u (T_k x T_k) exactly as Algorithm 1's loop body */
+    CFPQ_SCHED_AUTO = 2       /* the library chooses: INPLACE in cfpq_solve; in batched solves and
+                                 serving, the schedule the batch tuning holds for the query's size
+                                 class (cfpq_batch_tuning). Every choice reaches the same least
+                                 fixpoint; switching between loop executions keeps it exact */
 };
 
 enum cfpq_path {
@@ -114,6 +118,8 @@ typedef struct {
     double product_bytes;     /* profile mode: bytes the gather products read or wrote (rows
                                  scanned, rows gathered, result rows merged) */
     int64_t worklist_items;   /* worklist path: pairs joined with their partners */
+    int32_t schedule;         /* schedule the last solve ran (INPLACE or JACOBI; AUTO resolved) */
+    int32_t gather_cpl;       /* batched solves: gather tile width used (32-bit words per lane) */
 } cfpq_stats;
 
 typedef struct cfpq_ctx cfpq_ctx;
@@ -206,6 +212,67 @@ void cfpq_grammar_free(cfpq_parsed_grammar *pg);
  * cap; the others are still complete).
  */
 int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream);
+
+/*
+ * Launch configuration of batched solves and serving steps, and its autotuner.
+ *
+ * The grouped launch spreads work items over a persistent grid; a product item is one row
+ * i of one production group and a tile of 32 * cpl words of that row (one word per lane
+ * per step, cpl words per lane), so cpl sets the tile shape: wide tiles scan the left
+ * operand's row once for many output words, narrow tiles give more items for the same
+ * row. Queries are put into size classes by their row length W = n_pad / 32 words: class
+ * c holds 2^(c-1) < W <= 2^c (W >= 8, so the classes in use are 3 .. 21). Per class the
+ * configuration gives cpl and the schedule taken by contexts created with
+ * CFPQ_SCHED_AUTO; for the whole launch, the number of resident blocks per SM.
+ *
+ * Every configuration computes the same result (bit-identical triples); only the device
+ * time and, for the schedule, the number of loop executions differ.
+ */
+#define CFPQ_TUNE_CLASSES 24
+typedef struct {
+    int32_t blocks_per_sm;                 /* 1 .. 8; 0 = the occupancy limit, at most 8 */
+    int32_t cpl[CFPQ_TUNE_CLASSES];        /* 1, 2, 4 or 8; 0 = built-in (the smallest cpl with
+                                              32 * cpl >= W, at most 8) */
+    int32_t schedule[CFPQ_TUNE_CLASSES];   /* CFPQ_SCHED_INPLACE or _JACOBI for AUTO contexts */
+} cfpq_batch_tuning;
+
+typedef struct {
+    int32_t trials;        /* batched solves the tuner timed (the final confirmation included) */
+    double default_ms;     /* device time of the batch with the built-in configuration */
+    double best_ms;        /* device time with the configuration returned */
+} cfpq_tune_report;
+
+/* The built-in configuration (blocks_per_sm 0, cpl 0, schedule INPLACE). Host only. */
+void cfpq_batch_tuning_default(cfpq_batch_tuning *t);
+/* Copies the configuration batched solves and serving steps of this process use now. */
+int cfpq_batch_tuning_get(cfpq_batch_tuning *t);
+/* Installs a configuration after checking every field (INVALID if one is out of range;
+ * nothing changes then). Host only; takes effect at the next batched launch. */
+int cfpq_batch_tuning_set(const cfpq_batch_tuning *t);
+/*
+ * Autotuner: times batched solves of these contexts (each a complete solve from the seed,
+ * so the contexts end solved, with the results of the last run) under candidate
+ * configurations, by coordinate descent from the built-in one: blocks per SM (1, 2, 4, 8,
+ * within occupancy), then cpl (1, 2, 4, 8) for each size class present, heaviest class
+ * first, then the schedule of each class that holds AUTO contexts. A candidate replaces
+ * the current choice only if it is at least 3 % faster. Every step is timed with CUDA
+ * events on `stream` (NULL: the first context's stream). The best configuration is
+ * merged into the installed one (the classes present and blocks_per_sm), copied to
+ * *best if best != NULL, and confirmed by one more run whose time is report->best_ms.
+ * Errors: those of cfpq_solve_batch (nothing is installed then).
+ */
+int cfpq_autotune_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream, cfpq_batch_tuning *best,
+                        cfpq_tune_report *report);
+/* Batched solve under an explicit configuration instead of the installed one. */
+int cfpq_solve_batch_tuned(cfpq_ctx *const *ctxs, int32_t k, const cfpq_batch_tuning *t, void *stream);
+/*
+ * Device time per phase of the last batched launch in this process (a batched solve or a
+ * serving step), in ms summed over its rounds, and the number of rounds. Phases: 0 start
+ * (clear, seed, first work tables), 1 products, 2 Jacobi merge, 3 delta clear, 4 per-query
+ * end of iteration, 5 work-table rebuild; entries beyond 5 are set to 0. Host only.
+ */
+#define CFPQ_BATCH_PHASES 6
+int cfpq_batch_last_profile(double *phase_ms, int32_t n_phases, int64_t *rounds);
 
 /*
  * Serving (continuous batching). A server takes independent queries (grammar + graph) at

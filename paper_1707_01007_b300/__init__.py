@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcfpq.so")
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_NOT_SOLVED, ERR_ITER_LIMIT, ERR_TIMEOUT, ERR_CUDA, ERR_BUFFER, \
     ERR_UNSUPPORTED = range(9)
-SCHED_INPLACE, SCHED_JACOBI = 0, 1
+SCHED_INPLACE, SCHED_JACOBI, SCHED_AUTO = 0, 1, 2
+TUNE_CLASSES = 24
 PATH_AUTO, PATH_TENSOR, PATH_GATHER, PATH_WORKLIST = 0, 1, 2, 3
 
 
@@ -67,7 +68,7 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("product_launches", ctypes.c_int64),
                 ("product_ms", ctypes.c_double), ("tensor_ms", ctypes.c_double),
                 ("tensor_launches", ctypes.c_int64), ("product_bytes", ctypes.c_double),
-                ("worklist_items", ctypes.c_int64)]
+                ("worklist_items", ctypes.c_int64), ("schedule", ctypes.c_int32), ("gather_cpl", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +92,21 @@ class ServerStats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("cpl", ctypes.c_int32 * TUNE_CLASSES),
+                ("schedule", ctypes.c_int32 * TUNE_CLASSES)]
+
+    def as_dict(self):
+        """blocks_per_sm plus the non-built-in entries per size class."""
+        return {"blocks_per_sm": self.blocks_per_sm,
+                "cpl": {c: self.cpl[c] for c in range(TUNE_CLASSES) if self.cpl[c]},
+                "schedule": {c: self.schedule[c] for c in range(TUNE_CLASSES) if self.schedule[c]}}
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("trials", ctypes.c_int32), ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double)]
 
 
 QUERY_QUEUED, QUERY_RUNNING, QUERY_DONE, QUERY_FAILED = range(4)
@@ -117,6 +133,12 @@ SIGNATURES = {
     "cfpq_grammar_name": (ctypes.c_char_p, [_VP, ctypes.c_int32]),
     "cfpq_grammar_free": (None, [_VP]),
     "cfpq_solve_batch": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP]),
+    "cfpq_batch_tuning_default": (None, [_P(BatchTuning)]),
+    "cfpq_batch_tuning_get": (ctypes.c_int, [_P(BatchTuning)]),
+    "cfpq_batch_tuning_set": (ctypes.c_int, [_P(BatchTuning)]),
+    "cfpq_autotune_batch": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP, _P(BatchTuning), _P(TuneReport)]),
+    "cfpq_solve_batch_tuned": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _P(BatchTuning), _VP]),
+    "cfpq_batch_last_profile": (ctypes.c_int, [_P(ctypes.c_double), ctypes.c_int32, _P(ctypes.c_int64)]),
     "cfpq_server_options_default": (ctypes.c_int, [_P(ServerOptions)]),
     "cfpq_server_create": (ctypes.c_int, [_P(ServerOptions), _P(_VP)]),
     "cfpq_server_submit": (ctypes.c_int, [_VP, _P(GrammarCNF), ctypes.c_uint32, _P(Edge), ctypes.c_size_t,
@@ -368,12 +390,62 @@ class Server:
         self.close()
 
 
-def solve_batch(queries, stream=None, check: bool = True) -> int:
-    """Solves many queries in one grouped persistent launch (``cfpq_solve_batch``)."""
-    arr = (ctypes.c_void_p * len(queries))(*[q.handle.value for q in queries])
-    code = _lib().cfpq_solve_batch(arr, len(queries), _stream_handle(stream))
+def _handles(queries):
+    return (ctypes.c_void_p * len(queries))(*[q.handle.value for q in queries])
+
+
+def solve_batch(queries, stream=None, check: bool = True, tuning: BatchTuning | None = None) -> int:
+    """Solves many queries in one grouped persistent launch (``cfpq_solve_batch``, or
+    ``cfpq_solve_batch_tuned`` under an explicit configuration)."""
+    arr = _handles(queries)
+    if tuning is None:
+        code = _lib().cfpq_solve_batch(arr, len(queries), _stream_handle(stream))
+    else:
+        code = _lib().cfpq_solve_batch_tuned(arr, len(queries), ctypes.byref(tuning), _stream_handle(stream))
     for q in queries:
         q.status = code
     if check:
         _check(code, "cfpq_solve_batch")
     return code
+
+
+def batch_tuning_default() -> BatchTuning:
+    t = BatchTuning()
+    _lib().cfpq_batch_tuning_default(ctypes.byref(t))
+    return t
+
+
+def batch_tuning() -> BatchTuning:
+    """The configuration batched solves and serving steps use now."""
+    t = BatchTuning()
+    _check(_lib().cfpq_batch_tuning_get(ctypes.byref(t)), "cfpq_batch_tuning_get")
+    return t
+
+
+def set_batch_tuning(t: BatchTuning) -> None:
+    _check(_lib().cfpq_batch_tuning_set(ctypes.byref(t)), "cfpq_batch_tuning_set")
+
+
+def autotune_batch(queries, stream=None):
+    """Times candidate launch configurations on this batch (``cfpq_autotune_batch``),
+    installs the best and returns (BatchTuning, report dict)."""
+    best, rep = BatchTuning(), TuneReport()
+    code = _lib().cfpq_autotune_batch(_handles(queries), len(queries), _stream_handle(stream), ctypes.byref(best),
+                                      ctypes.byref(rep))
+    for q in queries:
+        q.status = code
+    _check(code, "cfpq_autotune_batch")
+    return best, {"trials": rep.trials, "default_ms": rep.default_ms, "best_ms": rep.best_ms}
+
+
+BATCH_PHASES = ("start", "products", "jacobi_merge", "delta_clear", "tails", "tables")
+
+
+def batch_last_profile() -> dict:
+    """Per-phase device time (ms) and round count of the last batched launch."""
+    arr = (ctypes.c_double * len(BATCH_PHASES))()
+    rounds = ctypes.c_int64()
+    _check(_lib().cfpq_batch_last_profile(arr, len(BATCH_PHASES), ctypes.byref(rounds)), "cfpq_batch_last_profile")
+    out = {name: arr[i] for i, name in enumerate(BATCH_PHASES)}
+    out["rounds"] = int(rounds.value)
+    return out

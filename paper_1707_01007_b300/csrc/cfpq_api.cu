@@ -452,6 +452,10 @@ int read_status(cfpq_ctx *c, cudaStream_t s) {
     DevState st;
     CK(cudaMemcpyAsync(&st, c->d_state, sizeof(st), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    return apply_status(c, st);
+}
+
+int apply_status(cfpq_ctx *c, const DevState &st) {
     c->stats.iterations = (int64_t)st.iter;
     c->stats.new_bits = (int64_t)st.new_bits;
     c->stats.seed_bits = (int64_t)st.seed_bits;
@@ -476,7 +480,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     c->plane = (uint64_t)c->n_pad * c->W;
     c->n_nt = g->n_nonterm;
     c->n_term = g->n_term;
-    c->schedule = o.schedule;
+    c->schedule_req = o.schedule;
+    c->schedule = o.schedule == CFPQ_SCHED_AUTO ? CFPQ_SCHED_INPLACE : o.schedule;  // single solves
     c->path = o.path;
     c->use_graph = o.use_graph;
     c->profile = o.profile;
@@ -530,7 +535,9 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         c->prof_ev.assign(2 * std::max(1, c->n_groups), nullptr);
         for (auto &e : c->prof_ev) CK(cudaEventCreate(&e));
     }
-    // one arena for every buffer of the query (one allocation, one free)
+    // one arena for every buffer of the query (one allocation, one free). The batched
+    // launch clears T, X0, X1 as one span and R0, R1, Trow as another: keep each run of
+    // parts adjacent and in this order
     const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
     const size_t rowsz = (size_t)c->n_nt * c->W * sizeof(uint32_t);
     const size_t cells = (size_t)c->n_nt * c->n_pad;  // (non-terminal, row) extraction cells
@@ -637,7 +644,9 @@ int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edge
         if (edges[e].src >= n || edges[e].dst >= n || edges[e].label < 0 || edges[e].label >= g->n_term)
             return CFPQ_ERR_INVALID;
     if (opt) {
-        if (opt->schedule != CFPQ_SCHED_INPLACE && opt->schedule != CFPQ_SCHED_JACOBI) return CFPQ_ERR_INVALID;
+        if (opt->schedule != CFPQ_SCHED_INPLACE && opt->schedule != CFPQ_SCHED_JACOBI &&
+            opt->schedule != CFPQ_SCHED_AUTO)
+            return CFPQ_ERR_INVALID;
         if (opt->path < CFPQ_PATH_AUTO || opt->path > CFPQ_PATH_WORKLIST) return CFPQ_ERR_INVALID;
     }
     return CFPQ_OK;
@@ -748,6 +757,8 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     c->stats.solve_ms = ms;
+    c->stats.schedule = c->schedule;
+    c->stats.gather_cpl = 0;
     c->solved = true;
     return rc;
 }

@@ -7,8 +7,14 @@
 //
 // Every wait in this file (the grid barrier) is bounded by a %globaltimer deadline;
 // on expiry the kernel records an error and returns.
+//
+// The launch configuration (persistent grid size, gather tile width per size class, and
+// the schedule of CFPQ_SCHED_AUTO queries) comes from a process-wide table that the
+// autotuner at the end of this file fills by timing candidate configurations on the
+// caller's own batch.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "cfpq_batch.h"
@@ -116,6 +122,30 @@ __device__ void build_tables(BatchCtl *ctl, const BatchQuery *bq, int round) {
     __syncthreads();
 }
 
+constexpr unsigned long long kClrChunk = 2048;   // uint4 per clear item (32 KB)
+constexpr unsigned long long kSeedChunk = 256;   // edges or eps pairs per seed item
+
+// query j with off(j) <= x < off(j+1) for a start-phase prefix field (clr_off or seed_off)
+template <unsigned long long BatchQuery::*OFF>
+__device__ __forceinline__ int find_query(const BatchQuery *bq, int k, unsigned long long x) {
+    int lo = 0, hi = k;  // invariant: bq[lo].*OFF <= x, and x < bq[hi].*OFF when hi < k
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bq[mid].*OFF <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void zero_span(uint4 *p, unsigned long long lo, unsigned long long hi, int lane) {
+    for (unsigned long long w = lo + lane; w < hi; w += 32) p[w] = make_uint4(0, 0, 0, 0);
+}
+
+// Rows (of the 32 in row word wq) of a query that has n rows: mask of rows that exist.
+__device__ __forceinline__ uint32_t rows_in_word(uint32_t n, uint32_t wq) {
+    const uint32_t left = n - wq * 32u;
+    return left >= 32u ? 0xFFFFFFFFu : ((1u << left) - 1u);
+}
+
 __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *bq) {
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
@@ -124,64 +154,106 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
     const int k = ctl->k;
     if (gtid == 0) ctl->start_ns = globaltimer_ns();
 
-    // 1) queries starting in this launch: clear their matrices and state
-    for (int j = 0; j < k; j++) {
+    // 1) queries starting in this launch: clear their matrices (chunks over all such
+    //    queries) and reset their state
+    for (unsigned long long it = gwarp; it < ctl->clr_total; it += gwarps) {
+        const int j = find_query<&BatchQuery::clr_off>(bq, k, it);
+        const BatchQuery &b = bq[j];
+        const unsigned long long c = it - b.clr_off;
+        const unsigned long long ca = (b.clr_a_n + kClrChunk - 1) / kClrChunk;
+        if (c < ca) zero_span(b.clr_a, c * kClrChunk, min(b.clr_a_n, (c + 1) * kClrChunk), lane);
+        else zero_span(b.clr_b, (c - ca) * kClrChunk, min(b.clr_b_n, (c - ca + 1) * kClrChunk), lane);
+    }
+    for (int j = (int)gtid; j < k; j += (int)gthreads) {
         if (!bq[j].init) continue;
         const QDesc &q = bq[j].q;
-        const uint64_t words = (uint64_t)q.n_nt * q.plane;
-        uint4 *p4[3] = {(uint4 *)q.T, (uint4 *)q.X0, (uint4 *)q.X1};
-        for (int b = 0; b < 3; b++)
-            for (uint64_t w = gtid; w < words / 4; w += gthreads) p4[b][w] = make_uint4(0, 0, 0, 0);
-        const uint64_t rw = (uint64_t)q.n_nt * q.W;
-        for (uint64_t w = gtid; w < rw; w += gthreads) {
-            q.R0[w] = 0;
-            q.R1[w] = 0;
-            q.Trow[w] = 0;
-        }
-        if (gtid == 0) {
-            DevState *st = q.st;
-            const unsigned long long mi = st->max_iter;
-            memset(st, 0, sizeof(DevState));
-            st->max_iter = mi;
-            for (int a = 0; a < q.n_nt; a++) st->dirty[a] = 1u;
-        }
+        DevState *st = q.st;
+        memset(st, 0, sizeof(DevState));
+        st->max_iter = bq[j].max_iter;
+        for (int a = 0; a < q.n_nt; a++) st->dirty[a] = 1u;
     }
     if (!grid_barrier(ctl)) return;
-    // 2) matrix initialisation of the new queries
-    for (int j = 0; j < k; j++)
-        if (bq[j].init) seed_query(bq[j].q, gtid, gthreads);
+    // 2) matrix initialisation of the new queries (chunks of edges, then of eps pairs)
+    for (unsigned long long it = gwarp; it < ctl->seed_total; it += gwarps) {
+        const int j = find_query<&BatchQuery::seed_off>(bq, k, it);
+        const QDesc &q = bq[j].q;
+        const unsigned long long items = q.n_edges + (unsigned long long)q.n_eps * q.n;
+        const unsigned long long lo = (it - bq[j].seed_off) * kSeedChunk;
+        const unsigned long long hi = min(items, lo + kSeedChunk);
+        unsigned long long cnt = 0;
+        for (unsigned long long e = lo + lane; e < hi; e += 32) {
+            if (e < q.n_edges) {
+                const cfpq_edge ed = q.edges[e];
+                for (int u = 0; u < q.n_unary; u++)
+                    if (q.unary[u].y == ed.label) seed_pair(q, q.unary[u].x, ed.src, ed.dst, &cnt);
+            } else {
+                const unsigned long long t = e - q.n_edges;
+                const uint32_t m = (uint32_t)(t % q.n);
+                seed_pair(q, q.eps[t / q.n], m, m, &cnt);
+            }
+        }
+        if (cnt) atomicAdd(&q.st->seed_bits, cnt);
+    }
     if (!grid_barrier(ctl)) return;
     if (blockIdx.x == 0) build_tables(ctl, bq, 0);
     if (!grid_barrier(ctl)) return;
+    // phase clock (block 0, thread 0): time from the previous barrier to this one
+    unsigned long long t_prev = 0;
+    auto mark = [&](int phase) {
+        if (gtid == 0) {
+            const unsigned long long t = globaltimer_ns();
+            ctl->phase_ns[phase] += t - (phase == 0 ? ctl->start_ns : t_prev);
+            t_prev = t;
+        }
+    };
+    mark(0);
 
     for (int round = 0; round < ctl->max_rounds; round++) {
         const int na = min((int)ld_u32(&ctl->n_active), k);
         if (na <= 0) break;
-        // 3) products of every active query
+        if (gtid == 0) ctl->rounds++;
+        // 3) products of every active query: item = (group, row word, column chunk); the
+        //    warp visits the rows of its word that have a left delta row or, where the right
+        //    operand has a delta, a non-empty left row
         const unsigned long long np = __ldcg(ctl->prod_off + na);
         for (unsigned long long it = gwarp; it < np; it += gwarps) {
             const int s = find_slot(ctl->prod_off, na, it);
             const int j = __ldcg(ctl->act + s);
             if (j < 0 || j >= k) continue;
             const BatchQuery &b = bq[j];
+            const QDesc &q = b.q;
+            const uint32_t rw = (q.n + 31u) / 32u;
             const unsigned long long loc = it - __ldcg(ctl->prod_off + s);
-            const unsigned long long per_group = (unsigned long long)b.q.n * b.nch;
+            const unsigned long long per_group = (unsigned long long)rw * b.nch;
             const unsigned long long g64 = loc / per_group;
             const unsigned long long r = loc % per_group;
-            const uint32_t i = (uint32_t)(r / b.nch), ch = (uint32_t)(r % b.nch);
-            if (g64 >= (unsigned long long)b.q.n_groups || i >= b.q.n) continue;
+            const uint32_t wq = (uint32_t)(r / b.nch), ch = (uint32_t)(r % b.nch);
+            if (g64 >= (unsigned long long)q.n_groups || wq >= rw) continue;
             const int g = (int)g64;
-            const uint32_t parity = (uint32_t)(ld_u64(&b.q.st->iter) & 1ull);
-            switch (b.cpl) {
-                case 1: gather_row_chunk<1>(b.q, g, i, ch, lane, parity); break;
-                case 2: gather_row_chunk<2>(b.q, g, i, ch, lane, parity); break;
-                case 4: gather_row_chunk<4>(b.q, g, i, ch, lane, parity); break;
-                default: gather_row_chunk<8>(b.q, g, i, ch, lane, parity); break;
+            const uint32_t parity = (uint32_t)(ld_u64(&q.st->iter) & 1ull);
+            const uint32_t *DR = parity ? q.R1 : q.R0;
+            uint32_t cand = 0;
+            for (int ri = q.gstart[g]; ri < q.gstart[g + 1]; ri++) {
+                const int B = q.rules[ri].b, C = q.rules[ri].c;
+                cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
+                if (ld_u64(&q.st->dcount[parity][C]) != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
+            }
+            cand &= rows_in_word(q.n, wq);
+            while (cand) {
+                const uint32_t i = wq * 32u + (uint32_t)(__ffs(cand) - 1);
+                cand &= cand - 1;
+                switch (b.cpl) {
+                    case 1: gather_row_chunk<1>(q, g, i, ch, lane, parity); break;
+                    case 2: gather_row_chunk<2>(q, g, i, ch, lane, parity); break;
+                    case 4: gather_row_chunk<4>(q, g, i, ch, lane, parity); break;
+                    default: gather_row_chunk<8>(q, g, i, ch, lane, parity); break;
+                }
             }
         }
         if (!grid_barrier(ctl)) return;
+        mark(1);
         const unsigned long long nr = __ldcg(ctl->row_off + na);
-        // 4) Jacobi queries: T |= N
+        // 4) Jacobi queries: T |= N (item = non-terminal, row word: the rows N touched)
         if (ctl->any_jacobi) {
             for (unsigned long long it = gwarp; it < nr; it += gwarps) {
                 const int s = find_slot(ctl->row_off, na, it);
@@ -191,12 +263,21 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
                 if (b.q.schedule != CFPQ_SCHED_JACOBI) continue;
                 const unsigned long long loc = it - __ldcg(ctl->row_off + s);
                 if (loc >= b.row_items) continue;
-                merge_row(b.q, (int)(loc / b.q.n), (uint32_t)(loc % b.q.n), lane,
-                          (uint32_t)(ld_u64(&b.q.st->iter) & 1ull));
+                const uint32_t rw = (b.q.n + 31u) / 32u;
+                const int a = (int)(loc / rw);
+                const uint32_t wq = (uint32_t)(loc % rw);
+                const uint32_t parity = (uint32_t)(ld_u64(&b.q.st->iter) & 1ull);
+                uint32_t rows = __ldcg((parity ? b.q.R0 : b.q.R1) + (uint64_t)a * b.q.W + wq) & rows_in_word(b.q.n, wq);
+                while (rows) {
+                    const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+                    rows &= rows - 1;
+                    merge_row(b.q, a, i, lane, parity);
+                }
             }
             if (!grid_barrier(ctl)) return;
+            mark(2);
         }
-        // 5) clear the delta plane that was read
+        // 5) clear the delta plane that was read (item = non-terminal, row word)
         for (unsigned long long it = gwarp; it < nr; it += gwarps) {
             const int s = find_slot(ctl->row_off, na, it);
             const int j = __ldcg(ctl->act + s);
@@ -204,9 +285,19 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
             const BatchQuery &b = bq[j];
             const unsigned long long loc = it - __ldcg(ctl->row_off + s);
             if (loc >= b.row_items) continue;
-            clear_row(b.q, (int)(loc / b.q.n), (uint32_t)(loc % b.q.n), lane, (uint32_t)(ld_u64(&b.q.st->iter) & 1ull));
+            const uint32_t rw = (b.q.n + 31u) / 32u;
+            const int a = (int)(loc / rw);
+            const uint32_t wq = (uint32_t)(loc % rw);
+            const uint32_t parity = (uint32_t)(ld_u64(&b.q.st->iter) & 1ull);
+            uint32_t rows = __ldcg((parity ? b.q.R1 : b.q.R0) + (uint64_t)a * b.q.W + wq) & rows_in_word(b.q.n, wq);
+            while (rows) {
+                const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+                rows &= rows - 1;
+                clear_row(b.q, a, i, lane, parity);
+            }
         }
         if (!grid_barrier(ctl)) return;
+        mark(3);
         // 6) per-query end of iteration; a converged query is retired
         for (int s = blockIdx.x; s < na; s += gridDim.x) {
             const int j = __ldcg(ctl->act + s);
@@ -220,6 +311,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
         }
         // every tail must be done (it reads act[] and writes active[]) before the tables change
         if (!grid_barrier(ctl)) return;
+        mark(4);
         if (blockIdx.x == 0) {
             build_tables(ctl, bq, round + 1);
             if (threadIdx.x == 0 && ctl->limit_ns && globaltimer_ns() - ctl->start_ns > ctl->limit_ns)
@@ -227,10 +319,11 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
             __syncthreads();
         }
         if (!grid_barrier(ctl)) return;
+        mark(5);
     }
 }
 
-int batch_launch(BatchCtl *d_ctl, const BatchQuery *d_bq, cudaStream_t s, int *grid_out) {
+int batch_launch(BatchCtl *d_ctl, const BatchQuery *d_bq, cudaStream_t s, int blocks_per_sm, int *grid_out) {
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CFPQ_ERR_CUDA;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -238,7 +331,9 @@ int batch_launch(BatchCtl *d_ctl, const BatchQuery *d_bq, cudaStream_t s, int *g
     if (!coop) return CFPQ_ERR_UNSUPPORTED;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, 0) != cudaSuccess || per_sm < 1)
         return CFPQ_ERR_CUDA;
-    const int grid = sms * std::min(per_sm, 8);
+    // a cooperative grid must be co-resident: never more blocks per SM than occupancy allows
+    const int bps = blocks_per_sm > 0 ? std::min(blocks_per_sm, per_sm) : std::min(per_sm, 8);
+    const int grid = sms * bps;
     void *args[] = {(void *)&d_ctl, (void *)&d_bq};
     if (cudaLaunchCooperativeKernel((const void *)k_batch, dim3(grid), dim3(256), args, 0, s) != cudaSuccess)
         return CFPQ_ERR_CUDA;
@@ -246,16 +341,62 @@ int batch_launch(BatchCtl *d_ctl, const BatchQuery *d_bq, cudaStream_t s, int *g
     return CFPQ_OK;
 }
 
-void fill_batch_query(const cfpq_ctx *c, BatchQuery *b, int init) {
+// ------------------------------------------------------------------------------------ tuning
+
+int batch_size_class(uint32_t W) {
+    int c = 0;
+    while (c < CFPQ_TUNE_CLASSES - 1 && (1u << c) < W) c++;
+    return c;
+}
+
+static std::mutex g_tune_mu;
+static cfpq_batch_tuning g_tune = [] {
+    cfpq_batch_tuning t;
+    cfpq_batch_tuning_default(&t);
+    return t;
+}();
+
+void batch_tuning_snapshot(cfpq_batch_tuning *t) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    *t = g_tune;
+}
+
+static bool tuning_valid(const cfpq_batch_tuning &t) {
+    if (t.blocks_per_sm < 0 || t.blocks_per_sm > 8) return false;
+    for (int c = 0; c < CFPQ_TUNE_CLASSES; c++) {
+        const int v = t.cpl[c];
+        if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return false;
+        if (t.schedule[c] != CFPQ_SCHED_INPLACE && t.schedule[c] != CFPQ_SCHED_JACOBI) return false;
+    }
+    return true;
+}
+
+void fill_batch_query(const cfpq_ctx *c, BatchQuery *b, int init, const cfpq_batch_tuning &t) {
     memset(b, 0, sizeof(*b));
     b->q = c->hq;
+    const int cls = batch_size_class(c->W);
     int cpl = 1;
-    const uint32_t nch = gather_chunks(c->W, &cpl);
+    uint32_t nch = gather_chunks(c->W, &cpl);
+    if (t.cpl[cls] > 0) {
+        cpl = t.cpl[cls];
+        nch = (c->W + 32u * (uint32_t)cpl - 1) / (32u * (uint32_t)cpl);
+    }
     b->cpl = cpl;
     b->nch = nch;
-    b->prod_items = (unsigned long long)c->n_groups * c->n * nch;
-    b->row_items = (unsigned long long)c->n_nt * c->n;
+    if (c->schedule_req == CFPQ_SCHED_AUTO) b->q.schedule = t.schedule[cls];
+    const unsigned long long rw = (c->n + 31u) / 32u;  // row words: 32 rows per work item
+    b->prod_items = (unsigned long long)c->n_groups * rw * nch;
+    b->row_items = (unsigned long long)c->n_nt * rw;
     b->init = init;
+    b->max_iter = c->max_iter;
+    // [T, X1 end) and [R0, Trow end) are contiguous in the query's arena (parts are
+    // 256-byte aligned and padded, so both spans are whole uint4s)
+    const size_t planes = (size_t)c->n_nt * c->plane * 4;
+    const size_t rowsz = ((size_t)c->n_nt * c->W * 4 + 255) / 256 * 256;
+    b->clr_a = reinterpret_cast<uint4 *>(c->d_T);
+    b->clr_a_n = 3 * planes / 16;
+    b->clr_b = reinterpret_cast<uint4 *>(c->d_R0);
+    b->clr_b_n = ((size_t)(reinterpret_cast<char *>(c->d_Trow) - reinterpret_cast<char *>(c->d_R0)) + rowsz) / 16;
     b->max_rounds = 1 << 30;
 }
 
@@ -267,7 +408,8 @@ int batch_buffers_alloc(BatchBuffers *b, int k) {
         cudaMalloc(&b->active, sizeof(int) * k) != cudaSuccess ||
         cudaMalloc(&b->act, sizeof(int) * k) != cudaSuccess ||
         cudaMalloc(&b->prod_off, sizeof(unsigned long long) * (k + 1)) != cudaSuccess ||
-        cudaMalloc(&b->row_off, sizeof(unsigned long long) * (k + 1)) != cudaSuccess) {
+        cudaMalloc(&b->row_off, sizeof(unsigned long long) * (k + 1)) != cudaSuccess ||
+        cudaMalloc(&b->states, sizeof(DevState) * k) != cudaSuccess) {
         cudaGetLastError();
         batch_buffers_free(b);
         return CFPQ_ERR_NOMEM;
@@ -275,10 +417,21 @@ int batch_buffers_alloc(BatchBuffers *b, int k) {
     return CFPQ_OK;
 }
 
-int batch_buffers_upload(BatchBuffers *b, const BatchQuery *hb, const int *active, int k, int max_rounds,
+int batch_buffers_upload(BatchBuffers *b, BatchQuery *hb, const int *active, int k, int max_rounds,
                          bool any_jacobi, cudaStream_t s) {
     BatchCtl ctl;
     memset(&ctl, 0, sizeof(ctl));
+    unsigned long long clr = 0, seed = 0;
+    for (int j = 0; j < k; j++) {
+        hb[j].clr_off = clr;
+        hb[j].seed_off = seed;
+        if (!hb[j].init) continue;
+        clr += (hb[j].clr_a_n + kClrChunk - 1) / kClrChunk + (hb[j].clr_b_n + kClrChunk - 1) / kClrChunk;
+        const unsigned long long items = hb[j].q.n_edges + (unsigned long long)hb[j].q.n_eps * hb[j].q.n;
+        seed += (items + kSeedChunk - 1) / kSeedChunk;
+    }
+    ctl.clr_total = clr;
+    ctl.seed_total = seed;
     ctl.k = k;
     ctl.max_rounds = max_rounds;
     ctl.any_jacobi = any_jacobi ? 1 : 0;
@@ -293,8 +446,35 @@ int batch_buffers_upload(BatchBuffers *b, const BatchQuery *hb, const int *activ
     return CFPQ_OK;
 }
 
+__global__ void k_collect_states(const BatchQuery *bq, int k, DevState *out) {
+    const int j = blockIdx.x;
+    if (j >= k) return;
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(bq[j].q.st);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(out + j);
+    for (int w = threadIdx.x; w < (int)(sizeof(DevState) / 8); w += blockDim.x) dst[w] = __ldcg(src + w);
+}
+static_assert(sizeof(DevState) % 8 == 0, "DevState copied as 64-bit words");
+
+int batch_collect_states(const BatchBuffers *b, const BatchQuery *d_bq, int k, cudaStream_t s) {
+    k_collect_states<<<k, 128, 0, s>>>(d_bq, k, b->states);
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
+
+static std::mutex g_prof_mu;
+static unsigned long long g_prof_ns[kBatchPhases], g_prof_rounds;
+
+void batch_record_profile(const BatchBuffers *b, cudaStream_t s) {
+    BatchCtl ctl;
+    if (cudaMemcpyAsync(&ctl, b->ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    memcpy(g_prof_ns, ctl.phase_ns, sizeof(g_prof_ns));
+    g_prof_rounds = ctl.rounds;
+}
+
 void batch_buffers_free(BatchBuffers *b) {
-    void *ptrs[] = {b->ctl, b->bq, b->active, b->act, b->prod_off, b->row_off};
+    void *ptrs[] = {b->ctl, b->bq, b->active, b->act, b->prod_off, b->row_off, b->states};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     memset(b, 0, sizeof(*b));
@@ -304,59 +484,214 @@ void batch_buffers_free(BatchBuffers *b) {
 
 using namespace cfpq;
 
-extern "C" int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream) {
-    if (!ctxs || k <= 0) return CFPQ_ERR_INVALID;
-    for (int j = 0; j < k; j++)
-        if (!ctxs[j]) return CFPQ_ERR_INVALID;
-    cudaStream_t s = stream ? (cudaStream_t)stream : ctxs[0]->stream;
+// Control buffers of batched solves, kept per device and grown on demand (no allocation
+// or free, and so no device synchronisation, per call). Calls are serialised by the lock,
+// which a solve holds until its launch has finished.
+constexpr int kMaxBatchDevices = 64;
+static std::mutex g_bufs_mu;
+static BatchBuffers g_bufs[kMaxBatchDevices];
+
+static int batch_buffers_for(int k, BatchBuffers **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxBatchDevices) return CFPQ_ERR_CUDA;
+    BatchBuffers *b = &g_bufs[dev];
+    if (b->k < k) {
+        if (b->k) batch_buffers_free(b);
+        const int rc = batch_buffers_alloc(b, std::max(k, 2 * b->k));
+        if (rc != CFPQ_OK) return rc;
+    }
+    *out = b;
+    return CFPQ_OK;
+}
+
+// One complete batched solve of ctxs under configuration t; *ms = device time of the launch.
+static int solve_batch_with(cfpq_ctx *const *ctxs, int k, cudaStream_t s, const cfpq_batch_tuning &t, float *ms_out) {
+    std::lock_guard<std::mutex> lock(g_bufs_mu);
     std::vector<BatchQuery> hb(k);
     bool any_jacobi = false;
     for (int j = 0; j < k; j++) {
-        fill_batch_query(ctxs[j], &hb[j], 1);
-        any_jacobi |= ctxs[j]->schedule == CFPQ_SCHED_JACOBI;
+        fill_batch_query(ctxs[j], &hb[j], 1, t);
+        any_jacobi |= hb[j].q.schedule == CFPQ_SCHED_JACOBI;
         ctxs[j]->solved = false;
         ctxs[j]->last_stream = s;
         ctxs[j]->fixed_launches = 0;
         ctxs[j]->iter_launches = 0;
     }
-    BatchBuffers bufs;
-    int rc = batch_buffers_alloc(&bufs, k);
+    BatchBuffers *pb = nullptr;
+    int rc = batch_buffers_for(k, &pb);
     if (rc != CFPQ_OK) return rc;
-    // the per-query state carries each query's iteration cap into the kernel
-    for (int j = 0; j < k && rc == CFPQ_OK; j++) {
-        DevState st0;
-        memset(&st0, 0, sizeof(st0));
-        st0.max_iter = ctxs[j]->max_iter;
-        if (cudaMemcpyAsync(ctxs[j]->d_state, &st0, sizeof(st0), cudaMemcpyHostToDevice, s) != cudaSuccess)
-            rc = CFPQ_ERR_CUDA;
-    }
+    BatchBuffers &bufs = *pb;
     std::vector<int> active(k, 1);
     if (rc == CFPQ_OK) rc = batch_buffers_upload(&bufs, hb.data(), active.data(), k, 1 << 30, any_jacobi, s);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    if (rc == CFPQ_OK) rc = batch_launch(bufs.ctl, bufs.bq, s, nullptr);
+    if (rc == CFPQ_OK) rc = batch_launch(bufs.ctl, bufs.bq, s, t.blocks_per_sm, nullptr);
     cudaEventRecord(e1, s);
     unsigned err = 0;
-    if (rc == CFPQ_OK && cudaMemcpyAsync(&err, &bufs.ctl->error, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    std::vector<DevState> states(k);
+    if (rc == CFPQ_OK) rc = batch_collect_states(&bufs, bufs.bq, k, s);
+    if (rc == CFPQ_OK && (cudaMemcpyAsync(&err, &bufs.ctl->error, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                          cudaMemcpyAsync(states.data(), bufs.states, sizeof(DevState) * k, cudaMemcpyDeviceToHost, s) !=
+                              cudaSuccess))
         rc = CFPQ_ERR_CUDA;
     if (rc == CFPQ_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = CFPQ_ERR_CUDA;
     float ms = 0.f;
-    if (rc == CFPQ_OK) cudaEventElapsedTime(&ms, e0, e1);
+    if (rc == CFPQ_OK) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        batch_record_profile(&bufs, s);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    batch_buffers_free(&bufs);
     if (rc != CFPQ_OK) return rc;
     if (err) return CFPQ_ERR_TIMEOUT;
+    if (ms_out) *ms_out = ms;
     int worst = CFPQ_OK;
     for (int j = 0; j < k; j++) {
-        const int r = read_status(ctxs[j], s);
+        const int r = apply_status(ctxs[j], states[j]);
         ctxs[j]->stats.solve_ms = ms;
+        ctxs[j]->stats.schedule = hb[j].q.schedule;
+        ctxs[j]->stats.gather_cpl = hb[j].cpl;
         ctxs[j]->stats.kernel_launches = 1;  // the whole batch is one cooperative launch
         ctxs[j]->solved = true;
         if (r == CFPQ_ERR_CUDA) return r;
         if (r != CFPQ_OK) worst = r;
     }
     return worst;
+}
+
+static int check_batch_args(cfpq_ctx *const *ctxs, int32_t k) {
+    if (!ctxs || k <= 0) return CFPQ_ERR_INVALID;
+    for (int j = 0; j < k; j++)
+        if (!ctxs[j]) return CFPQ_ERR_INVALID;
+    return CFPQ_OK;
+}
+
+extern "C" void cfpq_batch_tuning_default(cfpq_batch_tuning *t) {
+    if (!t) return;
+    memset(t, 0, sizeof(*t));
+    for (int c = 0; c < CFPQ_TUNE_CLASSES; c++) t->schedule[c] = CFPQ_SCHED_INPLACE;
+}
+
+extern "C" int cfpq_batch_tuning_get(cfpq_batch_tuning *t) {
+    if (!t) return CFPQ_ERR_INVALID;
+    batch_tuning_snapshot(t);
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_batch_tuning_set(const cfpq_batch_tuning *t) {
+    if (!t || !tuning_valid(*t)) return CFPQ_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune = *t;
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream) {
+    const int rc = check_batch_args(ctxs, k);
+    if (rc != CFPQ_OK) return rc;
+    cfpq_batch_tuning t;
+    batch_tuning_snapshot(&t);
+    return solve_batch_with(ctxs, k, stream ? (cudaStream_t)stream : ctxs[0]->stream, t, nullptr);
+}
+
+extern "C" int cfpq_solve_batch_tuned(cfpq_ctx *const *ctxs, int32_t k, const cfpq_batch_tuning *t, void *stream) {
+    const int rc = check_batch_args(ctxs, k);
+    if (rc != CFPQ_OK) return rc;
+    if (!t || !tuning_valid(*t)) return CFPQ_ERR_INVALID;
+    return solve_batch_with(ctxs, k, stream ? (cudaStream_t)stream : ctxs[0]->stream, *t, nullptr);
+}
+
+extern "C" int cfpq_autotune_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream, cfpq_batch_tuning *best,
+                                   cfpq_tune_report *report) {
+    int rc = check_batch_args(ctxs, k);
+    if (rc != CFPQ_OK) return rc;
+    cudaStream_t s = stream ? (cudaStream_t)stream : ctxs[0]->stream;
+    // size classes present, heaviest first (work ~ groups x rows x row words), and the
+    // classes holding contexts whose schedule is the library's choice
+    std::vector<double> work(CFPQ_TUNE_CLASSES, 0.0);
+    std::vector<bool> has_auto(CFPQ_TUNE_CLASSES, false);
+    for (int j = 0; j < k; j++) {
+        const int c = batch_size_class(ctxs[j]->W);
+        work[c] += (double)ctxs[j]->n_groups * ctxs[j]->n * ctxs[j]->W;
+        if (ctxs[j]->schedule_req == CFPQ_SCHED_AUTO) has_auto[c] = true;
+    }
+    std::vector<int> classes;
+    for (int c = 0; c < CFPQ_TUNE_CLASSES; c++)
+        if (work[c] > 0.0) classes.push_back(c);
+    std::sort(classes.begin(), classes.end(), [&](int a, int b) { return work[a] > work[b]; });
+
+    int trials = 0;
+    auto timed = [&](const cfpq_batch_tuning &t, float *ms) {
+        trials++;
+        return solve_batch_with(ctxs, k, s, t, ms);
+    };
+    cfpq_batch_tuning cur;
+    cfpq_batch_tuning_default(&cur);
+    float cur_ms = 0.f;
+    rc = timed(cur, &cur_ms);
+    if (rc != CFPQ_OK) return rc;
+    const float default_ms = cur_ms;
+    auto consider = [&](const cfpq_batch_tuning &cand) -> int {
+        float ms = 0.f;
+        const int r = timed(cand, &ms);
+        if (r != CFPQ_OK) return r;
+        if (ms < 0.97f * cur_ms) {
+            cur = cand;
+            cur_ms = ms;
+        }
+        return CFPQ_OK;
+    };
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, 0) != cudaSuccess || per_sm < 1)
+        return CFPQ_ERR_CUDA;
+    for (int bps : {1, 2, 4, 8}) {
+        if (bps > per_sm || bps == std::min(per_sm, 8)) continue;  // the default is already timed
+        cfpq_batch_tuning cand = cur;
+        cand.blocks_per_sm = bps;
+        if ((rc = consider(cand)) != CFPQ_OK) return rc;
+    }
+    for (int c : classes) {
+        int builtin = 1;
+        gather_chunks(1u << c, &builtin);
+        const int now = cur.cpl[c] > 0 ? cur.cpl[c] : builtin;
+        for (int v : {1, 2, 4, 8}) {
+            if (v == now) continue;
+            cfpq_batch_tuning cand = cur;
+            cand.cpl[c] = v;
+            if ((rc = consider(cand)) != CFPQ_OK) return rc;
+        }
+    }
+    for (int c : classes) {
+        if (!has_auto[c]) continue;
+        cfpq_batch_tuning cand = cur;
+        cand.schedule[c] = cur.schedule[c] == CFPQ_SCHED_INPLACE ? CFPQ_SCHED_JACOBI : CFPQ_SCHED_INPLACE;
+        if ((rc = consider(cand)) != CFPQ_OK) return rc;
+    }
+    // confirm (the contexts end with the chosen configuration's results and statistics)
+    float best_ms = 0.f;
+    if ((rc = timed(cur, &best_ms)) != CFPQ_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune.blocks_per_sm = cur.blocks_per_sm;
+        for (int c : classes) {
+            g_tune.cpl[c] = cur.cpl[c];
+            if (has_auto[c]) g_tune.schedule[c] = cur.schedule[c];
+        }
+    }
+    if (best) *best = cur;
+    if (report) {
+        report->trials = trials;
+        report->default_ms = default_ms;
+        report->best_ms = best_ms;
+    }
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_batch_last_profile(double *phase_ms, int32_t n_phases, int64_t *rounds) {
+    if ((!phase_ms && n_phases > 0) || n_phases < 0) return CFPQ_ERR_INVALID;
+    std::lock_guard<std::mutex> lock(g_prof_mu);
+    for (int i = 0; i < n_phases; i++) phase_ms[i] = i < kBatchPhases ? (double)g_prof_ns[i] * 1e-6 : 0.0;
+    if (rounds) *rounds = (int64_t)g_prof_rounds;
+    return CFPQ_OK;
 }

@@ -15,6 +15,7 @@ struct cfpq_ctx {
     int n_nt = 0, n_term = 0, n_groups = 0, n_unary = 0, n_eps_rules = 0;
     size_t n_edges = 0;
     int schedule = 0, path = 0, use_graph = 1, profile = 0;
+    int schedule_req = 0;          // as requested (CFPQ_SCHED_AUTO resolved per launch kind)
     double timeout_s = 0.0;
     uint64_t max_iter = 0;
     std::vector<cfpq::Rule> rules;
@@ -83,6 +84,8 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
 void launch_gather(cfpq_ctx *c, int g, cudaStream_t s);
 void arm_deadline(cfpq_ctx *c, cudaStream_t s);
 int read_status(cfpq_ctx *c, cudaStream_t s);
+// Statistics and status of a solve from a copy of its device state.
+int apply_status(cfpq_ctx *c, const DevState &st);
 int run_loop(cfpq_ctx *c, cudaStream_t s);
 uint32_t gather_chunks(uint32_t W, int *cpl);
 

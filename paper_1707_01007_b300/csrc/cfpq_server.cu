@@ -222,17 +222,19 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
     std::vector<BatchQuery> hb(k);
     std::vector<int> active(k, 1);
     bool any_jacobi = false;
+    cfpq_batch_tuning tune;
+    batch_tuning_snapshot(&tune);
     for (int j = 0; j < k; j++) {
-        fill_batch_query(s->resident[j]->ctx, &hb[j], s->resident[j]->init);
+        fill_batch_query(s->resident[j]->ctx, &hb[j], s->resident[j]->init, tune);
         // round budget: cheap queries run up to `rounds` executions per launch, expensive ones
         // fewer, so small queries are not held to the pace of a large one
         const double scale = 4096.0 / (double)s->resident[j]->ctx->n_pad;
         hb[j].max_rounds = std::max(1, std::min(s->rounds, (int)(s->rounds * scale * scale)));
-        any_jacobi |= s->resident[j]->ctx->schedule == CFPQ_SCHED_JACOBI;
+        any_jacobi |= hb[j].q.schedule == CFPQ_SCHED_JACOBI;
     }
     rc = batch_buffers_upload(&s->bufs, hb.data(), active.data(), k, s->rounds, any_jacobi, s->stream);
     if (rc != CFPQ_OK) return rc;
-    rc = batch_launch(s->bufs.ctl, s->bufs.bq, s->stream, nullptr);
+    rc = batch_launch(s->bufs.ctl, s->bufs.bq, s->stream, tune.blocks_per_sm, nullptr);
     if (rc != CFPQ_OK) return rc;
     s->launches++;
     unsigned err = 0;
@@ -242,6 +244,7 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
         cudaStreamSynchronize(s->stream) != cudaSuccess)
         return CFPQ_ERR_CUDA;
     if (err) return CFPQ_ERR_TIMEOUT;
+    batch_record_profile(&s->bufs, s->stream);
     // 3) retire the queries that stopped
     std::vector<Served *> keep;
     for (int j = 0; j < k; j++) {

@@ -109,3 +109,43 @@ def test_options_defaults():
     assert eng.library().cfpq_options_default(ctypes.byref(opt)) == eng.OK
     assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter) == \
         (eng.SCHED_INPLACE, eng.PATH_AUTO, 1, 0, 0)
+
+
+def test_batch_tuning_host_calls():
+    lib = eng.library()
+    d = eng.batch_tuning_default()
+    assert d.blocks_per_sm == 0 and all(v == 0 for v in d.cpl) and all(v == eng.SCHED_INPLACE for v in d.schedule)
+    before = eng.batch_tuning()
+    try:
+        t = eng.batch_tuning_default()
+        t.blocks_per_sm = 4
+        t.cpl[5], t.cpl[9] = 2, 8
+        t.schedule[7] = eng.SCHED_JACOBI
+        eng.set_batch_tuning(t)
+        got = eng.batch_tuning()
+        assert got.as_dict() == {"blocks_per_sm": 4, "cpl": {5: 2, 9: 8}, "schedule": {7: eng.SCHED_JACOBI}}
+        # every invalid field is rejected and leaves the installed configuration unchanged
+        for field, idx, value in [("blocks_per_sm", None, 9), ("blocks_per_sm", None, -1), ("cpl", 3, 3),
+                                  ("cpl", 4, 16), ("schedule", 6, eng.SCHED_AUTO), ("schedule", 2, -1)]:
+            bad = eng.batch_tuning_default()
+            if idx is None:
+                setattr(bad, field, value)
+            else:
+                getattr(bad, field)[idx] = value
+            assert lib.cfpq_batch_tuning_set(ctypes.byref(bad)) == eng.ERR_INVALID, (field, idx, value)
+            assert eng.batch_tuning().as_dict() == got.as_dict()
+        assert lib.cfpq_batch_tuning_set(None) == eng.ERR_INVALID
+        assert lib.cfpq_batch_tuning_get(None) == eng.ERR_INVALID
+        assert lib.cfpq_autotune_batch(None, 0, None, None, None) == eng.ERR_INVALID
+        assert lib.cfpq_solve_batch_tuned(None, 0, ctypes.byref(t), None) == eng.ERR_INVALID
+    finally:
+        eng.set_batch_tuning(before)
+
+
+
+def test_batch_profile_host_call():
+    lib = eng.library()
+    assert lib.cfpq_batch_last_profile(None, 3, None) == eng.ERR_INVALID
+    assert lib.cfpq_batch_last_profile(None, 0, None) == eng.OK
+    p = eng.batch_last_profile()
+    assert list(p)[:len(eng.BATCH_PHASES)] == list(eng.BATCH_PHASES) and p["rounds"] >= 0
