@@ -440,6 +440,13 @@ def batch_arm(args):
         eng.solve_batch(qs, stream)
     ms_batch = timed(lambda: eng.solve_batch(qs, stream), args.steps)
     phases = eng.batch_last_profile()
+    # bytes the products phase moves: the same batch once more with word counting on
+    # (profile mode: scanned left rows, gathered right-row chunks, merged result chunks)
+    prof_qs = [eng.Query(gr, g.n, g.edges, path=eng.PATH_GATHER, schedule=eng.SCHED_AUTO, profile=True)
+               for (g, _), gr in zip(work, gs)]
+    eng.solve_batch(prof_qs, stream)
+    product_bytes = sum(q.stats()["product_bytes"] for q in prof_qs)
+    del prof_qs
 
     def serial():
         for q in qs:
@@ -456,7 +463,10 @@ def batch_arm(args):
             "serial_ms": ms_serial, "serial_queries_per_s": 256 / (ms_serial / 1e3),
             "speedup_vs_serial": ms_serial / ms_batch,
             "built_in_config_ms": ms_default, "tuned_config": best.as_dict(), "tuner": report,
-            "phase_ms": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in phases.items()}}
+            "phase_ms": {k: (round(v, 3) if isinstance(v, float) else
+                             ([round(x, 3) for x in v] if isinstance(v, list) else v)) for k, v in phases.items()},
+            "products_phase": {"bytes": product_bytes,
+                               "gbs": product_bytes / (phases["products"] * 1e6) if phases["products"] else None}}
     print(json.dumps(line))
     return 0
 

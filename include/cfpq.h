@@ -268,11 +268,16 @@ int cfpq_solve_batch_tuned(cfpq_ctx *const *ctxs, int32_t k, const cfpq_batch_tu
 /*
  * Device time per phase of the last batched launch in this process (a batched solve or a
  * serving step), in ms summed over its rounds, and the number of rounds. Phases: 0 start
- * (clear, seed, first work tables), 1 products, 2 Jacobi merge, 3 delta clear, 4 per-query
- * end of iteration, 5 work-table rebuild; entries beyond 5 are set to 0. Host only.
+ * (clear, seed, first work tables), 1 scan (rows that take part in the products, and the
+ * clear of the delta plane the products will write), 2 products, 3 Jacobi merge, 4
+ * per-query end of iteration, 5 work-table rebuild; entries beyond 5 are set to 0. round_product_ms
+ * (may be NULL when n_round_slots is 0) receives the products phase of each of the first
+ * CFPQ_BATCH_PROFILE_ROUNDS rounds; other slots are set to 0. Host only.
  */
 #define CFPQ_BATCH_PHASES 6
-int cfpq_batch_last_profile(double *phase_ms, int32_t n_phases, int64_t *rounds);
+#define CFPQ_BATCH_PROFILE_ROUNDS 64
+int cfpq_batch_last_profile(double *phase_ms, int32_t n_phases, int64_t *rounds, double *round_product_ms,
+                            int32_t n_round_slots);
 
 /*
  * Serving (continuous batching). A server takes independent queries (grammar + graph) at
@@ -292,7 +297,7 @@ typedef struct {
     uint64_t hbm_budget_bytes;  /* device bytes resident queries may hold; 0 = 90 % of free memory at creation */
     int32_t rounds_per_step;    /* most loop executions per step of a query (queries with n above
                                    4096 get proportionally fewer, at least one); 0 = 8 */
-    int32_t max_resident;       /* upper bound on resident queries; 0 = 4096 */
+    int32_t max_resident;       /* upper bound on resident queries (at most 2^24); 0 = 4096 */
 } cfpq_server_options;
 
 typedef struct {

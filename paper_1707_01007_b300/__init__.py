@@ -138,7 +138,8 @@ SIGNATURES = {
     "cfpq_batch_tuning_set": (ctypes.c_int, [_P(BatchTuning)]),
     "cfpq_autotune_batch": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP, _P(BatchTuning), _P(TuneReport)]),
     "cfpq_solve_batch_tuned": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _P(BatchTuning), _VP]),
-    "cfpq_batch_last_profile": (ctypes.c_int, [_P(ctypes.c_double), ctypes.c_int32, _P(ctypes.c_int64)]),
+    "cfpq_batch_last_profile": (ctypes.c_int, [_P(ctypes.c_double), ctypes.c_int32, _P(ctypes.c_int64),
+                                               _P(ctypes.c_double), ctypes.c_int32]),
     "cfpq_server_options_default": (ctypes.c_int, [_P(ServerOptions)]),
     "cfpq_server_create": (ctypes.c_int, [_P(ServerOptions), _P(_VP)]),
     "cfpq_server_submit": (ctypes.c_int, [_VP, _P(GrammarCNF), ctypes.c_uint32, _P(Edge), ctypes.c_size_t,
@@ -438,14 +439,18 @@ def autotune_batch(queries, stream=None):
     return best, {"trials": rep.trials, "default_ms": rep.default_ms, "best_ms": rep.best_ms}
 
 
-BATCH_PHASES = ("start", "products", "jacobi_merge", "delta_clear", "tails", "tables")
+BATCH_PHASES = ("start", "scan", "products", "jacobi_merge", "tails", "tables")
+BATCH_PROFILE_ROUNDS = 64
 
 
 def batch_last_profile() -> dict:
     """Per-phase device time (ms) and round count of the last batched launch."""
     arr = (ctypes.c_double * len(BATCH_PHASES))()
+    per_round = (ctypes.c_double * BATCH_PROFILE_ROUNDS)()
     rounds = ctypes.c_int64()
-    _check(_lib().cfpq_batch_last_profile(arr, len(BATCH_PHASES), ctypes.byref(rounds)), "cfpq_batch_last_profile")
+    _check(_lib().cfpq_batch_last_profile(arr, len(BATCH_PHASES), ctypes.byref(rounds), per_round,
+                                          BATCH_PROFILE_ROUNDS), "cfpq_batch_last_profile")
     out = {name: arr[i] for i, name in enumerate(BATCH_PHASES)}
     out["rounds"] = int(rounds.value)
+    out["round_products"] = [per_round[i] for i in range(min(out["rounds"], BATCH_PROFILE_ROUNDS))]
     return out

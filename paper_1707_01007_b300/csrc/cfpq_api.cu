@@ -54,7 +54,7 @@ __global__ void k_clear(const QDesc *qd) {
 }
 
 __global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle) {
-    const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x);
+    const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x, true);
     if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, cont);
 }
 

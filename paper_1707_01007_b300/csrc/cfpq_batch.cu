@@ -116,6 +116,7 @@ __device__ void build_tables(BatchCtl *ctl, const BatchQuery *bq, int round) {
         }
     if (threadIdx.x == blockDim.x - 1) {
         ctl->n_active = (unsigned)A;
+        ctl->list_len = 0;  // every reader of the previous list has passed a barrier since
         ctl->prod_off[A] = P;
         ctl->row_off[A] = R;
     }
@@ -138,6 +139,17 @@ __device__ __forceinline__ int find_query(const BatchQuery *bq, int k, unsigned 
 
 __device__ __forceinline__ void zero_span(uint4 *p, unsigned long long lo, unsigned long long hi, int lane) {
     for (unsigned long long w = lo + lane; w < hi; w += 32) p[w] = make_uint4(0, 0, 0, 0);
+}
+
+// Product item: query j (24 bits), group g (8), row i (20), column chunk ch (12).
+__device__ __forceinline__ unsigned long long pack_item(int j, int g, uint32_t i, uint32_t ch) {
+    return ((unsigned long long)j << 40) | ((unsigned long long)g << 32) | ((unsigned long long)i << 12) | ch;
+}
+__device__ __forceinline__ void unpack_item(unsigned long long v, int *j, int *g, uint32_t *i, uint32_t *ch) {
+    *j = (int)(v >> 40);
+    *g = (int)((v >> 32) & 0xFFu);
+    *i = (uint32_t)((v >> 12) & 0xFFFFFu);
+    *ch = (uint32_t)(v & 0xFFFu);
 }
 
 // Rows (of the 32 in row word wq) of a query that has n rows: mask of rows that exist.
@@ -199,22 +211,24 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
     if (!grid_barrier(ctl)) return;
     // phase clock (block 0, thread 0): time from the previous barrier to this one
     unsigned long long t_prev = 0;
-    auto mark = [&](int phase) {
+    auto mark = [&](int phase, int round) {
         if (gtid == 0) {
             const unsigned long long t = globaltimer_ns();
-            ctl->phase_ns[phase] += t - (phase == 0 ? ctl->start_ns : t_prev);
+            const unsigned long long d = t - (phase == 0 ? ctl->start_ns : t_prev);
+            ctl->phase_ns[phase] += d;
+            if (phase == 2 && round < kProfRounds) ctl->round_product_ns[round] = d;
             t_prev = t;
         }
     };
-    mark(0);
+    mark(0, 0);
 
     for (int round = 0; round < ctl->max_rounds; round++) {
         const int na = min((int)ld_u32(&ctl->n_active), k);
         if (na <= 0) break;
         if (gtid == 0) ctl->rounds++;
-        // 3) products of every active query: item = (group, row word, column chunk); the
-        //    warp visits the rows of its word that have a left delta row or, where the right
-        //    operand has a delta, a non-empty left row
+        // 3a) candidate rows: item = (query, group, row word); the warp lists, for each row
+        //     of its word that has a left delta row or (where the right operand has a delta)
+        //     a non-empty left row, one product item per column chunk
         const unsigned long long np = __ldcg(ctl->prod_off + na);
         for (unsigned long long it = gwarp; it < np; it += gwarps) {
             const int s = find_slot(ctl->prod_off, na, it);
@@ -224,11 +238,9 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
             const QDesc &q = b.q;
             const uint32_t rw = (q.n + 31u) / 32u;
             const unsigned long long loc = it - __ldcg(ctl->prod_off + s);
-            const unsigned long long per_group = (unsigned long long)rw * b.nch;
-            const unsigned long long g64 = loc / per_group;
-            const unsigned long long r = loc % per_group;
-            const uint32_t wq = (uint32_t)(r / b.nch), ch = (uint32_t)(r % b.nch);
-            if (g64 >= (unsigned long long)q.n_groups || wq >= rw) continue;
+            const unsigned long long g64 = loc / rw;
+            const uint32_t wq = (uint32_t)(loc % rw);
+            if (g64 >= (unsigned long long)q.n_groups) continue;
             const int g = (int)g64;
             const uint32_t parity = (uint32_t)(ld_u64(&q.st->iter) & 1ull);
             const uint32_t *DR = parity ? q.R1 : q.R0;
@@ -239,20 +251,66 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
                 if (ld_u64(&q.st->dcount[parity][C]) != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
             }
             cand &= rows_in_word(q.n, wq);
-            while (cand) {
-                const uint32_t i = wq * 32u + (uint32_t)(__ffs(cand) - 1);
-                cand &= cand - 1;
-                switch (b.cpl) {
-                    case 1: gather_row_chunk<1>(q, g, i, ch, lane, parity); break;
-                    case 2: gather_row_chunk<2>(q, g, i, ch, lane, parity); break;
-                    case 4: gather_row_chunk<4>(q, g, i, ch, lane, parity); break;
-                    default: gather_row_chunk<8>(q, g, i, ch, lane, parity); break;
-                }
+            if (!cand) continue;
+            const unsigned n_emit = (unsigned)__popc(cand) * b.nch;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ctl->list_len, (unsigned long long)n_emit);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + n_emit > ctl->list_cap) {  // cannot happen: the capacity covers every row
+                if (lane == 0) atomicExch(&ctl->error, 3u);
+                continue;
+            }
+            for (unsigned e = lane; e < n_emit; e += 32) {
+                const unsigned r = e / b.nch, ch = e % b.nch;
+                const uint32_t i = wq * 32u + (uint32_t)(__fns(cand, 0, (int)r + 1));
+                ctl->list[base + e] = pack_item(j, g, i, ch);
+            }
+        }
+        // the plane this round's products write (N) is the one the previous round read (its
+        // D): clear the rows its bitmap flags, then the bitmap (item = non-terminal, row word)
+        const unsigned long long nr = __ldcg(ctl->row_off + na);
+        for (unsigned long long it = gwarp; it < nr; it += gwarps) {
+            const int s = find_slot(ctl->row_off, na, it);
+            const int j = __ldcg(ctl->act + s);
+            if (j < 0 || j >= k) continue;
+            const BatchQuery &b = bq[j];
+            const unsigned long long loc = it - __ldcg(ctl->row_off + s);
+            if (loc >= b.row_items) continue;
+            const uint32_t rw = (b.q.n + 31u) / 32u;
+            const int a = (int)(loc / rw);
+            const uint32_t wq = (uint32_t)(loc % rw);
+            const uint32_t prev = (uint32_t)((ld_u64(&b.q.st->iter) + 1ull) & 1ull);
+            uint32_t *bm = (prev ? b.q.R1 : b.q.R0) + (uint64_t)a * b.q.W + wq;
+            const uint32_t word = __ldcg(bm);
+            uint32_t rows = word & rows_in_word(b.q.n, wq);
+            while (rows) {
+                const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+                rows &= rows - 1;
+                clear_row(b.q, a, i, lane, prev);
+            }
+            if (word && lane == 0) *bm = 0u;
+        }
+        if (!grid_barrier(ctl)) return;
+        mark(1, round);
+        // 3b) products of the listed items (one warp per row chunk)
+        const unsigned long long nl = min(__ldcg(&ctl->list_len), ctl->list_cap);
+        for (unsigned long long it = gwarp; it < nl; it += gwarps) {
+            int j, g;
+            uint32_t i, ch;
+            unpack_item(__ldcg(ctl->list + it), &j, &g, &i, &ch);
+            if (j >= k) continue;
+            const BatchQuery &b = bq[j];
+            if (g >= b.q.n_groups || i >= b.q.n || ch >= b.nch) continue;
+            const uint32_t parity = (uint32_t)(ld_u64(&b.q.st->iter) & 1ull);
+            switch (b.cpl) {
+                case 1: gather_row_chunk<1>(b.q, g, i, ch, lane, parity); break;
+                case 2: gather_row_chunk<2>(b.q, g, i, ch, lane, parity); break;
+                case 4: gather_row_chunk<4>(b.q, g, i, ch, lane, parity); break;
+                default: gather_row_chunk<8>(b.q, g, i, ch, lane, parity); break;
             }
         }
         if (!grid_barrier(ctl)) return;
-        mark(1);
-        const unsigned long long nr = __ldcg(ctl->row_off + na);
+        mark(2, round);
         // 4) Jacobi queries: T |= N (item = non-terminal, row word: the rows N touched)
         if (ctl->any_jacobi) {
             for (unsigned long long it = gwarp; it < nr; it += gwarps) {
@@ -275,34 +333,13 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
                 }
             }
             if (!grid_barrier(ctl)) return;
-            mark(2);
+            mark(3, round);
         }
-        // 5) clear the delta plane that was read (item = non-terminal, row word)
-        for (unsigned long long it = gwarp; it < nr; it += gwarps) {
-            const int s = find_slot(ctl->row_off, na, it);
-            const int j = __ldcg(ctl->act + s);
-            if (j < 0 || j >= k) continue;
-            const BatchQuery &b = bq[j];
-            const unsigned long long loc = it - __ldcg(ctl->row_off + s);
-            if (loc >= b.row_items) continue;
-            const uint32_t rw = (b.q.n + 31u) / 32u;
-            const int a = (int)(loc / rw);
-            const uint32_t wq = (uint32_t)(loc % rw);
-            const uint32_t parity = (uint32_t)(ld_u64(&b.q.st->iter) & 1ull);
-            uint32_t rows = __ldcg((parity ? b.q.R1 : b.q.R0) + (uint64_t)a * b.q.W + wq) & rows_in_word(b.q.n, wq);
-            while (rows) {
-                const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
-                rows &= rows - 1;
-                clear_row(b.q, a, i, lane, parity);
-            }
-        }
-        if (!grid_barrier(ctl)) return;
-        mark(3);
         // 6) per-query end of iteration; a converged query is retired
         for (int s = blockIdx.x; s < na; s += gridDim.x) {
             const int j = __ldcg(ctl->act + s);
             if (j < 0 || j >= k) continue;  // uniform across the block
-            const unsigned cont = tail_query(bq[j].q, threadIdx.x, blockDim.x);
+            const unsigned cont = tail_query(bq[j].q, threadIdx.x, blockDim.x, false);
             if (threadIdx.x == 0) {
                 bq[j].q.st->gather_products += (unsigned long long)bq[j].q.n_rules;
                 if (!cont) ctl->active[j] = 0;
@@ -311,7 +348,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
         }
         // every tail must be done (it reads act[] and writes active[]) before the tables change
         if (!grid_barrier(ctl)) return;
-        mark(4);
+        mark(4, round);
         if (blockIdx.x == 0) {
             build_tables(ctl, bq, round + 1);
             if (threadIdx.x == 0 && ctl->limit_ns && globaltimer_ns() - ctl->start_ns > ctl->limit_ns)
@@ -319,7 +356,7 @@ __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *
             __syncthreads();
         }
         if (!grid_barrier(ctl)) return;
-        mark(5);
+        mark(5, round);
     }
 }
 
@@ -385,7 +422,8 @@ void fill_batch_query(const cfpq_ctx *c, BatchQuery *b, int init, const cfpq_bat
     b->nch = nch;
     if (c->schedule_req == CFPQ_SCHED_AUTO) b->q.schedule = t.schedule[cls];
     const unsigned long long rw = (c->n + 31u) / 32u;  // row words: 32 rows per work item
-    b->prod_items = (unsigned long long)c->n_groups * rw * nch;
+    b->prod_items = (unsigned long long)c->n_groups * rw;
+    b->row_slots = (unsigned long long)c->n_groups * c->n * nch;
     b->row_items = (unsigned long long)c->n_nt * rw;
     b->init = init;
     b->max_iter = c->max_iter;
@@ -432,6 +470,21 @@ int batch_buffers_upload(BatchBuffers *b, BatchQuery *hb, const int *active, int
     }
     ctl.clr_total = clr;
     ctl.seed_total = seed;
+    unsigned long long slots = 0;
+    for (int j = 0; j < k; j++) slots += hb[j].row_slots;
+    if (slots > b->list_cap) {
+        const unsigned long long cap = std::max(slots, 2 * b->list_cap);
+        if (b->list) cudaFree(b->list);
+        b->list = nullptr;
+        b->list_cap = 0;
+        if (cudaMalloc(&b->list, cap * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return CFPQ_ERR_NOMEM;
+        }
+        b->list_cap = cap;
+    }
+    ctl.list = b->list;
+    ctl.list_cap = b->list_cap;
     ctl.k = k;
     ctl.max_rounds = max_rounds;
     ctl.any_jacobi = any_jacobi ? 1 : 0;
@@ -461,7 +514,7 @@ int batch_collect_states(const BatchBuffers *b, const BatchQuery *d_bq, int k, c
 }
 
 static std::mutex g_prof_mu;
-static unsigned long long g_prof_ns[kBatchPhases], g_prof_rounds;
+static unsigned long long g_prof_ns[kBatchPhases], g_prof_rounds, g_prof_round_ns[kProfRounds];
 
 void batch_record_profile(const BatchBuffers *b, cudaStream_t s) {
     BatchCtl ctl;
@@ -470,11 +523,12 @@ void batch_record_profile(const BatchBuffers *b, cudaStream_t s) {
         return;
     std::lock_guard<std::mutex> lock(g_prof_mu);
     memcpy(g_prof_ns, ctl.phase_ns, sizeof(g_prof_ns));
+    memcpy(g_prof_round_ns, ctl.round_product_ns, sizeof(g_prof_round_ns));
     g_prof_rounds = ctl.rounds;
 }
 
 void batch_buffers_free(BatchBuffers *b) {
-    void *ptrs[] = {b->ctl, b->bq, b->active, b->act, b->prod_off, b->row_off, b->states};
+    void *ptrs[] = {b->ctl, b->bq, b->active, b->act, b->prod_off, b->row_off, b->states, b->list};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     memset(b, 0, sizeof(*b));
@@ -562,7 +616,7 @@ static int solve_batch_with(cfpq_ctx *const *ctxs, int k, cudaStream_t s, const 
 }
 
 static int check_batch_args(cfpq_ctx *const *ctxs, int32_t k) {
-    if (!ctxs || k <= 0) return CFPQ_ERR_INVALID;
+    if (!ctxs || k <= 0 || k > kMaxBatch) return CFPQ_ERR_INVALID;
     for (int j = 0; j < k; j++)
         if (!ctxs[j]) return CFPQ_ERR_INVALID;
     return CFPQ_OK;
@@ -688,10 +742,14 @@ extern "C" int cfpq_autotune_batch(cfpq_ctx *const *ctxs, int32_t k, void *strea
     return CFPQ_OK;
 }
 
-extern "C" int cfpq_batch_last_profile(double *phase_ms, int32_t n_phases, int64_t *rounds) {
+extern "C" int cfpq_batch_last_profile(double *phase_ms, int32_t n_phases, int64_t *rounds,
+                                       double *round_product_ms, int32_t n_round_slots) {
     if ((!phase_ms && n_phases > 0) || n_phases < 0) return CFPQ_ERR_INVALID;
+    if ((!round_product_ms && n_round_slots > 0) || n_round_slots < 0) return CFPQ_ERR_INVALID;
     std::lock_guard<std::mutex> lock(g_prof_mu);
     for (int i = 0; i < n_phases; i++) phase_ms[i] = i < kBatchPhases ? (double)g_prof_ns[i] * 1e-6 : 0.0;
+    for (int i = 0; i < n_round_slots; i++)
+        round_product_ms[i] = (i < kProfRounds && (uint64_t)i < g_prof_rounds) ? (double)g_prof_round_ns[i] * 1e-6 : 0.0;
     if (rounds) *rounds = (int64_t)g_prof_rounds;
     return CFPQ_OK;
 }

@@ -5,10 +5,13 @@
 namespace cfpq {
 
 constexpr int kBatchPhases = 6;
+constexpr int kMaxBatch = 1 << 24;  // queries per launch (product items carry a 24-bit index)
+constexpr int kProfRounds = CFPQ_BATCH_PROFILE_ROUNDS;
 
 struct BatchQuery {
     QDesc q;                          // copy of the query's descriptor
-    unsigned long long prod_items;    // warps of one product round: groups * n * chunks
+    unsigned long long prod_items;    // candidate-scan items of one round: groups * row words
+    unsigned long long row_slots;     // most (group, row, chunk) product items one round can list
     unsigned long long row_items;     // warps of one clear / merge pass: n_nt * n
     int cpl;                          // words per lane of the gather accumulator
     uint32_t nch;                     // column chunks per row
@@ -26,6 +29,8 @@ struct BatchCtl {
     unsigned bar_count, bar_spare, error, n_active;   // bar_count: grid barrier (top bit flips per barrier)
     int k, max_rounds, any_jacobi, pad;
     unsigned long long clr_total, seed_total;  // chunks of the two start phases
+    unsigned long long *list;         // product items of the current round (packed, see pack_item)
+    unsigned long long list_cap, list_len;
     unsigned long long limit_ns;      // whole-launch wall-clock limit (0 = none)
     unsigned long long start_ns;      // %globaltimer at launch start (set by the kernel)
     int *active;                      // [k] 1 while the query has not converged
@@ -33,10 +38,12 @@ struct BatchCtl {
     unsigned long long *prod_off;     // [k+1] prefix sums of prod_items over act
     unsigned long long *row_off;      // [k+1] prefix sums of row_items over act
     // device time per phase, summed over rounds (block 0 reads %globaltimer after each
-    // barrier): 0 start (clear, seed, first tables), 1 products, 2 Jacobi merge, 3 delta
-    // clear, 4 per-query tails, 5 table rebuild; and the rounds run
+    // barrier): 0 start (clear, seed, first tables), 1 scan (candidate rows, clear of the
+    // previous delta), 2 products, 3 Jacobi merge, 4 per-query tails, 5 table rebuild;
+    // and the rounds run
     unsigned long long phase_ns[kBatchPhases];
     unsigned long long rounds;
+    unsigned long long round_product_ns[kProfRounds];  // products phase of rounds 0 .. kProfRounds-1
 };
 
 struct BatchBuffers {
@@ -46,6 +53,8 @@ struct BatchBuffers {
     int *active, *act;
     unsigned long long *prod_off, *row_off;
     DevState *states;                 // [k] copies of the queries' states after a launch
+    unsigned long long *list;         // product item list, list_cap entries
+    unsigned long long list_cap;
 };
 
 int batch_buffers_alloc(BatchBuffers *b, int k);

@@ -117,26 +117,46 @@ __device__ inline void seed_query(const QDesc &q, uint64_t tid, uint64_t nthread
 // bits of the left operand's row ("AND" = the bit test, "OR" = the accumulation). The
 // OR-merge into T_A and the change detection are fused at the end.
 // ------------------------------------------------------------------------------------
+// Rows gathered per step: the loads of kGatherU rows are issued before any of them is
+// OR-ed in, so a warp keeps kGatherU row reads in flight instead of one.
+constexpr int kGatherU = 4;
+
 template <int CPL>
 __device__ __forceinline__ void or_rows_for_bits(uint32_t (&acc)[CPL], uint32_t bw, uint32_t w0,
                                                  const uint32_t *__restrict__ rhs_plane, uint32_t W,
                                                  uint32_t base, int lane, unsigned &rows) {
     unsigned nz = __ballot_sync(0xffffffffu, bw != 0);
     rows += __popc(bw);
-    while (nz) {
-        const int src = __ffs(nz) - 1;
-        nz &= nz - 1;
-        uint32_t bits = __shfl_sync(0xffffffffu, bw, src);
-        while (bits) {
-            const uint32_t k = (w0 + src) * 32u + (uint32_t)(__ffs(bits) - 1);
-            bits &= bits - 1;
-            const uint32_t *row = rhs_plane + (uint64_t)k * W + base;
+    uint32_t bits = 0, kb = 0;  // set bits of the current left word (warp-uniform) and its first column
+    while (nz || bits) {
+        const uint32_t *r[kGatherU];
+#pragma unroll
+        for (int u = 0; u < kGatherU; u++) {
+            if (!bits && nz) {  // warp-uniform: refill from the next non-zero word of the block
+                const int src = __ffs(nz) - 1;
+                nz &= nz - 1;
+                bits = __shfl_sync(0xffffffffu, bw, src);
+                kb = (w0 + src) * 32u;
+            }
+            r[u] = nullptr;
+            if (bits) {
+                const uint32_t k = kb + (uint32_t)(__ffs(bits) - 1);
+                bits &= bits - 1;
+                r[u] = rhs_plane + (uint64_t)k * W + base;
+            }
+        }
+        uint32_t v[kGatherU][CPL];
+#pragma unroll
+        for (int u = 0; u < kGatherU; u++)
 #pragma unroll
             for (int c = 0; c < CPL; c++) {
                 const uint32_t col = base + lane + 32 * c;
-                if (col < W) acc[c] |= __ldcg(row + lane + 32 * c);
+                v[u][c] = (r[u] && col < W) ? __ldcg(r[u] + lane + 32 * c) : 0u;
             }
-        }
+#pragma unroll
+        for (int u = 0; u < kGatherU; u++)
+#pragma unroll
+            for (int c = 0; c < CPL; c++) acc[c] |= v[u][c];
     }
 }
 
@@ -249,15 +269,17 @@ __device__ inline void clear_row(const QDesc &q, int a, uint32_t i, int lane, ui
     for (uint32_t w = lane; w < W; w += 32) row[w] = 0u;
 }
 
-// End of one loop execution (one block): clears the old delta's row bitmaps, counts the
-// iteration and decides whether the loop continues. Returns the loop condition (valid
-// in thread 0).
-__device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads) {
+// End of one loop execution (one block): clears the old delta's row bitmaps (unless the
+// caller clears them later, together with the rows they flag), counts the iteration and
+// decides whether the loop continues. Returns the loop condition (valid in thread 0).
+__device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, bool zero_read_bitmap) {
     DevState *st = q.st;
     const unsigned long long it = ld_u64(&st->iter);
     const uint32_t old = (uint32_t)(it & 1ull);
-    uint32_t *DR = old ? q.R1 : q.R0;
-    for (uint64_t w = tid; w < (uint64_t)q.n_nt * q.W; w += nthreads) DR[w] = 0u;
+    if (zero_read_bitmap) {
+        uint32_t *DR = old ? q.R1 : q.R0;
+        for (uint64_t w = tid; w < (uint64_t)q.n_nt * q.W; w += nthreads) DR[w] = 0u;
+    }
     __syncthreads();
     unsigned cont = 0;
     if (tid == 0) {

@@ -92,7 +92,7 @@ extern "C" int cfpq_server_create(const cfpq_server_options *opt, cfpq_server **
     cfpq_server_options o;
     cfpq_server_options_default(&o);
     if (opt) o = *opt;
-    if (o.rounds_per_step < 0 || o.max_resident < 0) return CFPQ_ERR_INVALID;
+    if (o.rounds_per_step < 0 || o.max_resident < 0 || o.max_resident > kMaxBatch) return CFPQ_ERR_INVALID;
     cfpq_server *s = new (std::nothrow) cfpq_server();
     if (!s) return CFPQ_ERR_NOMEM;
     s->rounds = o.rounds_per_step ? o.rounds_per_step : 8;

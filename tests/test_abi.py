@@ -145,7 +145,8 @@ def test_batch_tuning_host_calls():
 
 def test_batch_profile_host_call():
     lib = eng.library()
-    assert lib.cfpq_batch_last_profile(None, 3, None) == eng.ERR_INVALID
-    assert lib.cfpq_batch_last_profile(None, 0, None) == eng.OK
+    assert lib.cfpq_batch_last_profile(None, 3, None, None, 0) == eng.ERR_INVALID
+    assert lib.cfpq_batch_last_profile(None, 0, None, None, 2) == eng.ERR_INVALID
+    assert lib.cfpq_batch_last_profile(None, 0, None, None, 0) == eng.OK
     p = eng.batch_last_profile()
     assert list(p)[:len(eng.BATCH_PHASES)] == list(eng.BATCH_PHASES) and p["rounds"] >= 0

@@ -73,8 +73,9 @@ def test_auto_schedule_and_tile_follow_the_class_entry():
     assert (st["schedule"], st["gather_cpl"], st["iterations"]) == (eng.SCHED_JACOBI, 4, 2 * 5 * 4 + 1)
     prof = eng.batch_last_profile()
     assert prof["rounds"] == 2 * 5 * 4 + 1      # one round per loop execution of the only query
-    assert prof["products"] > 0 and prof["jacobi_merge"] > 0 and prof["start"] > 0
+    assert prof["products"] > 0 and prof["scan"] > 0 and prof["jacobi_merge"] > 0 and prof["start"] > 0
     assert sum(prof[k] for k in eng.BATCH_PHASES) <= st["solve_ms"] * 1.01
+    assert len(prof["round_products"]) == 41 and abs(sum(prof["round_products"]) - prof["products"]) < 1e-3
     t.schedule[3] = eng.SCHED_INPLACE
     t.cpl[3] = 0                          # built-in: one word per lane for W <= 32
     eng.solve_batch([q], tuning=t)
