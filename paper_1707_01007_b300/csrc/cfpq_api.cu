@@ -53,6 +53,53 @@ __global__ void k_clear(const QDesc *qd) {
     clear_row(q, (int)(warp / q.n), (uint32_t)(warp % q.n), lane, (uint32_t)(q.st->iter & 1ull));
 }
 
+// AUTO path, start of a loop execution (one thread): for every production group, the cheaper
+// of the two product kinds by a cost model on the device-side counts, and which group
+// refreshes each transpose that a tensor product will read. Gather cost: one right-operand
+// row (W words) per bit of D_B, plus, where the right operand has a delta, a scan of the
+// non-empty rows of T_B (2W words each) and one D_C row per bit of T_B that meets a
+// non-empty row of D_C (expected |T_B| * min(1, |D_C| / n)). Tensor cost: 2 n_pad^3 Boolean
+// ops per production, plus a transpose per right operand changed since its last refresh.
+constexpr double kTensorOpsPerNs = 2.9e6;     // measured tensor-core Boolean product rate
+constexpr double kGatherBytesPerNs = 600.0;   // measured gather rate (latency-bound)
+constexpr double kTransposeBytesPerNs = 3000.0;
+
+__global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *handles, int use_handles) {
+    const QDesc &q = *qd;
+    DevState *st = q.st;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint32_t p = (uint32_t)(st->iter & 1ull);
+    const double n = (double)q.n, W = (double)q.W, np = (double)q.n_pad;
+    const double per_rule_ns = 2.0 * np * np * np / kTensorOpsPerNs;
+    const double transpose_ns = 2.0 * np * np / 8.0 / kTransposeBytesPerNs;
+    unsigned owner[kMaxNT], any = 0u;
+    for (int a = 0; a < q.n_nt; a++) owner[a] = 0u;
+    for (int g = 0; g < q.n_groups; g++) {
+        const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
+        double words = 0.0, tensor_ns = (double)(r1 - r0) * per_rule_ns;
+        for (int r = r0; r < r1; r++) {
+            const int B = q.rules[r].b, C = q.rules[r].c;
+            const double dB = (double)st->dcount[p][B], dC = (double)st->dcount[p][C], tB = (double)st->tcount[B];
+            words += dB * W;
+            if (dC > 0.0) words += fmin(n, tB) * 2.0 * W + tB * fmin(1.0, dC / n) * W;
+            if (st->dirty[C]) tensor_ns += transpose_ns;
+        }
+        const unsigned use = tensor_ns < words * 4.0 / kGatherBytesPerNs ? 1u : 0u;
+        st->use_tensor[g] = use;
+        if (use)
+            for (int r = r0; r < r1; r++)
+                if (owner[q.rules[r].c] == 0u) owner[q.rules[r].c] = (unsigned)g + 1u;
+        if (use_handles) cudaGraphSetConditional(handles[g], use);
+        any |= use;
+    }
+    if (use_handles) cudaGraphSetConditional(handles[q.n_groups], any);
+    for (int a = 0; a < q.n_nt; a++) {
+        const unsigned now = (owner[a] != 0u && st->dirty[a]) ? owner[a] : 0u;
+        st->tt_now[a] = now;
+        if (now) st->dirty[a] = 0u;
+    }
+}
+
 __global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle) {
     const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x, true);
     if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, cont);
@@ -318,10 +365,97 @@ void launch_gather(cfpq_ctx *c, int g, cudaStream_t s) {
 static uint32_t row_warp_blocks(uint64_t rows) { return (uint32_t)((rows * 32 + 255) / 256); }
 
 // One loop execution (the body of Algorithm 1's while loop).
+// Adds an IF/ELSE node on handle h to the graph that stream s is capturing (after the
+// capture's current dependencies) and makes it the capture's only dependency. The bodies
+// are returned for capturing on another stream.
+static int add_if_else(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *then_g, cudaGraph_t *else_g) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &nd));
+    if (cs != cudaStreamCaptureStatusActive) return CFPQ_ERR_CUDA;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 2;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &p));
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    *then_g = p.conditional.phGraph_out[0];
+    *else_g = p.conditional.phGraph_out[1];
+    return CFPQ_OK;
+}
+
+static int begin_branch(cudaStream_t b, cudaGraph_t body) {
+    CK(cudaStreamBeginCaptureToGraph(b, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    return CFPQ_OK;
+}
+static int end_branch(cudaStream_t b, int rc) {
+    cudaGraph_t unused = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b, &unused);
+    if (rc != CFPQ_OK) return rc;
+    CK(e);
+    return CFPQ_OK;
+}
+
+// AUTO path, one loop execution's products inside a graph capture on s. An IF/ELSE node on
+// "some group chose the tensor product": its ELSE body is every group's gather (the usual
+// case on sparse inputs: one conditional node per execution); its IF body holds one IF/ELSE
+// node per group, tensor product (with its transposes) or gather.
+static int enqueue_auto_products_graph(cfpq_ctx *c, cudaStream_t s) {
+    cudaGraph_t any_then, any_else;
+    int rc = add_if_else(s, c->h_choice[c->n_groups], &any_then, &any_else);
+    if (rc != CFPQ_OK) return rc;
+    if ((rc = begin_branch(c->aux_stream, any_else)) != CFPQ_OK) return rc;
+    for (int g = 0; g < c->n_groups; g++) launch_gather(c, g, c->aux_stream);
+    if ((rc = end_branch(c->aux_stream, CFPQ_OK)) != CFPQ_OK) return rc;
+    if ((rc = begin_branch(c->aux_stream, any_then)) != CFPQ_OK) return rc;
+    for (int g = 0; g < c->n_groups && rc == CFPQ_OK; g++) {
+        cudaGraph_t t, e;
+        rc = add_if_else(c->aux_stream, c->h_choice[g], &t, &e);
+        if (rc != CFPQ_OK) break;
+        if ((rc = begin_branch(c->aux2_stream, t)) != CFPQ_OK) break;
+        int r2 = enqueue_tensor_transposes_gated(c, g, c->aux2_stream);
+        if (r2 == CFPQ_OK) r2 = enqueue_tensor_group(c, g, c->aux2_stream);
+        if ((rc = end_branch(c->aux2_stream, r2)) != CFPQ_OK) break;
+        if ((rc = begin_branch(c->aux2_stream, e)) != CFPQ_OK) break;
+        launch_gather(c, g, c->aux2_stream);
+        rc = end_branch(c->aux2_stream, CFPQ_OK);
+    }
+    return end_branch(c->aux_stream, rc);
+}
+
 int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
     c->iter_launches = 0;
     const bool prof = c->profile && !use_handle;
-    for (int g = 0; g < c->n_groups; g++) {
+    if (c->auto_mixed) {
+        // choose per group, then run the chosen product of each group: in a graph through
+        // conditional nodes; otherwise both kernels are launched and the unchosen one
+        // returns at once
+        k_choose<<<1, 32, 0, s>>>(c->d_q, use_handle ? c->d_choice : nullptr, use_handle);
+        c->iter_launches++;
+        for (int g = 0; g < c->n_groups; g++) {
+            if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
+            if (use_handle) {
+                continue;  // all groups at once below
+            } else {
+                int rc = enqueue_tensor_transposes_gated(c, g, s);
+                if (rc == CFPQ_OK) rc = enqueue_tensor_group(c, g, s);
+                if (rc != CFPQ_OK) return rc;
+                launch_gather(c, g, s);
+            }
+            c->iter_launches++;  // the product that runs
+            if (prof) CK(cudaEventRecord(c->prof_ev[2 * g + 1], s));
+        }
+        if (use_handle) {
+            const int rc = enqueue_auto_products_graph(c, s);
+            if (rc != CFPQ_OK) return rc;
+            c->iter_launches += c->n_groups;  // the product of each group that runs
+        }
+    }
+    for (int g = 0; g < c->n_groups && !c->auto_mixed; g++) {
         if (c->group_tensor[g]) {
             const int rc = enqueue_tensor_transposes(c, g, s);
             if (rc != CFPQ_OK) return rc;
@@ -378,6 +512,25 @@ static int build_graph(cfpq_ctx *c) {
     e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "addnode", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
     cudaGraph_t body = p.conditional.phGraph_out[0];
+    if (c->auto_mixed) {
+        // one IF/ELSE handle per production group, set by k_choose in every loop execution
+        const int prc = tensor_prepare(c);
+        if (prc != CFPQ_OK) { cudaGraphDestroy(g); return prc; }
+        for (cudaStream_t *as : {&c->aux_stream, &c->aux2_stream})
+            if (!*as && (e = cudaStreamCreateWithFlags(as, cudaStreamNonBlocking)) != cudaSuccess) {
+                cudaGraphDestroy(g);
+                note_cuda_error(e, "aux stream", __FILE__, __LINE__);
+                return CFPQ_ERR_CUDA;
+            }
+        c->h_choice.assign(c->n_groups + 1, 0);  // one per group, then "any group chose tensor"
+        for (int k = 0; k <= c->n_groups; k++) {
+            e = cudaGraphConditionalHandleCreate(&c->h_choice[k], g, 0, 0);
+            if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "choice handle", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
+        }
+        e = cudaMemcpy(c->d_choice, c->h_choice.data(), sizeof(cudaGraphConditionalHandle) * (c->n_groups + 1),
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "choice copy", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
+    }
     e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "capture", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
     const int rc = enqueue_iteration(c, c->stream, h, 1);
@@ -411,6 +564,9 @@ void free_ctx_device(cfpq_ctx *c) {
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);
+    if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+    if (c->aux2_stream) cudaStreamDestroy(c->aux2_stream);
+    c->aux_stream = c->aux2_stream = nullptr;
 }
 
 void arm_deadline(cfpq_ctx *c, cudaStream_t s) {
@@ -523,6 +679,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         if (!tensor_path_available()) return CFPQ_ERR_UNSUPPORTED;
         c->group_tensor.assign(std::max(1, c->n_groups), 1);
     }
+    c->auto_mixed = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && tensor_path_available();
 
     if (!c->pooled) {
         CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -554,7 +711,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_counts, cells * sizeof(uint32_t)}, {(void **)&c->d_offsets, cells * sizeof(uint64_t)},
         {(void **)&c->d_block_sums, (kScanMaxBlocks + 1) * sizeof(unsigned long long)},
         {(void **)&c->d_nt_off, (size_t)(c->n_nt + 1) * sizeof(unsigned long long)},
-        {(void **)&c->d_total, sizeof(unsigned long long)}};
+        {(void **)&c->d_total, sizeof(unsigned long long)},
+        {(void **)&c->d_choice, sizeof(cudaGraphConditionalHandle) * (kMaxNT + 1)}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
     {

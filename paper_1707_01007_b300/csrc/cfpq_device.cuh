@@ -36,7 +36,9 @@ struct DevState {
     unsigned int cont;                  // loop condition written by the tail
     unsigned int dirty[kMaxNT];         // T[A] changed since TT[A] was rebuilt
     unsigned long long dcount[2][kMaxNT];  // pairs in X[p][A]
-    unsigned int use_tensor[kMaxNT];    // AUTO path: per group, 1 = tensor product this iteration
+    unsigned int use_tensor[kMaxNT];    // per group, 1 = tensor product this iteration (AUTO: chosen per iteration)
+    unsigned long long tcount[kMaxNT];  // pairs in T[A] (seed + every product's new pairs)
+    unsigned int tt_now[kMaxNT];        // AUTO path: g + 1 if group g refreshes TT[A] this iteration, else 0
     unsigned long long prof_words;      // profile mode: 32-bit words the gather products read or wrote
 };
 
@@ -90,6 +92,7 @@ __device__ __forceinline__ void seed_pair(const QDesc &q, int a, uint32_t i, uin
         atomicOr(&q.R0[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
         atomicOr(&q.Trow[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
         atomicAdd(&q.st->dcount[0][a], 1ull);
+        atomicAdd(&q.st->tcount[a], 1ull);
         (*cnt)++;
     }
 }
@@ -241,6 +244,7 @@ __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint3
         atomicOr(&NR[(uint64_t)A * W + (i >> 5)], 1u << (i & 31));
         if (inplace) atomicOr(&q.Trow[(uint64_t)A * W + (i >> 5)], 1u << (i & 31));
         atomicAdd(&q.st->dcount[parity ^ 1u][A], (unsigned long long)cnt);
+        atomicAdd(&q.st->tcount[A], (unsigned long long)cnt);
         atomicAdd(&q.st->new_bits, (unsigned long long)cnt);
         q.st->changed = 1u;
         q.st->dirty[A] = 1u;

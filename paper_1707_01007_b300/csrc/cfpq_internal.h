@@ -22,6 +22,7 @@ struct cfpq_ctx {
     std::vector<int32_t> gstart;
     std::vector<char> group_tensor;   // per group: 1 = tensor-core product
     std::vector<char> nt_dynamic;     // per non-terminal: 1 = left-hand side of a binary production
+    bool auto_mixed = false;          // AUTO path with tensor cores: product kind chosen per group and iteration
     // device memory
     uint32_t *d_T = nullptr, *d_TT = nullptr, *d_X0 = nullptr, *d_X1 = nullptr;
     uint32_t *d_R0 = nullptr, *d_R1 = nullptr, *d_Trow = nullptr;
@@ -52,6 +53,10 @@ struct cfpq_ctx {
     bool pooled = false;                     // device memory from the stream-ordered pool of `stream`
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t aux_stream = nullptr;       // capture the branches of the AUTO choice nodes
+    cudaStream_t aux2_stream = nullptr;
+    std::vector<cudaGraphConditionalHandle> h_choice;  // per group: IF (tensor) / ELSE (gather); then "any tensor"
+    cudaGraphConditionalHandle *d_choice = nullptr;    // device copy of h_choice (in the arena)
     cudaStream_t last_stream = nullptr;      // stream of the last cfpq_solve (results are read on it)
     int64_t iter_launches = 0;               // kernels one loop execution launches
     int64_t fixed_launches = 0;              // kernels a solve launches outside the loop
@@ -84,6 +89,8 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
 void launch_gather(cfpq_ctx *c, int g, cudaStream_t s);
 void arm_deadline(cfpq_ctx *c, cudaStream_t s);
 int read_status(cfpq_ctx *c, cudaStream_t s);
+int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s);
+int tensor_prepare(cfpq_ctx *c);
 // Statistics and status of a solve from a copy of its device state.
 int apply_status(cfpq_ctx *c, const DevState &st);
 int run_loop(cfpq_ctx *c, cudaStream_t s);

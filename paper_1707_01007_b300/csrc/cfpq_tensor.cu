@@ -356,6 +356,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if (any && lane == 0) {
             atomicAdd(&st->dcount[parity ^ 1u][A], (unsigned long long)cnt);
+            atomicAdd(&st->tcount[A], (unsigned long long)cnt);
             atomicAdd(&st->new_bits, (unsigned long long)cnt);
             st->changed = 1u;
             st->dirty[A] = 1u;
@@ -374,10 +375,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // Bit-matrix transpose of plane a: TT[a] = T[a]^T. One CTA: 256 rows x 8 words (256 x 256 bits).
-__global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a) {
+// gate >= 0 (AUTO path): only if the per-iteration choice assigned this refresh to group gate.
+__global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a, int gate) {
     __shared__ uint32_t in[256][9];
     __shared__ uint32_t out[256][9];
     const QDesc &q = *qd;
+    if (gate >= 0 && q.st->tt_now[a] != (unsigned)gate + 1u) return;
     const uint32_t W = q.W;
     const uint32_t r0 = blockIdx.y * 256, wc0 = blockIdx.x * 8;
     const uint32_t *src = q.T + (uint64_t)a * q.plane;
@@ -478,11 +481,29 @@ void tensor_release(cfpq_ctx *c) {
     c->h_tc_work = nullptr;
 }
 
-static void launch_transpose(cfpq_ctx *c, int a, cudaStream_t s, int64_t *launches) {
+static void launch_transpose(cfpq_ctx *c, int a, cudaStream_t s, int64_t *launches, int gate = -1) {
     const dim3 grid(c->W / 8, c->n_pad / 256);
-    tc::k_transpose<<<grid, 256, 0, s>>>(c->d_q, a);
+    tc::k_transpose<<<grid, 256, 0, s>>>(c->d_q, a, gate);
     (*launches)++;
 }
+
+// AUTO path: transposes of the group's right operands, each run only if this iteration's
+// choice (k_choose) assigned its refresh to group g.
+int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s) {
+    const int rc = tensor_setup(c);
+    if (rc != CFPQ_OK) return rc;
+    std::vector<char> done(c->n_nt, 0);
+    int64_t ignored = 0;
+    for (int r = c->gstart[g]; r < c->gstart[g + 1]; r++) {
+        const int C = c->rules[r].c;
+        if (done[C]) continue;
+        done[C] = 1;
+        launch_transpose(c, C, s, &ignored, g);
+    }
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
+
+int tensor_prepare(cfpq_ctx *c) { return tensor_setup(c); }
 
 // After the matrix initialisation: transposes of every right operand of a tensor group.
 int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launches) {

@@ -1,0 +1,68 @@
+"""AUTO path: each production group takes, in every loop execution, the cheaper of the
+tensor-core product and the CUDA-core gather (chosen on the device). Results equal the
+oracle's; every (production, execution) is computed by exactly one of the two kinds."""
+import numpy as np
+import pytest
+
+import cfpq_synth as synth
+import oracle
+import paper_1707_01007_b300 as eng
+
+pytestmark = pytest.mark.gpu
+
+
+def auto_parity(graph, text, **kw):
+    kw.setdefault("timeout_s", 120.0)
+    g = eng.Grammar(text, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, **kw)
+    q.solve()
+    ref = oracle.hellings(graph, text)
+    for nm in g.names:
+        got, exp = q.get(nm), ref.pairs(nm)
+        assert got.shape == exp.shape and np.array_equal(got, exp), \
+            f"{nm}: engine {got.shape[0]} pairs, oracle {exp.shape[0]}"
+    return g, q, q.stats()
+
+
+def products_each_once(s, text, graph):
+    """tensor + gather products = distinct productions x loop executions (the last one included)."""
+    cnf = eng.Grammar(text, graph.labels).cnf.contents
+    n_bin = len({(cnf.binary[i].lhs, cnf.binary[i].b, cnf.binary[i].c) for i in range(cnf.n_binary)})
+    assert s["tensor_products"] + s["gather_products"] == n_bin * s["iterations"]
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("n", [1100, 2600])
+def test_dense_closure_picks_tensor(n, use_graph):
+    # one dense transitive closure: early executions have large deltas (tensor), the last
+    # ones almost none (gather)
+    graph = synth.random_graph(n, int(1.6 * n), 1, seed=n)
+    _, q, s = auto_parity(graph, "S S S\nS t0\n", use_graph=use_graph)
+    assert s["tensor_products"] > 0
+    products_each_once(s, "S S S\nS t0\n", graph)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_sparse_hierarchy_mixed(use_graph):
+    graph = synth.hierarchy(4096, 1200, seed=4)
+    _, q, s = auto_parity(graph, synth.GRAMMAR_Q1, use_graph=use_graph)
+    products_each_once(s, synth.GRAMMAR_Q1, graph)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("schedule", [eng.SCHED_INPLACE, eng.SCHED_JACOBI])
+def test_random_grammars(seed, schedule):
+    graph = synth.random_graph(150 + 120 * seed, 900 + 700 * seed, 3, seed=seed)
+    text = synth.random_grammar_text(5, 3, 9, 6, seed % 3, seed=seed)
+    _, q, s = auto_parity(graph, text, schedule=schedule)
+    products_each_once(s, text, graph)
+
+
+def test_jacobi_loop_count_matches_algorithm1():
+    # whichever kind computes a product, a Jacobi execution is one application of the
+    # loop body: the loop count is Algorithm 1's
+    graph = synth.random_graph(1500, 2400, 1, seed=3)
+    text = "S S S\nS t0\n"
+    _, q, s = auto_parity(graph, text, schedule=eng.SCHED_JACOBI)
+    _, _, k = oracle.matrix_closure_sparse(graph, text)
+    assert s["iterations"] == k
