@@ -22,35 +22,115 @@ __global__ void k_seed(const QDesc *qd) {
     seed_query(q, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
-template <int CPL>
-__global__ void __launch_bounds__(256) k_gather(const QDesc *qd, int g, uint32_t n_chunks) {
-    const QDesc &q = *qd;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const uint64_t total = (uint64_t)q.n * n_chunks;
-    if (warp == 0 && lane == 0 && q.st->use_tensor[g] == 0)
-        atomicAdd(&q.st->gather_products, (unsigned long long)(q.gstart[g + 1] - q.gstart[g]));
-    if (warp >= total || q.st->use_tensor[g]) return;
-    const uint32_t i = (uint32_t)(warp / n_chunks);
-    const uint32_t ch = (uint32_t)(warp % n_chunks);
-    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
-    gather_row_chunk<CPL>(q, g, i, ch, lane, parity);
+// Product item of the single-query gather list: group (6 bits), column chunk (5), row (17).
+__device__ __forceinline__ uint32_t pack_row_item(int g, uint32_t ch, uint32_t i) {
+    return ((uint32_t)g << 22) | (ch << 17) | i;
 }
 
+// Gather scan (one lane per (group, row word)): the rows of the word that have a left delta
+// row or, where the right operand has a delta, a non-empty left row, become one list item
+// per column chunk. Groups on the tensor cores this execution are skipped.
+__global__ void __launch_bounds__(256) k_scan_rows(const QDesc *qd, uint32_t *list, uint32_t cap, uint32_t nch) {
+    const QDesc &q = *qd;
+    DevState *st = q.st;
+    const uint32_t rw = (q.n + 31u) / 32u;
+    const uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (item == 0)
+        for (int g = 0; g < q.n_groups; g++)
+            if (!st->use_tensor[g]) atomicAdd(&st->gather_products, (unsigned long long)(q.gstart[g + 1] - q.gstart[g]));
+    uint32_t cand = 0, wq = 0;
+    int g = 0;
+    if (item < (uint64_t)q.n_groups * rw) {
+        g = (int)(item / rw);
+        wq = (uint32_t)(item % rw);
+        if (!st->use_tensor[g]) {
+            const uint32_t parity = (uint32_t)(st->iter & 1ull);
+            const uint32_t *DR = parity ? q.R1 : q.R0;
+            for (int r = q.gstart[g]; r < q.gstart[g + 1]; r++) {
+                const int B = q.rules[r].b, C = q.rules[r].c;
+                cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
+                if (st->dcount[parity][C] != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
+            }
+            cand &= rows_in_word(q.n, wq);
+        }
+    }
+    const uint32_t cnt = (uint32_t)__popc(cand) * nch;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t base = 0;
+    if (lane == 31 && wtotal) base = atomicAdd(&st->list_len, wtotal);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    uint32_t pos = base + incl - cnt;
+    if ((uint64_t)pos + cnt > cap) {  // cannot happen: the list holds every (group, row, chunk)
+        if (cnt) atomicExch(&st->error, kErrTimeout);
+        return;
+    }
+    while (cand) {
+        const uint32_t i = wq * 32u + (uint32_t)(__ffs(cand) - 1);
+        cand &= cand - 1;
+        for (uint32_t ch = 0; ch < nch; ch++) list[pos++] = pack_row_item(g, ch, i);
+    }
+}
+
+template <int CPL>
+__global__ void __launch_bounds__(256) k_gather_list(const QDesc *qd, const uint32_t *list, uint32_t cap) {
+    const QDesc &q = *qd;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t len = min(q.st->list_len, cap);
+    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
+    for (uint64_t w = gwarp; w < len; w += gwarps) {
+        const uint32_t e = list[w];
+        gather_row_chunk<CPL>(q, (int)(e >> 22), e & 0x1FFFFu, (e >> 17) & 31u, lane, parity);
+    }
+}
+
+// Jacobi schedule: T |= N over the rows N touched (one warp per non-terminal and row word).
 __global__ void k_merge(const QDesc *qd) {
     const QDesc &q = *qd;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= (uint64_t)q.n_nt * q.n) return;
-    merge_row(q, (int)(warp / q.n), (uint32_t)(warp % q.n), lane, (uint32_t)(q.st->iter & 1ull));
+    const uint32_t rw = (q.n + 31u) / 32u;
+    if (warp >= (uint64_t)q.n_nt * rw) return;
+    const int a = (int)(warp / rw);
+    const uint32_t wq = (uint32_t)(warp % rw);
+    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
+    uint32_t rows = __ldcg((parity ? q.R0 : q.R1) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
+    while (rows) {
+        const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+        rows &= rows - 1;
+        merge_row(q, a, i, lane, parity);
+    }
 }
 
+// Clears the rows of the delta plane read in this execution (one warp per non-terminal and row word).
 __global__ void k_clear(const QDesc *qd) {
     const QDesc &q = *qd;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= (uint64_t)q.n_nt * q.n) return;
-    clear_row(q, (int)(warp / q.n), (uint32_t)(warp % q.n), lane, (uint32_t)(q.st->iter & 1ull));
+    const uint32_t rw = (q.n + 31u) / 32u;
+    if (warp >= (uint64_t)q.n_nt * rw) return;
+    const int a = (int)(warp / rw);
+    const uint32_t wq = (uint32_t)(warp % rw);
+    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
+    uint32_t rows = __ldcg((parity ? q.R1 : q.R0) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
+    while (rows) {
+        const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+        rows &= rows - 1;
+        clear_row(q, a, i, lane, parity);
+    }
+}
+
+__global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle) {
+    const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x, true);
+    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, cont);
 }
 
 // AUTO path, start of a loop execution (one thread): for every production group, the cheaper
@@ -100,10 +180,6 @@ __global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *hand
     }
 }
 
-__global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle) {
-    const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x, true);
-    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, cont);
-}
 
 __global__ void k_arm_deadline(DevState *st, unsigned long long dt_ns) { st->deadline_ns = globaltimer_ns() + dt_ns; }
 
@@ -349,26 +425,31 @@ uint32_t gather_chunks(uint32_t W, int *cpl) {
     return (W + 255) / 256;
 }
 
-void launch_gather(cfpq_ctx *c, int g, cudaStream_t s) {
-    int cpl;
-    const uint32_t nch = gather_chunks(c->W, &cpl);
-    const uint64_t warps = (uint64_t)c->n * nch;
-    const uint32_t blocks = (uint32_t)((warps * 32 + 255) / 256);
-    switch (cpl) {
-        case 1: k_gather<1><<<blocks, 256, 0, s>>>(c->d_q, g, nch); break;
-        case 2: k_gather<2><<<blocks, 256, 0, s>>>(c->d_q, g, nch); break;
-        case 4: k_gather<4><<<blocks, 256, 0, s>>>(c->d_q, g, nch); break;
-        default: k_gather<8><<<blocks, 256, 0, s>>>(c->d_q, g, nch); break;
-    }
-}
-
 static uint32_t row_warp_blocks(uint64_t rows) { return (uint32_t)((rows * 32 + 255) / 256); }
 
-// One loop execution (the body of Algorithm 1's while loop).
-// Adds an IF/ELSE node on handle h to the graph that stream s is capturing (after the
-// capture's current dependencies) and makes it the capture's only dependency. The bodies
-// are returned for capturing on another stream.
-static int add_if_else(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *then_g, cudaGraph_t *else_g) {
+// The gather products of one loop execution, for every group not on the tensor cores: a
+// scan lists the (group, row, column chunk) items that have work, then a persistent grid
+// runs one warp per listed item.
+static int enqueue_gathers(cfpq_ctx *c, cudaStream_t s) {
+    int cpl;
+    const uint32_t nch = gather_chunks(c->W, &cpl);
+    const uint64_t items = (uint64_t)c->n_groups * ((c->n + 31) / 32);
+    k_scan_rows<<<(uint32_t)((items + 255) / 256), 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, nch);
+    const uint32_t grid = (uint32_t)c->gather_grid;
+    switch (cpl) {
+        case 1: k_gather_list<1><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
+        case 2: k_gather_list<2><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
+        case 4: k_gather_list<4><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
+        default: k_gather_list<8><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
+    }
+    c->iter_launches += 2;
+    CK(cudaGetLastError());
+    return CFPQ_OK;
+}
+
+// Adds an IF node on handle h to the graph that stream s is capturing (after the capture's
+// current dependencies), makes it the capture's only dependency and returns its body.
+static int add_if(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *body) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t *deps = nullptr;
@@ -379,12 +460,11 @@ static int add_if_else(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t
     p.type = cudaGraphNodeTypeConditional;
     p.conditional.handle = h;
     p.conditional.type = cudaGraphCondTypeIf;
-    p.conditional.size = 2;
+    p.conditional.size = 1;
     cudaGraphNode_t node;
     CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &p));
     CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-    *then_g = p.conditional.phGraph_out[0];
-    *else_g = p.conditional.phGraph_out[1];
+    *body = p.conditional.phGraph_out[0];
     return CFPQ_OK;
 }
 
@@ -400,98 +480,97 @@ static int end_branch(cudaStream_t b, int rc) {
     return CFPQ_OK;
 }
 
-// AUTO path, one loop execution's products inside a graph capture on s. An IF/ELSE node on
-// "some group chose the tensor product": its ELSE body is every group's gather (the usual
-// case on sparse inputs: one conditional node per execution); its IF body holds one IF/ELSE
-// node per group, tensor product (with its transposes) or gather.
-static int enqueue_auto_products_graph(cfpq_ctx *c, cudaStream_t s) {
-    cudaGraph_t any_then, any_else;
-    int rc = add_if_else(s, c->h_choice[c->n_groups], &any_then, &any_else);
+// AUTO path inside a graph capture on s: the tensor products this execution chose. One IF
+// node on "some group chose the tensor product" (on sparse inputs the only node this adds
+// per execution) holding one IF node per group: its transposes and tensor product.
+static int enqueue_auto_tensor_graph(cfpq_ctx *c, cudaStream_t s) {
+    cudaGraph_t any_body;
+    int rc = add_if(s, c->h_choice[c->n_groups], &any_body);
     if (rc != CFPQ_OK) return rc;
-    if ((rc = begin_branch(c->aux_stream, any_else)) != CFPQ_OK) return rc;
-    for (int g = 0; g < c->n_groups; g++) launch_gather(c, g, c->aux_stream);
-    if ((rc = end_branch(c->aux_stream, CFPQ_OK)) != CFPQ_OK) return rc;
-    if ((rc = begin_branch(c->aux_stream, any_then)) != CFPQ_OK) return rc;
+    if ((rc = begin_branch(c->aux_stream, any_body)) != CFPQ_OK) return rc;
     for (int g = 0; g < c->n_groups && rc == CFPQ_OK; g++) {
-        cudaGraph_t t, e;
-        rc = add_if_else(c->aux_stream, c->h_choice[g], &t, &e);
-        if (rc != CFPQ_OK) break;
-        if ((rc = begin_branch(c->aux2_stream, t)) != CFPQ_OK) break;
+        cudaGraph_t body;
+        if ((rc = add_if(c->aux_stream, c->h_choice[g], &body)) != CFPQ_OK) break;
+        if ((rc = begin_branch(c->aux2_stream, body)) != CFPQ_OK) break;
         int r2 = enqueue_tensor_transposes_gated(c, g, c->aux2_stream);
         if (r2 == CFPQ_OK) r2 = enqueue_tensor_group(c, g, c->aux2_stream);
-        if ((rc = end_branch(c->aux2_stream, r2)) != CFPQ_OK) break;
-        if ((rc = begin_branch(c->aux2_stream, e)) != CFPQ_OK) break;
-        launch_gather(c, g, c->aux2_stream);
-        rc = end_branch(c->aux2_stream, CFPQ_OK);
+        rc = end_branch(c->aux2_stream, r2);
     }
     return end_branch(c->aux_stream, rc);
 }
 
+// One loop execution (the body of Algorithm 1's while loop). In profile mode, CUDA events
+// bracket every tensor-product launch (one pair per group) and the gather products of the
+// execution (one pair).
 int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
     c->iter_launches = 0;
     const bool prof = c->profile && !use_handle;
     if (c->auto_mixed) {
-        // choose per group, then run the chosen product of each group: in a graph through
-        // conditional nodes; otherwise both kernels are launched and the unchosen one
-        // returns at once
+        // choose per group; in a graph the chosen tensor products run under conditional
+        // nodes, otherwise every tensor launch is made and returns at once if not chosen
         k_choose<<<1, 32, 0, s>>>(c->d_q, use_handle ? c->d_choice : nullptr, use_handle);
         c->iter_launches++;
-        for (int g = 0; g < c->n_groups; g++) {
-            if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
-            if (use_handle) {
-                continue;  // all groups at once below
-            } else {
-                int rc = enqueue_tensor_transposes_gated(c, g, s);
-                if (rc == CFPQ_OK) rc = enqueue_tensor_group(c, g, s);
-                if (rc != CFPQ_OK) return rc;
-                launch_gather(c, g, s);
-            }
-            c->iter_launches++;  // the product that runs
-            if (prof) CK(cudaEventRecord(c->prof_ev[2 * g + 1], s));
-        }
         if (use_handle) {
-            const int rc = enqueue_auto_products_graph(c, s);
-            if (rc != CFPQ_OK) return rc;
-            c->iter_launches += c->n_groups;  // the product of each group that runs
-        }
-    }
-    for (int g = 0; g < c->n_groups && !c->auto_mixed; g++) {
-        if (c->group_tensor[g]) {
-            const int rc = enqueue_tensor_transposes(c, g, s);
-            if (rc != CFPQ_OK) return rc;
-        }
-        if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
-        if (c->group_tensor[g]) {
-            const int rc = enqueue_tensor_group(c, g, s);
+            const int rc = enqueue_auto_tensor_graph(c, s);
             if (rc != CFPQ_OK) return rc;
         } else {
-            launch_gather(c, g, s);
-            c->iter_launches++;
+            for (int g = 0; g < c->n_groups; g++) {
+                int rc = enqueue_tensor_transposes_gated(c, g, s);
+                if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
+                if (rc == CFPQ_OK) rc = enqueue_tensor_group(c, g, s);
+                if (prof) CK(cudaEventRecord(c->prof_ev[2 * g + 1], s));
+                if (rc != CFPQ_OK) return rc;
+            }
         }
-        if (prof) CK(cudaEventRecord(c->prof_ev[2 * g + 1], s));
+    } else {
+        for (int g = 0; g < c->n_groups; g++) {
+            if (!c->group_tensor[g]) continue;
+            int rc = enqueue_tensor_transposes(c, g, s);
+            if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
+            if (rc == CFPQ_OK) rc = enqueue_tensor_group(c, g, s);
+            if (prof) CK(cudaEventRecord(c->prof_ev[2 * g + 1], s));
+            if (rc != CFPQ_OK) return rc;
+        }
     }
+    if (c->any_gather) {
+        if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups], s));
+        const int rc = enqueue_gathers(c, s);
+        if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 1], s));
+        if (rc != CFPQ_OK) return rc;
+    }
+    const uint32_t word_blocks = row_warp_blocks((uint64_t)c->n_nt * ((c->n + 31) / 32));
     if (c->schedule == CFPQ_SCHED_JACOBI) {
-        k_merge<<<row_warp_blocks((uint64_t)c->n_nt * c->n), 256, 0, s>>>(c->d_q);
+        k_merge<<<word_blocks, 256, 0, s>>>(c->d_q);
         c->iter_launches++;
     }
-    k_clear<<<row_warp_blocks((uint64_t)c->n_nt * c->n), 256, 0, s>>>(c->d_q);
+    k_clear<<<word_blocks, 256, 0, s>>>(c->d_q);
     k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle);
     c->iter_launches += 2;
     CK(cudaGetLastError());
     return CFPQ_OK;
 }
 
-// profile mode: adds the product launches of the iteration just synchronised
+// profile mode: adds the product launches of the iteration just synchronised. Tensor
+// launches count only where the group ran on the tensor cores (AUTO: this execution's choice).
 static int collect_profile(cfpq_ctx *c) {
+    unsigned used[kMaxNT] = {0};
+    if (c->auto_mixed)
+        CK(cudaMemcpy(used, c->d_state->use_tensor, sizeof(unsigned) * c->n_groups, cudaMemcpyDeviceToHost));
     for (int g = 0; g < c->n_groups; g++) {
+        const bool tensor = c->auto_mixed ? used[g] != 0 : c->group_tensor[g] != 0;
+        if (!tensor) continue;
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * g], c->prof_ev[2 * g + 1]));
         c->stats.product_ms += ms;
         c->stats.product_launches++;
-        if (c->group_tensor[g]) {
-            c->stats.tensor_ms += ms;
-            c->stats.tensor_launches++;
-        }
+        c->stats.tensor_ms += ms;
+        c->stats.tensor_launches++;
+    }
+    if (c->any_gather) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * c->n_groups], c->prof_ev[2 * c->n_groups + 1]));
+        c->stats.product_ms += ms;
+        c->stats.product_launches++;
     }
     return CFPQ_OK;
 }
@@ -680,6 +759,22 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         c->group_tensor.assign(std::max(1, c->n_groups), 1);
     }
     c->auto_mixed = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && tensor_path_available();
+    c->any_gather = c->n_groups > 0 && c->path != CFPQ_PATH_TENSOR && c->path != CFPQ_PATH_WORKLIST;
+    {
+        int cpl;
+        const uint64_t slots = c->any_gather ? (uint64_t)c->n_groups * c->n * gather_chunks(c->W, &cpl) : 0;
+        if (slots > 0xFFFFFFFFull) return CFPQ_ERR_INVALID;
+        c->list_cap = (uint32_t)slots;
+        if (c->any_gather) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const void *fn = cpl == 1 ? (const void *)k_gather_list<1> : cpl == 2 ? (const void *)k_gather_list<2>
+                           : cpl == 4 ? (const void *)k_gather_list<4> : (const void *)k_gather_list<8>;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+            c->gather_grid = std::max(1, sms) * per_sm;
+        }
+    }
 
     if (!c->pooled) {
         CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -689,7 +784,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
     if (c->profile) {
-        c->prof_ev.assign(2 * std::max(1, c->n_groups), nullptr);
+        c->prof_ev.assign(2 * (c->n_groups + 1), nullptr);
         for (auto &e : c->prof_ev) CK(cudaEventCreate(&e));
     }
     // one arena for every buffer of the query (one allocation, one free). The batched
@@ -712,7 +807,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_block_sums, (kScanMaxBlocks + 1) * sizeof(unsigned long long)},
         {(void **)&c->d_nt_off, (size_t)(c->n_nt + 1) * sizeof(unsigned long long)},
         {(void **)&c->d_total, sizeof(unsigned long long)},
-        {(void **)&c->d_choice, sizeof(cudaGraphConditionalHandle) * (kMaxNT + 1)}};
+        {(void **)&c->d_choice, sizeof(cudaGraphConditionalHandle) * (kMaxNT + 1)},
+        {(void **)&c->d_list, (size_t)c->list_cap * sizeof(uint32_t)}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
     {
@@ -775,7 +871,8 @@ size_t query_footprint(uint32_t n, int n_nt, size_t n_edges, int n_rules, bool t
     const size_t plane = n_pad * (n_pad / 32) * 4;
     const size_t planes = (tensor ? 4 : 3) * (size_t)n_nt * plane;
     const size_t rows = 3 * (size_t)n_nt * (n_pad / 8);
-    const size_t misc = n_edges * sizeof(cfpq_edge) + n_pad * 12 + (size_t)n_rules * 32 + 64 * 1024;
+    const size_t list = (size_t)n_rules * n * ((n_pad / 32 + 255) / 256) * 4;  // gather items (at most)
+    const size_t misc = n_edges * sizeof(cfpq_edge) + n_pad * 12 + (size_t)n_rules * 32 + 64 * 1024 + list;
     return planes + rows + misc;
 }
 

@@ -152,11 +152,6 @@ __device__ __forceinline__ void unpack_item(unsigned long long v, int *j, int *g
     *ch = (uint32_t)(v & 0xFFFu);
 }
 
-// Rows (of the 32 in row word wq) of a query that has n rows: mask of rows that exist.
-__device__ __forceinline__ uint32_t rows_in_word(uint32_t n, uint32_t wq) {
-    const uint32_t left = n - wq * 32u;
-    return left >= 32u ? 0xFFFFFFFFu : ((1u << left) - 1u);
-}
 
 __global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *bq) {
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;

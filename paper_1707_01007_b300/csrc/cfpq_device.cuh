@@ -40,6 +40,8 @@ struct DevState {
     unsigned long long tcount[kMaxNT];  // pairs in T[A] (seed + every product's new pairs)
     unsigned int tt_now[kMaxNT];        // AUTO path: g + 1 if group g refreshes TT[A] this iteration, else 0
     unsigned long long prof_words;      // profile mode: 32-bit words the gather products read or wrote
+    unsigned int list_len;              // gather items listed in this loop execution (single-query path)
+    unsigned int pad_list;
 };
 
 struct Rule {
@@ -70,6 +72,12 @@ __device__ __forceinline__ bool test_bit(const uint32_t *bm, uint32_t i) {
 
 __device__ __forceinline__ unsigned long long ld_u64(const unsigned long long *p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned ld_u32(const unsigned *p) { return __ldcg(p); }
+
+// Rows (of the 32 in row word wq) of a query that has n rows: mask of rows that exist.
+__device__ __forceinline__ uint32_t rows_in_word(uint32_t n, uint32_t wq) {
+    const uint32_t left = n - wq * 32u;
+    return left >= 32u ? 0xFFFFFFFFu : ((1u << left) - 1u);
+}
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -288,6 +296,7 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
     unsigned cont = 0;
     if (tid == 0) {
         for (int a = 0; a < q.n_nt; a++) st->dcount[old][a] = 0ull;
+        st->list_len = 0u;
         const unsigned changed = ld_u32(&st->changed);
         st->changed = 0u;
         st->iter = it + 1;

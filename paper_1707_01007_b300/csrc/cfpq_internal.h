@@ -23,6 +23,10 @@ struct cfpq_ctx {
     std::vector<char> group_tensor;   // per group: 1 = tensor-core product
     std::vector<char> nt_dynamic;     // per non-terminal: 1 = left-hand side of a binary production
     bool auto_mixed = false;          // AUTO path with tensor cores: product kind chosen per group and iteration
+    bool any_gather = false;          // some group may take the gather product
+    uint32_t *d_list = nullptr;       // gather items of one loop execution (in the arena)
+    uint32_t list_cap = 0;
+    int gather_grid = 0;              // persistent grid of the listed gathers
     // device memory
     uint32_t *d_T = nullptr, *d_TT = nullptr, *d_X0 = nullptr, *d_X1 = nullptr;
     uint32_t *d_R0 = nullptr, *d_R1 = nullptr, *d_Trow = nullptr;
@@ -86,7 +90,6 @@ size_t query_footprint(uint32_t n, int n_nt, size_t n_edges, int n_rules, bool t
 void free_ctx_device(cfpq_ctx *c);
 int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s);
 int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle);
-void launch_gather(cfpq_ctx *c, int g, cudaStream_t s);
 void arm_deadline(cfpq_ctx *c, cudaStream_t s);
 int read_status(cfpq_ctx *c, cudaStream_t s);
 int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s);
