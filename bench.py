@@ -211,7 +211,7 @@ def roofline(eng, graph, gs, path, schedule, stream):
     launch is 2 n^3 per production of the group (tensor) or the counted words (gather)."""
     peaks, kind = load_peaks()
     prod_ms = prod_l = tens_ms = tens_l = 0
-    flops = bytes_ = 0.0
+    flops = bytes_ = useful = 0.0
     for g in gs:
         q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, profile=True, timeout_s=300.0)
         q.solve(stream)
@@ -222,22 +222,30 @@ def roofline(eng, graph, gs, path, schedule, stream):
         tens_l += s["tensor_launches"]
         flops += s["dense_ops"]
         bytes_ += s["product_bytes"]
+        useful += s["useful_ops"]
         q.close()
     if tens_l > 0 and tens_ms >= 0.5 * prod_ms:
         achieved = flops / (tens_ms / 1e3) / 1e12
         peak = 2.0 * peaks["bf16_tflops"]
         sustained = 2.0 * peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        # the integer tensor references of this device (sm_103a has no 8-bit integer tcgen05 kind)
+        mma = eng.measure_mma_sync_peaks()
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": tc_traffic_per_launch(), "kernel": "k_tc_bool_gemm", "launches": tens_l,
                 "launch_ms": tens_ms / tens_l, "flops_per_launch": flops / tens_l,
                 "peak_note": f"{kind} bf16 dense burst x 2 (fp8 e4m3 : bf16 nominal ratio); "
-                             f"frac against the sustained figure x 2: {achieved / sustained:.3f}"}
+                             f"frac against the sustained figure x 2: {achieved / sustained:.3f}",
+                "useful_ops_per_step": useful,
+                "int_tensor_refs": {"mma_sync_s8_tops": mma["s8_tops"], "frac_of_mma_sync_s8": achieved / mma["s8_tops"],
+                                    "mma_sync_b1_tops": mma["b1_tops"],
+                                    "frac_of_mma_sync_b1": achieved / mma["b1_tops"],
+                                    "note": "measured on this device (cfpq_measure_mma_sync_peaks)"}}
     gather_ms = prod_ms - tens_ms
     launches = max(1, prod_l - tens_l)
     achieved = bytes_ / (gather_ms / 1e3) / 1e9 if gather_ms > 0 else None
     peak = peaks["hbm_gbs"]
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None, "kernel": "k_gather",
+            "frac": (achieved / peak) if achieved else None, "traffic": None, "kernel": "k_scan_rows + k_gather_list",
             "launches": launches, "launch_ms": gather_ms / launches, "bytes_per_launch": bytes_ / launches,
             "peak_note": f"{kind} HBM copy bandwidth"}
 
@@ -386,6 +394,12 @@ def engine_arm(args):
         "roofline": roof,
         "alternatives": alternatives,
     }
+    if roof.get("useful_ops_per_step"):
+        # Boolean ops whose operands are both 1 (sum_k nnz(col k of T_B) nnz(row k of T_C) per
+        # product, counted in profile mode on the same closure), beside the dense count
+        u = roof.pop("useful_ops_per_step")
+        line["useful_work"] = {"ops_per_step": u, "fraction_of_dense": u / ops_per_step,
+                               "gops": world * u / (ms / 1e3) / 1e9}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
         reps = 0

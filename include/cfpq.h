@@ -122,6 +122,8 @@ typedef struct {
     int64_t worklist_items;   /* worklist path: pairs joined with their partners */
     int32_t schedule;         /* schedule the last solve ran (INPLACE or JACOBI; AUTO resolved) */
     int32_t gather_cpl;       /* batched solves: gather tile width used (32-bit words per lane) */
+    double useful_ops;        /* profile mode: 2 x sum over tensor products of sum_k nnz(column k
+                                 of T_B) nnz(row k of T_C), the Boolean ops with both operands 1 */
 } cfpq_stats;
 
 typedef struct cfpq_ctx cfpq_ctx;
@@ -265,6 +267,16 @@ int cfpq_batch_tuning_set(const cfpq_batch_tuning *t);
  */
 int cfpq_autotune_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream, cfpq_batch_tuning *best,
                         cfpq_tune_report *report);
+/*
+ * Measured throughput of the warp-level integer tensor instructions on this device, in
+ * tera-ops/s (2 ops per multiply-add): mma.sync m16n8k32 s8 x s8 -> s32 and m16n8k256
+ * b1 AND/popc -> s32. On sm_103a these are the only 8-bit integer and 1-bit tensor paths
+ * (tcgen05 has no 8-bit integer kind there); the Boolean product's rate is also reported
+ * against them. Runs two timed launches of a few tens of ms on the current device; not
+ * part of any solve. Errors: INVALID (NULL output), NOMEM, CUDA.
+ */
+int cfpq_measure_mma_sync_peaks(double *s8_tops, double *b1_tops);
+
 /* Batched solve under an explicit configuration instead of the installed one. */
 int cfpq_solve_batch_tuned(cfpq_ctx *const *ctxs, int32_t k, const cfpq_batch_tuning *t, void *stream);
 /*

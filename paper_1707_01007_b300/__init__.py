@@ -68,7 +68,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("product_launches", ctypes.c_int64),
                 ("product_ms", ctypes.c_double), ("tensor_ms", ctypes.c_double),
                 ("tensor_launches", ctypes.c_int64), ("product_bytes", ctypes.c_double),
-                ("worklist_items", ctypes.c_int64), ("schedule", ctypes.c_int32), ("gather_cpl", ctypes.c_int32)]
+                ("worklist_items", ctypes.c_int64), ("schedule", ctypes.c_int32), ("gather_cpl", ctypes.c_int32),
+                ("useful_ops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -138,6 +139,7 @@ SIGNATURES = {
     "cfpq_batch_tuning_set": (ctypes.c_int, [_P(BatchTuning)]),
     "cfpq_autotune_batch": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP, _P(BatchTuning), _P(TuneReport)]),
     "cfpq_solve_batch_tuned": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _P(BatchTuning), _VP]),
+    "cfpq_measure_mma_sync_peaks": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double)]),
     "cfpq_batch_last_profile": (ctypes.c_int, [_P(ctypes.c_double), ctypes.c_int32, _P(ctypes.c_int64),
                                                _P(ctypes.c_double), ctypes.c_int32]),
     "cfpq_server_options_default": (ctypes.c_int, [_P(ServerOptions)]),
@@ -454,3 +456,10 @@ def batch_last_profile() -> dict:
     out["rounds"] = int(rounds.value)
     out["round_products"] = [per_round[i] for i in range(min(out["rounds"], BATCH_PROFILE_ROUNDS))]
     return out
+
+
+def measure_mma_sync_peaks() -> dict:
+    """Measured mma.sync s8 and b1 (AND/popc) tensor throughput of the current device, TOPS."""
+    s8, b1 = ctypes.c_double(), ctypes.c_double()
+    _check(_lib().cfpq_measure_mma_sync_peaks(ctypes.byref(s8), ctypes.byref(b1)), "cfpq_measure_mma_sync_peaks")
+    return {"s8_tops": s8.value, "b1_tops": b1.value}

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(const QDesc *qd, uint32_t *li
 }
 
 template <int CPL>
-__global__ void __launch_bounds__(256) k_gather_list(const QDesc *qd, const uint32_t *list, uint32_t cap) {
+__global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDesc *qd, const uint32_t *list, uint32_t cap) {
     const QDesc &q = *qd;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -92,39 +92,42 @@ __global__ void __launch_bounds__(256) k_gather_list(const QDesc *qd, const uint
     }
 }
 
-// Jacobi schedule: T |= N over the rows N touched (one warp per non-terminal and row word).
-__global__ void k_merge(const QDesc *qd) {
+// Jacobi schedule: T |= N over the rows N touched. One block per (non-terminal, row word of
+// 32 rows); the block's threads share each flagged row's words.
+__global__ void __launch_bounds__(128) k_merge(const QDesc *qd) {
     const QDesc &q = *qd;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
     const uint32_t rw = (q.n + 31u) / 32u;
-    if (warp >= (uint64_t)q.n_nt * rw) return;
-    const int a = (int)(warp / rw);
-    const uint32_t wq = (uint32_t)(warp % rw);
+    const int a = (int)(blockIdx.x / rw);
+    const uint32_t wq = blockIdx.x % rw;
     const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
     uint32_t rows = __ldcg((parity ? q.R0 : q.R1) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
+    if (rows && threadIdx.x == 0) atomicOr(&q.Trow[(uint64_t)a * q.W + wq], rows);
+    const uint32_t *N = (parity ? q.X0 : q.X1) + (uint64_t)a * q.plane;
+    uint32_t *T = q.T + (uint64_t)a * q.plane;
     while (rows) {
-        const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+        const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
         rows &= rows - 1;
-        merge_row(q, a, i, lane, parity);
+        for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) {
+            const uint32_t nw = __ldcg(N + i * q.W + w);
+            if (nw) T[i * q.W + w] = __ldcg(T + i * q.W + w) | nw;
+        }
     }
 }
 
-// Clears the rows of the delta plane read in this execution (one warp per non-terminal and row word).
-__global__ void k_clear(const QDesc *qd) {
+// Clears the rows of the delta plane read in this execution (one block per non-terminal and
+// row word of 32 rows).
+__global__ void __launch_bounds__(128) k_clear(const QDesc *qd) {
     const QDesc &q = *qd;
-    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
     const uint32_t rw = (q.n + 31u) / 32u;
-    if (warp >= (uint64_t)q.n_nt * rw) return;
-    const int a = (int)(warp / rw);
-    const uint32_t wq = (uint32_t)(warp % rw);
+    const int a = (int)(blockIdx.x / rw);
+    const uint32_t wq = blockIdx.x % rw;
     const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
     uint32_t rows = __ldcg((parity ? q.R1 : q.R0) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
+    uint32_t *D = (parity ? q.X1 : q.X0) + (uint64_t)a * q.plane;
     while (rows) {
-        const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+        const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
         rows &= rows - 1;
-        clear_row(q, a, i, lane, parity);
+        for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) D[i * q.W + w] = 0u;
     }
 }
 
@@ -516,6 +519,7 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         } else {
             for (int g = 0; g < c->n_groups; g++) {
                 int rc = enqueue_tensor_transposes_gated(c, g, s);
+                if (rc == CFPQ_OK && prof) rc = enqueue_useful_work(c, g, s);
                 if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
                 if (rc == CFPQ_OK) rc = enqueue_tensor_group(c, g, s);
                 if (prof) CK(cudaEventRecord(c->prof_ev[2 * g + 1], s));
@@ -526,6 +530,7 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         for (int g = 0; g < c->n_groups; g++) {
             if (!c->group_tensor[g]) continue;
             int rc = enqueue_tensor_transposes(c, g, s);
+            if (rc == CFPQ_OK && prof) rc = enqueue_useful_work(c, g, s);
             if (prof) CK(cudaEventRecord(c->prof_ev[2 * g], s));
             if (rc == CFPQ_OK) rc = enqueue_tensor_group(c, g, s);
             if (prof) CK(cudaEventRecord(c->prof_ev[2 * g + 1], s));
@@ -538,12 +543,12 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 1], s));
         if (rc != CFPQ_OK) return rc;
     }
-    const uint32_t word_blocks = row_warp_blocks((uint64_t)c->n_nt * ((c->n + 31) / 32));
+    const uint32_t word_blocks = (uint32_t)((uint64_t)c->n_nt * ((c->n + 31) / 32));  // one per (A, row word)
     if (c->schedule == CFPQ_SCHED_JACOBI) {
-        k_merge<<<word_blocks, 256, 0, s>>>(c->d_q);
+        k_merge<<<word_blocks, 128, 0, s>>>(c->d_q);
         c->iter_launches++;
     }
-    k_clear<<<word_blocks, 256, 0, s>>>(c->d_q);
+    k_clear<<<word_blocks, 128, 0, s>>>(c->d_q);
     k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle);
     c->iter_launches += 2;
     CK(cudaGetLastError());
@@ -700,6 +705,7 @@ int apply_status(cfpq_ctx *c, const DevState &st) {
     c->stats.n_pad = c->n_pad;
     c->stats.kernel_launches = c->fixed_launches + (int64_t)st.iter * c->iter_launches;
     c->stats.product_bytes = 4.0 * (double)st.prof_words;
+    c->stats.useful_ops = 2.0 * (double)st.useful_macs;
     int rc = CFPQ_OK;
     if (st.error == kErrIterLimit) rc = CFPQ_ERR_ITER_LIMIT;
     else if (st.error == kErrTimeout) rc = CFPQ_ERR_TIMEOUT;
@@ -808,7 +814,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_nt_off, (size_t)(c->n_nt + 1) * sizeof(unsigned long long)},
         {(void **)&c->d_total, sizeof(unsigned long long)},
         {(void **)&c->d_choice, sizeof(cudaGraphConditionalHandle) * (kMaxNT + 1)},
-        {(void **)&c->d_list, (size_t)c->list_cap * sizeof(uint32_t)}};
+        {(void **)&c->d_list, (size_t)c->list_cap * sizeof(uint32_t)},
+        {(void **)&c->d_colcnt, c->profile ? sizeof(uint32_t) * c->n_pad : 0}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
     {

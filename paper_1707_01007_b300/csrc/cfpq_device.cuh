@@ -42,6 +42,7 @@ struct DevState {
     unsigned long long prof_words;      // profile mode: 32-bit words the gather products read or wrote
     unsigned int list_len;              // gather items listed in this loop execution (single-query path)
     unsigned int pad_list;
+    unsigned long long useful_macs;     // profile mode: sum over tensor products of nnz(col k of T_B) nnz(row k of T_C)
 };
 
 struct Rule {

@@ -25,6 +25,7 @@ struct cfpq_ctx {
     bool auto_mixed = false;          // AUTO path with tensor cores: product kind chosen per group and iteration
     bool any_gather = false;          // some group may take the gather product
     uint32_t *d_list = nullptr;       // gather items of one loop execution (in the arena)
+    uint32_t *d_colcnt = nullptr;     // profile mode: column counts of a left operand (n_pad)
     uint32_t list_cap = 0;
     int gather_grid = 0;              // persistent grid of the listed gathers
     // device memory
@@ -93,6 +94,7 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
 void arm_deadline(cfpq_ctx *c, cudaStream_t s);
 int read_status(cfpq_ctx *c, cudaStream_t s);
 int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s);
+int enqueue_useful_work(cfpq_ctx *c, int g, cudaStream_t s);
 int tensor_prepare(cfpq_ctx *c);
 // Statistics and status of a solve from a copy of its device state.
 int apply_status(cfpq_ctx *c, const DevState &st);

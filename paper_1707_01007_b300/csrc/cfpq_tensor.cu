@@ -409,9 +409,49 @@ __global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a, int g
     }
 }
 
+// Profile mode, useful work of one tensor product T_B x T_C: sum over k of the ones in
+// column k of T_B times the ones in row k of T_C (the multiply-adds with both operands 1).
+// Column counts: one thread per column of a 256-column band, over 256 rows per block.
+__global__ void __launch_bounds__(256) k_colcount(const QDesc *qd, int b, uint32_t *colcnt) {
+    const QDesc &q = *qd;
+    const uint32_t w = blockIdx.x * 8u + (threadIdx.x >> 5), bit = threadIdx.x & 31u;
+    const uint32_t r0 = blockIdx.y * 256u;
+    const uint32_t *src = q.T + (uint64_t)b * q.plane;
+    uint32_t cnt = 0;
+    for (uint32_t i = r0; i < r0 + 256u && i < q.n; i++) cnt += (__ldcg(src + (uint64_t)i * q.W + w) >> bit) & 1u;
+    if (cnt) atomicAdd(&colcnt[w * 32u + bit], cnt);
+}
+
+// Row counts of T_C (one warp per row), then the dot product with the column counts.
+__global__ void __launch_bounds__(256) k_useful_dot(const QDesc *qd, int c, int g, const uint32_t *colcnt) {
+    const QDesc &q = *qd;
+    if (q.st->use_tensor[g] == 0) return;  // this product ran on the gather path
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= q.n) return;
+    const uint32_t *row = q.T + (uint64_t)c * q.plane + warp * q.W;
+    uint32_t cnt = 0;
+    for (uint32_t w = lane; w < q.W; w += 32) cnt += __popc(__ldcg(row + w));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0 && cnt) atomicAdd(&q.st->useful_macs, (unsigned long long)cnt * colcnt[warp]);
+}
+
 }  // namespace tc
 
 // ------------------------------------------------------------------------------------ host
+
+// Profile mode: adds the useful multiply-adds of group g's tensor products (at the operands'
+// current contents, which are what the products read) to the device state.
+int enqueue_useful_work(cfpq_ctx *c, int g, cudaStream_t s) {
+    for (int r = c->gstart[g]; r < c->gstart[g + 1]; r++) {
+        if (cudaMemsetAsync(c->d_colcnt, 0, sizeof(uint32_t) * c->n_pad, s) != cudaSuccess) return CFPQ_ERR_CUDA;
+        tc::k_colcount<<<dim3(c->W / 8, c->n_pad / 256), 256, 0, s>>>(c->d_q, c->rules[r].b, c->d_colcnt);
+        tc::k_useful_dot<<<(uint32_t)(((uint64_t)c->n * 32 + 255) / 256), 256, 0, s>>>(c->d_q, c->rules[r].c, g,
+                                                                                       c->d_colcnt);
+    }
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
 
 static int g_tc_available = -1;
 

@@ -101,6 +101,7 @@ def test_null_arguments():
     assert lib.cfpq_stats_get(None, None) == eng.ERR_INVALID
     assert lib.cfpq_options_default(None) == eng.ERR_INVALID
     assert lib.cfpq_solve_batch(None, 0, None) == eng.ERR_INVALID
+    assert lib.cfpq_measure_mma_sync_peaks(None, None) == eng.ERR_INVALID
     lib.cfpq_destroy(None)
 
 

@@ -223,3 +223,9 @@ def test_get_all_equals_per_relation(n, c):
     allt = q.triples_all()
     per = np.concatenate([q.triples(nm) for nm in g.names], axis=0)
     assert np.array_equal(allt, per)
+
+
+def test_mma_sync_peaks_are_measured():
+    p = eng.measure_mma_sync_peaks()
+    # both are real device rates: far above zero, far below the FP8 tcgen05 peak (4.5 PF)
+    assert 10.0 < p["s8_tops"] < 4500.0 and 10.0 < p["b1_tops"] < 40000.0

@@ -64,3 +64,21 @@ def test_hierarchy_q1(n, c):
 @pytest.mark.parametrize("text", [synth.GRAMMAR_Q1, synth.GRAMMAR_QSC])
 def test_hierarchy_n16384(text):
     tensor_parity(synth.hierarchy(16384, 5000, seed=0), text)
+
+
+def test_useful_work_of_one_product():
+    # S -> A B, A -> t0, B -> t1: every execution multiplies the same seeded A and B, whose
+    # useful multiply-adds are sum_k (ones in column k of A) (ones in row k of B)
+    graph = synth.random_graph(700, 9000, 2, seed=11)
+    text = "S A B\nA t0\nB t1\n"
+    g = eng.Grammar(text, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_TENSOR, schedule=eng.SCHED_JACOBI, profile=True)
+    q.solve()
+    e = np.unique(np.asarray(graph.edges, dtype=np.int64), axis=0)
+    a = e[e[:, 1] == 0]
+    b = e[e[:, 1] == 1]
+    col_a = np.bincount(a[:, 2], minlength=graph.n)
+    row_b = np.bincount(b[:, 0], minlength=graph.n)
+    s = q.stats()
+    assert s["useful_ops"] == 2.0 * s["iterations"] * float(np.dot(col_a, row_b))
+    assert 0 < s["useful_ops"] < s["dense_ops"]
