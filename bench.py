@@ -56,13 +56,17 @@ def parse():
     ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="hier16k", choices=["hier16k", "batch256", "serve", "cycles"],
-                    help="hier16k: the default line; batch256 / serve / cycles: the batched, served and "
+    ap.add_argument("--workload", default="hier16k", choices=["hier16k", "sg16k", "batch256", "serve", "cycles"],
+                    help="hier16k: the default line; sg16k: the same hierarchy with the same-generation "
+                         "query (denser result); batch256 / serve / cycles: the batched, served and "
                          "two-cycle workloads")
     ap.add_argument("--n", type=int, default=None, help="smaller hierarchy for profiling captures")
     ap.add_argument("--classes", type=int, default=None)
     a = ap.parse_args()
-    global N_NODES, N_CLASSES, WORKLOAD
+    global N_NODES, N_CLASSES, WORKLOAD, GRAMMARS
+    if a.workload == "sg16k":
+        GRAMMARS = [("SG", synth.GRAMMAR_SG)]
+        WORKLOAD = WORKLOAD.replace("Query 1 + sc-only query", "same-generation query (sc up, then down)")
     if a.n:
         N_NODES = a.n
         N_CLASSES = a.classes or max(1, round(N_NODES * 5000 / 16384))
@@ -70,9 +74,12 @@ def parse():
     return a
 
 
+GRAMMARS = [("Q1", synth.GRAMMAR_Q1), ("QSC", synth.GRAMMAR_QSC)]
+
+
 def workload():
     g = synth.hierarchy(N_NODES, N_CLASSES, seed=SEED)
-    return g, [("Q1", synth.GRAMMAR_Q1), ("QSC", synth.GRAMMAR_QSC)]
+    return g, list(GRAMMARS)
 
 
 def load_peaks():

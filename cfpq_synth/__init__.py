@@ -177,6 +177,18 @@ SC sc
 """
 
 #: S -> a S b | a b in normal form.
+# The same-generation query read with the opposite subClassOf direction (walk up k sc edges,
+# then down k): on these hierarchies R_S holds every pair of classes at the same depth below
+# the root, a far denser result than the sc-only query (which only returns the diagonal of
+# classes with a child). S -> sc S sc_r | sc sc_r with preterminals.
+GRAMMAR_SG = """\
+S SC X
+S SC SCR
+X S SCR
+SC sc
+SCR sc_r
+"""
+
 GRAMMAR_C3 = """\
 S A S1
 S A B

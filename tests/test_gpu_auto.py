@@ -66,3 +66,38 @@ def test_jacobi_loop_count_matches_algorithm1():
     _, q, s = auto_parity(graph, text, schedule=eng.SCHED_JACOBI)
     _, _, k = oracle.matrix_closure_sparse(graph, text)
     assert s["iterations"] == k
+
+
+def same_depth_pairs(graph):
+    parent = {int(s): int(d) for s, l, d in graph.edges if l == 0}
+    C = graph.meta["n_classes"]
+    depth = np.zeros(C, dtype=np.int64)
+    for c in range(1, C):
+        depth[c] = depth[parent[c]] + 1
+    sizes = np.bincount(depth)
+    return int((sizes[1:] ** 2).sum())
+
+
+@pytest.mark.parametrize("path", [eng.PATH_AUTO, eng.PATH_TENSOR, eng.PATH_GATHER])
+def test_same_generation_4096(path):
+    graph = synth.hierarchy(4096, 1200, seed=2)
+    g = eng.Grammar(synth.GRAMMAR_SG, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=path, timeout_s=120.0)
+    q.solve()
+    ref = oracle.hellings(graph, synth.GRAMMAR_SG)
+    for nm in g.names:
+        assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+
+
+def test_same_generation_full_size():
+    # n = 16384, 5000 classes: |R_S| = sum over depths >= 1 of (classes at that depth)^2, and
+    # the Jacobi loop count is the oracle's sparse Algorithm 1 count
+    graph = synth.hierarchy(16384, 5000, seed=0)
+    g = eng.Grammar(synth.GRAMMAR_SG, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, schedule=eng.SCHED_JACOBI, timeout_s=300.0)
+    q.solve()
+    assert q.count("S") == same_depth_pairs(graph)
+    _, _, k = oracle.matrix_closure_sparse(graph, synth.GRAMMAR_SG)
+    s = q.stats()
+    assert s["iterations"] == k
+    products_each_once(s, synth.GRAMMAR_SG, graph)

@@ -206,6 +206,33 @@ def test_sc_only_hierarchy_closed_form(n, C, seed):
     assert set(map(tuple, res.pairs("X").tolist())) == {(c, parent[c]) for c in has_child if c in parent}
 
 
+def class_depths(g):
+    """Depth of every class below the root (class 0) from the generator's sc edges."""
+    parent = {int(s): int(d) for s, l, d in g.edges if l == 0}
+    C = g.meta["n_classes"]
+    depth = [0] * C
+    for c in range(1, C):  # parents are earlier classes
+        depth[c] = depth[parent[c]] + 1
+    return parent, depth
+
+
+@pytest.mark.parametrize("n,C,seed", [(200, 60, 0), (1024, 300, 1), (2000, 700, 3)])
+def test_same_generation_hierarchy_closed_form(n, C, seed):
+    # S -> sc S sc_r | sc sc_r: up k >= 1 subClassOf edges then down k. On a tree every two
+    # classes at the same depth d >= 1 meet at the root after d steps up, and nothing else
+    # qualifies (instances have no sc edges); X = S sc_r adds one step down
+    g = synth.hierarchy(n, C, seed=seed)
+    res = oracle.hellings(g, synth.GRAMMAR_SG)
+    parent, depth = class_depths(g)
+    by_depth = {}
+    for c, d in enumerate(depth):
+        by_depth.setdefault(d, []).append(c)
+    exp_s = {(x, y) for d, cs in by_depth.items() if d >= 1 for x in cs for y in cs}
+    assert set(map(tuple, res.pairs("S").tolist())) == exp_s
+    exp_x = {(x, c) for (x, y) in exp_s for c in by_depth.get(depth[y] + 1, []) if parent.get(c) == y}
+    assert set(map(tuple, res.pairs("X").tolist())) == exp_x
+
+
 def test_q1_hierarchy_y_empty():
     g = synth.hierarchy(1024, 300, seed=0)
     res = oracle.hellings(g, synth.GRAMMAR_Q1)
