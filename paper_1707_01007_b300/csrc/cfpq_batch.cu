@@ -153,7 +153,9 @@ __device__ __forceinline__ void unpack_item(unsigned long long v, int *j, int *g
 }
 
 
-__global__ void __launch_bounds__(256) k_batch(BatchCtl *ctl, const BatchQuery *bq) {
+// 4 blocks of 256 per SM (registers capped at 64; a few spill): the phases are latency-bound and
+// gain more from resident warps than they lose to the spills (measured 4.7 -> 4.1 ms on 256 queries)
+__global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuery *bq) {
     const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t gthreads = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t gwarp = gtid >> 5, gwarps = gthreads >> 5;
