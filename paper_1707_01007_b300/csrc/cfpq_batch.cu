@@ -223,69 +223,102 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
         const int na = min((int)ld_u32(&ctl->n_active), k);
         if (na <= 0) break;
         if (gtid == 0) ctl->rounds++;
-        // 3a) candidate rows: item = (query, group, row word); the warp lists, for each row
-        //     of its word that has a left delta row or (where the right operand has a delta)
-        //     a non-empty left row, one product item per column chunk
+        // 3a) candidate rows, one lane per item (query, group, row word): the rows of the
+        //     word that have a left delta row or (where the right operand has a delta) a
+        //     non-empty left row become one product item per column chunk; the warp reserves
+        //     its lanes' items with one atomic and each lane writes its own
         const unsigned long long np = __ldcg(ctl->prod_off + na);
-        for (unsigned long long it = gwarp; it < np; it += gwarps) {
-            const int s = find_slot(ctl->prod_off, na, it);
-            const int j = __ldcg(ctl->act + s);
-            if (j < 0 || j >= k) continue;
-            const BatchQuery &b = bq[j];
-            const QDesc &q = b.q;
-            const uint32_t rw = (q.n + 31u) / 32u;
-            const unsigned long long loc = it - __ldcg(ctl->prod_off + s);
-            const unsigned long long g64 = loc / rw;
-            const uint32_t wq = (uint32_t)(loc % rw);
-            if (g64 >= (unsigned long long)q.n_groups) continue;
-            const int g = (int)g64;
-            const uint32_t parity = (uint32_t)(ld_u64(&q.st->iter) & 1ull);
-            const uint32_t *DR = parity ? q.R1 : q.R0;
-            uint32_t cand = 0;
-            for (int ri = q.gstart[g]; ri < q.gstart[g + 1]; ri++) {
-                const int B = q.rules[ri].b, C = q.rules[ri].c;
-                cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
-                if (ld_u64(&q.st->dcount[parity][C]) != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
+        for (unsigned long long it0 = gwarp * 32ull; it0 < np; it0 += gwarps * 32ull) {
+            const unsigned long long it = it0 + (unsigned)lane;
+            uint32_t cand = 0, wq = 0, nch = 0;
+            int j = 0, g = 0;
+            if (it < np) {
+                const int s = find_slot(ctl->prod_off, na, it);
+                j = __ldcg(ctl->act + s);
+                if (j >= 0 && j < k) {
+                    const BatchQuery &b = bq[j];
+                    const QDesc &q = b.q;
+                    const uint32_t rw = (q.n + 31u) / 32u;
+                    const unsigned long long loc = it - __ldcg(ctl->prod_off + s);
+                    const unsigned long long g64 = loc / rw;
+                    wq = (uint32_t)(loc % rw);
+                    if (g64 < (unsigned long long)q.n_groups) {
+                        g = (int)g64;
+                        nch = b.nch;
+                        const uint32_t parity = (uint32_t)(ld_u64(&q.st->iter) & 1ull);
+                        const uint32_t *DR = parity ? q.R1 : q.R0;
+                        for (int ri = q.gstart[g]; ri < q.gstart[g + 1]; ri++) {
+                            const int B = q.rules[ri].b, C = q.rules[ri].c;
+                            cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
+                            if (ld_u64(&q.st->dcount[parity][C]) != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
+                        }
+                        cand &= rows_in_word(q.n, wq);
+                    }
+                }
             }
-            cand &= rows_in_word(q.n, wq);
-            if (!cand) continue;
-            const unsigned n_emit = (unsigned)__popc(cand) * b.nch;
+            const uint32_t cnt = (uint32_t)__popc(cand) * nch;
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
+            if (wtotal == 0) continue;
             unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(&ctl->list_len, (unsigned long long)n_emit);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base + n_emit > ctl->list_cap) {  // cannot happen: the capacity covers every row
+            if (lane == 31) base = atomicAdd(&ctl->list_len, (unsigned long long)wtotal);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            if (base + wtotal > ctl->list_cap) {  // cannot happen: the capacity covers every row
                 if (lane == 0) atomicExch(&ctl->error, 3u);
                 continue;
             }
-            for (unsigned e = lane; e < n_emit; e += 32) {
-                const unsigned r = e / b.nch, ch = e % b.nch;
-                const uint32_t i = wq * 32u + (uint32_t)(__fns(cand, 0, (int)r + 1));
-                ctl->list[base + e] = pack_item(j, g, i, ch);
+            unsigned long long pos = base + incl - cnt;
+            while (cand) {
+                const uint32_t i = wq * 32u + (uint32_t)(__ffs(cand) - 1);
+                cand &= cand - 1;
+                for (uint32_t ch = 0; ch < nch; ch++) ctl->list[pos++] = pack_item(j, g, i, ch);
             }
         }
         // the plane this round's products write (N) is the one the previous round read (its
-        // D): clear the rows its bitmap flags, then the bitmap (item = non-terminal, row word)
+        // D): clear the rows its bitmap flags, then the bitmap. One lane per (query,
+        // non-terminal, row word) finds the rows; the warp clears them together.
         const unsigned long long nr = __ldcg(ctl->row_off + na);
-        for (unsigned long long it = gwarp; it < nr; it += gwarps) {
-            const int s = find_slot(ctl->row_off, na, it);
-            const int j = __ldcg(ctl->act + s);
-            if (j < 0 || j >= k) continue;
-            const BatchQuery &b = bq[j];
-            const unsigned long long loc = it - __ldcg(ctl->row_off + s);
-            if (loc >= b.row_items) continue;
-            const uint32_t rw = (b.q.n + 31u) / 32u;
-            const int a = (int)(loc / rw);
-            const uint32_t wq = (uint32_t)(loc % rw);
-            const uint32_t prev = (uint32_t)((ld_u64(&b.q.st->iter) + 1ull) & 1ull);
-            uint32_t *bm = (prev ? b.q.R1 : b.q.R0) + (uint64_t)a * b.q.W + wq;
-            const uint32_t word = __ldcg(bm);
-            uint32_t rows = word & rows_in_word(b.q.n, wq);
-            while (rows) {
-                const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
-                rows &= rows - 1;
-                clear_row(b.q, a, i, lane, prev);
+        for (unsigned long long it0 = gwarp * 32ull; it0 < nr; it0 += gwarps * 32ull) {
+            const unsigned long long it = it0 + (unsigned)lane;
+            uint32_t rows = 0, wq = 0, W = 0;
+            uint32_t *plane = nullptr;
+            if (it < nr) {
+                const int s = find_slot(ctl->row_off, na, it);
+                const int j = __ldcg(ctl->act + s);
+                const unsigned long long loc = it - __ldcg(ctl->row_off + s);
+                if (j >= 0 && j < k && loc < bq[j].row_items) {
+                    const QDesc &q = bq[j].q;
+                    const uint32_t rw = (q.n + 31u) / 32u;
+                    const int a = (int)(loc / rw);
+                    wq = (uint32_t)(loc % rw);
+                    W = q.W;
+                    const uint32_t prev = (uint32_t)((ld_u64(&q.st->iter) + 1ull) & 1ull);
+                    uint32_t *bm = (prev ? q.R1 : q.R0) + (uint64_t)a * q.W + wq;
+                    const uint32_t word = __ldcg(bm);
+                    rows = word & rows_in_word(q.n, wq);
+                    plane = (prev ? q.X1 : q.X0) + (uint64_t)a * q.plane;
+                    if (word) *bm = 0u;
+                }
             }
-            if (word && lane == 0) *bm = 0u;
+            unsigned todo = __ballot_sync(0xffffffffu, rows != 0);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                uint32_t r = __shfl_sync(0xffffffffu, rows, src);
+                const uint32_t sw = __shfl_sync(0xffffffffu, W, src), swq = __shfl_sync(0xffffffffu, wq, src);
+                uint32_t *sp = reinterpret_cast<uint32_t *>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(plane), src));
+                while (r) {
+                    const uint64_t i = swq * 32u + (uint32_t)(__ffs(r) - 1);
+                    r &= r - 1;
+                    for (uint32_t w = lane; w < sw; w += 32) sp[i * sw + w] = 0u;
+                }
+            }
         }
         if (!grid_barrier(ctl)) return;
         mark(1, round);
@@ -308,25 +341,50 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
         }
         if (!grid_barrier(ctl)) return;
         mark(2, round);
-        // 4) Jacobi queries: T |= N (item = non-terminal, row word: the rows N touched)
+        // 4) Jacobi queries: T |= N over the rows N touched (one lane per (query, non-terminal,
+        //    row word) finds them and sets the row bitmap of T; the warp merges them together)
         if (ctl->any_jacobi) {
-            for (unsigned long long it = gwarp; it < nr; it += gwarps) {
-                const int s = find_slot(ctl->row_off, na, it);
-                const int j = __ldcg(ctl->act + s);
-                if (j < 0 || j >= k) continue;
-                const BatchQuery &b = bq[j];
-                if (b.q.schedule != CFPQ_SCHED_JACOBI) continue;
-                const unsigned long long loc = it - __ldcg(ctl->row_off + s);
-                if (loc >= b.row_items) continue;
-                const uint32_t rw = (b.q.n + 31u) / 32u;
-                const int a = (int)(loc / rw);
-                const uint32_t wq = (uint32_t)(loc % rw);
-                const uint32_t parity = (uint32_t)(ld_u64(&b.q.st->iter) & 1ull);
-                uint32_t rows = __ldcg((parity ? b.q.R0 : b.q.R1) + (uint64_t)a * b.q.W + wq) & rows_in_word(b.q.n, wq);
-                while (rows) {
-                    const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
-                    rows &= rows - 1;
-                    merge_row(b.q, a, i, lane, parity);
+            const unsigned long long nr = __ldcg(ctl->row_off + na);
+            for (unsigned long long it0 = gwarp * 32ull; it0 < nr; it0 += gwarps * 32ull) {
+                const unsigned long long it = it0 + (unsigned)lane;
+                uint32_t rows = 0, wq = 0, W = 0;
+                uint32_t *tp = nullptr;
+                const uint32_t *np_ = nullptr;
+                if (it < nr) {
+                    const int s = find_slot(ctl->row_off, na, it);
+                    const int j = __ldcg(ctl->act + s);
+                    const unsigned long long loc = it - __ldcg(ctl->row_off + s);
+                    if (j >= 0 && j < k && loc < bq[j].row_items && bq[j].q.schedule == CFPQ_SCHED_JACOBI) {
+                        const QDesc &q = bq[j].q;
+                        const uint32_t rw = (q.n + 31u) / 32u;
+                        const int a = (int)(loc / rw);
+                        wq = (uint32_t)(loc % rw);
+                        W = q.W;
+                        const uint32_t parity = (uint32_t)(ld_u64(&q.st->iter) & 1ull);
+                        rows = __ldcg((parity ? q.R0 : q.R1) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
+                        tp = q.T + (uint64_t)a * q.plane;
+                        np_ = (parity ? q.X0 : q.X1) + (uint64_t)a * q.plane;
+                        if (rows) atomicOr(&q.Trow[(uint64_t)a * q.W + wq], rows);
+                    }
+                }
+                unsigned todo = __ballot_sync(0xffffffffu, rows != 0);
+                while (todo) {
+                    const int src = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    uint32_t r = __shfl_sync(0xffffffffu, rows, src);
+                    const uint32_t sw = __shfl_sync(0xffffffffu, W, src), swq = __shfl_sync(0xffffffffu, wq, src);
+                    uint32_t *st_ = reinterpret_cast<uint32_t *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(tp), src));
+                    const uint32_t *sn = reinterpret_cast<const uint32_t *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(np_), src));
+                    while (r) {
+                        const uint64_t i = swq * 32u + (uint32_t)(__ffs(r) - 1);
+                        r &= r - 1;
+                        for (uint32_t w = lane; w < sw; w += 32) {
+                            const uint32_t nw = __ldcg(sn + i * sw + w);
+                            if (nw) st_[i * sw + w] = __ldcg(st_ + i * sw + w) | nw;
+                        }
+                    }
                 }
             }
             if (!grid_barrier(ctl)) return;
