@@ -210,10 +210,12 @@ void cfpq_grammar_free(cfpq_parsed_grammar *pg);
  * context advances one loop iteration per round; a context whose iteration added no
  * pair is retired (per-query convergence) while the others continue. Results are
  * identical to solving each context alone. Each context keeps its own schedule and
- * iteration cap; products always take the gather path inside the grouped launch, and
- * timeouts are not applied. Errors: INVALID, NOMEM, CUDA, UNSUPPORTED (no cooperative
- * launch), TIMEOUT (a bounded grid barrier gave up), ITER_LIMIT (some context hit its
- * cap; the others are still complete).
+ * iteration cap; products always take the gather path inside the grouped launch. The
+ * smallest positive timeout_s among the contexts limits the whole launch (checked on the
+ * device after every round; the contexts are then left unsolved). Errors: INVALID, NOMEM,
+ * CUDA, UNSUPPORTED (no cooperative launch), TIMEOUT (the launch's wall-clock limit passed
+ * or a bounded grid barrier gave up), ITER_LIMIT (some context hit its cap; the others are
+ * still complete).
  */
 int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream);
 

@@ -511,7 +511,7 @@ int batch_buffers_alloc(BatchBuffers *b, int k) {
 }
 
 int batch_buffers_upload(BatchBuffers *b, BatchQuery *hb, const int *active, int k, int max_rounds,
-                         bool any_jacobi, cudaStream_t s) {
+                         bool any_jacobi, cudaStream_t s, unsigned long long limit_ns) {
     BatchCtl ctl;
     memset(&ctl, 0, sizeof(ctl));
     unsigned long long clr = 0, seed = 0;
@@ -543,7 +543,7 @@ int batch_buffers_upload(BatchBuffers *b, BatchQuery *hb, const int *active, int
     ctl.k = k;
     ctl.max_rounds = max_rounds;
     ctl.any_jacobi = any_jacobi ? 1 : 0;
-    ctl.limit_ns = kLaunchLimitNs;
+    ctl.limit_ns = (limit_ns > 0 && limit_ns < kLaunchLimitNs) ? limit_ns : kLaunchLimitNs;
     ctl.active = b->active;
     ctl.act = b->act;
     ctl.prod_off = b->prod_off;
@@ -631,7 +631,13 @@ static int solve_batch_with(cfpq_ctx *const *ctxs, int k, cudaStream_t s, const 
     if (rc != CFPQ_OK) return rc;
     BatchBuffers &bufs = *pb;
     std::vector<int> active(k, 1);
-    if (rc == CFPQ_OK) rc = batch_buffers_upload(&bufs, hb.data(), active.data(), k, 1 << 30, any_jacobi, s);
+    // the smallest wall-clock limit among the contexts bounds the whole launch
+    double limit_s = 0.0;
+    for (int j = 0; j < k; j++)
+        if (ctxs[j]->timeout_s > 0.0 && (limit_s == 0.0 || ctxs[j]->timeout_s < limit_s)) limit_s = ctxs[j]->timeout_s;
+    if (rc == CFPQ_OK)
+        rc = batch_buffers_upload(&bufs, hb.data(), active.data(), k, 1 << 30, any_jacobi, s,
+                                  (unsigned long long)(limit_s * 1e9));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

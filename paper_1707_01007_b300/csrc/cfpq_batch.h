@@ -63,8 +63,9 @@ void batch_record_profile(const BatchBuffers *b, cudaStream_t s);
 // Copies the k queries' device states into b->states (one small launch).
 int batch_collect_states(const BatchBuffers *b, const BatchQuery *d_bq, int k, cudaStream_t s);
 // Computes the start-phase prefix sums in hb, then copies control block and descriptors.
+// limit_ns: wall-clock limit of the launch, checked after every round (0 = the default cap).
 int batch_buffers_upload(BatchBuffers *b, BatchQuery *hb, const int *active, int k, int max_rounds,
-                         bool any_jacobi, cudaStream_t s);
+                         bool any_jacobi, cudaStream_t s, unsigned long long limit_ns = 0);
 void batch_buffers_free(BatchBuffers *b);
 int batch_launch(BatchCtl *d_ctl, const BatchQuery *d_bq, cudaStream_t s, int blocks_per_sm, int *grid_out);
 // Descriptor of one query for a grouped launch under configuration t: tile width (cpl) and,

@@ -78,3 +78,19 @@ def test_batch_iteration_limit_is_per_query():
     ref = oracle.hellings(graph, synth.GRAMMAR_Q1)
     for nm in b[0].names:
         assert np.array_equal(b[1].get(nm), ref.pairs(nm))
+
+
+def test_batch_wall_clock_limit_is_checked_on_the_device():
+    # two cycles 64/63 need 2pq+1 = 8065 Jacobi rounds; a 2 ms limit ends the launch early with
+    # TIMEOUT, the contexts stay unsolved, and the same contexts solve normally afterwards
+    graph = synth.two_cycles(64, 63)
+    g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
+    slow = eng.Query(g, graph.n, graph.edges, path=eng.PATH_GATHER, schedule=eng.SCHED_JACOBI, timeout_s=0.002)
+    other = eng.Query(g, graph.n, graph.edges, path=eng.PATH_GATHER)
+    assert eng.solve_batch([slow, other], check=False) == eng.ERR_TIMEOUT
+    with pytest.raises(eng.CfpqError):
+        other.count("S")
+    fresh = eng.Query(g, graph.n, graph.edges, path=eng.PATH_GATHER, schedule=eng.SCHED_JACOBI)
+    eng.solve_batch([fresh, other])
+    assert fresh.count("S") == 64 * 63 and other.count("S") == 64 * 63
+    assert fresh.stats()["iterations"] == 2 * 64 * 63 + 1
