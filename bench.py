@@ -62,6 +62,7 @@ def parse():
                          "two-cycle workloads")
     ap.add_argument("--n", type=int, default=None, help="smaller hierarchy for profiling captures")
     ap.add_argument("--classes", type=int, default=None)
+    ap.add_argument("--cycle-p", type=int, default=None, help="a-cycle length of the cycles workload (profiling)")
     a = ap.parse_args()
     global N_NODES, N_CLASSES, WORKLOAD, GRAMMARS
     if a.workload == "sg16k":
@@ -541,7 +542,8 @@ def cycles_arm(args):
     import paper_1707_01007_b300 as eng
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    p, q = 4096, 4095
+    p = args.cycle_p or 4096
+    q = p - 1
     graph = synth.two_cycles(p, q)
     g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
     qy = eng.Query(g, graph.n, graph.edges, path=eng.PATH_WORKLIST, timeout_s=600.0)
@@ -558,7 +560,7 @@ def cycles_arm(args):
     line = {"metric": "two-cycle closure time (worklist path)", "value": ms / 1e3, "unit": "s", "n_gpus": 1,
             "steps": len(times), "warmup": 1, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
-            "config": {"workload": "two cycles 4096 / 4095 sharing node 0, S -> a S b | a b (n = 8190)"},
+            "config": {"workload": f"two cycles {p} / {q} sharing node 0, S -> a S b | a b (n = {graph.n})"},
             "pairs_S": qy.count("S"), "closed_form_count_ok": bool(ok), "worklist_items": st["worklist_items"],
             "ns_per_item": ms * 1e6 / max(1, st["worklist_items"])}
     if not args.no_cpu_baseline:

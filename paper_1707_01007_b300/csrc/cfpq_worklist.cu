@@ -21,6 +21,28 @@
 
 namespace cfpq {
 
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kWlWarps = 16, kWlThreads = 32 * kWlWarps;  // warp 0 runs the worklist, all 16 the chains
+constexpr int kLiftLevels = 17;          // powers 2^0 .. 2^16 of a period map
+constexpr int kPcSteps = 64, kPcBatch = 16;                 // a round: 512 threads x 64 steps
+constexpr uint32_t kPcRound = kWlThreads * kPcSteps;        // chain steps per round (a power of two)
+static_assert((kPcRound & (kPcRound - 1)) == 0 && (1u << (kLiftLevels - 1)) >= kPcRound, "power tables");
+static_assert(kPcSteps % kPcBatch == 0, "batches");
+
+// A periodic chain: from a pair of non-terminal a the chain goes a -> a1 -> a (P = 2) or
+// a -> a (P = 1), each step moving one coordinate of the pair through the unique-successor
+// table of a static relation (row: i -> the only k with (k, i) in the partner, when a is a
+// right operand; column: j -> the only k with (j, k), when a is a left operand). Over one
+// period the row goes through the map G and the column through H (compositions of the
+// period's steps; identity if a coordinate does not move), so the pair after P u + r steps
+// is (G^u(i), H^u(j)) followed by the first r steps. Powers G^(2^k), H^(2^k) are tabulated.
+struct PChain {
+    int32_t P, a1, c0, g_id;      // c0: coordinate of step 0 (0 row, 1 column); g_id: G is identity
+    int32_t h_id, pad0, pad1, pad2;
+    uint64_t m0;                  // step 0's table in uniq
+    uint64_t lg, lh;              // G's and H's power tables in lift (level k at + k n)
+};
+
 struct WLDesc {
     const int2 *occ;              // per non-terminal a: (production index, side 0 = left / 1 = right)
     const int32_t *occ_start;     // [n_nt + 1]
@@ -34,6 +56,8 @@ struct WLDesc {
                                   // occurrence and its partner is static, else (0, ...)
     const uint64_t *chain_base;   // [n_nt] start of the partner's unique-successor table
     const uint32_t *uniq;         // per static partner and direction: the only k, or 0xFFFFFFFF
+    const PChain *pchain;         // [n_nt] periodic chain starting at a (P = 0: none)
+    const uint32_t *lift;         // per periodic chain: kLiftLevels tables of n entries for G and H
     uint32_t *stack;              // triples (a, i, j)
     uint64_t cap;                 // stack capacity in triples
     unsigned long long *items;    // pairs processed
@@ -44,7 +68,6 @@ __device__ __forceinline__ bool wl_set(const QDesc &q, const WLDesc &w, int x, u
     const uint32_t bit = 1u << (b & 31);
     const uint32_t old = atomicOr(&q.T[(uint64_t)x * q.plane + (uint64_t)a * q.W + (b >> 5)], bit);
     if (old & bit) return false;
-    atomicOr(&q.Trow[(uint64_t)x * q.W + (a >> 5)], 1u << (a & 31));  // extraction skips empty rows
     if (w.needs_tt[x]) atomicOr(&q.TT[(uint64_t)x * q.plane + (uint64_t)b * q.W + (a >> 5)], 1u << (a & 31));
     return true;
 }
@@ -65,25 +88,138 @@ __device__ __forceinline__ bool single_successor(const int4 *chain, const uint64
     return true;
 }
 
-// One warp. Processes the stack until it is empty, the deadline passes or it overflows.
-// Chain lookahead: when the current pair has a single successor through static operands,
+enum : int32_t { kPcExit = 0, kPcFirst = 1, kPcNext = 2 };
+
+struct PcTask {
+    PChain pc;
+    uint32_t a, i, j;  // the pair the round's steps start from (kPcFirst)
+    int32_t cmd;
+};
+
+__shared__ PcTask s_task;
+__shared__ uint32_t s_valid[kWlWarps], s_fresh[kWlWarps];
+__shared__ uint4 s_last[kWlThreads];  // each thread's last pair set (a, i, j, new)
+
+__device__ __forceinline__ void named_barrier(int id) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kWlThreads) : "memory");
+}
+
+struct PcLane {
+    uint32_t gi = 0, hj = 0;  // (G^u, H^u) of this thread's first step in the current round
+};
+
+// One thread's share of a periodic-chain round: steps 64 t + 1 .. 64 t + 64 from the task's
+// pair (thread t of the block). Writes the thread's last pair and the warp's counts.
+__device__ void pc_round(const QDesc &q, const WLDesc &w, const PcTask &task, PcLane &me) {
+    const PChain &pc = task.pc;
+    const uint32_t n = q.n, P = (uint32_t)pc.P;
+    const uint32_t *LG = w.lift + pc.lg, *LH = w.lift + pc.lh, *M0 = w.uniq + pc.m0;
+    const uint32_t a0 = task.a, a1 = (uint32_t)pc.a1;
+    const uint32_t t0 = threadIdx.x * (uint32_t)kPcSteps + 1u;
+    const uint32_t u0 = t0 / P, r0 = t0 % P;
+    if (task.cmd == kPcFirst) {
+        me.gi = task.i;
+        me.hj = task.j;
+        for (int k = 0; k < kLiftLevels; k++)
+            if ((u0 >> k) & 1u) {
+                if (!pc.g_id) me.gi = me.gi == kNone ? kNone : __ldg(LG + (uint64_t)k * n + me.gi);
+                if (!pc.h_id) me.hj = me.hj == kNone ? kNone : __ldg(LH + (uint64_t)k * n + me.hj);
+            }
+    } else {  // kPcNext: 32768 steps further along the same chain
+        const int jump = 31 - __clz(kPcRound / P);
+        if (!pc.g_id) me.gi = me.gi == kNone ? kNone : __ldg(LG + (uint64_t)jump * n + me.gi);
+        if (!pc.h_id) me.hj = me.hj == kNone ? kNone : __ldg(LH + (uint64_t)jump * n + me.hj);
+    }
+    uint32_t g = me.gi, h = me.hj, r = r0, valid = 0, fresh = 0;
+    uint32_t la = 0, li = 0, lj = 0, lnew = 0;
+#pragma unroll 1
+    for (int b = 0; b < kPcSteps / kPcBatch; b++) {
+        uint32_t pa[kPcBatch], pi[kPcBatch], pj[kPcBatch], old[kPcBatch];
+        bool ok[kPcBatch];
+#pragma unroll
+        for (int s2 = 0; s2 < kPcBatch; s2++) {
+            uint32_t xi = g, xj = h;
+            if (r == 1u) {
+                if (pc.c0 == 0) xi = xi == kNone ? kNone : __ldg(M0 + xi);
+                else xj = xj == kNone ? kNone : __ldg(M0 + xj);
+            }
+            ok[s2] = xi != kNone && xj != kNone;
+            pa[s2] = r == 0u ? a0 : a1;
+            pi[s2] = xi;
+            pj[s2] = xj;
+            if (++r == P) {
+                r = 0;
+                if (!pc.g_id) g = g == kNone ? kNone : __ldg(LG + g);
+                if (!pc.h_id) h = h == kNone ? kNone : __ldg(LH + h);
+            }
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < kPcBatch; s2++)
+            old[s2] = ok[s2] ? atomicOr(&q.T[(uint64_t)pa[s2] * q.plane + (uint64_t)pi[s2] * q.W + (pj[s2] >> 5)],
+                                        1u << (pj[s2] & 31))
+                             : 0u;
+#pragma unroll
+        for (int s2 = 0; s2 < kPcBatch; s2++) {
+            if (!ok[s2]) continue;
+            valid++;
+            const bool nw = !((old[s2] >> (pj[s2] & 31)) & 1u);
+            if (nw) {
+                fresh++;
+                if (w.needs_tt[pa[s2]])
+                    atomicOr(&q.TT[(uint64_t)pa[s2] * q.plane + (uint64_t)pj[s2] * q.W + (pi[s2] >> 5)],
+                             1u << (pi[s2] & 31));
+            }
+            la = pa[s2];
+            li = pi[s2];
+            lj = pj[s2];
+            lnew = nw ? 1u : 0u;
+        }
+    }
+    s_last[threadIdx.x] = make_uint4(la, li, lj, lnew);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        valid += __shfl_xor_sync(0xffffffffu, valid, o);
+        fresh += __shfl_xor_sync(0xffffffffu, fresh, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_valid[threadIdx.x >> 5] = valid;
+        s_fresh[threadIdx.x >> 5] = fresh;
+    }
+}
+
+// Warp 0 processes the stack until it is empty, the deadline passes or it overflows; the
+// other warps help with periodic chains.
+// Chain lookahead (warp 0 alone): when the current pair has a single successor through static operands,
 // the warp follows the chain up to 31 steps ahead (lane l holds step l + 1) and sets all of
 // them with one round of atomics. Every pair set in the batch has its successor set in the
 // same batch except the last one, so the chain continues from the last pair if it was new
 // and stops otherwise: the pairs processed are exactly those the one-at-a-time loop would
 // process, and the result is the same least fixpoint.
-__global__ void __launch_bounds__(32) k_worklist(const QDesc *qd, WLDesc w, unsigned long long top0) {
+__global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLDesc w, unsigned long long top0) {
     const QDesc &q = *qd;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) {
+        // helper warps: one share of every periodic-chain round, until warp 0 is done
+        PcLane me;
+        for (;;) {
+            named_barrier(1);
+            if (s_task.cmd == kPcExit) break;
+            pc_round(q, w, s_task, me);
+            named_barrier(2);
+        }
+        return;
+    }
     unsigned long long top = top0, processed = 0;
     uint32_t ca = 0, ci = 0, cj = 0;  // item handed over in registers
-    bool have = false;
+    bool have = false, timed_out = false, force_general = false;
     const unsigned long long deadline = ld_u64(&q.st->deadline_ns);
     __shared__ int4 s_chain[kMaxNT];
     __shared__ uint64_t s_cbase[kMaxNT];
+    __shared__ PChain s_pc[kMaxNT];
     for (int a = lane; a < q.n_nt; a += 32) {
         s_chain[a] = w.chain[a];
         s_cbase[a] = w.chain_base[a];
+        s_pc[a] = w.pchain[a];
     }
     __syncwarp();
     for (;;) {
@@ -97,11 +233,78 @@ __global__ void __launch_bounds__(32) k_worklist(const QDesc *qd, WLDesc w, unsi
         }
         have = false;
         processed++;
-        if ((processed & 4095u) == 0 && deadline && globaltimer_ns() > deadline) {
+        bool skip_fast = force_general;  // the pair ended a chain: general join only
+        force_general = false;
+        if ((processed & 4095u) == 0 && deadline &&
+            __shfl_sync(0xffffffffu, globaltimer_ns() > deadline ? 1 : 0, 0)) {  // one decision for the warp
             if (lane == 0) q.st->error = kErrTimeout;
             break;
         }
-        {
+        if (!skip_fast && s_pc[ca].P > 0) {
+            // periodic chain, all 16 warps of the block: 32768 steps per round, each thread 64
+            // consecutive ones with 16 atomics in flight; thread positions jump 32768 steps
+            // ahead between rounds through the power tables, so a round costs no dependent
+            // walk of the chain. A step with no unique successor ends the chain: the last
+            // pair set then goes to the general join below (it may have several successors).
+            bool handled = false;  // false: (ca, ci, cj) still needs the general join
+            if (lane == 0) {
+                s_task.pc = s_pc[ca];
+                s_task.a = ca;
+                s_task.i = ci;
+                s_task.j = cj;
+                s_task.cmd = kPcFirst;
+            }
+            __syncwarp();
+            PcLane me;
+            for (;;) {
+                named_barrier(1);  // helpers start the round
+                pc_round(q, w, s_task, me);
+                named_barrier(2);  // every thread's share is done
+                unsigned tot_valid = 0, tot_fresh = 0;
+                for (int k = 0; k < kWlWarps; k++) {
+                    tot_valid += s_valid[k];
+                    tot_fresh += s_fresh[k];
+                }
+                processed += tot_valid;
+                if (tot_fresh && lane == 0) atomicAdd(&q.st->new_bits, (unsigned long long)tot_fresh);
+                if (tot_valid == 0) break;  // (ca, ci, cj) has no unique successor: general join
+                // the last pair set: held by the thread of step tot_valid
+                const int src = (int)((tot_valid - 1u) / kPcSteps);
+                const uint32_t ea = s_last[src].x, ei = s_last[src].y, ej = s_last[src].z;
+                const bool enew = s_last[src].w != 0;
+                if (tot_valid < kPcRound) {
+                    handled = true;
+                    if (enew) {
+                        ca = ea;
+                        ci = ei;
+                        cj = ej;
+                        have = true;
+                        force_general = true;
+                    }
+                    break;
+                }
+                if (!enew) {
+                    handled = true;  // the pair was already set: whoever set it continues
+                    break;
+                }
+                const int expired = __shfl_sync(0xffffffffu, (deadline && globaltimer_ns() > deadline) ? 1 : 0, 0);
+                if (expired) {
+                    if (lane == 0) q.st->error = kErrTimeout;
+                    timed_out = true;
+                    break;
+                }
+                ca = ea;  // continue from the round's last pair
+                ci = ei;
+                cj = ej;
+                __syncwarp();
+                if (lane == 0) s_task.cmd = kPcNext;
+                __syncwarp();
+            }
+            if (timed_out) break;
+            if (handled) continue;
+            skip_fast = true;  // fall through with (ca, ci, cj)
+        }
+        if (!skip_fast) {
             // chain lookahead
             uint32_t xa = ca, xi = ci, xj = cj, ma = 0, mi = 0, mj = 0;
             int len = 0;
@@ -228,7 +431,25 @@ __global__ void __launch_bounds__(32) k_worklist(const QDesc *qd, WLDesc w, unsi
     if (lane == 0) {
         *w.items = processed;
         q.st->iter = 1;
+        s_task.cmd = kPcExit;
     }
+    __syncwarp();
+    named_barrier(1);  // releases the helpers, which see kPcExit
+}
+
+// After the walk: the row bitmap of every T_a (extraction visits only non-empty rows), rebuilt
+// from the matrix rather than kept with one more atomic per set pair. One warp per row.
+__global__ void k_worklist_rows(const QDesc *qd) {
+    const QDesc &q = *qd;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= (uint64_t)q.n_nt * q.n) return;
+    const uint32_t a = (uint32_t)(warp / q.n), i = (uint32_t)(warp % q.n);
+    const uint32_t *row = q.T + (uint64_t)a * q.plane + (uint64_t)i * q.W;
+    uint32_t any = 0;
+    for (uint32_t w0 = 0; w0 < q.W && !__any_sync(0xffffffffu, any != 0); w0 += 32)
+        any |= (w0 + lane < q.W) ? __ldcg(row + w0 + lane) : 0u;
+    if (__any_sync(0xffffffffu, any != 0) && lane == 0) atomicOr(&q.Trow[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
 }
 
 // Every seeded pair goes on the stack (and into T^T where kept).
@@ -338,6 +559,53 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
         chain[a] = make_int4(1, r.lhs, left ? 1 : 0, p);
         chain_base[a] = left ? uniq_out_base[p] : uniq_in_base[p];
     }
+    // periodic chains (a -> a or a -> a1 -> a through chain steps) and the power tables of
+    // their period maps G (row) and H (column)
+    std::vector<PChain> pchain(n_nt);
+    memset(pchain.data(), 0, sizeof(PChain) * n_nt);
+    std::vector<uint32_t> lift;
+    for (int a = 0; a < n_nt; a++) {
+        if (!chain[a].x) continue;
+        const int a1 = chain[a].y;
+        int P = 0;
+        if (a1 == a) P = 1;
+        else if (chain[a1].x && chain[a1].y == a) P = 2;
+        if (P == 0) continue;
+        std::vector<uint32_t> G(n), H(n);
+        for (uint32_t x = 0; x < n; x++) G[x] = H[x] = x;
+        bool row_moves = false, col_moves = false;
+        for (int st = 0; st < P; st++) {
+            const int x = st == 0 ? a : a1;
+            const bool col = chain[x].z != 0;  // left operand: the column moves
+            const uint32_t *M = uniq.data() + chain_base[x];
+            std::vector<uint32_t> &F = col ? H : G;
+            (col ? col_moves : row_moves) = true;
+            for (uint32_t y = 0; y < n; y++) F[y] = F[y] == kNone ? kNone : M[F[y]];
+        }
+        PChain pc;
+        memset(&pc, 0, sizeof(pc));
+        pc.P = P;
+        pc.a1 = a1;
+        pc.c0 = chain[a].z != 0 ? 1 : 0;
+        pc.m0 = chain_base[a];
+        pc.g_id = row_moves ? 0 : 1;
+        pc.h_id = col_moves ? 0 : 1;
+        auto powers = [&](const std::vector<uint32_t> &F) {
+            const uint64_t base = lift.size();
+            lift.insert(lift.end(), F.begin(), F.end());
+            for (int k = 1; k < kLiftLevels; k++) {
+                const uint64_t prev = base + (uint64_t)(k - 1) * n;
+                for (uint32_t y = 0; y < n; y++) {
+                    const uint32_t v = lift[prev + y];
+                    lift.push_back(v == kNone ? kNone : lift[prev + v]);
+                }
+            }
+            return base;
+        };
+        pc.lg = row_moves ? powers(G) : 0;
+        pc.lh = col_moves ? powers(H) : 0;
+        pchain[a] = pc;
+    }
     // device arena
     const uint64_t cap_full = (uint64_t)n_nt * (uint64_t)n * (uint64_t)n;
     const uint64_t cap = std::max<uint64_t>(1024, std::min<uint64_t>(cap_full, 1ull << 27));
@@ -356,6 +624,8 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
                           {(void **)&d.chain, (size_t)n_nt * sizeof(int4)},
                           {(void **)&d.chain_base, (size_t)n_nt * 8},
                           {(void **)&d.uniq, uniq.size() * 4 + 8},
+                          {(void **)&d.pchain, (size_t)n_nt * sizeof(PChain)},
+                          {(void **)&d.lift, lift.size() * 4 + 8},
                           {(void **)&d.stack, cap * 12},
                           {(void **)&d.items, 8},
                           {(void **)&d.overflow, 8},
@@ -391,6 +661,8 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
     up(d.chain, chain.data(), (size_t)n_nt * sizeof(int4));
     up(d.chain_base, chain_base.data(), (size_t)n_nt * 8);
     up(d.uniq, uniq.data(), uniq.size() * 4);
+    up(d.pchain, pchain.data(), (size_t)n_nt * sizeof(PChain));
+    up(d.lift, lift.data(), lift.size() * 4);
     if (!ok) {
         if (c->pooled) cudaFreeAsync(ws->arena, s);
         else cudaFree(ws->arena);
@@ -427,9 +699,10 @@ int worklist_run(cfpq_ctx *c, cudaStream_t s) {
         cudaStreamSynchronize(s) != cudaSuccess)
         return CFPQ_ERR_CUDA;
     if (top > d.cap) return CFPQ_ERR_NOMEM;
-    k_worklist<<<1, 32, 0, s>>>(c->d_q, d, top);
+    k_worklist<<<1, kWlThreads, 0, s>>>(c->d_q, d, top);
+    k_worklist_rows<<<(uint32_t)((rows * 32 + 255) / 256), 256, 0, s>>>(c->d_q);
     c->iter_launches = 1;
-    c->fixed_launches += 2;
+    c->fixed_launches += 3;
     unsigned overflow = 0;
     unsigned long long items = 0;
     if (cudaGetLastError() != cudaSuccess ||
