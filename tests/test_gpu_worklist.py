@@ -65,3 +65,45 @@ def test_two_cycles_full_size_closed_form():
         assert got.shape == (p * qq, 2)
         assert np.array_equal(got, exp), nm
     assert q.count("A") == p and q.count("B") == qq
+
+
+def labelled_graph(n, edges, labels):
+    return synth.Graph(n=n, edges=np.asarray(edges, dtype=np.int64).reshape(-1, 3), labels=list(labels),
+                       meta={"kind": "test"})
+
+
+def test_period_one_chain_is_transitive_closure():
+    # S -> S B | B on a directed path: S is the left operand of its own production with the
+    # static B as partner (a chain of period 1 moving the column); R_S = all (i, j), i < j
+    n = 3000
+    graph = labelled_graph(n, [(i, 0, i + 1) for i in range(n - 1)], ["b"])
+    text = "S S B\nS b\nB b\n"
+    g, q = wl(graph, text)
+    assert q.count("S") == n * (n - 1) // 2
+    small = labelled_graph(300, [(i, 0, i + 1) for i in range(299)], ["b"])
+    parity(small, text)
+
+
+def test_chain_through_a_branch_and_a_merge():
+    # a b-path with a fork (node 700 has two b-successors) and a node of in-degree 2: the
+    # chain loses its unique successor at the fork, the general join takes over, and the two
+    # branches' chains meet pairs that are already set
+    n = 1500
+    e = [(i, 0, i + 1) for i in range(n - 1) if i != 1000]
+    e += [(700, 0, 1001), (1000, 0, 1200)]
+    e += [(i, 1, i) for i in range(0, n, 7)]  # a-loops: S seeds a b* on every seventh node
+    graph = labelled_graph(n, e, ["b", "a"])
+    parity(graph, "S S B\nS a\nB b\n")
+
+
+def test_period_two_chain_on_one_coordinate():
+    # S -> S1 C, S1 -> S B: both chain steps move the column (b then c), S = a (b c)*
+    n = 2401
+    e = [(i, 0 if i % 2 == 0 else 1, i + 1) for i in range(n - 1)]  # b, c, b, c, ...
+    e += [(i, 2, i) for i in range(0, n, 2)]  # a-loops at the even nodes
+    graph = labelled_graph(n, e, ["b", "c", "a"])
+    text = "S S1 C\nS1 S B\nS a\nB b\nC c\n"
+    g, q = wl(graph, text)
+    # (i, j) with i even and j = i + 2k, k >= 0
+    assert q.count("S") == sum((n - 1 - i) // 2 + 1 for i in range(0, n, 2))
+    parity(labelled_graph(401, e[:400] + [(i, 2, i) for i in range(0, 401, 2)], ["b", "c", "a"]), text)
