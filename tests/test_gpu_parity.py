@@ -229,3 +229,24 @@ def test_mma_sync_peaks_are_measured():
     p = eng.measure_mma_sync_peaks()
     # both are real device rates: far above zero, far below the FP8 tcgen05 peak (4.5 PF)
     assert 10.0 < p["s8_tops"] < 4500.0 and 10.0 < p["b1_tops"] < 40000.0
+
+
+def test_serving_workload_large_query_full_size():
+    # the served stream's n = 65536 Query 1 query (bit-packed, 7 x 512 MiB per plane set):
+    # every relation against the oracle, through the single-query path and through a server
+    graph = synth.hierarchy(65536, round(65536 * 0.3), seed=5)
+    ref = oracle.hellings(graph, synth.GRAMMAR_Q1)
+    g = eng.Grammar(synth.GRAMMAR_Q1, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, timeout_s=300.0)
+    q.solve()
+    for nm in g.names:
+        assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+    q.close()
+    srv = eng.Server(rounds_per_step=8)
+    t = srv.submit(g, graph.n, graph.edges)
+    while srv.stats()["completed"] + srv.stats()["failed"] < 1:
+        srv.step()
+    assert srv.info(t)["status"] == eng.OK
+    for nm in g.names:
+        assert np.array_equal(srv.result(t, g.id(nm)), ref.pairs(nm)), nm
+    srv.close()
