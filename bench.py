@@ -78,6 +78,25 @@ def parse():
 GRAMMARS = [("Q1", synth.GRAMMAR_Q1), ("QSC", synth.GRAMMAR_QSC)]
 
 
+def max_over_ranks(x: float, device: str = "cuda") -> float:
+    """The job's time: the slowest rank's (max over the default process group); the value
+    itself when there is no group (one process)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput of replicas: every rank processes its own units (weak scaling),
+    the job takes the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def workload():
     g = synth.hierarchy(N_NODES, N_CLASSES, seed=SEED)
     return g, list(GRAMMARS)
@@ -336,11 +355,8 @@ def engine_arm(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * ops_per_step / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms)
+    value = job_rate(ops_per_step, ms / 1e3, world) / 1e9
     executed_dense = sum(s["dense_ops"] for s in st)
     results = {f"{label}:{g.names[0]}": q.count(g.names[0]) for (label, _), g, q in zip(grammars, gs, main.qs)}
     main.close()
@@ -376,11 +392,8 @@ def engine_arm(args):
                 d2h += q.triples(nm).shape[0] * 12
             q.close()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = world * ops_per_step / e2e_s / 1e9
+    e2e_s = max_over_ranks(e2e_s)
+    e2e_val = job_rate(ops_per_step, e2e_s, world) / 1e9
 
     roof = roofline(eng, graph, gs, path, schedule, stream)
 
