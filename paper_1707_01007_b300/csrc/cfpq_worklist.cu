@@ -22,12 +22,15 @@
 namespace cfpq {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr int kWlWarps = 16, kWlThreads = 32 * kWlWarps;  // warp 0 runs the worklist, all 16 the chains
-constexpr int kLiftLevels = 17;          // powers 2^0 .. 2^16 of a period map
-constexpr int kPcSteps = 64, kPcBatch = 16;                 // a round: 512 threads x 64 steps
-constexpr uint32_t kPcRound = kWlThreads * kPcSteps;        // chain steps per round (a power of two)
-static_assert((kPcRound & (kPcRound - 1)) == 0 && (1u << (kLiftLevels - 1)) >= kPcRound, "power tables");
+constexpr int kWlWarps = 16, kWlThreads = 32 * kWlWarps;  // per block; block 0's warp 0 runs the worklist
+constexpr int kPcSteps = 64, kPcBatch = 16;                 // chain steps per thread and round
+constexpr uint32_t kPcBlockSteps = kWlThreads * kPcSteps;   // 32768 per block and round
+constexpr int kMaxPcBlocks = 128;                           // blocks a periodic round can span
+constexpr int kLiftLevels = 24;          // powers 2^0 .. 2^23 of a period map (covers 128 x 32768 steps)
+static_assert((1ull << (kLiftLevels - 1)) >= (unsigned long long)kMaxPcBlocks * kPcBlockSteps, "power tables");
 static_assert(kPcSteps % kPcBatch == 0, "batches");
+constexpr unsigned long long kPcRoundWaitNs = 5ull * 1000 * 1000 * 1000;   // a round never takes this long
+constexpr unsigned long long kPcIdleWaitNs = 600ull * 1000 * 1000 * 1000;  // helpers' wait for work
 
 // A periodic chain: from a pair of non-terminal a the chain goes a -> a1 -> a (P = 2) or
 // a -> a (P = 1), each step moving one coordinate of the pair through the unique-successor
@@ -58,6 +61,7 @@ struct WLDesc {
     const uint32_t *uniq;         // per static partner and direction: the only k, or 0xFFFFFFFF
     const PChain *pchain;         // [n_nt] periodic chain starting at a (P = 0: none)
     const uint32_t *lift;         // per periodic chain: kLiftLevels tables of n entries for G and H
+    struct PcCtl *pcc;            // periodic rounds: task and per-block results (device memory)
     uint32_t *stack;              // triples (a, i, j)
     uint64_t cap;                 // stack capacity in triples
     unsigned long long *items;    // pairs processed
@@ -88,50 +92,65 @@ __device__ __forceinline__ bool single_successor(const int4 *chain, const uint64
     return true;
 }
 
-enum : int32_t { kPcExit = 0, kPcFirst = 1, kPcNext = 2 };
+enum : int32_t { kPcIdle = 0, kPcRun = 1, kPcExit = 2 };
 
-struct PcTask {
+// Periodic rounds across blocks. Block 0's warp 0 (the worklist warp) posts a round: the
+// chain, the pair its steps start from, and how many blocks take part; every thread of
+// those blocks computes 64 consecutive steps (thread g of the grid: steps 64 g + 1 ..
+// 64 g + 64). Blocks 1.. wait for a new round number (one thread polls, bounded); block 0's
+// helper warps wait on a block barrier that warp 0 arrives at after posting. Each block
+// reports its count of valid and of new steps and its last valid pair; warp 0 waits until
+// all blocks of the round have reported (bounded) and decides how to continue.
+struct PcCtl {
+    unsigned gen, done, helpers_gone, pad;
+    int32_t cmd, active;
+    uint32_t a, i, j;             // the pair the round's steps start from
     PChain pc;
-    uint32_t a, i, j;  // the pair the round's steps start from (kPcFirst)
-    int32_t cmd;
+    uint32_t valid[kMaxPcBlocks], fresh[kMaxPcBlocks];
+    uint4 last[kMaxPcBlocks];     // (a, i, j, new) of the block's last valid step
 };
 
-__shared__ PcTask s_task;
 __shared__ uint32_t s_valid[kWlWarps], s_fresh[kWlWarps];
 __shared__ uint4 s_last[kWlThreads];  // each thread's last pair set (a, i, j, new)
+__shared__ int s_cmd;
 
 __device__ __forceinline__ void named_barrier(int id) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kWlThreads) : "memory");
 }
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
-struct PcLane {
-    uint32_t gi = 0, hj = 0;  // (G^u, H^u) of this thread's first step in the current round
-};
-
-// One thread's share of a periodic-chain round: steps 64 t + 1 .. 64 t + 64 from the task's
-// pair (thread t of the block). Writes the thread's last pair and the warp's counts.
-__device__ void pc_round(const QDesc &q, const WLDesc &w, const PcTask &task, PcLane &me) {
-    const PChain &pc = task.pc;
+// One thread's share of a round (thread g of the grid: steps 64 g + 1 .. 64 g + 64 from the
+// round's pair), then the block's counts and last valid pair into the control block. All
+// threads of the block call it.
+__device__ void pc_block_round(const QDesc &q, const WLDesc &w, PcCtl *c) {
+    // the task, read from L2 (it changes between rounds; the round was posted before the
+    // barrier that released this block)
+    PChain pc;
+    pc.P = __ldcg(&c->pc.P);
+    pc.a1 = __ldcg(&c->pc.a1);
+    pc.c0 = __ldcg(&c->pc.c0);
+    pc.g_id = __ldcg(&c->pc.g_id);
+    pc.h_id = __ldcg(&c->pc.h_id);
+    pc.m0 = __ldcg(reinterpret_cast<const unsigned long long *>(&c->pc.m0));
+    pc.lg = __ldcg(reinterpret_cast<const unsigned long long *>(&c->pc.lg));
+    pc.lh = __ldcg(reinterpret_cast<const unsigned long long *>(&c->pc.lh));
     const uint32_t n = q.n, P = (uint32_t)pc.P;
     const uint32_t *LG = w.lift + pc.lg, *LH = w.lift + pc.lh, *M0 = w.uniq + pc.m0;
-    const uint32_t a0 = task.a, a1 = (uint32_t)pc.a1;
-    const uint32_t t0 = threadIdx.x * (uint32_t)kPcSteps + 1u;
-    const uint32_t u0 = t0 / P, r0 = t0 % P;
-    if (task.cmd == kPcFirst) {
-        me.gi = task.i;
-        me.hj = task.j;
-        for (int k = 0; k < kLiftLevels; k++)
-            if ((u0 >> k) & 1u) {
-                if (!pc.g_id) me.gi = me.gi == kNone ? kNone : __ldg(LG + (uint64_t)k * n + me.gi);
-                if (!pc.h_id) me.hj = me.hj == kNone ? kNone : __ldg(LH + (uint64_t)k * n + me.hj);
-            }
-    } else {  // kPcNext: 32768 steps further along the same chain
-        const int jump = 31 - __clz(kPcRound / P);
-        if (!pc.g_id) me.gi = me.gi == kNone ? kNone : __ldg(LG + (uint64_t)jump * n + me.gi);
-        if (!pc.h_id) me.hj = me.hj == kNone ? kNone : __ldg(LH + (uint64_t)jump * n + me.hj);
-    }
-    uint32_t g = me.gi, h = me.hj, r = r0, valid = 0, fresh = 0;
-    uint32_t la = 0, li = 0, lj = 0, lnew = 0;
+    const uint32_t a0 = __ldcg(&c->a), a1 = (uint32_t)pc.a1;
+    const uint64_t t0 = ((uint64_t)blockIdx.x * kWlThreads + threadIdx.x) * (uint64_t)kPcSteps + 1u;
+    const uint64_t u0 = t0 / P;
+    uint32_t r = (uint32_t)(t0 % P);
+    uint32_t g = __ldcg(&c->i), h = __ldcg(&c->j);
+    for (int k = 0; k < kLiftLevels; k++)
+        if ((u0 >> k) & 1u) {
+            if (!pc.g_id) g = g == kNone ? kNone : __ldg(LG + (uint64_t)k * n + g);
+            if (!pc.h_id) h = h == kNone ? kNone : __ldg(LH + (uint64_t)k * n + h);
+        }
+    uint32_t valid = 0, fresh = 0, la = 0, li = 0, lj = 0, lnew = 0;
 #pragma unroll 1
     for (int b = 0; b < kPcSteps / kPcBatch; b++) {
         uint32_t pa[kPcBatch], pi[kPcBatch], pj[kPcBatch], old[kPcBatch];
@@ -185,6 +204,19 @@ __device__ void pc_round(const QDesc &q, const WLDesc &w, const PcTask &task, Pc
         s_valid[threadIdx.x >> 5] = valid;
         s_fresh[threadIdx.x >> 5] = fresh;
     }
+    named_barrier(2);
+    if (threadIdx.x == 0) {
+        uint32_t bv = 0, bf = 0;
+        for (int k = 0; k < kWlWarps; k++) {
+            bv += s_valid[k];
+            bf += s_fresh[k];
+        }
+        c->valid[blockIdx.x] = bv;
+        c->fresh[blockIdx.x] = bf;
+        c->last[blockIdx.x] = bv ? s_last[(bv - 1u) / kPcSteps] : make_uint4(0, 0, 0, 0);
+        __threadfence();
+        atomicAdd(&c->done, 1u);
+    }
 }
 
 // Warp 0 processes the stack until it is empty, the deadline passes or it overflows; the
@@ -198,16 +230,47 @@ __device__ void pc_round(const QDesc &q, const WLDesc &w, const PcTask &task, Pc
 __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLDesc w, unsigned long long top0) {
     const QDesc &q = *qd;
     const int lane = threadIdx.x & 31;
+    PcCtl *pcc = w.pcc;
+    if (blockIdx.x > 0) {
+        // helper block: one share of every round it is asked to take part in
+        unsigned seen = 0;
+        const unsigned long long dl = ld_u64(&q.st->deadline_ns);
+        for (;;) {
+            if (threadIdx.x == 0) {
+                int cmd = kPcExit;
+                const unsigned long long t0 = globaltimer_ns();
+                for (;;) {
+                    const unsigned gnow = ld_acquire(&pcc->gen);
+                    if (gnow != seen) {
+                        seen = gnow;
+                        cmd = (int)__ldcg(&pcc->cmd);
+                        if (cmd == kPcRun && (int)blockIdx.x >= __ldcg(&pcc->active)) cmd = kPcIdle;
+                        break;
+                    }
+                    const unsigned long long now = globaltimer_ns();
+                    if (now - t0 > kPcIdleWaitNs || (dl && now > dl)) {
+                        atomicExch(&pcc->helpers_gone, 1u);  // rounds continue on block 0 alone
+                        break;
+                    }
+                    __nanosleep(200);
+                }
+                s_cmd = cmd;
+            }
+            __syncthreads();
+            const int cmd = s_cmd;
+            __syncthreads();
+            if (cmd == kPcExit) return;
+            if (cmd == kPcRun) pc_block_round(q, w, pcc);
+        }
+    }
     if (threadIdx.x >= 32) {
-        // helper warps: one share of every periodic-chain round, until warp 0 is done
-        PcLane me;
+        // block 0's helper warps: released by warp 0 after it posts a round
         for (;;) {
             named_barrier(1);
-            if (s_task.cmd == kPcExit) break;
-            pc_round(q, w, s_task, me);
-            named_barrier(2);
+            const int cmd = (int)__ldcg(&pcc->cmd);
+            if (cmd == kPcExit) return;
+            pc_block_round(q, w, pcc);
         }
-        return;
     }
     unsigned long long top = top0, processed = 0;
     uint32_t ca = 0, ci = 0, cj = 0;  // item handed over in registers
@@ -241,49 +304,74 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
             break;
         }
         if (!skip_fast && s_pc[ca].P > 0) {
-            // periodic chain, all 16 warps of the block: 32768 steps per round, each thread 64
-            // consecutive ones with 16 atomics in flight; thread positions jump 32768 steps
-            // ahead between rounds through the power tables, so a round costs no dependent
-            // walk of the chain. A step with no unique successor ends the chain: the last
-            // pair set then goes to the general join below (it may have several successors).
+            // periodic chain: rounds of 32768 steps per block over 1, 2, 4, .. blocks (up to
+            // the grid), every thread 64 consecutive steps computed from the round's first pair
+            // by binary lifting, with 16 atomics in flight; no dependent walk of the chain. A
+            // step with no unique successor ends the chain: the last pair set then goes to the
+            // general join below (it may have several successors, or none).
             bool handled = false;  // false: (ca, ci, cj) still needs the general join
-            if (lane == 0) {
-                s_task.pc = s_pc[ca];
-                s_task.a = ca;
-                s_task.i = ci;
-                s_task.j = cj;
-                s_task.cmd = kPcFirst;
-            }
-            __syncwarp();
-            PcLane me;
+            int active = 1;
             for (;;) {
-                named_barrier(1);  // helpers start the round
-                pc_round(q, w, s_task, me);
-                named_barrier(2);  // every thread's share is done
+                if (__ldcg(&pcc->helpers_gone)) active = 1;
+                if (lane == 0) {
+                    pcc->pc = s_pc[ca];
+                    pcc->a = ca;
+                    pcc->i = ci;
+                    pcc->j = cj;
+                    pcc->cmd = kPcRun;
+                    pcc->active = active;
+                    pcc->done = 0u;
+                    __threadfence();
+                    atomicAdd(&pcc->gen, 1u);
+                }
+                __syncwarp();
+                named_barrier(1);          // block 0's helper warps start
+                pc_block_round(q, w, pcc); // block 0's share (warp 0 included)
+                int ok = 1;
+                if (lane == 0) {
+                    const unsigned long long t0 = globaltimer_ns();
+                    while (ld_acquire(&pcc->done) < (unsigned)active) {
+                        if (globaltimer_ns() - t0 > kPcRoundWaitNs) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(100);
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    if (lane == 0) q.st->error = kErrTimeout;
+                    timed_out = true;
+                    break;
+                }
                 unsigned tot_valid = 0, tot_fresh = 0;
-                for (int k = 0; k < kWlWarps; k++) {
-                    tot_valid += s_valid[k];
-                    tot_fresh += s_fresh[k];
+                for (int b = lane; b < active; b += 32) {
+                    tot_valid += __ldcg(&pcc->valid[b]);
+                    tot_fresh += __ldcg(&pcc->fresh[b]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    tot_valid += __shfl_xor_sync(0xffffffffu, tot_valid, o);
+                    tot_fresh += __shfl_xor_sync(0xffffffffu, tot_fresh, o);
                 }
                 processed += tot_valid;
                 if (tot_fresh && lane == 0) atomicAdd(&q.st->new_bits, (unsigned long long)tot_fresh);
                 if (tot_valid == 0) break;  // (ca, ci, cj) has no unique successor: general join
-                // the last pair set: held by the thread of step tot_valid
-                const int src = (int)((tot_valid - 1u) / kPcSteps);
-                const uint32_t ea = s_last[src].x, ei = s_last[src].y, ej = s_last[src].z;
-                const bool enew = s_last[src].w != 0;
-                if (tot_valid < kPcRound) {
+                // the last pair set: reported by the block of step tot_valid
+                const uint4 e = __ldcg(&pcc->last[(tot_valid - 1u) / kPcBlockSteps]);
+                const unsigned long long round_steps = (unsigned long long)active * kPcBlockSteps;
+                if (tot_valid < round_steps) {
                     handled = true;
-                    if (enew) {
-                        ca = ea;
-                        ci = ei;
-                        cj = ej;
+                    if (e.w) {
+                        ca = e.x;
+                        ci = e.y;
+                        cj = e.z;
                         have = true;
                         force_general = true;
                     }
                     break;
                 }
-                if (!enew) {
+                if (!e.w) {
                     handled = true;  // the pair was already set: whoever set it continues
                     break;
                 }
@@ -293,12 +381,10 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
                     timed_out = true;
                     break;
                 }
-                ca = ea;  // continue from the round's last pair
-                ci = ei;
-                cj = ej;
-                __syncwarp();
-                if (lane == 0) s_task.cmd = kPcNext;
-                __syncwarp();
+                ca = e.x;  // continue from the round's last pair, on twice as many blocks
+                ci = e.y;
+                cj = e.z;
+                active = min(2 * active, (int)gridDim.x);
             }
             if (timed_out) break;
             if (handled) continue;
@@ -377,8 +463,21 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
             } else {
                 const uint32_t *row = left ? q.T + (uint64_t)p * q.plane + (uint64_t)key * q.W
                                            : q.TT + (uint64_t)p * q.plane + (uint64_t)key * q.W;
+                uint32_t *dst_row = q.T + (uint64_t)x * q.plane + (uint64_t)ci * q.W;
                 for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
                     uint32_t bits = (w0 + lane < q.W) ? __ldcg(row + w0 + lane) : 0u;
+                    if (left && bits) {
+                        // the derived pairs (x, ci, k) fill row ci of T_x: one word-wide OR
+                        // per 32 of them, and only the bits that were not set yet go on
+                        const uint32_t old = atomicOr(dst_row + w0 + lane, bits);
+                        bits &= ~old;
+                        if (bits && w.needs_tt[x]) {
+                            for (uint32_t nb = bits; nb; nb &= nb - 1) {
+                                const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(nb) - 1);
+                                atomicOr(&q.TT[(uint64_t)x * q.plane + (uint64_t)k * q.W + (ci >> 5)], 1u << (ci & 31));
+                            }
+                        }
+                    }
                     while (__any_sync(0xffffffffu, bits != 0)) {
                         bool nw = false;
                         uint32_t a = 0, b = 0;
@@ -387,7 +486,7 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
                             bits &= bits - 1;
                             a = left ? ci : k;
                             b = left ? k : cj;
-                            nw = wl_set(q, w, x, a, b);
+                            nw = left ? true : wl_set(q, w, x, a, b);  // left: already set and new
                         }
                         const unsigned m = __ballot_sync(0xffffffffu, nw);
                         if (m) {
@@ -431,10 +530,12 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
     if (lane == 0) {
         *w.items = processed;
         q.st->iter = 1;
-        s_task.cmd = kPcExit;
+        pcc->cmd = kPcExit;
+        __threadfence();
+        atomicAdd(&pcc->gen, 1u);  // helper blocks leave
     }
     __syncwarp();
-    named_barrier(1);  // releases the helpers, which see kPcExit
+    named_barrier(1);  // block 0's helper warps see kPcExit and leave
 }
 
 // After the walk: the row bitmap of every T_a (extraction visits only non-empty rows), rebuilt
@@ -483,6 +584,7 @@ struct WorklistState {
     WLDesc d;
     void *arena = nullptr;
     unsigned long long *d_top = nullptr;
+    int blocks = 1;  // grid of the walk: periodic chains use up to kMaxPcBlocks blocks
 };
 
 int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
@@ -626,6 +728,7 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
                           {(void **)&d.uniq, uniq.size() * 4 + 8},
                           {(void **)&d.pchain, (size_t)n_nt * sizeof(PChain)},
                           {(void **)&d.lift, lift.size() * 4 + 8},
+                          {(void **)&d.pcc, sizeof(PcCtl)},
                           {(void **)&d.stack, cap * 12},
                           {(void **)&d.items, 8},
                           {(void **)&d.overflow, 8},
@@ -644,6 +747,20 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
         ptr += (p.bytes + 255) / 256 * 256;
     }
     d.cap = cap;
+    bool any_periodic = false;
+    for (const PChain &pc : pchain) any_periodic |= pc.P > 0;
+    if (any_periodic) {
+        // every block of the grid must be resident at once (cooperative launch)
+        int dev = 0, sms = 0, per_sm = 0, coop = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_worklist, kWlThreads, 0) == cudaSuccess) {
+            const int fit = std::min(kMaxPcBlocks, sms * std::max(per_sm, 0));
+            while (ws->blocks * 2 <= fit) ws->blocks *= 2;
+        }
+        cudaGetLastError();
+    }
     cudaStream_t s = c->stream;
     bool ok = true;
     auto up = [&](const void *dst, const void *src, size_t bytes) {
@@ -690,6 +807,7 @@ int worklist_run(cfpq_ctx *c, cudaStream_t s) {
     if (!ws) return CFPQ_ERR_UNSUPPORTED;
     WLDesc &d = ws->d;
     if (cudaMemsetAsync(ws->d_top, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d.overflow, 0, 8, s) != cudaSuccess ||
+        cudaMemsetAsync(d.pcc, 0, sizeof(PcCtl), s) != cudaSuccess ||
         cudaMemsetAsync(c->d_TT, 0, (size_t)c->n_nt * c->plane * 4, s) != cudaSuccess)
         return CFPQ_ERR_CUDA;
     const uint64_t rows = (uint64_t)c->n_nt * c->n;
@@ -699,7 +817,15 @@ int worklist_run(cfpq_ctx *c, cudaStream_t s) {
         cudaStreamSynchronize(s) != cudaSuccess)
         return CFPQ_ERR_CUDA;
     if (top > d.cap) return CFPQ_ERR_NOMEM;
-    k_worklist<<<1, kWlThreads, 0, s>>>(c->d_q, d, top);
+    {
+        const QDesc *qd = c->d_q;
+        void *args[] = {(void *)&qd, (void *)&d, (void *)&top};
+        const cudaError_t e = ws->blocks > 1
+                                  ? cudaLaunchCooperativeKernel((const void *)k_worklist, dim3(ws->blocks),
+                                                                dim3(kWlThreads), args, 0, s)
+                                  : cudaLaunchKernel((const void *)k_worklist, dim3(1), dim3(kWlThreads), args, 0, s);
+        if (e != cudaSuccess) return CFPQ_ERR_CUDA;
+    }
     k_worklist_rows<<<(uint32_t)((rows * 32 + 255) / 256), 256, 0, s>>>(c->d_q);
     c->iter_launches = 1;
     c->fixed_launches += 3;
