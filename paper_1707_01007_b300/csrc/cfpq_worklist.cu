@@ -464,8 +464,19 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
                 const uint32_t *row = left ? q.T + (uint64_t)p * q.plane + (uint64_t)key * q.W
                                            : q.TT + (uint64_t)p * q.plane + (uint64_t)key * q.W;
                 uint32_t *dst_row = q.T + (uint64_t)x * q.plane + (uint64_t)ci * q.W;
+                uint32_t *dst_col = q.TT + (uint64_t)x * q.plane + (uint64_t)cj * q.W;  // column cj of T_x
                 for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
                     uint32_t bits = (w0 + lane < q.W) ? __ldcg(row + w0 + lane) : 0u;
+                    if (!left && bits) {
+                        // the derived pairs (x, k, cj) fill column cj of T_x: one word-wide OR
+                        // into T_x^T per 32 of them; the new ones are then set in T_x
+                        const uint32_t old = atomicOr(dst_col + w0 + lane, bits);
+                        bits &= ~old;
+                        for (uint32_t nb = bits; nb; nb &= nb - 1) {
+                            const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(nb) - 1);
+                            atomicOr(&q.T[(uint64_t)x * q.plane + (uint64_t)k * q.W + (cj >> 5)], 1u << (cj & 31));
+                        }
+                    }
                     if (left && bits) {
                         // the derived pairs (x, ci, k) fill row ci of T_x: one word-wide OR
                         // per 32 of them, and only the bits that were not set yet go on
@@ -486,7 +497,7 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
                             bits &= bits - 1;
                             a = left ? ci : k;
                             b = left ? k : cj;
-                            nw = left ? true : wl_set(q, w, x, a, b);  // left: already set and new
+                            nw = true;  // set above, and new
                         }
                         const unsigned m = __ballot_sync(0xffffffffu, nw);
                         if (m) {
@@ -592,8 +603,9 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
     const uint32_t n = c->n;
     std::vector<int32_t> is_static(n_nt, 1), needs_tt(n_nt, 0);
     for (const Rule &r : c->rules) is_static[r.lhs] = 0;
-    for (const Rule &r : c->rules)
-        if (!is_static[r.b]) needs_tt[r.b] = 1;
+    // T^T is kept for every derived non-terminal: right-operand joins read T_p^T of a dynamic
+    // left partner p, and OR word-wide into T_x^T to find which derived pairs are new
+    for (int a = 0; a < n_nt; a++) needs_tt[a] = is_static[a] ? 0 : 1;
     // occurrences of each non-terminal as an operand
     std::vector<std::vector<int2>> occ(n_nt);
     for (size_t k = 0; k < c->rules.size(); k++) {
