@@ -219,6 +219,142 @@ __device__ void pc_block_round(const QDesc &q, const WLDesc &w, PcCtl *c) {
     }
 }
 
+// Stack push of the new pairs of a ballot m (lane l holds pair (x, a, b) if bit l is set).
+// With handoff, the first new pair of the join is kept in (ha, hi, hj) instead of pushed.
+// shared_top: when set, stack slots are reserved with an atomic on it (several warps push
+// at once); otherwise the warp's own top is used.
+__device__ __forceinline__ void push_new(const WLDesc &w, unsigned m, uint32_t x, uint32_t a, uint32_t b,
+                                         unsigned long long &top, unsigned long long *shared_top, bool handoff,
+                                         uint32_t &n_new, uint32_t &ha, uint32_t &hi, uint32_t &hj, int lane) {
+    if (!m) return;
+    unsigned push = m;
+    if (handoff && n_new == 0) {
+        const int first = __ffs(m) - 1;
+        ha = x;
+        hi = __shfl_sync(0xffffffffu, a, first);
+        hj = __shfl_sync(0xffffffffu, b, first);
+        push = m & (m - 1);
+    }
+    if (push) {
+        const unsigned cnt = __popc(push);
+        unsigned long long base = top;
+        if (shared_top) {
+            if (lane == 0) base = atomicAdd(shared_top, (unsigned long long)cnt);
+            base = __shfl_sync(0xffffffffu, base, 0);
+        } else {
+            top += cnt;
+        }
+        if ((push >> lane) & 1u) {
+            const unsigned long long pos = base + __popc(push & ((1u << lane) - 1u));
+            if (pos < w.cap) {
+                w.stack[3 * pos] = x;
+                w.stack[3 * pos + 1] = a;
+                w.stack[3 * pos + 2] = b;
+            }
+        }
+    }
+    n_new += __popc(m);
+}
+
+// The general join of one popped pair (ca, ci, cj) by one warp: through every occurrence of
+// ca as an operand, with the partner's CSR (static partner) or bit rows (dynamic partner).
+// Returns the number of new pairs.
+__device__ uint32_t general_join(const QDesc &q, const WLDesc &w, uint32_t ca, uint32_t ci, uint32_t cj,
+                                 unsigned long long &top, unsigned long long *shared_top, bool handoff, uint32_t &ha,
+                                 uint32_t &hi, uint32_t &hj, int lane) {
+    uint32_t n_new = 0;
+    for (int o = w.occ_start[ca]; o < w.occ_start[ca + 1]; o++) {
+        const int2 oc = w.occ[o];
+        const Rule r = q.rules[oc.x];
+        const int x = r.lhs;
+        const bool left = oc.y == 0;
+        const int p = left ? r.c : r.b;        // partner non-terminal
+        const uint32_t key = left ? cj : ci;   // row of T_p (left) or of T_p^T (right)
+        if (w.is_static[p]) {
+            const uint64_t base = left ? w.out_base[p] : w.in_base[p];
+            const uint32_t lo = __ldg(w.csr_off + base + key), hi_ = __ldg(w.csr_off + base + key + 1);
+            for (uint32_t e0 = lo; e0 < hi_; e0 += 32) {
+                const uint32_t e = e0 + lane;
+                bool nw = false;
+                uint32_t a = 0, b = 0;
+                if (e < hi_) {
+                    const uint32_t k = __ldg(w.csr_col + e);
+                    a = left ? ci : k;
+                    b = left ? k : cj;
+                    nw = wl_set(q, w, x, a, b);
+                }
+                push_new(w, __ballot_sync(0xffffffffu, nw), (uint32_t)x, a, b, top, shared_top, handoff, n_new, ha,
+                         hi, hj, lane);
+            }
+        } else {
+            const uint32_t *row = left ? q.T + (uint64_t)p * q.plane + (uint64_t)key * q.W
+                                       : q.TT + (uint64_t)p * q.plane + (uint64_t)key * q.W;
+            uint32_t *dst_row = q.T + (uint64_t)x * q.plane + (uint64_t)ci * q.W;
+            uint32_t *dst_col = q.TT + (uint64_t)x * q.plane + (uint64_t)cj * q.W;  // column cj of T_x
+            for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
+                uint32_t bits = (w0 + lane < q.W) ? __ldcg(row + w0 + lane) : 0u;
+                if (!left && bits) {
+                    // the derived pairs (x, k, cj) fill column cj of T_x: one word-wide OR
+                    // into T_x^T per 32 of them; the new ones are then set in T_x
+                    const uint32_t old = atomicOr(dst_col + w0 + lane, bits);
+                    bits &= ~old;
+                    for (uint32_t nb = bits; nb; nb &= nb - 1) {
+                        const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(nb) - 1);
+                        atomicOr(&q.T[(uint64_t)x * q.plane + (uint64_t)k * q.W + (cj >> 5)], 1u << (cj & 31));
+                    }
+                }
+                if (left && bits) {
+                    // the derived pairs (x, ci, k) fill row ci of T_x: one word-wide OR
+                    // per 32 of them, and only the bits that were not set yet go on
+                    const uint32_t old = atomicOr(dst_row + w0 + lane, bits);
+                    bits &= ~old;
+                    if (bits && w.needs_tt[x]) {
+                        for (uint32_t nb = bits; nb; nb &= nb - 1) {
+                            const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(nb) - 1);
+                            atomicOr(&q.TT[(uint64_t)x * q.plane + (uint64_t)k * q.W + (ci >> 5)], 1u << (ci & 31));
+                        }
+                    }
+                }
+                while (__any_sync(0xffffffffu, bits != 0)) {
+                    bool nw = false;
+                    uint32_t a = 0, b = 0;
+                    if (bits) {
+                        const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(bits) - 1);
+                        bits &= bits - 1;
+                        a = left ? ci : k;
+                        b = left ? k : cj;
+                        nw = true;  // set above, and new
+                    }
+                    push_new(w, __ballot_sync(0xffffffffu, nw), (uint32_t)x, a, b, top, shared_top, handoff,
+                             n_new, ha, hi, hj, lane);
+                }
+            }
+        }
+    }
+    return n_new;
+}
+
+enum : int32_t { kBlkExit = 0, kBlkRound = 1, kBlkJoin = 2 };
+constexpr uint32_t kJoinBatch = 64;  // general items joined together by block 0's 16 warps
+__shared__ uint4 s_batch[kJoinBatch];
+__shared__ uint32_t s_nbatch;
+__shared__ unsigned long long s_top;
+__shared__ int s_block_cmd;
+
+// A batch of general items (posted by warp 0 in s_batch): warp k of block 0 joins items
+// k, k + 16, ..; new pairs go on the stack through the shared top.
+__device__ void join_batch(const QDesc &q, const WLDesc &w) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t fresh = 0;
+    for (uint32_t k = (uint32_t)warp; k < s_nbatch; k += kWlWarps) {
+        const uint4 it = s_batch[k];
+        unsigned long long unused = 0;
+        uint32_t ha, hi, hj;
+        fresh += general_join(q, w, it.x, it.y, it.z, unused, &s_top, false, ha, hi, hj, lane);
+    }
+    if (fresh && lane == 0) atomicAdd(&q.st->new_bits, (unsigned long long)fresh);
+}
+
 // Warp 0 processes the stack until it is empty, the deadline passes or it overflows; the
 // other warps help with periodic chains.
 // Chain lookahead (warp 0 alone): when the current pair has a single successor through static operands,
@@ -264,12 +400,17 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
         }
     }
     if (threadIdx.x >= 32) {
-        // block 0's helper warps: released by warp 0 after it posts a round
+        // block 0's helper warps: released by warp 0 for a periodic round or a join batch
         for (;;) {
             named_barrier(1);
-            const int cmd = (int)__ldcg(&pcc->cmd);
-            if (cmd == kPcExit) return;
-            pc_block_round(q, w, pcc);
+            const int cmd = s_block_cmd;
+            if (cmd == kBlkExit) return;
+            if (cmd == kBlkRound) {
+                pc_block_round(q, w, pcc);
+            } else {
+                join_batch(q, w);
+                named_barrier(2);
+            }
         }
     }
     unsigned long long top = top0, processed = 0;
@@ -323,6 +464,7 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
                     pcc->done = 0u;
                     __threadfence();
                     atomicAdd(&pcc->gen, 1u);
+                    s_block_cmd = kBlkRound;
                 }
                 __syncwarp();
                 named_barrier(1);          // block 0's helper warps start
@@ -414,118 +556,42 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
                 continue;
             }
         }
-        uint32_t n_new = 0, ha = 0, hi = 0, hj = 0;
-        for (int o = w.occ_start[ca]; o < w.occ_start[ca + 1]; o++) {
-            const int2 oc = w.occ[o];
-            const Rule r = q.rules[oc.x];
-            const int x = r.lhs;
-            const bool left = oc.y == 0;
-            const int p = left ? r.c : r.b;        // partner non-terminal
-            const uint32_t key = left ? cj : ci;   // row of T_p (left) or of T_p^T (right)
-            if (w.is_static[p]) {
-                const uint64_t base = left ? w.out_base[p] : w.in_base[p];
-                const uint32_t lo = __ldg(w.csr_off + base + key), hi_ = __ldg(w.csr_off + base + key + 1);
-                for (uint32_t e0 = lo; e0 < hi_; e0 += 32) {
-                    const uint32_t e = e0 + lane;
-                    bool nw = false;
-                    uint32_t a = 0, b = 0;
-                    if (e < hi_) {
-                        const uint32_t k = __ldg(w.csr_col + e);
-                        a = left ? ci : k;
-                        b = left ? k : cj;
-                        nw = wl_set(q, w, x, a, b);
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, nw);
-                    if (m) {
-                        const int first = __ffs(m) - 1;
-                        if (n_new == 0 && __popc(m) >= 1) {
-                            ha = (uint32_t)x;
-                            hi = __shfl_sync(0xffffffffu, a, first);
-                            hj = __shfl_sync(0xffffffffu, b, first);
-                        }
-                        // every new pair but the one kept in registers goes on the stack
-                        const unsigned push = (n_new == 0) ? (m & (m - 1)) : m;
-                        if (push) {
-                            const unsigned before = __popc(push & ((1u << lane) - 1u));
-                            if ((push >> lane) & 1u) {
-                                const unsigned long long pos = top + before;
-                                if (pos < w.cap) {
-                                    w.stack[3 * pos] = (uint32_t)x;
-                                    w.stack[3 * pos + 1] = a;
-                                    w.stack[3 * pos + 2] = b;
-                                }
-                            }
-                            top += __popc(push);
-                        }
-                        n_new += __popc(m);
-                    }
-                }
-            } else {
-                const uint32_t *row = left ? q.T + (uint64_t)p * q.plane + (uint64_t)key * q.W
-                                           : q.TT + (uint64_t)p * q.plane + (uint64_t)key * q.W;
-                uint32_t *dst_row = q.T + (uint64_t)x * q.plane + (uint64_t)ci * q.W;
-                uint32_t *dst_col = q.TT + (uint64_t)x * q.plane + (uint64_t)cj * q.W;  // column cj of T_x
-                for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
-                    uint32_t bits = (w0 + lane < q.W) ? __ldcg(row + w0 + lane) : 0u;
-                    if (!left && bits) {
-                        // the derived pairs (x, k, cj) fill column cj of T_x: one word-wide OR
-                        // into T_x^T per 32 of them; the new ones are then set in T_x
-                        const uint32_t old = atomicOr(dst_col + w0 + lane, bits);
-                        bits &= ~old;
-                        for (uint32_t nb = bits; nb; nb &= nb - 1) {
-                            const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(nb) - 1);
-                            atomicOr(&q.T[(uint64_t)x * q.plane + (uint64_t)k * q.W + (cj >> 5)], 1u << (cj & 31));
-                        }
-                    }
-                    if (left && bits) {
-                        // the derived pairs (x, ci, k) fill row ci of T_x: one word-wide OR
-                        // per 32 of them, and only the bits that were not set yet go on
-                        const uint32_t old = atomicOr(dst_row + w0 + lane, bits);
-                        bits &= ~old;
-                        if (bits && w.needs_tt[x]) {
-                            for (uint32_t nb = bits; nb; nb &= nb - 1) {
-                                const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(nb) - 1);
-                                atomicOr(&q.TT[(uint64_t)x * q.plane + (uint64_t)k * q.W + (ci >> 5)], 1u << (ci & 31));
-                            }
-                        }
-                    }
-                    while (__any_sync(0xffffffffu, bits != 0)) {
-                        bool nw = false;
-                        uint32_t a = 0, b = 0;
-                        if (bits) {
-                            const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(bits) - 1);
-                            bits &= bits - 1;
-                            a = left ? ci : k;
-                            b = left ? k : cj;
-                            nw = true;  // set above, and new
-                        }
-                        const unsigned m = __ballot_sync(0xffffffffu, nw);
-                        if (m) {
-                            const int first = __ffs(m) - 1;
-                            if (n_new == 0) {
-                                ha = (uint32_t)x;
-                                hi = __shfl_sync(0xffffffffu, a, first);
-                                hj = __shfl_sync(0xffffffffu, b, first);
-                            }
-                            const unsigned push = (n_new == 0) ? (m & (m - 1)) : m;
-                            if (push) {
-                                const unsigned before = __popc(push & ((1u << lane) - 1u));
-                                if ((push >> lane) & 1u) {
-                                    const unsigned long long pos = top + before;
-                                    if (pos < w.cap) {
-                                        w.stack[3 * pos] = (uint32_t)x;
-                                        w.stack[3 * pos + 1] = a;
-                                        w.stack[3 * pos + 2] = b;
-                                    }
-                                }
-                                top += __popc(push);
-                            }
-                            n_new += __popc(m);
-                        }
-                    }
+        uint32_t ha = 0, hi = 0, hj = 0;
+        uint32_t n_new = 0;
+        {
+            // more general items right below on the stack: join them in one batch on all warps
+            uint32_t nb = 1;
+            if (lane == 0) {
+                s_batch[0] = make_uint4(ca, ci, cj, 0);
+                while (nb < kJoinBatch && top > 0) {
+                    const uint32_t xa = w.stack[3 * (top - 1)];
+                    if (s_pc[xa].P > 0 || s_chain[xa].x) break;  // chains stay with this warp
+                    top--;
+                    s_batch[nb++] = make_uint4(xa, w.stack[3 * top + 1], w.stack[3 * top + 2], 0);
                 }
             }
+            nb = __shfl_sync(0xffffffffu, nb, 0);
+            top = __shfl_sync(0xffffffffu, top, 0);
+            if (nb > 1) {
+                processed += nb - 1;
+                if (lane == 0) {
+                    s_nbatch = nb;
+                    s_top = top;
+                    s_block_cmd = kBlkJoin;
+                }
+                __syncwarp();
+                named_barrier(1);  // block 0's helper warps join the batch too
+                join_batch(q, w);
+                named_barrier(2);
+                top = s_top;
+                if (top > w.cap) {
+                    if (lane == 0) atomicExch(w.overflow, 1u);
+                    break;
+                }
+                continue;
+            }
         }
+        n_new = general_join(q, w, ca, ci, cj, top, nullptr, true, ha, hi, hj, lane);
         if (top > w.cap) {
             if (lane == 0) atomicExch(w.overflow, 1u);
             break;
@@ -544,6 +610,7 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
         pcc->cmd = kPcExit;
         __threadfence();
         atomicAdd(&pcc->gen, 1u);  // helper blocks leave
+        s_block_cmd = kBlkExit;
     }
     __syncwarp();
     named_barrier(1);  // block 0's helper warps see kPcExit and leave
