@@ -570,12 +570,21 @@ def cycles_arm(args):
     ok = qy.count("S") == p * q and qy.count("S1") == p * q
     st = qy.stats()
     ms = float(np.median(times))
+    # the automatic path on the same input: matrix loop, then the hand-over to the worklist
+    qa = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, timeout_s=600.0)
+    qa.solve(stream)
+    auto_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        qa.solve(stream)
+        auto_times.append(qa.stats()["solve_ms"])
+    auto = {"ms": float(np.median(auto_times)), "loop_executions_before_hand_over": qa.stats()["iterations"],
+            "closed_form_count_ok": bool(qa.count("S") == p * q)}
     line = {"metric": "two-cycle closure time (worklist path)", "value": ms / 1e3, "unit": "s", "n_gpus": 1,
             "steps": len(times), "warmup": 1, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
             "config": {"workload": f"two cycles {p} / {q} sharing node 0, S -> a S b | a b (n = {graph.n})"},
             "pairs_S": qy.count("S"), "closed_form_count_ok": bool(ok), "worklist_items": st["worklist_items"],
-            "ns_per_item": ms * 1e6 / max(1, st["worklist_items"])}
+            "ns_per_item": ms * 1e6 / max(1, st["worklist_items"]), "automatic_path": auto}
     if not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()

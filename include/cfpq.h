@@ -83,7 +83,10 @@ enum cfpq_schedule {
 enum cfpq_path {
     CFPQ_PATH_AUTO = 0,       /* per production group and loop execution, the cheaper of the two
                                  below, chosen on the device from the current pair counts (falls
-                                 back to GATHER where tensor cores are not available) */
+                                 back to GATHER where tensor cores are not available); unless the
+                                 schedule is JACOBI, 256 executions in a row that add at most 8
+                                 pairs each end the loop and the WORKLIST path finishes the
+                                 closure (cfpq_stats.iterations: the executions before that) */
     CFPQ_PATH_TENSOR = 1,     /* dense tcgen05 product of every production, every iteration */
     CFPQ_PATH_GATHER = 2,     /* CUDA-core bit-gather over changed bits only (semi-naive) */
     CFPQ_PATH_WORKLIST = 3    /* one warp joins each new pair with its partners (semi-naive at the

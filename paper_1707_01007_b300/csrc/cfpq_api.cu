@@ -765,6 +765,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         c->group_tensor.assign(std::max(1, c->n_groups), 1);
     }
     c->auto_mixed = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && tensor_path_available();
+    c->allow_switch = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && c->schedule_req != CFPQ_SCHED_JACOBI;
+    if (c->allow_switch) c->h_edges.assign(edges, edges + n_edges);
     c->any_gather = c->n_groups > 0 && c->path != CFPQ_PATH_TENSOR && c->path != CFPQ_PATH_WORKLIST;
     {
         int cpl;
@@ -799,7 +801,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
     const size_t rowsz = (size_t)c->n_nt * c->W * sizeof(uint32_t);
     const size_t cells = (size_t)c->n_nt * c->n_pad;  // (non-terminal, row) extraction cells
-    const bool want_tt = (c->path == CFPQ_PATH_WORKLIST) ||
+    const bool want_tt = (c->path == CFPQ_PATH_WORKLIST) || c->allow_switch ||
                          ((c->path == CFPQ_PATH_AUTO || c->path == CFPQ_PATH_TENSOR) && tensor_path_available());
     struct Part { void **dst; size_t bytes; };
     const Part parts[] = {
@@ -850,6 +852,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.n_groups = c->n_groups;
     q.schedule = c->schedule;
     q.profile = c->profile;
+    q.allow_switch = c->allow_switch ? 1 : 0;
     q.n_unary = c->n_unary;
     q.n_eps = c->n_eps_rules;
     q.plane = c->plane;
@@ -1016,6 +1019,24 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
     CK(cudaEventRecord(c->ev1, s));
     rc = read_status(c, s);
     if (rc == CFPQ_ERR_CUDA) return rc;
+    c->switched = false;
+    if (rc == CFPQ_OK && c->allow_switch) {
+        // the loop stopped after a long run of tiny deltas: the worklist path finishes the
+        // closure from the current delta (same least fixpoint)
+        unsigned to_wl = 0;
+        CK(cudaMemcpyAsync(&to_wl, &c->d_state->to_worklist, sizeof(to_wl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (to_wl) {
+            if (!c->h_wl && (rc = worklist_setup(c, c->h_edges.data(), c->h_edges.size())) != CFPQ_OK) return rc;
+            const int64_t loops = c->stats.iterations;
+            if ((rc = worklist_run(c, s, true)) != CFPQ_OK) return rc;
+            CK(cudaEventRecord(c->ev1, s));
+            rc = read_status(c, s);
+            if (rc == CFPQ_ERR_CUDA) return rc;
+            c->stats.iterations = loops;  // loop executions before the hand-over
+            c->switched = true;
+        }
+    }
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     c->stats.solve_ms = ms;

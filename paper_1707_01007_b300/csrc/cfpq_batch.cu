@@ -466,6 +466,7 @@ static bool tuning_valid(const cfpq_batch_tuning &t) {
 void fill_batch_query(const cfpq_ctx *c, BatchQuery *b, int init, const cfpq_batch_tuning &t) {
     memset(b, 0, sizeof(*b));
     b->q = c->hq;
+    b->q.allow_switch = 0;  // the grouped launch runs every query by the matrix loop
     const int cls = batch_size_class(c->W);
     int cpl = 1;
     uint32_t nch = gather_chunks(c->W, &cpl);

@@ -21,6 +21,11 @@ constexpr int kMaxNT = CFPQ_MAX_NONTERM;
 
 enum : uint32_t { kErrNone = 0, kErrIterLimit = 1, kErrTimeout = 2 };
 
+// A loop execution that adds at most kSmallDelta pairs is "small"; after kSwitchAfter small
+// executions in a row, a loop that may switch hands the closure to the worklist path (a long
+// chain of derivations: one pair per execution would cost a matrix pass per pair).
+constexpr unsigned kSmallDelta = 8, kSwitchAfter = 256;
+
 // Per-query device state; one instance in device memory per context.
 struct DevState {
     unsigned long long iter;            // loop executions completed
@@ -43,6 +48,8 @@ struct DevState {
     unsigned int list_len;              // gather items listed in this loop execution (single-query path)
     unsigned int pad_list;
     unsigned long long useful_macs;     // profile mode: sum over tensor products of nnz(col k of T_B) nnz(row k of T_C)
+    unsigned int small_run;             // consecutive executions that added at most kSmallDelta pairs
+    unsigned int to_worklist;           // the loop stopped to hand the closure to the worklist path
 };
 
 struct Rule {
@@ -53,7 +60,7 @@ struct Rule {
 struct QDesc {
     uint32_t n, n_pad, W;
     int32_t n_nt, n_rules, n_groups, schedule, n_unary, n_eps;
-    int32_t profile, pad0;
+    int32_t profile, allow_switch;      // allow_switch: long runs of tiny deltas end the loop (worklist next)
     uint64_t plane;                     // words per matrix = n_pad * W
     uint64_t n_edges;
     uint32_t *T, *TT, *X0, *X1, *R0, *R1, *Trow;
@@ -302,6 +309,15 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
         st->changed = 0u;
         st->iter = it + 1;
         cont = changed ? 1u : 0u;
+        if (cont && q.allow_switch) {
+            unsigned long long added = 0;
+            for (int a = 0; a < q.n_nt; a++) added += st->dcount[old ^ 1u][a];
+            st->small_run = added <= kSmallDelta ? st->small_run + 1u : 0u;
+            if (st->small_run >= kSwitchAfter) {
+                st->to_worklist = 1u;
+                cont = 0;
+            }
+        }
         if (cont && it + 1 >= ld_u64(&st->max_iter)) {
             st->error = kErrIterLimit;
             cont = 0;

@@ -24,6 +24,9 @@ struct cfpq_ctx {
     std::vector<char> nt_dynamic;     // per non-terminal: 1 = left-hand side of a binary production
     bool auto_mixed = false;          // AUTO path with tensor cores: product kind chosen per group and iteration
     bool any_gather = false;          // some group may take the gather product
+    bool allow_switch = false;        // AUTO, not Jacobi: a long run of tiny deltas hands over to the worklist
+    bool switched = false;            // the last solve finished on the worklist path
+    std::vector<cfpq_edge> h_edges;   // host copy of the edges (worklist set-up on a switch)
     uint32_t *d_list = nullptr;       // gather items of one loop execution (in the arena)
     uint32_t *d_colcnt = nullptr;     // profile mode: column counts of a left operand (n_pad)
     uint32_t list_cap = 0;
@@ -96,6 +99,7 @@ int read_status(cfpq_ctx *c, cudaStream_t s);
 int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_useful_work(cfpq_ctx *c, int g, cudaStream_t s);
 int tensor_prepare(cfpq_ctx *c);
+int enqueue_all_transposes(cfpq_ctx *c, cudaStream_t s);
 // Statistics and status of a solve from a copy of its device state.
 int apply_status(cfpq_ctx *c, const DevState &st);
 int run_loop(cfpq_ctx *c, cudaStream_t s);
@@ -110,7 +114,9 @@ void tensor_release(cfpq_ctx *c);
 
 // worklist path (cfpq_worklist.cu)
 int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges);
-int worklist_run(cfpq_ctx *c, cudaStream_t s);
+// from_delta: continue a closure the matrix loop started (stack = the current delta pairs,
+// T^T rebuilt from T); otherwise a full solve from the seeds.
+int worklist_run(cfpq_ctx *c, cudaStream_t s, bool from_delta = false);
 void worklist_release(cfpq_ctx *c);
 
 }  // namespace cfpq

@@ -545,6 +545,14 @@ int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s) {
 
 int tensor_prepare(cfpq_ctx *c) { return tensor_setup(c); }
 
+// T^T of every non-terminal that a production derives (the worklist's hand-over).
+int enqueue_all_transposes(cfpq_ctx *c, cudaStream_t s) {
+    int64_t ignored = 0;
+    for (int a = 0; a < c->n_nt; a++)
+        if (c->nt_dynamic[a]) launch_transpose(c, a, s, &ignored);
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
+
 // After the matrix initialisation: transposes of every right operand of a tensor group.
 int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launches) {
     int rc = tensor_setup(c);

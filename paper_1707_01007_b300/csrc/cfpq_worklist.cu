@@ -62,6 +62,7 @@ struct WLDesc {
     const PChain *pchain;         // [n_nt] periodic chain starting at a (P = 0: none)
     const uint32_t *lift;         // per periodic chain: kLiftLevels tables of n entries for G and H
     struct PcCtl *pcc;            // periodic rounds: task and per-block results (device memory)
+    int32_t keep_iter;            // 1: leave the loop count of the matrix loop that ran before
     uint32_t *stack;              // triples (a, i, j)
     uint64_t cap;                 // stack capacity in triples
     unsigned long long *items;    // pairs processed
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(kWlThreads, 1) k_worklist(const QDesc *qd, WLD
     }
     if (lane == 0) {
         *w.items = processed;
-        q.st->iter = 1;
+        if (!w.keep_iter) q.st->iter = 1;
         pcc->cmd = kPcExit;
         __threadfence();
         atomicAdd(&pcc->gen, 1u);  // helper blocks leave
@@ -629,6 +630,32 @@ __global__ void k_worklist_rows(const QDesc *qd) {
     for (uint32_t w0 = 0; w0 < q.W && !__any_sync(0xffffffffu, any != 0); w0 += 32)
         any |= (w0 + lane < q.W) ? __ldcg(row + w0 + lane) : 0u;
     if (__any_sync(0xffffffffu, any != 0) && lane == 0) atomicOr(&q.Trow[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
+}
+
+// Hand-over from the matrix loop: every pair of the current delta plane (the pairs the
+// loop added last, not yet joined) goes on the stack. One warp per (non-terminal, row).
+__global__ void k_worklist_init_delta(const QDesc *qd, WLDesc w, unsigned long long *top) {
+    const QDesc &q = *qd;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= (uint64_t)q.n_nt * q.n) return;
+    const uint32_t a = (uint32_t)(warp / q.n), i = (uint32_t)(warp % q.n);
+    const uint32_t par = (uint32_t)(q.st->iter & 1ull);
+    if (!test_bit((par ? q.R1 : q.R0) + (uint64_t)a * q.W, i)) return;
+    const uint32_t *row = (par ? q.X1 : q.X0) + (uint64_t)a * q.plane + (uint64_t)i * q.W;
+    for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
+        uint32_t bits = (w0 + lane < q.W) ? row[w0 + lane] : 0u;
+        while (bits) {
+            const uint32_t j = (w0 + lane) * 32u + (uint32_t)(__ffs(bits) - 1);
+            bits &= bits - 1;
+            const unsigned long long pos = atomicAdd(top, 1ull);
+            if (pos < w.cap) {
+                w.stack[3 * pos] = a;
+                w.stack[3 * pos + 1] = i;
+                w.stack[3 * pos + 2] = j;
+            }
+        }
+    }
 }
 
 // Every seeded pair goes on the stack (and into T^T where kept).
@@ -881,16 +908,23 @@ void worklist_release(cfpq_ctx *c) {
 }
 
 // After enqueue_reset_and_seed: stack the seeds, run the warp, read its counters.
-int worklist_run(cfpq_ctx *c, cudaStream_t s) {
+int worklist_run(cfpq_ctx *c, cudaStream_t s, bool from_delta) {
     WorklistState *ws = static_cast<WorklistState *>(c->h_wl);
     if (!ws) return CFPQ_ERR_UNSUPPORTED;
     WLDesc &d = ws->d;
+    d.keep_iter = from_delta ? 1 : 0;
     if (cudaMemsetAsync(ws->d_top, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d.overflow, 0, 8, s) != cudaSuccess ||
-        cudaMemsetAsync(d.pcc, 0, sizeof(PcCtl), s) != cudaSuccess ||
-        cudaMemsetAsync(c->d_TT, 0, (size_t)c->n_nt * c->plane * 4, s) != cudaSuccess)
+        cudaMemsetAsync(d.pcc, 0, sizeof(PcCtl), s) != cudaSuccess)
         return CFPQ_ERR_CUDA;
     const uint64_t rows = (uint64_t)c->n_nt * c->n;
-    k_worklist_init<<<(uint32_t)((rows * 32 + 255) / 256), 256, 0, s>>>(c->d_q, d, ws->d_top);
+    if (from_delta) {
+        // T^T of every derived non-terminal from T as the loop left it, then the delta stacked
+        if (enqueue_all_transposes(c, s) != CFPQ_OK) return CFPQ_ERR_CUDA;
+        k_worklist_init_delta<<<(uint32_t)((rows * 32 + 255) / 256), 256, 0, s>>>(c->d_q, d, ws->d_top);
+    } else {
+        if (cudaMemsetAsync(c->d_TT, 0, (size_t)c->n_nt * c->plane * 4, s) != cudaSuccess) return CFPQ_ERR_CUDA;
+        k_worklist_init<<<(uint32_t)((rows * 32 + 255) / 256), 256, 0, s>>>(c->d_q, d, ws->d_top);
+    }
     unsigned long long top = 0;
     if (cudaMemcpyAsync(&top, ws->d_top, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -101,3 +101,32 @@ def test_same_generation_full_size():
     s = q.stats()
     assert s["iterations"] == k
     products_each_once(s, synth.GRAMMAR_SG, graph)
+
+
+def test_long_chain_hands_over_to_the_worklist():
+    # two cycles: every loop execution adds about one pair; after a long run of such
+    # executions the automatic path stops the matrix loop and the worklist path finishes the
+    # closure from the current delta
+    graph = synth.two_cycles(64, 63)
+    g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO)
+    q.solve()
+    s = q.stats()
+    assert s["worklist_items"] > 0 and 256 <= s["iterations"] < 64 * 63
+    ref = oracle.hellings(graph, synth.GRAMMAR_C3)
+    for nm in g.names:
+        assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+    # under Jacobi the loop keeps Algorithm 1's exact count, so it never hands over
+    qj = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, schedule=eng.SCHED_JACOBI, timeout_s=120.0)
+    qj.solve()
+    assert qj.stats()["worklist_items"] == 0 and qj.stats()["iterations"] == 2 * 64 * 63 + 1
+
+
+def test_long_chain_full_size_automatic():
+    p, qq = 4096, 4095
+    graph = synth.two_cycles(p, qq)
+    g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, timeout_s=300.0)
+    q.solve()
+    assert q.stats()["worklist_items"] > 0
+    assert q.count("S") == p * qq and q.count("S1") == p * qq
