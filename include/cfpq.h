@@ -89,9 +89,11 @@ enum cfpq_path {
                                  closure (cfpq_stats.iterations: the executions before that) */
     CFPQ_PATH_TENSOR = 1,     /* dense tcgen05 product of every production, every iteration */
     CFPQ_PATH_GATHER = 2,     /* CUDA-core bit-gather over changed bits only (semi-naive) */
-    CFPQ_PATH_WORKLIST = 3    /* one warp joins each new pair with its partners (semi-naive at the
-                                 grain of single pairs): for long chains of tiny deltas; the loop
-                                 count is not defined (reported as 1) */
+    CFPQ_PATH_WORKLIST = 3    /* each new pair is joined with its partners (semi-naive at the grain
+                                 of single pairs; warps of one block take batches of pairs, and
+                                 periodic chains of single-successor steps run across many
+                                 blocks): for long chains of tiny deltas; the loop count is not
+                                 defined (reported as 1) */
 };
 
 typedef struct {

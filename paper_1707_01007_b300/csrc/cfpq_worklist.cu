@@ -1,5 +1,5 @@
 // Worklist path (CFPQ_PATH_WORKLIST): the closure of Algorithm 1 (Section 4.2) evaluated
-// semi-naively at the finest grain, one new pair at a time, by a single warp on the GPU.
+// semi-naively at the finest grain, one new pair at a time, on the GPU.
 //
 // Algorithm 1 joins the whole matrix with itself each iteration. When every iteration adds
 // only a pair or two (long derivation chains, e.g. two cycles sharing a node, where the loop
@@ -12,7 +12,12 @@
 // is empty, T is closed under every production: the same least fixpoint as the matrix loop.
 // Partners of non-terminals that no production derives (their relation is exactly the seed)
 // come from CSR adjacency built on the host; partners of the others from the bit matrices:
-// row j of T_C, and row i of T_B^T (T^T is maintained for them as pairs are set).
+// row j of T_C, and row i of T_B^T (T^T is kept for every derived non-terminal).
+//
+// Warp 0 of block 0 owns the stack. Batches of general pairs are joined by all 16 warps of
+// block 0; chains of single-successor steps are walked 31 steps per ballot, and periodic
+// chains (which return to their non-terminal) are computed by binary lifting in rounds that
+// span up to 128 blocks of a cooperative launch.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -257,7 +262,7 @@ __device__ __forceinline__ void push_new(const WLDesc &w, unsigned m, uint32_t x
     n_new += __popc(m);
 }
 
-// The general join of one popped pair (ca, ci, cj) by one warp: through every occurrence of
+// The general join of one popped pair (ca, ci, cj) by the calling warp: through every occurrence of
 // ca as an operand, with the partner's CSR (static partner) or bit rows (dynamic partner).
 // Returns the number of new pairs.
 __device__ uint32_t general_join(const QDesc &q, const WLDesc &w, uint32_t ca, uint32_t ci, uint32_t cj,

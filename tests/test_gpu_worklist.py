@@ -1,4 +1,4 @@
-"""Worklist path (semi-naive at the grain of single pairs, one warp): the same least
+"""Worklist path (semi-naive at the grain of single pairs): the same least
 fixpoint as Algorithm 1, against the oracle and the two-cycle closed form at full size."""
 import numpy as np
 import pytest
