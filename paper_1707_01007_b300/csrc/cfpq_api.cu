@@ -131,10 +131,6 @@ __global__ void __launch_bounds__(128) k_clear(const QDesc *qd) {
     }
 }
 
-__global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle) {
-    const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x, true);
-    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, cont);
-}
 
 // AUTO path, start of a loop execution (one thread): for every production group, the cheaper
 // of the two product kinds by a cost model on the device-side counts, and which group
@@ -147,10 +143,8 @@ constexpr double kTensorOpsPerNs = 2.9e6;     // measured tensor-core Boolean pr
 constexpr double kGatherBytesPerNs = 600.0;   // measured gather rate (latency-bound)
 constexpr double kTransposeBytesPerNs = 3000.0;
 
-__global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *handles, int use_handles) {
-    const QDesc &q = *qd;
+__device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle *handles, int use_handles) {
     DevState *st = q.st;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const uint32_t p = (uint32_t)(st->iter & 1ull);
     const double n = (double)q.n, W = (double)q.W, np = (double)q.n_pad;
     const double per_rule_ns = 2.0 * np * np * np / kTensorOpsPerNs;
@@ -180,6 +174,21 @@ __global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *hand
         const unsigned now = (owner[a] != 0u && st->dirty[a]) ? owner[a] : 0u;
         st->tt_now[a] = now;
         if (now) st->dirty[a] = 0u;
+    }
+}
+
+__global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *handles, int use_handles) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) choose_products(*qd, handles, use_handles);
+}
+
+// End of a loop execution. choice != NULL (automatic path in a graph): the product choice for
+// the next execution is made here too, saving a launch per execution.
+__global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle,
+                       const cudaGraphConditionalHandle *choice) {
+    const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x, true);
+    if (threadIdx.x == 0) {
+        if (cont && choice) choose_products(*qd, choice, 1);
+        if (use_handle) cudaGraphSetConditional(handle, cont);
     }
 }
 
@@ -511,8 +520,10 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
     if (c->auto_mixed) {
         // choose per group; in a graph the chosen tensor products run under conditional
         // nodes, otherwise every tensor launch is made and returns at once if not chosen
-        k_choose<<<1, 32, 0, s>>>(c->d_q, use_handle ? c->d_choice : nullptr, use_handle);
-        c->iter_launches++;
+        if (!use_handle) {  // in the graph, the previous execution's tail (or the node before the loop) chose
+            k_choose<<<1, 32, 0, s>>>(c->d_q, nullptr, 0);
+            c->iter_launches++;
+        }
         if (use_handle) {
             const int rc = enqueue_auto_tensor_graph(c, s);
             if (rc != CFPQ_OK) return rc;
@@ -549,7 +560,7 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         c->iter_launches++;
     }
     k_clear<<<word_blocks, 128, 0, s>>>(c->d_q);
-    k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle);
+    k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle, (use_handle && c->auto_mixed) ? c->d_choice : nullptr);
     c->iter_launches += 2;
     CK(cudaGetLastError());
     return CFPQ_OK;
@@ -587,17 +598,10 @@ static int build_graph(cfpq_ctx *c) {
     cudaGraphConditionalHandle h;
     cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "handle", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
-    cudaGraphNodeParams p = {};
-    p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeWhile;
-    p.conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
-    if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "addnode", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
-    cudaGraph_t body = p.conditional.phGraph_out[0];
+    cudaGraphNode_t first = nullptr;  // automatic path: the first execution's product choice
     if (c->auto_mixed) {
-        // one IF/ELSE handle per production group, set by k_choose in every loop execution
+        // one IF handle per production group, then "any group chose tensor", set by the
+        // choice before the loop and by every execution's tail for the next one
         const int prc = tensor_prepare(c);
         if (prc != CFPQ_OK) { cudaGraphDestroy(g); return prc; }
         for (cudaStream_t *as : {&c->aux_stream, &c->aux2_stream})
@@ -606,7 +610,7 @@ static int build_graph(cfpq_ctx *c) {
                 note_cuda_error(e, "aux stream", __FILE__, __LINE__);
                 return CFPQ_ERR_CUDA;
             }
-        c->h_choice.assign(c->n_groups + 1, 0);  // one per group, then "any group chose tensor"
+        c->h_choice.assign(c->n_groups + 1, 0);
         for (int k = 0; k <= c->n_groups; k++) {
             e = cudaGraphConditionalHandleCreate(&c->h_choice[k], g, 0, 0);
             if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "choice handle", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
@@ -614,7 +618,27 @@ static int build_graph(cfpq_ctx *c) {
         e = cudaMemcpy(c->d_choice, c->h_choice.data(), sizeof(cudaGraphConditionalHandle) * (c->n_groups + 1),
                        cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "choice copy", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
+        const QDesc *qd = c->d_q;
+        const cudaGraphConditionalHandle *hs = c->d_choice;
+        int use = 1;
+        void *args[] = {(void *)&qd, (void *)&hs, (void *)&use};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void *)k_choose;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(32);
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&first, g, nullptr, 0, &kp);
+        if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "choice node", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
     }
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, first ? &first : nullptr, nullptr, first ? 1 : 0, &p);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "addnode", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
+    cudaGraph_t body = p.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "capture", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
     const int rc = enqueue_iteration(c, c->stream, h, 1);
@@ -943,7 +967,7 @@ void ctx_destroy(cfpq_ctx *c) {
 int run_loop(cfpq_ctx *c, cudaStream_t s) {
     if (c->n_groups == 0) {
         // no binary productions: one execution of the loop body finds nothing new
-        k_tail<<<1, 1024, 0, s>>>(c->d_q, 0, 0);
+        k_tail<<<1, 1024, 0, s>>>(c->d_q, 0, 0, nullptr);
         c->iter_launches = 1;
         CK(cudaGetLastError());
         return CFPQ_OK;
