@@ -260,6 +260,82 @@ def matrix_closure(graph, grammar_text: str, max_iter: int | None = None):
     return cnf, snaps, k
 
 
+def single_path_lengths(graph, grammar_text: str, max_iter: int | None = None, _plant: str | None = None):
+    """The closure of Section 5 (single-path semantics): every pair carries the length of
+    one path whose labels the non-terminal derives. a^(1): (A, 1) for every edge (i, x, j)
+    with A -> x (and, reading A -> eps as the empty walk, (A, 0) on the diagonal); each loop
+    execution p adds (A, l_B + l_C) at (i, j) for A -> B C, (B, l_B) in a^(p-1)_{i,k} and
+    (C, l_C) in a^(p-1)_{k,j}, but only where A is not at (i, j) yet: the length first found
+    is kept. Where one execution finds several lengths for the same new (A, i, j) the paper
+    does not say which is kept; this reading keeps the smallest (so the result is unique).
+    Returns (cnf, lengths, k): lengths[A] = {(i, j): l}, k the loop count as in
+    ``matrix_closure``. Plain dictionaries; small inputs only. ``_plant`` (tests only) puts a
+    known mistake in: "plus_one" (l_B + l_C + 1), "last_wins" (a later length replaces the
+    first), "max_tie" (the largest of one execution's lengths)."""
+    cnf = parse_grammar(grammar_text, graph.labels)
+    n = graph.n
+    L = {a: {} for a in range(len(cnf.names))}
+    heads = {}
+    for a, t in cnf.unary:
+        heads.setdefault(t, []).append(a)
+    for src, lab, dst in np.asarray(graph.edges, dtype=np.int64).reshape(-1, 3):
+        for a in heads.get(int(lab), []):
+            L[a][(int(src), int(dst))] = 1
+    for a in cnf.eps:
+        for m in range(n):
+            L[a][(m, m)] = 0
+    # right operands by row, for the joins
+    k = 0
+    while True:
+        k += 1
+        by_row = {a: {} for a in L}
+        for a, pairs in L.items():
+            for (i, j), l in pairs.items():
+                by_row[a].setdefault(i, []).append((j, l))
+        found = {}
+        for a, b, c in cnf.binary:
+            for (i, kk), lb in L[b].items():
+                for j, lc in by_row[c].get(kk, []):
+                    if (i, j) in L[a] and _plant != "last_wins":
+                        continue
+                    key = (a, i, j)
+                    cand = lb + lc + (1 if _plant == "plus_one" else 0)
+                    if _plant == "last_wins" and (i, j) in L[a] and L[a][(i, j)] == cand:
+                        continue
+                    better = cand > found[key] if _plant == "max_tie" and key in found else \
+                        (key not in found or cand < found[key])
+                    if better:
+                        found[key] = cand
+        for (a, i, j), l in found.items():
+            L[a][(i, j)] = l
+        if not found:
+            break
+        if max_iter is not None and k >= max_iter:
+            break
+    return cnf, L, k
+
+
+def walk_exists(graph, cnf, a: int, i: int, j: int, length: int) -> bool:
+    """Brute force: is there a walk of exactly `length` edges from i to j whose label string
+    non-terminal a derives (CYK on every walk label)? Tiny inputs only."""
+    by_src = {}
+    for src, lab, dst in np.asarray(graph.edges, dtype=np.int64).reshape(-1, 3):
+        by_src.setdefault(int(src), []).append((int(lab), int(dst)))
+    if length == 0:
+        return i == j and a in cyk_table(cnf, [])[0][0]  # the nullable non-terminals
+    frontier = {(i, ())}
+    for _ in range(length):
+        nxt = set()
+        for node, labels in frontier:
+            for lab, dst in by_src.get(node, []):
+                nxt.add((dst, labels + (lab,)))
+        frontier = nxt
+    for node, labels in frontier:
+        if node == j and a in cyk_table(cnf, list(labels))[0][length]:
+            return True
+    return False
+
+
 def matrix_closure_sparse(graph, grammar_text: str, max_iter: int | None = None):
     """Algorithm 1 as in ``matrix_closure`` but with sparse Boolean matrices (scipy CSR
     products as the library primitive, the representation of the paper's sCPU variant),

@@ -375,3 +375,97 @@ def test_property_checks_detect_broken_results():
     broken3 = dict(good)
     broken3["S"] = np.concatenate([good["S"], np.array([[g.n - 1, g.n - 1]], dtype=np.uint32)])
     assert not oracle.check_witnessed(cnf, g.n, g.edges, broken3)
+
+
+# ----------------------------------------------------------------------------- single-path lengths (Section 5)
+
+def _labelled(n, edges, labels):
+    return synth.Graph(n=n, edges=np.asarray(edges, dtype=np.int64).reshape(-1, 3), labels=list(labels),
+                       meta={"kind": "test"})
+
+
+@pytest.mark.parametrize("n", [2, 9, 40])
+def test_lengths_on_a_path_are_distances(n):
+    # S -> S S | a on a directed path: the only walk from i to j has j - i edges
+    g = _labelled(n, [(i, 0, i + 1) for i in range(n - 1)], ["a"])
+    cnf, L, k = oracle.single_path_lengths(g, "S S S\nS a\n")
+    assert len(L[0]) == n * (n - 1) // 2
+    assert all(l == j - i for (i, j), l in L[0].items())
+
+
+@pytest.mark.parametrize("p,q", [(5, 4), (7, 3), (6, 5), (3, 2), (1, 1)])
+def test_lengths_on_two_cycles_closed_form(p, q):
+    # S -> a S b | a b: a walk a^k b^k from a-node i must pass node 0 after k a-steps, so
+    # k = d_i (mod p) and k = e_j (mod q); derivations of smaller k appear in earlier loop
+    # executions, so the length found first is 2 k_min
+    g = synth.two_cycles(p, q)
+    cnf, L, k = oracle.single_path_lengths(g, synth.GRAMMAR_C3)
+    S = cnf.names.index("S")
+    bnodes = [0] + list(range(p, p + q - 1))
+    assert len(L[S]) == p * q  # gcd(p, q) = 1: every (a-node, b-node) pair
+    for (i, j), l in L[S].items():
+        d, e = (p - i) % p, bnodes.index(j)
+        kmin = next(kk for kk in range(1, 2 * p * q + 2) if kk % p == d % p and kk % q == e % q)
+        assert l == 2 * kmin, (i, j)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_lengths_have_witness_walks(seed):
+    # Theorem 5 of Section 5: (A, l) at (i, j) means a walk of exactly l edges from i to j
+    # whose labels A derives (brute force: every walk of that length, CYK on its labels)
+    g = synth.random_graph(6, 9, 2, seed=seed)
+    text = synth.random_grammar_text(4, 2, 6, 4, seed % 2, seed=seed)
+    cnf, L, k = oracle.single_path_lengths(g, text, max_iter=6)
+    for a, pairs in L.items():
+        for (i, j), l in pairs.items():
+            if l <= 7:
+                assert oracle.walk_exists(g, cnf, a, i, j, l), (cnf.names[a], i, j, l)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_lengths_cover_the_relational_result(seed):
+    # the pairs carrying a length are exactly R_A (the relational result)
+    g = synth.random_graph(30, 70, 3, seed=seed)
+    text = synth.random_grammar_text(5, 3, 9, 6, seed % 3, seed=seed)
+    cnf, L, k = oracle.single_path_lengths(g, text)
+    ref = oracle.hellings(g, text).as_sets()
+    for a, name in enumerate(cnf.names):
+        assert set(L[a]) == ref[name]
+    # and the loop runs exactly as many executions as Algorithm 1
+    assert k == oracle.matrix_closure(g, text)[2]
+
+
+def _diamond():
+    # two walks from 0 to 3: 0-1-2-3 (3 edges) and 0-4-5-6-3 (4 edges); with S -> S S | a both
+    # complete in the same loop execution (lengths in (2, 4]), and the smaller is kept
+    return _labelled(7, [(0, 0, 1), (1, 0, 2), (2, 0, 3), (0, 0, 4), (4, 0, 5), (5, 0, 6), (6, 0, 3)], ["a"])
+
+
+def test_lengths_tie_in_one_execution_keeps_the_smallest():
+    cnf, L, _ = oracle.single_path_lengths(_diamond(), "S S S\nS a\n")
+    assert L[0][(0, 3)] == 3
+
+
+@pytest.mark.parametrize("plant", ["plus_one", "last_wins", "max_tie"])
+def test_lengths_planted_mistakes_fail_a_pin(plant):
+    # each run is capped well above the executions Algorithm 1 needs there, and "the loop ends
+    # before the cap" is a pin of its own (a length that keeps changing never lets it end)
+    cap = 40
+    failed = []
+    path = _labelled(12, [(i, 0, i + 1) for i in range(11)], ["a"])
+    _, L, k = oracle.single_path_lengths(path, "S S S\nS a\n", max_iter=cap, _plant=plant)
+    failed.append(k >= cap or any(l != j - i for (i, j), l in L[0].items()))
+    _, L, k = oracle.single_path_lengths(_diamond(), "S S S\nS a\n", max_iter=cap, _plant=plant)
+    failed.append(k >= cap or L[0][(0, 3)] != 3)
+    p, q = 3, 2
+    g = synth.two_cycles(p, q)
+    cnf, L, k = oracle.single_path_lengths(g, synth.GRAMMAR_C3, max_iter=cap, _plant=plant)
+    S = cnf.names.index("S")
+    bnodes = [0] + list(range(p, p + q - 1))
+    wrong = k >= cap
+    for (i, j), l in L[S].items():
+        d, e = (p - i) % p, bnodes.index(j)
+        kmin = next(kk for kk in range(1, 2 * p * q + 2) if kk % p == d % p and kk % q == e % q)
+        wrong |= l != 2 * kmin
+    failed.append(wrong)
+    assert any(failed), plant
