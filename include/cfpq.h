@@ -105,6 +105,12 @@ typedef struct {
                                  events (cfpq_stats.product_ms / product_launches); default 0 */
     int64_t max_iter;         /* iteration cap; 0 = |V|^2 |N| + 1 (Theorem 3's bound on changes) */
     double timeout_s;         /* wall-clock limit checked on the device; <= 0 = none */
+    int32_t lengths;          /* 1: single-path semantics (Section 5) as well -- every pair also
+                                 carries the length of one walk whose labels A derives; read it with
+                                 cfpq_get_lengths. Needs schedule JACOBI (AUTO is taken as JACOBI)
+                                 and a matrix path (not WORKLIST); adds one uint32 per (A, m, n)
+                                 cell (n_pad^2 * |N| * 4 bytes) to the context. Default 0 */
+    int32_t reserved;         /* must be 0 */
 } cfpq_options;
 
 typedef struct {
@@ -129,6 +135,11 @@ typedef struct {
     int32_t gather_cpl;       /* batched solves: gather tile width used (32-bit words per lane) */
     double useful_ops;        /* profile mode: 2 x sum over tensor products of sum_k nnz(column k
                                  of T_B) nnz(row k of T_C), the Boolean ops with both operands 1 */
+    double lengths_ms;        /* lengths on, profile mode: summed device time of the length kernels */
+    int64_t lengths_launches; /* lengths on, profile mode: length kernel launches timed */
+    double lengths_splits;    /* lengths on, profile mode: (production, middle node k) splits the
+                                 length kernels examined, i.e. sum over new pairs (A, i, j) and
+                                 productions A -> B C of |{k : (i, k) in T_B, (k, j) in T_C}| */
 } cfpq_stats;
 
 typedef struct cfpq_ctx cfpq_ctx;
@@ -146,7 +157,8 @@ int cfpq_options_default(cfpq_options *opt);
  *   edges   host array of n_edges edges (may be NULL iff n_edges == 0)
  *   opt     options, NULL for defaults
  *   out     receives the context; untouched on error
- * Errors: INVALID, NOMEM, CUDA, UNSUPPORTED.
+ * Errors: INVALID, NOMEM, CUDA, UNSUPPORTED (tensor path unavailable; lengths with schedule
+ * INPLACE or path WORKLIST).
  */
 int cfpq_create(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
                 const cfpq_options *opt, cfpq_ctx **out);
@@ -176,6 +188,22 @@ int cfpq_get_device(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, size_t cap, size
 /* Every relation at once: triples (A, m, n) sorted by (A, m, n) into buf (host memory, cap
  * triples); buf == NULL: only *count. Errors: INVALID, NOT_SOLVED, BUFFER, NOMEM, CUDA. */
 int cfpq_get_all(cfpq_ctx *ctx, cfpq_triple *buf, size_t cap, size_t *count);
+
+/*
+ * Single-path semantics (Section 5): R_A as in cfpq_get, triples sorted by (m, n) into buf,
+ * and in lengths[t] the length l of the walk that triple t carries (host memory, cap
+ * entries each; buf == NULL and lengths == NULL: only *count). The lengths follow the
+ * paper's rule: an edge (m, x, n) gives every A -> x the length 1, A -> eps gives (m, m) the
+ * length 0, and a loop execution that first derives (m, n) for A through A -> B C and a
+ * middle node k gives it l_B(m, k) + l_C(k, n) from the matrices before that execution; a
+ * length once set is kept. Where one execution derives (m, n) for A through several
+ * productions or middle nodes, the paper does not say which length is kept: this library
+ * keeps the smallest of them, so the result is unique. Every length is that of some walk
+ * from m to n whose labels A derives; lengths of 2^32 - 1 or more read as UINT32_MAX.
+ * Errors: INVALID (A out of range, count NULL, exactly one of buf and lengths NULL),
+ * UNSUPPORTED (context created without options.lengths), NOT_SOLVED, BUFFER, NOMEM, CUDA.
+ */
+int cfpq_get_lengths(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, uint32_t *lengths, size_t cap, size_t *count);
 
 /* |R_A| without copying pairs. Errors: as cfpq_get. */
 int cfpq_count(cfpq_ctx *ctx, int32_t A, size_t *count);
@@ -217,8 +245,9 @@ void cfpq_grammar_free(cfpq_parsed_grammar *pg);
  * identical to solving each context alone. Each context keeps its own schedule and
  * iteration cap; products always take the gather path inside the grouped launch. The
  * smallest positive timeout_s among the contexts limits the whole launch (checked on the
- * device after every round; the contexts are then left unsolved). Errors: INVALID, NOMEM,
- * CUDA, UNSUPPORTED (no cooperative launch), TIMEOUT (the launch's wall-clock limit passed
+ * device after every round; the contexts are then left unsolved). Contexts created with
+ * options.lengths are not taken (UNSUPPORTED). Errors: INVALID, NOMEM,
+ * CUDA, UNSUPPORTED (no cooperative launch; a lengths context), TIMEOUT (the launch's wall-clock limit passed
  * or a bounded grid barrier gave up), ITER_LIMIT (some context hit its cap; the others are
  * still complete).
  */

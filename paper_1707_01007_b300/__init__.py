@@ -57,7 +57,8 @@ class Triple(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("path", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("timeout_s", ctypes.c_double)]
+                ("profile", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("timeout_s", ctypes.c_double),
+                ("lengths", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -69,7 +70,8 @@ class Stats(ctypes.Structure):
                 ("product_ms", ctypes.c_double), ("tensor_ms", ctypes.c_double),
                 ("tensor_launches", ctypes.c_int64), ("product_bytes", ctypes.c_double),
                 ("worklist_items", ctypes.c_int64), ("schedule", ctypes.c_int32), ("gather_cpl", ctypes.c_int32),
-                ("useful_ops", ctypes.c_double)]
+                ("useful_ops", ctypes.c_double), ("lengths_ms", ctypes.c_double),
+                ("lengths_launches", ctypes.c_int64), ("lengths_splits", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -125,6 +127,8 @@ SIGNATURES = {
     "cfpq_get_all": (ctypes.c_int, [_VP, _P(Triple), ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_get_device": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_count": (ctypes.c_int, [_VP, ctypes.c_int32, _P(ctypes.c_size_t)]),
+    "cfpq_get_lengths": (ctypes.c_int, [_VP, ctypes.c_int32, _P(Triple), _P(ctypes.c_uint32), ctypes.c_size_t,
+                                        _P(ctypes.c_size_t)]),
     "cfpq_stats_get": (ctypes.c_int, [_VP, _P(Stats)]),
     "cfpq_destroy": (None, [_VP]),
     "cfpq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -228,7 +232,8 @@ class Query:
     """One CFPQ query (graph + grammar) resident on the device (``cfpq_create``)."""
 
     def __init__(self, grammar: Grammar, n: int, edges, schedule: int = SCHED_INPLACE, path: int = PATH_AUTO,
-                 use_graph: bool = True, max_iter: int = 0, timeout_s: float = 0.0, profile: bool = False):
+                 use_graph: bool = True, max_iter: int = 0, timeout_s: float = 0.0, profile: bool = False,
+                 lengths: bool = False):
         self.grammar = grammar
         self.n = int(n)
         self._h = None
@@ -237,6 +242,7 @@ class Query:
         opt.schedule, opt.path, opt.use_graph = schedule, path, int(bool(use_graph))
         opt.profile = int(bool(profile))
         opt.max_iter, opt.timeout_s = int(max_iter), float(timeout_s)
+        opt.lengths = int(bool(lengths))
         rec = _edges_struct(edges)
         h = ctypes.c_void_p()
         ptr = rec.ctypes.data_as(ctypes.POINTER(Edge)) if rec.size else None
@@ -290,6 +296,21 @@ class Query:
     def get(self, A) -> np.ndarray:
         """R_A as a sorted (k, 2) uint32 array of (m, n)."""
         return self.triples(A)[:, 1:].astype(np.uint32)
+
+    def lengths(self, A):
+        """Single-path semantics (``cfpq_get_lengths``): R_A as a sorted (k, 2) uint32 array of
+        (m, n) and, per pair, the uint32 length of the walk it carries."""
+        a = self._aid(A)
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_get_lengths(self._h, a, None, None, 0, ctypes.byref(c)), "cfpq_get_lengths")
+        k = int(c.value)
+        buf = np.zeros(max(k, 1), dtype=[("A", "<i4"), ("m", "<u4"), ("n", "<u4")])
+        lens = np.zeros(max(k, 1), dtype=np.uint32)
+        _check(_lib().cfpq_get_lengths(self._h, a, buf.ctypes.data_as(ctypes.POINTER(Triple)),
+                                       lens.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), k, ctypes.byref(c)),
+               "cfpq_get_lengths")
+        pairs = np.stack([buf["m"][:k], buf["n"][:k]], axis=1).astype(np.uint32)
+        return pairs, lens[:k]
 
     def get_device(self, A, dev_ptr: int, cap: int) -> int:
         """Writes R_A as triples into device memory at dev_ptr (cap triples); returns |R_A|."""

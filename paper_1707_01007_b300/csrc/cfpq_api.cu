@@ -555,6 +555,12 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         if (rc != CFPQ_OK) return rc;
     }
     const uint32_t word_blocks = (uint32_t)((uint64_t)c->n_nt * ((c->n + 31) / 32));  // one per (A, row word)
+    if (c->lengths) {  // before the merge: T still holds the previous execution's matrices
+        if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 2], s));
+        const int rc = lengths_enqueue_iteration(c, s);
+        if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 3], s));
+        if (rc != CFPQ_OK) return rc;
+    }
     if (c->schedule == CFPQ_SCHED_JACOBI) {
         k_merge<<<word_blocks, 128, 0, s>>>(c->d_q);
         c->iter_launches++;
@@ -587,6 +593,12 @@ static int collect_profile(cfpq_ctx *c) {
         CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * c->n_groups], c->prof_ev[2 * c->n_groups + 1]));
         c->stats.product_ms += ms;
         c->stats.product_launches++;
+    }
+    if (c->lengths) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->prof_ev[2 * c->n_groups + 2], c->prof_ev[2 * c->n_groups + 3]));
+        c->stats.lengths_ms += ms;
+        c->stats.lengths_launches++;
     }
     return CFPQ_OK;
 }
@@ -660,7 +672,7 @@ void free_ctx_device(cfpq_ctx *c) {
     worklist_release(c);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
-    void *ptrs[] = {c->d_arena, c->d_triples, c->d_tc_work};
+    void *ptrs[] = {c->d_arena, c->d_triples, c->d_tc_work, c->d_lens};
     for (void *p : ptrs)
         if (p) {
             if (c->pooled) cudaFreeAsync(p, c->stream);
@@ -706,6 +718,11 @@ int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
     const uint32_t blocks = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (work + 255) / 256), 148ull * 16);
     k_seed<<<blocks, 256, 0, s>>>(c->d_q);
     CK(cudaGetLastError());
+    if (c->lengths) {
+        const int rc = lengths_enqueue_seed(c, s);
+        if (rc != CFPQ_OK) return rc;
+        c->fixed_launches++;
+    }
     bool any_tensor = false;
     for (int g = 0; g < c->n_groups; g++) any_tensor |= c->group_tensor[g] != 0;
     if (any_tensor) return enqueue_tensor_seed_transposes(c, s, &c->fixed_launches);
@@ -730,6 +747,7 @@ int apply_status(cfpq_ctx *c, const DevState &st) {
     c->stats.kernel_launches = c->fixed_launches + (int64_t)st.iter * c->iter_launches;
     c->stats.product_bytes = 4.0 * (double)st.prof_words;
     c->stats.useful_ops = 2.0 * (double)st.useful_macs;
+    c->stats.lengths_splits = (double)st.len_splits;
     int rc = CFPQ_OK;
     if (st.error == kErrIterLimit) rc = CFPQ_ERR_ITER_LIMIT;
     else if (st.error == kErrTimeout) rc = CFPQ_ERR_TIMEOUT;
@@ -743,11 +761,18 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     c->n_pad = (n + 255u) / 256u * 256u;
     c->W = c->n_pad / 32u;
     c->plane = (uint64_t)c->n_pad * c->W;
+    c->lplane = (uint64_t)c->n_pad * c->n_pad;
     c->n_nt = g->n_nonterm;
     c->n_term = g->n_term;
     c->schedule_req = o.schedule;
     c->schedule = o.schedule == CFPQ_SCHED_AUTO ? CFPQ_SCHED_INPLACE : o.schedule;  // single solves
     c->path = o.path;
+    c->lengths = o.lengths != 0;
+    if (c->lengths) {
+        // the lengths come from the matrices before each loop execution: Jacobi schedule only
+        if (o.schedule == CFPQ_SCHED_INPLACE || o.path == CFPQ_PATH_WORKLIST) return CFPQ_ERR_UNSUPPORTED;
+        c->schedule = CFPQ_SCHED_JACOBI;
+    }
     c->use_graph = o.use_graph;
     c->profile = o.profile;
     c->timeout_s = o.timeout_s;
@@ -789,7 +814,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         c->group_tensor.assign(std::max(1, c->n_groups), 1);
     }
     c->auto_mixed = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && tensor_path_available();
-    c->allow_switch = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && c->schedule_req != CFPQ_SCHED_JACOBI;
+    c->allow_switch = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && c->schedule != CFPQ_SCHED_JACOBI;
     if (c->allow_switch) c->h_edges.assign(edges, edges + n_edges);
     c->any_gather = c->n_groups > 0 && c->path != CFPQ_PATH_TENSOR && c->path != CFPQ_PATH_WORKLIST;
     {
@@ -816,7 +841,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
     if (c->profile) {
-        c->prof_ev.assign(2 * (c->n_groups + 1), nullptr);
+        c->prof_ev.assign(2 * (c->n_groups + 2), nullptr);
         for (auto &e : c->prof_ev) CK(cudaEventCreate(&e));
     }
     // one arena for every buffer of the query (one allocation, one free). The batched
@@ -841,7 +866,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_total, sizeof(unsigned long long)},
         {(void **)&c->d_choice, sizeof(cudaGraphConditionalHandle) * (kMaxNT + 1)},
         {(void **)&c->d_list, (size_t)c->list_cap * sizeof(uint32_t)},
-        {(void **)&c->d_colcnt, c->profile ? sizeof(uint32_t) * c->n_pad : 0}};
+        {(void **)&c->d_colcnt, c->profile ? sizeof(uint32_t) * c->n_pad : 0},
+        {(void **)&c->d_L, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
     {
@@ -937,6 +963,7 @@ int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edge
             opt->schedule != CFPQ_SCHED_AUTO)
             return CFPQ_ERR_INVALID;
         if (opt->path < CFPQ_PATH_AUTO || opt->path > CFPQ_PATH_WORKLIST) return CFPQ_ERR_INVALID;
+        if ((opt->lengths != 0 && opt->lengths != 1) || opt->reserved != 0) return CFPQ_ERR_INVALID;
     }
     return CFPQ_OK;
 }
@@ -1033,8 +1060,8 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     c->solved = false;
     c->last_stream = s;
-    c->stats.product_ms = c->stats.tensor_ms = 0.0;
-    c->stats.product_launches = c->stats.tensor_launches = 0;
+    c->stats.product_ms = c->stats.tensor_ms = c->stats.lengths_ms = 0.0;
+    c->stats.product_launches = c->stats.tensor_launches = c->stats.lengths_launches = 0;
     CK(cudaEventRecord(c->ev0, s));
     int rc = enqueue_reset_and_seed(c, s);
     if (rc != CFPQ_OK) return rc;
@@ -1198,6 +1225,44 @@ extern "C" int cfpq_get_all(cfpq_ctx *c, cfpq_triple *buf, size_t cap, size_t *c
     if ((rc = ensure_triples(c, total, s)) != CFPQ_OK) return rc;
     if ((rc = emit_all(c, c->d_triples, s)) != CFPQ_OK) return rc;
     CK(cudaMemcpyAsync(buf, c->d_triples, total * sizeof(cfpq_triple), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_get_lengths(cfpq_ctx *c, int32_t A, cfpq_triple *buf, uint32_t *lengths, size_t cap,
+                                size_t *count) {
+    if (!c || !count || A < 0 || A >= c->n_nt || (!buf) != (!lengths)) return CFPQ_ERR_INVALID;
+    if (!c->lengths) return CFPQ_ERR_UNSUPPORTED;
+    if (!c->solved) return CFPQ_ERR_NOT_SOLVED;
+    cudaStream_t s = c->last_stream;
+    unsigned long long total = 0;
+    int rc = count_rows_and_scan(c, A, s, &total);
+    if (rc != CFPQ_OK) return rc;
+    *count = (size_t)total;
+    if (!buf) return CFPQ_OK;
+    if (cap < total) return CFPQ_ERR_BUFFER;
+    if (total == 0) return CFPQ_OK;
+    if ((rc = ensure_triples(c, total, s)) != CFPQ_OK) return rc;
+    if (c->lens_cap < total) {
+        if (c->d_lens) {
+            if (c->pooled) cudaFreeAsync(c->d_lens, s);
+            else cudaFree(c->d_lens);
+        }
+        c->d_lens = nullptr;
+        c->lens_cap = 0;
+        const cudaError_t e = c->pooled ? cudaMallocAsync(&c->d_lens, total * sizeof(uint32_t), s)
+                                        : cudaMalloc(&c->d_lens, total * sizeof(uint32_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->d_lens = nullptr;
+            return CFPQ_ERR_NOMEM;
+        }
+        c->lens_cap = total;
+    }
+    if ((rc = emit(c, A, c->d_triples, s)) != CFPQ_OK) return rc;
+    if ((rc = lengths_of_triples(c, c->d_triples, total, c->d_lens, s)) != CFPQ_OK) return rc;
+    CK(cudaMemcpyAsync(buf, c->d_triples, total * sizeof(cfpq_triple), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(lengths, c->d_lens, total * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return CFPQ_OK;
 }

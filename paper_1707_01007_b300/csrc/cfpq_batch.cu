@@ -681,6 +681,8 @@ static int check_batch_args(cfpq_ctx *const *ctxs, int32_t k) {
     if (!ctxs || k <= 0 || k > kMaxBatch) return CFPQ_ERR_INVALID;
     for (int j = 0; j < k; j++)
         if (!ctxs[j]) return CFPQ_ERR_INVALID;
+    for (int j = 0; j < k; j++)
+        if (ctxs[j]->lengths) return CFPQ_ERR_UNSUPPORTED;  // the grouped launch keeps no length planes
     return CFPQ_OK;
 }
 

@@ -50,6 +50,8 @@ struct DevState {
     unsigned long long useful_macs;     // profile mode: sum over tensor products of nnz(col k of T_B) nnz(row k of T_C)
     unsigned int small_run;             // consecutive executions that added at most kSmallDelta pairs
     unsigned int to_worklist;           // the loop stopped to hand the closure to the worklist path
+    unsigned int pad_len;
+    unsigned long long len_splits;      // lengths, profile mode: (production, middle node) splits examined
 };
 
 struct Rule {

@@ -30,6 +30,11 @@ struct cfpq_ctx {
     uint32_t *d_list = nullptr;       // gather items of one loop execution (in the arena)
     uint32_t *d_colcnt = nullptr;     // profile mode: column counts of a left operand (n_pad)
     uint32_t list_cap = 0;
+    bool lengths = false;             // single-path semantics: a length plane per non-terminal
+    uint32_t *d_L = nullptr;          // [n_nt][n_pad][n_pad] lengths (in the arena)
+    uint64_t lplane = 0;              // cells per length plane = n_pad * n_pad
+    uint32_t *d_lens = nullptr;       // extraction: lengths of the emitted triples
+    size_t lens_cap = 0;
     int gather_grid = 0;              // persistent grid of the listed gathers
     // device memory
     uint32_t *d_T = nullptr, *d_TT = nullptr, *d_X0 = nullptr, *d_X1 = nullptr;
@@ -111,6 +116,11 @@ int enqueue_tensor_transposes(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launches);
 void tensor_release(cfpq_ctx *c);
+
+// single-path lengths (cfpq_lengths.cu)
+int lengths_enqueue_seed(cfpq_ctx *c, cudaStream_t s);
+int lengths_enqueue_iteration(cfpq_ctx *c, cudaStream_t s);
+int lengths_of_triples(cfpq_ctx *c, const cfpq_triple *d_tr, size_t count, uint32_t *d_out, cudaStream_t s);
 
 // worklist path (cfpq_worklist.cu)
 int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges);

@@ -92,6 +92,25 @@ def test_create_rejects_invalid_input_before_device_use():
     assert _create(g.cnf, 4, [], ctypes.byref(opt))[0] == eng.ERR_INVALID
 
 
+def test_lengths_options_checked_before_device_use():
+    # single-path lengths (Section 5) come from the matrices before each loop execution, so
+    # they need the Jacobi schedule and a matrix path; bad flag values are rejected
+    g = eng.Grammar("S S S\nS a\n", ["a"])
+    lib = eng.library()
+    for field, value, code in [("lengths", 2, eng.ERR_INVALID), ("reserved", 1, eng.ERR_INVALID)]:
+        opt = eng.Options()
+        lib.cfpq_options_default(ctypes.byref(opt))
+        opt.schedule = eng.SCHED_JACOBI
+        setattr(opt, field, value)
+        assert _create(g.cnf, 4, [(0, 0, 1)], ctypes.byref(opt))[0] == code, field
+    for schedule, path in [(eng.SCHED_INPLACE, eng.PATH_GATHER), (eng.SCHED_JACOBI, eng.PATH_WORKLIST)]:
+        opt = eng.Options()
+        lib.cfpq_options_default(ctypes.byref(opt))
+        opt.schedule, opt.path, opt.lengths = schedule, path, 1
+        assert _create(g.cnf, 4, [(0, 0, 1)], ctypes.byref(opt))[0] == eng.ERR_UNSUPPORTED
+    assert lib.cfpq_get_lengths(None, 0, None, None, 0, None) == eng.ERR_INVALID
+
+
 def test_null_arguments():
     lib = eng.library()
     assert lib.cfpq_solve(None, None) == eng.ERR_INVALID
@@ -108,8 +127,9 @@ def test_null_arguments():
 def test_options_defaults():
     opt = eng.Options()
     assert eng.library().cfpq_options_default(ctypes.byref(opt)) == eng.OK
-    assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter) == \
-        (eng.SCHED_INPLACE, eng.PATH_AUTO, 1, 0, 0)
+    assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter, opt.lengths, opt.reserved) == \
+        (eng.SCHED_INPLACE, eng.PATH_AUTO, 1, 0, 0, 0, 0)
+    assert ctypes.sizeof(eng.Options) == 40
 
 
 def test_batch_tuning_host_calls():
