@@ -56,10 +56,11 @@ def parse():
     ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="hier16k", choices=["hier16k", "sg16k", "batch256", "serve", "cycles"],
+    ap.add_argument("--workload", default="hier16k",
+                    choices=["hier16k", "sg16k", "batch256", "serve", "cycles", "lengths16k"],
                     help="hier16k: the default line; sg16k: the same hierarchy with the same-generation "
                          "query (denser result); batch256 / serve / cycles: the batched, served and "
-                         "two-cycle workloads")
+                         "two-cycle workloads; lengths16k: single-path lengths (Section 5) on the hierarchy")
     ap.add_argument("--n", type=int, default=None, help="smaller hierarchy for profiling captures")
     ap.add_argument("--classes", type=int, default=None)
     ap.add_argument("--cycle-p", type=int, default=None, help="a-cycle length of the cycles workload (profiling)")
@@ -595,6 +596,70 @@ def cycles_arm(args):
     return 0
 
 
+def lengths_arm(args):
+    """Single-path semantics (Section 5) on the n = 16384 hierarchy: Query 1 and the
+    same-generation query with a length per pair, Jacobi schedule, automatic product path.
+    Reported: the device time of the closure with lengths, the same closure without them, the
+    length kernels' own time and splits (profile mode), and Query 1's pairs and lengths checked
+    one by one against the oracle (whose run is the CPU baseline)."""
+    import torch
+
+    import paper_1707_01007_b300 as eng
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    graph, _ = workload()
+    stream = torch.cuda.current_stream()
+    queries = [("Q1", synth.GRAMMAR_Q1), ("SG", synth.GRAMMAR_SG)]
+    per, total_ms, kept = {}, 0.0, {}
+    for nm, text in queries:
+        g = eng.Grammar(text, graph.labels)
+        mk = lambda **kw: eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, schedule=eng.SCHED_JACOBI,
+                                    timeout_s=600.0, **kw)
+        out = {}
+        for label, q in (("with_lengths", mk(lengths=True)), ("without", mk())):
+            for _ in range(args.warmup):
+                q.solve(stream)
+            ts = []
+            for _ in range(args.steps):
+                q.solve(stream)
+                ts.append(q.stats()["solve_ms"])
+            out[label + "_ms"] = float(np.median(ts))
+            if label == "with_lengths":
+                kept[nm] = (g, q)
+        qp = mk(lengths=True, profile=True)
+        qp.solve(stream)
+        st = qp.stats()
+        out.update({"iterations": st["iterations"], "new_pairs": st["new_bits"], "lengths_kernel_ms": st["lengths_ms"],
+                    "lengths_launches": st["lengths_launches"], "splits": st["lengths_splits"],
+                    "ns_per_new_pair": st["lengths_ms"] * 1e6 / max(1, st["new_bits"])})
+        qp.close()
+        per[nm] = out
+        total_ms += out["with_lengths_ms"]
+    line = {"metric": "single-path closure time (Query 1 + same-generation query, lengths per pair)",
+            "value": total_ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32 bit-packed + u32 lengths", "data": "synthetic",
+            "config": {"workload": f"hierarchy n={N_NODES} ({N_CLASSES} classes, seed {SEED}), Query 1 + "
+                                   "same-generation query, single-path lengths, Jacobi schedule, automatic path"},
+            "queries": per}
+    if not args.no_cpu_baseline:
+        import oracle
+        g, q = kept["Q1"]
+        t0 = time.perf_counter()
+        cnf, L, _ = oracle.single_path_lengths(graph, synth.GRAMMAR_Q1)
+        dt = time.perf_counter() - t0
+        same = True
+        for a, name in enumerate(cnf.names):
+            pairs, lens = q.lengths(name)
+            got = {(int(m), int(n)): int(l) for (m, n), l in zip(pairs.tolist(), lens.tolist())}
+            same &= got == L[a]
+        line["parity_Q1_vs_oracle"] = bool(same)
+        line["cpu_baseline"] = {"value": dt, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": "Query 1 only (the same-generation query takes minutes), one host thread"}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -605,6 +670,8 @@ def main():
         return serve_arm(args)
     if args.workload == "cycles":
         return cycles_arm(args)
+    if args.workload == "lengths16k":
+        return lengths_arm(args)
     return engine_arm(args)
 
 

@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDe
 }
 
 // Jacobi schedule: T |= N over the rows N touched. One block per (non-terminal, row word of
-// 32 rows); the block's threads share each flagged row's words.
+// 32 rows); the block's warps share each flagged row's words, 32 consecutive words a warp.
+// Where lengths are kept, the word summary of T follows (one bit per 32-word chunk word).
 __global__ void __launch_bounds__(128) k_merge(const QDesc *qd) {
     const QDesc &q = *qd;
     const uint32_t rw = (q.n + 31u) / 32u;
@@ -104,12 +105,25 @@ __global__ void __launch_bounds__(128) k_merge(const QDesc *qd) {
     if (rows && threadIdx.x == 0) atomicOr(&q.Trow[(uint64_t)a * q.W + wq], rows);
     const uint32_t *N = (parity ? q.X0 : q.X1) + (uint64_t)a * q.plane;
     uint32_t *T = q.T + (uint64_t)a * q.plane;
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     while (rows) {
         const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
         rows &= rows - 1;
-        for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) {
-            const uint32_t nw = __ldcg(N + i * q.W + w);
+        for (uint32_t w0 = warp * 32u; w0 < q.W; w0 += blockDim.x) {
+            const uint32_t w = w0 + lane;
+            const uint32_t nw = w < q.W ? __ldcg(N + i * q.W + w) : 0u;
             if (nw) T[i * q.W + w] = __ldcg(T + i * q.W + w) | nw;
+            if (q.Tsum) {  // lengths kept: summaries of T and of T^T, and T^T itself, follow
+                const unsigned sb = __ballot_sync(0xffffffffu, nw != 0u);
+                if (lane == 0 && sb) atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + (w0 >> 5)], sb);
+                uint32_t x = nw;
+                while (x) {
+                    const uint64_t j = (uint64_t)w * 32u + (uint32_t)(__ffs(x) - 1);
+                    x &= x - 1;
+                    atomicOr(&q.TT[(uint64_t)a * q.plane + j * q.W + (i >> 5)], 1u << (i & 31));
+                    atomicOr(&q.TTsum[((uint64_t)a * q.n_pad + j) * q.SW + (i >> 10)], 1u << ((i >> 5) & 31));
+                }
+            }
         }
     }
 }
@@ -703,6 +717,12 @@ int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
     CK(cudaMemsetAsync(c->d_R0, 0, rows, s));
     CK(cudaMemsetAsync(c->d_R1, 0, rows, s));
     CK(cudaMemsetAsync(c->d_Trow, 0, rows, s));
+    if (c->lengths) {  // T^T and both word summaries are built pair by pair from here on
+        const size_t sum = (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t);
+        CK(cudaMemsetAsync(c->d_Tsum, 0, sum, s));
+        CK(cudaMemsetAsync(c->d_TTsum, 0, sum, s));
+        CK(cudaMemsetAsync(c->d_TT, 0, planes, s));
+    }
     DevState st0;
     memset(&st0, 0, sizeof(st0));
     st0.max_iter = c->max_iter;
@@ -762,6 +782,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     c->W = c->n_pad / 32u;
     c->plane = (uint64_t)c->n_pad * c->W;
     c->lplane = (uint64_t)c->n_pad * c->n_pad;
+    c->SW = ((c->W + 31u) / 32u + 3u) & ~3u;
     c->n_nt = g->n_nonterm;
     c->n_term = g->n_term;
     c->schedule_req = o.schedule;
@@ -850,7 +871,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
     const size_t rowsz = (size_t)c->n_nt * c->W * sizeof(uint32_t);
     const size_t cells = (size_t)c->n_nt * c->n_pad;  // (non-terminal, row) extraction cells
-    const bool want_tt = (c->path == CFPQ_PATH_WORKLIST) || c->allow_switch ||
+    const bool want_tt = (c->path == CFPQ_PATH_WORKLIST) || c->allow_switch || c->lengths ||
                          ((c->path == CFPQ_PATH_AUTO || c->path == CFPQ_PATH_TENSOR) && tensor_path_available());
     struct Part { void **dst; size_t bytes; };
     const Part parts[] = {
@@ -867,7 +888,9 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_choice, sizeof(cudaGraphConditionalHandle) * (kMaxNT + 1)},
         {(void **)&c->d_list, (size_t)c->list_cap * sizeof(uint32_t)},
         {(void **)&c->d_colcnt, c->profile ? sizeof(uint32_t) * c->n_pad : 0},
-        {(void **)&c->d_L, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0}};
+        {(void **)&c->d_L, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0},
+        {(void **)&c->d_Tsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
+        {(void **)&c->d_TTsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
     {
@@ -914,6 +937,9 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.R0 = c->d_R0;
     q.R1 = c->d_R1;
     q.Trow = c->d_Trow;
+    q.Tsum = c->d_Tsum;
+    q.TTsum = c->d_TTsum;
+    q.SW = c->SW;
     q.rules = c->d_rules;
     q.gstart = c->d_gstart;
     q.unary = c->d_unary;

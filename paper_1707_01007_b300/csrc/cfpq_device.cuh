@@ -9,6 +9,11 @@
 //   R[p][A]   row bitmaps of X[p][A] (bit i set iff row i of X[p][A] may be non-zero)
 //   Trow[A]   row bitmap of T[A] (bit i set iff row i of T[A] is non-empty)
 //   TT[A]     T_A transposed, refreshed before tensor-core products that read it
+//   Tsum[A]   single-path lengths only: word summary of T_A, SW words per row (ceil(W / 32)
+//             rounded up to a multiple of 4), bit w of row i set iff word w of row i of T_A
+//             may be non-zero
+//   TTsum[A]  single-path lengths only: the same summary of TT_A (with lengths kept, TT_A is
+//             updated pair by pair by the seed and the merge)
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -66,6 +71,9 @@ struct QDesc {
     uint64_t plane;                     // words per matrix = n_pad * W
     uint64_t n_edges;
     uint32_t *T, *TT, *X0, *X1, *R0, *R1, *Trow;
+    uint32_t *Tsum;                     // word summary of T (NULL unless lengths are kept)
+    uint32_t *TTsum;                    // word summary of TT (NULL unless lengths are kept)
+    uint32_t SW;                        // summary words per row (a multiple of 4)
     const Rule *rules;                  // sorted by lhs; group g = rules[gstart[g] .. gstart[g+1])
     const int32_t *gstart;
     const int2 *unary;                  // (lhs, term)
@@ -111,6 +119,11 @@ __device__ __forceinline__ void seed_pair(const QDesc &q, int a, uint32_t i, uin
         atomicOr(&q.Trow[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
         atomicAdd(&q.st->dcount[0][a], 1ull);
         atomicAdd(&q.st->tcount[a], 1ull);
+        if (q.Tsum) {
+            atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + (j >> 10)], 1u << ((j >> 5) & 31));
+            atomicOr(&q.TT[(uint64_t)a * q.plane + (uint64_t)j * q.W + (i >> 5)], 1u << (i & 31));
+            atomicOr(&q.TTsum[((uint64_t)a * q.n_pad + j) * q.SW + (i >> 10)], 1u << ((i >> 5) & 31));
+        }
         (*cnt)++;
     }
 }

@@ -33,6 +33,10 @@ struct cfpq_ctx {
     bool lengths = false;             // single-path semantics: a length plane per non-terminal
     uint32_t *d_L = nullptr;          // [n_nt][n_pad][n_pad] lengths (in the arena)
     uint64_t lplane = 0;              // cells per length plane = n_pad * n_pad
+    uint32_t *d_Tsum = nullptr;       // word summary of T (lengths only; in the arena)
+    uint32_t *d_TTsum = nullptr;      // word summary of T^T (lengths only; in the arena)
+    uint32_t SW = 0;                  // summary words per row: ceil(W / 32) rounded up to a multiple of 4
+    int len_grid = 0;                 // persistent grid of the length kernel
     uint32_t *d_lens = nullptr;       // extraction: lengths of the emitted triples
     size_t lens_cap = 0;
     int gather_grid = 0;              // persistent grid of the listed gathers

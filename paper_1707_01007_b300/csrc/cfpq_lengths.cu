@@ -11,7 +11,11 @@
 // through several productions or middle nodes; this engine keeps the smallest, so the result
 // is unique and does not depend on the order in which the device finds the derivations.
 //
-// Layout: one uint32 plane per non-terminal next to T, L[A][i * n_pad + j]. A cell is only
+// Layout: one uint32 plane per non-terminal next to T, L[A][i * n_pad + j]. The search for the
+// middle nodes k of a pair (i, j) intersects row i of T_B with column j of T_C; for that the
+// seed and the Jacobi merge keep T^T up to date pair by pair, with a word summary of T and of
+// T^T (one bit per 32-bit word, SW words per row), so that only words that are non-zero on
+// both sides are read. A length cell is only
 // written when its pair enters T_A and only read while the pair is in T_A, so the planes are
 // never cleared. The loop runs under the Jacobi schedule (T_{k+1} = T_k u T_k x T_k): after
 // every product of an execution has written its new pairs to the delta plane N and before
@@ -49,120 +53,164 @@ __global__ void k_seed_lengths(const QDesc *qd, uint32_t *L, uint64_t lplane, un
     }
 }
 
-// Middle nodes taken per step of the split loop: their T_C words are loaded together, then
-// their lengths, so that a warp keeps several independent loads in flight.
-constexpr int kSplitU = 4;
-
-// Lengths of the new pairs (A, i, 32 w + lane) flagged in `bits` (one bit per lane), for the
-// productions r0 .. r1 - 1 of A. The warp walks the set bits k of row i of T_B (warp-uniform);
-// for each k one word of T_C (row k, word w) says which lanes' j have (k, j) in T_C; those
-// lanes take l_B(i, k) + l_C(k, j). Returns the lane's minimum (UINT64_MAX if it has no pair).
-__device__ __forceinline__ unsigned long long min_split(const QDesc &q, const uint32_t *__restrict__ L, uint64_t lplane,
-                                                        int r0, int r1, uint32_t i, uint32_t w, uint32_t bits,
-                                                        int lane, unsigned long long *splits) {
-    const uint32_t W = q.W, np = q.n_pad;
-    const uint32_t j = w * 32u + (uint32_t)lane;
-    const bool mine = (bits >> lane) & 1u;
+// Length of one new pair (A, i, j) from the productions r0 .. r1 - 1 of A (one lane, one
+// pair). The middle nodes k under A -> B C are the set bits of row i of T_B AND row j of TT_C
+// (column j of T_C): the two rows' word summaries are ANDed 16 words at a time (vector
+// loads), and only the words both flag are read and ANDed. Returns the minimum of
+// l_B(i, k) + l_C(k, j) (UINT64_MAX if there is no middle node).
+__device__ __forceinline__ unsigned long long pair_length(const QDesc &q, const uint32_t *__restrict__ L,
+                                                          uint64_t lplane, int r0, int r1, uint32_t i, uint32_t j,
+                                                          unsigned *hits) {
+    const uint32_t W = q.W, np = q.n_pad, SW = q.SW;
     unsigned long long best = ~0ull;
-    unsigned hits = 0;
     for (int r = r0; r < r1; r++) {
         const int B = q.rules[r].b, C = q.rules[r].c;
+        const uint4 *sumB = reinterpret_cast<const uint4 *>(q.Tsum + ((uint64_t)B * np + i) * SW);
+        const uint4 *sumC = reinterpret_cast<const uint4 *>(q.TTsum + ((uint64_t)C * np + j) * SW);
         const uint32_t *rowB = q.T + (uint64_t)B * q.plane + (uint64_t)i * W;
-        const uint32_t *TC = q.T + (uint64_t)C * q.plane + w;
+        const uint32_t *colC = q.TT + (uint64_t)C * q.plane + (uint64_t)j * W;
         const uint32_t *LB = L + (uint64_t)B * lplane + (uint64_t)i * np;
         const uint32_t *LC = L + (uint64_t)C * lplane + j;
-        for (uint32_t w0 = 0; w0 < W; w0 += 32) {
-            const uint32_t bw = (w0 + lane < W) ? __ldcg(rowB + w0 + lane) : 0u;
-            unsigned nz = __ballot_sync(0xffffffffu, bw != 0u);
-            uint32_t x = 0, kb = 0;
-            while (nz || x) {
-                uint32_t k[kSplitU];
+        for (uint32_t s0 = 0; s0 < SW; s0 += 16) {
+            uint4 b[4], c[4];
 #pragma unroll
-                for (int u = 0; u < kSplitU; u++) {
-                    if (!x && nz) {  // warp-uniform refill from the next non-zero word of the row
-                        const int src = __ffs(nz) - 1;
-                        nz &= nz - 1;
-                        x = __shfl_sync(0xffffffffu, bw, src);
-                        kb = (w0 + (uint32_t)src) * 32u;
-                    }
-                    k[u] = 0xFFFFFFFFu;
-                    if (x) {
-                        k[u] = kb + (uint32_t)(__ffs(x) - 1);
+            for (int t = 0; t < 4; t++) {
+                const bool in = s0 + 4u * t < SW;
+                b[t] = in ? __ldcg(sumB + s0 / 4 + t) : make_uint4(0u, 0u, 0u, 0u);
+                c[t] = in ? __ldcg(sumC + s0 / 4 + t) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const uint32_t xs[4] = {b[t].x & c[t].x, b[t].y & c[t].y, b[t].z & c[t].z, b[t].w & c[t].w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    uint32_t x = xs[e];  // words flagged in row i of T_B and in column j of T_C
+                    while (x) {
+                        const uint32_t wk = (s0 + 4u * t + (uint32_t)e) * 32u + (uint32_t)(__ffs(x) - 1);
                         x &= x - 1;
+                        uint32_t kw = __ldcg(rowB + wk) & __ldcg(colC + wk);
+                        while (kw) {
+                            const uint32_t k = wk * 32u + (uint32_t)(__ffs(kw) - 1);
+                            kw &= kw - 1;
+                            const unsigned long long cand =
+                                (unsigned long long)__ldcg(LB + k) + __ldcg(LC + (uint64_t)k * np);
+                            best = cand < best ? cand : best;
+                            (*hits)++;
+                        }
                     }
                 }
-                uint32_t cw[kSplitU];
-#pragma unroll
-                for (int u = 0; u < kSplitU; u++) cw[u] = k[u] != 0xFFFFFFFFu ? __ldcg(TC + (uint64_t)k[u] * W) : 0u;
-                uint32_t lb[kSplitU], lc[kSplitU];
-                unsigned take = 0;  // bit u: (i, k[u]) in T_B and (k[u], j) in T_C for this lane's j
-#pragma unroll
-                for (int u = 0; u < kSplitU; u++) {
-                    lb[u] = lc[u] = 0u;
-                    if (mine && ((cw[u] >> lane) & 1u)) {
-                        take |= 1u << u;
-                        lb[u] = __ldcg(LB + k[u]);
-                        lc[u] = __ldcg(LC + (uint64_t)k[u] * np);
-                    }
-                }
-                hits += (unsigned)__popc(take);
-#pragma unroll
-                for (int u = 0; u < kSplitU; u++)
-                    if ((take >> u) & 1u) {
-                        const unsigned long long cand = (unsigned long long)lb[u] + lc[u];
-                        best = cand < best ? cand : best;
-                    }
             }
         }
     }
-    *splits += hits;
     return best;
 }
 
-// One block (4 warps) per (non-terminal A, row word of 32 rows): every new pair of A in those
-// rows (the bits of N_A, before the Jacobi merge) gets its length. A warp takes 32 words of a
-// flagged row at a time and, for each non-zero word, the up to 32 pairs in it.
-__global__ void __launch_bounds__(128, 6) k_lengths(const QDesc *qd, uint32_t *L, uint64_t lplane) {
+// Pairs queued per warp before the lanes take one each (two rounds of 32 fit).
+constexpr int kLenQ = 64;
+constexpr int kLenWarps = 8;
+constexpr int kScanU = 8;  // 32-word chunks of a row of N loaded together
+
+// Persistent grid. Warp g scans the rows (A, i) = g, g + warps, ... of the n_nt x n row space
+// whose bit in the new delta's row bitmap is set (its lanes test 32 of those rows at once); the
+// bits of N_A's row i are exactly the pairs this execution adds (read before the merge). Each new pair goes into the warp's queue in
+// shared memory (every lane still holding bits gives one per round); whenever 32 are queued,
+// every lane computes one pair's length, so the lanes stay busy however the new pairs are
+// spread over rows and words.
+__global__ void __launch_bounds__(256, 2) k_lengths(const QDesc *qd, uint32_t *L, uint64_t lplane) {
+    __shared__ uint32_t q_i[kLenWarps][kLenQ], q_j[kLenWarps][kLenQ];
+    __shared__ uint8_t q_a[kLenWarps][kLenQ];
+    __shared__ int2 grp[kMaxNT];  // productions of each left-hand side: [x, y)
     const QDesc &q = *qd;
-    const uint32_t rw = (q.n + 31u) / 32u;
-    const int a = (int)(blockIdx.x / rw);
-    const uint32_t wq = blockIdx.x % rw;
-    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
-    uint32_t rows = __ldcg((parity ? q.R0 : q.R1) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
-    if (!rows) return;
-    int r0 = -1, r1 = -1;
-    for (int g = 0; g < q.n_groups; g++)
-        if (q.rules[q.gstart[g]].lhs == a) {
-            r0 = q.gstart[g];
-            r1 = q.gstart[g + 1];
-        }
-    if (r0 < 0) return;
-    const uint32_t *N = (parity ? q.X0 : q.X1) + (uint64_t)a * q.plane;
-    uint32_t *LA = L + (uint64_t)a * lplane;
+    if (threadIdx.x < (unsigned)q.n_nt) {
+        int2 g2 = make_int2(-1, -1);
+        for (int gr = 0; gr < q.n_groups; gr++)
+            if (q.rules[q.gstart[gr]].lhs == (int)threadIdx.x) g2 = make_int2(q.gstart[gr], q.gstart[gr + 1]);
+        grp[threadIdx.x] = g2;
+    }
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
+    const uint32_t *NR = parity ? q.R0 : q.R1;
+    const uint32_t *Nall = parity ? q.X0 : q.X1;
     const uint32_t W = q.W;
-    unsigned long long splits = 0;
-    while (rows) {
-        const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
-        rows &= rows - 1;
-        for (uint32_t w0 = (uint32_t)warp * 32u; w0 < W; w0 += 128u) {
-            const uint32_t nw = (w0 + lane < W) ? __ldcg(N + (uint64_t)i * W + w0 + lane) : 0u;
-            unsigned nz = __ballot_sync(0xffffffffu, nw != 0u);
-            while (nz) {
-                const int src = __ffs(nz) - 1;
-                nz &= nz - 1;
-                const uint32_t bits = __shfl_sync(0xffffffffu, nw, src);
-                const uint32_t w = w0 + (uint32_t)src;
-                const unsigned long long best = min_split(q, L, lplane, r0, r1, i, w, bits, lane, &splits);
-                if ((bits >> lane) & 1u)
-                    LA[(uint64_t)i * q.n_pad + w * 32u + lane] = best >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)best;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned hits = 0;
+    int fill = 0;  // warp-uniform queue length
+
+    // every lane takes queue entry `lane` (if it exists) and writes its pair's length
+    auto run = [&](int cnt) {
+        __syncwarp();
+        if (lane < cnt) {
+            const int a = q_a[warp][lane];
+            const uint32_t i = q_i[warp][lane], j = q_j[warp][lane];
+            const unsigned long long best = pair_length(q, L, lplane, grp[a].x, grp[a].y, i, j, &hits);
+            L[(uint64_t)a * lplane + (uint64_t)i * q.n_pad + j] = best >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)best;
+        }
+        __syncwarp();
+    };
+
+    // rows of this warp: g = gwarp + m * gwarps; lane l tests row m = 32 t + l of round t
+    const uint64_t total = (uint64_t)q.n_nt * q.n;
+    for (uint64_t base = gwarp; base < total; base += 32ull * gwarps) {
+        const uint64_t mine = base + (uint64_t)lane * gwarps;
+        bool flagged = false;
+        if (mine < total) {
+            const int a = (int)(mine / q.n);
+            flagged = grp[a].x >= 0 && test_bit(NR + (uint64_t)a * W, (uint32_t)(mine % q.n));
+        }
+        unsigned rowmask = __ballot_sync(0xffffffffu, flagged);
+        while (rowmask) {
+            const int src = __ffs(rowmask) - 1;
+            rowmask &= rowmask - 1;
+            const uint64_t g = base + (uint64_t)src * gwarps;
+            const int a = (int)(g / q.n);
+            const uint32_t i = (uint32_t)(g % q.n);
+            const uint32_t *N = Nall + (uint64_t)a * q.plane + (uint64_t)i * W;
+            for (uint32_t w0 = 0; w0 < W; w0 += 32u * kScanU) {
+                uint32_t nw[kScanU];
+#pragma unroll
+                for (int u = 0; u < kScanU; u++) {
+                    const uint32_t w = w0 + 32u * u + lane;
+                    nw[u] = w < W ? __ldcg(N + w) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < kScanU; u++) {
+                    uint32_t x = nw[u];
+                    const uint32_t jb = (w0 + 32u * u + lane) * 32u;
+                    for (;;) {
+                        const unsigned m = __ballot_sync(0xffffffffu, x != 0u);
+                        if (!m) break;
+                        if (x) {
+                            const int pos = fill + __popc(m & lt);
+                            q_a[warp][pos] = (uint8_t)a;
+                            q_i[warp][pos] = i;
+                            q_j[warp][pos] = jb + (uint32_t)(__ffs(x) - 1);
+                            x &= x - 1;
+                        }
+                        fill += __popc(m);
+                        if (fill >= 32) {
+                            run(32);
+                            if (lane < fill - 32) {  // move the rest (at most 31) to the front
+                                q_a[warp][lane] = q_a[warp][32 + lane];
+                                q_i[warp][lane] = q_i[warp][32 + lane];
+                                q_j[warp][lane] = q_j[warp][32 + lane];
+                            }
+                            __syncwarp();
+                            fill -= 32;
+                        }
+                    }
+                }
             }
         }
     }
+    if (fill > 0) run(fill);
     if (q.profile) {
+        unsigned long long sp = hits;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) splits += __shfl_xor_sync(0xffffffffu, splits, o);
-        if (lane == 0 && splits) atomicAdd(&q.st->len_splits, splits);
+        for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+        if (lane == 0 && sp) atomicAdd(&q.st->len_splits, sp);
     }
 }
 
@@ -189,8 +237,17 @@ int lengths_enqueue_seed(cfpq_ctx *c, cudaStream_t s) {
 }
 
 int lengths_enqueue_iteration(cfpq_ctx *c, cudaStream_t s) {
-    const uint32_t blocks = (uint32_t)((uint64_t)c->n_nt * ((c->n + 31) / 32));
-    k_lengths<<<blocks, 128, 0, s>>>(c->d_q, c->d_L, c->lplane);
+    if (!c->len_grid) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lengths, 256, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        c->len_grid = std::max(1, sms) * per_sm;
+    }
+    const uint64_t rows_warps = ((uint64_t)c->n_nt * c->n + kLenWarps - 1) / kLenWarps;
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)c->len_grid, std::max<uint64_t>(1, rows_warps));
+    k_lengths<<<blocks, 256, 0, s>>>(c->d_q, c->d_L, c->lplane);
     c->iter_launches++;
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
