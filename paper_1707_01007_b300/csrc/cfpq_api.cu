@@ -94,7 +94,6 @@ __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDe
 
 // Jacobi schedule: T |= N over the rows N touched. One block per (non-terminal, row word of
 // 32 rows); the block's warps share each flagged row's words, 32 consecutive words a warp.
-// Where lengths are kept, the word summary of T follows (one bit per 32-word chunk word).
 __global__ void __launch_bounds__(128) k_merge(const QDesc *qd) {
     const QDesc &q = *qd;
     const uint32_t rw = (q.n + 31u) / 32u;
@@ -113,17 +112,6 @@ __global__ void __launch_bounds__(128) k_merge(const QDesc *qd) {
             const uint32_t w = w0 + lane;
             const uint32_t nw = w < q.W ? __ldcg(N + i * q.W + w) : 0u;
             if (nw) T[i * q.W + w] = __ldcg(T + i * q.W + w) | nw;
-            if (q.Tsum) {  // lengths kept: summaries of T and of T^T, and T^T itself, follow
-                const unsigned sb = __ballot_sync(0xffffffffu, nw != 0u);
-                if (lane == 0 && sb) atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + (w0 >> 5)], sb);
-                uint32_t x = nw;
-                while (x) {
-                    const uint64_t j = (uint64_t)w * 32u + (uint32_t)(__ffs(x) - 1);
-                    x &= x - 1;
-                    atomicOr(&q.TT[(uint64_t)a * q.plane + j * q.W + (i >> 5)], 1u << (i & 31));
-                    atomicOr(&q.TTsum[((uint64_t)a * q.n_pad + j) * q.SW + (i >> 10)], 1u << ((i >> 5) & 31));
-                }
-            }
         }
     }
 }
@@ -575,7 +563,10 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 3], s));
         if (rc != CFPQ_OK) return rc;
     }
-    if (c->schedule == CFPQ_SCHED_JACOBI) {
+    if (c->lengths) {
+        const int rc = lengths_enqueue_merge(c, s);
+        if (rc != CFPQ_OK) return rc;
+    } else if (c->schedule == CFPQ_SCHED_JACOBI) {
         k_merge<<<word_blocks, 128, 0, s>>>(c->d_q);
         c->iter_launches++;
     }

@@ -124,6 +124,7 @@ void tensor_release(cfpq_ctx *c);
 // single-path lengths (cfpq_lengths.cu)
 int lengths_enqueue_seed(cfpq_ctx *c, cudaStream_t s);
 int lengths_enqueue_iteration(cfpq_ctx *c, cudaStream_t s);
+int lengths_enqueue_merge(cfpq_ctx *c, cudaStream_t s);
 int lengths_of_triples(cfpq_ctx *c, const cfpq_triple *d_tr, size_t count, uint32_t *d_out, cudaStream_t s);
 
 // worklist path (cfpq_worklist.cu)

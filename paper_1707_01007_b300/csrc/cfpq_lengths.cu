@@ -214,6 +214,64 @@ __global__ void __launch_bounds__(256, 2) k_lengths(const QDesc *qd, uint32_t *L
     }
 }
 
+// Jacobi merge where lengths are kept: as k_merge, and T^T and the word summaries of T and
+// T^T follow pair by pair. Persistent grid, one warp per flagged row (the lanes test 32 rows
+// of the warp's share at once); the T^T bits of a chunk of 32 words are set one bit per lane
+// per round, so dense and sparse words keep every lane busy.
+__global__ void __launch_bounds__(256) k_merge_tt(const QDesc *qd) {
+    const QDesc &q = *qd;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
+    const uint32_t *NR = parity ? q.R0 : q.R1;
+    const uint32_t W = q.W;
+    const uint64_t total = (uint64_t)q.n_nt * q.n;
+    for (uint64_t base = gwarp; base < total; base += 32ull * gwarps) {
+        const uint64_t mine = base + (uint64_t)lane * gwarps;
+        const bool flagged = mine < total && test_bit(NR + (mine / q.n) * W, (uint32_t)(mine % q.n));
+        unsigned rowmask = __ballot_sync(0xffffffffu, flagged);
+        while (rowmask) {
+            const int src = __ffs(rowmask) - 1;
+            rowmask &= rowmask - 1;
+            const uint64_t g = base + (uint64_t)src * gwarps;
+            const int a = (int)(g / q.n);
+            const uint32_t i = (uint32_t)(g % q.n);
+            if (lane == 0) atomicOr(&q.Trow[(uint64_t)a * W + (i >> 5)], 1u << (i & 31));
+            const uint32_t *N = (parity ? q.X0 : q.X1) + (uint64_t)a * q.plane + (uint64_t)i * W;
+            uint32_t *T = q.T + (uint64_t)a * q.plane + (uint64_t)i * W;
+            uint32_t *TT = q.TT + (uint64_t)a * q.plane + (i >> 5);
+            uint32_t *TTsum = q.TTsum + (uint64_t)a * q.n_pad * q.SW + (i >> 10);
+            const uint32_t tbit = 1u << (i & 31), sbit = 1u << ((i >> 5) & 31);
+            for (uint32_t w0 = 0; w0 < W; w0 += 128) {
+                uint32_t nw[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t w = w0 + 32u * u + lane;
+                    nw[u] = w < W ? __ldcg(N + w) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t w = w0 + 32u * u + lane;
+                    if (nw[u]) T[w] = __ldcg(T + w) | nw[u];
+                    const unsigned sb = __ballot_sync(0xffffffffu, nw[u] != 0u);
+                    if (lane == 0 && sb)
+                        atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + ((w0 + 32u * u) >> 5)], sb);
+                    uint32_t x = nw[u];
+                    while (__any_sync(0xffffffffu, x != 0u)) {
+                        if (x) {
+                            const uint64_t j = (uint64_t)w * 32u + (uint32_t)(__ffs(x) - 1);
+                            x &= x - 1;
+                            atomicOr(TT + j * W, tbit);
+                            atomicOr(TTsum + j * q.SW, sbit);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 // Lengths of extracted triples: out[t] = L[A][m * n_pad + n].
 __global__ void k_triple_lengths(const cfpq_triple *tr, uint64_t count, const uint32_t *L, uint64_t lplane,
                                  uint32_t n_pad, uint32_t *out) {
@@ -236,18 +294,35 @@ int lengths_enqueue_seed(cfpq_ctx *c, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 
+// Persistent grid of the length kernels: the SMs times the resident blocks of k_lengths (the
+// kernel of the two with the most registers).
+static int ensure_len_grid(cfpq_ctx *c) {
+    if (c->len_grid) return CFPQ_OK;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CFPQ_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lengths, 256, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    c->len_grid = std::max(1, sms) * per_sm;
+    return CFPQ_OK;
+}
+
 int lengths_enqueue_iteration(cfpq_ctx *c, cudaStream_t s) {
-    if (!c->len_grid) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lengths, 256, 0) != cudaSuccess || per_sm < 1)
-            per_sm = 1;
-        c->len_grid = std::max(1, sms) * per_sm;
-    }
-    const uint64_t rows_warps = ((uint64_t)c->n_nt * c->n + kLenWarps - 1) / kLenWarps;
-    const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)c->len_grid, std::max<uint64_t>(1, rows_warps));
+    const int rc = ensure_len_grid(c);
+    if (rc != CFPQ_OK) return rc;
+    const uint64_t blocks_needed = ((uint64_t)c->n_nt * c->n + kLenWarps - 1) / kLenWarps;
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)c->len_grid, std::max<uint64_t>(1, blocks_needed));
     k_lengths<<<blocks, 256, 0, s>>>(c->d_q, c->d_L, c->lplane);
+    c->iter_launches++;
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
+
+int lengths_enqueue_merge(cfpq_ctx *c, cudaStream_t s) {
+    const int rc = ensure_len_grid(c);
+    if (rc != CFPQ_OK) return rc;
+    const uint64_t blocks_needed = ((uint64_t)c->n_nt * c->n + kLenWarps - 1) / kLenWarps;
+    const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)c->len_grid, std::max<uint64_t>(1, blocks_needed));
+    k_merge_tt<<<blocks, 256, 0, s>>>(c->d_q);
     c->iter_launches++;
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
