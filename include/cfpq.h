@@ -47,7 +47,8 @@ enum cfpq_status {
     CFPQ_ERR_TIMEOUT = 5,     /* the wall-clock limit was reached before the fixpoint */
     CFPQ_ERR_CUDA = 6,        /* a CUDA runtime call failed (no device, launch error, ...) */
     CFPQ_ERR_BUFFER = 7,      /* output capacity smaller than the result */
-    CFPQ_ERR_UNSUPPORTED = 8  /* option combination not available (e.g. tensor path on a non-sm_103 device) */
+    CFPQ_ERR_UNSUPPORTED = 8, /* option combination not available (e.g. tensor path on a non-sm_103 device) */
+    CFPQ_ERR_NOT_FOUND = 9    /* the pair asked for is not in the relation */
 };
 
 /* A -> x : lhs is a non-terminal id in [0, n_nonterm), term a terminal id in [0, n_term). */
@@ -107,9 +108,11 @@ typedef struct {
     double timeout_s;         /* wall-clock limit checked on the device; <= 0 = none */
     int32_t lengths;          /* 1: single-path semantics (Section 5) as well -- every pair also
                                  carries the length of one walk whose labels A derives; read it with
-                                 cfpq_get_lengths. Needs schedule JACOBI (AUTO is taken as JACOBI)
-                                 and a matrix path (not WORKLIST); adds one uint32 per (A, m, n)
-                                 cell (n_pad^2 * |N| * 4 bytes) to the context. Default 0 */
+                                 cfpq_get_lengths, and the walk itself with cfpq_get_path. Needs
+                                 schedule JACOBI (AUTO is taken as JACOBI), a matrix path (not
+                                 WORKLIST) and fewer than 8192 distinct binary productions; adds
+                                 two uint32 per (A, m, n) cell (a length and the derivation step
+                                 that set it: 2 * n_pad^2 * |N| * 4 bytes) to the context. Default 0 */
     int32_t reserved;         /* must be 0 */
 } cfpq_options;
 
@@ -204,6 +207,24 @@ int cfpq_get_all(cfpq_ctx *ctx, cfpq_triple *buf, size_t cap, size_t *count);
  * UNSUPPORTED (context created without options.lengths), NOT_SOLVED, BUFFER, NOMEM, CUDA.
  */
 int cfpq_get_lengths(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, uint32_t *lengths, size_t cap, size_t *count);
+
+/*
+ * Single-path semantics (Section 5): one walk m = v_0 -x_1-> v_1 ... -x_l-> v_l = n whose
+ * label string x_1 .. x_l the non-terminal A derives, of the length cfpq_get_lengths reports
+ * for (A, m, n). The walk is rebuilt on the device from the derivation step each pair
+ * recorded when its length was set (the production A -> B C and middle node k of the
+ * smallest length, the smallest production index and then the smallest k among equal
+ * lengths; an edge label for length 1, the smallest label where several edges qualify; the
+ * empty walk for A -> eps), so no search is needed. nodes receives l + 1 node ids and labels
+ * l terminal ids (host memory; cap = capacity of labels, nodes holds cap + 1). With nodes ==
+ * NULL and labels == NULL only *len = l is set. The rebuild runs one device thread per walk,
+ * one step per derivation node (about 2 l steps).
+ * Errors: INVALID (A, m or n out of range, len NULL, exactly one of nodes and labels NULL),
+ * UNSUPPORTED (context without options.lengths, or a length of UINT32_MAX), NOT_SOLVED,
+ * NOT_FOUND ((m, n) not in R_A), BUFFER (cap < l; *len still set), NOMEM, CUDA.
+ */
+int cfpq_get_path(cfpq_ctx *ctx, int32_t A, uint32_t m, uint32_t n, uint32_t *nodes, int32_t *labels, size_t cap,
+                  size_t *len);
 
 /* |R_A| without copying pairs. Errors: as cfpq_get. */
 int cfpq_count(cfpq_ctx *ctx, int32_t A, size_t *count);

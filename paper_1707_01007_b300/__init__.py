@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libcfpq.so")
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_NOT_SOLVED, ERR_ITER_LIMIT, ERR_TIMEOUT, ERR_CUDA, ERR_BUFFER, \
-    ERR_UNSUPPORTED = range(9)
+    ERR_UNSUPPORTED, ERR_NOT_FOUND = range(10)
 SCHED_INPLACE, SCHED_JACOBI, SCHED_AUTO = 0, 1, 2
 TUNE_CLASSES = 24
 PATH_AUTO, PATH_TENSOR, PATH_GATHER, PATH_WORKLIST = 0, 1, 2, 3
@@ -129,6 +129,8 @@ SIGNATURES = {
     "cfpq_count": (ctypes.c_int, [_VP, ctypes.c_int32, _P(ctypes.c_size_t)]),
     "cfpq_get_lengths": (ctypes.c_int, [_VP, ctypes.c_int32, _P(Triple), _P(ctypes.c_uint32), ctypes.c_size_t,
                                         _P(ctypes.c_size_t)]),
+    "cfpq_get_path": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint32, _P(ctypes.c_uint32),
+                                     _P(ctypes.c_int32), ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_stats_get": (ctypes.c_int, [_VP, _P(Stats)]),
     "cfpq_destroy": (None, [_VP]),
     "cfpq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -311,6 +313,20 @@ class Query:
                "cfpq_get_lengths")
         pairs = np.stack([buf["m"][:k], buf["n"][:k]], axis=1).astype(np.uint32)
         return pairs, lens[:k]
+
+    def path(self, A, m: int, n: int):
+        """Single-path semantics (``cfpq_get_path``): one walk from m to n whose labels A
+        derives, as (nodes, labels): l + 1 uint32 node ids and l int32 terminal ids."""
+        a = self._aid(A)
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_get_path(self._h, a, int(m), int(n), None, None, 0, ctypes.byref(c)), "cfpq_get_path")
+        k = int(c.value)
+        nodes = np.zeros(k + 1, dtype=np.uint32)
+        labels = np.zeros(max(k, 1), dtype=np.int32)
+        _check(_lib().cfpq_get_path(self._h, a, int(m), int(n), nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                    labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), k, ctypes.byref(c)),
+               "cfpq_get_path")
+        return nodes, labels[:k]
 
     def get_device(self, A, dev_ptr: int, cap: int) -> int:
         """Writes R_A as triples into device memory at dev_ptr (cap triples); returns |R_A|."""

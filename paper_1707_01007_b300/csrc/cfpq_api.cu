@@ -413,6 +413,7 @@ extern "C" const char *cfpq_strerror(int code) {
         case CFPQ_ERR_CUDA: return "CUDA error";
         case CFPQ_ERR_BUFFER: return "buffer too small";
         case CFPQ_ERR_UNSUPPORTED: return "unsupported";
+        case CFPQ_ERR_NOT_FOUND: return "not found";
         default: return "unknown status";
     }
 }
@@ -810,6 +811,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     for (const Rule &r : rules) c->nt_dynamic[r.lhs] = 1;
     c->rules = rules;
     c->gstart = gstart;
+    if (c->lengths && !lengths_rules_ok(c)) return CFPQ_ERR_UNSUPPORTED;
     std::vector<int2> unary;
     for (int i = 0; i < g->n_unary; i++) unary.push_back(make_int2(g->unary[i].lhs, g->unary[i].term));
     std::vector<int32_t> eps(g->eps_lhs, g->eps_lhs + g->n_eps);
@@ -870,6 +872,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_TT, want_tt ? planes : 0}, {(void **)&c->d_R0, rowsz}, {(void **)&c->d_R1, rowsz},
         {(void **)&c->d_Trow, rowsz}, {(void **)&c->d_rules, rules.size() * sizeof(Rule)},
         {(void **)&c->d_gstart, gstart.size() * sizeof(int32_t)}, {(void **)&c->d_unary, unary.size() * sizeof(int2)},
+        {(void **)&c->d_nt_rules, (size_t)c->n_nt * sizeof(int2)},
         {(void **)&c->d_eps, eps.size() * sizeof(int32_t)}, {(void **)&c->d_edges, n_edges * sizeof(cfpq_edge)},
         {(void **)&c->d_state, sizeof(DevState)}, {(void **)&c->d_q, sizeof(QDesc)},
         {(void **)&c->d_counts, cells * sizeof(uint32_t)}, {(void **)&c->d_offsets, cells * sizeof(uint64_t)},
@@ -880,6 +883,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_list, (size_t)c->list_cap * sizeof(uint32_t)},
         {(void **)&c->d_colcnt, c->profile ? sizeof(uint32_t) * c->n_pad : 0},
         {(void **)&c->d_L, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0},
+        {(void **)&c->d_Wit, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0},
         {(void **)&c->d_Tsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
         {(void **)&c->d_TTsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0}};
     size_t arena = 0;
@@ -902,6 +906,9 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     if (!rules.empty())
         CK(cudaMemcpyAsync(c->d_rules, rules.data(), rules.size() * sizeof(Rule), cudaMemcpyHostToDevice, cs));
     CK(cudaMemcpyAsync(c->d_gstart, gstart.data(), gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, cs));
+    c->h_nt_rules.assign(c->n_nt, make_int2(-1, -1));
+    for (int gr = 0; gr < c->n_groups; gr++) c->h_nt_rules[rules[gstart[gr]].lhs] = make_int2(gstart[gr], gstart[gr + 1]);
+    CK(cudaMemcpyAsync(c->d_nt_rules, c->h_nt_rules.data(), c->n_nt * sizeof(int2), cudaMemcpyHostToDevice, cs));
     if (!unary.empty())
         CK(cudaMemcpyAsync(c->d_unary, unary.data(), unary.size() * sizeof(int2), cudaMemcpyHostToDevice, cs));
     if (!eps.empty()) CK(cudaMemcpyAsync(c->d_eps, eps.data(), eps.size() * sizeof(int32_t), cudaMemcpyHostToDevice, cs));
@@ -933,6 +940,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.SW = c->SW;
     q.rules = c->d_rules;
     q.gstart = c->d_gstart;
+    q.nt_rules = c->d_nt_rules;
     q.unary = c->d_unary;
     q.eps = c->d_eps;
     q.edges = c->d_edges;
@@ -1282,6 +1290,26 @@ extern "C" int cfpq_get_lengths(cfpq_ctx *c, int32_t A, cfpq_triple *buf, uint32
     CK(cudaMemcpyAsync(lengths, c->d_lens, total * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return CFPQ_OK;
+}
+
+extern "C" int cfpq_get_path(cfpq_ctx *c, int32_t A, uint32_t m, uint32_t n, uint32_t *nodes, int32_t *labels,
+                             size_t cap, size_t *len) {
+    if (!c || !len || A < 0 || A >= c->n_nt || m >= c->n || n >= c->n || (!nodes) != (!labels)) return CFPQ_ERR_INVALID;
+    if (!c->lengths) return CFPQ_ERR_UNSUPPORTED;
+    if (!c->solved) return CFPQ_ERR_NOT_SOLVED;
+    cudaStream_t s = c->last_stream;
+    uint32_t word = 0, l = 0;
+    CK(cudaMemcpyAsync(&word, c->d_T + (uint64_t)A * c->plane + (uint64_t)m * c->W + n / 32, sizeof(word),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&l, c->d_L + (uint64_t)A * c->lplane + (uint64_t)m * c->n_pad + n, sizeof(l),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!((word >> (n & 31)) & 1u)) return CFPQ_ERR_NOT_FOUND;
+    if (l == 0xFFFFFFFFu) return CFPQ_ERR_UNSUPPORTED;
+    *len = l;
+    if (!nodes) return CFPQ_OK;
+    if (cap < l) return CFPQ_ERR_BUFFER;
+    return lengths_path(c, A, m, n, l, nodes, labels);
 }
 
 extern "C" int cfpq_stats_get(const cfpq_ctx *c, cfpq_stats *out) {

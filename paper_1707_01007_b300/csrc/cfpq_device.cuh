@@ -76,6 +76,7 @@ struct QDesc {
     uint32_t SW;                        // summary words per row (a multiple of 4)
     const Rule *rules;                  // sorted by lhs; group g = rules[gstart[g] .. gstart[g+1])
     const int32_t *gstart;
+    const int2 *nt_rules;               // per non-terminal A: its productions rules[x .. y) (-1, -1: none)
     const int2 *unary;                  // (lhs, term)
     const int32_t *eps;
     const cfpq_edge *edges;

@@ -32,6 +32,7 @@ struct cfpq_ctx {
     uint32_t list_cap = 0;
     bool lengths = false;             // single-path semantics: a length plane per non-terminal
     uint32_t *d_L = nullptr;          // [n_nt][n_pad][n_pad] lengths (in the arena)
+    uint32_t *d_Wit = nullptr;        // [n_nt][n_pad][n_pad] derivation step of each pair (in the arena)
     uint64_t lplane = 0;              // cells per length plane = n_pad * n_pad
     uint32_t *d_Tsum = nullptr;       // word summary of T (lengths only; in the arena)
     uint32_t *d_TTsum = nullptr;      // word summary of T^T (lengths only; in the arena)
@@ -45,6 +46,7 @@ struct cfpq_ctx {
     uint32_t *d_R0 = nullptr, *d_R1 = nullptr, *d_Trow = nullptr;
     cfpq::Rule *d_rules = nullptr;
     int32_t *d_gstart = nullptr;
+    int2 *d_nt_rules = nullptr;       // per non-terminal: range of its productions in d_rules
     int2 *d_unary = nullptr;
     int32_t *d_eps = nullptr;
     cfpq_edge *d_edges = nullptr;
@@ -64,6 +66,7 @@ struct cfpq_ctx {
     void *h_wl = nullptr;                    // worklist path state
     std::vector<int2> h_unary;               // (lhs, terminal) productions, host copy
     std::vector<int32_t> h_eps;
+    std::vector<int2> h_nt_rules;            // host copy of d_nt_rules (kept alive for the async copy)
     // execution
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -126,6 +129,8 @@ int lengths_enqueue_seed(cfpq_ctx *c, cudaStream_t s);
 int lengths_enqueue_iteration(cfpq_ctx *c, cudaStream_t s);
 int lengths_enqueue_merge(cfpq_ctx *c, cudaStream_t s);
 int lengths_of_triples(cfpq_ctx *c, const cfpq_triple *d_tr, size_t count, uint32_t *d_out, cudaStream_t s);
+int lengths_rules_ok(const cfpq_ctx *c);  // few enough productions for the derivation-step encoding
+int lengths_path(cfpq_ctx *c, int32_t A, uint32_t m, uint32_t n, uint32_t len, uint32_t *nodes, int32_t *labels);
 
 // worklist path (cfpq_worklist.cu)
 int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges);

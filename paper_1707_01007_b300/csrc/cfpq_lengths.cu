@@ -31,9 +31,20 @@
 
 namespace cfpq {
 
+// Derivation step of a pair (one uint32 per cell beside its length, the "witness"), from
+// which cfpq_get_path rebuilds the walk: the empty walk (A -> eps), an edge with its label,
+// or production rules[r] with middle node k. Ordered so that a smaller word is preferred.
+constexpr uint32_t kWitEps = 0x40000000u;             // (m, m) by A -> eps: length 0
+constexpr uint32_t kWitEdge = 0x80000000u;            // | label: an edge (m, label, n), length 1
+constexpr uint32_t kWitK = 17;                        // split: (r << 17) | k, r < 8192
+constexpr uint32_t kMaxLenRules = 1u << (30 - kWitK);
+
 // Matrix initialisation of the lengths; runs after k_seed (which sets the same pairs in T).
-// eps_mask bit a: A -> eps, so a loop edge (m, x, m) of a nullable A keeps the length 0.
-__global__ void k_seed_lengths(const QDesc *qd, uint32_t *L, uint64_t lplane, unsigned long long eps_mask) {
+// eps_mask bit a: A -> eps, so a loop edge (m, x, m) of a nullable A is left to the empty walk
+// (length 0). Several edges of one pair store their labels in any order here; the next
+// kernel keeps the smallest.
+__global__ void k_seed_lengths(const QDesc *qd, uint32_t *L, uint32_t *Wit, uint64_t lplane,
+                               unsigned long long eps_mask) {
     const QDesc &q = *qd;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
@@ -42,14 +53,32 @@ __global__ void k_seed_lengths(const QDesc *qd, uint32_t *L, uint64_t lplane, un
         for (int u = 0; u < q.n_unary; u++)
             if (q.unary[u].y == ed.label) {
                 const int a = q.unary[u].x;
-                const uint32_t len = (ed.src == ed.dst && ((eps_mask >> a) & 1ull)) ? 0u : 1u;
-                L[(uint64_t)a * lplane + (uint64_t)ed.src * q.n_pad + ed.dst] = len;
+                if (ed.src == ed.dst && ((eps_mask >> a) & 1ull)) continue;
+                const uint64_t cell = (uint64_t)a * lplane + (uint64_t)ed.src * q.n_pad + ed.dst;
+                L[cell] = 1u;
+                Wit[cell] = kWitEdge | (uint32_t)ed.label;
             }
     }
     for (uint64_t t = tid; t < (uint64_t)q.n_eps * q.n; t += nth) {
         const int a = q.eps[t / q.n];
-        const uint64_t m = t % q.n;
-        L[(uint64_t)a * lplane + m * q.n_pad + m] = 0u;
+        const uint64_t cell = (uint64_t)a * lplane + (t % q.n) * q.n_pad + t % q.n;
+        L[cell] = 0u;
+        Wit[cell] = kWitEps;
+    }
+}
+
+// Second pass over the edges: the smallest label among several edges of one pair.
+__global__ void k_seed_witness_min(const QDesc *qd, uint32_t *Wit, uint64_t lplane, unsigned long long eps_mask) {
+    const QDesc &q = *qd;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < q.n_edges;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const cfpq_edge ed = q.edges[e];
+        for (int u = 0; u < q.n_unary; u++)
+            if (q.unary[u].y == ed.label) {
+                const int a = q.unary[u].x;
+                if (ed.src == ed.dst && ((eps_mask >> a) & 1ull)) continue;
+                atomicMin(&Wit[(uint64_t)a * lplane + (uint64_t)ed.src * q.n_pad + ed.dst], kWitEdge | (uint32_t)ed.label);
+            }
     }
 }
 
@@ -57,12 +86,14 @@ __global__ void k_seed_lengths(const QDesc *qd, uint32_t *L, uint64_t lplane, un
 // pair). The middle nodes k under A -> B C are the set bits of row i of T_B AND row j of TT_C
 // (column j of T_C): the two rows' word summaries are ANDed 16 words at a time (vector
 // loads), and only the words both flag are read and ANDed. Returns the minimum of
-// l_B(i, k) + l_C(k, j) (UINT64_MAX if there is no middle node).
+// l_B(i, k) + l_C(k, j) (UINT64_MAX if there is no middle node) and, in *wit, the production
+// index and middle node of the first minimum found (smallest index, then smallest k).
 __device__ __forceinline__ unsigned long long pair_length(const QDesc &q, const uint32_t *__restrict__ L,
                                                           uint64_t lplane, int r0, int r1, uint32_t i, uint32_t j,
-                                                          unsigned *hits) {
+                                                          unsigned *hits, uint32_t *wit) {
     const uint32_t W = q.W, np = q.n_pad, SW = q.SW;
     unsigned long long best = ~0ull;
+    *wit = 0u;
     for (int r = r0; r < r1; r++) {
         const int B = q.rules[r].b, C = q.rules[r].c;
         const uint4 *sumB = reinterpret_cast<const uint4 *>(q.Tsum + ((uint64_t)B * np + i) * SW);
@@ -94,7 +125,10 @@ __device__ __forceinline__ unsigned long long pair_length(const QDesc &q, const 
                             kw &= kw - 1;
                             const unsigned long long cand =
                                 (unsigned long long)__ldcg(LB + k) + __ldcg(LC + (uint64_t)k * np);
-                            best = cand < best ? cand : best;
+                            if (cand < best) {  // productions, then k, ascending: the first minimum is kept
+                                best = cand;
+                                *wit = ((uint32_t)r << kWitK) | k;
+                            }
                             (*hits)++;
                         }
                     }
@@ -116,17 +150,12 @@ constexpr int kScanU = 8;  // 32-word chunks of a row of N loaded together
 // shared memory (every lane still holding bits gives one per round); whenever 32 are queued,
 // every lane computes one pair's length, so the lanes stay busy however the new pairs are
 // spread over rows and words.
-__global__ void __launch_bounds__(256, 2) k_lengths(const QDesc *qd, uint32_t *L, uint64_t lplane) {
+__global__ void __launch_bounds__(256, 2) k_lengths(const QDesc *qd, uint32_t *L, uint32_t *Wit, uint64_t lplane) {
     __shared__ uint32_t q_i[kLenWarps][kLenQ], q_j[kLenWarps][kLenQ];
     __shared__ uint8_t q_a[kLenWarps][kLenQ];
     __shared__ int2 grp[kMaxNT];  // productions of each left-hand side: [x, y)
     const QDesc &q = *qd;
-    if (threadIdx.x < (unsigned)q.n_nt) {
-        int2 g2 = make_int2(-1, -1);
-        for (int gr = 0; gr < q.n_groups; gr++)
-            if (q.rules[q.gstart[gr]].lhs == (int)threadIdx.x) g2 = make_int2(q.gstart[gr], q.gstart[gr + 1]);
-        grp[threadIdx.x] = g2;
-    }
+    if (threadIdx.x < (unsigned)q.n_nt) grp[threadIdx.x] = q.nt_rules[threadIdx.x];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -145,8 +174,11 @@ __global__ void __launch_bounds__(256, 2) k_lengths(const QDesc *qd, uint32_t *L
         if (lane < cnt) {
             const int a = q_a[warp][lane];
             const uint32_t i = q_i[warp][lane], j = q_j[warp][lane];
-            const unsigned long long best = pair_length(q, L, lplane, grp[a].x, grp[a].y, i, j, &hits);
-            L[(uint64_t)a * lplane + (uint64_t)i * q.n_pad + j] = best >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)best;
+            uint32_t wit;
+            const unsigned long long best = pair_length(q, L, lplane, grp[a].x, grp[a].y, i, j, &hits, &wit);
+            const uint64_t cell = (uint64_t)a * lplane + (uint64_t)i * q.n_pad + j;
+            L[cell] = best >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)best;
+            Wit[cell] = wit;
         }
         __syncwarp();
     };
@@ -272,6 +304,44 @@ __global__ void __launch_bounds__(256) k_merge_tt(const QDesc *qd) {
     }
 }
 
+// Rebuilds the walk of (a, m, n) from the recorded derivation steps, depth first, left child
+// first (one thread). Stack entries (A, i, j, offset of the sub-walk's first edge). Every
+// child was derived in an earlier loop execution than its parent, so the stack never holds
+// more entries than executions + 1; stack_cap and max_steps only guard against a corrupt
+// state. status: 0 ok, 1 stack full, 2 step limit, 3 inconsistent witness.
+__global__ void k_path(const QDesc *qd, const uint32_t *L, const uint32_t *Wit, uint64_t lplane, int a, uint32_t m,
+                       uint32_t n, uint32_t len, uint32_t *nodes, int32_t *labels, uint4 *stack, uint32_t stack_cap,
+                       unsigned long long max_steps, uint32_t *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const QDesc &q = *qd;
+    const uint64_t np = q.n_pad;
+    nodes[0] = m;
+    uint32_t sp = 0;
+    stack[sp++] = make_uint4((uint32_t)a, m, n, 0u);
+    unsigned long long steps = 0;
+    while (sp > 0) {
+        if (++steps > max_steps) { *status = 2u; return; }
+        const uint4 e = stack[--sp];
+        const uint32_t w = Wit[(uint64_t)e.x * lplane + (uint64_t)e.y * np + e.z];
+        if (w == kWitEps) continue;
+        if (w & kWitEdge) {
+            if (e.w >= len) { *status = 3u; return; }
+            labels[e.w] = (int32_t)(w & ~kWitEdge);
+            nodes[e.w + 1] = e.z;
+            continue;
+        }
+        const uint32_t r = w >> kWitK, k = w & ((1u << kWitK) - 1u);
+        if (r >= (uint32_t)q.n_rules || k >= q.n) { *status = 3u; return; }
+        const int B = q.rules[r].b, C = q.rules[r].c;
+        const uint32_t lb = L[(uint64_t)B * lplane + (uint64_t)e.y * np + k];
+        if ((unsigned long long)e.w + lb > len) { *status = 3u; return; }
+        if (sp + 2 > stack_cap) { *status = 1u; return; }
+        stack[sp++] = make_uint4((uint32_t)C, k, e.z, e.w + lb);
+        stack[sp++] = make_uint4((uint32_t)B, e.y, k, e.w);
+    }
+    *status = 0u;
+}
+
 // Lengths of extracted triples: out[t] = L[A][m * n_pad + n].
 __global__ void k_triple_lengths(const cfpq_triple *tr, uint64_t count, const uint32_t *L, uint64_t lplane,
                                  uint32_t n_pad, uint32_t *out) {
@@ -290,7 +360,8 @@ static unsigned long long eps_mask(const cfpq_ctx *c) {
 int lengths_enqueue_seed(cfpq_ctx *c, cudaStream_t s) {
     const uint64_t work = std::max<uint64_t>(c->n_edges, (uint64_t)c->n_eps_rules * c->n);
     const uint32_t blocks = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (work + 255) / 256), 148ull * 16);
-    k_seed_lengths<<<blocks, 256, 0, s>>>(c->d_q, c->d_L, c->lplane, eps_mask(c));
+    k_seed_lengths<<<blocks, 256, 0, s>>>(c->d_q, c->d_L, c->d_Wit, c->lplane, eps_mask(c));
+    k_seed_witness_min<<<blocks, 256, 0, s>>>(c->d_q, c->d_Wit, c->lplane, eps_mask(c));
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 
@@ -312,7 +383,7 @@ int lengths_enqueue_iteration(cfpq_ctx *c, cudaStream_t s) {
     if (rc != CFPQ_OK) return rc;
     const uint64_t blocks_needed = ((uint64_t)c->n_nt * c->n + kLenWarps - 1) / kLenWarps;
     const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)c->len_grid, std::max<uint64_t>(1, blocks_needed));
-    k_lengths<<<blocks, 256, 0, s>>>(c->d_q, c->d_L, c->lplane);
+    k_lengths<<<blocks, 256, 0, s>>>(c->d_q, c->d_L, c->d_Wit, c->lplane);
     c->iter_launches++;
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
@@ -332,6 +403,41 @@ int lengths_of_triples(cfpq_ctx *c, const cfpq_triple *d_tr, size_t count, uint3
     const uint32_t blocks = (uint32_t)std::min<uint64_t>((count + 255) / 256, 148ull * 32);
     k_triple_lengths<<<blocks, 256, 0, s>>>(d_tr, count, c->d_L, c->lplane, c->n_pad, d_out);
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
+
+int lengths_rules_ok(const cfpq_ctx *c) { return c->rules.size() < kMaxLenRules; }
+
+// One walk of (A, m, n) into host memory (cfpq_get_path after its checks).
+int lengths_path(cfpq_ctx *c, int32_t A, uint32_t m, uint32_t n, uint32_t len, uint32_t *nodes, int32_t *labels) {
+    cudaStream_t s = c->last_stream;
+    const uint32_t stack_cap = (uint32_t)std::min<uint64_t>((uint64_t)c->stats.iterations + 8, 1ull << 30);
+    const unsigned long long max_steps = (2ull * len + 1ull) * ((unsigned long long)c->stats.iterations + 1ull) + 16ull;
+    const size_t b_nodes = ((size_t)len + 1) * sizeof(uint32_t), b_labels = std::max<size_t>(1, len) * sizeof(int32_t);
+    const size_t b_stack = (size_t)stack_cap * sizeof(uint4);
+    const size_t off_labels = (b_nodes + 255) / 256 * 256, off_stack = off_labels + (b_labels + 255) / 256 * 256;
+    const size_t off_status = off_stack + (b_stack + 255) / 256 * 256;
+    char *buf = nullptr;
+    if (cudaMalloc(&buf, off_status + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return CFPQ_ERR_NOMEM;
+    }
+    uint32_t *d_nodes = reinterpret_cast<uint32_t *>(buf);
+    int32_t *d_labels = reinterpret_cast<int32_t *>(buf + off_labels);
+    uint4 *d_stack = reinterpret_cast<uint4 *>(buf + off_stack);
+    uint32_t *d_status = reinterpret_cast<uint32_t *>(buf + off_status);
+    uint32_t status = 4u;
+    int rc = CFPQ_OK;
+    k_path<<<1, 32, 0, s>>>(c->d_q, c->d_L, c->d_Wit, c->lplane, A, m, n, len, d_nodes, d_labels, d_stack, stack_cap,
+                            max_steps, d_status);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&status, d_status, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(nodes, d_nodes, b_nodes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        (len && cudaMemcpyAsync(labels, d_labels, (size_t)len * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        rc = CFPQ_ERR_CUDA;
+    cudaFree(buf);
+    if (rc == CFPQ_OK && status != 0u) rc = CFPQ_ERR_CUDA;
+    return rc;
 }
 
 }  // namespace cfpq

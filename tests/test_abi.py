@@ -35,8 +35,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_strerror_names_every_status():
     lib = eng.library()
-    names = {lib.cfpq_strerror(c).decode() for c in range(9)}
-    assert len(names) == 9
+    names = {lib.cfpq_strerror(c).decode() for c in range(10)}
+    assert len(names) == 10
     assert lib.cfpq_strerror(99).decode() == "unknown status"
 
 
@@ -109,6 +109,7 @@ def test_lengths_options_checked_before_device_use():
         opt.schedule, opt.path, opt.lengths = schedule, path, 1
         assert _create(g.cnf, 4, [(0, 0, 1)], ctypes.byref(opt))[0] == eng.ERR_UNSUPPORTED
     assert lib.cfpq_get_lengths(None, 0, None, None, 0, None) == eng.ERR_INVALID
+    assert lib.cfpq_get_path(None, 0, 0, 0, None, None, 0, None) == eng.ERR_INVALID
 
 
 def test_null_arguments():

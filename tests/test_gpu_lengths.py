@@ -223,3 +223,99 @@ def test_lengths_unavailable_without_the_option_and_in_batches():
     with pytest.raises(eng.CfpqError) as ei:
         eng.solve_batch([withlen])
     assert ei.value.code == eng.ERR_UNSUPPORTED
+
+
+# ----------------------------------------------------------------------------- walks (Section 5)
+
+_EDGE_SETS = {}
+
+
+def _edge_set(graph):
+    key = id(graph)
+    if key not in _EDGE_SETS:
+        _EDGE_SETS.clear()
+        _EDGE_SETS[key] = (graph, set(map(tuple, np.asarray(graph.edges).reshape(-1, 3).tolist())))
+    return _EDGE_SETS[key][1]
+
+
+def _check_walk(graph, cnf, a, m, n, length, nodes, labels, cyk_up_to=24):
+    """The walk starts at m, ends at n, has the reported length, uses only edges of the graph
+    and (for short walks) its label string is derived from A (CYK)."""
+    assert len(labels) == length and len(nodes) == length + 1
+    assert int(nodes[0]) == m and int(nodes[-1]) == n
+    edges = _edge_set(graph)
+    for t in range(length):
+        assert (int(nodes[t]), int(labels[t]), int(nodes[t + 1])) in edges, (t, nodes[t], labels[t], nodes[t + 1])
+    if length <= cyk_up_to:
+        assert a in oracle.cyk_table(cnf, [int(x) for x in labels])[0][length]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_every_pair_has_a_walk_of_its_length(seed):
+    graph = synth.random_graph(30 + 7 * seed, 70 + 15 * seed, 3, seed=seed)
+    text = synth.random_grammar_text(5, 3, 9, 6, seed % 3, seed=seed)
+    g, q = solve_lengths(graph, text)
+    cnf = oracle.parse_grammar(text, graph.labels)
+    checked = 0
+    for a, nm in enumerate(cnf.names):
+        pairs, lens = q.lengths(nm)
+        for (m, n), l in zip(pairs.tolist()[:60], lens.tolist()[:60]):
+            nodes, labels = q.path(nm, m, n)
+            _check_walk(graph, cnf, a, m, n, l, nodes, labels)
+            checked += 1
+    assert checked > 0
+
+
+def test_walks_on_two_cycles_are_a_k_b_k():
+    p, qq = 33, 32
+    graph = synth.two_cycles(p, qq)
+    g, q = solve_lengths(graph, synth.GRAMMAR_C3)
+    cnf = oracle.parse_grammar(synth.GRAMMAR_C3, graph.labels)
+    pairs, lens = q.lengths("S")
+    for (m, n), l in list(zip(pairs.tolist(), lens.tolist()))[::37]:
+        nodes, labels = q.path("S", m, n)
+        k = l // 2
+        assert labels.tolist() == [0] * k + [1] * k
+        _check_walk(graph, cnf, cnf.names.index("S"), m, n, l, nodes, labels)
+
+
+def test_empty_walk_missing_pair_and_determinism():
+    graph = synth.Graph(n=4, edges=np.array([(0, 0, 1), (1, 1, 2), (0, 0, 1)], dtype=np.int64),
+                        labels=["t0", "t1"], meta={"kind": "test"})
+    text = "S A B\nA t0\nB t1\nE eps\n"
+    g, q = solve_lengths(graph, text)
+    nodes, labels = q.path("E", 3, 3)
+    assert nodes.tolist() == [3] and labels.size == 0
+    nodes, labels = q.path("S", 0, 2)
+    assert nodes.tolist() == [0, 1, 2] and labels.tolist() == [0, 1]
+    with pytest.raises(eng.CfpqError) as ei:
+        q.path("S", 2, 0)
+    assert ei.value.code == eng.ERR_NOT_FOUND
+    c = ctypes.c_size_t()
+    small = (ctypes.c_uint32 * 2)()
+    lab = (ctypes.c_int32 * 1)()
+    assert eng.library().cfpq_get_path(q.handle, g.id("S"), 0, 2, small, lab, 1, ctypes.byref(c)) == eng.ERR_BUFFER
+    assert c.value == 2
+    graph2 = synth.hierarchy(2000, 600, seed=3)
+    g2, q2 = solve_lengths(graph2, synth.GRAMMAR_SG)
+    pairs, _ = q2.lengths("S")
+    for m, n in pairs.tolist()[::997]:
+        a1, b1 = q2.path("S", m, n)
+        a2, b2 = q2.path("S", m, n)
+        assert np.array_equal(a1, a2) and np.array_equal(b1, b2)
+
+
+@pytest.mark.parametrize("text", [synth.GRAMMAR_Q1, synth.GRAMMAR_SG])
+def test_full_size_hierarchy_walks(text):
+    graph = synth.hierarchy(16384, 5000, seed=1)
+    g, q = solve_lengths(graph, text)
+    cnf = oracle.parse_grammar(text, graph.labels)
+    rng = np.random.default_rng(3)
+    for a, nm in enumerate(cnf.names):
+        pairs, lens = q.lengths(nm)
+        if pairs.shape[0] == 0:
+            continue
+        for t in rng.choice(pairs.shape[0], size=min(40, pairs.shape[0]), replace=False).tolist():
+            m, n, l = int(pairs[t, 0]), int(pairs[t, 1]), int(lens[t])
+            nodes, labels = q.path(nm, m, n)
+            _check_walk(graph, cnf, a, m, n, l, nodes, labels, cyk_up_to=16)
