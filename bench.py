@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--path", default="tensor", choices=["auto", "tensor", "gather"])
     ap.add_argument("--schedule", default="jacobi", choices=["jacobi", "inplace"])
+    ap.add_argument("--tensor", default="dense", choices=["dense", "skip"],
+                    help="tensor products of the timed leg: every K step (Algorithm 1's dense product) or "
+                         "only the K steps whose operand tiles are both non-zero")
     ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -233,22 +236,24 @@ def tc_traffic_per_launch():
         return None
 
 
-def roofline(eng, graph, gs, path, schedule, stream):
+def roofline(eng, graph, gs, path, schedule, stream, dense=True):
     """Dominant product kernel: every product launch of a solve with the timed options is
     bracketed by CUDA events on the launching stream (profile mode); algorithmic work per
-    launch is 2 n^3 per production of the group (tensor) or the counted words (gather)."""
+    launch is 2 n^3 per production of the group (tensor; with tile skipping, the K steps the
+    launch issued) or the counted words (gather)."""
     peaks, kind = load_peaks()
     prod_ms = prod_l = tens_ms = tens_l = 0
     flops = bytes_ = useful = 0.0
     for g in gs:
-        q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, profile=True, timeout_s=300.0)
+        q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, profile=True, timeout_s=300.0,
+                      dense_tensor=dense)
         q.solve(stream)
         s = q.stats()
         prod_ms += s["product_ms"]
         prod_l += s["product_launches"]
         tens_ms += s["tensor_ms"]
         tens_l += s["tensor_launches"]
-        flops += s["dense_ops"]
+        flops += s["tensor_live_ops"]
         bytes_ += s["product_bytes"]
         useful += s["useful_ops"]
         q.close()
@@ -259,7 +264,8 @@ def roofline(eng, graph, gs, path, schedule, stream):
         # the integer tensor references of this device (sm_103a has no 8-bit integer tcgen05 kind)
         mma = eng.measure_mma_sync_peaks()
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": tc_traffic_per_launch(), "kernel": "k_tc_bool_gemm", "launches": tens_l,
+                "traffic": tc_traffic_per_launch() if dense else None, "kernel": "k_tc_bool_gemm",
+                "tile_skipping": not dense, "launches": tens_l,
                 "launch_ms": tens_ms / tens_l, "flops_per_launch": flops / tens_l,
                 "peak_note": f"{kind} bf16 dense burst x 2 (fp8 e4m3 : bf16 nominal ratio); "
                              f"frac against the sustained figure x 2: {achieved / sustained:.3f}",
@@ -281,9 +287,10 @@ def roofline(eng, graph, gs, path, schedule, stream):
 class Leg:
     """The queries of the workload resident on the device with one set of options."""
 
-    def __init__(self, eng, torch, graph, gs, path, schedule, stream):
+    def __init__(self, eng, torch, graph, gs, path, schedule, stream, dense=True):
         self.eng, self.torch, self.gs, self.stream = eng, torch, gs, stream
-        self.qs = [eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0) for g in gs]
+        self.qs = [eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0,
+                             dense_tensor=dense) for g in gs]
         caps = []
         for q, g in zip(self.qs, gs):
             q.solve(stream)
@@ -342,7 +349,8 @@ def engine_arm(args):
         qj.close()
     ops_per_step = products * 2.0 * float(N_NODES) ** 3
 
-    main = Leg(eng, torch, graph, gs, path, schedule, stream)
+    dense = args.tensor == "dense"
+    main = Leg(eng, torch, graph, gs, path, schedule, stream, dense)
     for _ in range(args.warmup):
         main.step()
     st = [q.stats() for q in main.qs]
@@ -365,18 +373,25 @@ def engine_arm(args):
     # the same closure with the other schedules / product paths (exact results in all)
     alternatives = {}
     if not args.no_alternatives:
-        for name, (pth, sch) in {"tensor_inplace": (eng.PATH_TENSOR, eng.SCHED_INPLACE),
-                                 "auto_inplace": (eng.PATH_AUTO, eng.SCHED_INPLACE)}.items():
-            if pth == path and sch == schedule:
+        for name, (pth, sch, dns) in {"tensor_tile_skip": (eng.PATH_TENSOR, eng.SCHED_JACOBI, False),
+                                      "tensor_inplace": (eng.PATH_TENSOR, eng.SCHED_INPLACE, True),
+                                      "tensor_inplace_tile_skip": (eng.PATH_TENSOR, eng.SCHED_INPLACE, False),
+                                      "auto_inplace": (eng.PATH_AUTO, eng.SCHED_INPLACE, False)}.items():
+            if pth == path and sch == schedule and dns == dense:
                 continue
-            leg = Leg(eng, torch, graph, gs, pth, sch, stream)
+            leg = Leg(eng, torch, graph, gs, pth, sch, stream, dns)
             leg.step()
             ams = leg.time(max(2, min(args.steps, 5)))
             alternatives[name] = {"ms_per_step": ams, "value": world * ops_per_step / (ams / 1e3) / 1e9,
                                   "iterations": [q.stats()["iterations"] for q in leg.qs],
                                   "tensor_products": sum(q.stats()["tensor_products"] for q in leg.qs),
-                                  "gather_products": sum(q.stats()["gather_products"] for q in leg.qs)}
+                                  "gather_products": sum(q.stats()["gather_products"] for q in leg.qs),
+                                  "tensor_ops_executed": sum(q.stats()["tensor_live_ops"] for q in leg.qs)}
             leg.close()
+            if name == "tensor_tile_skip":
+                r = roofline(eng, graph, gs, pth, sch, stream, dense=False)
+                alternatives[name]["roofline_executed"] = {k: r.get(k) for k in
+                                                           ("achieved", "peak", "unit", "frac", "launches", "launch_ms")}
 
     # e2e through the C ABI with host buffers: create (edge upload), solve, copy triples back
     h2d = graph.n_edges * 12 * len(grammars)
@@ -387,7 +402,7 @@ def engine_arm(args):
     for _ in range(e2e_steps):
         d2h = 0
         for g in gs:
-            q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0)
+            q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0, dense_tensor=dense)
             q.solve()
             for nm in g.names:
                 d2h += q.triples(nm).shape[0] * 12
@@ -396,7 +411,7 @@ def engine_arm(args):
     e2e_s = max_over_ranks(e2e_s)
     e2e_val = job_rate(ops_per_step, e2e_s, world) / 1e9
 
-    roof = roofline(eng, graph, gs, path, schedule, stream)
+    roof = roofline(eng, graph, gs, path, schedule, stream, dense)
 
     line = {
         "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
@@ -406,6 +421,7 @@ def engine_arm(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_NODES, "classes": N_CLASSES, "seed": SEED,
                    "grammars": [nm for nm, _ in grammars], "path": args.path, "schedule": args.schedule,
+                   "tensor_products": args.tensor,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per query 3 x 7 x 32 MiB bit planes + 7 x 32 MiB transposes)",
                    "products_per_step": products, "dense_ops_executed_per_step": executed_dense,

@@ -113,7 +113,12 @@ typedef struct {
                                  WORKLIST) and fewer than 8192 distinct binary productions; adds
                                  two uint32 per (A, m, n) cell (a length and the derivation step
                                  that set it: 2 * n_pad^2 * |N| * 4 bytes) to the context. Default 0 */
-    int32_t reserved;         /* must be 0 */
+    int32_t dense_tensor;     /* 0 (default): tensor-core products skip the K steps where either
+                                 operand tile (128 x 128 bits of T_B, 256 x 128 bits of T_C^T) is
+                                 all zero, and output tiles with no such step (occupancy bitmaps
+                                 refreshed at the start of each loop execution for the operands
+                                 that changed); 1: every K step of every tile, Algorithm 1's dense
+                                 product as written. Both give the same result */
 } cfpq_options;
 
 typedef struct {
@@ -143,6 +148,8 @@ typedef struct {
     double lengths_splits;    /* lengths on, profile mode: (production, middle node k) splits the
                                  length kernels examined, i.e. sum over new pairs (A, i, j) and
                                  productions A -> B C of |{k : (i, k) in T_B, (k, j) in T_C}| */
+    double tensor_live_ops;   /* Boolean ops the tensor-core products executed: 2 x 128 x 256 x 128
+                                 per K step issued (equals dense_ops with dense_tensor = 1) */
 } cfpq_stats;
 
 typedef struct cfpq_ctx cfpq_ctx;

@@ -58,7 +58,7 @@ class Triple(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("path", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("timeout_s", ctypes.c_double),
-                ("lengths", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lengths", ctypes.c_int32), ("dense_tensor", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -71,7 +71,8 @@ class Stats(ctypes.Structure):
                 ("tensor_launches", ctypes.c_int64), ("product_bytes", ctypes.c_double),
                 ("worklist_items", ctypes.c_int64), ("schedule", ctypes.c_int32), ("gather_cpl", ctypes.c_int32),
                 ("useful_ops", ctypes.c_double), ("lengths_ms", ctypes.c_double),
-                ("lengths_launches", ctypes.c_int64), ("lengths_splits", ctypes.c_double)]
+                ("lengths_launches", ctypes.c_int64), ("lengths_splits", ctypes.c_double),
+                ("tensor_live_ops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -235,7 +236,7 @@ class Query:
 
     def __init__(self, grammar: Grammar, n: int, edges, schedule: int = SCHED_INPLACE, path: int = PATH_AUTO,
                  use_graph: bool = True, max_iter: int = 0, timeout_s: float = 0.0, profile: bool = False,
-                 lengths: bool = False):
+                 lengths: bool = False, dense_tensor: bool = False):
         self.grammar = grammar
         self.n = int(n)
         self._h = None
@@ -245,6 +246,7 @@ class Query:
         opt.profile = int(bool(profile))
         opt.max_iter, opt.timeout_s = int(max_iter), float(timeout_s)
         opt.lengths = int(bool(lengths))
+        opt.dense_tensor = int(bool(dense_tensor))
         rec = _edges_struct(edges)
         h = ctypes.c_void_p()
         ptr = rec.ctypes.data_as(ctypes.POINTER(Edge)) if rec.size else None

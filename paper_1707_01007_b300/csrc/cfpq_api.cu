@@ -503,6 +503,7 @@ static int enqueue_auto_tensor_graph(cfpq_ctx *c, cudaStream_t s) {
     int rc = add_if(s, c->h_choice[c->n_groups], &any_body);
     if (rc != CFPQ_OK) return rc;
     if ((rc = begin_branch(c->aux_stream, any_body)) != CFPQ_OK) return rc;
+    rc = enqueue_tensor_occupancy(c, c->aux_stream);
     for (int g = 0; g < c->n_groups && rc == CFPQ_OK; g++) {
         cudaGraph_t body;
         if ((rc = add_if(c->aux_stream, c->h_choice[g], &body)) != CFPQ_OK) break;
@@ -531,6 +532,8 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
             const int rc = enqueue_auto_tensor_graph(c, s);
             if (rc != CFPQ_OK) return rc;
         } else {
+            const int orc = enqueue_tensor_occupancy(c, s);
+            if (orc != CFPQ_OK) return orc;
             for (int g = 0; g < c->n_groups; g++) {
                 int rc = enqueue_tensor_transposes_gated(c, g, s);
                 if (rc == CFPQ_OK && prof) rc = enqueue_useful_work(c, g, s);
@@ -541,6 +544,10 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
             }
         }
     } else {
+        if (c->path == CFPQ_PATH_TENSOR) {
+            const int orc = enqueue_tensor_occupancy(c, s);
+            if (orc != CFPQ_OK) return orc;
+        }
         for (int g = 0; g < c->n_groups; g++) {
             if (!c->group_tensor[g]) continue;
             int rc = enqueue_tensor_transposes(c, g, s);
@@ -718,7 +725,7 @@ int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
     DevState st0;
     memset(&st0, 0, sizeof(st0));
     st0.max_iter = c->max_iter;
-    for (int a = 0; a < c->n_nt; a++) st0.dirty[a] = 1u;
+    for (int a = 0; a < c->n_nt; a++) st0.dirty[a] = st0.occ_now[a] = 1u;
     for (int g = 0; g < c->n_groups && g < kMaxNT; g++) st0.use_tensor[g] = c->group_tensor[g] ? 1u : 0u;
     CK(cudaMemcpyAsync(c->d_state, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
     c->fixed_launches = 1;
@@ -760,6 +767,7 @@ int apply_status(cfpq_ctx *c, const DevState &st) {
     c->stats.product_bytes = 4.0 * (double)st.prof_words;
     c->stats.useful_ops = 2.0 * (double)st.useful_macs;
     c->stats.lengths_splits = (double)st.len_splits;
+    c->stats.tensor_live_ops = kTcOpsPerStep * (double)st.tc_live_steps;
     int rc = CFPQ_OK;
     if (st.error == kErrIterLimit) rc = CFPQ_ERR_ITER_LIMIT;
     else if (st.error == kErrTimeout) rc = CFPQ_ERR_TIMEOUT;
@@ -781,6 +789,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     c->schedule = o.schedule == CFPQ_SCHED_AUTO ? CFPQ_SCHED_INPLACE : o.schedule;  // single solves
     c->path = o.path;
     c->lengths = o.lengths != 0;
+    c->dense_tensor = o.dense_tensor != 0;
     if (c->lengths) {
         // the lengths come from the matrices before each loop execution: Jacobi schedule only
         if (o.schedule == CFPQ_SCHED_INPLACE || o.path == CFPQ_PATH_WORKLIST) return CFPQ_ERR_UNSUPPORTED;
@@ -866,6 +875,10 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     const size_t cells = (size_t)c->n_nt * c->n_pad;  // (non-terminal, row) extraction cells
     const bool want_tt = (c->path == CFPQ_PATH_WORKLIST) || c->allow_switch || c->lengths ||
                          ((c->path == CFPQ_PATH_AUTO || c->path == CFPQ_PATH_TENSOR) && tensor_path_available());
+    // tile occupancy for the tensor products (unless dense products were asked for)
+    const bool occ = !c->dense_tensor && (c->path == CFPQ_PATH_AUTO || c->path == CFPQ_PATH_TENSOR) &&
+                     tensor_path_available() && c->n_groups > 0;
+    const size_t swk = ((c->n_pad / 128) + 31) / 32;
     struct Part { void **dst; size_t bytes; };
     const Part parts[] = {
         {(void **)&c->d_T, planes}, {(void **)&c->d_X0, planes}, {(void **)&c->d_X1, planes},
@@ -885,7 +898,9 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_L, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0},
         {(void **)&c->d_Wit, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0},
         {(void **)&c->d_Tsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
-        {(void **)&c->d_TTsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0}};
+        {(void **)&c->d_TTsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
+        {(void **)&c->d_occA, occ ? (size_t)c->n_nt * (c->n_pad / 128) * swk * sizeof(uint32_t) : 0},
+        {(void **)&c->d_occB, occ ? (size_t)c->n_nt * (c->n_pad / 256) * swk * sizeof(uint32_t) : 0}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
     {
@@ -935,6 +950,10 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.R0 = c->d_R0;
     q.R1 = c->d_R1;
     q.Trow = c->d_Trow;
+    q.occA = c->d_occA;
+    q.occB = c->d_occB;
+    q.KS = c->n_pad / 128;
+    q.SWK = (q.KS + 31) / 32;
     q.Tsum = c->d_Tsum;
     q.TTsum = c->d_TTsum;
     q.SW = c->SW;
@@ -988,7 +1007,8 @@ int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edge
             opt->schedule != CFPQ_SCHED_AUTO)
             return CFPQ_ERR_INVALID;
         if (opt->path < CFPQ_PATH_AUTO || opt->path > CFPQ_PATH_WORKLIST) return CFPQ_ERR_INVALID;
-        if ((opt->lengths != 0 && opt->lengths != 1) || opt->reserved != 0) return CFPQ_ERR_INVALID;
+        if ((opt->lengths != 0 && opt->lengths != 1) || (opt->dense_tensor != 0 && opt->dense_tensor != 1))
+            return CFPQ_ERR_INVALID;
     }
     return CFPQ_OK;
 }

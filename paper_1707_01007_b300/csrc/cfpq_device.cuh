@@ -9,6 +9,10 @@
 //   R[p][A]   row bitmaps of X[p][A] (bit i set iff row i of X[p][A] may be non-zero)
 //   Trow[A]   row bitmap of T[A] (bit i set iff row i of T[A] is non-empty)
 //   TT[A]     T_A transposed, refreshed before tensor-core products that read it
+//   occA[A]   tensor path, tile skipping: bit (m-tile, K slice) set iff the 128 x 128-bit tile of
+//             T_A is non-zero; occB[A]: bit (n-tile, K slice) set iff the 256 x 128-bit tile of
+//             T_A^T is non-zero (the same bits of T_A, tiled as a right operand). SWK words
+//             per tile row; refreshed at the start of a loop execution for operands that changed
 //   Tsum[A]   single-path lengths only: word summary of T_A, SW words per row (ceil(W / 32)
 //             rounded up to a multiple of 4), bit w of row i set iff word w of row i of T_A
 //             may be non-zero
@@ -57,6 +61,9 @@ struct DevState {
     unsigned int to_worklist;           // the loop stopped to hand the closure to the worklist path
     unsigned int pad_len;
     unsigned long long len_splits;      // lengths, profile mode: (production, middle node) splits examined
+    unsigned int odirty[kMaxNT];        // T[A] changed since its tile occupancy was computed
+    unsigned int occ_now[kMaxNT];       // tile occupancy of A to be recomputed at the next tensor execution
+    unsigned long long tc_live_steps;   // K steps the tensor-core products issued (after tile skipping)
 };
 
 struct Rule {
@@ -71,6 +78,8 @@ struct QDesc {
     uint64_t plane;                     // words per matrix = n_pad * W
     uint64_t n_edges;
     uint32_t *T, *TT, *X0, *X1, *R0, *R1, *Trow;
+    uint32_t *occA, *occB;              // tile occupancy (NULL: dense tensor products)
+    uint32_t KS, SWK;                   // K slices of 128 bits per row; occupancy words per tile row
     uint32_t *Tsum;                     // word summary of T (NULL unless lengths are kept)
     uint32_t *TTsum;                    // word summary of TT (NULL unless lengths are kept)
     uint32_t SW;                        // summary words per row (a multiple of 4)
@@ -280,6 +289,7 @@ __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint3
         atomicAdd(&q.st->new_bits, (unsigned long long)cnt);
         q.st->changed = 1u;
         q.st->dirty[A] = 1u;
+        q.st->odirty[A] = 1u;
     }
 }
 
@@ -321,6 +331,15 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
     if (tid == 0) {
         for (int a = 0; a < q.n_nt; a++) st->dcount[old][a] = 0ull;
         st->list_len = 0u;
+        // tile occupancy to refresh at the next tensor execution: what changed now, plus what
+        // is still pending if no tensor product ran in this execution
+        unsigned any_tc = 0u;
+        for (int g = 0; g < q.n_groups; g++) any_tc |= st->use_tensor[g];
+        for (int a = 0; a < q.n_nt; a++) {
+            const unsigned d = st->odirty[a];
+            st->odirty[a] = 0u;
+            st->occ_now[a] = any_tc ? d : (st->occ_now[a] | d);
+        }
         const unsigned changed = ld_u32(&st->changed);
         st->changed = 0u;
         st->iter = it + 1;

@@ -34,6 +34,8 @@ struct cfpq_ctx {
     uint32_t *d_L = nullptr;          // [n_nt][n_pad][n_pad] lengths (in the arena)
     uint32_t *d_Wit = nullptr;        // [n_nt][n_pad][n_pad] derivation step of each pair (in the arena)
     uint64_t lplane = 0;              // cells per length plane = n_pad * n_pad
+    uint32_t *d_occA = nullptr, *d_occB = nullptr;  // tile occupancy (tensor path with tile skipping; arena)
+    bool dense_tensor = false;        // tensor products over every K step (no tile skipping)
     uint32_t *d_Tsum = nullptr;       // word summary of T (lengths only; in the arena)
     uint32_t *d_TTsum = nullptr;      // word summary of T^T (lengths only; in the arena)
     uint32_t SW = 0;                  // summary words per row: ceil(W / 32) rounded up to a multiple of 4
@@ -121,6 +123,8 @@ uint32_t gather_chunks(uint32_t W, int *cpl);
 bool tensor_path_available();
 int enqueue_tensor_transposes(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s);
+int enqueue_tensor_occupancy(cfpq_ctx *c, cudaStream_t s);
+constexpr double kTcOpsPerStep = 2.0 * 128 * 256 * 128;  // Boolean ops of one K step of a tensor tile
 int enqueue_tensor_seed_transposes(cfpq_ctx *c, cudaStream_t s, int64_t *launches);
 void tensor_release(cfpq_ctx *c);
 

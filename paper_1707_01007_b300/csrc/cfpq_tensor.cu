@@ -59,6 +59,7 @@ struct __align__(1024) Smem {
     uint32_t b_pack[PST][BN * KW];
     unsigned long long full_p[PST], empty_p[PST], full_u[UST], empty_u[UST], acc_full;
     uint32_t tmem_base;
+    uint32_t total;
     int err;
 };
 
@@ -206,6 +207,18 @@ __device__ __forceinline__ void unpack_half_row_tmem(uint32_t taddr, uint2 p) {
     tmem_st16(taddr, v);
 }
 
+// K slices (bit kb of word w: slice 32 w + kb) that production B x C needs for output tile
+// (mt, nt): with tile skipping, those where both operand tiles are non-zero; dense, all.
+__device__ __forceinline__ uint32_t live_slices(const QDesc &q, int B, int C, uint32_t mt, uint32_t nt, uint32_t w) {
+    if (q.occA) {
+        const uint32_t ntiles_m = q.n_pad / BM, ntiles_n = q.n_pad / BN;
+        return __ldcg(q.occA + ((uint64_t)B * ntiles_m + mt) * q.SWK + w) &
+               __ldcg(q.occB + ((uint64_t)C * ntiles_n + nt) * q.SWK + w);
+    }
+    const uint32_t left = q.KS - w * 32u;
+    return left >= 32u ? 0xFFFFFFFFu : ((1u << left) - 1u);
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_bool_gemm(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmTT, const QDesc *qd,
                    int g) {
@@ -230,11 +243,17 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
     const int A = q.rules[r0].lhs;
-    const uint32_t kpr = q.n_pad / BK;  // stages per production
-    const uint32_t total = (uint32_t)(r1 - r0) * kpr;
+    const uint32_t mt = m0 / BM, nt = n0 / BN;
     volatile int *err = &S.err;
 
     if (threadIdx.x == 0) {
+        // K steps of this tile over the group's productions (tile skipping: the live ones)
+        uint32_t live = 0;
+        for (int r = r0; r < r1; r++)
+            for (uint32_t w = 0; w < q.SWK; w++) live += __popc(live_slices(q, q.rules[r].b, q.rules[r].c, mt, nt, w));
+        S.total = live;
+        if (live) atomicAdd(&st->tc_live_steps, (unsigned long long)live);
+        if (blockIdx.x == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
         for (int i = 0; i < PST; i++) {
             mbar_init(&S.full_p[i], 1);
             mbar_init(&S.empty_p[i], UNPACK_THREADS);
@@ -248,6 +267,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    __syncthreads();
+    const uint32_t total = S.total;
+    if (total == 0) return;  // every K step skipped: the tile of the product is zero
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
                      "r"(TMEM_COLS)
@@ -261,18 +283,29 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- producer: TMA of the bit-packed tiles
+            // ---------------- producer: TMA of the bit-packed tiles of the live K steps, in
+            // the order (production, slice) that the count above used
             uint32_t issued = 0;
-            for (uint32_t s = 0; s < total; s++) {
-                const uint32_t slot = s % PST, ph = (s / PST) & 1u;
-                if (!mbar_wait(&S.empty_p[slot], ph ^ 1u, err)) break;
-                const int r = r0 + (int)(s / kpr);
-                const uint32_t kb = s % kpr;
+            bool stop = false;
+            for (int r = r0; r < r1 && !stop; r++) {
                 const int B = q.rules[r].b, C = q.rules[r].c;
-                mbar_expect_tx(&S.full_p[slot], A_PACK + B_PACK);
-                tma_load_2d(S.a_pack[slot], &tmT, &S.full_p[slot], (int)(kb * KW), (int)((uint32_t)B * q.n_pad + m0));
-                tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * KW), (int)((uint32_t)C * q.n_pad + n0));
-                issued = s + 1;
+                for (uint32_t w = 0; w < q.SWK && !stop; w++) {
+                    uint32_t live = live_slices(q, B, C, mt, nt, w);
+                    while (live && issued < total) {
+                        const uint32_t kb = w * 32u + (uint32_t)(__ffs(live) - 1);
+                        live &= live - 1;
+                        const uint32_t s = issued;
+                        const uint32_t slot = s % PST, ph = (s / PST) & 1u;
+                        if (!mbar_wait(&S.empty_p[slot], ph ^ 1u, err)) {
+                            stop = true;
+                            break;
+                        }
+                        mbar_expect_tx(&S.full_p[slot], A_PACK + B_PACK);
+                        tma_load_2d(S.a_pack[slot], &tmT, &S.full_p[slot], (int)(kb * KW), (int)((uint32_t)B * q.n_pad + m0));
+                        tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * KW), (int)((uint32_t)C * q.n_pad + n0));
+                        issued = s + 1;
+                    }
+                }
             }
             if (*err) {
                 // drain: the last load issued into each slot must land before the CTA exits
@@ -360,14 +393,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             atomicAdd(&st->new_bits, (unsigned long long)cnt);
             st->changed = 1u;
             st->dirty[A] = 1u;
+            st->odirty[A] = 1u;
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (S.err) atomicExch(&st->error, 3u);
-        if (blockIdx.x == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
-    }
+    if (threadIdx.x == 0 && S.err) atomicExch(&st->error, 3u);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -407,6 +438,49 @@ __global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a, int g
         const int j = idx >> 3, ib = idx & 7;
         dst[(uint64_t)(wc0 * 32 + j) * W + r0 / 32 + ib] = out[j][ib];
     }
+}
+
+// Tile occupancy of T_a for tile skipping (one CTA per 256 rows x 256 columns, as k_transpose):
+// the CTA's 2 x 2 blocks of 128 rows x 128 columns give two (m-tile, K slice) bits of occA[a]
+// per m-tile and, ORed over the columns, the two (n-tile, K slice) bits of occB[a] (T_a^T's
+// tile of 256 rows x 128 columns is T_a's 128 rows x 256 columns). Each bit belongs to exactly
+// one CTA, which writes it whether set or clear (no clearing pass). Runs only if the plan of
+// this execution asks for a (occ_now) and some group takes the tensor product now.
+__global__ void __launch_bounds__(256) k_occupancy(const QDesc *qd, int a) {
+    const QDesc &q = *qd;
+    const DevState *st = q.st;
+    if (!st->occ_now[a]) return;
+    unsigned any_tc = 0u;
+    for (int g = 0; g < q.n_groups; g++) any_tc |= st->use_tensor[g];
+    if (!any_tc) return;
+    __shared__ uint32_t mask;
+    if (threadIdx.x == 0) mask = 0u;
+    __syncthreads();
+    const uint32_t r0 = blockIdx.y * 256u, wc0 = blockIdx.x * 8u;
+    const uint32_t *src = q.T + (uint64_t)a * q.plane;
+    uint32_t m = 0;
+    for (int idx = threadIdx.x; idx < 2048; idx += 256) {
+        const uint32_t row = (uint32_t)idx >> 3, w = (uint32_t)idx & 7u;
+        if (__ldcg(src + (uint64_t)(r0 + row) * q.W + wc0 + w)) m |= 1u << ((row >> 7) * 2u + (w >> 2));
+    }
+    m = __reduce_or_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m) atomicOr(&mask, m);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const uint32_t M = mask;
+    const uint32_t ntiles_m = q.n_pad / BM, ntiles_n = q.n_pad / BN;
+    const uint32_t ks = wc0 / 4u;  // first of the two K slices of the columns (even)
+    for (uint32_t h = 0; h < 2; h++) {
+        uint32_t *word = q.occA + ((uint64_t)a * ntiles_m + r0 / BM + h) * q.SWK + ks / 32u;
+        const uint32_t bits = ((M >> (2u * h)) & 3u) << (ks & 31u);
+        atomicAnd(word, ~(3u << (ks & 31u)));
+        if (bits) atomicOr(word, bits);
+    }
+    const uint32_t ksr = r0 / 128u;  // the two K slices of the rows (even), as T_a^T columns
+    const uint32_t rb = ((M | (M >> 1)) & 1u) | (((M >> 2) | (M >> 3)) & 1u) << 1;
+    uint32_t *wordB = q.occB + ((uint64_t)a * ntiles_n + wc0 / 8u) * q.SWK + ksr / 32u;
+    atomicAnd(wordB, ~(3u << (ksr & 31u)));
+    if (rb) atomicOr(wordB, rb << (ksr & 31u));
 }
 
 // Profile mode, useful work of one tensor product T_B x T_C: sum over k of the ones in
@@ -544,6 +618,22 @@ int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s) {
 }
 
 int tensor_prepare(cfpq_ctx *c) { return tensor_setup(c); }
+
+// Tile occupancy of every operand of a tensor-capable group (tile skipping); each launch
+// returns at once unless this execution's plan asks for it and a tensor product runs now.
+int enqueue_tensor_occupancy(cfpq_ctx *c, cudaStream_t s) {
+    if (!c->d_occA) return CFPQ_OK;
+    std::vector<char> need(c->n_nt, 0);
+    for (int g = 0; g < c->n_groups; g++)
+        for (int r = c->gstart[g]; r < c->gstart[g + 1]; r++) need[c->rules[r].b] = need[c->rules[r].c] = 1;
+    const dim3 grid(c->W / 8, c->n_pad / 256);
+    for (int a = 0; a < c->n_nt; a++)
+        if (need[a]) {
+            tc::k_occupancy<<<grid, 256, 0, s>>>(c->d_q, a);
+            c->iter_launches++;
+        }
+    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
 
 // T^T of every non-terminal that a production derives (the worklist's hand-over).
 int enqueue_all_transposes(cfpq_ctx *c, cudaStream_t s) {

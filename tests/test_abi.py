@@ -97,7 +97,7 @@ def test_lengths_options_checked_before_device_use():
     # they need the Jacobi schedule and a matrix path; bad flag values are rejected
     g = eng.Grammar("S S S\nS a\n", ["a"])
     lib = eng.library()
-    for field, value, code in [("lengths", 2, eng.ERR_INVALID), ("reserved", 1, eng.ERR_INVALID)]:
+    for field, value, code in [("lengths", 2, eng.ERR_INVALID), ("dense_tensor", 2, eng.ERR_INVALID)]:
         opt = eng.Options()
         lib.cfpq_options_default(ctypes.byref(opt))
         opt.schedule = eng.SCHED_JACOBI
@@ -128,7 +128,7 @@ def test_null_arguments():
 def test_options_defaults():
     opt = eng.Options()
     assert eng.library().cfpq_options_default(ctypes.byref(opt)) == eng.OK
-    assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter, opt.lengths, opt.reserved) == \
+    assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter, opt.lengths, opt.dense_tensor) == \
         (eng.SCHED_INPLACE, eng.PATH_AUTO, 1, 0, 0, 0, 0)
     assert ctypes.sizeof(eng.Options) == 40
 

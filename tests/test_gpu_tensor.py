@@ -41,10 +41,11 @@ def test_worked_example_jacobi_iterations():
 
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("schedule", [eng.SCHED_INPLACE, eng.SCHED_JACOBI])
-def test_random(seed, schedule):
+@pytest.mark.parametrize("dense", [False, True])
+def test_random(seed, schedule, dense):
     graph = synth.random_graph(90 + 61 * seed, 200 + 40 * seed, 3, seed=seed)
     text = synth.random_grammar_text(5, 3, 9, 6, seed % 3, seed=seed)
-    tensor_parity(graph, text, schedule=schedule)
+    tensor_parity(graph, text, schedule=schedule, dense_tensor=dense)
 
 
 @pytest.mark.parametrize("n", [1100, 2600])
@@ -57,8 +58,14 @@ def test_two_cycles():
 
 
 @pytest.mark.parametrize("n,c", [(1024, 300), (4096, 1200)])
-def test_hierarchy_q1(n, c):
-    tensor_parity(synth.hierarchy(n, c, seed=1), synth.GRAMMAR_Q1)
+@pytest.mark.parametrize("dense", [False, True])
+def test_hierarchy_q1(n, c, dense):
+    g, q = tensor_parity(synth.hierarchy(n, c, seed=1), synth.GRAMMAR_Q1, dense_tensor=dense)
+    s = q.stats()
+    if dense:
+        assert s["tensor_live_ops"] == s["dense_ops"]
+    else:  # classes and instances occupy separate index ranges: most operand tiles are zero
+        assert 0 < s["tensor_live_ops"] < 0.5 * s["dense_ops"]
 
 
 @pytest.mark.parametrize("text", [synth.GRAMMAR_Q1, synth.GRAMMAR_QSC])
@@ -82,3 +89,32 @@ def test_useful_work_of_one_product():
     s = q.stats()
     assert s["useful_ops"] == 2.0 * s["iterations"] * float(np.dot(col_a, row_b))
     assert 0 < s["useful_ops"] < s["dense_ops"]
+
+
+def _block_edges(n, m, label, src_range, dst_range, seed):
+    k = synth.key(seed, 5)
+    i = np.arange(m, dtype=np.int64)
+    src = src_range[0] + synth.uniform_int(k, 2 * i, src_range[1] - src_range[0])
+    dst = dst_range[0] + synth.uniform_int(k, 2 * i + 1, dst_range[1] - dst_range[0])
+    return np.stack([src, np.full_like(src, label), dst], axis=1)
+
+
+@pytest.mark.parametrize("schedule", [eng.SCHED_JACOBI, eng.SCHED_INPLACE])
+def test_tile_skipping_issues_exactly_the_live_steps(schedule):
+    """S -> A B with A and B static: every execution multiplies the same operands, so the K
+    steps issued are (executions) x sum over output tiles (128 x 256) of the K slices (128) in
+    which A's tile and B^T's tile are both non-zero, counted here from the edge list."""
+    n = 1024
+    e = np.concatenate([_block_edges(n, 900, 0, (0, 400), (0, 520), 1),
+                        _block_edges(n, 900, 1, (384, 1024), (0, 300), 2)])
+    graph = synth.Graph(n=n, edges=e, labels=["t0", "t1"], meta={"kind": "test"})
+    g, q = tensor_parity(graph, "S A B\nA t0\nB t1\n", schedule=schedule)
+    occ_a = np.zeros((n // 128, n // 128), dtype=bool)   # (m-tile, K slice) of A
+    occ_b = np.zeros((n // 256, n // 128), dtype=bool)   # (n-tile, K slice) of B^T
+    a_e, b_e = e[e[:, 1] == 0], e[e[:, 1] == 1]
+    occ_a[a_e[:, 0] // 128, a_e[:, 2] // 128] = True
+    occ_b[b_e[:, 2] // 256, b_e[:, 0] // 128] = True
+    live = int((occ_a.astype(np.int64) @ occ_b.T.astype(np.int64)).sum())
+    s = q.stats()
+    assert 0 < live < (n // 128) * (n // 256) * (n // 128)
+    assert s["tensor_live_ops"] == s["iterations"] * live * 2.0 * 128 * 256 * 128
