@@ -900,7 +900,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_Tsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
         {(void **)&c->d_TTsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
         {(void **)&c->d_occA, occ ? (size_t)c->n_nt * (c->n_pad / 128) * swk * sizeof(uint32_t) : 0},
-        {(void **)&c->d_occB, occ ? (size_t)c->n_nt * (c->n_pad / 256) * swk * sizeof(uint32_t) : 0}};
+        {(void **)&c->d_occB, occ ? (size_t)c->n_nt * (c->n_pad / 256) * swk * sizeof(uint32_t) : 0},
+        {(void **)&c->d_tile_list, occ ? (size_t)(c->n_pad / 256) * (c->n_pad / 128) * 8 : 0}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
     {

@@ -64,6 +64,7 @@ struct DevState {
     unsigned int odirty[kMaxNT];        // T[A] changed since its tile occupancy was computed
     unsigned int occ_now[kMaxNT];       // tile occupancy of A to be recomputed at the next tensor execution
     unsigned long long tc_live_steps;   // K steps the tensor-core products issued (after tile skipping)
+    unsigned int plan_count[kMaxNT][2]; // tile skipping: live output tiles listed for group g, by execution parity
 };
 
 struct Rule {
@@ -340,6 +341,7 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
             st->odirty[a] = 0u;
             st->occ_now[a] = any_tc ? d : (st->occ_now[a] | d);
         }
+        for (int g = 0; g < q.n_groups; g++) st->plan_count[g][(it + 1ull) & 1ull] = 0u;  // next execution's slot
         const unsigned changed = ld_u32(&st->changed);
         st->changed = 0u;
         st->iter = it + 1;

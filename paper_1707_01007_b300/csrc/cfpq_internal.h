@@ -35,6 +35,7 @@ struct cfpq_ctx {
     uint32_t *d_Wit = nullptr;        // [n_nt][n_pad][n_pad] derivation step of each pair (in the arena)
     uint64_t lplane = 0;              // cells per length plane = n_pad * n_pad
     uint32_t *d_occA = nullptr, *d_occB = nullptr;  // tile occupancy (tensor path with tile skipping; arena)
+    void *d_tile_list = nullptr;      // tile skipping: live output tiles of one product (uint2 each; arena)
     bool dense_tensor = false;        // tensor products over every K step (no tile skipping)
     uint32_t *d_Tsum = nullptr;       // word summary of T (lengths only; in the arena)
     uint32_t *d_TTsum = nullptr;      // word summary of T^T (lengths only; in the arena)

@@ -29,6 +29,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -57,9 +58,8 @@ struct __align__(1024) Smem {
     uint8_t b_tile[UST][B_TILE];
     uint32_t a_pack[PST][BM * KW];
     uint32_t b_pack[PST][BN * KW];
-    unsigned long long full_p[PST], empty_p[PST], full_u[UST], empty_u[UST], acc_full;
+    unsigned long long full_p[PST], empty_p[PST], full_u[UST], empty_u[UST], acc_full, acc_empty;
     uint32_t tmem_base;
-    uint32_t total;
     int err;
 };
 
@@ -219,41 +219,66 @@ __device__ __forceinline__ uint32_t live_slices(const QDesc &q, int B, int C, ui
     return left >= 32u ? 0xFFFFFFFFu : ((1u << left) - 1u);
 }
 
+// Origin of output tile t of a product (grouped rasterisation: consecutive tiles sweep the M
+// tiles of a band of RASTER_N N tiles, so CTAs running at the same time touch about RASTER_N
+// right-operand tile columns, which stay in L2).
+__device__ __forceinline__ void tile_origin(const QDesc &q, uint32_t t, uint32_t &m0, uint32_t &n0) {
+    const uint32_t n_tiles = q.n_pad / BN, m_tiles = q.n_pad / BM;
+    const uint32_t band = t / (RASTER_N * m_tiles);
+    const uint32_t first_n = band * RASTER_N;
+    const uint32_t width = min((uint32_t)RASTER_N, n_tiles - first_n);
+    const uint32_t local = t - band * RASTER_N * m_tiles;
+    n0 = (first_n + local % width) * BN;
+    m0 = (local / width) * BM;
+}
+
+// Tile skipping, one thread per output tile of group g: the tiles with at least one live K
+// step go to the list as (tile, live K steps); the count is the plan slot of this execution.
+__global__ void __launch_bounds__(256) k_tile_plan(const QDesc *qd, int g, uint2 *list) {
+    const QDesc &q = *qd;
+    DevState *st = q.st;
+    if (st->use_tensor[g] == 0) return;
+    const uint32_t tiles = (q.n_pad / BN) * (q.n_pad / BM);
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
+    uint32_t live = 0;
+    if (t < tiles) {
+        uint32_t m0, n0;
+        tile_origin(q, t, m0, n0);
+        for (int r = r0; r < r1; r++)
+            for (uint32_t w = 0; w < q.SWK; w++)
+                live += __popc(live_slices(q, q.rules[r].b, q.rules[r].c, m0 / BM, n0 / BN, w));
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, live != 0u);
+    uint32_t base = 0;
+    if (lane == 0 && m) base = atomicAdd(&st->plan_count[g][st->iter & 1ull], (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (live) list[base + __popc(m & ((1u << lane) - 1u))] = make_uint2(t, live);
+}
+
+// The product of group g over a sequence of output tiles: with list == NULL every tile, one
+// per CTA (grid = tiles); with a tile-skipping plan, the live tiles of the list, CTA b taking
+// entries b, b + grid, ... The roles keep one running stage counter across the CTA's tiles;
+// the accumulator is handed back by the epilogue (acc_empty) before the next tile's MMAs.
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_bool_gemm(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmTT, const QDesc *qd,
-                   int g) {
+                   int g, const uint2 *list) {
     extern __shared__ uint8_t smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const QDesc &q = *qd;
     DevState *st = q.st;
     if (st->use_tensor[g] == 0) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // grouped rasterisation: consecutive CTAs sweep the M tiles of a band of RASTER_N N tiles,
-    // so one wave of CTAs touches about RASTER_N right-operand tile columns (L2-resident)
-    uint32_t n0, m0;
-    {
-        const uint32_t n_tiles = q.n_pad / BN, m_tiles = q.n_pad / BM;
-        const uint32_t t = blockIdx.x;
-        const uint32_t band = t / (RASTER_N * m_tiles);
-        const uint32_t first_n = band * RASTER_N;
-        const uint32_t width = min((uint32_t)RASTER_N, n_tiles - first_n);
-        const uint32_t local = t - band * RASTER_N * m_tiles;
-        n0 = (first_n + local % width) * BN;
-        m0 = (local / width) * BM;
-    }
     const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
     const int A = q.rules[r0].lhs;
-    const uint32_t mt = m0 / BM, nt = n0 / BN;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
+    const uint32_t ntile = list ? __ldcg(&st->plan_count[g][st->iter & 1ull]) : (q.n_pad / BN) * (q.n_pad / BM);
+    if (blockIdx.x >= ntile) return;  // (uniform over the CTA) no tile for this CTA
+    const uint32_t dense_steps = (uint32_t)(r1 - r0) * q.KS;
     volatile int *err = &S.err;
 
     if (threadIdx.x == 0) {
-        // K steps of this tile over the group's productions (tile skipping: the live ones)
-        uint32_t live = 0;
-        for (int r = r0; r < r1; r++)
-            for (uint32_t w = 0; w < q.SWK; w++) live += __popc(live_slices(q, q.rules[r].b, q.rules[r].c, mt, nt, w));
-        S.total = live;
-        if (live) atomicAdd(&st->tc_live_steps, (unsigned long long)live);
-        if (blockIdx.x == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
         for (int i = 0; i < PST; i++) {
             mbar_init(&S.full_p[i], 1);
             mbar_init(&S.empty_p[i], UNPACK_THREADS);
@@ -263,13 +288,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&S.empty_u[i], 1);
         }
         mbar_init(&S.acc_full, 1);
+        mbar_init(&S.acc_empty, UNPACK_THREADS);
         S.err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    __syncthreads();
-    const uint32_t total = S.total;
-    if (total == 0) return;  // every K step skipped: the tile of the product is zero
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&S.tmem_base)),
                      "r"(TMEM_COLS)
@@ -283,28 +306,42 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- producer: TMA of the bit-packed tiles of the live K steps, in
-            // the order (production, slice) that the count above used
+            // ---------------- producer: TMA of the bit-packed tiles of each live K step, in the
+            // order (production, slice) in which the plan counted them
             uint32_t issued = 0;
             bool stop = false;
-            for (int r = r0; r < r1 && !stop; r++) {
-                const int B = q.rules[r].b, C = q.rules[r].c;
-                for (uint32_t w = 0; w < q.SWK && !stop; w++) {
-                    uint32_t live = live_slices(q, B, C, mt, nt, w);
-                    while (live && issued < total) {
-                        const uint32_t kb = w * 32u + (uint32_t)(__ffs(live) - 1);
-                        live &= live - 1;
-                        const uint32_t s = issued;
-                        const uint32_t slot = s % PST, ph = (s / PST) & 1u;
-                        if (!mbar_wait(&S.empty_p[slot], ph ^ 1u, err)) {
-                            stop = true;
-                            break;
+            for (uint32_t i = blockIdx.x; i < ntile && !stop; i += gridDim.x) {
+                const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
+                uint32_t m0, n0;
+                tile_origin(q, e.x, m0, n0);
+                atomicAdd(&st->tc_live_steps, (unsigned long long)e.y);
+                uint32_t done = 0;
+                for (int r = r0; r < r1 && !stop; r++) {
+                    const int B = q.rules[r].b, C = q.rules[r].c;
+                    for (uint32_t w = 0; w < q.SWK && !stop; w++) {
+                        uint32_t live = live_slices(q, B, C, m0 / BM, n0 / BN, w);
+                        while (live && done < e.y) {
+                            const uint32_t kb = w * 32u + (uint32_t)(__ffs(live) - 1);
+                            live &= live - 1;
+                            const uint32_t s = issued;
+                            const uint32_t slot = s % PST, ph = (s / PST) & 1u;
+                            if (!mbar_wait(&S.empty_p[slot], ph ^ 1u, err)) {
+                                stop = true;
+                                break;
+                            }
+                            mbar_expect_tx(&S.full_p[slot], A_PACK + B_PACK);
+                            tma_load_2d(S.a_pack[slot], &tmT, &S.full_p[slot], (int)(kb * KW),
+                                        (int)((uint32_t)B * q.n_pad + m0));
+                            tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * KW),
+                                        (int)((uint32_t)C * q.n_pad + n0));
+                            issued = s + 1;
+                            done++;
                         }
-                        mbar_expect_tx(&S.full_p[slot], A_PACK + B_PACK);
-                        tma_load_2d(S.a_pack[slot], &tmT, &S.full_p[slot], (int)(kb * KW), (int)((uint32_t)B * q.n_pad + m0));
-                        tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * KW), (int)((uint32_t)C * q.n_pad + n0));
-                        issued = s + 1;
                     }
+                }
+                if (!stop && done != e.y) {  // the plan and the bitmaps disagree: give up cleanly
+                    *err = 1;
+                    stop = true;
                 }
             }
             if (*err) {
@@ -318,82 +355,105 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {
             // ---------------- MMA issuer
             const uint32_t b0 = sa(S.b_tile[0]);
-            for (uint32_t s = 0; s < total; s++) {
-                const uint32_t slot = s % UST, ph = (s / UST) & 1u;
-                if (!mbar_wait(&S.full_u[slot], ph, err)) break;
-                tc_fence_after();
-                const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + slot * B_TILE;
+            uint32_t s = 0, tiles_done = 0;
+            bool stop = false;
+            for (uint32_t i = blockIdx.x; i < ntile && !stop; i += gridDim.x) {
+                const uint32_t steps = list ? list[i].y : dense_steps;
+                if (tiles_done > 0) {  // the epilogue has read the previous tile's accumulator
+                    if (!mbar_wait(&S.acc_empty, (tiles_done - 1) & 1u, err)) break;
+                    tc_fence_after();
+                }
+                for (uint32_t u = 0; u < steps; u++, s++) {
+                    const uint32_t slot = s % UST, ph = (s / UST) & 1u;
+                    if (!mbar_wait(&S.full_u[slot], ph, err)) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + slot * B_TILE;
 #pragma unroll
-                for (int kk = 0; kk < BK / 32; kk++)
-                    mma_f8_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), (s > 0 || kk > 0) ? 1u : 0u);
-                mma_commit(&S.empty_u[slot]);
+                    for (int kk = 0; kk < BK / 32; kk++)
+                        mma_f8_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), (u > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&S.empty_u[slot]);
+                }
+                mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
+                tiles_done++;
             }
-            mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
         }
     } else {
-        // ---------------- unpack (8 warps), then epilogue
+        // ---------------- unpack (8 warps), then the epilogue of each tile
         const int t = threadIdx.x - 64;             // 0 .. 255: the B row of this thread
         const int quad = warp & 3;                  // TMEM lane quadrant this warp may access
         const int half = (warp - 2) >> 2;           // which half of the A slice / of the columns
         const int arow = quad * 32 + lane;
         const uint32_t a_lane = tmem + ((uint32_t)(quad * 32) << 16) + ACC_COLS + (uint32_t)(16 * half);
-        for (uint32_t s = 0; s < total; s++) {
-            const uint32_t ps = s % PST, pph = (s / PST) & 1u;
-            const uint32_t us = s % UST, uph = (s / UST) & 1u;
-            if (!mbar_wait(&S.full_p[ps], pph, err)) break;
-            if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) break;
-            tc_fence_after();
-            const uint2 pa = reinterpret_cast<const uint2 *>(S.a_pack[ps])[2 * arow + half];
-            const uint4 pb = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
-            mbar_arrive(&S.empty_p[ps]);
-            unpack_half_row_tmem(a_lane + us * A_COLS, pa);
-            unpack_row(S.b_tile[us], t, pb);
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tc_fence_before();
-            mbar_arrive(&S.full_u[us]);
-        }
-        const bool ok = mbar_wait(&S.acc_full, 0, err);
-        tc_fence_after();
-        const uint32_t row = m0 + quad * 32 + lane;
         const uint32_t W = q.W;
         const bool inplace = q.schedule == CFPQ_SCHED_INPLACE;
         const uint32_t parity = (uint32_t)(st->iter & 1ull);
         uint32_t *NA = (parity ? q.X0 : q.X1) + (uint64_t)A * q.plane;
         uint32_t *NR = (parity ? q.R0 : q.R1) + (uint64_t)A * W;
         uint32_t *TA = q.T + (uint64_t)A * q.plane;
-        unsigned cnt = 0;
-#pragma unroll 1
-        for (int c = half * (BN / 64); c < (half + 1) * (BN / 64); c++) {
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
-            uint32_t word = 0;
-#pragma unroll
-            for (int j = 0; j < 32; j++) word |= (v[j] != 0u ? 1u : 0u) << j;
-            if (!ok || *err || row >= q.n || word == 0) continue;
-            const uint64_t idx = (uint64_t)row * W + n0 / 32 + c;
-            const uint32_t old = __ldcg(TA + idx);
-            const uint32_t nw = word & ~old;
-            if (nw) {
-                cnt += __popc(nw);
-                if (inplace) TA[idx] = old | nw;
-                NA[idx] = __ldcg(NA + idx) | nw;
+        uint32_t s = 0, tiles_done = 0;
+        for (uint32_t i = blockIdx.x; i < ntile; i += gridDim.x) {
+            const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
+            uint32_t m0, n0;
+            tile_origin(q, e.x, m0, n0);
+            for (uint32_t u = 0; u < e.y; u++, s++) {
+                const uint32_t ps = s % PST, pph = (s / PST) & 1u;
+                const uint32_t us = s % UST, uph = (s / UST) & 1u;
+                if (!mbar_wait(&S.full_p[ps], pph, err)) break;
+                if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) break;
+                tc_fence_after();
+                const uint2 pa = reinterpret_cast<const uint2 *>(S.a_pack[ps])[2 * arow + half];
+                const uint4 pb = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
+                mbar_arrive(&S.empty_p[ps]);
+                unpack_half_row_tmem(a_lane + us * A_COLS, pa);
+                unpack_row(S.b_tile[us], t, pb);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(&S.full_u[us]);
             }
-        }
-        if (cnt) {
-            atomicOr(&NR[row >> 5], 1u << (row & 31));
-            if (inplace) atomicOr(&q.Trow[(uint64_t)A * W + (row >> 5)], 1u << (row & 31));
-        }
-        const unsigned any = __ballot_sync(0xffffffffu, cnt != 0);
+            const bool ok = !*err && mbar_wait(&S.acc_full, tiles_done & 1u, err);
+            tc_fence_after();
+            const uint32_t row = m0 + quad * 32 + lane;
+            unsigned cnt = 0;
+#pragma unroll 1
+            for (int c = half * (BN / 64); c < (half + 1) * (BN / 64); c++) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
+                uint32_t word = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (any && lane == 0) {
-            atomicAdd(&st->dcount[parity ^ 1u][A], (unsigned long long)cnt);
-            atomicAdd(&st->tcount[A], (unsigned long long)cnt);
-            atomicAdd(&st->new_bits, (unsigned long long)cnt);
-            st->changed = 1u;
-            st->dirty[A] = 1u;
-            st->odirty[A] = 1u;
+                for (int j = 0; j < 32; j++) word |= (v[j] != 0u ? 1u : 0u) << j;
+                if (!ok || *err || row >= q.n || word == 0) continue;
+                const uint64_t idx = (uint64_t)row * W + n0 / 32 + c;
+                const uint32_t old = __ldcg(TA + idx);
+                const uint32_t nw = word & ~old;
+                if (nw) {
+                    cnt += __popc(nw);
+                    if (inplace) TA[idx] = old | nw;
+                    NA[idx] = __ldcg(NA + idx) | nw;
+                }
+            }
+            if (cnt) {
+                atomicOr(&NR[row >> 5], 1u << (row & 31));
+                if (inplace) atomicOr(&q.Trow[(uint64_t)A * W + (row >> 5)], 1u << (row & 31));
+            }
+            const unsigned any = __ballot_sync(0xffffffffu, cnt != 0);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (any && lane == 0) {
+                atomicAdd(&st->dcount[parity ^ 1u][A], (unsigned long long)cnt);
+                atomicAdd(&st->tcount[A], (unsigned long long)cnt);
+                atomicAdd(&st->new_bits, (unsigned long long)cnt);
+                st->changed = 1u;
+                st->dirty[A] = 1u;
+                st->odirty[A] = 1u;
+            }
+            tc_fence_before();
+            mbar_arrive(&S.acc_empty);  // the accumulator may be overwritten by the next tile
+            tiles_done++;
+            if (!ok) break;
         }
     }
     tc_fence_before();
@@ -679,9 +739,25 @@ int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
     const int rc = tensor_setup(c);
     if (rc != CFPQ_OK) return rc;
     TensorWork *w = static_cast<TensorWork *>(c->h_tc_work);
-    const dim3 grid((c->n_pad / tc::BN) * (c->n_pad / tc::BM));
-    tc::k_tc_bool_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(w->tmT, w->tmTT, c->d_q, g);
-    c->iter_launches++;
+    const uint32_t tiles = (c->n_pad / tc::BN) * (c->n_pad / tc::BM);
+    if (c->d_tile_list) {
+        // tile skipping: list the live output tiles, then one CTA per SM over the list
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        tc::k_tile_plan<<<(tiles + 255) / 256, 256, 0, s>>>(c->d_q, g, reinterpret_cast<uint2 *>(c->d_tile_list));
+        const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)std::max(1, sms));
+        tc::k_tc_bool_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(w->tmT, w->tmTT, c->d_q, g,
+                                                                    reinterpret_cast<const uint2 *>(c->d_tile_list));
+        c->iter_launches += 2;
+    } else {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)std::max(1, sms));
+        tc::k_tc_bool_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(w->tmT, w->tmTT, c->d_q, g, nullptr);
+        c->iter_launches++;
+    }
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 
