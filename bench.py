@@ -217,9 +217,10 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tc_bool_gemm_hier16k_dram.txt")
 TC_SOURCE = os.path.join(ROOT, "paper_1707_01007_b300", "csrc", "cfpq_tensor.cu")
 
 
-def tc_traffic_per_launch():
-    """DRAM bytes per k_tc_bool_gemm launch from the committed ncu summary, or None when the
-    summary is missing or the kernel source changed since the counters were taken."""
+def tc_traffic_per_launch(dense=True):
+    """DRAM bytes per k_tc_bool_gemm launch (dense products, or with tile skipping) from the
+    committed ncu summary, or None when the summary is missing or the kernel source changed
+    since the counters were taken."""
     import hashlib
 
     try:
@@ -231,7 +232,7 @@ def tc_traffic_per_launch():
         src = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
         if vals.get("source_sha256") != src:
             return None
-        return float(vals["dram_bytes_per_launch_avg"])
+        return float(vals["dram_bytes_per_launch_avg" if dense else "dram_bytes_per_launch_skip_avg"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -264,7 +265,7 @@ def roofline(eng, graph, gs, path, schedule, stream, dense=True):
         # the integer tensor references of this device (sm_103a has no 8-bit integer tcgen05 kind)
         mma = eng.measure_mma_sync_peaks()
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": tc_traffic_per_launch() if dense else None, "kernel": "k_tc_bool_gemm",
+                "traffic": tc_traffic_per_launch(dense), "kernel": "k_tc_bool_gemm",
                 "tile_skipping": not dense, "launches": tens_l,
                 "launch_ms": tens_ms / tens_l, "flops_per_launch": flops / tens_l,
                 "peak_note": f"{kind} bf16 dense burst x 2 (fp8 e4m3 : bf16 nominal ratio); "
