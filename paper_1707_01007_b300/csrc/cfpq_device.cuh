@@ -165,6 +165,8 @@ __device__ inline void seed_query(const QDesc &q, uint64_t tid, uint64_t nthread
 // Rows gathered per step: the loads of kGatherU rows are issued before any of them is
 // OR-ed in, so a warp keeps kGatherU row reads in flight instead of one.
 constexpr int kGatherU = 4;
+// 32-word chunks of a left-operand row whose loads are issued together when a row is scanned.
+constexpr int kScanChunks = 4;
 
 template <int CPL>
 __device__ __forceinline__ void or_rows_for_bits(uint32_t (&acc)[CPL], uint32_t bw, uint32_t w0,
@@ -232,9 +234,16 @@ __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint3
             touched = true;
             scans += W;
             const uint32_t *rowB = D + (uint64_t)B * plane + (uint64_t)i * W;
-            for (uint32_t w0 = 0; w0 < W; w0 += 32) {
-                const uint32_t bw = (w0 + lane < W) ? __ldcg(rowB + w0 + lane) : 0u;
-                or_rows_for_bits<CPL>(acc, bw, w0, q.T + (uint64_t)C * plane, W, base, lane, rows);
+            for (uint32_t w0 = 0; w0 < W; w0 += 32 * kScanChunks) {
+                uint32_t bw[kScanChunks];  // the chunks' loads are issued together
+#pragma unroll
+                for (int u = 0; u < kScanChunks; u++) {
+                    const uint32_t w = w0 + 32u * u + lane;
+                    bw[u] = w < W ? __ldcg(rowB + w) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < kScanChunks; u++)
+                    or_rows_for_bits<CPL>(acc, bw[u], w0 + 32u * u, q.T + (uint64_t)C * plane, W, base, lane, rows);
             }
         }
         // T_B x D_C: only rows k of the right delta that may be non-zero
@@ -243,9 +252,16 @@ __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint3
             scans += 2 * W;
             const uint32_t *rowB = q.T + (uint64_t)B * plane + (uint64_t)i * W;
             const uint32_t *rC = DR + (uint64_t)C * W;
-            for (uint32_t w0 = 0; w0 < W; w0 += 32) {
-                const uint32_t bw = (w0 + lane < W) ? (__ldcg(rowB + w0 + lane) & __ldcg(rC + w0 + lane)) : 0u;
-                or_rows_for_bits<CPL>(acc, bw, w0, D + (uint64_t)C * plane, W, base, lane, rows);
+            for (uint32_t w0 = 0; w0 < W; w0 += 32 * kScanChunks) {
+                uint32_t bw[kScanChunks];
+#pragma unroll
+                for (int u = 0; u < kScanChunks; u++) {
+                    const uint32_t w = w0 + 32u * u + lane;
+                    bw[u] = w < W ? (__ldcg(rowB + w) & __ldcg(rC + w)) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < kScanChunks; u++)
+                    or_rows_for_bits<CPL>(acc, bw[u], w0 + 32u * u, D + (uint64_t)C * plane, W, base, lane, rows);
             }
         }
     }
