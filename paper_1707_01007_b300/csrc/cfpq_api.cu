@@ -116,6 +116,23 @@ __global__ void __launch_bounds__(128) k_merge(const QDesc *qd) {
     }
 }
 
+// Start of a solve on a context whose last solve converged: zeroes the rows of T that its row
+// bitmap flags (every other row of T, and both delta planes, are zero already). One block per
+// (non-terminal, row word of 32 rows).
+__global__ void __launch_bounds__(128) k_clear_t_rows(const QDesc *qd) {
+    const QDesc &q = *qd;
+    const uint32_t rw = (q.n + 31u) / 32u;
+    const int a = (int)(blockIdx.x / rw);
+    const uint32_t wq = blockIdx.x % rw;
+    uint32_t rows = __ldcg(q.Trow + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
+    uint32_t *T = q.T + (uint64_t)a * q.plane;
+    while (rows) {
+        const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+        rows &= rows - 1;
+        for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) T[i * q.W + w] = 0u;
+    }
+}
+
 // Clears the rows of the delta plane read in this execution (one block per non-terminal and
 // row word of 32 rows).
 __global__ void __launch_bounds__(128) k_clear(const QDesc *qd) {
@@ -710,9 +727,16 @@ void arm_deadline(cfpq_ctx *c, cudaStream_t s) {
 int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
     const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
     const size_t rows = (size_t)c->n_nt * c->W * sizeof(uint32_t);
-    CK(cudaMemsetAsync(c->d_T, 0, planes, s));
-    CK(cudaMemsetAsync(c->d_X0, 0, planes, s));
-    CK(cudaMemsetAsync(c->d_X1, 0, planes, s));
+    if (c->clean) {
+        // the last solve converged: only the non-empty rows of T hold bits
+        k_clear_t_rows<<<(uint32_t)((uint64_t)c->n_nt * ((c->n + 31) / 32)), 128, 0, s>>>(c->d_q);
+        CK(cudaGetLastError());
+    } else {
+        CK(cudaMemsetAsync(c->d_T, 0, planes, s));
+        CK(cudaMemsetAsync(c->d_X0, 0, planes, s));
+        CK(cudaMemsetAsync(c->d_X1, 0, planes, s));
+    }
+    c->clean = false;
     CK(cudaMemsetAsync(c->d_R0, 0, rows, s));
     CK(cudaMemsetAsync(c->d_R1, 0, rows, s));
     CK(cudaMemsetAsync(c->d_Trow, 0, rows, s));
@@ -1134,6 +1158,9 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
             c->switched = true;
         }
     }
+    // a loop that converged leaves both delta planes zero (each execution clears the delta it
+    // read, the last one adds nothing); the worklist path and an interrupted loop do not
+    c->clean = rc == CFPQ_OK && !c->switched && c->path != CFPQ_PATH_WORKLIST && c->n_groups > 0;
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     c->stats.solve_ms = ms;

@@ -623,6 +623,7 @@ static int solve_batch_with(cfpq_ctx *const *ctxs, int k, cudaStream_t s, const 
         fill_batch_query(ctxs[j], &hb[j], 1, t);
         any_jacobi |= hb[j].q.schedule == CFPQ_SCHED_JACOBI;
         ctxs[j]->solved = false;
+        ctxs[j]->clean = false;
         ctxs[j]->last_stream = s;
         ctxs[j]->fixed_launches = 0;
         ctxs[j]->iter_launches = 0;

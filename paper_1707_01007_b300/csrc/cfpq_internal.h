@@ -85,6 +85,8 @@ struct cfpq_ctx {
     int64_t fixed_launches = 0;              // kernels a solve launches outside the loop
     std::vector<cudaEvent_t> prof_ev;        // profile mode: a start/stop pair per group
     bool solved = false;
+    bool clean = false;                      // after a solve that converged on the matrix path: X0, X1
+                                             // are zero and T is zero outside the rows Trow flags
     cfpq_stats stats{};
 };
 

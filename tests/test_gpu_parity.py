@@ -250,3 +250,39 @@ def test_serving_workload_large_query_full_size():
     for nm in g.names:
         assert np.array_equal(srv.result(t, g.id(nm)), ref.pairs(nm)), nm
     srv.close()
+
+
+@pytest.mark.parametrize("path,schedule,dense", [
+    (eng.PATH_AUTO, eng.SCHED_INPLACE, False), (eng.PATH_GATHER, eng.SCHED_JACOBI, False),
+    (eng.PATH_TENSOR, eng.SCHED_INPLACE, False), (eng.PATH_TENSOR, eng.SCHED_JACOBI, True),
+    (eng.PATH_WORKLIST, eng.SCHED_INPLACE, False)])
+def test_solving_again_starts_from_the_edges(path, schedule, dense):
+    # a solve after a converged one clears only the rows of T that hold bits (the delta planes
+    # are already zero); after an interrupted one, everything: each solve equals the oracle
+    graph = synth.hierarchy(3000, 900, seed=4)
+    text = synth.GRAMMAR_Q1
+    g = eng.Grammar(text, graph.labels)
+    ref = oracle.hellings(graph, text)
+    q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, dense_tensor=dense, timeout_s=120.0)
+    for _ in range(3):
+        q.solve()
+        for nm in g.names:
+            assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+    if path != eng.PATH_WORKLIST:
+        qi = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, dense_tensor=dense, max_iter=2)
+        assert qi.solve(check=False) == eng.ERR_ITER_LIMIT
+        assert qi.solve(check=False) == eng.ERR_ITER_LIMIT
+        part = {nm: set(map(tuple, qi.get(nm).tolist())) for nm in g.names}
+        full = ref.as_sets()
+        assert all(part[nm] <= full[nm] for nm in g.names)
+
+
+def test_solving_again_after_the_hand_over_to_the_worklist():
+    graph = synth.two_cycles(64, 63)
+    g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, timeout_s=120.0)
+    ref = oracle.hellings(graph, synth.GRAMMAR_C3)
+    for _ in range(2):
+        q.solve()
+        for nm in g.names:
+            assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
