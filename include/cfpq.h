@@ -199,6 +199,10 @@ int cfpq_get_device(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, size_t cap, size
  * triples); buf == NULL: only *count. Errors: INVALID, NOT_SOLVED, BUFFER, NOMEM, CUDA. */
 int cfpq_get_all(cfpq_ctx *ctx, cfpq_triple *buf, size_t cap, size_t *count);
 
+/* As cfpq_get_all, but buf is device memory (cap triples); one host synchronisation (for the
+ * count) per call. buf == NULL: only *count. Errors: as cfpq_get_all. */
+int cfpq_get_all_device(cfpq_ctx *ctx, cfpq_triple *buf, size_t cap, size_t *count);
+
 /*
  * Single-path semantics (Section 5): R_A as in cfpq_get, triples sorted by (m, n) into buf,
  * and in lengths[t] the length l of the walk that triple t carries (host memory, cap

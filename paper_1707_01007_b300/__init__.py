@@ -127,6 +127,7 @@ SIGNATURES = {
     "cfpq_get": (ctypes.c_int, [_VP, ctypes.c_int32, _P(Triple), ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_get_all": (ctypes.c_int, [_VP, _P(Triple), ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_get_device": (ctypes.c_int, [_VP, ctypes.c_int32, _VP, ctypes.c_size_t, _P(ctypes.c_size_t)]),
+    "cfpq_get_all_device": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_count": (ctypes.c_int, [_VP, ctypes.c_int32, _P(ctypes.c_size_t)]),
     "cfpq_get_lengths": (ctypes.c_int, [_VP, ctypes.c_int32, _P(Triple), _P(ctypes.c_uint32), ctypes.c_size_t,
                                         _P(ctypes.c_size_t)]),
@@ -335,6 +336,14 @@ class Query:
         c = ctypes.c_size_t()
         _check(_lib().cfpq_get_device(self._h, self._aid(A), ctypes.c_void_p(dev_ptr), cap, ctypes.byref(c)),
                "cfpq_get_device")
+        return int(c.value)
+
+    def get_all_device(self, dev_ptr: int, cap: int) -> int:
+        """Writes every relation as triples sorted by (A, m, n) into device memory at dev_ptr
+        (cap triples; one host synchronisation); returns the number of triples."""
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_get_all_device(self._h, ctypes.c_void_p(dev_ptr) if dev_ptr else None, cap,
+                                          ctypes.byref(c)), "cfpq_get_all_device")
         return int(c.value)
 
     def stats(self) -> dict:

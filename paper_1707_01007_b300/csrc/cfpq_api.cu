@@ -1360,6 +1360,21 @@ extern "C" int cfpq_get_path(cfpq_ctx *c, int32_t A, uint32_t m, uint32_t n, uin
     return lengths_path(c, A, m, n, l, nodes, labels);
 }
 
+extern "C" int cfpq_get_all_device(cfpq_ctx *c, cfpq_triple *buf, size_t cap, size_t *count) {
+    if (!c || !count) return CFPQ_ERR_INVALID;
+    if (!c->solved) return CFPQ_ERR_NOT_SOLVED;
+    cudaStream_t s = c->last_stream;
+    std::vector<unsigned long long> nt_off;
+    int rc = count_all(c, s, nt_off);
+    if (rc != CFPQ_OK) return rc;
+    const size_t total = (size_t)nt_off[c->n_nt];
+    *count = total;
+    if (!buf) return CFPQ_OK;
+    if (cap < total) return CFPQ_ERR_BUFFER;
+    if (total == 0) return CFPQ_OK;
+    return emit_all(c, buf, s);
+}
+
 extern "C" int cfpq_stats_get(const cfpq_ctx *c, cfpq_stats *out) {
     if (!c || !out) return CFPQ_ERR_INVALID;
     *out = c->stats;

@@ -117,6 +117,7 @@ def test_null_arguments():
     assert lib.cfpq_solve(None, None) == eng.ERR_INVALID
     assert lib.cfpq_get(None, 0, None, 0, None) == eng.ERR_INVALID
     assert lib.cfpq_get_device(None, 0, None, 0, None) == eng.ERR_INVALID
+    assert lib.cfpq_get_all_device(None, None, 0, None) == eng.ERR_INVALID
     assert lib.cfpq_count(None, 0, None) == eng.ERR_INVALID
     assert lib.cfpq_stats_get(None, None) == eng.ERR_INVALID
     assert lib.cfpq_options_default(None) == eng.ERR_INVALID

@@ -189,6 +189,21 @@ def test_get_device_matches_get():
         assert np.array_equal(dev, q.triples(nm))
 
 
+def test_get_all_device_matches_get_all():
+    import torch
+    graph = synth.hierarchy(900, 250, seed=2)
+    g, q = solve_engine(graph, synth.GRAMMAR_Q1)
+    k = q.get_all_device(0, 0)
+    buf = torch.empty(max(1, k) * 3, dtype=torch.int32, device="cuda")
+    assert q.get_all_device(buf.data_ptr(), max(1, k)) == k
+    torch.cuda.synchronize()
+    dev = buf[: 3 * k].view(-1, 3).cpu().numpy().astype(np.int64)
+    assert np.array_equal(dev, q.triples_all())
+    with pytest.raises(eng.CfpqError) as ei:
+        q.get_all_device(buf.data_ptr(), k - 1)
+    assert ei.value.code == eng.ERR_BUFFER
+
+
 def test_resolve_is_repeatable_and_profile_mode():
     graph = synth.hierarchy(700, 200, seed=9)
     g = eng.Grammar(synth.GRAMMAR_Q1, graph.labels)
