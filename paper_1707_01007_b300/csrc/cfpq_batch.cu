@@ -173,13 +173,15 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
         if (c < ca) zero_span(b.clr_a, c * kClrChunk, min(b.clr_a_n, (c + 1) * kClrChunk), lane);
         else zero_span(b.clr_b, (c - ca) * kClrChunk, min(b.clr_b_n, (c - ca + 1) * kClrChunk), lane);
     }
-    for (int j = (int)gtid; j < k; j += (int)gthreads) {
+    for (int j = (int)gwarp; j < k; j += (int)gwarps) {  // a warp zeroes a new query's state
         if (!bq[j].init) continue;
         const QDesc &q = bq[j].q;
         DevState *st = q.st;
-        memset(st, 0, sizeof(DevState));
-        st->max_iter = bq[j].max_iter;
-        for (int a = 0; a < q.n_nt; a++) st->dirty[a] = 1u;
+        unsigned long long *w = reinterpret_cast<unsigned long long *>(st);
+        for (int i = lane; i < (int)(sizeof(DevState) / 8); i += 32) w[i] = 0ull;
+        __syncwarp();
+        if (lane == 0) st->max_iter = bq[j].max_iter;
+        for (int a = lane; a < q.n_nt; a += 32) st->dirty[a] = 1u;
     }
     if (!grid_barrier(ctl)) return;
     // 2) matrix initialisation of the new queries (chunks of edges, then of eps pairs)
@@ -467,6 +469,8 @@ void fill_batch_query(const cfpq_ctx *c, BatchQuery *b, int init, const cfpq_bat
     memset(b, 0, sizeof(*b));
     b->q = c->hq;
     b->q.allow_switch = 0;  // the grouped launch runs every query by the matrix loop
+    b->q.occA = b->q.occB = nullptr;  // gather products only: no tile occupancy, no length summaries
+    b->q.Tsum = b->q.TTsum = nullptr;
     const int cls = batch_size_class(c->W);
     int cpl = 1;
     uint32_t nch = gather_chunks(c->W, &cpl);

@@ -348,16 +348,18 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
     if (tid == 0) {
         for (int a = 0; a < q.n_nt; a++) st->dcount[old][a] = 0ull;
         st->list_len = 0u;
-        // tile occupancy to refresh at the next tensor execution: what changed now, plus what
-        // is still pending if no tensor product ran in this execution
-        unsigned any_tc = 0u;
-        for (int g = 0; g < q.n_groups; g++) any_tc |= st->use_tensor[g];
-        for (int a = 0; a < q.n_nt; a++) {
-            const unsigned d = st->odirty[a];
-            st->odirty[a] = 0u;
-            st->occ_now[a] = any_tc ? d : (st->occ_now[a] | d);
+        if (q.occA) {
+            // tile occupancy to refresh at the next tensor execution: what changed now, plus
+            // what is still pending if no tensor product ran in this execution
+            unsigned any_tc = 0u;
+            for (int g = 0; g < q.n_groups; g++) any_tc |= st->use_tensor[g];
+            for (int a = 0; a < q.n_nt; a++) {
+                const unsigned d = st->odirty[a];
+                st->odirty[a] = 0u;
+                st->occ_now[a] = any_tc ? d : (st->occ_now[a] | d);
+            }
+            for (int g = 0; g < q.n_groups; g++) st->plan_count[g][(it + 1ull) & 1ull] = 0u;  // next execution's slot
         }
-        for (int g = 0; g < q.n_groups; g++) st->plan_count[g][(it + 1ull) & 1ull] = 0u;  // next execution's slot
         const unsigned changed = ld_u32(&st->changed);
         st->changed = 0u;
         st->iter = it + 1;
