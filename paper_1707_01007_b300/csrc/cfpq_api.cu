@@ -112,6 +112,10 @@ __global__ void __launch_bounds__(128) k_merge(const QDesc *qd) {
             const uint32_t w = w0 + lane;
             const uint32_t nw = w < q.W ? __ldcg(N + i * q.W + w) : 0u;
             if (nw) T[i * q.W + w] = __ldcg(T + i * q.W + w) | nw;
+            if (q.Tsum) {  // the word summary of T follows
+                const unsigned sb = __ballot_sync(0xffffffffu, nw != 0u);
+                if (lane == 0 && sb) atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + (w0 >> 5)], sb);
+            }
         }
     }
 }
@@ -130,6 +134,8 @@ __global__ void __launch_bounds__(128) k_clear_t_rows(const QDesc *qd) {
         const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
         rows &= rows - 1;
         for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) T[i * q.W + w] = 0u;
+        if (q.Tsum)
+            for (uint32_t w = threadIdx.x; w < q.SW; w += blockDim.x) q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + w] = 0u;
     }
 }
 
@@ -735,14 +741,14 @@ int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
         CK(cudaMemsetAsync(c->d_T, 0, planes, s));
         CK(cudaMemsetAsync(c->d_X0, 0, planes, s));
         CK(cudaMemsetAsync(c->d_X1, 0, planes, s));
+        CK(cudaMemsetAsync(c->d_Tsum, 0, (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t), s));
     }
     c->clean = false;
     CK(cudaMemsetAsync(c->d_R0, 0, rows, s));
     CK(cudaMemsetAsync(c->d_R1, 0, rows, s));
     CK(cudaMemsetAsync(c->d_Trow, 0, rows, s));
-    if (c->lengths) {  // T^T and both word summaries are built pair by pair from here on
+    if (c->lengths) {  // T^T and its word summary are built pair by pair from here on
         const size_t sum = (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t);
-        CK(cudaMemsetAsync(c->d_Tsum, 0, sum, s));
         CK(cudaMemsetAsync(c->d_TTsum, 0, sum, s));
         CK(cudaMemsetAsync(c->d_TT, 0, planes, s));
     }
@@ -921,7 +927,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_colcnt, c->profile ? sizeof(uint32_t) * c->n_pad : 0},
         {(void **)&c->d_L, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0},
         {(void **)&c->d_Wit, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0},
-        {(void **)&c->d_Tsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
+        {(void **)&c->d_Tsum, (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t)},
         {(void **)&c->d_TTsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
         {(void **)&c->d_occA, occ ? (size_t)c->n_nt * (c->n_pad / 128) * swk * sizeof(uint32_t) : 0},
         {(void **)&c->d_occB, occ ? (size_t)c->n_nt * (c->n_pad / 256) * swk * sizeof(uint32_t) : 0},

@@ -13,9 +13,10 @@
 //             T_A is non-zero; occB[A]: bit (n-tile, K slice) set iff the 256 x 128-bit tile of
 //             T_A^T is non-zero (the same bits of T_A, tiled as a right operand). SWK words
 //             per tile row; refreshed at the start of a loop execution for operands that changed
-//   Tsum[A]   single-path lengths only: word summary of T_A, SW words per row (ceil(W / 32)
-//             rounded up to a multiple of 4), bit w of row i set iff word w of row i of T_A
-//             may be non-zero
+//   Tsum[A]   word summary of T_A, SW words per row (ceil(W / 32) rounded up to a multiple of
+//             4), bit w of row i set iff word w of row i of T_A may be non-zero; kept by every
+//             writer of T on the matrix paths (seed, product epilogues, merges) so that a scan
+//             of a row of T reads only its non-zero words
 //   TTsum[A]  single-path lengths only: the same summary of TT_A (with lengths kept, TT_A is
 //             updated pair by pair by the seed and the merge)
 #pragma once
@@ -81,7 +82,7 @@ struct QDesc {
     uint32_t *T, *TT, *X0, *X1, *R0, *R1, *Trow;
     uint32_t *occA, *occB;              // tile occupancy (NULL: dense tensor products)
     uint32_t KS, SWK;                   // K slices of 128 bits per row; occupancy words per tile row
-    uint32_t *Tsum;                     // word summary of T (NULL unless lengths are kept)
+    uint32_t *Tsum;                     // word summary of T (NULL in batched launches)
     uint32_t *TTsum;                    // word summary of TT (NULL unless lengths are kept)
     uint32_t SW;                        // summary words per row (a multiple of 4)
     const Rule *rules;                  // sorted by lhs; group g = rules[gstart[g] .. gstart[g+1])
@@ -130,8 +131,8 @@ __device__ __forceinline__ void seed_pair(const QDesc &q, int a, uint32_t i, uin
         atomicOr(&q.Trow[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
         atomicAdd(&q.st->dcount[0][a], 1ull);
         atomicAdd(&q.st->tcount[a], 1ull);
-        if (q.Tsum) {
-            atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + (j >> 10)], 1u << ((j >> 5) & 31));
+        if (q.Tsum) atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + (j >> 10)], 1u << ((j >> 5) & 31));
+        if (q.TTsum) {
             atomicOr(&q.TT[(uint64_t)a * q.plane + (uint64_t)j * q.W + (i >> 5)], 1u << (i & 31));
             atomicOr(&q.TTsum[((uint64_t)a * q.n_pad + j) * q.SW + (i >> 10)], 1u << ((i >> 5) & 31));
         }
@@ -249,9 +250,29 @@ __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint3
         // T_B x D_C: only rows k of the right delta that may be non-zero
         if (ld_u64(&st->dcount[parity][C]) != 0 && test_bit(q.Trow + (uint64_t)B * W, i)) {
             touched = true;
-            scans += 2 * W;
             const uint32_t *rowB = q.T + (uint64_t)B * plane + (uint64_t)i * W;
             const uint32_t *rC = DR + (uint64_t)C * W;
+            if (q.Tsum) {
+                // only the words of row i of T_B that its word summary flags
+                const uint32_t *sumB = q.Tsum + ((uint64_t)B * q.n_pad + i) * q.SW;
+                scans += q.SW;
+                for (uint32_t s0 = 0; s0 < q.SW; s0 += 32) {
+                    const uint32_t sv = (s0 + lane < q.SW) ? __ldcg(sumB + s0 + lane) : 0u;
+                    unsigned snz = __ballot_sync(0xffffffffu, sv != 0u);
+                    while (snz) {
+                        const int src = __ffs(snz) - 1;
+                        snz &= snz - 1;
+                        const uint32_t flagged = __shfl_sync(0xffffffffu, sv, src);
+                        const uint32_t w0 = (s0 + (uint32_t)src) * 32u;
+                        scans += 2u * (uint32_t)__popc(flagged);
+                        const uint32_t bw =
+                            ((flagged >> lane) & 1u) ? (__ldcg(rowB + w0 + lane) & __ldcg(rC + w0 + lane)) : 0u;
+                        or_rows_for_bits<CPL>(acc, bw, w0, D + (uint64_t)C * plane, W, base, lane, rows);
+                    }
+                }
+                continue;
+            }
+            scans += 2 * W;
             for (uint32_t w0 = 0; w0 < W; w0 += 32 * kScanChunks) {
                 uint32_t bw[kScanChunks];
 #pragma unroll
@@ -275,14 +296,19 @@ __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint3
 #pragma unroll
     for (int c = 0; c < CPL; c++) {
         const uint32_t col = base + lane + 32 * c;
+        uint32_t nw = 0;
         if (col < W && acc[c]) {
             const uint32_t old = __ldcg(TA + col);
-            const uint32_t nw = acc[c] & ~old;
+            nw = acc[c] & ~old;
             if (nw) {
                 cnt += __popc(nw);
                 if (inplace) TA[col] = old | nw;
                 NA[col] = __ldcg(NA + col) | nw;
             }
+        }
+        if (inplace && q.Tsum) {  // the 32 lanes' words form one word of the summary of T_A
+            const unsigned sb = __ballot_sync(0xffffffffu, nw != 0u);
+            if (lane == 0 && sb) atomicOr(&q.Tsum[((uint64_t)A * q.n_pad + i) * q.SW + ((base + 32u * c) >> 5)], sb);
         }
     }
     const unsigned any = __ballot_sync(0xffffffffu, cnt != 0);

@@ -418,6 +418,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_after();
             const uint32_t row = m0 + quad * 32 + lane;
             unsigned cnt = 0;
+            uint32_t smask = 0;  // words of this row written in place (one word of the summary of T_A)
 #pragma unroll 1
             for (int c = half * (BN / 64); c < (half + 1) * (BN / 64); c++) {
                 uint32_t v[32];
@@ -433,11 +434,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                     cnt += __popc(nw);
                     if (inplace) TA[idx] = old | nw;
                     NA[idx] = __ldcg(NA + idx) | nw;
+                    smask |= 1u << ((n0 / 32u + (uint32_t)c) & 31u);
                 }
             }
             if (cnt) {
                 atomicOr(&NR[row >> 5], 1u << (row & 31));
                 if (inplace) atomicOr(&q.Trow[(uint64_t)A * W + (row >> 5)], 1u << (row & 31));
+                if (inplace && q.Tsum) atomicOr(&q.Tsum[((uint64_t)A * q.n_pad + row) * q.SW + (n0 / 32u >> 5)], smask);
             }
             const unsigned any = __ballot_sync(0xffffffffu, cnt != 0);
 #pragma unroll
