@@ -144,15 +144,18 @@ __global__ void __launch_bounds__(128) k_clear_t_rows(const QDesc *qd) {
 __global__ void __launch_bounds__(128) k_clear(const QDesc *qd) {
     const QDesc &q = *qd;
     const uint32_t rw = (q.n + 31u) / 32u;
-    const int a = (int)(blockIdx.x / rw);
-    const uint32_t wq = blockIdx.x % rw;
     const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
-    uint32_t rows = __ldcg((parity ? q.R1 : q.R0) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
-    uint32_t *D = (parity ? q.X1 : q.X0) + (uint64_t)a * q.plane;
-    while (rows) {
-        const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
-        rows &= rows - 1;
-        for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) D[i * q.W + w] = 0u;
+    // grid-stride over the (non-terminal, row word) units: most have no flagged row
+    for (uint32_t unit = blockIdx.x; unit < (uint32_t)q.n_nt * rw; unit += gridDim.x) {
+        const int a = (int)(unit / rw);
+        const uint32_t wq = unit % rw;
+        uint32_t rows = __ldcg((parity ? q.R1 : q.R0) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
+        uint32_t *D = (parity ? q.X1 : q.X0) + (uint64_t)a * q.plane;
+        while (rows) {
+            const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+            rows &= rows - 1;
+            for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) D[i * q.W + w] = 0u;
+        }
     }
 }
 
@@ -168,15 +171,20 @@ constexpr double kTensorOpsPerNs = 2.9e6;     // measured tensor-core Boolean pr
 constexpr double kGatherBytesPerNs = 600.0;   // measured gather rate (latency-bound)
 constexpr double kTransposeBytesPerNs = 3000.0;
 
+// Every thread of one block (at least max(n_nt, n_groups) threads) calls this: thread g
+// costs group g from the device-side counts, thread a assigns the refresh of TT[A].
 __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle *handles, int use_handles) {
+    __shared__ unsigned s_use[kMaxNT], s_any;
     DevState *st = q.st;
+    const int tid = threadIdx.x;
     const uint32_t p = (uint32_t)(st->iter & 1ull);
-    const double n = (double)q.n, W = (double)q.W, np = (double)q.n_pad;
-    const double per_rule_ns = 2.0 * np * np * np / kTensorOpsPerNs;
-    const double transpose_ns = 2.0 * np * np / 8.0 / kTransposeBytesPerNs;
-    unsigned owner[kMaxNT], any = 0u;
-    for (int a = 0; a < q.n_nt; a++) owner[a] = 0u;
-    for (int g = 0; g < q.n_groups; g++) {
+    if (tid == 0) s_any = 0u;
+    __syncthreads();
+    if (tid < q.n_groups) {
+        const int g = tid;
+        const double n = (double)q.n, W = (double)q.W, np = (double)q.n_pad;
+        const double per_rule_ns = 2.0 * np * np * np / kTensorOpsPerNs;
+        const double transpose_ns = 2.0 * np * np / 8.0 / kTransposeBytesPerNs;
         const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
         double words = 0.0, tensor_ns = (double)(r1 - r0) * per_rule_ns;
         for (int r = r0; r < r1; r++) {
@@ -188,22 +196,33 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
         }
         const unsigned use = tensor_ns < words * 4.0 / kGatherBytesPerNs ? 1u : 0u;
         st->use_tensor[g] = use;
-        if (use)
-            for (int r = r0; r < r1; r++)
-                if (owner[q.rules[r].c] == 0u) owner[q.rules[r].c] = (unsigned)g + 1u;
+        s_use[g] = use;
         if (use_handles) cudaGraphSetConditional(handles[g], use);
-        any |= use;
+        if (use) atomicOr(&s_any, 1u);
     }
-    if (use_handles) cudaGraphSetConditional(handles[q.n_groups], any);
-    for (int a = 0; a < q.n_nt; a++) {
-        const unsigned now = (owner[a] != 0u && st->dirty[a]) ? owner[a] : 0u;
+    __syncthreads();
+    if (tid == 0 && use_handles) cudaGraphSetConditional(handles[q.n_groups], s_any);
+    if (tid < q.n_nt) {
+        // the first group (in order) taking the tensor product with A as a right operand
+        // refreshes TT[A] if A changed since its last refresh
+        const int a = tid;
+        unsigned owner = 0u;
+        for (int g = 0; g < q.n_groups && !owner; g++)
+            if (s_use[g])
+                for (int r = q.gstart[g]; r < q.gstart[g + 1]; r++)
+                    if (q.rules[r].c == a) {
+                        owner = (unsigned)g + 1u;
+                        break;
+                    }
+        const unsigned now = (owner != 0u && st->dirty[a]) ? owner : 0u;
         st->tt_now[a] = now;
         if (now) st->dirty[a] = 0u;
     }
+    __syncthreads();
 }
 
 __global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *handles, int use_handles) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) choose_products(*qd, handles, use_handles);
+    choose_products(*qd, handles, use_handles);
 }
 
 // End of a loop execution. choice != NULL (automatic path in a graph): the product choice for
@@ -211,10 +230,8 @@ __global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *hand
 __global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle,
                        const cudaGraphConditionalHandle *choice) {
     const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x, true);
-    if (threadIdx.x == 0) {
-        if (cont && choice) choose_products(*qd, choice, 1);
-        if (use_handle) cudaGraphSetConditional(handle, cont);
-    }
+    if (cont && choice) choose_products(*qd, choice, 1);
+    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, cont);
 }
 
 
@@ -548,7 +565,7 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         // choose per group; in a graph the chosen tensor products run under conditional
         // nodes, otherwise every tensor launch is made and returns at once if not chosen
         if (!use_handle) {  // in the graph, the previous execution's tail (or the node before the loop) chose
-            k_choose<<<1, 32, 0, s>>>(c->d_q, nullptr, 0);
+            k_choose<<<1, 64, 0, s>>>(c->d_q, nullptr, 0);
             c->iter_launches++;
         }
         if (use_handle) {
@@ -601,7 +618,7 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         k_merge<<<word_blocks, 128, 0, s>>>(c->d_q);
         c->iter_launches++;
     }
-    k_clear<<<word_blocks, 128, 0, s>>>(c->d_q);
+    k_clear<<<std::min<uint32_t>(word_blocks, 4u * (uint32_t)c->sms), 128, 0, s>>>(c->d_q);
     k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle, (use_handle && c->auto_mixed) ? c->d_choice : nullptr);
     c->iter_launches += 2;
     CK(cudaGetLastError());
@@ -673,7 +690,7 @@ static int build_graph(cfpq_ctx *c) {
         cudaKernelNodeParams kp = {};
         kp.func = (void *)k_choose;
         kp.gridDim = dim3(1);
-        kp.blockDim = dim3(32);
+        kp.blockDim = dim3(64);
         kp.kernelParams = args;
         e = cudaGraphAddKernelNode(&first, g, nullptr, 0, &kp);
         if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "choice node", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
@@ -870,6 +887,13 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     c->allow_switch = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && c->schedule != CFPQ_SCHED_JACOBI;
     if (c->allow_switch) c->h_edges.assign(edges, edges + n_edges);
     c->any_gather = c->n_groups > 0 && c->path != CFPQ_PATH_TENSOR && c->path != CFPQ_PATH_WORKLIST;
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            c->sms = sms;
+        cudaGetLastError();
+    }
     {
         int cpl;
         const uint64_t slots = c->any_gather ? (uint64_t)c->n_groups * c->n * gather_chunks(c->W, &cpl) : 0;

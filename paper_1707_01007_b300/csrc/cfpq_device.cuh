@@ -358,10 +358,15 @@ __device__ inline void clear_row(const QDesc &q, int a, uint32_t i, int lane, ui
     for (uint32_t w = lane; w < W; w += 32) row[w] = 0u;
 }
 
-// End of one loop execution (one block): clears the old delta's row bitmaps (unless the
-// caller clears them later, together with the rows they flag), counts the iteration and
-// decides whether the loop continues. Returns the loop condition (valid in thread 0).
+// End of one loop execution (every thread of one block calls it; the block has at least
+// max(n_nt, n_groups) threads): clears the old delta's row bitmaps (unless the caller clears
+// them later, together with the rows they flag), counts the iteration and decides whether the
+// loop continues. The per-non-terminal and per-group bookkeeping is spread over the threads
+// (each is a load or a store of its own); thread 0 then takes the decision. Returns the loop
+// condition in every thread.
 __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, bool zero_read_bitmap) {
+    __shared__ unsigned long long s_added;
+    __shared__ unsigned s_anytc, s_cont;
     DevState *st = q.st;
     const unsigned long long it = ld_u64(&st->iter);
     const uint32_t old = (uint32_t)(it & 1ull);
@@ -369,31 +374,36 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
         uint32_t *DR = old ? q.R1 : q.R0;
         for (uint64_t w = tid; w < (uint64_t)q.n_nt * q.W; w += nthreads) DR[w] = 0u;
     }
-    __syncthreads();
-    unsigned cont = 0;
     if (tid == 0) {
-        for (int a = 0; a < q.n_nt; a++) st->dcount[old][a] = 0ull;
-        st->list_len = 0u;
-        if (q.occA) {
-            // tile occupancy to refresh at the next tensor execution: what changed now, plus
-            // what is still pending if no tensor product ran in this execution
-            unsigned any_tc = 0u;
-            for (int g = 0; g < q.n_groups; g++) any_tc |= st->use_tensor[g];
-            for (int a = 0; a < q.n_nt; a++) {
-                const unsigned d = st->odirty[a];
-                st->odirty[a] = 0u;
-                st->occ_now[a] = any_tc ? d : (st->occ_now[a] | d);
-            }
-            for (int g = 0; g < q.n_groups; g++) st->plan_count[g][(it + 1ull) & 1ull] = 0u;  // next execution's slot
+        s_added = 0ull;
+        s_anytc = 0u;
+    }
+    __syncthreads();
+    if (tid < q.n_nt) {
+        const unsigned long long add = ld_u64(&st->dcount[old ^ 1u][tid]);  // pairs added now
+        if (add) atomicAdd(&s_added, add);
+        st->dcount[old][tid] = 0ull;
+    }
+    if (tid < q.n_groups && ld_u32(&st->use_tensor[tid])) atomicOr(&s_anytc, 1u);
+    __syncthreads();
+    if (q.occA) {
+        // tile occupancy to refresh at the next tensor execution: what changed now, plus what
+        // is still pending if no tensor product ran in this execution
+        if (tid < q.n_nt) {
+            const unsigned d = ld_u32(&st->odirty[tid]);
+            st->odirty[tid] = 0u;
+            st->occ_now[tid] = s_anytc ? d : (ld_u32(&st->occ_now[tid]) | d);
         }
+        if (tid < q.n_groups) st->plan_count[tid][(it + 1ull) & 1ull] = 0u;  // next execution's slot
+    }
+    if (tid == 0) {
+        st->list_len = 0u;
         const unsigned changed = ld_u32(&st->changed);
         st->changed = 0u;
         st->iter = it + 1;
-        cont = changed ? 1u : 0u;
+        unsigned cont = changed ? 1u : 0u;
         if (cont && q.allow_switch) {
-            unsigned long long added = 0;
-            for (int a = 0; a < q.n_nt; a++) added += st->dcount[old ^ 1u][a];
-            st->small_run = added <= kSmallDelta ? st->small_run + 1u : 0u;
+            st->small_run = s_added <= kSmallDelta ? st->small_run + 1u : 0u;
             if (st->small_run >= kSwitchAfter) {
                 st->to_worklist = 1u;
                 cont = 0;
@@ -410,9 +420,10 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
         }
         st->cont = cont;
         if (!cont) st->done = 1u;
+        s_cont = cont;
     }
     __syncthreads();
-    return cont;
+    return s_cont;
 }
 
 }  // namespace cfpq
