@@ -468,10 +468,26 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-// Bit-matrix transpose of plane a: TT[a] = T[a]^T. One CTA: 256 rows x 8 words (256 x 256 bits).
+// Transpose of a 32 x 32 bit block held one row per lane (bit j of lane i = element (i, j)):
+// afterwards lane j holds column j (bit i = element (i, j)). Five butterfly steps; in step s the
+// lanes l and l ^ s exchange the off-diagonal s x s blocks of each 2s x 2s block.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        const int sh = 16 >> k;
+        const uint32_t m = masks[k];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sh);
+        x = (lane & sh) ? ((x & ~m) | ((y >> sh) & m)) : ((x & m) | ((y << sh) & ~m));
+    }
+    return x;
+}
+
+// Bit-matrix transpose of plane a: TT[a] = T[a]^T. One CTA: 256 rows x 8 words (256 x 256 bits);
+// warp w reads rows 32 w .. 32 w + 31 (one row per lane, its 8 words as two 16-byte loads),
+// transposes the 8 blocks of 32 x 32 bits in registers and stages them for row-wise stores.
 // gate >= 0 (AUTO path): only if the per-iteration choice assigned this refresh to group gate.
 __global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a, int gate) {
-    __shared__ uint32_t in[256][9];
     __shared__ uint32_t out[256][9];
     const QDesc &q = *qd;
     if (gate >= 0 && q.st->tt_now[a] != (unsigned)gate + 1u) return;
@@ -480,27 +496,17 @@ __global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a, int g
     const uint32_t *src = q.T + (uint64_t)a * q.plane;
     uint32_t *dst = q.TT + (uint64_t)a * q.plane;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    for (int idx = t; idx < 2048; idx += 256) {
-        const int row = idx >> 3, w = idx & 7;
-        in[row][w] = __ldcg(src + (uint64_t)(r0 + row) * W + wc0 + w);
-    }
-    __syncthreads();
-    // warp `warp` owns input rows warp*32 .. +31 (one output word per output row)
-    for (int wc = 0; wc < 8; wc++) {
-        const uint32_t x = in[warp * 32 + lane][wc];
-        uint32_t mine = 0;
+    // W is a multiple of 8 and wc0 of 8: the row's 8 words are 32-byte aligned
+    const uint4 *row = reinterpret_cast<const uint4 *>(src + (uint64_t)(r0 + t) * W + wc0);
+    const uint4 lo = __ldcg(row), hi = __ldcg(row + 1);
+    const uint32_t in[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
-        for (int b = 0; b < 32; b++) {
-            const uint32_t tb = __ballot_sync(0xffffffffu, (x >> b) & 1u);
-            if (lane == b) mine = tb;
-        }
-        out[wc * 32 + lane][warp] = mine;
-    }
+    for (int c = 0; c < 8; c++) out[c * 32 + lane][warp] = transpose32(in[c], lane);
     __syncthreads();
-    for (int idx = t; idx < 2048; idx += 256) {
-        const int j = idx >> 3, ib = idx & 7;
-        dst[(uint64_t)(wc0 * 32 + j) * W + r0 / 32 + ib] = out[j][ib];
-    }
+    // output row wc0 * 32 + t: words r0 / 32 .. r0 / 32 + 7 (32-byte aligned: r0 is a multiple of 256)
+    uint4 *drow = reinterpret_cast<uint4 *>(dst + (uint64_t)(wc0 * 32 + t) * W + r0 / 32);
+    drow[0] = make_uint4(out[t][0], out[t][1], out[t][2], out[t][3]);
+    drow[1] = make_uint4(out[t][4], out[t][5], out[t][6], out[t][7]);
 }
 
 // Tile occupancy of T_a for tile skipping (one CTA per 256 rows x 256 columns, as k_transpose):
