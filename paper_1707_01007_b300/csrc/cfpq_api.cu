@@ -92,29 +92,58 @@ __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDe
     }
 }
 
-// Jacobi schedule: T |= N over the rows N touched. One block per (non-terminal, row word of
-// 32 rows); the block's warps share each flagged row's words, 32 consecutive words a warp.
-__global__ void __launch_bounds__(128) k_merge(const QDesc *qd) {
+// Jacobi schedule: T |= N over the rows N touched (T_{k+1} = T_k u T_k x T_k). Persistent grid,
+// one warp per flagged row (the lanes test 32 rows of the warp's share at once; four chunks of
+// 32 words in flight); the word summary of T follows, and where lengths are kept (TTsum set)
+// T^T and its summary too, their bits set one per lane per round.
+__global__ void __launch_bounds__(256) k_merge(const QDesc *qd) {
     const QDesc &q = *qd;
-    const uint32_t rw = (q.n + 31u) / 32u;
-    const int a = (int)(blockIdx.x / rw);
-    const uint32_t wq = blockIdx.x % rw;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
-    uint32_t rows = __ldcg((parity ? q.R0 : q.R1) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
-    if (rows && threadIdx.x == 0) atomicOr(&q.Trow[(uint64_t)a * q.W + wq], rows);
-    const uint32_t *N = (parity ? q.X0 : q.X1) + (uint64_t)a * q.plane;
-    uint32_t *T = q.T + (uint64_t)a * q.plane;
-    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    while (rows) {
-        const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
-        rows &= rows - 1;
-        for (uint32_t w0 = warp * 32u; w0 < q.W; w0 += blockDim.x) {
-            const uint32_t w = w0 + lane;
-            const uint32_t nw = w < q.W ? __ldcg(N + i * q.W + w) : 0u;
-            if (nw) T[i * q.W + w] = __ldcg(T + i * q.W + w) | nw;
-            if (q.Tsum) {  // the word summary of T follows
-                const unsigned sb = __ballot_sync(0xffffffffu, nw != 0u);
-                if (lane == 0 && sb) atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + (w0 >> 5)], sb);
+    const uint32_t *NR = parity ? q.R0 : q.R1;
+    const uint32_t W = q.W;
+    const bool keep_tt = q.TTsum != nullptr;
+    const uint64_t total = (uint64_t)q.n_nt * q.n;
+    for (uint64_t base = gwarp; base < total; base += 32ull * gwarps) {
+        const uint64_t mine = base + (uint64_t)lane * gwarps;
+        const bool flagged = mine < total && test_bit(NR + (mine / q.n) * W, (uint32_t)(mine % q.n));
+        unsigned rowmask = __ballot_sync(0xffffffffu, flagged);
+        while (rowmask) {
+            const int src = __ffs(rowmask) - 1;
+            rowmask &= rowmask - 1;
+            const uint64_t g = base + (uint64_t)src * gwarps;
+            const int a = (int)(g / q.n);
+            const uint32_t i = (uint32_t)(g % q.n);
+            if (lane == 0) atomicOr(&q.Trow[(uint64_t)a * W + (i >> 5)], 1u << (i & 31));
+            const uint32_t *N = (parity ? q.X0 : q.X1) + (uint64_t)a * q.plane + (uint64_t)i * W;
+            uint32_t *T = q.T + (uint64_t)a * q.plane + (uint64_t)i * W;
+            for (uint32_t w0 = 0; w0 < W; w0 += 128) {
+                uint32_t nw[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t w = w0 + 32u * u + lane;
+                    nw[u] = w < W ? __ldcg(N + w) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t w = w0 + 32u * u + lane;
+                    if (nw[u]) T[w] = __ldcg(T + w) | nw[u];
+                    const unsigned sb = __ballot_sync(0xffffffffu, nw[u] != 0u);
+                    if (lane == 0 && sb && q.Tsum)
+                        atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + ((w0 + 32u * u) >> 5)], sb);
+                    if (!keep_tt) continue;
+                    uint32_t x = nw[u];
+                    while (__any_sync(0xffffffffu, x != 0u)) {
+                        if (x) {
+                            const uint64_t j = (uint64_t)w * 32u + (uint32_t)(__ffs(x) - 1);
+                            x &= x - 1;
+                            atomicOr(q.TT + (uint64_t)a * q.plane + j * W + (i >> 5), 1u << (i & 31));
+                            atomicOr(q.TTsum + ((uint64_t)a * q.n_pad + j) * q.SW + (i >> 10), 1u << ((i >> 5) & 31));
+                        }
+                    }
+                }
             }
         }
     }
@@ -611,11 +640,9 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 3], s));
         if (rc != CFPQ_OK) return rc;
     }
-    if (c->lengths) {
-        const int rc = lengths_enqueue_merge(c, s);
-        if (rc != CFPQ_OK) return rc;
-    } else if (c->schedule == CFPQ_SCHED_JACOBI) {
-        k_merge<<<word_blocks, 128, 0, s>>>(c->d_q);
+    if (c->schedule == CFPQ_SCHED_JACOBI) {
+        const uint64_t blocks_needed = ((uint64_t)c->n_nt * c->n + 7) / 8;  // 8 warps per block
+        k_merge<<<(uint32_t)std::min<uint64_t>(blocks_needed, 4ull * (uint64_t)c->sms), 256, 0, s>>>(c->d_q);
         c->iter_launches++;
     }
     k_clear<<<std::min<uint32_t>(word_blocks, 4u * (uint32_t)c->sms), 128, 0, s>>>(c->d_q);

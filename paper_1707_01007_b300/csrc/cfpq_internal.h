@@ -135,7 +135,6 @@ void tensor_release(cfpq_ctx *c);
 // single-path lengths (cfpq_lengths.cu)
 int lengths_enqueue_seed(cfpq_ctx *c, cudaStream_t s);
 int lengths_enqueue_iteration(cfpq_ctx *c, cudaStream_t s);
-int lengths_enqueue_merge(cfpq_ctx *c, cudaStream_t s);
 int lengths_of_triples(cfpq_ctx *c, const cfpq_triple *d_tr, size_t count, uint32_t *d_out, cudaStream_t s);
 int lengths_rules_ok(const cfpq_ctx *c);  // few enough productions for the derivation-step encoding
 int lengths_path(cfpq_ctx *c, int32_t A, uint32_t m, uint32_t n, uint32_t len, uint32_t *nodes, int32_t *labels);

@@ -13,9 +13,9 @@
 //
 // Layout: one uint32 plane per non-terminal next to T, L[A][i * n_pad + j]. The search for the
 // middle nodes k of a pair (i, j) intersects row i of T_B with column j of T_C; for that the
-// seed and the Jacobi merge keep T^T up to date pair by pair, with a word summary of T and of
-// T^T (one bit per 32-bit word, SW words per row), so that only words that are non-zero on
-// both sides are read. A length cell is only
+// seed and the Jacobi merge (k_merge) keep T^T up to date pair by pair, with a word summary of
+// T and of T^T (one bit per 32-bit word, SW words per row), so that only words that are
+// non-zero on both sides are read. A length cell is only
 // written when its pair enters T_A and only read while the pair is in T_A, so the planes are
 // never cleared. The loop runs under the Jacobi schedule (T_{k+1} = T_k u T_k x T_k): after
 // every product of an execution has written its new pairs to the delta plane N and before
@@ -246,64 +246,6 @@ __global__ void __launch_bounds__(256, 2) k_lengths(const QDesc *qd, uint32_t *L
     }
 }
 
-// Jacobi merge where lengths are kept: as k_merge, and T^T and the word summaries of T and
-// T^T follow pair by pair. Persistent grid, one warp per flagged row (the lanes test 32 rows
-// of the warp's share at once); the T^T bits of a chunk of 32 words are set one bit per lane
-// per round, so dense and sparse words keep every lane busy.
-__global__ void __launch_bounds__(256) k_merge_tt(const QDesc *qd) {
-    const QDesc &q = *qd;
-    const int lane = threadIdx.x & 31;
-    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
-    const uint32_t *NR = parity ? q.R0 : q.R1;
-    const uint32_t W = q.W;
-    const uint64_t total = (uint64_t)q.n_nt * q.n;
-    for (uint64_t base = gwarp; base < total; base += 32ull * gwarps) {
-        const uint64_t mine = base + (uint64_t)lane * gwarps;
-        const bool flagged = mine < total && test_bit(NR + (mine / q.n) * W, (uint32_t)(mine % q.n));
-        unsigned rowmask = __ballot_sync(0xffffffffu, flagged);
-        while (rowmask) {
-            const int src = __ffs(rowmask) - 1;
-            rowmask &= rowmask - 1;
-            const uint64_t g = base + (uint64_t)src * gwarps;
-            const int a = (int)(g / q.n);
-            const uint32_t i = (uint32_t)(g % q.n);
-            if (lane == 0) atomicOr(&q.Trow[(uint64_t)a * W + (i >> 5)], 1u << (i & 31));
-            const uint32_t *N = (parity ? q.X0 : q.X1) + (uint64_t)a * q.plane + (uint64_t)i * W;
-            uint32_t *T = q.T + (uint64_t)a * q.plane + (uint64_t)i * W;
-            uint32_t *TT = q.TT + (uint64_t)a * q.plane + (i >> 5);
-            uint32_t *TTsum = q.TTsum + (uint64_t)a * q.n_pad * q.SW + (i >> 10);
-            const uint32_t tbit = 1u << (i & 31), sbit = 1u << ((i >> 5) & 31);
-            for (uint32_t w0 = 0; w0 < W; w0 += 128) {
-                uint32_t nw[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const uint32_t w = w0 + 32u * u + lane;
-                    nw[u] = w < W ? __ldcg(N + w) : 0u;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const uint32_t w = w0 + 32u * u + lane;
-                    if (nw[u]) T[w] = __ldcg(T + w) | nw[u];
-                    const unsigned sb = __ballot_sync(0xffffffffu, nw[u] != 0u);
-                    if (lane == 0 && sb)
-                        atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + ((w0 + 32u * u) >> 5)], sb);
-                    uint32_t x = nw[u];
-                    while (__any_sync(0xffffffffu, x != 0u)) {
-                        if (x) {
-                            const uint64_t j = (uint64_t)w * 32u + (uint32_t)(__ffs(x) - 1);
-                            x &= x - 1;
-                            atomicOr(TT + j * W, tbit);
-                            atomicOr(TTsum + j * q.SW, sbit);
-                        }
-                    }
-                }
-            }
-        }
-    }
-}
-
 // Rebuilds the walk of (a, m, n) from the recorded derivation steps, depth first, left child
 // first (one thread). Stack entries (A, i, j, offset of the sub-walk's first edge). Every
 // child was derived in an earlier loop execution than its parent, so the stack never holds
@@ -384,16 +326,6 @@ int lengths_enqueue_iteration(cfpq_ctx *c, cudaStream_t s) {
     const uint64_t blocks_needed = ((uint64_t)c->n_nt * c->n + kLenWarps - 1) / kLenWarps;
     const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)c->len_grid, std::max<uint64_t>(1, blocks_needed));
     k_lengths<<<blocks, 256, 0, s>>>(c->d_q, c->d_L, c->d_Wit, c->lplane);
-    c->iter_launches++;
-    return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
-}
-
-int lengths_enqueue_merge(cfpq_ctx *c, cudaStream_t s) {
-    const int rc = ensure_len_grid(c);
-    if (rc != CFPQ_OK) return rc;
-    const uint64_t blocks_needed = ((uint64_t)c->n_nt * c->n + kLenWarps - 1) / kLenWarps;
-    const uint32_t blocks = (uint32_t)std::min<uint64_t>((uint64_t)c->len_grid, std::max<uint64_t>(1, blocks_needed));
-    k_merge_tt<<<blocks, 256, 0, s>>>(c->d_q);
     c->iter_launches++;
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
