@@ -120,8 +120,10 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // edge (i, x, j); A -> eps adds (m, m). Every seeded pair is also a delta pair of
 // iteration 0 so that the first semi-naive iteration joins everything with everything.
 // ------------------------------------------------------------------------------------
+// block_cnt (shared memory, one counter per non-terminal) gathers the new pairs of a block for
+// one global update per non-terminal; NULL: a global atomic per new pair.
 __device__ __forceinline__ void seed_pair(const QDesc &q, int a, uint32_t i, uint32_t j,
-                                          unsigned long long *cnt) {
+                                          unsigned long long *cnt, unsigned *block_cnt = nullptr) {
     const uint64_t w = (uint64_t)a * q.plane + (uint64_t)i * q.W + (j >> 5);
     const uint32_t bit = 1u << (j & 31);
     const uint32_t old = atomicOr(&q.T[w], bit);
@@ -129,8 +131,12 @@ __device__ __forceinline__ void seed_pair(const QDesc &q, int a, uint32_t i, uin
         atomicOr(&q.X0[w], bit);
         atomicOr(&q.R0[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
         atomicOr(&q.Trow[(uint64_t)a * q.W + (i >> 5)], 1u << (i & 31));
-        atomicAdd(&q.st->dcount[0][a], 1ull);
-        atomicAdd(&q.st->tcount[a], 1ull);
+        if (block_cnt) {
+            atomicAdd(&block_cnt[a], 1u);
+        } else {
+            atomicAdd(&q.st->dcount[0][a], 1ull);
+            atomicAdd(&q.st->tcount[a], 1ull);
+        }
         if (q.Tsum) atomicOr(&q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + (j >> 10)], 1u << ((j >> 5) & 31));
         if (q.TTsum) {
             atomicOr(&q.TT[(uint64_t)a * q.plane + (uint64_t)j * q.W + (i >> 5)], 1u << (i & 31));
@@ -140,19 +146,29 @@ __device__ __forceinline__ void seed_pair(const QDesc &q, int a, uint32_t i, uin
     }
 }
 
+// Every thread of the block calls this (the per-non-terminal counts are gathered per block).
 __device__ inline void seed_query(const QDesc &q, uint64_t tid, uint64_t nthreads) {
+    __shared__ unsigned s_cnt[kMaxNT];
+    for (int a = threadIdx.x; a < q.n_nt; a += blockDim.x) s_cnt[a] = 0u;
+    __syncthreads();
     unsigned long long cnt = 0;
     for (uint64_t e = tid; e < q.n_edges; e += nthreads) {
         const cfpq_edge ed = q.edges[e];
         for (int u = 0; u < q.n_unary; u++)
-            if (q.unary[u].y == ed.label) seed_pair(q, q.unary[u].x, ed.src, ed.dst, &cnt);
+            if (q.unary[u].y == ed.label) seed_pair(q, q.unary[u].x, ed.src, ed.dst, &cnt, s_cnt);
     }
     for (uint64_t t = tid; t < (uint64_t)q.n_eps * q.n; t += nthreads) {
         const int a = q.eps[t / q.n];
         const uint32_t m = (uint32_t)(t % q.n);
-        seed_pair(q, a, m, m, &cnt);
+        seed_pair(q, a, m, m, &cnt, s_cnt);
     }
     if (cnt) atomicAdd(&q.st->seed_bits, cnt);
+    __syncthreads();
+    for (int a = threadIdx.x; a < q.n_nt; a += blockDim.x)
+        if (s_cnt[a]) {
+            atomicAdd(&q.st->dcount[0][a], (unsigned long long)s_cnt[a]);
+            atomicAdd(&q.st->tcount[a], (unsigned long long)s_cnt[a]);
+        }
 }
 
 // ------------------------------------------------------------------------------------
