@@ -82,10 +82,13 @@ __global__ void k_seed_witness_min(const QDesc *qd, uint32_t *Wit, uint64_t lpla
     }
 }
 
+// Summary words of a row taken per step of the middle-node search: kSumVec 16-byte loads.
+constexpr int kSumVec = 2;
+
 // Length of one new pair (A, i, j) from the productions r0 .. r1 - 1 of A (one lane, one
 // pair). The middle nodes k under A -> B C are the set bits of row i of T_B AND row j of TT_C
-// (column j of T_C): the two rows' word summaries are ANDed 16 words at a time (vector
-// loads), and only the words both flag are read and ANDed. Returns the minimum of
+// (column j of T_C): the two rows' word summaries are ANDed 4 kSumVec words at a time
+// (vector loads), and only the words both flag are read and ANDed. Returns the minimum of
 // l_B(i, k) + l_C(k, j) (UINT64_MAX if there is no middle node) and, in *wit, the production
 // index and middle node of the first minimum found (smallest index, then smallest k).
 __device__ __forceinline__ unsigned long long pair_length(const QDesc &q, const uint32_t *__restrict__ L,
@@ -102,16 +105,16 @@ __device__ __forceinline__ unsigned long long pair_length(const QDesc &q, const 
         const uint32_t *colC = q.TT + (uint64_t)C * q.plane + (uint64_t)j * W;
         const uint32_t *LB = L + (uint64_t)B * lplane + (uint64_t)i * np;
         const uint32_t *LC = L + (uint64_t)C * lplane + j;
-        for (uint32_t s0 = 0; s0 < SW; s0 += 16) {
-            uint4 b[4], c[4];
+        for (uint32_t s0 = 0; s0 < SW; s0 += 4u * kSumVec) {
+            uint4 b[kSumVec], c[kSumVec];
 #pragma unroll
-            for (int t = 0; t < 4; t++) {
+            for (int t = 0; t < kSumVec; t++) {
                 const bool in = s0 + 4u * t < SW;
                 b[t] = in ? __ldcg(sumB + s0 / 4 + t) : make_uint4(0u, 0u, 0u, 0u);
                 c[t] = in ? __ldcg(sumC + s0 / 4 + t) : make_uint4(0u, 0u, 0u, 0u);
             }
 #pragma unroll
-            for (int t = 0; t < 4; t++) {
+            for (int t = 0; t < kSumVec; t++) {
                 const uint32_t xs[4] = {b[t].x & c[t].x, b[t].y & c[t].y, b[t].z & c[t].z, b[t].w & c[t].w};
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
@@ -142,7 +145,7 @@ __device__ __forceinline__ unsigned long long pair_length(const QDesc &q, const 
 // Pairs queued per warp before the lanes take one each (two rounds of 32 fit).
 constexpr int kLenQ = 64;
 constexpr int kLenWarps = 8;
-constexpr int kScanU = 8;  // 32-word chunks of a row of N loaded together
+constexpr int kScanU = 4;  // 32-word chunks of a row of N loaded together
 
 // Persistent grid. Warp g scans the rows (A, i) = g, g + warps, ... of the n_nt x n row space
 // whose bit in the new delta's row bitmap is set (its lanes test 32 of those rows at once); the
@@ -150,7 +153,7 @@ constexpr int kScanU = 8;  // 32-word chunks of a row of N loaded together
 // shared memory (every lane still holding bits gives one per round); whenever 32 are queued,
 // every lane computes one pair's length, so the lanes stay busy however the new pairs are
 // spread over rows and words.
-__global__ void __launch_bounds__(256, 2) k_lengths(const QDesc *qd, uint32_t *L, uint32_t *Wit, uint64_t lplane) {
+__global__ void __launch_bounds__(256, 3) k_lengths(const QDesc *qd, uint32_t *L, uint32_t *Wit, uint64_t lplane) {
     __shared__ uint32_t q_i[kLenWarps][kLenQ], q_j[kLenWarps][kLenQ];
     __shared__ uint8_t q_a[kLenWarps][kLenQ];
     __shared__ int2 grp[kMaxNT];  // productions of each left-hand side: [x, y)
