@@ -822,10 +822,11 @@ int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
     return CFPQ_OK;
 }
 
-int read_status(cfpq_ctx *c, cudaStream_t s) {
+int read_status(cfpq_ctx *c, cudaStream_t s, unsigned *to_worklist) {
     DevState st;
     CK(cudaMemcpyAsync(&st, c->d_state, sizeof(st), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (to_worklist) *to_worklist = st.to_worklist;
     return apply_status(c, st);
 }
 
@@ -1195,15 +1196,13 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
     rc = c->path == CFPQ_PATH_WORKLIST ? worklist_run(c, s) : run_loop(c, s);
     if (rc != CFPQ_OK) return rc;
     CK(cudaEventRecord(c->ev1, s));
-    rc = read_status(c, s);
+    unsigned to_wl = 0;
+    rc = read_status(c, s, &to_wl);
     if (rc == CFPQ_ERR_CUDA) return rc;
     c->switched = false;
     if (rc == CFPQ_OK && c->allow_switch) {
         // the loop stopped after a long run of tiny deltas: the worklist path finishes the
         // closure from the current delta (same least fixpoint)
-        unsigned to_wl = 0;
-        CK(cudaMemcpyAsync(&to_wl, &c->d_state->to_worklist, sizeof(to_wl), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
         if (to_wl) {
             if (!c->h_wl && (rc = worklist_setup(c, c->h_edges.data(), c->h_edges.size())) != CFPQ_OK) return rc;
             const int64_t loops = c->stats.iterations;

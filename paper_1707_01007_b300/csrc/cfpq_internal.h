@@ -113,7 +113,9 @@ void free_ctx_device(cfpq_ctx *c);
 int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s);
 int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle);
 void arm_deadline(cfpq_ctx *c, cudaStream_t s);
-int read_status(cfpq_ctx *c, cudaStream_t s);
+// Copies the device state, applies it to the statistics; *to_worklist (may be NULL) receives
+// whether the loop stopped to hand over to the worklist path.
+int read_status(cfpq_ctx *c, cudaStream_t s, unsigned *to_worklist = nullptr);
 int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_useful_work(cfpq_ctx *c, int g, cudaStream_t s);
 int tensor_prepare(cfpq_ctx *c);
