@@ -85,7 +85,7 @@ enum cfpq_path {
     CFPQ_PATH_AUTO = 0,       /* per production group and loop execution, the cheaper of the two
                                  below, chosen on the device from the current pair counts (falls
                                  back to GATHER where tensor cores are not available); unless the
-                                 schedule is JACOBI, 256 executions in a row that add at most 8
+                                 schedule is JACOBI, 64 executions in a row that add at most 8
                                  pairs each end the loop and the WORKLIST path finishes the
                                  closure (cfpq_stats.iterations: the executions before that) */
     CFPQ_PATH_TENSOR = 1,     /* dense tcgen05 product of every production, every iteration */

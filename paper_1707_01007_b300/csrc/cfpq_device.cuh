@@ -34,7 +34,7 @@ enum : uint32_t { kErrNone = 0, kErrIterLimit = 1, kErrTimeout = 2 };
 // A loop execution that adds at most kSmallDelta pairs is "small"; after kSwitchAfter small
 // executions in a row, a loop that may switch hands the closure to the worklist path (a long
 // chain of derivations: one pair per execution would cost a matrix pass per pair).
-constexpr unsigned kSmallDelta = 8, kSwitchAfter = 256;
+constexpr unsigned kSmallDelta = 8, kSwitchAfter = 64;
 
 // Per-query device state; one instance in device memory per context.
 struct DevState {
