@@ -301,3 +301,41 @@ def test_solving_again_after_the_hand_over_to_the_worklist():
         q.solve()
         for nm in g.names:
             assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+
+
+@pytest.mark.parametrize("path,schedule", [(eng.PATH_AUTO, eng.SCHED_INPLACE), (eng.PATH_GATHER, eng.SCHED_JACOBI),
+                                           (eng.PATH_TENSOR, eng.SCHED_INPLACE), (eng.PATH_WORKLIST, eng.SCHED_INPLACE)])
+def test_most_nonterminals(path, schedule):
+    # CFPQ_MAX_NONTERM = 64 non-terminals (per-non-terminal arrays, groups and choice threads at
+    # their limit); 150 binary productions, 70 unary, 4 with A -> eps
+    text = synth.random_grammar_text(64, 3, 150, 70, 4, seed=9)
+    graph = synth.random_graph(120, 300, 3, seed=9)
+    g = eng.Grammar(text, graph.labels)
+    assert len(g.names) == 64
+    q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=120.0)
+    q.solve()
+    ref = oracle.hellings(graph, text)
+    for nm in g.names:
+        assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+
+
+def test_most_nonterminals_batched_and_lengths():
+    text = synth.random_grammar_text(64, 3, 150, 70, 4, seed=9)
+    graph = synth.random_graph(120, 300, 3, seed=9)
+    g = eng.Grammar(text, graph.labels)
+    ref = oracle.hellings(graph, text)
+    qs = [eng.Query(g, graph.n, graph.edges) for _ in range(3)]
+    eng.solve_batch(qs)
+    for q in qs:
+        for nm in g.names:
+            assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+    text_l = synth.random_grammar_text(64, 3, 100, 70, 4, seed=9)
+    small = synth.random_graph(40, 60, 3, seed=9)
+    gl = eng.Grammar(text_l, small.labels)
+    ql = eng.Query(gl, small.n, small.edges, schedule=eng.SCHED_JACOBI, lengths=True, timeout_s=120.0)
+    ql.solve()
+    cnf, L, _ = oracle.single_path_lengths(small, text_l)
+    for a, nm in enumerate(cnf.names):
+        pairs, lens = ql.lengths(nm)
+        got = {(int(m), int(n)): int(x) for (m, n), x in zip(pairs.tolist(), lens.tolist())}
+        assert got == L[a], nm
