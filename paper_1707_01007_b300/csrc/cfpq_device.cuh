@@ -66,6 +66,7 @@ struct DevState {
     unsigned int occ_now[kMaxNT];       // tile occupancy of A to be recomputed at the next tensor execution
     unsigned long long tc_live_steps;   // K steps the tensor-core products issued (after tile skipping)
     unsigned int plan_count[kMaxNT][2]; // tile skipping: live output tiles listed for group g, by execution parity
+    unsigned int plan_take[kMaxNT][2];  // tile skipping: listed tiles already claimed by a CTA
 };
 
 struct Rule {
@@ -410,7 +411,10 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
             st->odirty[tid] = 0u;
             st->occ_now[tid] = s_anytc ? d : (ld_u32(&st->occ_now[tid]) | d);
         }
-        if (tid < q.n_groups) st->plan_count[tid][(it + 1ull) & 1ull] = 0u;  // next execution's slot
+        if (tid < q.n_groups) {  // next execution's slots
+            st->plan_count[tid][(it + 1ull) & 1ull] = 0u;
+            st->plan_take[tid][(it + 1ull) & 1ull] = 0u;
+        }
     }
     if (tid == 0) {
         st->list_len = 0u;

@@ -59,6 +59,8 @@ struct __align__(1024) Smem {
     uint32_t a_pack[PST][BM * KW];
     uint32_t b_pack[PST][BN * KW];
     unsigned long long full_p[PST], empty_p[PST], full_u[UST], empty_u[UST], acc_full, acc_empty;
+    unsigned long long tile_full[2], tile_empty[2];  // tile skipping: claimed tile handed to the consumers
+    uint32_t tile_q[2];
     uint32_t tmem_base;
     int err;
 };
@@ -257,10 +259,12 @@ __global__ void __launch_bounds__(256) k_tile_plan(const QDesc *qd, int g, uint2
     if (live) list[base + __popc(m & ((1u << lane) - 1u))] = make_uint2(t, live);
 }
 
-// The product of group g over a sequence of output tiles: with list == NULL every tile, one
-// per CTA (grid = tiles); with a tile-skipping plan, the live tiles of the list, CTA b taking
-// entries b, b + grid, ... The roles keep one running stage counter across the CTA's tiles;
-// the accumulator is handed back by the epilogue (acc_empty) before the next tile's MMAs.
+// The product of group g over a sequence of output tiles: with list == NULL every tile, CTA b
+// taking tiles b, b + grid, ...; with a tile-skipping plan, the live tiles of the list, claimed
+// one at a time by the CTA's producer (an atomic on the plan's counter, so CTAs with short tiles
+// take more of them) and handed to the MMA and unpack warps through a two-slot ring in shared
+// memory. The roles keep one running stage counter across the CTA's tiles; the accumulator is
+// handed back by the epilogue (acc_empty) before the next tile's MMAs.
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_bool_gemm(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmTT, const QDesc *qd,
                    int g, const uint2 *list) {
@@ -289,6 +293,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mbar_init(&S.acc_full, 1);
         mbar_init(&S.acc_empty, UNPACK_THREADS);
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&S.tile_full[i], 1);
+            mbar_init(&S.tile_empty[i], 1 + UNPACK_THREADS);
+        }
         S.err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -303,6 +311,30 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = S.tmem_base;
+    constexpr uint32_t kNoTile = 0xFFFFFFFFu;
+    unsigned *take = &st->plan_take[g][st->iter & 1ull];
+    // ord-th tile of this CTA (the producer claims it; every consumer reads the claim once)
+    auto claim_tile = [&](uint32_t ord) -> uint32_t {
+        if (!list) {
+            const uint64_t i = (uint64_t)blockIdx.x + (uint64_t)ord * gridDim.x;
+            return i < ntile ? (uint32_t)i : kNoTile;
+        }
+        if (!mbar_wait(&S.tile_empty[ord & 1u], ((ord >> 1) & 1u) ^ 1u, err)) return kNoTile;
+        const uint32_t i = atomicAdd(take, 1u);
+        S.tile_q[ord & 1u] = i < ntile ? i : kNoTile;
+        mbar_arrive(&S.tile_full[ord & 1u]);
+        return i < ntile ? i : kNoTile;
+    };
+    auto read_tile = [&](uint32_t ord) -> uint32_t {
+        if (!list) {
+            const uint64_t i = (uint64_t)blockIdx.x + (uint64_t)ord * gridDim.x;
+            return i < ntile ? (uint32_t)i : kNoTile;
+        }
+        if (!mbar_wait(&S.tile_full[ord & 1u], (ord >> 1) & 1u, err)) return kNoTile;
+        const uint32_t i = S.tile_q[ord & 1u];
+        mbar_arrive(&S.tile_empty[ord & 1u]);
+        return i;
+    };
 
     if (warp == 0) {
         if (lane == 0) {
@@ -310,7 +342,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             // order (production, slice) in which the plan counted them
             uint32_t issued = 0;
             bool stop = false;
-            for (uint32_t i = blockIdx.x; i < ntile && !stop; i += gridDim.x) {
+            for (uint32_t ord = 0; !stop; ord++) {
+                const uint32_t i = claim_tile(ord);
+                if (i == kNoTile) break;
                 const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
                 uint32_t m0, n0;
                 tile_origin(q, e.x, m0, n0);
@@ -357,7 +391,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint32_t b0 = sa(S.b_tile[0]);
             uint32_t s = 0, tiles_done = 0;
             bool stop = false;
-            for (uint32_t i = blockIdx.x; i < ntile && !stop; i += gridDim.x) {
+            for (uint32_t ord = 0; !stop; ord++) {
+                const uint32_t i = read_tile(ord);
+                if (i == kNoTile) break;
                 const uint32_t steps = list ? list[i].y : dense_steps;
                 if (tiles_done > 0) {  // the epilogue has read the previous tile's accumulator
                     if (!mbar_wait(&S.acc_empty, (tiles_done - 1) & 1u, err)) break;
@@ -394,7 +430,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t *NR = (parity ? q.R0 : q.R1) + (uint64_t)A * W;
         uint32_t *TA = q.T + (uint64_t)A * q.plane;
         uint32_t s = 0, tiles_done = 0;
-        for (uint32_t i = blockIdx.x; i < ntile; i += gridDim.x) {
+        for (uint32_t ord = 0;; ord++) {  // ord: this CTA's ord-th tile (t is the thread's B row)
+            const uint32_t i = read_tile(ord);
+            if (i == kNoTile) break;
             const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
             uint32_t m0, n0;
             tile_origin(q, e.x, m0, n0);
