@@ -305,13 +305,14 @@ class Leg:
     def time(self, steps):
         torch = self.torch
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(self.stream)
-        for _ in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(self.stream)
+        for i in range(steps):
             self.step()
-        e1.record(self.stream)
+            ev[i + 1].record(self.stream)  # per-step boundaries (best and median beside the mean)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
+        self.step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        return ev[0].elapsed_time(ev[steps]) / steps
 
     def close(self):
         for q in self.qs:
@@ -366,6 +367,7 @@ def engine_arm(args):
         dist.barrier()
     clk = clocks.stop()
     ms = max_over_ranks(ms)
+    step_ms = {"best": min(main.step_ms), "median": float(np.median(main.step_ms)), "worst": max(main.step_ms)}
     value = job_rate(ops_per_step, ms / 1e3, world) / 1e9
     executed_dense = sum(s["dense_ops"] for s in st)
     results = {f"{label}:{g.names[0]}": q.count(g.names[0]) for (label, _), g, q in zip(grammars, gs, main.qs)}
@@ -416,8 +418,8 @@ def engine_arm(args):
 
     line = {
         "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None,
+        "warmup": args.warmup, "ms_per_step": ms, "step_ms_this_rank": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
         "dtype": "fp8e4m3 0/1 operands, f32 accumulate (tensor path); u32 bit-packed storage",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_NODES, "classes": N_CLASSES, "seed": SEED,

@@ -6,15 +6,17 @@
 // Section 2 (one Boolean matrix product per production, Valiant's |N|^2 reduction) with
 // the union T <- T u (T x T) of Algorithm 1 fused into the epilogue.
 //
-// Exactness: operands are 0/1 in FP8 E4M3 (the encoding 0x08 = 2^-6), products are
-// 0 or 2^-12 and are accumulated in F32: a sum of at most K <= 4 * 131072 such terms is
-// exact, and it is non-zero iff some term is, so "accumulator != 0" is the Boolean OR
-// of ANDs. (tcgen05 has no 8-bit integer kind on sm_103a.)
+// Exactness: operands are 0 or a positive FP8 E4M3 value (a one at K position q of a byte
+// group is the byte 1 << q, 2^-9 .. 2^1, and 0x40 = 2.0 for q = 7; both operands use the
+// same values at the same K), products are 0 or at least 2^-18 and are accumulated in F32:
+// every term is non-negative, so the sum is non-zero iff some term is, and "accumulator
+// != 0" is the Boolean OR of ANDs. (tcgen05 has no 8-bit integer kind on sm_103a.)
 //
 // Data flow per CTA (one 128 x 256 output tile):
 //   warp 0     TMA: bit-packed 128 x 128-bit tile of T_B and 256 x 128-bit tile of T_C^T
 //              (the transposed copy, so both operands are K-major) into a packed ring
-//   warps 2-9  unpack: 1 bit -> 1 byte. The T_B tile goes straight into tensor memory
+//   warps 2-17 unpack, in two groups of 8 warps taking alternate K stages (so one group's
+//              waits and stores overlap the other's unpacking): 1 bit -> 1 byte. The T_B tile goes straight into tensor memory
 //              (tcgen05.st, half a 128-byte K slice per row, lane and warp), the T_C^T tile into
 //              shared memory in the 128-byte-swizzled K-major layout. Within each 32-bit
 //              word, bit q + 8r becomes byte 4q + r of the word's 32 bytes: the same
@@ -22,7 +24,7 @@
 //              each 4 output bytes cost a shift and a mask
 //   warp 1     one thread issues tcgen05.mma (M=128, N=256, K=32, A from tensor memory,
 //              B from shared memory) into the TMEM accumulator (256 columns)
-//   warps 2-9  epilogue: tcgen05.ld, threshold, pack 32 columns per word, OR-merge into
+//   warps 2-17 epilogue: tcgen05.ld, threshold, pack 32 columns per word, OR-merge into
 //              T_A, record the new pairs (delta plane, row bitmap), set the change flag
 // Every mbarrier wait is bounded (%globaltimer); on expiry the CTA records an error,
 // drains what it started and returns.
@@ -44,7 +46,9 @@ constexpr int BK = 32 * KW;           // 128 K elements per stage
 constexpr int PST = 8, UST = 5;       // packed / unpacked ring depths
 constexpr int A_PACK = BM * KW * 4, B_PACK = BN * KW * 4;  // bytes of one packed stage
 constexpr int B_TILE = BN * BK;       // bytes of one unpacked B stage (FP8)
-constexpr int UNPACK_WARPS = 8;      // two per SM sub-partition
+constexpr int UNPACK_GROUPS = 2;     // groups of 8 unpack warps; group g takes the K stages s = g mod 2
+constexpr int GROUP_THREADS = 256;   // one group: two warps per SM sub-partition
+constexpr int UNPACK_WARPS = 8 * UNPACK_GROUPS;
 constexpr uint32_t RASTER_N = 8;      // N tiles per rasterisation band
 constexpr int UNPACK_THREADS = 32 * UNPACK_WARPS;
 constexpr int THREADS = 64 + UNPACK_THREADS;
@@ -173,9 +177,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16
         : "memory");
 }
 
-// 4 bytes of the unpacked K-row: byte r = bit (q + 8r) of w, as FP8 E4M3 0x08 (2^-6) or 0.
+// 4 bytes of the unpacked K-row: byte r = bit (q + 8r) of w, as a positive FP8 E4M3 value or
+// 0. For q < 7 the bit stays where it is (byte 1 << q: one AND per 4 bytes); bit 7 would be
+// the sign, so it moves to bit 6 (0x40 = 2.0).
 __device__ __forceinline__ uint32_t spread(uint32_t w, int q) {
-    return (q <= 3 ? (w << (3 - q)) : (w >> (q - 3))) & 0x08080808u;
+    return q < 7 ? (w & (0x01010101u << q)) : ((w >> 1) & 0x40404040u);
 }
 
 // Unpacks one 128-bit K slice of a row into the 128-byte swizzled row r of a tile.
@@ -285,10 +291,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < PST; i++) {
             mbar_init(&S.full_p[i], 1);
-            mbar_init(&S.empty_p[i], UNPACK_THREADS);
+            mbar_init(&S.empty_p[i], GROUP_THREADS);
         }
         for (int i = 0; i < UST; i++) {
-            mbar_init(&S.full_u[i], UNPACK_THREADS);
+            mbar_init(&S.full_u[i], GROUP_THREADS);
             mbar_init(&S.empty_u[i], 1);
         }
         mbar_init(&S.acc_full, 1);
@@ -418,9 +424,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // ---------------- unpack (8 warps), then the epilogue of each tile
-        const int t = threadIdx.x - 64;             // 0 .. 255: the B row of this thread
+        const int uw = warp - 2;                    // unpack warp 0 .. UNPACK_WARPS-1
+        const uint32_t grp = (uint32_t)(uw >> 3);   // K stages s with s % UNPACK_GROUPS == grp
+        const int t = (threadIdx.x - 64) & 255;     // the B row of this thread
         const int quad = warp & 3;                  // TMEM lane quadrant this warp may access
-        const int half = (warp - 2) >> 2;           // which half of the A slice / of the columns
+        const int half = (uw >> 2) & 1;             // which half of the A slice
+        constexpr int CH = (BN / 32) / (UNPACK_WARPS / 4);  // epilogue: 32-column chunks per warp
+        const int cq = uw >> 2;                     // ... chunks cq * CH .. cq * CH + CH - 1
         const int arow = quad * 32 + lane;
         const uint32_t a_lane = tmem + ((uint32_t)(quad * 32) << 16) + ACC_COLS + (uint32_t)(16 * half);
         const uint32_t W = q.W;
@@ -437,6 +447,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t m0, n0;
             tile_origin(q, e.x, m0, n0);
             for (uint32_t u = 0; u < e.y; u++, s++) {
+                if (s % UNPACK_GROUPS != grp) continue;
                 const uint32_t ps = s % PST, pph = (s / PST) & 1u;
                 const uint32_t us = s % UST, uph = (s / UST) & 1u;
                 if (!mbar_wait(&S.full_p[ps], pph, err)) break;
@@ -458,7 +469,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             unsigned cnt = 0;
             uint32_t smask = 0;  // words of this row written in place (one word of the summary of T_A)
 #pragma unroll 1
-            for (int c = half * (BN / 64); c < (half + 1) * (BN / 64); c++) {
+            for (int c = cq * CH; c < (cq + 1) * CH; c++) {
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(c * 32), v);
                 uint32_t word = 0;
