@@ -49,6 +49,7 @@ constexpr int B_TILE = BN * BK;       // bytes of one unpacked B stage (FP8)
 constexpr int UNPACK_GROUPS = 2;     // groups of 8 unpack warps; group g takes the K stages s = g mod 2
 constexpr int GROUP_THREADS = 256;   // one group: two warps per SM sub-partition
 constexpr int UNPACK_WARPS = 8 * UNPACK_GROUPS;
+static_assert(UNPACK_GROUPS < UST, "a group's ring slot advances by UNPACK_GROUPS with one wrap at most");
 constexpr uint32_t RASTER_N = 8;      // N tiles per rasterisation band
 constexpr int UNPACK_THREADS = 32 * UNPACK_WARPS;
 constexpr int THREADS = 64 + UNPACK_THREADS;
@@ -184,21 +185,25 @@ __device__ __forceinline__ uint32_t spread(uint32_t w, int q) {
     return q < 7 ? (w & (0x01010101u << q)) : ((w >> 1) & 0x40404040u);
 }
 
-// Unpacks one 128-bit K slice of a row into the 128-byte swizzled row r of a tile.
-__device__ __forceinline__ void unpack_row(uint8_t *tile, int r, uint4 p) {
+// Byte offsets of the 16-byte chunks c = 0..7 of row r in a 128-byte-swizzled K-major tile.
+__device__ __forceinline__ void swizzled_row(int r, uint32_t (&off)[8]) {
+#pragma unroll
+    for (int c = 0; c < 8; c++) off[c] = (uint32_t)r * 128u + ((uint32_t)(c ^ (r & 7)) << 4);
+}
+
+// Unpacks one 128-bit K slice of a row into its swizzled row of a tile (chunk offsets off).
+__device__ __forceinline__ void unpack_row(uint8_t *tile, const uint32_t (&off)[8], uint4 p) {
     const uint32_t w[4] = {p.x, p.y, p.z, p.w};
-    uint8_t *row = tile + r * 128;
 #pragma unroll
     for (int wi = 0; wi < 4; wi++)
 #pragma unroll
         for (int h = 0; h < 2; h++) {
-            const int c = wi * 2 + h;
             uint4 o;
             o.x = spread(w[wi], 4 * h + 0);
             o.y = spread(w[wi], 4 * h + 1);
             o.z = spread(w[wi], 4 * h + 2);
             o.w = spread(w[wi], 4 * h + 3);
-            *reinterpret_cast<uint4 *>(row + ((c ^ (r & 7)) << 4)) = o;
+            *reinterpret_cast<uint4 *>(tile + off[wi * 2 + h]) = o;
         }
 }
 
@@ -439,17 +444,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t *NA = (parity ? q.X0 : q.X1) + (uint64_t)A * q.plane;
         uint32_t *NR = (parity ? q.R0 : q.R1) + (uint64_t)A * W;
         uint32_t *TA = q.T + (uint64_t)A * q.plane;
-        uint32_t s = 0, tiles_done = 0;
+        uint32_t off[8];
+        swizzled_row(t, off);
+        uint32_t s_end = 0, tiles_done = 0;
+        uint32_t sn = grp;                          // this group's next K stage (counted over the CTA's tiles)
+        uint32_t us = grp % UST, uph = 0;           // its unpacked ring slot and phase: sn % UST, (sn / UST) & 1
         for (uint32_t ord = 0;; ord++) {  // ord: this CTA's ord-th tile (t is the thread's B row)
             const uint32_t i = read_tile(ord);
             if (i == kNoTile) break;
             const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
             uint32_t m0, n0;
             tile_origin(q, e.x, m0, n0);
-            for (uint32_t u = 0; u < e.y; u++, s++) {
-                if (s % UNPACK_GROUPS != grp) continue;
-                const uint32_t ps = s % PST, pph = (s / PST) & 1u;
-                const uint32_t us = s % UST, uph = (s / UST) & 1u;
+            s_end += e.y;
+            for (; sn < s_end; sn += UNPACK_GROUPS) {
+                const uint32_t ps = sn % PST, pph = (sn / PST) & 1u;
                 if (!mbar_wait(&S.full_p[ps], pph, err)) break;
                 if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) break;
                 tc_fence_after();
@@ -457,11 +465,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint4 pb = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
                 mbar_arrive(&S.empty_p[ps]);
                 unpack_half_row_tmem(a_lane + us * A_COLS, pa);
-                unpack_row(S.b_tile[us], t, pb);
+                unpack_row(S.b_tile[us], off, pb);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(&S.full_u[us]);
+                us += UNPACK_GROUPS;
+                if (us >= UST) {
+                    us -= UST;
+                    uph ^= 1u;
+                }
             }
             const bool ok = !*err && mbar_wait(&S.acc_full, tiles_done & 1u, err);
             tc_fence_after();
