@@ -168,22 +168,25 @@ __global__ void __launch_bounds__(128) k_clear_t_rows(const QDesc *qd) {
     }
 }
 
-// Clears the rows of the delta plane read in this execution (one block per non-terminal and
-// row word of 32 rows).
+// Clears the rows of the delta plane read in this execution. Blocks take (non-terminal, row
+// word of 32 rows) units grid-stride; the k-th flagged row of a unit goes to warp k % 4, which
+// zeroes it with 16-byte stores (W is a multiple of 8, so every row is whole uint4s).
 __global__ void __launch_bounds__(128) k_clear(const QDesc *qd) {
     const QDesc &q = *qd;
     const uint32_t rw = (q.n + 31u) / 32u;
     const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
-    // grid-stride over the (non-terminal, row word) units: most have no flagged row
+    const uint32_t W4 = q.W / 4u;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (uint32_t unit = blockIdx.x; unit < (uint32_t)q.n_nt * rw; unit += gridDim.x) {
         const int a = (int)(unit / rw);
         const uint32_t wq = unit % rw;
         uint32_t rows = __ldcg((parity ? q.R1 : q.R0) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
-        uint32_t *D = (parity ? q.X1 : q.X0) + (uint64_t)a * q.plane;
-        while (rows) {
+        uint4 *D = reinterpret_cast<uint4 *>((parity ? q.X1 : q.X0) + (uint64_t)a * q.plane);
+        for (int k = 0; rows; k++) {
             const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
             rows &= rows - 1;
-            for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) D[i * q.W + w] = 0u;
+            if ((k & 3) != warp) continue;
+            for (uint32_t w = (uint32_t)lane; w < W4; w += 32u) D[i * W4 + w] = make_uint4(0u, 0u, 0u, 0u);
         }
     }
 }
@@ -196,9 +199,9 @@ __global__ void __launch_bounds__(128) k_clear(const QDesc *qd) {
 // non-empty rows of T_B (2W words each) and one D_C row per bit of T_B that meets a
 // non-empty row of D_C (expected |T_B| * min(1, |D_C| / n)). Tensor cost: 2 n_pad^3 Boolean
 // ops per production, plus a transpose per right operand changed since its last refresh.
-constexpr double kTensorOpsPerNs = 2.9e6;     // measured tensor-core Boolean product rate
-constexpr double kGatherBytesPerNs = 600.0;   // measured gather rate (latency-bound)
-constexpr double kTransposeBytesPerNs = 3000.0;
+constexpr float kTensorOpsPerNs = 2.9e6f;     // measured tensor-core Boolean product rate
+constexpr float kGatherBytesPerNs = 600.0f;   // measured gather rate (latency-bound)
+constexpr float kTransposeBytesPerNs = 3000.0f;
 
 // Every thread of one block (at least max(n_nt, n_groups) threads) calls this: thread g
 // costs group g from the device-side counts, thread a assigns the refresh of TT[A].
@@ -211,19 +214,20 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
     __syncthreads();
     if (tid < q.n_groups) {
         const int g = tid;
-        const double n = (double)q.n, W = (double)q.W, np = (double)q.n_pad;
-        const double per_rule_ns = 2.0 * np * np * np / kTensorOpsPerNs;
-        const double transpose_ns = 2.0 * np * np / 8.0 / kTransposeBytesPerNs;
+        // single precision: a cost estimate (either choice is exact), and FP32 is the fast pipe
+        const float n = (float)q.n, W = (float)q.W, np = (float)q.n_pad;
+        const float per_rule_ns = 2.0f * np * np * np / kTensorOpsPerNs;
+        const float transpose_ns = 2.0f * np * np / 8.0f / kTransposeBytesPerNs;
         const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
-        double words = 0.0, tensor_ns = (double)(r1 - r0) * per_rule_ns;
+        float words = 0.0f, tensor_ns = (float)(r1 - r0) * per_rule_ns;
         for (int r = r0; r < r1; r++) {
             const int B = q.rules[r].b, C = q.rules[r].c;
-            const double dB = (double)st->dcount[p][B], dC = (double)st->dcount[p][C], tB = (double)st->tcount[B];
+            const float dB = (float)st->dcount[p][B], dC = (float)st->dcount[p][C], tB = (float)st->tcount[B];
             words += dB * W;
-            if (dC > 0.0) words += fmin(n, tB) * 2.0 * W + tB * fmin(1.0, dC / n) * W;
+            if (dC > 0.0f) words += fminf(n, tB) * 2.0f * W + tB * fminf(1.0f, dC / n) * W;
             if (st->dirty[C]) tensor_ns += transpose_ns;
         }
-        const unsigned use = tensor_ns < words * 4.0 / kGatherBytesPerNs ? 1u : 0u;
+        const unsigned use = tensor_ns < words * 4.0f / kGatherBytesPerNs ? 1u : 0u;
         st->use_tensor[g] = use;
         s_use[g] = use;
         if (use_handles) cudaGraphSetConditional(handles[g], use);
