@@ -27,33 +27,27 @@ __device__ __forceinline__ uint32_t pack_row_item(int g, uint32_t ch, uint32_t i
     return ((uint32_t)g << 22) | (ch << 17) | i;
 }
 
-// Gather scan (one lane per (group, row word)): the rows of the word that have a left delta
-// row or, where the right operand has a delta, a non-empty left row, become one list item
-// per column chunk. Groups on the tensor cores this execution are skipped.
-__global__ void __launch_bounds__(256) k_scan_rows(const QDesc *qd, uint32_t *list, uint32_t cap, uint32_t nch) {
-    const QDesc &q = *qd;
+// Gather scan for the loop execution of parity par (one lane per (group, row word)): the rows
+// of the word that have a left delta row or, where the right operand has a delta, a non-empty
+// left row, become one list item per column chunk. Every group is listed; the gather skips
+// the groups that the execution's choice puts on the tensor cores.
+__device__ __forceinline__ void scan_rows(const QDesc &q, uint64_t item, uint32_t par, uint32_t *list, uint32_t cap,
+                                          uint32_t nch) {
     DevState *st = q.st;
     const uint32_t rw = (q.n + 31u) / 32u;
-    const uint64_t item = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (item == 0)
-        for (int g = 0; g < q.n_groups; g++)
-            if (!st->use_tensor[g]) atomicAdd(&st->gather_products, (unsigned long long)(q.gstart[g + 1] - q.gstart[g]));
     uint32_t cand = 0, wq = 0;
     int g = 0;
     if (item < (uint64_t)q.n_groups * rw) {
         g = (int)(item / rw);
         wq = (uint32_t)(item % rw);
-        if (!st->use_tensor[g]) {
-            const uint32_t parity = (uint32_t)(st->iter & 1ull);
-            const uint32_t *DR = parity ? q.R1 : q.R0;
-            for (int r = q.gstart[g]; r < q.gstart[g + 1]; r++) {
-                const int B = q.rules[r].b, C = q.rules[r].c;
-                cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
-                if (st->dcount[parity][C] != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
-            }
-            cand &= rows_in_word(q.n, wq);
+        const uint32_t *DR = par ? q.R1 : q.R0;
+        for (int r = q.gstart[g]; r < q.gstart[g + 1]; r++) {
+            const int B = q.rules[r].b, C = q.rules[r].c;
+            cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
+            if (__ldcg(&st->dcount[par][C]) != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
         }
+        cand &= rows_in_word(q.n, wq);
     }
     const uint32_t cnt = (uint32_t)__popc(cand) * nch;
     uint32_t incl = cnt;
@@ -64,7 +58,7 @@ __global__ void __launch_bounds__(256) k_scan_rows(const QDesc *qd, uint32_t *li
     }
     const uint32_t wtotal = __shfl_sync(0xffffffffu, incl, 31);
     uint32_t base = 0;
-    if (lane == 31 && wtotal) base = atomicAdd(&st->list_len, wtotal);
+    if (lane == 31 && wtotal) base = atomicAdd(&st->list_len[par], wtotal);
     base = __shfl_sync(0xffffffffu, base, 31);
     uint32_t pos = base + incl - cnt;
     if ((uint64_t)pos + cnt > cap) {  // cannot happen: the list holds every (group, row, chunk)
@@ -78,17 +72,33 @@ __global__ void __launch_bounds__(256) k_scan_rows(const QDesc *qd, uint32_t *li
     }
 }
 
+// The first loop execution's list (after the seed).
+__global__ void __launch_bounds__(256) k_scan_rows(const QDesc *qd, uint32_t *list, uint32_t cap, uint32_t nch) {
+    const QDesc &q = *qd;
+    scan_rows(q, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint32_t)(q.st->iter & 1ull), list, cap, nch);
+}
+
 template <int CPL>
 __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDesc *qd, const uint32_t *list, uint32_t cap) {
     const QDesc &q = *qd;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const uint32_t len = min(q.st->list_len, cap);
-    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
+    const DevState *st = q.st;
+    const uint32_t parity = (uint32_t)(st->iter & 1ull);
+    const uint32_t len = min(st->list_len[parity], cap);
+    uint64_t tensor_groups = 0;  // this execution's tensor-core groups: their listed items are skipped
+    for (int g = 0; g < q.n_groups; g++)
+        if (st->use_tensor[g]) tensor_groups |= 1ull << g;
+    if (gwarp == 0 && lane == 0)
+        for (int g = 0; g < q.n_groups; g++)
+            if (!((tensor_groups >> g) & 1ull))
+                atomicAdd(&q.st->gather_products, (unsigned long long)(q.gstart[g + 1] - q.gstart[g]));
     for (uint64_t w = gwarp; w < len; w += gwarps) {
         const uint32_t e = list[w];
-        gather_row_chunk<CPL>(q, (int)(e >> 22), e & 0x1FFFFu, (e >> 17) & 31u, lane, parity);
+        const int g = (int)(e >> 22);
+        if ((tensor_groups >> g) & 1ull) continue;
+        gather_row_chunk<CPL>(q, g, e & 0x1FFFFu, (e >> 17) & 31u, lane, parity);
     }
 }
 
@@ -169,15 +179,15 @@ __global__ void __launch_bounds__(128) k_clear_t_rows(const QDesc *qd) {
 }
 
 // Clears the rows of the delta plane read in this execution. Blocks take (non-terminal, row
-// word of 32 rows) units grid-stride; the k-th flagged row of a unit goes to warp k % 4, which
-// zeroes it with 16-byte stores (W is a multiple of 8, so every row is whole uint4s).
-__global__ void __launch_bounds__(128) k_clear(const QDesc *qd) {
-    const QDesc &q = *qd;
+// word of 32 rows) units grid-stride (block b of nb); the k-th flagged row of a unit goes to
+// warp k % (warps per block), which zeroes it with 16-byte stores (W is a multiple of 8, so
+// every row is whole uint4s).
+__device__ __forceinline__ void clear_delta_rows(const QDesc &q, uint32_t b, uint32_t nb) {
     const uint32_t rw = (q.n + 31u) / 32u;
     const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
     const uint32_t W4 = q.W / 4u;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (uint32_t unit = blockIdx.x; unit < (uint32_t)q.n_nt * rw; unit += gridDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    for (uint32_t unit = b; unit < (uint32_t)q.n_nt * rw; unit += nb) {
         const int a = (int)(unit / rw);
         const uint32_t wq = unit % rw;
         uint32_t rows = __ldcg((parity ? q.R1 : q.R0) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
@@ -185,10 +195,25 @@ __global__ void __launch_bounds__(128) k_clear(const QDesc *qd) {
         for (int k = 0; rows; k++) {
             const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
             rows &= rows - 1;
-            if ((k & 3) != warp) continue;
+            if (k % nw != warp) continue;
             for (uint32_t w = (uint32_t)lane; w < W4; w += 32u) D[i * W4 + w] = make_uint4(0u, 0u, 0u, 0u);
         }
     }
+}
+
+__global__ void __launch_bounds__(128) k_clear(const QDesc *qd) { clear_delta_rows(*qd, blockIdx.x, gridDim.x); }
+
+// End of a loop execution on a path with gathers: blocks below scan_blocks list the next
+// execution's gather items (its delta rows and counts are final here), the others clear the
+// delta rows read in this execution (the two touch different planes).
+__global__ void __launch_bounds__(256) k_clear_scan(const QDesc *qd, uint32_t *list, uint32_t cap, uint32_t nch,
+                                                    uint32_t scan_blocks) {
+    const QDesc &q = *qd;
+    if (blockIdx.x < scan_blocks)
+        scan_rows(q, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint32_t)((q.st->iter + 1ull) & 1ull), list,
+                  cap, nch);
+    else
+        clear_delta_rows(q, blockIdx.x - scan_blocks, gridDim.x - scan_blocks);
 }
 
 
@@ -516,13 +541,11 @@ uint32_t gather_chunks(uint32_t W, int *cpl) {
 static uint32_t row_warp_blocks(uint64_t rows) { return (uint32_t)((rows * 32 + 255) / 256); }
 
 // The gather products of one loop execution, for every group not on the tensor cores: a
-// scan lists the (group, row, column chunk) items that have work, then a persistent grid
-// runs one warp per listed item.
+// persistent grid runs one warp per (group, row, column chunk) item that the list of this
+// execution holds (listed after the seed, then at the end of each execution for the next).
 static int enqueue_gathers(cfpq_ctx *c, cudaStream_t s) {
     int cpl;
-    const uint32_t nch = gather_chunks(c->W, &cpl);
-    const uint64_t items = (uint64_t)c->n_groups * ((c->n + 31) / 32);
-    k_scan_rows<<<(uint32_t)((items + 255) / 256), 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, nch);
+    gather_chunks(c->W, &cpl);
     const uint32_t grid = (uint32_t)c->gather_grid;
     switch (cpl) {
         case 1: k_gather_list<1><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
@@ -530,7 +553,7 @@ static int enqueue_gathers(cfpq_ctx *c, cudaStream_t s) {
         case 4: k_gather_list<4><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
         default: k_gather_list<8><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
     }
-    c->iter_launches += 2;
+    c->iter_launches += 1;
     CK(cudaGetLastError());
     return CFPQ_OK;
 }
@@ -649,7 +672,15 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         k_merge<<<(uint32_t)std::min<uint64_t>(blocks_needed, 4ull * (uint64_t)c->sms), 256, 0, s>>>(c->d_q);
         c->iter_launches++;
     }
-    k_clear<<<std::min<uint32_t>(word_blocks, 4u * (uint32_t)c->sms), 128, 0, s>>>(c->d_q);
+    if (c->any_gather) {
+        int cpl;
+        const uint32_t nch = gather_chunks(c->W, &cpl);
+        const uint32_t scan_blocks = (uint32_t)(((uint64_t)c->n_groups * ((c->n + 31) / 32) + 255) / 256);
+        const uint32_t clear_blocks = std::min<uint32_t>(word_blocks, 2u * (uint32_t)c->sms);
+        k_clear_scan<<<scan_blocks + clear_blocks, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, nch, scan_blocks);
+    } else {
+        k_clear<<<std::min<uint32_t>(word_blocks, 4u * (uint32_t)c->sms), 128, 0, s>>>(c->d_q);
+    }
     k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle, (use_handle && c->auto_mixed) ? c->d_choice : nullptr);
     c->iter_launches += 2;
     CK(cudaGetLastError());
@@ -818,6 +849,14 @@ int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
     if (c->lengths) {
         const int rc = lengths_enqueue_seed(c, s);
         if (rc != CFPQ_OK) return rc;
+        c->fixed_launches++;
+    }
+    if (c->any_gather) {  // the first execution's gather list
+        int cpl;
+        const uint32_t nch = gather_chunks(c->W, &cpl);
+        const uint64_t items = (uint64_t)c->n_groups * ((c->n + 31) / 32);
+        k_scan_rows<<<(uint32_t)((items + 255) / 256), 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, nch);
+        CK(cudaGetLastError());
         c->fixed_launches++;
     }
     bool any_tensor = false;

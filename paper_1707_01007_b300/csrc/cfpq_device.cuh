@@ -55,8 +55,7 @@ struct DevState {
     unsigned long long tcount[kMaxNT];  // pairs in T[A] (seed + every product's new pairs)
     unsigned int tt_now[kMaxNT];        // AUTO path: g + 1 if group g refreshes TT[A] this iteration, else 0
     unsigned long long prof_words;      // profile mode: 32-bit words the gather products read or wrote
-    unsigned int list_len;              // gather items listed in this loop execution (single-query path)
-    unsigned int pad_list;
+    unsigned int list_len[2];           // gather items listed for the loop execution of this parity (single-query path)
     unsigned long long useful_macs;     // profile mode: sum over tensor products of nnz(col k of T_B) nnz(row k of T_C)
     unsigned int small_run;             // consecutive executions that added at most kSmallDelta pairs
     unsigned int to_worklist;           // the loop stopped to hand the closure to the worklist path
@@ -417,7 +416,7 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
         }
     }
     if (tid == 0) {
-        st->list_len = 0u;
+        st->list_len[old] = 0u;  // consumed; the next list of this parity is built one execution later
         const unsigned changed = ld_u32(&st->changed);
         st->changed = 0u;
         st->iter = it + 1;
