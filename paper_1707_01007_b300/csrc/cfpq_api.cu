@@ -297,6 +297,42 @@ __global__ void k_arm_deadline(DevState *st, unsigned long long dt_ns) { st->dea
 
 // --- extraction: popc per row -> exclusive scan -> emit (A, m, n) in row-major order ---
 
+// Emits the pairs of row i of T_a (W words) as triples (a, i, j) from position off on, in
+// column order (one warp). Eight 32-word chunks are loaded at once, then each non-empty chunk
+// is placed by a warp prefix sum of its words' bit counts; empty chunks cost no scan.
+__device__ __forceinline__ void emit_row(const uint32_t *row, uint32_t W, int a, uint32_t i, uint64_t off, int lane,
+                                         cfpq_triple *out) {
+    constexpr int kBatch = 8;
+    for (uint32_t b0 = 0; b0 < W; b0 += 32u * kBatch) {
+        uint32_t xs[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; k++) {
+            const uint32_t w = b0 + 32u * k + (uint32_t)lane;
+            xs[k] = w < W ? row[w] : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; k++) {
+            uint32_t x = xs[k];
+            if (__ballot_sync(0xffffffffu, x != 0u) == 0u) continue;  // warp-uniform
+            const uint32_t w0 = b0 + 32u * k;
+            const uint32_t c = __popc(x);
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            uint64_t pos = off + incl - c;
+            while (x) {
+                const uint32_t j = (w0 + lane) * 32u + (uint32_t)(__ffs(x) - 1);
+                x &= x - 1;
+                out[pos++] = cfpq_triple{a, i, j};
+            }
+            off += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
 __global__ void k_count_rows(const QDesc *qd, int a, uint32_t *counts) {
     const QDesc &q = *qd;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -342,24 +378,7 @@ __global__ void k_emit(const QDesc *qd, int a, const uint64_t *offsets, const ui
     const int lane = threadIdx.x & 31;
     if (warp >= q.n_pad || counts[warp] == 0) return;
     const uint32_t *row = q.T + (uint64_t)a * q.plane + warp * q.W;
-    uint64_t off = offsets[warp];
-    for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
-        uint32_t x = (w0 + lane < q.W) ? row[w0 + lane] : 0u;
-        const uint32_t c = __popc(x);
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        uint64_t pos = off + incl - c;
-        while (x) {
-            const uint32_t j = (w0 + lane) * 32u + (uint32_t)(__ffs(x) - 1);
-            x &= x - 1;
-            out[pos++] = cfpq_triple{a, (uint32_t)warp, j};
-        }
-        off += __shfl_sync(0xffffffffu, incl, 31);
-    }
+    emit_row(row, q.W, a, (uint32_t)warp, offsets[warp], lane, out);
 }
 
 // --- extraction of every relation at once: counts over (non-terminal, row) cells, a
@@ -459,24 +478,7 @@ __global__ void k_emit_all(const QDesc *qd, const uint64_t *offsets, const uint3
     const int a = (int)(cell / q.n_pad);
     const uint32_t i = (uint32_t)(cell % q.n_pad);
     const uint32_t *row = q.T + (uint64_t)a * q.plane + (uint64_t)i * q.W;
-    uint64_t off = offsets[cell];
-    for (uint32_t w0 = 0; w0 < q.W; w0 += 32) {
-        uint32_t x = (w0 + lane < q.W) ? row[w0 + lane] : 0u;
-        const uint32_t c = __popc(x);
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        uint64_t pos = off + incl - c;
-        while (x) {
-            const uint32_t j = (w0 + lane) * 32u + (uint32_t)(__ffs(x) - 1);
-            x &= x - 1;
-            out[pos++] = cfpq_triple{a, i, j};
-        }
-        off += __shfl_sync(0xffffffffu, incl, 31);
-    }
+    emit_row(row, q.W, a, i, offsets[cell], lane, out);
 }
 
 }  // namespace cfpq
