@@ -184,26 +184,40 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
         for (int a = lane; a < q.n_nt; a += 32) st->dirty[a] = 1u;
     }
     if (!grid_barrier(ctl)) return;
-    // 2) matrix initialisation of the new queries (chunks of edges, then of eps pairs)
+    // 2) matrix initialisation of the new queries (chunks of edges, then of eps pairs); the new
+    // pairs are counted per non-terminal in the warp's shared table and added to the query's
+    // counts once per chunk (not one global atomic per pair on the same few addresses)
+    __shared__ unsigned s_seed_cnt[256 / 32][kMaxNT];
+    unsigned *wcnt = s_seed_cnt[threadIdx.x >> 5];
     for (unsigned long long it = gwarp; it < ctl->seed_total; it += gwarps) {
         const int j = find_query<&BatchQuery::seed_off>(bq, k, it);
         const QDesc &q = bq[j].q;
         const unsigned long long items = q.n_edges + (unsigned long long)q.n_eps * q.n;
         const unsigned long long lo = (it - bq[j].seed_off) * kSeedChunk;
         const unsigned long long hi = min(items, lo + kSeedChunk);
+        for (int a = lane; a < q.n_nt; a += 32) wcnt[a] = 0u;
+        __syncwarp();
         unsigned long long cnt = 0;
         for (unsigned long long e = lo + lane; e < hi; e += 32) {
             if (e < q.n_edges) {
                 const cfpq_edge ed = q.edges[e];
                 for (int u = 0; u < q.n_unary; u++)
-                    if (q.unary[u].y == ed.label) seed_pair(q, q.unary[u].x, ed.src, ed.dst, &cnt);
+                    if (q.unary[u].y == ed.label) seed_pair(q, q.unary[u].x, ed.src, ed.dst, &cnt, wcnt);
             } else {
                 const unsigned long long t = e - q.n_edges;
                 const uint32_t m = (uint32_t)(t % q.n);
-                seed_pair(q, q.eps[t / q.n], m, m, &cnt);
+                seed_pair(q, q.eps[t / q.n], m, m, &cnt, wcnt);
             }
         }
-        if (cnt) atomicAdd(&q.st->seed_bits, cnt);
+        __syncwarp();
+        for (int a = lane; a < q.n_nt; a += 32)
+            if (wcnt[a]) {
+                atomicAdd(&q.st->dcount[0][a], (unsigned long long)wcnt[a]);
+                atomicAdd(&q.st->tcount[a], (unsigned long long)wcnt[a]);
+            }
+        const unsigned wsum = __reduce_add_sync(0xffffffffu, (unsigned)cnt);
+        if (lane == 0 && wsum) atomicAdd(&q.st->seed_bits, (unsigned long long)wsum);
+        __syncwarp();  // the table is reset by the next item only after every lane has read it
     }
     if (!grid_barrier(ctl)) return;
     if (blockIdx.x == 0) build_tables(ctl, bq, 0);

@@ -162,13 +162,18 @@ __device__ inline void seed_query(const QDesc &q, uint64_t tid, uint64_t nthread
         const uint32_t m = (uint32_t)(t % q.n);
         seed_pair(q, a, m, m, &cnt, s_cnt);
     }
-    if (cnt) atomicAdd(&q.st->seed_bits, cnt);
+    (void)cnt;  // the block's new pairs are the sum of s_cnt
     __syncthreads();
     for (int a = threadIdx.x; a < q.n_nt; a += blockDim.x)
         if (s_cnt[a]) {
             atomicAdd(&q.st->dcount[0][a], (unsigned long long)s_cnt[a]);
             atomicAdd(&q.st->tcount[a], (unsigned long long)s_cnt[a]);
         }
+    if (threadIdx.x == 0) {  // one update of the seed total per block, not one per thread
+        unsigned long long total = 0;
+        for (int a = 0; a < q.n_nt; a++) total += s_cnt[a];
+        if (total) atomicAdd(&q.st->seed_bits, total);
+    }
 }
 
 // ------------------------------------------------------------------------------------
