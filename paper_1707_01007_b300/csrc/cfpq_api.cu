@@ -94,11 +94,27 @@ __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDe
         for (int g = 0; g < q.n_groups; g++)
             if (!((tensor_groups >> g) & 1ull))
                 atomicAdd(&q.st->gather_products, (unsigned long long)(q.gstart[g + 1] - q.gstart[g]));
+    // new pairs per non-terminal, gathered per block and added to the counts once per block
+    // (the items' counts all go to the same few addresses)
+    __shared__ unsigned long long s_new[kMaxNT];
+    for (int a = threadIdx.x; a < q.n_nt; a += blockDim.x) s_new[a] = 0ull;
+    __syncthreads();
     for (uint64_t w = gwarp; w < len; w += gwarps) {
         const uint32_t e = list[w];
         const int g = (int)(e >> 22);
         if ((tensor_groups >> g) & 1ull) continue;
-        gather_row_chunk<CPL>(q, g, e & 0x1FFFFu, (e >> 17) & 31u, lane, parity);
+        gather_row_chunk<CPL>(q, g, e & 0x1FFFFu, (e >> 17) & 31u, lane, parity, s_new);
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < q.n_nt; a += blockDim.x) {
+        const unsigned long long v = s_new[a];
+        if (!v) continue;
+        atomicAdd(&q.st->dcount[parity ^ 1u][a], v);
+        atomicAdd(&q.st->tcount[a], v);
+        atomicAdd(&q.st->new_bits, v);
+        q.st->changed = 1u;
+        q.st->dirty[a] = 1u;
+        q.st->odirty[a] = 1u;
     }
 }
 

@@ -229,9 +229,12 @@ __device__ __forceinline__ void or_rows_for_bits(uint32_t (&acc)[CPL], uint32_t 
     }
 }
 
+// blk_new != NULL: the new pairs are added to blk_new[A] (the calling block's shared table,
+// which the caller flushes into the counts and flags once per block); NULL: straight into the
+// device-side counts and flags.
 template <int CPL>
 __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint32_t ch, int lane,
-                                        uint32_t parity) {
+                                        uint32_t parity, unsigned long long *blk_new = nullptr) {
     const uint32_t W = q.W;
     const uint64_t plane = q.plane;
     const uint32_t *D = parity ? q.X1 : q.X0;
@@ -348,12 +351,16 @@ __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint3
     if (any && lane == 0) {
         atomicOr(&NR[(uint64_t)A * W + (i >> 5)], 1u << (i & 31));
         if (inplace) atomicOr(&q.Trow[(uint64_t)A * W + (i >> 5)], 1u << (i & 31));
-        atomicAdd(&q.st->dcount[parity ^ 1u][A], (unsigned long long)cnt);
-        atomicAdd(&q.st->tcount[A], (unsigned long long)cnt);
-        atomicAdd(&q.st->new_bits, (unsigned long long)cnt);
-        q.st->changed = 1u;
-        q.st->dirty[A] = 1u;
-        q.st->odirty[A] = 1u;
+        if (blk_new) {
+            atomicAdd(&blk_new[A], (unsigned long long)cnt);
+        } else {
+            atomicAdd(&q.st->dcount[parity ^ 1u][A], (unsigned long long)cnt);
+            atomicAdd(&q.st->tcount[A], (unsigned long long)cnt);
+            atomicAdd(&q.st->new_bits, (unsigned long long)cnt);
+            q.st->changed = 1u;
+            q.st->dirty[A] = 1u;
+            q.st->odirty[A] = 1u;
+        }
     }
 }
 
