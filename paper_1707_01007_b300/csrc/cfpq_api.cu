@@ -364,27 +364,44 @@ __global__ void k_count_rows(const QDesc *qd, int a, uint32_t *counts) {
 }
 
 // one block of 1024 threads
+// Inclusive prefix sum of one value per thread over a block of 1024 threads: a shuffle scan
+// in each warp, then one over the 32 warp totals (ws: 32 shared words), two barriers in all.
+__device__ __forceinline__ unsigned long long block_inclusive_scan(unsigned long long x, unsigned long long *ws) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long t = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    return x + (w > 0 ? ws[w - 1] : 0ull);
+}
+
 __global__ void __launch_bounds__(1024) k_scan(const uint32_t *counts, uint64_t *offsets, uint32_t n,
                                                unsigned long long *total) {
-    __shared__ unsigned long long part[1024];
+    __shared__ unsigned long long ws[32];
     const uint32_t per = (n + 1023) / 1024;
     const uint32_t lo = threadIdx.x * per, hi = min(n, lo + per);
     unsigned long long s = 0;
     for (uint32_t i = lo; i < hi; i++) s += counts[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const unsigned long long v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0ull;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    unsigned long long run = part[threadIdx.x] - s;  // exclusive prefix of this segment
+    const unsigned long long incl = block_inclusive_scan(s, ws);
+    unsigned long long run = incl - s;  // exclusive prefix of this segment
     for (uint32_t i = lo; i < hi; i++) {
         offsets[i] = run;
         run += counts[i];
     }
-    if (threadIdx.x == 1023) *total = part[1023];
+    if (threadIdx.x == 1023) *total = incl;
 }
 
 __global__ void k_emit(const QDesc *qd, int a, const uint64_t *offsets, const uint32_t *counts,
@@ -436,41 +453,27 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const uint32_t *counts, ui
 
 // pass 2 (one block): exclusive scan of the block sums; bsum[nb] = total
 __global__ void __launch_bounds__(1024) k_scan_bsums(unsigned long long *bsum, int nb, unsigned long long *total) {
-    __shared__ unsigned long long v[1024];
+    __shared__ unsigned long long ws[32];
     const int t = threadIdx.x;
     const unsigned long long mine = t < nb ? bsum[t] : 0ull;
-    v[t] = mine;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const unsigned long long x = t >= off ? v[t - off] : 0ull;
-        __syncthreads();
-        v[t] += x;
-        __syncthreads();
-    }
-    if (t < nb) bsum[t] = v[t] - mine;
+    const unsigned long long incl = block_inclusive_scan(mine, ws);
+    if (t < nb) bsum[t] = incl - mine;
     if (t == 1023) {
-        bsum[nb] = v[1023];
-        *total = v[1023];
+        bsum[nb] = incl;
+        *total = incl;
     }
 }
 
 // pass 3: offsets inside each block's segment (each thread a contiguous run of 8 cells)
 __global__ void __launch_bounds__(1024) k_scan_apply(const uint32_t *counts, uint64_t n, const unsigned long long *bsum,
                                                      uint64_t *offsets) {
-    __shared__ unsigned long long v[1024];
+    __shared__ unsigned long long ws[32];
     const int t = threadIdx.x;
     const uint64_t lo = (uint64_t)blockIdx.x * kScanSeg + (uint64_t)t * (kScanSeg / 1024);
     unsigned long long s = 0;
     for (uint64_t i = lo; i < min(n, lo + kScanSeg / 1024); i++) s += counts[i];
-    v[t] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const unsigned long long x = t >= off ? v[t - off] : 0ull;
-        __syncthreads();
-        v[t] += x;
-        __syncthreads();
-    }
-    unsigned long long run = bsum[blockIdx.x] + v[t] - s;
+    const unsigned long long incl = block_inclusive_scan(s, ws);
+    unsigned long long run = bsum[blockIdx.x] + incl - s;
     for (uint64_t i = lo; i < min(n, lo + kScanSeg / 1024); i++) {
         offsets[i] = run;
         run += counts[i];
