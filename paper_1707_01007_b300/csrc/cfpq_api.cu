@@ -176,21 +176,28 @@ __global__ void __launch_bounds__(256) k_merge(const QDesc *qd) {
 }
 
 // Start of a solve on a context whose last solve converged: zeroes the rows of T that its row
-// bitmap flags (every other row of T, and both delta planes, are zero already). One block per
-// (non-terminal, row word of 32 rows).
+// bitmap flags (every other row of T, and both delta planes, are zero already), and their
+// summary words. One block per (non-terminal, row word of 32 rows); the k-th flagged row goes
+// to warp k % 4, which zeroes it with 16-byte stores (W is a multiple of 8, SW of 4).
 __global__ void __launch_bounds__(128) k_clear_t_rows(const QDesc *qd) {
     const QDesc &q = *qd;
     const uint32_t rw = (q.n + 31u) / 32u;
     const int a = (int)(blockIdx.x / rw);
     const uint32_t wq = blockIdx.x % rw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t rows = __ldcg(q.Trow + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
-    uint32_t *T = q.T + (uint64_t)a * q.plane;
-    while (rows) {
+    uint4 *T = reinterpret_cast<uint4 *>(q.T + (uint64_t)a * q.plane);
+    const uint32_t W4 = q.W / 4u, SW4 = q.SW / 4u;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int k = 0; rows; k++) {
         const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
         rows &= rows - 1;
-        for (uint32_t w = threadIdx.x; w < q.W; w += blockDim.x) T[i * q.W + w] = 0u;
-        if (q.Tsum)
-            for (uint32_t w = threadIdx.x; w < q.SW; w += blockDim.x) q.Tsum[((uint64_t)a * q.n_pad + i) * q.SW + w] = 0u;
+        if ((k & 3) != warp) continue;
+        for (uint32_t w = (uint32_t)lane; w < W4; w += 32u) T[i * W4 + w] = z;
+        if (q.Tsum) {
+            uint4 *sum = reinterpret_cast<uint4 *>(q.Tsum + ((uint64_t)a * q.n_pad + i) * q.SW);
+            for (uint32_t w = (uint32_t)lane; w < SW4; w += 32u) sum[w] = z;
+        }
     }
 }
 
