@@ -43,6 +43,22 @@ def test_dense_closure_picks_tensor(n, use_graph):
 
 
 @pytest.mark.parametrize("use_graph", [True, False])
+def test_tensor_and_gather_groups_in_one_execution(use_graph):
+    # two independent closures: S over a dense random relation (its early executions take the
+    # tensor cores) and A over a short chain (its deltas stay tiny: always the gather), so the
+    # same executions run both kinds; the gather must still do A's listed items while it skips
+    # S's
+    n = 1100
+    dense = synth.random_graph(n, int(1.6 * n), 1, seed=7).edges
+    chain = np.array([[i, 1, i + 1] for i in range(40, 52)], dtype=np.int64)
+    graph = synth.Graph(n=n, edges=np.concatenate([dense, chain]), labels=["t0", "t1"], meta={"kind": "test"})
+    text = "S S S\nS t0\nA A A\nA t1\n"
+    _, q, s = auto_parity(graph, text, use_graph=use_graph)
+    assert s["tensor_products"] > 0 and s["gather_products"] > 0
+    products_each_once(s, text, graph)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
 def test_sparse_hierarchy_mixed(use_graph):
     graph = synth.hierarchy(4096, 1200, seed=4)
     _, q, s = auto_parity(graph, synth.GRAMMAR_Q1, use_graph=use_graph)
