@@ -449,17 +449,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t s_end = 0, tiles_done = 0;
         uint32_t sn = grp;                          // this group's next K stage (counted over the CTA's tiles)
         uint32_t us = grp % UST, uph = 0;           // its unpacked ring slot and phase: sn % UST, (sn / UST) & 1
-        for (uint32_t ord = 0;; ord++) {  // ord: this CTA's ord-th tile (t is the thread's B row)
-            const uint32_t i = read_tile(ord);
-            if (i == kNoTile) break;
-            const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
-            uint32_t m0, n0;
-            tile_origin(q, e.x, m0, n0);
-            s_end += e.y;
-            for (; sn < s_end; sn += UNPACK_GROUPS) {
+        // this group's stages below limit; false if a wait gave up
+        auto unpack_until = [&](uint32_t limit) -> bool {
+            for (; sn < limit; sn += UNPACK_GROUPS) {
                 const uint32_t ps = sn % PST, pph = (sn / PST) & 1u;
-                if (!mbar_wait(&S.full_p[ps], pph, err)) break;
-                if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) break;
+                if (!mbar_wait(&S.full_p[ps], pph, err)) return false;
+                if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) return false;
                 tc_fence_after();
                 const uint2 pa = reinterpret_cast<const uint2 *>(S.a_pack[ps])[2 * arow + half];
                 const uint4 pb = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
@@ -476,7 +471,30 @@ __global__ void __launch_bounds__(THREADS, 1)
                     uph ^= 1u;
                 }
             }
-            const bool ok = !*err && mbar_wait(&S.acc_full, tiles_done & 1u, err);
+            return true;
+        };
+        uint32_t ord = 0;  // this CTA's ord-th tile (t is the thread's B row)
+        uint32_t i = read_tile(0);
+        uint32_t m0 = 0, n0 = 0;
+        if (i != kNoTile) {
+            const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
+            tile_origin(q, e.x, m0, n0);
+            s_end = e.y;
+        }
+        while (i != kNoTile) {
+            bool fine = unpack_until(s_end);
+            // the next tile's first stages (at most UST: their ring slots are freed by this
+            // tile's own MMAs, which wait for nothing else) are unpacked before this tile's
+            // epilogue, so that its MMAs can start as soon as the accumulator is handed back
+            const uint32_t i2 = fine ? read_tile(ord + 1) : kNoTile;
+            uint32_t m2 = 0, n2 = 0, s_end2 = s_end;
+            if (i2 != kNoTile) {
+                const uint2 e2 = list ? list[i2] : make_uint2(i2, dense_steps);
+                tile_origin(q, e2.x, m2, n2);
+                s_end2 = s_end + e2.y;
+                fine = unpack_until(min(s_end2, s_end + (uint32_t)UST));
+            }
+            const bool ok = fine && !*err && mbar_wait(&S.acc_full, tiles_done & 1u, err);
             tc_fence_after();
             const uint32_t row = m0 + quad * 32 + lane;
             unsigned cnt = 0;
@@ -519,6 +537,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_arrive(&S.acc_empty);  // the accumulator may be overwritten by the next tile
             tiles_done++;
             if (!ok) break;
+            i = i2;
+            m0 = m2;
+            n0 = n2;
+            s_end = s_end2;
+            ord++;
         }
     }
     tc_fence_before();
