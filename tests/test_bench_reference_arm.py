@@ -1,7 +1,8 @@
-"""The reference arm of bench.py: the CPU oracle timed on the engine line's workload. It prints
-one JSON line with the engine line's metric, unit and workload, its own CPU baseline and
-end-to-end keys (no host-device copies); under a multi-rank launch only rank 0 runs and
-prints. Runs on the CPU (about a second)."""
+"""Host-side parts of bench.py, on the CPU. The reference arm (the CPU oracle timed on the
+engine line's workload) prints one JSON line with the engine line's metric, unit and workload,
+its own CPU baseline and end-to-end keys (no host-device copies); under a multi-rank launch
+only rank 0 runs and prints (about a second). The roofline's DRAM traffic is read from the
+committed ncu summary only while the kernel source matches the one profiled."""
 import json
 import os
 import subprocess
@@ -41,3 +42,23 @@ def test_reference_arm_prints_the_engine_lines_metric_and_workload():
 
 def test_reference_arm_other_ranks_do_no_work():
     assert run_reference(1) == []
+
+
+def test_traffic_is_reported_only_for_the_profiled_kernel_source(tmp_path, monkeypatch):
+    # the bench line's DRAM traffic per launch comes from the committed ncu summary, and only
+    # while the tensor kernel's source is the one the counters were taken from
+    import hashlib
+
+    src = tmp_path / "kernel.cu"
+    src.write_text("// kernel source\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "profile.txt"
+    prof.write_text(f"dram_bytes_per_launch_avg: 1234\ndram_bytes_per_launch_skip_avg: 56\nsource_sha256: {sha}\n")
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(prof))
+    monkeypatch.setattr(bench, "TC_SOURCE", str(src))
+    assert bench.tc_traffic_per_launch(True) == 1234.0
+    assert bench.tc_traffic_per_launch(False) == 56.0
+    src.write_text("// kernel source, changed\n")
+    assert bench.tc_traffic_per_launch(True) is None
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.txt"))
+    assert bench.tc_traffic_per_launch(True) is None
