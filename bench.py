@@ -17,8 +17,15 @@ time. `value` is device-timed (CUDA events on the launching stream, inputs resid
 HBM); `e2e` is the same metric through the C ABI with host buffers (edge upload, solve,
 triples copied back) inside the timed region.
 
+Every relation of the timed leg is compared with the CPU oracle's (`parity`; a mismatch
+ends the run with exit status 3). Beside the main workload the line carries the default
+path of cfpq_solve (`default_path`: its time, roofline and e2e) and the other workload
+configurations (`configs`): Query 1 on n = 1024 hierarchies (seeds 0-4), the two-cycle
+closure (n = 8190), 256 batched queries in one grouped launch, and the served Poisson
+stream at two loads over three arrival draws.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--path tensor|auto|gather]
-                    [--schedule jacobi|inplace]
+                    [--schedule jacobi|inplace] [--no-configs] [--no-alternatives]
     python bench.py --impl reference ...      # the CPU oracle on the same workload
 """
 from __future__ import annotations
@@ -58,6 +65,9 @@ def parse():
                          "only the K steps whose operand tiles are both non-zero")
     ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the other workload configurations (n = 1024 seeds, two cycles, 256 batched "
+                         "queries, served stream) that the default line reports beside the main workload")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="hier16k",
                     choices=["hier16k", "sg16k", "batch256", "serve", "cycles", "lengths16k"],
@@ -184,6 +194,24 @@ def oracle_work(graph, grammars):
     return total
 
 
+def check_against_oracle(graph, grammars, engine_pairs):
+    """Every relation the engine computed on the workload against the oracle's, element by
+    element; a mismatch ends the run (exit status 3) instead of printing a number."""
+    refs = oracle_step(graph, grammars)
+    rel = pairs = 0
+    for (label, _), ref, got in zip(grammars, refs, engine_pairs):
+        for nm, arr in got.items():
+            exp = ref.pairs(nm)
+            if arr.shape != exp.shape or not np.array_equal(arr, exp):
+                print(f"bench: {label} R_{nm} differs from the oracle ({arr.shape[0]} vs {exp.shape[0]} pairs)",
+                      file=sys.stderr)
+                sys.exit(3)
+            rel += 1
+            pairs += int(exp.shape[0])
+    return {"reference": "oracle (Hellings worklist on the CPU)", "relations_compared": rel,
+            "pairs_compared": pairs, "equal": True}
+
+
 def reference_arm(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
@@ -237,7 +265,20 @@ def tc_traffic_per_launch(dense=True):
         return None
 
 
-def roofline(eng, graph, gs, path, schedule, stream, dense=True):
+FP8_OPS_PER_CLK_SM = 16384  # dense tcgen05 kind::f8f6f4: 2 x 8192 multiply-adds per clock and SM
+
+
+def nominal_fp8_tflops(sm_mhz):
+    """The dense FP8 tensor rate of this device at an SM clock (SMs x ops per clock x clock)."""
+    import torch
+
+    if not sm_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * FP8_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+
+
+def roofline(eng, graph, gs, path, schedule, stream, dense=True, sm_mhz=None):
     """Dominant product kernel: every product launch of a solve with the timed options is
     bracketed by CUDA events on the launching stream (profile mode); algorithmic work per
     launch is 2 n^3 per production of the group (tensor; with tile skipping, the K steps the
@@ -264,6 +305,7 @@ def roofline(eng, graph, gs, path, schedule, stream, dense=True):
         sustained = 2.0 * peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         # the integer tensor references of this device (sm_103a has no 8-bit integer tcgen05 kind)
         mma = eng.measure_mma_sync_peaks()
+        nominal = nominal_fp8_tflops(sm_mhz)
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": tc_traffic_per_launch(dense), "kernel": "k_tc_bool_gemm",
                 "tile_skipping": not dense, "launches": tens_l,
@@ -271,6 +313,10 @@ def roofline(eng, graph, gs, path, schedule, stream, dense=True):
                 "peak_note": f"{kind} bf16 dense burst x 2 (fp8 e4m3 : bf16 nominal ratio); "
                              f"frac against the sustained figure x 2: {achieved / sustained:.3f}",
                 "useful_ops_per_step": useful,
+                "nominal_fp8_at_clock": {"peak": nominal, "sm_mhz": sm_mhz,
+                                         "frac": (achieved / nominal) if nominal else None,
+                                         "note": "SMs x 16384 dense FP8 ops per clock x the median SM clock "
+                                                 "sampled during the timed region"},
                 "int_tensor_refs": {"mma_sync_s8_tops": mma["s8_tops"], "frac_of_mma_sync_s8": achieved / mma["s8_tops"],
                                     "mma_sync_b1_tops": mma["b1_tops"],
                                     "frac_of_mma_sync_b1": achieved / mma["b1_tops"],
@@ -371,7 +417,10 @@ def engine_arm(args):
     value = job_rate(ops_per_step, ms / 1e3, world) / 1e9
     executed_dense = sum(s["dense_ops"] for s in st)
     results = {f"{label}:{g.names[0]}": q.count(g.names[0]) for (label, _), g, q in zip(grammars, gs, main.qs)}
+    # every relation of the timed leg, for the check against the oracle below
+    timed_pairs = [{nm: q.get(nm) for nm in g.names} for g, q in zip(gs, main.qs)]
     main.close()
+    parity = check_against_oracle(graph, grammars, timed_pairs)
 
     # the same closure with the other schedules / product paths (exact results in all)
     alternatives = {}
@@ -414,7 +463,31 @@ def engine_arm(args):
     e2e_s = max_over_ranks(e2e_s)
     e2e_val = job_rate(ops_per_step, e2e_s, world) / 1e9
 
-    roof = roofline(eng, graph, gs, path, schedule, stream, dense)
+    roof = roofline(eng, graph, gs, path, schedule, stream, dense, sm_mhz=clk.get("sm_mhz"))
+
+    # the default path of cfpq_solve (automatic product choice, in-place schedule): its
+    # dominant kernels' roofline and its own end-to-end figure
+    default_path = None
+    if not args.no_alternatives:
+        droof = roofline(eng, graph, gs, eng.PATH_AUTO, eng.SCHED_INPLACE, stream, dense=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_d2h = 0
+        for _ in range(e2e_steps):
+            d_d2h = 0
+            for g in gs:
+                q = eng.Query(g, graph.n, graph.edges, timeout_s=300.0)
+                q.solve()
+                d_d2h += q.triples_all().shape[0] * 12
+                q.close()
+        de2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+        auto = alternatives.get("auto_inplace", {})
+        default_path = {"options": "path auto, schedule in-place, tile skipping (the cfpq_solve defaults)",
+                        "ms_per_step": auto.get("ms_per_step"), "value": auto.get("value"), "unit": "GOPS",
+                        "roofline": droof,
+                        "e2e": {"value": job_rate(ops_per_step, de2e_s, world) / 1e9, "unit": "GOPS",
+                                "ms_per_step": de2e_s * 1e3, "h2d_bytes_per_step": h2d,
+                                "d2h_bytes_per_step": d_d2h}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
@@ -433,8 +506,13 @@ def engine_arm(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "roofline": roof,
+        "parity": parity,
+        "headline": "Algorithm 1 with every Boolean product on the tcgen05 tensor cores (dense products: the "
+                    "work the metric counts is executed); the default path's figure is under default_path",
         "alternatives": alternatives,
     }
+    if default_path:
+        line["default_path"] = default_path
     if roof.get("useful_ops_per_step"):
         # Boolean ops whose operands are both 1 (sum_k nnz(col k of T_B) nnz(row k of T_C) per
         # product, counted in profile mode on the same closure), beside the dense count
@@ -452,6 +530,17 @@ def engine_arm(args):
         per = (time.perf_counter() - t0) / reps
         line["cpu_baseline"] = {"value": ops_per_step / per / 1e9, "unit": "GOPS", "cores": 1, "kind": "oracle",
                                 "sample": f"full workload x{reps} ({per * 1e3:.0f} ms per step), one host thread"}
+        cpu_v = line["cpu_baseline"]["value"]
+        line["vs_cpu_baseline"] = {"value": value / cpu_v, "e2e": e2e_val / cpu_v,
+                                   "default_path": (default_path["value"] / cpu_v) if default_path else None,
+                                   "default_path_e2e": (default_path["e2e"]["value"] / cpu_v) if default_path else None}
+    if rank == 0 and world == 1 and not args.no_configs:
+        line["configs"] = {
+            "n1024_seeds": small_hierarchy_measure(eng, torch),
+            "two_cycles": cycles_measure(eng, torch, 4096, 3, 1, cpu=not args.no_cpu_baseline),
+            "batch256": batch_measure(eng, torch, 5, 3),
+            "serve": serve_measure(eng),
+        }
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -461,15 +550,11 @@ def engine_arm(args):
 
 # ------------------------------------------------------------------------------------ batched / served
 
-def batch_arm(args):
+def batch_measure(eng, torch, steps, warmup):
     """256 independent hierarchy queries (n log-uniform in [64, 4096], class fraction 0.3,
-    grammar Q1 or sc-only uniformly, seed 0): one grouped persistent launch vs the same
-    queries solved one at a time with the single-query path."""
-    import torch
-
-    import paper_1707_01007_b300 as eng
-
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    grammar Q1 or sc-only uniformly, seed 0): one grouped persistent launch (built-in and
+    autotuned launch configuration) vs the same queries solved one at a time with the
+    single-query path."""
     work = synth.batch_queries(256, 64, 4096, 0.3, seed=0)
     gs = [eng.Grammar(t, g.labels) for g, t in work]
     qs = [eng.Query(gr, g.n, g.edges, path=eng.PATH_GATHER, schedule=eng.SCHED_AUTO) for (g, _), gr in zip(work, gs)]
@@ -486,14 +571,14 @@ def batch_arm(args):
         return e0.elapsed_time(e1) / reps
 
     default = eng.batch_tuning_default()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         eng.solve_batch(qs, stream, tuning=default)
-    ms_default = timed(lambda: eng.solve_batch(qs, stream, tuning=default), args.steps)
+    ms_default = timed(lambda: eng.solve_batch(qs, stream, tuning=default), steps)
     # the autotuner times candidate launch configurations on this batch and installs the best
     best, report = eng.autotune_batch(qs, stream)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         eng.solve_batch(qs, stream)
-    ms_batch = timed(lambda: eng.solve_batch(qs, stream), args.steps)
+    ms_batch = timed(lambda: eng.solve_batch(qs, stream), steps)
     phases = eng.batch_last_profile()
     # bytes the products phase moves: the same batch once more with word counting on
     # (profile mode: scanned left rows, gathered right-row chunks, merged result chunks)
@@ -501,20 +586,21 @@ def batch_arm(args):
                for (g, _), gr in zip(work, gs)]
     eng.solve_batch(prof_qs, stream)
     product_bytes = sum(q.stats()["product_bytes"] for q in prof_qs)
-    del prof_qs
+    for q in prof_qs:
+        q.close()
 
     def serial():
         for q in qs:
             q.solve(stream)
     serial()
-    ms_serial = timed(serial, max(1, min(args.steps, 3)))
-    line = {"metric": "queries/s, 256 batched hierarchy queries (closure to fixpoint)",
-            "value": 256 / (ms_batch / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
-            "config": {"workload": "256 hierarchy queries, n log-uniform [64, 4096], class fraction 0.3, "
-                                   "Q1 or sc-only uniformly, seed 0", "path": "gather (grouped launch)",
-                       "launch_config": "autotuned on this batch (grid, tile width per size class, schedule)"},
+    ms_serial = timed(serial, max(1, min(steps, 3)))
+    for q in qs:
+        q.close()
+    return {"queries_per_s": 256 / (ms_batch / 1e3), "ms_per_batch": ms_batch,
+            "workload": "256 hierarchy queries, n log-uniform [64, 4096], class fraction 0.3, "
+                        "Q1 or sc-only uniformly, seed 0",
+            "path": "gather (grouped launch)",
+            "launch_config": "autotuned on this batch (grid, tile width per size class, schedule)",
             "serial_ms": ms_serial, "serial_queries_per_s": 256 / (ms_serial / 1e3),
             "speedup_vs_serial": ms_serial / ms_batch,
             "built_in_config_ms": ms_default, "tuned_config": best.as_dict(), "tuner": report,
@@ -522,21 +608,35 @@ def batch_arm(args):
                              ([round(x, 3) for x in v] if isinstance(v, list) else v)) for k, v in phases.items()},
             "products_phase": {"bytes": product_bytes,
                                "gbs": product_bytes / (phases["products"] * 1e6) if phases["products"] else None}}
+
+
+def batch_arm(args):
+    import torch
+
+    import paper_1707_01007_b300 as eng
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    b = batch_measure(eng, torch, args.steps, args.warmup)
+    line = {"metric": "queries/s, 256 batched hierarchy queries (closure to fixpoint)",
+            "value": b["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
+            "config": {"workload": b["workload"], "path": b["path"], "launch_config": b["launch_config"]}}
+    line.update({k: v for k, v in b.items() if k not in ("workload", "path", "launch_config")})
     print(json.dumps(line))
     return 0
 
 
-def serve_arm(args):
-    """Poisson stream of 2000 hierarchy queries (n log-uniform in [128, 32768], both grammars)
-    plus one n = 65536 Query 1 query, at 0.7x and 1.5x the measured serial throughput: the
-    continuous-batching server against serial FIFO solves of the same stream."""
-    import torch
+SERVE_ARRIVAL_SEEDS = (17, 18, 19)
 
-    import paper_1707_01007_b300 as eng
+
+def serve_measure(eng, count=2000, seeds=SERVE_ARRIVAL_SEEDS):
+    """Poisson stream of `count` hierarchy queries (n log-uniform in [128, 32768], both
+    grammars) plus one n = 65536 Query 1 query, at 0.7x and 1.5x the measured serial
+    throughput: the continuous-batching server against serial FIFO solves of the same stream,
+    one run per arrival draw (seeds), with the spread of p50 / p99 over the draws."""
     from paper_1707_01007_b300 import serve
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    count = 2000 if args.n is None else args.n
     work = synth.batch_queries(count, 128, 32768, 0.3, seed=5)
     big = synth.hierarchy(65536, round(65536 * 0.3), seed=5)
     work = work[: count // 2] + [(big, synth.GRAMMAR_Q1)] + work[count // 2:]
@@ -545,74 +645,150 @@ def serve_arm(args):
     probe = queries[:200]
     sp = serve.run_serial(probe, np.zeros(len(probe)))
     thr = sp["queries_per_s"]
-    out = {"serial_probe_queries_per_s": thr}
+    out = {"workload": f"{len(queries)} hierarchy queries, n log-uniform [128, 32768] + one n=65536 Q1, "
+                       "Poisson arrivals at 0.7x and 1.5x serial throughput",
+           "serial_probe_queries_per_s": thr, "arrival_seeds": list(seeds), "rounds_per_step": 8}
     for load in (0.7, 1.5):
-        arr = synth.poisson_arrivals(len(queries), rate_per_s=load * thr, seed=17)
-        srv = eng.Server(rounds_per_step=8)
-        s_sum, _ = serve.run_server(srv, queries, arr)
-        stats = srv.stats()
-        srv.close()
-        f_sum = serve.run_serial(queries, arr)
-        out[f"load_{load}"] = {"server": s_sum, "serial_fifo": f_sum, "server_launches": stats["launches"],
-                               "peak_hbm_bytes": stats["peak_used_bytes"], "budget_bytes": stats["budget_bytes"]}
+        runs = []
+        for sd in seeds:
+            arr = synth.poisson_arrivals(len(queries), rate_per_s=load * thr, seed=sd)
+            srv = eng.Server(rounds_per_step=8)
+            s_sum, _ = serve.run_server(srv, queries, arr)
+            stats = srv.stats()
+            srv.close()
+            f_sum = serve.run_serial(queries, arr)
+            runs.append({"seed": sd, "server": s_sum, "serial_fifo": f_sum, "server_launches": stats["launches"],
+                         "peak_hbm_bytes": stats["peak_used_bytes"], "budget_bytes": stats["budget_bytes"]})
+
+        def spread(who, key):
+            v = [r[who][key] for r in runs]
+            return {"mean": float(np.mean(v)), "min": float(min(v)), "max": float(max(v))}
+        out[f"load_{load}"] = {
+            "runs": runs,
+            "server": {k: spread("server", k) for k in ("queries_per_s", "p50_ms", "p99_ms", "mean_ms")},
+            "serial_fifo": {k: spread("serial_fifo", k) for k in ("queries_per_s", "p50_ms", "p99_ms", "mean_ms")}}
+    return out
+
+
+def serve_arm(args):
+    import torch
+
+    import paper_1707_01007_b300 as eng
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    out = serve_measure(eng, count=2000 if args.n is None else args.n)
     top = out["load_1.5"]["server"]
-    line = {"metric": "queries/s and p50/p99 latency, served Poisson stream", "value": top["queries_per_s"],
-            "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
-            "config": {"workload": f"{len(queries)} hierarchy queries, n log-uniform [128, 32768] + one n=65536 Q1, "
-                                   "Poisson arrivals at 0.7x and 1.5x serial throughput", "rounds_per_step": 8},
-            "detail": out}
+    line = {"metric": "queries/s and p50/p99 latency, served Poisson stream", "value": top["queries_per_s"]["mean"],
+            "unit": "queries/s", "n_gpus": 1, "steps": len(SERVE_ARRIVAL_SEEDS), "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit-packed",
+            "data": "synthetic", "config": {"workload": out["workload"], "rounds_per_step": 8}, "detail": out}
     print(json.dumps(line))
     return 0
 
 
+def cycles_measure(eng, torch, p, steps, warmup, cpu=True):
+    """Two directed cycles of p and p - 1 nodes sharing node 0, S -> a S b | a b: closure by
+    the worklist path (on-device) and by the automatic path (matrix loop, then the hand-over
+    to the worklist), timed with CUDA events inside the library (solve_ms); the results are
+    checked against the closed form R_S = R_S1 = (a-cycle) x (b-cycle). The host-side set-up
+    of the worklist path (adjacency, unique-successor and period tables) runs when the context
+    is created (worklist path) or at the first hand-over (automatic path); its time is
+    reported beside the solve times."""
+    q = p - 1
+    graph = synth.two_cycles(p, q)
+    g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qy = eng.Query(g, graph.n, graph.edges, path=eng.PATH_WORKLIST, timeout_s=600.0)
+    torch.cuda.synchronize()
+    create_ms = (time.perf_counter() - t0) * 1e3
+    for _ in range(max(1, min(warmup, 1))):
+        qy.solve(stream)
+    times = []
+    for _ in range(max(1, min(steps, 3))):
+        qy.solve(stream)
+        times.append(qy.stats()["solve_ms"])
+    ok = qy.count("S") == p * q and qy.count("S1") == p * q
+    st = qy.stats()
+    ms = float(np.median(times))
+    qy.close()
+    qa = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, timeout_s=600.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    qa.solve(stream)  # the first solve builds the worklist tables at the hand-over
+    torch.cuda.synchronize()
+    first_ms = (time.perf_counter() - t0) * 1e3
+    auto_times = []
+    for _ in range(max(1, min(steps, 3))):
+        qa.solve(stream)
+        auto_times.append(qa.stats()["solve_ms"])
+    auto = {"ms": float(np.median(auto_times)), "loop_executions_before_hand_over": qa.stats()["iterations"],
+            "first_solve_wall_ms_with_host_setup": first_ms, "closed_form_count_ok": bool(qa.count("S") == p * q)}
+    qa.close()
+    out = {"workload": f"two cycles {p} / {q} sharing node 0, S -> a S b | a b (n = {graph.n})",
+           "worklist_ms": ms, "pairs_S": p * q if ok else None, "closed_form_count_ok": bool(ok),
+           "worklist_items": st["worklist_items"], "ns_per_item": ms * 1e6 / max(1, st["worklist_items"]),
+           "worklist_create_wall_ms_with_host_setup": create_ms, "automatic_path": auto}
+    if cpu:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.hellings(graph, synth.GRAMMAR_C3)
+        out["cpu_baseline"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": 1, "kind": "oracle",
+                               "sample": "full workload once, one host thread"}
+    return out
+
+
 def cycles_arm(args):
-    """Two directed cycles of 4096 and 4095 nodes sharing node 0, S -> a S b | a b: closure
-    by the worklist path (one warp, on-device), timed with CUDA events; the result is checked
-    against the closed form R_S = R_S1 = (a-cycle) x (b-cycle)."""
     import torch
 
     import paper_1707_01007_b300 as eng
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     p = args.cycle_p or 4096
-    q = p - 1
-    graph = synth.two_cycles(p, q)
-    g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
-    qy = eng.Query(g, graph.n, graph.edges, path=eng.PATH_WORKLIST, timeout_s=600.0)
-    stream = torch.cuda.current_stream()
-    for _ in range(max(1, min(args.warmup, 1))):
-        qy.solve(stream)
-    times = []
-    for _ in range(max(1, min(args.steps, 3))):
-        qy.solve(stream)
-        times.append(qy.stats()["solve_ms"])
-    ok = qy.count("S") == p * q and qy.count("S1") == p * q
-    st = qy.stats()
-    ms = float(np.median(times))
-    # the automatic path on the same input: matrix loop, then the hand-over to the worklist
-    qa = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, timeout_s=600.0)
-    qa.solve(stream)
-    auto_times = []
-    for _ in range(max(1, min(args.steps, 3))):
-        qa.solve(stream)
-        auto_times.append(qa.stats()["solve_ms"])
-    auto = {"ms": float(np.median(auto_times)), "loop_executions_before_hand_over": qa.stats()["iterations"],
-            "closed_form_count_ok": bool(qa.count("S") == p * q)}
-    line = {"metric": "two-cycle closure time (worklist path)", "value": ms / 1e3, "unit": "s", "n_gpus": 1,
-            "steps": len(times), "warmup": 1, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32 bit-packed", "data": "synthetic",
-            "config": {"workload": f"two cycles {p} / {q} sharing node 0, S -> a S b | a b (n = {graph.n})"},
-            "pairs_S": qy.count("S"), "closed_form_count_ok": bool(ok), "worklist_items": st["worklist_items"],
-            "ns_per_item": ms * 1e6 / max(1, st["worklist_items"]), "automatic_path": auto}
-    if not args.no_cpu_baseline:
-        import oracle
-        t0 = time.perf_counter()
-        oracle.hellings(graph, synth.GRAMMAR_C3)
-        line["cpu_baseline"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": 1, "kind": "oracle",
-                                "sample": "full workload once, one host thread"}
+    c = cycles_measure(eng, torch, p, args.steps, args.warmup, cpu=not args.no_cpu_baseline)
+    line = {"metric": "two-cycle closure time (worklist path)", "value": c["worklist_ms"] / 1e3, "unit": "s",
+            "n_gpus": 1, "steps": max(1, min(args.steps, 3)), "warmup": 1, "ms_per_step": c["worklist_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit-packed",
+            "data": "synthetic", "config": {"workload": c["workload"]}}
+    line.update({k: v for k, v in c.items() if k != "workload"})
     print(json.dumps(line))
     return 0
+
+
+def small_hierarchy_measure(eng, torch, seeds=range(5), reps=5):
+    """Query 1 on the hierarchy of n = 1024 nodes (300 classes), one per seed: Algorithm 1's
+    loop count, and the solve time (CUDA events inside the library, median of reps) of the
+    automatic path and of Algorithm 1 with dense tensor-core products, with the Boolean GOPS
+    of the latter (loop executions x productions x 2 n^3 / time)."""
+    n, c = 1024, 300
+    stream = torch.cuda.current_stream()
+    per = []
+    for sd in seeds:
+        graph = synth.hierarchy(n, c, seed=sd)
+        g = eng.Grammar(synth.GRAMMAR_Q1, graph.labels)
+        nprod = len({(g.cnf.contents.binary[i].lhs, g.cnf.contents.binary[i].b, g.cnf.contents.binary[i].c)
+                     for i in range(g.cnf.contents.n_binary)})
+        row = {"seed": sd}
+        for label, kw in (("auto", dict(path=eng.PATH_AUTO)),
+                          ("tensor_dense_jacobi", dict(path=eng.PATH_TENSOR, schedule=eng.SCHED_JACOBI,
+                                                       dense_tensor=True))):
+            q = eng.Query(g, graph.n, graph.edges, timeout_s=60.0, **kw)
+            q.solve(stream)
+            ts = []
+            for _ in range(reps):
+                q.solve(stream)
+                ts.append(q.stats()["solve_ms"])
+            row[label + "_ms"] = float(np.median(ts))
+            if label == "tensor_dense_jacobi":
+                row["jacobi_iterations"] = q.stats()["iterations"]
+                row["tensor_gops"] = q.stats()["iterations"] * nprod * 2.0 * n ** 3 / (row[label + "_ms"] / 1e3) / 1e9
+            row["pairs_S_" + label] = q.count("S")
+            q.close()
+        per.append(row)
+    return {"workload": "hierarchy n=1024 (300 classes), Query 1, seeds 0-4", "per_seed": per,
+            "auto_ms_median": float(np.median([r["auto_ms"] for r in per])),
+            "tensor_dense_jacobi_ms_median": float(np.median([r["tensor_dense_jacobi_ms"] for r in per]))}
 
 
 def lengths_arm(args):

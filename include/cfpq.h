@@ -158,7 +158,11 @@ typedef struct cfpq_ctx cfpq_ctx;
 int cfpq_options_default(cfpq_options *opt);
 
 /*
- * Creates a context for one query: validates and copies the grammar and the edge list,
+ * Creates a context for one query -- the inputs of Algorithm 1 (Section 4.2): the
+ * edge-labelled graph D = (V, E) with nodes 0 .. |V| - 1 and the grammar in normal form
+ * (Section 2), and the matrix T of Algorithm 1 held as one Boolean n x n matrix per
+ * non-terminal (Section 4.1: T_ij is a set of non-terminals; bit (i, j) of matrix A says
+ * A in T_ij). Validates and copies the grammar and the edge list,
  * allocates the bit-packed matrices in device memory (row-major, n_pad = n rounded up to
  * a multiple of 256, bit j of row i in 32-bit word i * n_pad/32 + j/32 at bit j % 32),
  * and uploads the edges. Uses the current CUDA device.
@@ -184,23 +188,27 @@ int cfpq_create(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, s
 int cfpq_solve(cfpq_ctx *ctx, void *stream);
 
 /*
- * Copies R_A as triples (A, m, n), sorted by (m, n), into buf (host memory). With
+ * The context-free relation R_A = {(m, n) : A in T_mn} read off the closure (Section 2's
+ * definition; Theorem 2, Section 4.1: after the loop, A in T_mn iff there is a walk from
+ * m to n whose labels A derives). Copies R_A as triples (A, m, n), sorted by (m, n), into
+ * buf (host memory). With
  * buf == NULL only *count is set (the size query). Runs on the stream of the last
  * cfpq_solve. Errors: INVALID (A out of range, count NULL), NOT_SOLVED, BUFFER (cap <
  * count; *count still set), NOMEM, CUDA.
  */
 int cfpq_get(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, size_t cap, size_t *count);
 
-/* As cfpq_get, but buf is device memory (cap triples) and nothing is copied to the host
- * except the count. Errors: as cfpq_get. */
+/* R_A as in cfpq_get (Theorem 2), but buf is device memory (cap triples) and nothing is
+ * copied to the host except the count. Errors: as cfpq_get. */
 int cfpq_get_device(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, size_t cap, size_t *count);
 
-/* Every relation at once: triples (A, m, n) sorted by (A, m, n) into buf (host memory, cap
- * triples); buf == NULL: only *count. Errors: INVALID, NOT_SOLVED, BUFFER, NOMEM, CUDA. */
+/* Every relation R_A of the closure at once (Theorem 2, Section 4.1; the worked example of
+ * Section 4.3 lists all seven): triples (A, m, n) sorted by (A, m, n) into buf (host memory,
+ * cap triples); buf == NULL: only *count. Errors: INVALID, NOT_SOLVED, BUFFER, NOMEM, CUDA. */
 int cfpq_get_all(cfpq_ctx *ctx, cfpq_triple *buf, size_t cap, size_t *count);
 
-/* As cfpq_get_all, but buf is device memory (cap triples); one host synchronisation (for the
- * count) per call. buf == NULL: only *count. Errors: as cfpq_get_all. */
+/* Every R_A as in cfpq_get_all (Theorem 2), but buf is device memory (cap triples); one host
+ * synchronisation (for the count) per call. buf == NULL: only *count. Errors: as cfpq_get_all. */
 int cfpq_get_all_device(cfpq_ctx *ctx, cfpq_triple *buf, size_t cap, size_t *count);
 
 /*
@@ -237,10 +245,13 @@ int cfpq_get_lengths(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, uint32_t *lengt
 int cfpq_get_path(cfpq_ctx *ctx, int32_t A, uint32_t m, uint32_t n, uint32_t *nodes, int32_t *labels, size_t cap,
                   size_t *len);
 
-/* |R_A| without copying pairs. Errors: as cfpq_get. */
+/* |R_A| without copying pairs (for the start symbol, the #results column of the tables of
+ * Section 6, diagonal pairs included). Errors: as cfpq_get. */
 int cfpq_count(cfpq_ctx *ctx, int32_t A, size_t *count);
 
-/* Statistics of the last cfpq_solve. Errors: INVALID. */
+/* Statistics of the last cfpq_solve: loop executions of Algorithm 1 (k of Section 4.3),
+ * pairs added, Boolean products run and their dense work (Theorem 4's BMM terms), times.
+ * Errors: INVALID. */
 int cfpq_stats_get(const cfpq_ctx *ctx, cfpq_stats *out);
 
 /* Releases the context and its device memory; NULL is ignored. */
@@ -271,6 +282,9 @@ const char *cfpq_grammar_name(const cfpq_parsed_grammar *pg, int32_t id);
 void cfpq_grammar_free(cfpq_parsed_grammar *pg);
 
 /*
+ * Algorithm 1 (Section 4.2) for many independent queries at once. The paper solves one
+ * query per call; grouping queries is this library's own, and each context still reaches
+ * its own least fixpoint (Theorem 2, Section 4.1), the result of solving it alone.
  * Batched solve (many independent queries, one persistent grouped launch): every
  * context advances one loop iteration per round; a context whose iteration added no
  * pair is retired (per-query convergence) while the others continue. Results are
@@ -435,11 +449,14 @@ void cfpq_server_destroy(cfpq_server *s);
  * stream) and returns after the work is complete.
  * The library allocates nothing for this call: its scratch is one fixed device array
  * that every GPU loading the library holds until the process exits (~768 KiB). The
- * first call on a device looks up that array's device address (with the device
- * current); make this first call before any stream capture. All calls share the array:
- * calls whose work overlaps on the GPU race and must be serialised by the caller.
+ * first call on a device (and again in a new CUDA context of that device, e.g. after a
+ * device reset) looks up that array's device address with the device current. All calls
+ * share the array: calls whose work overlaps on the GPU race and must be serialised by the
+ * caller. Every call synchronises `stream` and reads the pair count on the host, so it
+ * must never be made on a stream that is being captured into a CUDA graph: such a call is
+ * refused (INVALID) before any device work, and the capture stays intact.
  * Errors: INVALID (count NULL, bits NULL with n_rows > 0, n_rows > CFPQ_NOALLOC_MAX_ROWS,
- * n_cols > 32 * row_words), BUFFER (cap < count; *count still set), CUDA.
+ * n_cols > 32 * row_words, stream capturing), BUFFER (cap < count; *count still set), CUDA.
  */
 int cfpq_extract_pairs_noalloc(const uint32_t *bits, uint32_t n_rows, uint32_t n_cols, uint32_t row_words,
                                int32_t A, cfpq_triple *out, size_t cap, size_t *count, void *stream);

@@ -16,8 +16,16 @@
 // caller.
 //
 // In host code the array's name is only a host-side stand-in, not a device address; the
-// device address is looked up once per device with cudaGetSymbolAddress while that
-// device is current, and passed to the kernels.
+// device address is looked up with cudaGetSymbolAddress while the device is current, once
+// per device and CUDA context (a device reset, or a primary context released and created
+// again, loads the module anew and gets a new context id, so the address is looked up
+// again), and passed to the kernels.
+//
+// Every call synchronises its stream and reads the total on the host, so it cannot be
+// part of a stream capture: a call on a capturing stream is refused before any device work.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "../../include/cfpq.h"
@@ -35,6 +43,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 static unsigned char *g_dev_ptr[kMaxDevices];
+static unsigned long long g_dev_ctx[kMaxDevices];  // context id the cached address belongs to
 static std::mutex g_mu;
 
 __device__ __forceinline__ uint32_t masked_word(const uint32_t *row, uint32_t w, uint32_t n_cols) {
@@ -111,20 +120,52 @@ __global__ void k_emit(const uint32_t *bits, uint32_t n_rows, uint32_t n_cols, u
     }
 }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Unique id of the CUDA context current on this thread (cuCtxGetId), 0 if there is none yet
+// or the driver entry points are unavailable.
+static unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &qr) == cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &qr) == cudaSuccess &&
+            qr == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device: looked up once per device and
+// context (every call where the context id cannot be read).
 static int scratch_address(unsigned char **out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CFPQ_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_dev_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return CFPQ_ERR_CUDA;
-        }
-        g_dev_ptr[dev] = static_cast<unsigned char *>(p);
+    const unsigned long long ctx = current_context_id();
+    if (ctx != 0 && g_dev_ptr[dev] && g_dev_ctx[dev] == ctx) {
+        *out = g_dev_ptr[dev];
+        return CFPQ_OK;
     }
-    *out = g_dev_ptr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return CFPQ_ERR_CUDA;
+    }
+    // the look-up makes the device's primary context current if it was not yet
+    const unsigned long long ctx_now = ctx != 0 ? ctx : current_context_id();
+    g_dev_ptr[dev] = ctx_now != 0 ? static_cast<unsigned char *>(p) : nullptr;
+    g_dev_ctx[dev] = ctx_now;
+    *out = static_cast<unsigned char *>(p);
     return CFPQ_OK;
 }
 
@@ -138,6 +179,15 @@ extern "C" int cfpq_extract_pairs_noalloc(const uint32_t *bits, uint32_t n_rows,
     if (!count || (!bits && n_rows > 0)) return CFPQ_ERR_INVALID;
     if (n_rows > kMaxRows) return CFPQ_ERR_INVALID;  // beyond the fixed scratch array
     if ((uint64_t)row_words * 32u < n_cols) return CFPQ_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the call synchronises the stream: never inside a stream capture (on the legacy stream
+    // while another stream captures, the query itself reports an error: refused as well)
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap_status) != cudaSuccess) {
+        cudaGetLastError();
+        return CFPQ_ERR_INVALID;
+    }
+    if (cap_status != cudaStreamCaptureStatusNone) return CFPQ_ERR_INVALID;
     if (n_rows == 0) {
         *count = 0;
         return CFPQ_OK;
@@ -145,7 +195,6 @@ extern "C" int cfpq_extract_pairs_noalloc(const uint32_t *bits, uint32_t n_rows,
     unsigned char *scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc != CFPQ_OK) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t blocks = (uint32_t)(((uint64_t)n_rows * 32 + 255) / 256);
     k_count<<<blocks, 256, 0, s>>>(bits, n_rows, n_cols, row_words, scratch);
     k_scan<<<1, 1024, 0, s>>>(n_rows, scratch);

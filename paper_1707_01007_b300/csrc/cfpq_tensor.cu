@@ -64,6 +64,7 @@ struct __align__(1024) Smem {
     uint32_t a_pack[PST][BM * KW];
     uint32_t b_pack[PST][BN * KW];
     unsigned long long full_p[PST], empty_p[PST], full_u[UST], empty_u[UST], acc_full, acc_empty;
+    unsigned long long mma_done;  // the issuer's last commit: every MMA it issued has completed
     unsigned long long tile_full[2], tile_empty[2];  // tile skipping: claimed tile handed to the consumers
     uint32_t tile_q[2];
     uint32_t tmem_base;
@@ -304,6 +305,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mbar_init(&S.acc_full, 1);
         mbar_init(&S.acc_empty, UNPACK_THREADS);
+        mbar_init(&S.mma_done, 1);
         for (int i = 0; i < 2; i++) {
             mbar_init(&S.tile_full[i], 1);
             mbar_init(&S.tile_empty[i], 1 + UNPACK_THREADS);
@@ -425,6 +427,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
                 tiles_done++;
+            }
+            // On every exit path (a wait that gave up included) the MMAs issued so far must have
+            // completed before the tensor memory they write is released: one more commit, and a
+            // bounded wait for it that does not stop at the CTA's error flag.
+            if (s > 0) {
+                mma_commit(&S.mma_done);
+                volatile int drain_err = 0;
+                mbar_wait(&S.mma_done, 0u, &drain_err);
             }
         }
     } else {

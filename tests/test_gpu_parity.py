@@ -137,6 +137,25 @@ def test_two_cycles_jacobi_iterations(p, q):
     assert qq.stats()["iterations"] == 2 * p * q + 1
 
 
+def test_graph_loop_at_depth_two_cycles_64_63():
+    """The conditional-while graph of one solve running thousands of loop executions: two
+    cycles of 64 and 63 nodes under the Jacobi schedule need k = 2pq + 1 = 8065 executions
+    (Lemma 3: derivation height <= k), every one of them launched by the graph (no hand-over
+    to the worklist under Jacobi); gcd(64, 63) = 1, so R_S = R_S1 = (a-cycle) x (b-cycle)."""
+    p, qn = 64, 63
+    graph = synth.two_cycles(p, qn)
+    g, q = solve_engine(graph, synth.GRAMMAR_C3, schedule=eng.SCHED_JACOBI, path=eng.PATH_GATHER, use_graph=True)
+    s = q.stats()
+    assert s["iterations"] == 2 * p * qn + 1 and s["worklist_items"] == 0
+    a_nodes = np.arange(p)
+    b_nodes = np.concatenate([[0], np.arange(p, p + qn - 1)])
+    closed = np.array(sorted((int(i), int(j)) for i in a_nodes for j in b_nodes), dtype=np.uint32)
+    assert np.array_equal(q.get("S"), closed)
+    ref = oracle.hellings(graph, synth.GRAMMAR_C3)
+    for nm in g.names:
+        assert np.array_equal(q.get(nm), ref.pairs(nm)), nm
+
+
 # ------------------------------------------------------------------ limits and statuses
 
 def test_iteration_limit_status_and_partial_result():

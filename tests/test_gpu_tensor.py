@@ -118,3 +118,32 @@ def test_tile_skipping_issues_exactly_the_live_steps(schedule):
     s = q.stats()
     assert 0 < live < (n // 128) * (n // 256) * (n // 128)
     assert s["tensor_live_ops"] == s["iterations"] * live * 2.0 * 128 * 256 * 128
+
+
+def _middle_restricted_graph(n, m, positions, seed):
+    """S -> A B over A-edges i -> k and B-edges k -> j whose middle node k has k % 8 in
+    `positions`: every K index of the product T_A x T_B that holds a one sits at one of those
+    positions of its byte group."""
+    ks = np.array([k for k in range(n) if k % 8 in positions], dtype=np.int64)
+    kk = synth.key(seed, 9)
+    i = np.arange(m, dtype=np.int64)
+    a = np.stack([synth.uniform_int(kk, 4 * i, n), np.zeros(m, dtype=np.int64),
+                  ks[synth.uniform_int(kk, 4 * i + 1, len(ks))]], axis=1)
+    b = np.stack([ks[synth.uniform_int(kk, 4 * i + 2, len(ks))], np.ones(m, dtype=np.int64),
+                  synth.uniform_int(kk, 4 * i + 3, n)], axis=1)
+    return synth.Graph(n=n, edges=np.concatenate([a, b]), labels=["t0", "t1"], meta={"kind": "test"})
+
+
+@pytest.mark.parametrize("positions", [(0,), (1,), (2,), (0, 1, 2), (3,), (6,), (7,), (3, 4, 5, 6, 7)],
+                         ids=lambda p: "q" + "".join(map(str, p)))
+@pytest.mark.parametrize("dense", [True, False])
+def test_operand_encoding_positions(positions, dense):
+    """The tensor product encodes a one at K position q of a byte group (bit q + 8r of a 32-bit
+    word) as the E4M3 byte 1 << q (q = 0, 1, 2 are the subnormals 2^-9, 2^-8, 2^-7) and q = 7
+    as 0x40 = 2.0; a product is non-zero iff its accumulator is. If the MMA flushed subnormal
+    inputs, or one position's encoding were wrong, the pairs whose only middle nodes sit at
+    those positions would be lost. Each case puts every middle node at the given positions
+    (530 nodes: several tiles and K stages plus a ragged tail) and compares with the oracle."""
+    graph = _middle_restricted_graph(530, 1500, set(positions), seed=sum(positions) + 31 * len(positions))
+    g, q = tensor_parity(graph, "S A B\nA t0\nB t1\n", schedule=eng.SCHED_JACOBI, dense_tensor=dense)
+    assert q.count("S") > 300

@@ -92,3 +92,34 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     code = eng.library().cfpq_extract_pairs_noalloc(ctypes.c_void_p(dummy.data_ptr()), 1, 64, 1, 0, None, 0,
                                                     ctypes.byref(c), None)
     assert code == eng.ERR_INVALID  # n_cols wider than the rows
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call synchronises its stream and reads the count on the host, which a stream
+    capture cannot contain: on a capturing stream it is refused before any device work, the
+    capture can still be ended, and the next ordinary call works."""
+    import torch
+
+    graph = synth.hierarchy(600, 180, seed=2)
+    g = eng.Grammar(synth.GRAMMAR_QSC, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, timeout_s=120.0)
+    q.solve()
+    ref = reference_triples(q, "S")
+    row_words = (graph.n + 31) // 32
+    bits_np = bit_matrix(ref[:, 1:], graph.n, row_words)
+    bits = torch.from_numpy(bits_np.view(np.int32)).cuda()
+    out = torch.zeros(max(1, len(ref)) * 3, dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    c = ctypes.c_size_t(0)
+    lib = eng.library()
+    cg = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(cg, stream=side):
+        out.add_(0)  # one captured operation, so that the graph is not empty
+        code = lib.cfpq_extract_pairs_noalloc(ctypes.c_void_p(bits.data_ptr()), graph.n, graph.n, row_words,
+                                              g.id("S"), ctypes.c_void_p(out.data_ptr()), len(ref),
+                                              ctypes.byref(c), ctypes.c_void_p(side.cuda_stream))
+    assert code == eng.ERR_INVALID
+    torch.cuda.synchronize()
+    got, arr = run_noalloc(bits_np, graph.n, graph.n, g.id("S"), len(ref))
+    assert got == len(ref) and np.array_equal(arr, ref)
