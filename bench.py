@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--tensor", default="dense", choices=["dense", "skip"],
                     help="tensor products of the timed leg: every K step (Algorithm 1's dense product) or "
                          "only the K steps whose operand tiles are both non-zero")
+    ap.add_argument("--tensor-kind", default="auto", choices=["auto", "fp8", "fp4"],
+                    help="operand format of the tensor products: E4M3 bytes (kind::f8f6f4) or E2M1 nibbles "
+                         "(kind::mxf4, unit scales); auto = the library's default (fp4)")
     ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
@@ -245,10 +248,10 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_tc_bool_gemm_hier16k_dram.txt")
 TC_SOURCE = os.path.join(ROOT, "paper_1707_01007_b300", "csrc", "cfpq_tensor.cu")
 
 
-def tc_traffic_per_launch(dense=True):
-    """DRAM bytes per k_tc_bool_gemm launch (dense products, or with tile skipping) from the
-    committed ncu summary, or None when the summary is missing or the kernel source changed
-    since the counters were taken."""
+def tc_traffic_per_launch(dense=True, tkind="fp8"):
+    """DRAM bytes per k_tc_bool_gemm launch (dense products, or with tile skipping; E4M3 or,
+    with the key suffix _fp4, E2M1 operands) from the committed ncu summary, or None when the
+    summary is missing or the kernel source changed since the counters were taken."""
     import hashlib
 
     try:
@@ -260,35 +263,54 @@ def tc_traffic_per_launch(dense=True):
         src = hashlib.sha256(open(TC_SOURCE, "rb").read()).hexdigest()
         if vals.get("source_sha256") != src:
             return None
-        return float(vals["dram_bytes_per_launch_avg" if dense else "dram_bytes_per_launch_skip_avg"])
+        key = "dram_bytes_per_launch_avg" if dense else "dram_bytes_per_launch_skip_avg"
+        return float(vals[key + ("_fp4" if tkind == "fp4" else "")])
     except (OSError, KeyError, ValueError):
         return None
 
 
-FP8_OPS_PER_CLK_SM = 16384  # dense tcgen05 kind::f8f6f4: 2 x 8192 multiply-adds per clock and SM
+# dense tcgen05 ops (2 per multiply-add) per SM clock, measured by cfpq_measure_tensor_peaks
+# (clock64 around back-to-back MMAs): kind::f8f6f4 16384, kind::mxf4 32768
+OPS_PER_CLK_SM = {"fp8": 16384, "fp4": 32768}
+# the recipe's nominal dense ratios to bf16 (2.25 PFLOP/s): fp8 4.5, fp4 13.5
+NOMINAL_RATIO_TO_BF16 = {"fp8": 2.0, "fp4": 6.0}
 
 
-def nominal_fp8_tflops(sm_mhz):
-    """The dense FP8 tensor rate of this device at an SM clock (SMs x ops per clock x clock)."""
+def effective_kind(name):
+    """The operand format a tensor_kind option runs with (the library's default is FP4)."""
+    return "fp4" if name == "auto" else name
+
+
+def nominal_tflops(sm_mhz, tkind="fp8"):
+    """The dense tensor rate of this device for an operand kind at an SM clock (SMs x ops per
+    clock x clock)."""
     import torch
 
     if not sm_mhz:
         return None
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    return sms * FP8_OPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+    return sms * OPS_PER_CLK_SM[effective_kind(tkind)] * sm_mhz * 1e6 / 1e12
 
 
-def roofline(eng, graph, gs, path, schedule, stream, dense=True, sm_mhz=None):
+def kind_code(eng, name):
+    return {"auto": eng.TENSOR_AUTO, "fp8": eng.TENSOR_FP8, "fp4": eng.TENSOR_FP4}[name]
+
+
+def roofline(eng, graph, gs, path, schedule, stream, dense=True, sm_mhz=None, tkind="auto"):
     """Dominant product kernel: every product launch of a solve with the timed options is
     bracketed by CUDA events on the launching stream (profile mode); algorithmic work per
     launch is 2 n^3 per production of the group (tensor; with tile skipping, the K steps the
-    launch issued) or the counted words (gather)."""
-    peaks, kind = load_peaks()
+    launch issued) or the counted words (gather). A tensor product's peak is that of its
+    operand kind: the measured bf16 burst x the nominal ratio of the kind, with the kind's
+    measured MMA-only rate (cfpq_measure_tensor_peaks, same run) and its nominal per-clock
+    rate at the sampled clock beside it."""
+    peaks, source = load_peaks()
+    ek = effective_kind(tkind)
     prod_ms = prod_l = tens_ms = tens_l = 0
     flops = bytes_ = useful = 0.0
     for g in gs:
         q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, profile=True, timeout_s=300.0,
-                      dense_tensor=dense)
+                      dense_tensor=dense, tensor_kind=kind_code(eng, tkind))
         q.solve(stream)
         s = q.stats()
         prod_ms += s["product_ms"]
@@ -301,22 +323,36 @@ def roofline(eng, graph, gs, path, schedule, stream, dense=True, sm_mhz=None):
         q.close()
     if tens_l > 0 and tens_ms >= 0.5 * prod_ms:
         achieved = flops / (tens_ms / 1e3) / 1e12
-        peak = 2.0 * peaks["bf16_tflops"]
-        sustained = 2.0 * peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        ratio = NOMINAL_RATIO_TO_BF16[ek]
+        peak = ratio * peaks["bf16_tflops"]
+        sustained = ratio * peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
         # the integer tensor references of this device (sm_103a has no 8-bit integer tcgen05 kind)
         mma = eng.measure_mma_sync_peaks()
-        nominal = nominal_fp8_tflops(sm_mhz)
+        tp = eng.measure_tensor_peaks()
+        mma_only = tp["mxf4_tflops"] if ek == "fp4" else tp["f8f6f4_tflops"]
+        nominal = nominal_tflops(sm_mhz, ek)
+        nominal8 = nominal_tflops(sm_mhz, "fp8")
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": tc_traffic_per_launch(dense), "kernel": "k_tc_bool_gemm",
+                "traffic": tc_traffic_per_launch(dense, ek), "kernel": f"k_tc_bool_gemm<{ek}>",
+                "operands": "E2M1 0/1 nibbles, kind::mxf4, unit UE8M0 scales" if ek == "fp4"
+                            else "E4M3 0/1 bytes, kind::f8f6f4",
                 "tile_skipping": not dense, "launches": tens_l,
                 "launch_ms": tens_ms / tens_l, "flops_per_launch": flops / tens_l,
-                "peak_note": f"{kind} bf16 dense burst x 2 (fp8 e4m3 : bf16 nominal ratio); "
-                             f"frac against the sustained figure x 2: {achieved / sustained:.3f}",
+                "peak_note": f"{source} bf16 dense burst x {ratio:g} (the {ek} : bf16 nominal ratio); "
+                             f"frac against the sustained figure x {ratio:g}: {achieved / sustained:.3f}",
                 "useful_ops_per_step": useful,
-                "nominal_fp8_at_clock": {"peak": nominal, "sm_mhz": sm_mhz,
-                                         "frac": (achieved / nominal) if nominal else None,
-                                         "note": "SMs x 16384 dense FP8 ops per clock x the median SM clock "
-                                                 "sampled during the timed region"},
+                "measured_mma_only": {"peak": mma_only, "frac": achieved / mma_only,
+                                      "note": "the same kind's MMAs back to back in the kernel's tile shape, "
+                                              "no unpacking (cfpq_measure_tensor_peaks, this run)",
+                                      "probe": tp},
+                "nominal_at_clock": {"peak": nominal, "sm_mhz": sm_mhz,
+                                     "frac": (achieved / nominal) if nominal else None,
+                                     "ops_per_clk_sm": OPS_PER_CLK_SM[ek],
+                                     "note": "SMs x the kind's dense ops per clock x the median SM clock "
+                                             "sampled during the timed region"},
+                "vs_fp8_at_clock": {"peak": nominal8, "frac": (achieved / nominal8) if nominal8 else None,
+                                    "note": "the E4M3 kind's dense rate at the same clock: the ceiling of an "
+                                            "FP8 product kernel"},
                 "int_tensor_refs": {"mma_sync_s8_tops": mma["s8_tops"], "frac_of_mma_sync_s8": achieved / mma["s8_tops"],
                                     "mma_sync_b1_tops": mma["b1_tops"],
                                     "frac_of_mma_sync_b1": achieved / mma["b1_tops"],
@@ -328,16 +364,16 @@ def roofline(eng, graph, gs, path, schedule, stream, dense=True, sm_mhz=None):
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None, "kernel": "k_scan_rows + k_gather_list",
             "launches": launches, "launch_ms": gather_ms / launches, "bytes_per_launch": bytes_ / launches,
-            "peak_note": f"{kind} HBM copy bandwidth"}
+            "peak_note": f"{source} HBM copy bandwidth"}
 
 
 class Leg:
     """The queries of the workload resident on the device with one set of options."""
 
-    def __init__(self, eng, torch, graph, gs, path, schedule, stream, dense=True):
+    def __init__(self, eng, torch, graph, gs, path, schedule, stream, dense=True, kind="auto"):
         self.eng, self.torch, self.gs, self.stream = eng, torch, gs, stream
         self.qs = [eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0,
-                             dense_tensor=dense) for g in gs]
+                             dense_tensor=dense, tensor_kind=kind_code(eng, kind)) for g in gs]
         self.bufs = []
         for q in self.qs:
             q.solve(stream)
@@ -396,7 +432,7 @@ def engine_arm(args):
     ops_per_step = products * 2.0 * float(N_NODES) ** 3
 
     dense = args.tensor == "dense"
-    main = Leg(eng, torch, graph, gs, path, schedule, stream, dense)
+    main = Leg(eng, torch, graph, gs, path, schedule, stream, dense, args.tensor_kind)
     for _ in range(args.warmup):
         main.step()
     st = [q.stats() for q in main.qs]
@@ -431,7 +467,7 @@ def engine_arm(args):
                                       "auto_inplace": (eng.PATH_AUTO, eng.SCHED_INPLACE, False)}.items():
             if pth == path and sch == schedule and dns == dense:
                 continue
-            leg = Leg(eng, torch, graph, gs, pth, sch, stream, dns)
+            leg = Leg(eng, torch, graph, gs, pth, sch, stream, dns, args.tensor_kind)
             leg.step()
             ams = leg.time(max(2, min(args.steps, 5)))
             alternatives[name] = {"ms_per_step": ams, "value": world * ops_per_step / (ams / 1e3) / 1e9,
@@ -441,7 +477,7 @@ def engine_arm(args):
                                   "tensor_ops_executed": sum(q.stats()["tensor_live_ops"] for q in leg.qs)}
             leg.close()
             if name == "tensor_tile_skip":
-                r = roofline(eng, graph, gs, pth, sch, stream, dense=False)
+                r = roofline(eng, graph, gs, pth, sch, stream, dense=False, tkind=args.tensor_kind)
                 alternatives[name]["roofline_executed"] = {k: r.get(k) for k in
                                                            ("achieved", "peak", "unit", "frac", "launches", "launch_ms")}
 
@@ -454,7 +490,8 @@ def engine_arm(args):
     for _ in range(e2e_steps):
         d2h = 0
         for g in gs:
-            q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0, dense_tensor=dense)
+            q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0, dense_tensor=dense,
+                          tensor_kind=kind_code(eng, args.tensor_kind))
             q.solve()
             for nm in g.names:
                 d2h += q.triples(nm).shape[0] * 12
@@ -463,7 +500,7 @@ def engine_arm(args):
     e2e_s = max_over_ranks(e2e_s)
     e2e_val = job_rate(ops_per_step, e2e_s, world) / 1e9
 
-    roof = roofline(eng, graph, gs, path, schedule, stream, dense, sm_mhz=clk.get("sm_mhz"))
+    roof = roofline(eng, graph, gs, path, schedule, stream, dense, sm_mhz=clk.get("sm_mhz"), tkind=args.tensor_kind)
 
     # the default path of cfpq_solve (automatic product choice, in-place schedule): its
     # dominant kernels' roofline and its own end-to-end figure
@@ -493,11 +530,12 @@ def engine_arm(args):
         "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "step_ms_this_rank": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "fp8e4m3 0/1 operands, f32 accumulate (tensor path); u32 bit-packed storage",
+        "dtype": ("fp4e2m1" if effective_kind(args.tensor_kind) == "fp4" else "fp8e4m3") +
+                 " 0/1 operands, f32 accumulate (tensor path); u32 bit-packed storage",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_NODES, "classes": N_CLASSES, "seed": SEED,
                    "grammars": [nm for nm, _ in grammars], "path": args.path, "schedule": args.schedule,
-                   "tensor_products": args.tensor,
+                   "tensor_products": args.tensor, "tensor_kind": effective_kind(args.tensor_kind),
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (per query 3 x 7 x 32 MiB bit planes + 7 x 32 MiB transposes)",
                    "products_per_step": products, "dense_ops_executed_per_step": executed_dense,

@@ -97,6 +97,19 @@ enum cfpq_path {
                                  defined (reported as 1) */
 };
 
+/* Operand format of the tensor-core Boolean products (Section 2's product, one Boolean
+ * matrix product per production). The 0/1 operands are unpacked from the bit-packed matrices
+ * into a floating-point kind the tensor cores multiply exactly: every product of two ones is a
+ * positive power of two and the F32 sum of non-negative terms is non-zero iff some AND is true,
+ * so the thresholded accumulator is the Boolean OR of ANDs (counts stay far below 2^24). */
+enum cfpq_tensor_kind {
+    CFPQ_TENSOR_AUTO = 0,     /* FP4 */
+    CFPQ_TENSOR_FP8 = 1,      /* E4M3 bytes, tcgen05 kind::f8f6f4 (K = 32 per instruction) */
+    CFPQ_TENSOR_FP4 = 2       /* E2M1 nibbles, tcgen05 kind::mxf4 with unit UE8M0 scale factors
+                                 (K = 64 per instruction): half the unpacked bytes and twice the
+                                 MMA rate of FP8 */
+};
+
 typedef struct {
     int32_t schedule;         /* enum cfpq_schedule; default INPLACE */
     int32_t path;             /* enum cfpq_path; default AUTO */
@@ -119,6 +132,8 @@ typedef struct {
                                  refreshed at the start of each loop execution for the operands
                                  that changed); 1: every K step of every tile, Algorithm 1's dense
                                  product as written. Both give the same result */
+    int32_t tensor_kind;      /* enum cfpq_tensor_kind: operand format of the tensor-core products;
+                                 default AUTO. Every kind gives the same result */
 } cfpq_options;
 
 typedef struct {
@@ -358,6 +373,30 @@ int cfpq_autotune_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream, cfpq_bat
  * part of any solve. Errors: INVALID (NULL output), NOMEM, CUDA.
  */
 int cfpq_measure_mma_sync_peaks(double *s8_tops, double *b1_tops);
+
+/*
+ * Measured dense rate of the tcgen05 MMA kinds a Boolean product (Section 2's product
+ * over subsets of N, one Boolean matrix product per production; the BMM term of Theorem 4)
+ * can use on sm_103a, in the tile shape of the product kernels: M = 128, N = 256, A in
+ * tensor memory, B in shared memory, F32 accumulation. One CTA per SM issues the MMAs back
+ * to back with no unpacking, so these are the ceilings of the product kernels of each kind.
+ * *_tflops: tera-ops/s over the device (2 ops per multiply-add, CUDA events around one
+ * launch); *_ops_per_clk_sm: ops per SM clock cycle of one CTA (clock64 around its MMAs),
+ * independent of the clock the device ran at; *_exact: 1 if every checked accumulator
+ * element equals the exact sum of the known operands (all 1.0, unit scale factors), i.e.
+ * the kind's operand encoding and instruction descriptor are the ones the kernels use.
+ * Two timed launches of a few ms each on the current device; not part of any solve.
+ * Errors: INVALID (NULL), UNSUPPORTED (not sm_103), NOMEM, CUDA.
+ */
+typedef struct {
+    double f8f6f4_tflops;          /* kind::f8f6f4, E4M3 operands, K = 32 per instruction */
+    double mxf4_tflops;            /* kind::mxf4 block-scaled, E2M1 operands, UE8M0 scales, K = 64 */
+    double f8f6f4_ops_per_clk_sm;
+    double mxf4_ops_per_clk_sm;
+    int32_t f8f6f4_exact;
+    int32_t mxf4_exact;
+} cfpq_tensor_peaks;
+int cfpq_measure_tensor_peaks(cfpq_tensor_peaks *out);
 
 /* Batched solve under an explicit configuration instead of the installed one. */
 int cfpq_solve_batch_tuned(cfpq_ctx *const *ctxs, int32_t k, const cfpq_batch_tuning *t, void *stream);

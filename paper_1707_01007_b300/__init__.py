@@ -24,6 +24,7 @@ OK, ERR_INVALID, ERR_NOMEM, ERR_NOT_SOLVED, ERR_ITER_LIMIT, ERR_TIMEOUT, ERR_CUD
 SCHED_INPLACE, SCHED_JACOBI, SCHED_AUTO = 0, 1, 2
 TUNE_CLASSES = 24
 PATH_AUTO, PATH_TENSOR, PATH_GATHER, PATH_WORKLIST = 0, 1, 2, 3
+TENSOR_AUTO, TENSOR_FP8, TENSOR_FP4 = 0, 1, 2
 
 
 class CfpqError(RuntimeError):
@@ -58,7 +59,7 @@ class Triple(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("path", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("timeout_s", ctypes.c_double),
-                ("lengths", ctypes.c_int32), ("dense_tensor", ctypes.c_int32)]
+                ("lengths", ctypes.c_int32), ("dense_tensor", ctypes.c_int32), ("tensor_kind", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -109,6 +110,15 @@ class BatchTuning(ctypes.Structure):
                 "schedule": {c: self.schedule[c] for c in range(TUNE_CLASSES) if self.schedule[c]}}
 
 
+class TensorPeaks(ctypes.Structure):
+    _fields_ = [("f8f6f4_tflops", ctypes.c_double), ("mxf4_tflops", ctypes.c_double),
+                ("f8f6f4_ops_per_clk_sm", ctypes.c_double), ("mxf4_ops_per_clk_sm", ctypes.c_double),
+                ("f8f6f4_exact", ctypes.c_int32), ("mxf4_exact", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class TuneReport(ctypes.Structure):
     _fields_ = [("trials", ctypes.c_int32), ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double)]
 
@@ -148,6 +158,7 @@ SIGNATURES = {
     "cfpq_autotune_batch": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _VP, _P(BatchTuning), _P(TuneReport)]),
     "cfpq_solve_batch_tuned": (ctypes.c_int, [_P(_VP), ctypes.c_int32, _P(BatchTuning), _VP]),
     "cfpq_measure_mma_sync_peaks": (ctypes.c_int, [_P(ctypes.c_double), _P(ctypes.c_double)]),
+    "cfpq_measure_tensor_peaks": (ctypes.c_int, [_VP]),
     "cfpq_batch_last_profile": (ctypes.c_int, [_P(ctypes.c_double), ctypes.c_int32, _P(ctypes.c_int64),
                                                _P(ctypes.c_double), ctypes.c_int32]),
     "cfpq_server_options_default": (ctypes.c_int, [_P(ServerOptions)]),
@@ -237,7 +248,7 @@ class Query:
 
     def __init__(self, grammar: Grammar, n: int, edges, schedule: int = SCHED_INPLACE, path: int = PATH_AUTO,
                  use_graph: bool = True, max_iter: int = 0, timeout_s: float = 0.0, profile: bool = False,
-                 lengths: bool = False, dense_tensor: bool = False):
+                 lengths: bool = False, dense_tensor: bool = False, tensor_kind: int = TENSOR_AUTO):
         self.grammar = grammar
         self.n = int(n)
         self._h = None
@@ -248,6 +259,7 @@ class Query:
         opt.max_iter, opt.timeout_s = int(max_iter), float(timeout_s)
         opt.lengths = int(bool(lengths))
         opt.dense_tensor = int(bool(dense_tensor))
+        opt.tensor_kind = int(tensor_kind)
         rec = _edges_struct(edges)
         h = ctypes.c_void_p()
         ptr = rec.ctypes.data_as(ctypes.POINTER(Edge)) if rec.size else None
@@ -511,3 +523,11 @@ def measure_mma_sync_peaks() -> dict:
     s8, b1 = ctypes.c_double(), ctypes.c_double()
     _check(_lib().cfpq_measure_mma_sync_peaks(ctypes.byref(s8), ctypes.byref(b1)), "cfpq_measure_mma_sync_peaks")
     return {"s8_tops": s8.value, "b1_tops": b1.value}
+
+
+def measure_tensor_peaks() -> dict:
+    """Measured dense rate of the tcgen05 kinds f8f6f4 (E4M3) and mxf4 (E2M1, unit scales) in
+    the product kernels' tile shape, TFLOP/s and ops per SM clock, with the exactness check."""
+    p = TensorPeaks()
+    _check(_lib().cfpq_measure_tensor_peaks(ctypes.byref(p)), "cfpq_measure_tensor_peaks")
+    return p.as_dict()

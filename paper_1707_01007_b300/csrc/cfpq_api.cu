@@ -936,6 +936,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     c->path = o.path;
     c->lengths = o.lengths != 0;
     c->dense_tensor = o.dense_tensor != 0;
+    c->tensor_kind = o.tensor_kind == CFPQ_TENSOR_FP8 ? CFPQ_TENSOR_FP8 : CFPQ_TENSOR_FP4;
     if (c->lengths) {
         // the lengths come from the matrices before each loop execution: Jacobi schedule only
         if (o.schedule == CFPQ_SCHED_INPLACE || o.path == CFPQ_PATH_WORKLIST) return CFPQ_ERR_UNSUPPORTED;
@@ -1163,6 +1164,7 @@ int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edge
         if (opt->path < CFPQ_PATH_AUTO || opt->path > CFPQ_PATH_WORKLIST) return CFPQ_ERR_INVALID;
         if ((opt->lengths != 0 && opt->lengths != 1) || (opt->dense_tensor != 0 && opt->dense_tensor != 1))
             return CFPQ_ERR_INVALID;
+        if (opt->tensor_kind < CFPQ_TENSOR_AUTO || opt->tensor_kind > CFPQ_TENSOR_FP4) return CFPQ_ERR_INVALID;
     }
     return CFPQ_OK;
 }

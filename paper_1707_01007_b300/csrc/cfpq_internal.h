@@ -37,6 +37,7 @@ struct cfpq_ctx {
     uint32_t *d_occA = nullptr, *d_occB = nullptr;  // tile occupancy (tensor path with tile skipping; arena)
     void *d_tile_list = nullptr;      // tile skipping: live output tiles of one product (uint2 each; arena)
     bool dense_tensor = false;        // tensor products over every K step (no tile skipping)
+    int tensor_kind = CFPQ_TENSOR_FP4;  // operand format of the tensor products (FP8 or FP4, resolved)
     uint32_t *d_Tsum = nullptr;       // word summary of T (in the arena)
     uint32_t *d_TTsum = nullptr;      // word summary of T^T (lengths only; in the arena)
     uint32_t SW = 0;                  // summary words per row: ceil(W / 32) rounded up to a multiple of 4

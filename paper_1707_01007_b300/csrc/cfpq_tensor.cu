@@ -36,16 +36,14 @@
 #include <cstring>
 
 #include "cfpq_internal.h"
+#include "cfpq_tcgen05.cuh"
 
 namespace cfpq {
 namespace tc {
 
 constexpr int BM = 128, BN = 256;
-constexpr int KW = 4;                 // 32-bit words of K per stage
-constexpr int BK = 32 * KW;           // 128 K elements per stage
-constexpr int PST = 8, UST = 5;       // packed / unpacked ring depths
-constexpr int A_PACK = BM * KW * 4, B_PACK = BN * KW * 4;  // bytes of one packed stage
-constexpr int B_TILE = BN * BK;       // bytes of one unpacked B stage (FP8)
+constexpr int UST = 5;                // unpacked ring depth
+constexpr int B_TILE = BN * 128;      // bytes of one unpacked B stage: 256 rows x 128 bytes
 constexpr int UNPACK_GROUPS = 2;     // groups of 8 unpack warps; group g takes the K stages s = g mod 2
 constexpr int GROUP_THREADS = 256;   // one group: two warps per SM sub-partition
 constexpr int UNPACK_WARPS = 8 * UNPACK_GROUPS;
@@ -54,12 +52,33 @@ constexpr uint32_t RASTER_N = 8;      // N tiles per rasterisation band
 constexpr int UNPACK_THREADS = 32 * UNPACK_WARPS;
 constexpr int THREADS = 64 + UNPACK_THREADS;
 constexpr uint32_t ACC_COLS = 256;                 // F32 accumulator, 128 lanes x 256 columns
-constexpr uint32_t A_COLS = BK / 4;                // one stage of A: 128 FP8 per lane = 32 columns
-constexpr uint32_t TMEM_COLS = 512;                // accumulator + UST stages of A, power of two
-static_assert(ACC_COLS + UST * A_COLS <= TMEM_COLS, "tensor memory budget");
-constexpr unsigned long long WAIT_LIMIT_NS = 2ull * 1000 * 1000 * 1000;  // 2 s per wait
+constexpr uint32_t A_COLS = 32;                    // one stage of A: 128 bytes per lane = 32 columns
+constexpr uint32_t SFA_COL = ACC_COLS + UST * A_COLS;  // FP4: scale factors of A (32 columns, all 2^0)
+constexpr uint32_t SFB_COL = SFA_COL + 32;             // FP4: scale factors of B (32 columns, all 2^0)
+constexpr uint32_t TMEM_COLS = 512;                // power of two
+static_assert(SFB_COL + 32 <= TMEM_COLS, "tensor memory budget");
 
+// Operand kinds. An unpacked K stage is 128 bytes per row either way (one 128-byte
+// swizzle row of a shared-memory tile, 32 tensor-memory columns) and feeds 4 MMAs.
+//   KIND 0  E4M3 bytes, kind::f8f6f4 (K = 32 per MMA): a stage is one 128-bit K slice of
+//           the bit-packed rows (4 words per row)
+//   KIND 1  E2M1 nibbles, kind::mxf4 with unit UE8M0 scale factors (K = 64 per MMA): a
+//           stage is two consecutive 128-bit K slices (8 words per row), half the unpacked
+//           bytes and half the MMA time per K of KIND 0
+template <int KIND>
+struct Kind;
+template <>
+struct Kind<0> {
+    static constexpr int KW = 4, PST = 8, SLICES = 1;  // packed words per row and stage, packed ring depth
+};
+template <>
+struct Kind<1> {
+    static constexpr int KW = 8, PST = 5, SLICES = 2;
+};
+
+template <int KIND>
 struct __align__(1024) Smem {
+    static constexpr int KW = Kind<KIND>::KW, PST = Kind<KIND>::PST;
     uint8_t b_tile[UST][B_TILE];
     uint32_t a_pack[PST][BM * KW];
     uint32_t b_pack[PST][BN * KW];
@@ -71,119 +90,77 @@ struct __align__(1024) Smem {
     int err;
 };
 
-constexpr size_t SMEM_BYTES = sizeof(Smem) + 1024;
+template <int KIND>
+constexpr size_t smem_bytes() {
+    return sizeof(Smem<KIND>) + 1024;
+}
+static_assert(smem_bytes<0>() <= 227 * 1024 && smem_bytes<1>() <= 227 * 1024, "shared memory per CTA");
 
-__device__ __forceinline__ uint32_t sa(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+// Instruction descriptors (both operands K-major, M = 128, N = 256, F32 accumulator):
+// kind::f8f6f4 with A = B = E4M3 (bits 4-5: D is F32); kind::mxf4 block-scaled with
+// A = B = E2M1 (type 1 in bits 7-9 and 10-12), UE8M0 scale factors (bit 23), scale-factor
+// ids 0 (bits 4-5 for B, 29-30 for A).
+constexpr uint32_t IDESC_F8 = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                              ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t IDESC_F4 = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
+                              ((uint32_t)(BM >> 4) << 24);
 
-__device__ __forceinline__ void mbar_init(unsigned long long *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(sa(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: false (and the CTA's error flag set) if the phase did not complete in time
-// or another role of the CTA already gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, volatile int *err) {
-    if (mbar_try(b, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    for (;;) {
-        if (mbar_try(b, parity)) return true;
-        if (*err) return false;
-        if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
-            *err = 1;
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, unsigned long long *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            sa(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(sa(bar))
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;            // leading-dimension byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;  // stride-dimension byte offset
-    d |= (uint64_t)1 << 46;            // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;            // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: kind::f8f6f4, A = B = E4M3, D = F32, both K-major, M x N.
-constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-// D[tmem] (+)= A[tmem] x B[smem]^T
+// D[tmem] (+)= A[tmem] x B[smem]^T, E4M3, K = 32
 __device__ __forceinline__ void mma_f8_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}" ::"r"(
             tmem_d),
-        "r"(tmem_a), "l"(bd), "r"(IDESC), "r"(accumulate)
+        "r"(tmem_a), "l"(bd), "r"(IDESC_F8), "r"(accumulate)
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(unsigned long long *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// D[tmem] (+)= (A[tmem] x SFA) x (B[smem] x SFB)^T, E2M1, K = 64, one scale factor per 32 K
+__device__ __forceinline__ void mma_f4_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bd, uint32_t sfa, uint32_t sfb,
+                                          uint32_t accumulate) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-        "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-        "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+        "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%4], [%5], p;\n}" ::"r"(
+            tmem_d),
+        "r"(tmem_a), "l"(bd), "r"(IDESC_F4), "r"(sfa), "r"(sfb), "r"(accumulate)
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
+// The 4 MMAs of one unpacked stage (A at tensor-memory column at, B at shared address bt).
+template <int KIND>
+__device__ __forceinline__ void mma_stage(uint32_t tmem, uint32_t at, uint32_t bt, bool first) {
+#pragma unroll
+    for (int kk = 0; kk < 4; kk++) {
+        const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+        if constexpr (KIND == 0)
+            mma_f8_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), acc);
+        else
+            mma_f4_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), tmem + SFA_COL, tmem + SFB_COL, acc);
+    }
 }
 
-// 4 bytes of the unpacked K-row: byte r = bit (q + 8r) of w, as a positive FP8 E4M3 value or
-// 0. For q < 7 the bit stays where it is (byte 1 << q: one AND per 4 bytes); bit 7 would be
+// E4M3: 4 bytes of the unpacked K-row, byte r = bit (q + 8r) of w, as a positive value or 0.
+// For q < 7 the bit stays where it is (byte 1 << q: one AND per 4 bytes); bit 7 would be
 // the sign, so it moves to bit 6 (0x40 = 2.0).
 __device__ __forceinline__ uint32_t spread(uint32_t w, int q) {
     return q < 7 ? (w & (0x01010101u << q)) : ((w >> 1) & 0x40404040u);
+}
+
+// E2M1: 8 nibbles of the unpacked K-row, nibble t = bit (4t + s) of w, as a positive value or
+// 0. For s < 3 the bit stays where it is (nibble 1 << s = 0.5, 1.0, 2.0: one AND per 8
+// nibbles); bit 3 of a nibble would be the sign, so it moves to bit 2 (2.0).
+__device__ __forceinline__ uint32_t spread4(uint32_t w, int s) {
+    return s < 3 ? (w & (0x11111111u << s)) : ((w >> 1) & 0x44444444u);
+}
+
+// Unpacked word u of a stage's K-row (bytes 4u .. 4u+3 of its 128 bytes) from the packed
+// words of that row: E4M3 spread(word u / 8, u % 8), E2M1 spread4(word u / 4, u % 4). The
+// same permutation of K for both operands, so the contraction is unchanged.
+template <int KIND>
+__device__ __forceinline__ uint32_t unpacked_word(const uint32_t *w, int u) {
+    if constexpr (KIND == 0)
+        return spread(w[u >> 3], u & 7);
+    else
+        return spread4(w[u >> 2], u & 3);
 }
 
 // Byte offsets of the 16-byte chunks c = 0..7 of row r in a 128-byte-swizzled K-major tile.
@@ -192,32 +169,29 @@ __device__ __forceinline__ void swizzled_row(int r, uint32_t (&off)[8]) {
     for (int c = 0; c < 8; c++) off[c] = (uint32_t)r * 128u + ((uint32_t)(c ^ (r & 7)) << 4);
 }
 
-// Unpacks one 128-bit K slice of a row into its swizzled row of a tile (chunk offsets off).
-__device__ __forceinline__ void unpack_row(uint8_t *tile, const uint32_t (&off)[8], uint4 p) {
-    const uint32_t w[4] = {p.x, p.y, p.z, p.w};
+// Unpacks one K stage of a row (Kind<KIND>::KW packed words) into its swizzled row of a
+// tile (chunk offsets off): chunk c holds the unpacked words 4c .. 4c+3.
+template <int KIND>
+__device__ __forceinline__ void unpack_row(uint8_t *tile, const uint32_t (&off)[8], const uint32_t *w) {
 #pragma unroll
-    for (int wi = 0; wi < 4; wi++)
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            uint4 o;
-            o.x = spread(w[wi], 4 * h + 0);
-            o.y = spread(w[wi], 4 * h + 1);
-            o.z = spread(w[wi], 4 * h + 2);
-            o.w = spread(w[wi], 4 * h + 3);
-            *reinterpret_cast<uint4 *>(tile + off[wi * 2 + h]) = o;
-        }
+    for (int c = 0; c < 8; c++) {
+        uint4 o;
+        o.x = unpacked_word<KIND>(w, 4 * c + 0);
+        o.y = unpacked_word<KIND>(w, 4 * c + 1);
+        o.z = unpacked_word<KIND>(w, 4 * c + 2);
+        o.w = unpacked_word<KIND>(w, 4 * c + 3);
+        *reinterpret_cast<uint4 *>(tile + off[c]) = o;
+    }
 }
 
-// Half (64 bytes, words 2h and 2h+1) of the same 128-byte K slice as unpack_row, as 16 TMEM
-// columns of one lane: column j of the slice holds logical bytes 4j .. 4j+3, i.e.
-// spread(word j/8, j%8); this half is columns 16h .. 16h+15.
-__device__ __forceinline__ void unpack_half_row_tmem(uint32_t taddr, uint2 p) {
+// Half h of the same K stage of a row (unpacked words 16h .. 16h+15, from the packed words
+// w = row + KW h / 2) as 16 tensor-memory columns of one lane: column j of the stage holds
+// unpacked word j.
+template <int KIND>
+__device__ __forceinline__ void unpack_half_row_tmem(uint32_t taddr, const uint32_t *w) {
     uint32_t v[16];
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-        v[j] = spread(p.x, j);
-        v[8 + j] = spread(p.y, j);
-    }
+    for (int j = 0; j < 16; j++) v[j] = unpacked_word<KIND>(w, j);
     tmem_st16(taddr, v);
 }
 
@@ -231,6 +205,17 @@ __device__ __forceinline__ uint32_t live_slices(const QDesc &q, int B, int C, ui
     }
     const uint32_t left = q.KS - w * 32u;
     return left >= 32u ? 0xFFFFFFFFu : ((1u << left) - 1u);
+}
+
+// K stages of a kind in word w of the slice masks: a KIND 1 stage (two slices 2j, 2j + 1,
+// bit 2j of the result) is live if either slice is.
+template <int KIND>
+__device__ __forceinline__ uint32_t live_steps(const QDesc &q, int B, int C, uint32_t mt, uint32_t nt, uint32_t w) {
+    const uint32_t x = live_slices(q, B, C, mt, nt, w);
+    if constexpr (KIND == 0)
+        return x;
+    else
+        return (x | (x >> 1)) & 0x55555555u;
 }
 
 // Origin of output tile t of a product (grouped rasterisation: consecutive tiles sweep the M
@@ -247,7 +232,9 @@ __device__ __forceinline__ void tile_origin(const QDesc &q, uint32_t t, uint32_t
 }
 
 // Tile skipping, one thread per output tile of group g: the tiles with at least one live K
-// step go to the list as (tile, live K steps); the count is the plan slot of this execution.
+// step (a stage of the product kernel's kind) go to the list as (tile, live K steps); the
+// count is the plan slot of this execution.
+template <int KIND>
 __global__ void __launch_bounds__(256) k_tile_plan(const QDesc *qd, int g, uint2 *list) {
     const QDesc &q = *qd;
     DevState *st = q.st;
@@ -262,7 +249,7 @@ __global__ void __launch_bounds__(256) k_tile_plan(const QDesc *qd, int g, uint2
         tile_origin(q, t, m0, n0);
         for (int r = r0; r < r1; r++)
             for (uint32_t w = 0; w < q.SWK; w++)
-                live += __popc(live_slices(q, q.rules[r].b, q.rules[r].c, m0 / BM, n0 / BN, w));
+                live += __popc(live_steps<KIND>(q, q.rules[r].b, q.rules[r].c, m0 / BM, n0 / BN, w));
     }
     const unsigned m = __ballot_sync(0xffffffffu, live != 0u);
     uint32_t base = 0;
@@ -277,11 +264,15 @@ __global__ void __launch_bounds__(256) k_tile_plan(const QDesc *qd, int g, uint2
 // take more of them) and handed to the MMA and unpack warps through a two-slot ring in shared
 // memory. The roles keep one running stage counter across the CTA's tiles; the accumulator is
 // handed back by the epilogue (acc_empty) before the next tile's MMAs.
+template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_bool_gemm(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmTT, const QDesc *qd,
                    int g, const uint2 *list) {
+    constexpr int KW = Kind<KIND>::KW, PST = Kind<KIND>::PST, SLICES = Kind<KIND>::SLICES;
+    constexpr uint32_t STAGE_BYTES = (uint32_t)(BM + BN) * KW * 4;  // packed bytes of one K stage
     extern __shared__ uint8_t smem_raw[];
-    Smem &S = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    Smem<KIND> &S =
+        *reinterpret_cast<Smem<KIND> *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const QDesc &q = *qd;
     DevState *st = q.st;
     if (st->use_tensor[g] == 0) return;
@@ -291,7 +282,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
     const uint32_t ntile = list ? __ldcg(&st->plan_count[g][st->iter & 1ull]) : (q.n_pad / BN) * (q.n_pad / BM);
     if (blockIdx.x >= ntile) return;  // (uniform over the CTA) no tile for this CTA
-    const uint32_t dense_steps = (uint32_t)(r1 - r0) * q.KS;
+    const uint32_t dense_steps = (uint32_t)(r1 - r0) * (q.KS / SLICES);
     volatile int *err = &S.err;
 
     if (threadIdx.x == 0) {
@@ -361,12 +352,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
                 uint32_t m0, n0;
                 tile_origin(q, e.x, m0, n0);
-                atomicAdd(&st->tc_live_steps, (unsigned long long)e.y);
+                atomicAdd(&st->tc_live_steps, (unsigned long long)e.y * SLICES);  // in 128-bit K slices
                 uint32_t done = 0;
                 for (int r = r0; r < r1 && !stop; r++) {
                     const int B = q.rules[r].b, C = q.rules[r].c;
                     for (uint32_t w = 0; w < q.SWK && !stop; w++) {
-                        uint32_t live = live_slices(q, B, C, m0 / BM, n0 / BN, w);
+                        uint32_t live = live_steps<KIND>(q, B, C, m0 / BM, n0 / BN, w);
                         while (live && done < e.y) {
                             const uint32_t kb = w * 32u + (uint32_t)(__ffs(live) - 1);
                             live &= live - 1;
@@ -376,10 +367,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 stop = true;
                                 break;
                             }
-                            mbar_expect_tx(&S.full_p[slot], A_PACK + B_PACK);
-                            tma_load_2d(S.a_pack[slot], &tmT, &S.full_p[slot], (int)(kb * KW),
+                            // K slice kb (for KIND 1 the first of the stage's two) starts at word 4 kb
+                            mbar_expect_tx(&S.full_p[slot], STAGE_BYTES);
+                            tma_load_2d(S.a_pack[slot], &tmT, &S.full_p[slot], (int)(kb * 4u),
                                         (int)((uint32_t)B * q.n_pad + m0));
-                            tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * KW),
+                            tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * 4u),
                                         (int)((uint32_t)C * q.n_pad + n0));
                             issued = s + 1;
                             done++;
@@ -420,9 +412,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + slot * B_TILE;
-#pragma unroll
-                    for (int kk = 0; kk < BK / 32; kk++)
-                        mma_f8_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), (u > 0 || kk > 0) ? 1u : 0u);
+                    mma_stage<KIND>(tmem, at, bt, u == 0);
                     mma_commit(&S.empty_u[slot]);
                 }
                 mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
@@ -456,6 +446,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t *TA = q.T + (uint64_t)A * q.plane;
         uint32_t off[8];
         swizzled_row(t, off);
+        if constexpr (KIND == 1) {
+            // unit scale factors (UE8M0 127 = 2^0) for every K block of both operands: warps 2-5
+            // (one per lane quadrant, all in group 0) write them before their first stage, whose
+            // completion the MMA issuer waits for before its first MMA
+            if (uw < 4) {
+                uint32_t v[32];
+#pragma unroll
+                for (int j = 0; j < 32; j++) v[j] = 0x7F7F7F7Fu;
+                tmem_st32(tmem + ((uint32_t)(quad * 32) << 16) + SFA_COL, v);
+                tmem_st32(tmem + ((uint32_t)(quad * 32) << 16) + SFB_COL, v);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
+        }
         uint32_t s_end = 0, tiles_done = 0;
         uint32_t sn = grp;                          // this group's next K stage (counted over the CTA's tiles)
         uint32_t us = grp % UST, uph = 0;           // its unpacked ring slot and phase: sn % UST, (sn / UST) & 1
@@ -466,11 +469,23 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!mbar_wait(&S.full_p[ps], pph, err)) return false;
                 if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) return false;
                 tc_fence_after();
-                const uint2 pa = reinterpret_cast<const uint2 *>(S.a_pack[ps])[2 * arow + half];
-                const uint4 pb = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
+                uint32_t pa[KW / 2], pb[KW];  // this lane's half row of A and the thread's row of B
+                if constexpr (KIND == 0) {
+                    const uint2 x = reinterpret_cast<const uint2 *>(S.a_pack[ps])[2 * arow + half];
+                    const uint4 y = reinterpret_cast<const uint4 *>(S.b_pack[ps])[t];
+                    pa[0] = x.x, pa[1] = x.y;
+                    pb[0] = y.x, pb[1] = y.y, pb[2] = y.z, pb[3] = y.w;
+                } else {
+                    const uint4 x = reinterpret_cast<const uint4 *>(S.a_pack[ps])[2 * arow + half];
+                    const uint4 y0 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[2 * t];
+                    const uint4 y1 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[2 * t + 1];
+                    pa[0] = x.x, pa[1] = x.y, pa[2] = x.z, pa[3] = x.w;
+                    pb[0] = y0.x, pb[1] = y0.y, pb[2] = y0.z, pb[3] = y0.w;
+                    pb[4] = y1.x, pb[5] = y1.y, pb[6] = y1.z, pb[7] = y1.w;
+                }
                 mbar_arrive(&S.empty_p[ps]);
-                unpack_half_row_tmem(a_lane + us * A_COLS, pa);
-                unpack_row(S.b_tile[us], off, pb);
+                unpack_half_row_tmem<KIND>(a_lane + us * A_COLS, pa);
+                unpack_row<KIND>(S.b_tile[us], off, pb);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc_fence_before();
@@ -706,7 +721,7 @@ bool tensor_path_available() {
 }
 
 struct TensorWork {
-    CUtensorMap tmT, tmTT;
+    CUtensorMap tmT[2], tmTT[2];  // per operand kind: boxes of Kind<KIND>::KW words
     bool attr_set;
 };
 
@@ -723,12 +738,12 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-static bool encode_map(CUtensorMap *m, uint32_t *base, const cfpq_ctx *c, uint32_t box_rows) {
+static bool encode_map(CUtensorMap *m, uint32_t *base, const cfpq_ctx *c, uint32_t box_words, uint32_t box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {c->W, (cuuint64_t)c->n_nt * c->n_pad};
     const cuuint64_t strides[1] = {(cuuint64_t)c->W * 4};
-    const cuuint32_t box[2] = {(cuuint32_t)tc::KW, box_rows};
+    const cuuint32_t box[2] = {(cuuint32_t)box_words, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
@@ -740,12 +755,17 @@ static int tensor_setup(cfpq_ctx *c) {
     if (!c->d_TT) return CFPQ_ERR_UNSUPPORTED;
     TensorWork *w = new TensorWork();
     memset(w, 0, sizeof(*w));
-    if (!encode_map(&w->tmT, c->d_T, c, tc::BM) || !encode_map(&w->tmTT, c->d_TT, c, tc::BN)) {
+    if (!encode_map(&w->tmT[0], c->d_T, c, tc::Kind<0>::KW, tc::BM) ||
+        !encode_map(&w->tmTT[0], c->d_TT, c, tc::Kind<0>::KW, tc::BN) ||
+        !encode_map(&w->tmT[1], c->d_T, c, tc::Kind<1>::KW, tc::BM) ||
+        !encode_map(&w->tmTT[1], c->d_TT, c, tc::Kind<1>::KW, tc::BN)) {
         delete w;
         return CFPQ_ERR_CUDA;
     }
-    if (cudaFuncSetAttribute(tc::k_tc_bool_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES) !=
-        cudaSuccess) {
+    if (cudaFuncSetAttribute(tc::k_tc_bool_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc::smem_bytes<0>()) != cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_tc_bool_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc::smem_bytes<1>()) != cudaSuccess) {
         delete w;
         return CFPQ_ERR_CUDA;
     }
@@ -838,30 +858,36 @@ int enqueue_tensor_transposes(cfpq_ctx *c, int g, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 
-// The tensor-core product of group g (after enqueue_tensor_transposes).
+// The tensor-core product of group g (after enqueue_tensor_transposes), with the operand
+// kind of the context (c->tensor_kind: 1 E4M3, 2 E2M1).
+template <int KIND>
+static void launch_group(cfpq_ctx *c, TensorWork *w, int g, cudaStream_t s, uint32_t tiles, uint32_t grid) {
+    if (c->d_tile_list) {
+        // tile skipping: list the live output tiles, then one CTA per SM over the list
+        tc::k_tile_plan<KIND><<<(tiles + 255) / 256, 256, 0, s>>>(c->d_q, g, reinterpret_cast<uint2 *>(c->d_tile_list));
+        tc::k_tc_bool_gemm<KIND><<<grid, tc::THREADS, tc::smem_bytes<KIND>(), s>>>(
+            w->tmT[KIND], w->tmTT[KIND], c->d_q, g, reinterpret_cast<const uint2 *>(c->d_tile_list));
+        c->iter_launches += 2;
+    } else {
+        tc::k_tc_bool_gemm<KIND><<<grid, tc::THREADS, tc::smem_bytes<KIND>(), s>>>(w->tmT[KIND], w->tmTT[KIND],
+                                                                                 c->d_q, g, nullptr);
+        c->iter_launches++;
+    }
+}
+
 int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
     const int rc = tensor_setup(c);
     if (rc != CFPQ_OK) return rc;
     TensorWork *w = static_cast<TensorWork *>(c->h_tc_work);
     const uint32_t tiles = (c->n_pad / tc::BN) * (c->n_pad / tc::BM);
-    if (c->d_tile_list) {
-        // tile skipping: list the live output tiles, then one CTA per SM over the list
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        tc::k_tile_plan<<<(tiles + 255) / 256, 256, 0, s>>>(c->d_q, g, reinterpret_cast<uint2 *>(c->d_tile_list));
-        const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)std::max(1, sms));
-        tc::k_tc_bool_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(w->tmT, w->tmTT, c->d_q, g,
-                                                                    reinterpret_cast<const uint2 *>(c->d_tile_list));
-        c->iter_launches += 2;
-    } else {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)std::max(1, sms));
-        tc::k_tc_bool_gemm<<<grid, tc::THREADS, tc::SMEM_BYTES, s>>>(w->tmT, w->tmTT, c->d_q, g, nullptr);
-        c->iter_launches++;
-    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)std::max(1, sms));
+    if (c->tensor_kind == CFPQ_TENSOR_FP8)
+        launch_group<0>(c, w, g, s, tiles, grid);
+    else
+        launch_group<1>(c, w, g, s, tiles, grid);
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 

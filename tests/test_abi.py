@@ -97,7 +97,8 @@ def test_lengths_options_checked_before_device_use():
     # they need the Jacobi schedule and a matrix path; bad flag values are rejected
     g = eng.Grammar("S S S\nS a\n", ["a"])
     lib = eng.library()
-    for field, value, code in [("lengths", 2, eng.ERR_INVALID), ("dense_tensor", 2, eng.ERR_INVALID)]:
+    for field, value, code in [("lengths", 2, eng.ERR_INVALID), ("dense_tensor", 2, eng.ERR_INVALID),
+                               ("tensor_kind", 3, eng.ERR_INVALID), ("tensor_kind", -1, eng.ERR_INVALID)]:
         opt = eng.Options()
         lib.cfpq_options_default(ctypes.byref(opt))
         opt.schedule = eng.SCHED_JACOBI
@@ -123,15 +124,16 @@ def test_null_arguments():
     assert lib.cfpq_options_default(None) == eng.ERR_INVALID
     assert lib.cfpq_solve_batch(None, 0, None) == eng.ERR_INVALID
     assert lib.cfpq_measure_mma_sync_peaks(None, None) == eng.ERR_INVALID
+    assert lib.cfpq_measure_tensor_peaks(None) == eng.ERR_INVALID
     lib.cfpq_destroy(None)
 
 
 def test_options_defaults():
     opt = eng.Options()
     assert eng.library().cfpq_options_default(ctypes.byref(opt)) == eng.OK
-    assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter, opt.lengths, opt.dense_tensor) == \
-        (eng.SCHED_INPLACE, eng.PATH_AUTO, 1, 0, 0, 0, 0)
-    assert ctypes.sizeof(eng.Options) == 40
+    assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter, opt.lengths, opt.dense_tensor,
+            opt.tensor_kind) == (eng.SCHED_INPLACE, eng.PATH_AUTO, 1, 0, 0, 0, 0, eng.TENSOR_AUTO)
+    assert ctypes.sizeof(eng.Options) == 48
 
 
 def test_batch_tuning_host_calls():

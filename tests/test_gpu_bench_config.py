@@ -5,7 +5,8 @@ on the tensor cores as a dense product (every K step issued, no tile skipping) o
 hierarchy of n = 16384 nodes (5000 classes, seed 0), for Query 1 and the subClassOf-only
 query. At that size one CTA runs about 55 output tiles of K = 65,536 in turn, so mbarrier
 phases and the accumulator hand-back carry across many tiles; these tests check every
-relation of that exact configuration against the oracle (Theorem 2: the closure is R_A)."""
+relation of that exact configuration against the oracle (Theorem 2: the closure is R_A), for
+each operand format of the tensor products (the default, E4M3 and E2M1)."""
 import numpy as np
 import pytest
 
@@ -23,11 +24,12 @@ def graph():
     return synth.hierarchy(N, CLASSES, seed=SEED)
 
 
+@pytest.mark.parametrize("kind", [eng.TENSOR_AUTO, eng.TENSOR_FP8, eng.TENSOR_FP4], ids=["auto", "fp8", "fp4"])
 @pytest.mark.parametrize("text", [synth.GRAMMAR_Q1, synth.GRAMMAR_QSC], ids=["Q1", "QSC"])
-def test_dense_tensor_jacobi_full_size(graph, text):
+def test_dense_tensor_jacobi_full_size(graph, text, kind):
     g = eng.Grammar(text, graph.labels)
     q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_TENSOR, schedule=eng.SCHED_JACOBI, dense_tensor=True,
-                  timeout_s=300.0)
+                  timeout_s=300.0, tensor_kind=kind)
     q.solve()
     ref = oracle.hellings(graph, text)
     for nm in g.names:

@@ -8,6 +8,9 @@ import paper_1707_01007_b300 as eng
 
 pytestmark = pytest.mark.gpu
 
+# operand formats of the tensor products: E4M3 bytes (kind::f8f6f4), E2M1 nibbles (kind::mxf4)
+KINDS = pytest.mark.parametrize("kind", [eng.TENSOR_FP8, eng.TENSOR_FP4], ids=["fp8", "fp4"])
+
 
 def tensor_parity(graph, text, **kw):
     kw.setdefault("timeout_s", 120.0)
@@ -24,10 +27,11 @@ def tensor_parity(graph, text, **kw):
     return g, q
 
 
+@KINDS
 @pytest.mark.parametrize("n,m", [(200, 3000), (256, 20000), (700, 30000)])
-def test_single_product(n, m):
+def test_single_product(n, m, kind):
     # S -> A B is one Boolean matrix product: exercises the GEMM, its K loop and epilogue
-    tensor_parity(synth.random_graph(n, m, 2, seed=n), "S A B\nA t0\nB t1\n")
+    tensor_parity(synth.random_graph(n, m, 2, seed=n), "S A B\nA t0\nB t1\n", tensor_kind=kind)
 
 
 def test_worked_example():
@@ -39,28 +43,31 @@ def test_worked_example_jacobi_iterations():
     assert q.stats()["iterations"] == 6
 
 
+@KINDS
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("schedule", [eng.SCHED_INPLACE, eng.SCHED_JACOBI])
 @pytest.mark.parametrize("dense", [False, True])
-def test_random(seed, schedule, dense):
+def test_random(seed, schedule, dense, kind):
     graph = synth.random_graph(90 + 61 * seed, 200 + 40 * seed, 3, seed=seed)
     text = synth.random_grammar_text(5, 3, 9, 6, seed % 3, seed=seed)
-    tensor_parity(graph, text, schedule=schedule, dense_tensor=dense)
+    tensor_parity(graph, text, schedule=schedule, dense_tensor=dense, tensor_kind=kind)
 
 
+@KINDS
 @pytest.mark.parametrize("n", [1100, 2600])
-def test_dense_closure(n):
-    tensor_parity(synth.random_graph(n, int(1.6 * n), 1, seed=n), "S S S\nS t0\n")
+def test_dense_closure(n, kind):
+    tensor_parity(synth.random_graph(n, int(1.6 * n), 1, seed=n), "S S S\nS t0\n", tensor_kind=kind)
 
 
 def test_two_cycles():
     tensor_parity(synth.two_cycles(17, 12), synth.GRAMMAR_C3)
 
 
+@KINDS
 @pytest.mark.parametrize("n,c", [(1024, 300), (4096, 1200)])
 @pytest.mark.parametrize("dense", [False, True])
-def test_hierarchy_q1(n, c, dense):
-    g, q = tensor_parity(synth.hierarchy(n, c, seed=1), synth.GRAMMAR_Q1, dense_tensor=dense)
+def test_hierarchy_q1(n, c, dense, kind):
+    g, q = tensor_parity(synth.hierarchy(n, c, seed=1), synth.GRAMMAR_Q1, dense_tensor=dense, tensor_kind=kind)
     s = q.stats()
     if dense:
         assert s["tensor_live_ops"] == s["dense_ops"]
@@ -68,9 +75,10 @@ def test_hierarchy_q1(n, c, dense):
         assert 0 < s["tensor_live_ops"] < 0.5 * s["dense_ops"]
 
 
+@KINDS
 @pytest.mark.parametrize("text", [synth.GRAMMAR_Q1, synth.GRAMMAR_QSC])
-def test_hierarchy_n16384(text):
-    tensor_parity(synth.hierarchy(16384, 5000, seed=0), text)
+def test_hierarchy_n16384(text, kind):
+    tensor_parity(synth.hierarchy(16384, 5000, seed=0), text, tensor_kind=kind)
 
 
 def test_useful_work_of_one_product():
@@ -99,25 +107,28 @@ def _block_edges(n, m, label, src_range, dst_range, seed):
     return np.stack([src, np.full_like(src, label), dst], axis=1)
 
 
+@KINDS
 @pytest.mark.parametrize("schedule", [eng.SCHED_JACOBI, eng.SCHED_INPLACE])
-def test_tile_skipping_issues_exactly_the_live_steps(schedule):
+def test_tile_skipping_issues_exactly_the_live_steps(schedule, kind):
     """S -> A B with A and B static: every execution multiplies the same operands, so the K
-    steps issued are (executions) x sum over output tiles (128 x 256) of the K slices (128) in
-    which A's tile and B^T's tile are both non-zero, counted here from the edge list."""
+    steps issued are (executions) x sum over output tiles (128 x 256) of the K steps in which
+    A's tile and B^T's tile are both non-zero, counted here from the edge list. An FP8 step is
+    one K slice of 128; an FP4 step two consecutive slices, live if either slice is."""
     n = 1024
     e = np.concatenate([_block_edges(n, 900, 0, (0, 400), (0, 520), 1),
                         _block_edges(n, 900, 1, (384, 1024), (0, 300), 2)])
     graph = synth.Graph(n=n, edges=e, labels=["t0", "t1"], meta={"kind": "test"})
-    g, q = tensor_parity(graph, "S A B\nA t0\nB t1\n", schedule=schedule)
-    occ_a = np.zeros((n // 128, n // 128), dtype=bool)   # (m-tile, K slice) of A
-    occ_b = np.zeros((n // 256, n // 128), dtype=bool)   # (n-tile, K slice) of B^T
+    g, q = tensor_parity(graph, "S A B\nA t0\nB t1\n", schedule=schedule, tensor_kind=kind)
+    step = 128 if kind == eng.TENSOR_FP8 else 256
+    occ_a = np.zeros((n // 128, n // step), dtype=bool)   # (m-tile, K step) of A
+    occ_b = np.zeros((n // 256, n // step), dtype=bool)   # (n-tile, K step) of B^T
     a_e, b_e = e[e[:, 1] == 0], e[e[:, 1] == 1]
-    occ_a[a_e[:, 0] // 128, a_e[:, 2] // 128] = True
-    occ_b[b_e[:, 2] // 256, b_e[:, 0] // 128] = True
+    occ_a[a_e[:, 0] // 128, a_e[:, 2] // step] = True
+    occ_b[b_e[:, 2] // 256, b_e[:, 0] // step] = True
     live = int((occ_a.astype(np.int64) @ occ_b.T.astype(np.int64)).sum())
     s = q.stats()
-    assert 0 < live < (n // 128) * (n // 256) * (n // 128)
-    assert s["tensor_live_ops"] == s["iterations"] * live * 2.0 * 128 * 256 * 128
+    assert 0 < live < (n // 128) * (n // 256) * (n // step)
+    assert s["tensor_live_ops"] == s["iterations"] * live * 2.0 * 128 * 256 * step
 
 
 def _middle_restricted_graph(n, m, positions, seed):
@@ -134,16 +145,20 @@ def _middle_restricted_graph(n, m, positions, seed):
     return synth.Graph(n=n, edges=np.concatenate([a, b]), labels=["t0", "t1"], meta={"kind": "test"})
 
 
+@KINDS
 @pytest.mark.parametrize("positions", [(0,), (1,), (2,), (0, 1, 2), (3,), (6,), (7,), (3, 4, 5, 6, 7)],
                          ids=lambda p: "q" + "".join(map(str, p)))
 @pytest.mark.parametrize("dense", [True, False])
-def test_operand_encoding_positions(positions, dense):
-    """The tensor product encodes a one at K position q of a byte group (bit q + 8r of a 32-bit
-    word) as the E4M3 byte 1 << q (q = 0, 1, 2 are the subnormals 2^-9, 2^-8, 2^-7) and q = 7
-    as 0x40 = 2.0; a product is non-zero iff its accumulator is. If the MMA flushed subnormal
-    inputs, or one position's encoding were wrong, the pairs whose only middle nodes sit at
-    those positions would be lost. Each case puts every middle node at the given positions
-    (530 nodes: several tiles and K stages plus a ragged tail) and compares with the oracle."""
+def test_operand_encoding_positions(positions, dense, kind):
+    """FP8: a one at K position q of a byte group (bit q + 8r of a 32-bit word) is the E4M3
+    byte 1 << q (q = 0, 1, 2 are the subnormals 2^-9, 2^-8, 2^-7) and q = 7 is 0x40 = 2.0.
+    FP4: a one at position s = q mod 4 of a nibble group (bit 4t + s) is the E2M1 nibble 1 << s
+    (s = 0 is the subnormal 0.5) and s = 3 is 0b0100 = 2.0. A product is non-zero iff its
+    accumulator is. If the MMA flushed subnormal inputs, or one position's encoding were wrong,
+    the pairs whose only middle nodes sit at those positions would be lost. Each case puts
+    every middle node at the given positions (530 nodes: several tiles and K stages plus a
+    ragged tail) and compares with the oracle."""
     graph = _middle_restricted_graph(530, 1500, set(positions), seed=sum(positions) + 31 * len(positions))
-    g, q = tensor_parity(graph, "S A B\nA t0\nB t1\n", schedule=eng.SCHED_JACOBI, dense_tensor=dense)
+    g, q = tensor_parity(graph, "S A B\nA t0\nB t1\n", schedule=eng.SCHED_JACOBI, dense_tensor=dense,
+                         tensor_kind=kind)
     assert q.count("S") > 300
