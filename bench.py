@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--tensor-kind", default="auto", choices=["auto", "fp8", "fp4"],
                     help="operand format of the tensor products: E4M3 bytes (kind::f8f6f4) or E2M1 nibbles "
                          "(kind::mxf4, unit scales); auto = the library's default (fp4)")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "rows"],
+                    help="with N > 1 ranks: replicas (every rank solves the whole workload, weak scaling) or "
+                         "rows (every query split into N row blocks, one per rank, new pairs exchanged by NCCL "
+                         "after each loop execution; strong scaling)")
     ap.add_argument("--no-alternatives", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
@@ -401,6 +405,65 @@ class Leg:
             q.close()
 
 
+class RowBlockLeg:
+    """The queries of the workload as row blocks of a sharded solve (Jacobi schedule, the
+    timed leg's product path). exchange=None: `parts` blocks of each query on this one device,
+    the records copied between them (shard.solve_local); otherwise this rank's block of each
+    query, the records all-gathered over the process group (shard.solve_sharded)."""
+
+    def __init__(self, eng, torch, graph, gs, path, stream, dense, kind, parts, rank=0, exchange=None):
+        from paper_1707_01007_b300 import shard
+
+        self.shard, self.torch, self.stream, self.exchange = shard, torch, stream, exchange
+        blocks = shard.row_blocks(graph.n, parts)
+        mine = range(len(blocks)) if exchange is None else [rank]
+        self.per_query = []
+        for g in gs:
+            bl = []
+            for r in mine:
+                b0, b1 = blocks[r]
+                q = eng.Query(g, graph.n, graph.edges, path=path, schedule=eng.SCHED_JACOBI, timeout_s=300.0,
+                              dense_tensor=dense, tensor_kind=kind_code(eng, kind), row_begin=b0, row_end=b1)
+                bl.append(shard.EngineBlock(q, b0, b1, len(g.names)))
+            self.per_query.append(bl)
+        self.executions = [self._solve(bl) for bl in self.per_query]
+        self.bufs = [torch.empty(max(1, bl[0].q.get_all_device(0, 0)) * 3, dtype=torch.int32, device="cuda")
+                     for bl in self.per_query]
+
+    def _solve(self, bl):
+        return self.shard.solve_local(bl) if self.exchange is None else self.shard.solve_sharded(bl[0], self.exchange)
+
+    def step(self):
+        # every query's closure, then every relation of it extracted into device memory
+        for bl, buf in zip(self.per_query, self.bufs):
+            self._solve(bl)
+            bl[0].q.get_all_device(buf.data_ptr(), buf.numel() // 3)
+
+    @property
+    def qs(self):
+        return [bl[0].q for bl in self.per_query]
+
+    def time(self, steps):
+        torch = self.torch
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(self.stream)
+        for i in range(steps):
+            self.step()
+            ev[i + 1].record(self.stream)
+        torch.cuda.synchronize()
+        self.step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        return ev[0].elapsed_time(ev[steps]) / steps
+
+    def relations(self):
+        return [{nm: bl[0].q.get(nm) for nm in bl[0].q.grammar.names} for bl in self.per_query]
+
+    def close(self):
+        for bl in self.per_query:
+            for b in bl:
+                b.q.close()
+
+
 def engine_arm(args):
     import torch
     import torch.distributed as dist
@@ -432,7 +495,15 @@ def engine_arm(args):
     ops_per_step = products * 2.0 * float(N_NODES) ** 3
 
     dense = args.tensor == "dense"
-    main = Leg(eng, torch, graph, gs, path, schedule, stream, dense, args.tensor_kind)
+    sharded = world > 1 and args.shard == "rows"
+    if sharded:
+        # every query split into `world` row blocks, this rank's block here; NCCL all-gathers
+        # the new pairs after each loop execution (Jacobi schedule)
+        from paper_1707_01007_b300 import shard as shardmod
+        main = RowBlockLeg(eng, torch, graph, gs, path, stream, dense, args.tensor_kind, world, rank,
+                           shardmod.TorchExchange("cuda"))
+    else:
+        main = Leg(eng, torch, graph, gs, path, schedule, stream, dense, args.tensor_kind)
     for _ in range(args.warmup):
         main.step()
     st = [q.stats() for q in main.qs]
@@ -450,17 +521,20 @@ def engine_arm(args):
     clk = clocks.stop()
     ms = max_over_ranks(ms)
     step_ms = {"best": min(main.step_ms), "median": float(np.median(main.step_ms)), "worst": max(main.step_ms)}
-    value = job_rate(ops_per_step, ms / 1e3, world) / 1e9
+    # replicas: every rank's workload counts; row blocks: the ranks solve one workload together
+    value = (ops_per_step / (ms / 1e3) if sharded else job_rate(ops_per_step, ms / 1e3, world)) / 1e9
     executed_dense = sum(s["dense_ops"] for s in st)
     results = {f"{label}:{g.names[0]}": q.count(g.names[0]) for (label, _), g, q in zip(grammars, gs, main.qs)}
     # every relation of the timed leg, for the check against the oracle below
     timed_pairs = [{nm: q.get(nm) for nm in g.names} for g, q in zip(gs, main.qs)]
     main.close()
+    if sharded:
+        dist.barrier()
     parity = check_against_oracle(graph, grammars, timed_pairs)
 
     # the same closure with the other schedules / product paths (exact results in all)
     alternatives = {}
-    if not args.no_alternatives:
+    if not args.no_alternatives and not sharded:
         for name, (pth, sch, dns) in {"tensor_tile_skip": (eng.PATH_TENSOR, eng.SCHED_JACOBI, False),
                                       "tensor_inplace": (eng.PATH_TENSOR, eng.SCHED_INPLACE, True),
                                       "tensor_inplace_tile_skip": (eng.PATH_TENSOR, eng.SCHED_INPLACE, False),
@@ -481,6 +555,23 @@ def engine_arm(args):
                 alternatives[name]["roofline_executed"] = {k: r.get(k) for k in
                                                            ("achieved", "peak", "unit", "frac", "launches", "launch_ms")}
 
+    if not args.no_alternatives and world == 1 and schedule == eng.SCHED_JACOBI and path != eng.PATH_WORKLIST:
+        # the timed solve as two row blocks of a sharded solve, both on this device: the same
+        # products split by rows, plus the per-execution export and import of the new pairs
+        rb = RowBlockLeg(eng, torch, graph, gs, path, stream, dense, args.tensor_kind, 2)
+        rbs = rb.time(max(2, min(args.steps, 3)))
+        same = all(set(a) == set(b) and all(np.array_equal(a[k], b[k]) for k in a)
+                   for a, b in zip(rb.relations(), timed_pairs))
+        alternatives["row_blocks_2_one_gpu"] = {
+            "ms_per_step": rbs, "value": ops_per_step / (rbs / 1e3) / 1e9, "executions": rb.executions,
+            "relations_equal_timed_leg": bool(same),
+            "note": "each query split into 2 row blocks (contexts), both on this GPU, new pairs exchanged as "
+                    "records after every loop execution; the multi-GPU form runs one block per rank (NCCL)"}
+        rb.close()
+        if not same:
+            print("bench: the row-block solve differs from the timed leg", file=sys.stderr)
+            sys.exit(3)
+
     # e2e through the C ABI with host buffers: create (edge upload), solve, copy triples back
     h2d = graph.n_edges * 12 * len(grammars)
     d2h = 0
@@ -489,6 +580,13 @@ def engine_arm(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         d2h = 0
+        if sharded:  # this rank's row blocks created, the sharded solve, the whole closure copied back
+            leg = RowBlockLeg(eng, torch, graph, gs, path, stream, dense, args.tensor_kind, world, rank,
+                              shardmod.TorchExchange("cuda"))
+            for q in leg.qs:
+                d2h += q.triples_all().shape[0] * 12
+            leg.close()
+            continue
         for g in gs:
             q = eng.Query(g, graph.n, graph.edges, path=path, schedule=schedule, timeout_s=300.0, dense_tensor=dense,
                           tensor_kind=kind_code(eng, args.tensor_kind))
@@ -498,14 +596,14 @@ def engine_arm(args):
             q.close()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_s = max_over_ranks(e2e_s)
-    e2e_val = job_rate(ops_per_step, e2e_s, world) / 1e9
+    e2e_val = (ops_per_step / e2e_s if sharded else job_rate(ops_per_step, e2e_s, world)) / 1e9
 
     roof = roofline(eng, graph, gs, path, schedule, stream, dense, sm_mhz=clk.get("sm_mhz"), tkind=args.tensor_kind)
 
     # the default path of cfpq_solve (automatic product choice, in-place schedule): its
     # dominant kernels' roofline and its own end-to-end figure
     default_path = None
-    if not args.no_alternatives:
+    if not args.no_alternatives and not sharded:
         droof = roofline(eng, graph, gs, eng.PATH_AUTO, eng.SCHED_INPLACE, stream, dense=False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -529,14 +627,14 @@ def engine_arm(args):
     line = {
         "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "step_ms_this_rank": step_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None,
         "dtype": ("fp4e2m1" if effective_kind(args.tensor_kind) == "fp4" else "fp8e4m3") +
                  " 0/1 operands, f32 accumulate (tensor path); u32 bit-packed storage",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_NODES, "classes": N_CLASSES, "seed": SEED,
                    "grammars": [nm for nm, _ in grammars], "path": args.path, "schedule": args.schedule,
                    "tensor_products": args.tensor, "tensor_kind": effective_kind(args.tensor_kind),
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"row blocks x{world} (NCCL exchange)" if sharded else f"replicas x{world}",
                    "l2": "inputs larger than L2 (per query 3 x 7 x 32 MiB bit planes + 7 x 32 MiB transposes)",
                    "products_per_step": products, "dense_ops_executed_per_step": executed_dense,
                    "iterations": [s["iterations"] for s in st], "results_start_symbol": results},

@@ -134,6 +134,13 @@ typedef struct {
                                  product as written. Both give the same result */
     int32_t tensor_kind;      /* enum cfpq_tensor_kind: operand format of the tensor-core products;
                                  default AUTO. Every kind gives the same result */
+    uint32_t row_begin;       /* row block of a sharded solve (cfpq_block_*): the products of this
+                                 context compute rows [row_begin, row_end) of every T_A. Both 0
+                                 (default): every row, an ordinary context. Otherwise row_begin is
+                                 a multiple of 256 and below row_end, and row_end is a multiple of
+                                 256 or equal to n; needs schedule JACOBI (AUTO is taken as
+                                 JACOBI), a matrix path (not WORKLIST) and no lengths */
+    uint32_t row_end;
 } cfpq_options;
 
 typedef struct {
@@ -197,8 +204,9 @@ int cfpq_create(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, s
  * closure loop until an iteration adds no pair. May be called again; each call starts
  * from the edges. Blocks until the fixpoint is reached (or a limit hits).
  *   stream  a cudaStream_t to run on, or NULL for the context's own stream
- * Errors: ITER_LIMIT, TIMEOUT, CUDA, UNSUPPORTED. After ITER_LIMIT or TIMEOUT the partial
- * closure is still readable with cfpq_get (it is a subset of the result).
+ * Errors: INVALID (NULL, or a row-block context of a sharded solve: see cfpq_block_start),
+ * ITER_LIMIT, TIMEOUT, CUDA, UNSUPPORTED. After ITER_LIMIT or TIMEOUT the partial closure is
+ * still readable with cfpq_get (it is a subset of the result).
  */
 int cfpq_solve(cfpq_ctx *ctx, void *stream);
 
@@ -260,6 +268,55 @@ int cfpq_get_lengths(cfpq_ctx *ctx, int32_t A, cfpq_triple *buf, uint32_t *lengt
 int cfpq_get_path(cfpq_ctx *ctx, int32_t A, uint32_t m, uint32_t n, uint32_t *nodes, int32_t *labels, size_t cap,
                   size_t *len);
 
+/*
+ * Sharded solve by row blocks. The paper's remark on parallelism (Section 7) is that the
+ * matrix products of one loop execution may run on different GPUs independently. Here each
+ * rank owns a block of rows: a context created with options.row_begin / row_end computes
+ * rows [row_begin, row_end) of every product T_B x T_C, which needs those rows of T_B and all
+ * of T_C, so every rank keeps all of T. After the products of an execution the ranks
+ * exchange the new pairs of their rows, and every rank merges all of them (Algorithm 1's
+ * loop body, Jacobi schedule: T_{k+1} = T_k u T_k x T_k). By induction every rank then holds
+ * the same T_k after k executions, the loop stops on all ranks at the same execution, and
+ * the result (read with cfpq_get and the other read-out calls) is the closure of Theorem 2.
+ * The calls, in the order of one solve:
+ *   cfpq_block_start     matrix initialisation from all edges (Algorithm 1, before the loop)
+ *   then, per loop execution:
+ *   cfpq_block_products  the products of the next execution, over the context's rows only
+ *   cfpq_block_export    the new pairs of the context's rows as records, for the other ranks
+ *   cfpq_block_import    (once per other rank) their records, ORed in as new pairs
+ *   cfpq_block_finish    merge and end of the execution; *changed = 1 if the loop continues
+ * until cfpq_block_finish reports *changed = 0. How the records travel between the ranks
+ * (NCCL or any other transport) is the caller's; the library only packs and unpacks them.
+ * A record is 2 + W 32-bit words: the non-terminal id, the row i, then the W = n_pad / 32
+ * words of the row's new pairs (bit j of word j / 32 at bit j % 32); records come in no
+ * particular order and importing is order-independent (an OR).
+ * Each call runs on `stream` (NULL: the context's stream).
+ */
+/* Matrix initialisation of a sharded solve (every edge, all rows). Errors: INVALID (NULL,
+ * or a context without a row block), CUDA. */
+int cfpq_block_start(cfpq_ctx *ctx, void *stream);
+/* The products of the next loop execution over the context's rows (asynchronous; nothing
+ * is read back). Errors: INVALID, NOT_SOLVED (no cfpq_block_start since the last finished
+ * solve), CUDA. */
+int cfpq_block_products(cfpq_ctx *ctx, void *stream);
+/* Packs the pairs that this execution's products added to the context's rows into buf
+ * (device memory, cap_words 32-bit words) as records of 2 + W words and sets *words (host)
+ * to the words written; returns after the packing is complete. At most (row_end -
+ * row_begin) * n_nonterm records. Errors: INVALID, NOT_SOLVED, BUFFER (cap_words too small:
+ * *words is the size needed, buf's contents undefined), CUDA. */
+int cfpq_block_export(cfpq_ctx *ctx, uint32_t *buf, size_t cap_words, size_t *words, void *stream);
+/* ORs another rank's records (device memory, words 32-bit words as cfpq_block_export wrote
+ * them) into this execution's new pairs (asynchronous). Errors: INVALID (words not a
+ * multiple of 2 + W, buf NULL with words > 0), NOT_SOLVED, CUDA; a record naming a
+ * non-terminal or row out of range is skipped and makes cfpq_block_finish return INVALID. */
+int cfpq_block_import(cfpq_ctx *ctx, const uint32_t *buf, size_t words, void *stream);
+/* Merges this execution's new pairs (the context's own and the imported ones) into T and
+ * ends the execution; *changed (host) = 1 if some rank added a pair, so the loop goes on,
+ * 0 when the closure is complete (the context then counts as solved). Synchronises the
+ * stream. Errors: INVALID (NULL, or an imported record out of range), NOT_SOLVED,
+ * ITER_LIMIT, TIMEOUT, CUDA. */
+int cfpq_block_finish(cfpq_ctx *ctx, void *stream, int32_t *changed);
+
 /* |R_A| without copying pairs (for the start symbol, the #results column of the tables of
  * Section 6, diagonal pairs included). Errors: as cfpq_get. */
 int cfpq_count(cfpq_ctx *ctx, int32_t A, size_t *count);
@@ -308,7 +365,8 @@ void cfpq_grammar_free(cfpq_parsed_grammar *pg);
  * smallest positive timeout_s among the contexts limits the whole launch (checked on the
  * device after every round; the contexts are then left unsolved). Contexts created with
  * options.lengths are not taken (UNSUPPORTED). Errors: INVALID, NOMEM,
- * CUDA, UNSUPPORTED (no cooperative launch; a lengths context), TIMEOUT (the launch's wall-clock limit passed
+ * CUDA, UNSUPPORTED (no cooperative launch; a lengths context), INVALID (also: a row-block
+ * context), TIMEOUT (the launch's wall-clock limit passed
  * or a bounded grid barrier gave up), ITER_LIMIT (some context hit its cap; the others are
  * still complete).
  */

@@ -59,7 +59,8 @@ class Triple(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("path", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("timeout_s", ctypes.c_double),
-                ("lengths", ctypes.c_int32), ("dense_tensor", ctypes.c_int32), ("tensor_kind", ctypes.c_int32)]
+                ("lengths", ctypes.c_int32), ("dense_tensor", ctypes.c_int32), ("tensor_kind", ctypes.c_int32),
+                ("row_begin", ctypes.c_uint32), ("row_end", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -175,6 +176,11 @@ SIGNATURES = {
     "cfpq_server_destroy": (None, [_VP]),
     "cfpq_extract_pairs_noalloc": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                   ctypes.c_int32, _VP, ctypes.c_size_t, _P(ctypes.c_size_t), _VP]),
+    "cfpq_block_start": (ctypes.c_int, [_VP, _VP]),
+    "cfpq_block_products": (ctypes.c_int, [_VP, _VP]),
+    "cfpq_block_export": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _P(ctypes.c_size_t), _VP]),
+    "cfpq_block_import": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _VP]),
+    "cfpq_block_finish": (ctypes.c_int, [_VP, _VP, _P(ctypes.c_int32)]),
 }
 EXPORTS = sorted(SIGNATURES)
 
@@ -248,7 +254,8 @@ class Query:
 
     def __init__(self, grammar: Grammar, n: int, edges, schedule: int = SCHED_INPLACE, path: int = PATH_AUTO,
                  use_graph: bool = True, max_iter: int = 0, timeout_s: float = 0.0, profile: bool = False,
-                 lengths: bool = False, dense_tensor: bool = False, tensor_kind: int = TENSOR_AUTO):
+                 lengths: bool = False, dense_tensor: bool = False, tensor_kind: int = TENSOR_AUTO,
+                 row_begin: int = 0, row_end: int = 0):
         self.grammar = grammar
         self.n = int(n)
         self._h = None
@@ -260,6 +267,7 @@ class Query:
         opt.lengths = int(bool(lengths))
         opt.dense_tensor = int(bool(dense_tensor))
         opt.tensor_kind = int(tensor_kind)
+        opt.row_begin, opt.row_end = int(row_begin), int(row_end)
         rec = _edges_struct(edges)
         h = ctypes.c_void_p()
         ptr = rec.ctypes.data_as(ctypes.POINTER(Edge)) if rec.size else None
@@ -357,6 +365,42 @@ class Query:
         _check(_lib().cfpq_get_all_device(self._h, ctypes.c_void_p(dev_ptr) if dev_ptr else None, cap,
                                           ctypes.byref(c)), "cfpq_get_all_device")
         return int(c.value)
+
+    # sharded solve by row blocks (contexts created with row_begin / row_end): the calls of
+    # cfpq_block_*; the exchange between them is the caller's (see shard.py)
+    @property
+    def record_words(self) -> int:
+        """32-bit words of one exchange record: non-terminal, row, then the row's n_pad / 32 words."""
+        return 2 + ((self.n + 255) // 256 * 256) // 32
+
+    def block_start(self, stream=None):
+        _check(_lib().cfpq_block_start(self._h, _stream_handle(stream)), "cfpq_block_start")
+
+    def block_products(self, stream=None):
+        _check(_lib().cfpq_block_products(self._h, _stream_handle(stream)), "cfpq_block_products")
+
+    def block_export(self, dev_ptr: int, cap_words: int, stream=None) -> int:
+        """Packs this execution's new pairs of the context's rows into device memory; returns the
+        words written (CfpqError ERR_BUFFER, with .words set, if cap_words is too small)."""
+        w = ctypes.c_size_t()
+        code = _lib().cfpq_block_export(self._h, ctypes.c_void_p(dev_ptr) if dev_ptr else None, cap_words,
+                                        ctypes.byref(w), _stream_handle(stream))
+        if code == ERR_BUFFER:
+            err = CfpqError(code, "cfpq_block_export")
+            err.words = int(w.value)
+            raise err
+        _check(code, "cfpq_block_export")
+        return int(w.value)
+
+    def block_import(self, dev_ptr: int, words: int, stream=None):
+        _check(_lib().cfpq_block_import(self._h, ctypes.c_void_p(dev_ptr) if dev_ptr else None, words,
+                                        _stream_handle(stream)), "cfpq_block_import")
+
+    def block_finish(self, stream=None) -> bool:
+        """Ends the execution; True if the loop goes on."""
+        ch = ctypes.c_int32()
+        _check(_lib().cfpq_block_finish(self._h, _stream_handle(stream), ctypes.byref(ch)), "cfpq_block_finish")
+        return bool(ch.value)
 
     def stats(self) -> dict:
         s = Stats()

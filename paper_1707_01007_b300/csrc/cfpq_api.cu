@@ -47,7 +47,7 @@ __device__ __forceinline__ void scan_rows(const QDesc &q, uint64_t item, uint32_
             cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
             if (__ldcg(&st->dcount[par][C]) != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
         }
-        cand &= rows_in_word(q.n, wq);
+        cand &= rows_in_word(q.n, wq) & rows_of_block(q, wq);
     }
     const uint32_t cnt = (uint32_t)__popc(cand) * nch;
     uint32_t incl = cnt;
@@ -317,6 +317,91 @@ __global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int u
 
 
 __global__ void k_arm_deadline(DevState *st, unsigned long long dt_ns) { st->deadline_ns = globaltimer_ns() + dt_ns; }
+
+// --- sharded solve by row blocks: the exchange of one loop execution's new pairs ---
+
+// Records of the pairs that this execution's products added to the context's rows: a record is
+// [A, i, the W words of row i of N_A]. One warp per (non-terminal, row word of 32 rows) of the
+// block; the word of the new delta's row bitmap flags the rows to pack. Records beyond
+// cap_records are counted but not written.
+__global__ void __launch_bounds__(256) k_block_pack(const QDesc *qd, uint32_t *out, uint64_t cap_records) {
+    const QDesc &q = *qd;
+    DevState *st = q.st;
+    const uint32_t parity = (uint32_t)(st->iter & 1ull);
+    const uint32_t *NR = parity ? q.R0 : q.R1;
+    const uint32_t *N = parity ? q.X0 : q.X1;
+    const uint32_t W = q.W, rec_words = 2u + W;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t w0 = q.row0 / 32u, nw = (min(q.row1, q.n) + 31u) / 32u - w0;  // row words of the block
+    for (uint64_t u = gwarp; u < (uint64_t)q.n_nt * nw; u += gwarps) {
+        const int a = (int)(u / nw);
+        const uint32_t wq = w0 + (uint32_t)(u % nw);
+        uint32_t rows = __ldcg(NR + (uint64_t)a * W + wq) & rows_in_word(q.n, wq);
+        while (rows) {
+            const uint32_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+            rows &= rows - 1;
+            unsigned long long slot = 0;
+            if (lane == 0) slot = atomicAdd(&st->block_records, 1ull);
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (slot >= cap_records) continue;
+            uint32_t *rec = out + slot * rec_words;
+            if (lane == 0) {
+                rec[0] = (uint32_t)a;
+                rec[1] = i;
+            }
+            const uint32_t *row = N + (uint64_t)a * q.plane + (uint64_t)i * W;
+            for (uint32_t w = lane; w < W; w += 32u) rec[2 + w] = __ldcg(row + w);
+        }
+    }
+}
+
+// Another rank's records ORed into this execution's new pairs, as a product epilogue adds
+// them (delta plane, its row bitmap, the counts and change flags), so that the merge and the
+// next execution treat them like the context's own. One warp per record.
+__global__ void __launch_bounds__(256) k_block_import(const QDesc *qd, const uint32_t *in, uint64_t n_records) {
+    const QDesc &q = *qd;
+    DevState *st = q.st;
+    const uint32_t parity = (uint32_t)(st->iter & 1ull);
+    uint32_t *NR = parity ? q.R0 : q.R1;
+    uint32_t *N = parity ? q.X0 : q.X1;
+    const uint32_t W = q.W, rec_words = 2u + W;
+    const int lane = threadIdx.x & 31;
+    const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r = gwarp; r < n_records; r += gwarps) {
+        const uint32_t *rec = in + r * rec_words;
+        const uint32_t a = __ldcg(rec), i = __ldcg(rec + 1);
+        if (a >= (uint32_t)q.n_nt || i >= q.n) {
+            if (lane == 0) st->block_bad = 1u;
+            continue;
+        }
+        uint32_t *row = N + (uint64_t)a * q.plane + (uint64_t)i * W;
+        unsigned cnt = 0;
+        for (uint32_t w = lane; w < W; w += 32u) {
+            const uint32_t x = __ldcg(rec + 2 + w);
+            if (!x) continue;
+            const uint32_t old = __ldcg(row + w);
+            const uint32_t nwv = x & ~old;
+            if (nwv) {
+                row[w] = old | nwv;
+                cnt += __popc(nwv);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt) {
+            atomicOr(&NR[(uint64_t)a * W + (i >> 5)], 1u << (i & 31));
+            atomicAdd(&st->dcount[parity ^ 1u][a], (unsigned long long)cnt);
+            atomicAdd(&st->tcount[a], (unsigned long long)cnt);
+            atomicAdd(&st->new_bits, (unsigned long long)cnt);
+            st->changed = 1u;
+            st->dirty[a] = 1u;
+            st->odirty[a] = 1u;
+        }
+    }
+}
 
 // --- extraction: popc per row -> exclusive scan -> emit (A, m, n) in row-major order ---
 
@@ -639,11 +724,20 @@ static int enqueue_auto_tensor_graph(cfpq_ctx *c, cudaStream_t s) {
     return end_branch(c->aux_stream, rc);
 }
 
-// One loop execution (the body of Algorithm 1's while loop). In profile mode, CUDA events
-// bracket every tensor-product launch (one pair per group) and the gather products of the
-// execution (one pair).
+// One loop execution (the body of Algorithm 1's while loop): the products, then the merge and
+// the end of the execution. In profile mode, CUDA events bracket every tensor-product launch
+// (one pair per group) and the gather products of the execution (one pair).
+static int enqueue_products(cfpq_ctx *c, cudaStream_t s, int use_handle);
+static int enqueue_iteration_end(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle);
+
 int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
     c->iter_launches = 0;
+    const int rc = enqueue_products(c, s, use_handle);
+    if (rc != CFPQ_OK) return rc;
+    return enqueue_iteration_end(c, s, h, use_handle);
+}
+
+static int enqueue_products(cfpq_ctx *c, cudaStream_t s, int use_handle) {
     const bool prof = c->profile && !use_handle;
     if (c->auto_mixed) {
         // choose per group; in a graph the chosen tensor products run under conditional
@@ -688,6 +782,11 @@ int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h,
         if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 1], s));
         if (rc != CFPQ_OK) return rc;
     }
+    return CFPQ_OK;
+}
+
+static int enqueue_iteration_end(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
+    const bool prof = c->profile && !use_handle;
     const uint32_t word_blocks = (uint32_t)((uint64_t)c->n_nt * ((c->n + 31) / 32));  // one per (A, row word)
     if (c->lengths) {  // before the merge: T still holds the previous execution's matrices
         if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 2], s));
@@ -937,6 +1036,15 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     c->lengths = o.lengths != 0;
     c->dense_tensor = o.dense_tensor != 0;
     c->tensor_kind = o.tensor_kind == CFPQ_TENSOR_FP8 ? CFPQ_TENSOR_FP8 : CFPQ_TENSOR_FP4;
+    c->block = o.row_begin != 0 || o.row_end != 0;
+    c->row0 = c->block ? o.row_begin : 0u;
+    c->row1 = (!c->block || o.row_end == n) ? c->n_pad : o.row_end;
+    if (c->block) {
+        // a row block of a sharded solve: Algorithm 1's Jacobi loop body, on a matrix path
+        if (o.schedule == CFPQ_SCHED_INPLACE || o.path == CFPQ_PATH_WORKLIST || c->lengths)
+            return CFPQ_ERR_UNSUPPORTED;
+        c->schedule = CFPQ_SCHED_JACOBI;
+    }
     if (c->lengths) {
         // the lengths come from the matrices before each loop execution: Jacobi schedule only
         if (o.schedule == CFPQ_SCHED_INPLACE || o.path == CFPQ_PATH_WORKLIST) return CFPQ_ERR_UNSUPPORTED;
@@ -1112,6 +1220,8 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.Tsum = c->d_Tsum;
     q.TTsum = c->d_TTsum;
     q.SW = c->SW;
+    q.row0 = c->row0;
+    q.row1 = c->row1;
     q.rules = c->d_rules;
     q.gstart = c->d_gstart;
     q.nt_rules = c->d_nt_rules;
@@ -1165,6 +1275,11 @@ int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edge
         if ((opt->lengths != 0 && opt->lengths != 1) || (opt->dense_tensor != 0 && opt->dense_tensor != 1))
             return CFPQ_ERR_INVALID;
         if (opt->tensor_kind < CFPQ_TENSOR_AUTO || opt->tensor_kind > CFPQ_TENSOR_FP4) return CFPQ_ERR_INVALID;
+        if (opt->row_begin != 0 || opt->row_end != 0) {  // a row block: 256-aligned ends inside [0, n]
+            if (opt->row_begin % 256u != 0 || opt->row_begin >= opt->row_end || opt->row_end > n ||
+                (opt->row_end % 256u != 0 && opt->row_end != n))
+                return CFPQ_ERR_INVALID;
+        }
     }
     return CFPQ_OK;
 }
@@ -1257,7 +1372,7 @@ extern "C" int cfpq_create(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edg
 }
 
 extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
-    if (!c) return CFPQ_ERR_INVALID;
+    if (!c || c->block) return CFPQ_ERR_INVALID;  // a row block is solved with the cfpq_block_* calls
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     c->solved = false;
     c->last_stream = s;
@@ -1296,6 +1411,95 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
     c->stats.schedule = c->schedule;
     c->stats.gather_cpl = 0;
     c->solved = true;
+    return rc;
+}
+
+extern "C" int cfpq_block_start(cfpq_ctx *c, void *stream) {
+    if (!c || !c->block) return CFPQ_ERR_INVALID;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    c->solved = false;
+    c->last_stream = s;
+    c->stats.product_ms = c->stats.tensor_ms = c->stats.lengths_ms = 0.0;
+    c->stats.product_launches = c->stats.tensor_launches = c->stats.lengths_launches = 0;
+    CK(cudaEventRecord(c->ev0, s));
+    const int rc = enqueue_reset_and_seed(c, s);
+    if (rc != CFPQ_OK) return rc;
+    c->block_started = true;
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_block_products(cfpq_ctx *c, void *stream) {
+    if (!c || !c->block) return CFPQ_ERR_INVALID;
+    if (!c->block_started) return CFPQ_ERR_NOT_SOLVED;
+    if (c->n_groups == 0) return CFPQ_OK;  // no binary productions: nothing to multiply
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    c->last_stream = s;
+    c->iter_launches = 0;
+    return enqueue_products(c, s, 0);
+}
+
+extern "C" int cfpq_block_export(cfpq_ctx *c, uint32_t *buf, size_t cap_words, size_t *words, void *stream) {
+    if (!c || !c->block || !words || (!buf && cap_words > 0)) return CFPQ_ERR_INVALID;
+    if (!c->block_started) return CFPQ_ERR_NOT_SOLVED;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const uint64_t rec_words = 2u + c->W;
+    unsigned long long records = 0;
+    if (c->n_groups > 0) {
+        CK(cudaMemsetAsync(&c->d_state->block_records, 0, sizeof(unsigned long long), s));
+        const uint32_t units = (uint32_t)((uint64_t)c->n_nt * ((std::min(c->row1, c->n) + 31u) / 32u - c->row0 / 32u));
+        k_block_pack<<<std::min<uint32_t>(std::max<uint32_t>(1u, (units + 7u) / 8u), 8u * (uint32_t)c->sms), 256, 0,
+                       s>>>(c->d_q, buf, buf ? (uint64_t)(cap_words / rec_words) : 0ull);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&records, &c->d_state->block_records, sizeof(records), cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    *words = (size_t)(records * rec_words);
+    return records * rec_words > cap_words ? CFPQ_ERR_BUFFER : CFPQ_OK;
+}
+
+extern "C" int cfpq_block_import(cfpq_ctx *c, const uint32_t *buf, size_t words, void *stream) {
+    if (!c || !c->block || (!buf && words > 0)) return CFPQ_ERR_INVALID;
+    if (!c->block_started) return CFPQ_ERR_NOT_SOLVED;
+    const uint64_t rec_words = 2u + c->W;
+    if (words % rec_words != 0) return CFPQ_ERR_INVALID;
+    if (words == 0 || c->n_groups == 0) return CFPQ_OK;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const uint64_t n_records = words / rec_words;
+    k_block_import<<<(uint32_t)std::min<uint64_t>((n_records + 7u) / 8u, 8ull * (uint64_t)c->sms), 256, 0, s>>>(
+        c->d_q, buf, n_records);
+    CK(cudaGetLastError());
+    return CFPQ_OK;
+}
+
+extern "C" int cfpq_block_finish(cfpq_ctx *c, void *stream, int32_t *changed) {
+    if (!c || !c->block || !changed) return CFPQ_ERR_INVALID;
+    if (!c->block_started) return CFPQ_ERR_NOT_SOLVED;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    int rc;
+    if (c->n_groups == 0) {
+        k_tail<<<1, 1024, 0, s>>>(c->d_q, 0, 0, nullptr);
+        c->iter_launches = 1;
+        CK(cudaGetLastError());
+    } else if ((rc = enqueue_iteration_end(c, s, 0, 0)) != CFPQ_OK) {
+        return rc;
+    }
+    CK(cudaEventRecord(c->ev1, s));
+    DevState st;
+    CK(cudaMemcpyAsync(&st, c->d_state, sizeof(st), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    rc = apply_status(c, st);
+    if (st.block_bad) rc = CFPQ_ERR_INVALID;
+    *changed = (rc == CFPQ_OK && st.cont) ? 1 : 0;
+    if (!*changed) {
+        // the solve ended (converged, or a limit or an error): the relations are readable
+        c->block_started = false;
+        c->solved = true;
+        c->clean = rc == CFPQ_OK;
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        c->stats.solve_ms = ms;
+        c->stats.schedule = c->schedule;
+    }
     return rc;
 }
 

@@ -699,7 +699,7 @@ static int solve_batch_with(cfpq_ctx *const *ctxs, int k, cudaStream_t s, const 
 static int check_batch_args(cfpq_ctx *const *ctxs, int32_t k) {
     if (!ctxs || k <= 0 || k > kMaxBatch) return CFPQ_ERR_INVALID;
     for (int j = 0; j < k; j++)
-        if (!ctxs[j]) return CFPQ_ERR_INVALID;
+        if (!ctxs[j] || ctxs[j]->block) return CFPQ_ERR_INVALID;  // a row block is solved with cfpq_block_*
     for (int j = 0; j < k; j++)
         if (ctxs[j]->lengths) return CFPQ_ERR_UNSUPPORTED;  // the grouped launch keeps no length planes
     return CFPQ_OK;

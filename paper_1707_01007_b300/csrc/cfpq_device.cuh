@@ -66,6 +66,8 @@ struct DevState {
     unsigned long long tc_live_steps;   // K steps the tensor-core products issued (after tile skipping)
     unsigned int plan_count[kMaxNT][2]; // tile skipping: live output tiles listed for group g, by execution parity
     unsigned int plan_take[kMaxNT][2];  // tile skipping: listed tiles already claimed by a CTA
+    unsigned long long block_records;   // sharded solve: records packed by the last export
+    unsigned int block_bad;             // sharded solve: an imported record was out of range
 };
 
 struct Rule {
@@ -85,6 +87,8 @@ struct QDesc {
     uint32_t *Tsum;                     // word summary of T (NULL in batched launches)
     uint32_t *TTsum;                    // word summary of TT (NULL unless lengths are kept)
     uint32_t SW;                        // summary words per row (a multiple of 4)
+    uint32_t row0, row1;                // rows the products compute: [row0, row1) (0, n_pad: all;
+                                        // a sharded solve's row block, multiples of 256)
     const Rule *rules;                  // sorted by lhs; group g = rules[gstart[g] .. gstart[g+1])
     const int32_t *gstart;
     const int2 *nt_rules;               // per non-terminal A: its productions rules[x .. y) (-1, -1: none)
@@ -107,6 +111,12 @@ __device__ __forceinline__ unsigned ld_u32(const unsigned *p) { return __ldcg(p)
 __device__ __forceinline__ uint32_t rows_in_word(uint32_t n, uint32_t wq) {
     const uint32_t left = n - wq * 32u;
     return left >= 32u ? 0xFFFFFFFFu : ((1u << left) - 1u);
+}
+
+// Rows of row word wq that the query's products compute (its row block [row0, row1), whose
+// ends are multiples of 32).
+__device__ __forceinline__ uint32_t rows_of_block(const QDesc &q, uint32_t wq) {
+    return (wq * 32u >= q.row0 && wq * 32u < q.row1) ? 0xFFFFFFFFu : 0u;
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

@@ -218,17 +218,20 @@ __device__ __forceinline__ uint32_t live_steps(const QDesc &q, int B, int C, uin
         return (x | (x >> 1)) & 0x55555555u;
 }
 
+// Output tiles of a product: every N tile of the rows the query computes ([row0, row1)).
+__device__ __forceinline__ uint32_t output_tiles(const QDesc &q) { return (q.n_pad / BN) * ((q.row1 - q.row0) / BM); }
+
 // Origin of output tile t of a product (grouped rasterisation: consecutive tiles sweep the M
 // tiles of a band of RASTER_N N tiles, so CTAs running at the same time touch about RASTER_N
 // right-operand tile columns, which stay in L2).
 __device__ __forceinline__ void tile_origin(const QDesc &q, uint32_t t, uint32_t &m0, uint32_t &n0) {
-    const uint32_t n_tiles = q.n_pad / BN, m_tiles = q.n_pad / BM;
+    const uint32_t n_tiles = q.n_pad / BN, m_tiles = (q.row1 - q.row0) / BM;
     const uint32_t band = t / (RASTER_N * m_tiles);
     const uint32_t first_n = band * RASTER_N;
     const uint32_t width = min((uint32_t)RASTER_N, n_tiles - first_n);
     const uint32_t local = t - band * RASTER_N * m_tiles;
     n0 = (first_n + local % width) * BN;
-    m0 = (local / width) * BM;
+    m0 = q.row0 + (local / width) * BM;
 }
 
 // Tile skipping, one thread per output tile of group g: the tiles with at least one live K
@@ -239,7 +242,7 @@ __global__ void __launch_bounds__(256) k_tile_plan(const QDesc *qd, int g, uint2
     const QDesc &q = *qd;
     DevState *st = q.st;
     if (st->use_tensor[g] == 0) return;
-    const uint32_t tiles = (q.n_pad / BN) * (q.n_pad / BM);
+    const uint32_t tiles = output_tiles(q);
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
     const int A = q.rules[r0].lhs;
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->tensor_products, (unsigned long long)(r1 - r0));
-    const uint32_t ntile = list ? __ldcg(&st->plan_count[g][st->iter & 1ull]) : (q.n_pad / BN) * (q.n_pad / BM);
+    const uint32_t ntile = list ? __ldcg(&st->plan_count[g][st->iter & 1ull]) : output_tiles(q);
     if (blockIdx.x >= ntile) return;  // (uniform over the CTA) no tile for this CTA
     const uint32_t dense_steps = (uint32_t)(r1 - r0) * (q.KS / SLICES);
     volatile int *err = &S.err;
@@ -879,7 +882,7 @@ int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
     const int rc = tensor_setup(c);
     if (rc != CFPQ_OK) return rc;
     TensorWork *w = static_cast<TensorWork *>(c->h_tc_work);
-    const uint32_t tiles = (c->n_pad / tc::BN) * (c->n_pad / tc::BM);
+    const uint32_t tiles = (c->n_pad / tc::BN) * ((c->row1 - c->row0) / tc::BM);  // the row block's tiles
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

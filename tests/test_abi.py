@@ -110,6 +110,23 @@ def test_lengths_options_checked_before_device_use():
         opt.schedule, opt.path, opt.lengths = schedule, path, 1
         assert _create(g.cnf, 4, [(0, 0, 1)], ctypes.byref(opt))[0] == eng.ERR_UNSUPPORTED
     assert lib.cfpq_get_lengths(None, 0, None, None, 0, None) == eng.ERR_INVALID
+    # row blocks of a sharded solve: 256-aligned ends inside [0, n], Jacobi on a matrix path
+    for b0, b1, code in [(100, 600, eng.ERR_INVALID), (0, 700, eng.ERR_INVALID), (512, 256, eng.ERR_INVALID),
+                         (256, 256, eng.ERR_INVALID), (0, 300, eng.ERR_INVALID)]:
+        opt = eng.Options()
+        lib.cfpq_options_default(ctypes.byref(opt))
+        opt.schedule, opt.row_begin, opt.row_end = eng.SCHED_JACOBI, b0, b1
+        assert _create(g.cnf, 600, [(0, 0, 1)], ctypes.byref(opt))[0] == code, (b0, b1)
+    for schedule, path in [(eng.SCHED_INPLACE, eng.PATH_GATHER), (eng.SCHED_JACOBI, eng.PATH_WORKLIST)]:
+        opt = eng.Options()
+        lib.cfpq_options_default(ctypes.byref(opt))
+        opt.schedule, opt.path, opt.row_begin, opt.row_end = schedule, path, 256, 600
+        assert _create(g.cnf, 600, [(0, 0, 1)], ctypes.byref(opt))[0] == eng.ERR_UNSUPPORTED
+    for name in ("cfpq_block_start", "cfpq_block_products"):
+        assert getattr(lib, name)(None, None) == eng.ERR_INVALID
+    assert lib.cfpq_block_export(None, None, 0, None, None) == eng.ERR_INVALID
+    assert lib.cfpq_block_import(None, None, 0, None) == eng.ERR_INVALID
+    assert lib.cfpq_block_finish(None, None, None) == eng.ERR_INVALID
     assert lib.cfpq_get_path(None, 0, 0, 0, None, None, 0, None) == eng.ERR_INVALID
 
 
@@ -133,7 +150,7 @@ def test_options_defaults():
     assert eng.library().cfpq_options_default(ctypes.byref(opt)) == eng.OK
     assert (opt.schedule, opt.path, opt.use_graph, opt.profile, opt.max_iter, opt.lengths, opt.dense_tensor,
             opt.tensor_kind) == (eng.SCHED_INPLACE, eng.PATH_AUTO, 1, 0, 0, 0, 0, eng.TENSOR_AUTO)
-    assert ctypes.sizeof(eng.Options) == 48
+    assert ctypes.sizeof(eng.Options) == 56
 
 
 def test_batch_tuning_host_calls():
