@@ -12,6 +12,12 @@
 //   3. retires the queries whose loop stopped (fixpoint or iteration cap): their R_A are
 //      copied to host memory and their device memory goes back to the stream-ordered
 //      pool at once, so the next step can admit more.
+// Large queries (n_pad >= kSoloRows) do not join the grouped launch: one large query's round
+// and the clearing of its planes would lengthen the step of every small query resident with
+// it, and the single-query loop (a CUDA graph with a conditional while node) runs a large
+// query several times faster than the grouped launch does. They are solved on a second
+// stream by that loop, concurrently with the grouped launches; each step polls their
+// completion events and retires the finished ones in the same way.
 // Results are identical to solving each query alone: each query runs Algorithm 1 to its
 // own least fixpoint; other queries only share the launch.
 #include <algorithm>
@@ -43,6 +49,7 @@ struct Pending {
 struct Served {
     int64_t ticket = 0;
     cfpq_ctx *ctx = nullptr;
+    bool solo = false;  // solved by the single-query loop on the server's second stream
     size_t footprint = 0;
     int state = CFPQ_QUERY_QUEUED;
     int status = CFPQ_OK;
@@ -53,10 +60,14 @@ struct Served {
 
 }  // namespace
 
+constexpr uint32_t kSoloRows = 16384;  // queries with at least this many (padded) rows run alone
+
 struct cfpq_server {
     size_t budget = 0, used = 0, peak_used = 0;
     int rounds = 8, max_resident = 4096;
     cudaStream_t stream = nullptr;
+    cudaStream_t solo_stream = nullptr;  // large queries' single-query loops
+    std::vector<Served *> solo;          // large queries in flight there
     cudaMemPool_t pool = nullptr;
     std::deque<Pending> waiting;
     std::vector<Served *> resident;
@@ -101,9 +112,11 @@ extern "C" int cfpq_server_create(const cfpq_server_options *opt, cfpq_server **
     size_t free_b = 0, total_b = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->solo_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaDeviceGetDefaultMemPool(&s->pool, dev) != cudaSuccess) {
         cudaGetLastError();
         if (s->stream) cudaStreamDestroy(s->stream);
+        if (s->solo_stream) cudaStreamDestroy(s->solo_stream);
         delete s;
         return CFPQ_ERR_CUDA;
     }
@@ -143,9 +156,10 @@ extern "C" int cfpq_server_submit(cfpq_server *s, const cfpq_grammar_cnf *g, uin
 // Copies every R_A of a stopped query to the host and returns its device memory.
 static int retire(cfpq_server *s, Served *q) {
     cfpq_ctx *c = q->ctx;
-    int rc = read_status(c, s->stream);
+    cudaStream_t st = q->solo ? s->solo_stream : s->stream;
+    int rc = read_status(c, st);
     q->status = rc;
-    c->last_stream = s->stream;
+    c->last_stream = st;
     q->iterations = c->stats.iterations;
     c->solved = true;
     if (rc == CFPQ_ERR_CUDA) return rc;
@@ -166,7 +180,7 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
     int done_now = 0;
     s->steps++;
     // 1) admission by free HBM, in arrival order
-    while (!s->waiting.empty() && (int)s->resident.size() < s->max_resident) {
+    while (!s->waiting.empty() && (int)(s->resident.size() + s->solo.size()) < s->max_resident) {
         Pending &p = s->waiting.front();
         if (p.footprint > s->budget) {
             Served *q = new Served();
@@ -188,10 +202,34 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
         cfpq_options_default(&o);
         o.path = CFPQ_PATH_GATHER;
         o.schedule = p.schedule;
+        const bool solo = (p.n + 255u) / 256u * 256u >= kSoloRows;
         cfpq_ctx *c = nullptr;
-        int rc = ctx_create_pooled(&g, p.n, p.edges.data(), p.edges.size(), o, s->stream, &c);
+        int rc = ctx_create_pooled(&g, p.n, p.edges.data(), p.edges.size(), o, solo ? s->solo_stream : s->stream, &c);
         if (rc == CFPQ_ERR_NOMEM) break;  // the pool could not serve it now: retry next step
         if (rc != CFPQ_OK) return rc;
+        if (solo) {
+            // seed and the single-query loop on the second stream, without waiting for them
+            c->solved = false;
+            c->last_stream = s->solo_stream;
+            if (cudaEventRecord(c->ev0, s->solo_stream) != cudaSuccess ||
+                (rc = enqueue_reset_and_seed(c, s->solo_stream)) != CFPQ_OK ||
+                (rc = run_loop(c, s->solo_stream)) != CFPQ_OK || cudaEventRecord(c->ev1, s->solo_stream) != cudaSuccess) {
+                ctx_destroy(c);
+                return rc != CFPQ_OK ? rc : CFPQ_ERR_CUDA;
+            }
+            Served *q = new Served();
+            q->ticket = p.ticket;
+            q->ctx = c;
+            q->solo = true;
+            q->footprint = p.footprint;
+            q->state = CFPQ_QUERY_RUNNING;
+            s->state_of[q->ticket] = q->state;
+            s->used += p.footprint;
+            s->peak_used = std::max(s->peak_used, s->used);
+            s->solo.push_back(q);
+            s->waiting.pop_front();
+            continue;
+        }
         DevState st0;
         memset(&st0, 0, sizeof(st0));
         st0.max_iter = c->max_iter;
@@ -211,6 +249,25 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
         s->resident.push_back(q);
         s->waiting.pop_front();
     }
+    // large queries whose single-query loop has finished
+    auto retire_solo = [&]() -> int {
+        std::vector<Served *> still;
+        for (Served *q : s->solo) {
+            const cudaError_t e = cudaEventQuery(q->ctx->ev1);
+            if (e == cudaErrorNotReady) {
+                still.push_back(q);
+                continue;
+            }
+            if (e != cudaSuccess) return CFPQ_ERR_CUDA;
+            const int rc = retire(s, q);
+            if (rc != CFPQ_OK) return rc;
+            done_now++;
+        }
+        s->solo.swap(still);
+        return CFPQ_OK;
+    };
+    int src = retire_solo();
+    if (src != CFPQ_OK) return src;
     if (s->resident.empty()) {
         if (n_completed) *n_completed = done_now;
         return CFPQ_OK;
@@ -258,6 +315,7 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
         done_now++;
     }
     s->resident.swap(keep);
+    if ((rc = retire_solo()) != CFPQ_OK) return rc;
     if (n_completed) *n_completed = done_now;
     return CFPQ_OK;
 }
@@ -317,7 +375,7 @@ extern "C" int cfpq_server_stats_get(const cfpq_server *s, cfpq_server_stats *ou
     if (!s || !out) return CFPQ_ERR_INVALID;
     memset(out, 0, sizeof(*out));
     out->queued = (int64_t)s->waiting.size();
-    out->resident = (int64_t)s->resident.size();
+    out->resident = (int64_t)(s->resident.size() + s->solo.size());
     out->completed = s->completed;
     out->failed = s->failed;
     out->launches = s->launches;
@@ -331,7 +389,12 @@ extern "C" int cfpq_server_stats_get(const cfpq_server *s, cfpq_server_stats *ou
 extern "C" void cfpq_server_destroy(cfpq_server *s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->solo_stream) cudaStreamSynchronize(s->solo_stream);
     for (Served *q : s->resident) {
+        ctx_destroy(q->ctx);
+        delete q;
+    }
+    for (Served *q : s->solo) {
         ctx_destroy(q->ctx);
         delete q;
     }
@@ -341,5 +404,6 @@ extern "C" void cfpq_server_destroy(cfpq_server *s) {
         cudaStreamSynchronize(s->stream);
         cudaStreamDestroy(s->stream);
     }
+    if (s->solo_stream) cudaStreamDestroy(s->solo_stream);
     delete s;
 }

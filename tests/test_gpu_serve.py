@@ -92,3 +92,34 @@ def test_ticket_errors():
     with pytest.raises(eng.CfpqError):
         srv.info(tk)
     srv.close()
+
+
+def test_large_queries_run_alone_beside_the_grouped_launches():
+    """Queries with at least 16,384 (padded) rows are solved by the single-query loop on the
+    server's second stream while the small ones go through the grouped launches: every
+    result still equals the oracle's and the query's result when solved alone."""
+    small = _work(30, 64, 2000, seed=21)
+    big = [(synth.hierarchy(n, round(0.3 * n), seed=n), text) for n, text in
+           [(16384, synth.GRAMMAR_Q1), (20000, synth.GRAMMAR_QSC), (16000, synth.GRAMMAR_Q1)]]
+    work = small[:10] + [(gr, t, eng.Grammar(t, gr.labels)) for gr, t in big[:2]] + small[10:20] + \
+        [(big[2][0], big[2][1], eng.Grammar(big[2][1], big[2][0].labels))] + small[20:]
+    srv = eng.Server(rounds_per_step=4)
+    tickets = []
+    for j, (graph, text, g) in enumerate(work):
+        tickets.append(srv.submit(g, graph.n, graph.edges))
+        if j % 5 == 4:
+            srv.step()  # arrivals while others are resident
+    while srv.stats()["completed"] + srv.stats()["failed"] < len(work):
+        srv.step()
+    for tk, (graph, text, g) in zip(tickets, work):
+        info = srv.info(tk)
+        assert info["state"] == eng.QUERY_DONE and info["status"] == eng.OK, graph.n
+        ref = oracle.hellings(graph, text)
+        alone = eng.Query(g, graph.n, graph.edges, path=eng.PATH_GATHER)
+        alone.solve()
+        for a, nm in enumerate(g.names):
+            got = srv.result(tk, a)
+            assert np.array_equal(got, ref.pairs(nm)), (graph.n, nm)
+            assert np.array_equal(got, alone.get(nm))
+        srv.release(tk)
+    srv.close()
