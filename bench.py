@@ -77,7 +77,7 @@ def parse():
                          "queries, served stream) that the default line reports beside the main workload")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", default="hier16k",
-                    choices=["hier16k", "sg16k", "batch256", "serve", "cycles", "lengths16k"],
+                    choices=["hier16k", "sg16k", "batch256", "serve", "cycles", "lengths16k", "blockdiag32k"],
                     help="hier16k: the default line; sg16k: the same hierarchy with the same-generation "
                          "query (denser result); batch256 / serve / cycles: the batched, served and "
                          "two-cycle workloads; lengths16k: single-path lengths (Section 5) on the hierarchy")
@@ -991,6 +991,65 @@ def lengths_arm(args):
     return 0
 
 
+def blockdiag_arm(args):
+    """A transitive closure (S -> S S | t0) over 64 communities of 512 nodes, n = 32768: the
+    matrices are block-diagonal, so tensor products with tile skipping execute 0.1 % of the
+    dense product. The automatic path (cost model pricing the live K steps once the tile
+    counts are known) against the gather alone and the tensor path alone; results checked
+    equal between them (and, with the CPU baseline, against the oracle)."""
+    import torch
+
+    import paper_1707_01007_b300 as eng
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    graph = synth.communities(32768, 64, 2, seed=4)
+    text = "S S S\nS t0\n"
+    g = eng.Grammar(text, graph.labels)
+    stream = torch.cuda.current_stream()
+    legs, first = {}, None
+    for name, kw in (("auto", dict(path=eng.PATH_AUTO)), ("gather", dict(path=eng.PATH_GATHER)),
+                     ("tensor_tile_skip", dict(path=eng.PATH_TENSOR)),
+                     ("tensor_tile_skip_jacobi", dict(path=eng.PATH_TENSOR, schedule=eng.SCHED_JACOBI))):
+        q = eng.Query(g, graph.n, graph.edges, timeout_s=300.0, **kw)
+        for _ in range(max(1, args.warmup)):
+            q.solve(stream)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            q.solve(stream)
+            ts.append(q.stats()["solve_ms"])
+        st = q.stats()
+        got = q.get("S")
+        if first is None:
+            first = got
+        elif not np.array_equal(got, first):
+            print(f"bench: {name} differs from the automatic path", file=sys.stderr)
+            return 3
+        legs[name] = {"ms": float(np.median(ts)), "iterations": st["iterations"],
+                      "tensor_products": st["tensor_products"], "gather_products": st["gather_products"],
+                      "tensor_live_fraction": (st["tensor_live_ops"] / st["dense_ops"]) if st["dense_ops"] else None}
+        q.close()
+    line = {"metric": "closure time, block-diagonal transitive closure", "value": legs["auto"]["ms"] / 1e3,
+            "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": legs["auto"]["ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit-packed",
+            "data": "synthetic",
+            "config": {"workload": "64 communities of 512 nodes (n = 32768, 2 out-edges per node inside its "
+                                   "community), S -> S S | t0"},
+            "pairs_S": int(first.shape[0]), "paths": legs,
+            "speedup_vs_gather": legs["gather"]["ms"] / legs["auto"]["ms"]}
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.hellings(graph, text)
+        line["cpu_baseline"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": "full workload once, one host thread"}
+        if not np.array_equal(ref.pairs("S"), first):
+            print("bench: the closure differs from the oracle", file=sys.stderr)
+            return 3
+        line["parity"] = {"reference": "oracle", "equal": True}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1003,6 +1062,8 @@ def main():
         return cycles_arm(args)
     if args.workload == "lengths16k":
         return lengths_arm(args)
+    if args.workload == "blockdiag32k":
+        return blockdiag_arm(args)
     return engine_arm(args)
 
 

@@ -150,6 +150,22 @@ def random_graph(n: int, n_edges: int, n_labels: int, seed: int = 0) -> Graph:
                  meta={"kind": "random", "seed": seed})
 
 
+def communities(n: int, k: int, degree: int = 2, seed: int = 0) -> Graph:
+    """k communities of about n / k consecutive nodes each (node v is in community
+    v * k // n); every node has `degree` out-edges, label t0, to uniform nodes of its own
+    community (drawn with replacement). The transitive closure S -> S S | t0 is dense inside
+    each community and empty between them: a closure whose matrices are block-diagonal."""
+    kk = key(seed, 13)
+    v = np.repeat(np.arange(n, dtype=np.int64), degree)
+    c = v * k // n
+    lo = (c * n + k - 1) // k           # first node of each community
+    hi = ((c + 1) * n + k - 1) // k     # one past its last node
+    i = np.arange(v.size, dtype=np.int64)
+    dst = lo + uniform_int(kk, i, hi - lo)
+    edges = np.stack([v, np.zeros_like(v), dst], axis=1)
+    return Graph(n=n, edges=edges, labels=["t0"], meta={"kind": "communities", "k": k, "seed": seed})
+
+
 # --------------------------------------------------------------------------------------
 # Grammars (text form: one production per line, "A B C", "A x" or "A eps"; a symbol is
 # a non-terminal iff it appears on some left-hand side; '#' starts a comment)

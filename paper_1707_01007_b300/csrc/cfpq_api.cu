@@ -240,49 +240,83 @@ __global__ void __launch_bounds__(256) k_clear_scan(const QDesc *qd, uint32_t *l
 }
 
 
-// AUTO path, start of a loop execution (one thread): for every production group, the cheaper
-// of the two product kinds by a cost model on the device-side counts, and which group
-// refreshes each transpose that a tensor product will read. Gather cost: one right-operand
-// row (W words) per bit of D_B, plus, where the right operand has a delta, a scan of the
-// non-empty rows of T_B (2W words each) and one D_C row per bit of T_B that meets a
-// non-empty row of D_C (expected |T_B| * min(1, |D_C| / n)). Tensor cost: 2 n_pad^3 Boolean
-// ops per production, plus a transpose per right operand changed since its last refresh.
-constexpr float kTensorOpsPerNs = 2.9e6f;     // measured tensor-core Boolean product rate
+// AUTO path, start of a loop execution (one thread per group): for every production group, the
+// cheaper of the two product kinds by a cost model on the device-side counts, and which group
+// refreshes each transpose that a tensor product will read. Gather cost: one right-operand row
+// (W words) per bit of D_B, plus, where the right operand has a delta, a scan of the non-empty
+// rows of T_B (2W words each) and one D_C row per bit of T_B that meets a non-empty row of D_C
+// (expected |T_B| * min(1, |D_C| / n)). Tensor cost, per production: with tile skipping and
+// both operands' tile counts known, the live K steps sum_k mB[k] nC[k] (mB[k]: m-tiles of T_B
+// whose K slice k is non-zero; nC[k]: n-tiles of T_C^T) at the measured rate of executed work
+// with skipping; otherwise the dense 2 n_pad^3 at the dense rate of the operand kind; plus a
+// transpose per right operand changed since its last refresh and the launches. When the gather
+// has become expensive (kProbeNs) and the dense price is higher still, the counts that tile
+// skipping would need are asked for (occ_probe: the next execution's occupancy pass runs even
+// if no group takes the tensor cores), so the next choice prices the live steps.
+// Measured rates (Boolean ops per ns) of dense products and of the work executed with tile
+// skipping, for E4M3 and E2M1 operands.
+__device__ __forceinline__ float tensor_ops_per_ns(int kind) { return kind ? 6.0e6f : 3.2e6f; }
+__device__ __forceinline__ float skip_ops_per_ns(int kind) { return kind ? 3.2e6f : 2.2e6f; }
+constexpr float kStepOps = 2.0f * 128.0f * 256.0f * 128.0f;  // Boolean ops of one K slice of a tile
+constexpr float kTensorLaunchNs = 8000.0f;               // plan and product launches of a group
+constexpr float kProbeNs = 100000.0f;
 constexpr float kGatherBytesPerNs = 600.0f;   // measured gather rate (latency-bound)
 constexpr float kTransposeBytesPerNs = 3000.0f;
 
 // Every thread of one block (at least max(n_nt, n_groups) threads) calls this: thread g
 // costs group g from the device-side counts, thread a assigns the refresh of TT[A].
 __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle *handles, int use_handles) {
-    __shared__ unsigned s_use[kMaxNT], s_any;
+    __shared__ unsigned s_use[kMaxNT], s_any, s_probe;
     DevState *st = q.st;
     const int tid = threadIdx.x;
     const uint32_t p = (uint32_t)(st->iter & 1ull);
-    if (tid == 0) s_any = 0u;
+    if (tid == 0) s_any = s_probe = 0u;
     __syncthreads();
     if (tid < q.n_groups) {
         const int g = tid;
         // single precision: a cost estimate (either choice is exact), and FP32 is the fast pipe
+        const int kind = q.tensor_kind == CFPQ_TENSOR_FP8 ? 0 : 1;
         const float n = (float)q.n, W = (float)q.W, np = (float)q.n_pad;
-        const float per_rule_ns = 2.0f * np * np * np / kTensorOpsPerNs;
+        const float dense_rule_ns = 2.0f * np * np * np / tensor_ops_per_ns(kind);
         const float transpose_ns = 2.0f * np * np / 8.0f / kTransposeBytesPerNs;
         const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
-        float words = 0.0f, tensor_ns = (float)(r1 - r0) * per_rule_ns;
+        float words = 0.0f, tensor_ns = kTensorLaunchNs;
+        bool unknown = false;
         for (int r = r0; r < r1; r++) {
             const int B = q.rules[r].b, C = q.rules[r].c;
             const float dB = (float)st->dcount[p][B], dC = (float)st->dcount[p][C], tB = (float)st->tcount[B];
             words += dB * W;
             if (dC > 0.0f) words += fminf(n, tB) * 2.0f * W + tB * fminf(1.0f, dC / n) * W;
-            if (st->dirty[C]) tensor_ns += transpose_ns;
+            const float extra = st->dirty[C] ? transpose_ns : 0.0f;
+            if (q.occA && q.occKnown[B] && q.occKnown[C]) {
+                float live = 0.0f;
+                const uint32_t *mB = q.occCA + (uint64_t)B * q.KS, *nC = q.occCB + (uint64_t)C * q.KS;
+                for (uint32_t k = 0; k < q.KS; k++) live += (float)__ldcg(mB + k) * (float)__ldcg(nC + k);
+                tensor_ns += live * kStepOps / skip_ops_per_ns(kind) + extra;
+            } else {
+                tensor_ns += dense_rule_ns + extra;
+                unknown = true;
+            }
         }
-        const unsigned use = tensor_ns < words * 4.0f / kGatherBytesPerNs ? 1u : 0u;
+        const float gather_ns = words * 4.0f / kGatherBytesPerNs;
+        const unsigned use = tensor_ns < gather_ns ? 1u : 0u;
+        // an occupancy pass reads each operand's plane once: worth it only where it is small
+        // against the gather it may replace
+        const float pass_ns = 2.0f * (float)(r1 - r0) * np * np / 8.0f / kTransposeBytesPerNs;
+        if (q.occA && unknown && !use && gather_ns > fmaxf(kProbeNs, 10.0f * pass_ns)) {
+            // tile skipping might beat the gather here: the next occupancy pass gets these counts
+            for (int r = r0; r < r1; r++) st->occ_now[q.rules[r].b] = st->occ_now[q.rules[r].c] = 1u;
+            atomicOr(&s_probe, 1u);
+        }
         st->use_tensor[g] = use;
         s_use[g] = use;
         if (use_handles) cudaGraphSetConditional(handles[g], use);
         if (use) atomicOr(&s_any, 1u);
     }
     __syncthreads();
-    if (tid == 0 && use_handles) cudaGraphSetConditional(handles[q.n_groups], s_any);
+    if (tid == 0) st->occ_probe = s_probe;
+    if (tid == 0 && use_handles) cudaGraphSetConditional(handles[q.n_groups], s_any | s_probe);
+
     if (tid < q.n_nt) {
         // the first group (in order) taking the tensor product with A as a right operand
         // refreshes TT[A] if A changed since its last refresh
@@ -1163,6 +1197,9 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_TTsum, c->lengths ? (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t) : 0},
         {(void **)&c->d_occA, occ ? (size_t)c->n_nt * (c->n_pad / 128) * swk * sizeof(uint32_t) : 0},
         {(void **)&c->d_occB, occ ? (size_t)c->n_nt * (c->n_pad / 256) * swk * sizeof(uint32_t) : 0},
+        {(void **)&c->d_occCA, occ ? (size_t)c->n_nt * (c->n_pad / 128) * sizeof(uint32_t) : 0},
+        {(void **)&c->d_occCB, occ ? (size_t)c->n_nt * (c->n_pad / 128) * sizeof(uint32_t) : 0},
+        {(void **)&c->d_occKnown, occ ? (size_t)c->n_nt * sizeof(uint32_t) : 0},
         {(void **)&c->d_tile_list, occ ? (size_t)(c->n_pad / 256) * (c->n_pad / 128) * 8 : 0}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
@@ -1181,6 +1218,16 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     // copies are stream-ordered after the (possibly stream-ordered) allocations; the host
     // sources are pageable, so each call returns once its source has been staged
     cudaStream_t cs = c->stream;
+    if (occ) {
+        // tile occupancy starts empty, its counts zero: the occupancy passes keep the two
+        // consistent by counting the bits they flip
+        const uint32_t swk2 = ((c->n_pad / 128) + 31) / 32;
+        CK(cudaMemsetAsync(c->d_occA, 0, (size_t)c->n_nt * (c->n_pad / 128) * swk2 * sizeof(uint32_t), cs));
+        CK(cudaMemsetAsync(c->d_occB, 0, (size_t)c->n_nt * (c->n_pad / 256) * swk2 * sizeof(uint32_t), cs));
+        CK(cudaMemsetAsync(c->d_occCA, 0, (size_t)c->n_nt * (c->n_pad / 128) * sizeof(uint32_t), cs));
+        CK(cudaMemsetAsync(c->d_occCB, 0, (size_t)c->n_nt * (c->n_pad / 128) * sizeof(uint32_t), cs));
+        CK(cudaMemsetAsync(c->d_occKnown, 0, (size_t)c->n_nt * sizeof(uint32_t), cs));
+    }
     if (!rules.empty())
         CK(cudaMemcpyAsync(c->d_rules, rules.data(), rules.size() * sizeof(Rule), cudaMemcpyHostToDevice, cs));
     CK(cudaMemcpyAsync(c->d_gstart, gstart.data(), gstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, cs));
@@ -1215,6 +1262,10 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.Trow = c->d_Trow;
     q.occA = c->d_occA;
     q.occB = c->d_occB;
+    q.occCA = c->d_occCA;
+    q.occCB = c->d_occCB;
+    q.occKnown = c->d_occKnown;
+    q.tensor_kind = c->tensor_kind;
     q.KS = c->n_pad / 128;
     q.SWK = (q.KS + 31) / 32;
     q.Tsum = c->d_Tsum;

@@ -66,6 +66,7 @@ struct DevState {
     unsigned long long tc_live_steps;   // K steps the tensor-core products issued (after tile skipping)
     unsigned int plan_count[kMaxNT][2]; // tile skipping: live output tiles listed for group g, by execution parity
     unsigned int plan_take[kMaxNT][2];  // tile skipping: listed tiles already claimed by a CTA
+    unsigned int occ_probe;             // AUTO: refresh tile occupancy this execution for the cost model
     unsigned long long block_records;   // sharded solve: records packed by the last export
     unsigned int block_bad;             // sharded solve: an imported record was out of range
 };
@@ -83,6 +84,9 @@ struct QDesc {
     uint64_t n_edges;
     uint32_t *T, *TT, *X0, *X1, *R0, *R1, *Trow;
     uint32_t *occA, *occB;              // tile occupancy (NULL: dense tensor products)
+    uint32_t *occCA, *occCB;            // per (non-terminal, K slice): m-tiles / n-tiles whose tile is non-zero
+    uint32_t *occKnown;                 // per non-terminal: its occupancy (and counts) has been computed
+    int32_t tensor_kind;                // CFPQ_TENSOR_FP8 or _FP4 (the product choice's rate)
     uint32_t KS, SWK;                   // K slices of 128 bits per row; occupancy words per tile row
     uint32_t *Tsum;                     // word summary of T (NULL in batched launches)
     uint32_t *TTsum;                    // word summary of TT (NULL unless lengths are kept)

@@ -35,6 +35,7 @@ struct cfpq_ctx {
     uint32_t *d_Wit = nullptr;        // [n_nt][n_pad][n_pad] derivation step of each pair (in the arena)
     uint64_t lplane = 0;              // cells per length plane = n_pad * n_pad
     uint32_t *d_occA = nullptr, *d_occB = nullptr;  // tile occupancy (tensor path with tile skipping; arena)
+    uint32_t *d_occCA = nullptr, *d_occCB = nullptr, *d_occKnown = nullptr;  // its counts per K slice (arena)
     void *d_tile_list = nullptr;      // tile skipping: live output tiles of one product (uint2 each; arena)
     bool dense_tensor = false;        // tensor products over every K step (no tile skipping)
     int tensor_kind = CFPQ_TENSOR_FP4;  // operand format of the tensor products (FP8 or FP4, resolved)

@@ -626,13 +626,24 @@ __global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a, int g
 // the CTA's 2 x 2 blocks of 128 rows x 128 columns give two (m-tile, K slice) bits of occA[a]
 // per m-tile and, ORed over the columns, the two (n-tile, K slice) bits of occB[a] (T_a^T's
 // tile of 256 rows x 128 columns is T_a's 128 rows x 256 columns). Each bit belongs to exactly
-// one CTA, which writes it whether set or clear (no clearing pass). Runs only if the plan of
-// this execution asks for a (occ_now) and some group takes the tensor product now.
+// one CTA, which writes it whether set or clear (no clearing pass) and adds the bits it flips
+// to the per-(non-terminal, K slice) counts of non-zero tiles that the automatic path's cost
+// model reads (occCA: m-tiles, occCB: n-tiles). Runs only if the plan of this execution asks
+// for a (occ_now) and some group takes the tensor product now, or the cost model asked for
+// the counts (occ_probe).
+__device__ __forceinline__ void count_flips(uint32_t *cnt, uint32_t old_word, uint32_t new_word, uint32_t sh) {
+#pragma unroll
+    for (uint32_t kk = 0; kk < 2; kk++) {
+        const uint32_t ob = (old_word >> (sh + kk)) & 1u, nb = (new_word >> (sh + kk)) & 1u;
+        if (ob != nb) atomicAdd(cnt + kk, nb ? 1u : 0xFFFFFFFFu);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_occupancy(const QDesc *qd, int a) {
     const QDesc &q = *qd;
     const DevState *st = q.st;
     if (!st->occ_now[a]) return;
-    unsigned any_tc = 0u;
+    unsigned any_tc = st->occ_probe;
     for (int g = 0; g < q.n_groups; g++) any_tc |= st->use_tensor[g];
     if (!any_tc) return;
     __shared__ uint32_t mask;
@@ -655,14 +666,17 @@ __global__ void __launch_bounds__(256) k_occupancy(const QDesc *qd, int a) {
     for (uint32_t h = 0; h < 2; h++) {
         uint32_t *word = q.occA + ((uint64_t)a * ntiles_m + r0 / BM + h) * q.SWK + ks / 32u;
         const uint32_t bits = ((M >> (2u * h)) & 3u) << (ks & 31u);
-        atomicAnd(word, ~(3u << (ks & 31u)));
+        const uint32_t old = atomicAnd(word, ~(3u << (ks & 31u)));
         if (bits) atomicOr(word, bits);
+        if (q.occCA) count_flips(q.occCA + (uint64_t)a * q.KS + ks, old, bits, ks & 31u);
     }
     const uint32_t ksr = r0 / 128u;  // the two K slices of the rows (even), as T_a^T columns
     const uint32_t rb = ((M | (M >> 1)) & 1u) | (((M >> 2) | (M >> 3)) & 1u) << 1;
     uint32_t *wordB = q.occB + ((uint64_t)a * ntiles_n + wc0 / 8u) * q.SWK + ksr / 32u;
-    atomicAnd(wordB, ~(3u << (ksr & 31u)));
+    const uint32_t oldB = atomicAnd(wordB, ~(3u << (ksr & 31u)));
     if (rb) atomicOr(wordB, rb << (ksr & 31u));
+    if (q.occCB) count_flips(q.occCB + (uint64_t)a * q.KS + ksr, oldB, rb << (ksr & 31u), ksr & 31u);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && q.occKnown) q.occKnown[a] = 1u;
 }
 
 // Profile mode, useful work of one tensor product T_B x T_C: sum over k of the ones in

@@ -146,3 +146,52 @@ def test_long_chain_full_size_automatic():
     q.solve()
     assert q.stats()["worklist_items"] > 0
     assert q.count("S") == p * qq and q.count("S1") == p * qq
+
+
+@pytest.fixture(scope="module")
+def block_diagonal():
+    graph = synth.communities(16384, 32, 2, seed=3)
+    text = "S S S\nS t0\n"
+    return graph, text, oracle.hellings(graph, text).pairs("S")
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("kind", [eng.TENSOR_FP4, eng.TENSOR_FP8], ids=["fp4", "fp8"])
+def test_block_diagonal_closure_prices_tile_skipping(block_diagonal, use_graph, kind):
+    """A transitive closure over 32 communities of 512 nodes (block-diagonal matrices): once
+    the gather has grown expensive, the cost model asks for the tile counts and then prices a
+    tensor product by its live K steps, which are a small fraction of the dense product here.
+    Some executions must run on the tensor cores with tile skipping (executed work far below
+    the dense product), and the result must equal the oracle's."""
+    graph, text, ref = block_diagonal
+    g = eng.Grammar(text, graph.labels)
+    q = eng.Query(g, graph.n, graph.edges, path=eng.PATH_AUTO, use_graph=use_graph, tensor_kind=kind,
+                  timeout_s=120.0)
+    q.solve()
+    assert np.array_equal(q.get("S"), ref)
+    s = q.stats()
+    products_each_once(s, text, graph)
+    assert s["tensor_products"] > 0
+    assert 0 < s["tensor_live_ops"] < 0.05 * s["dense_ops"]
+
+
+def test_block_diagonal_closure_default_path_beats_gather_only():
+    # the same closure (64 communities, n = 32768): the automatic path against the gather alone
+    graph = synth.communities(32768, 64, 2, seed=4)
+    text = "S S S\nS t0\n"
+    g = eng.Grammar(text, graph.labels)
+    times = {}
+    for name, path in (("auto", eng.PATH_AUTO), ("gather", eng.PATH_GATHER)):
+        q = eng.Query(g, graph.n, graph.edges, path=path, timeout_s=120.0)
+        q.solve()
+        ts = []
+        for _ in range(3):
+            q.solve()
+            ts.append(q.stats()["solve_ms"])
+        times[name] = min(ts)
+        if name == "auto":
+            assert q.stats()["tensor_products"] > 0
+            res = q.get("S")
+        else:
+            assert np.array_equal(q.get("S"), res)
+    assert times["auto"] < times["gather"], times
