@@ -68,3 +68,17 @@ def test_poisson_arrivals_rate():
     # mean gap 1 / rate, within a few standard errors (the gaps are exponential)
     gap = float(t[-1]) / len(t)
     assert abs(gap - 1.0 / 500.0) < 4.0 * (1.0 / 500.0) / math.sqrt(len(t))
+
+
+def test_communities_recipe():
+    # every node has `degree` out-edges, all inside its own community of about n / k nodes
+    n, k, d = 3000, 7, 3
+    g = synth.communities(n, k, d, seed=2)
+    e = np.asarray(g.edges, dtype=np.int64)
+    assert e.shape == (n * d, 3) and (e[:, 1] == 0).all()
+    assert (np.bincount(e[:, 0], minlength=n) == d).all()
+    assert (e[:, 0] * k // n == e[:, 2] * k // n).all()
+    sizes = np.bincount(np.arange(n) * k // n)
+    assert sizes.max() - sizes.min() <= 1
+    again = synth.communities(n, k, d, seed=2)
+    assert np.array_equal(again.edges, g.edges)
