@@ -732,6 +732,30 @@ def batch_measure(eng, torch, steps, warmup):
     ms_serial = timed(serial, max(1, min(steps, 3)))
     for q in qs:
         q.close()
+    # a batch with dense members: 24 sparse hierarchy queries (n 64..1500) and five
+    # block-diagonal closures of 2,048-8,192 nodes (communities of 512, S -> S S | t0): the
+    # tuner may take size classes out of the grouped launch, to be solved alone beside it by
+    # the single-query automatic path (tensor-core products with tile skipping where cheaper)
+    dense_work = [(eng.Grammar(t, g.labels), g) for g, t in synth.batch_queries(24, 64, 1500, 0.3, seed=31)]
+    for j, n in enumerate([2048, 3000, 4096, 6000, 8192]):
+        g = synth.communities(n, max(1, n // 512), 2, seed=40 + j)
+        dense_work.append((eng.Grammar("S S S\nS t0\n", g.labels), g))
+    dqs = [eng.Query(gr, g.n, g.edges) for gr, g in dense_work]
+    saved = eng.batch_tuning()
+    for _ in range(warmup):
+        eng.solve_batch(dqs, stream, tuning=default)
+    d_default = timed(lambda: eng.solve_batch(dqs, stream, tuning=default), steps)
+    d_best, d_report = eng.autotune_batch(dqs, stream)
+    for _ in range(warmup):
+        eng.solve_batch(dqs, stream, tuning=d_best)
+    d_tuned = timed(lambda: eng.solve_batch(dqs, stream, tuning=d_best), steps)
+    d_tensor = sum(q.stats()["tensor_products"] for q in dqs)
+    for q in dqs:
+        q.close()
+    eng.set_batch_tuning(saved)
+    dense_mix = {"workload": "24 hierarchy queries (n 64..1500) + 5 block-diagonal closures (n 2048..8192)",
+                 "built_in_ms": d_default, "tuned_ms": d_tuned, "speedup": d_default / d_tuned,
+                 "tuned_config": d_best.as_dict(), "tensor_products_tuned": d_tensor, "tuner": d_report}
     return {"queries_per_s": 256 / (ms_batch / 1e3), "ms_per_batch": ms_batch,
             "workload": "256 hierarchy queries, n log-uniform [64, 4096], class fraction 0.3, "
                         "Q1 or sc-only uniformly, seed 0",
@@ -743,7 +767,8 @@ def batch_measure(eng, torch, steps, warmup):
             "phase_ms": {k: (round(v, 3) if isinstance(v, float) else
                              ([round(x, 3) for x in v] if isinstance(v, list) else v)) for k, v in phases.items()},
             "products_phase": {"bytes": product_bytes,
-                               "gbs": product_bytes / (phases["products"] * 1e6) if phases["products"] else None}}
+                               "gbs": product_bytes / (phases["products"] * 1e6) if phases["products"] else None},
+            "dense_mix": dense_mix}
 
 
 def batch_arm(args):

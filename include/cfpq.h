@@ -385,7 +385,9 @@ int cfpq_solve_batch(cfpq_ctx *const *ctxs, int32_t k, void *stream);
  * CFPQ_SCHED_AUTO; for the whole launch, the number of resident blocks per SM.
  *
  * Every configuration computes the same result (bit-identical triples); only the device
- * time and, for the schedule, the number of loop executions differ.
+ * time and, for the schedule, the number of loop executions differ. A size class can also
+ * leave the grouped launch (product = CFPQ_BATCH_ALONE): large, dense queries, whose own tiles
+ * fill the GPU, then get tensor-core products, which the grouped launch does not run.
  */
 #define CFPQ_TUNE_CLASSES 24
 typedef struct {
@@ -393,7 +395,17 @@ typedef struct {
     int32_t cpl[CFPQ_TUNE_CLASSES];        /* 1, 2, 4 or 8; 0 = built-in (the smallest cpl with
                                               32 * cpl >= W, at most 8) */
     int32_t schedule[CFPQ_TUNE_CLASSES];   /* CFPQ_SCHED_INPLACE or _JACOBI for AUTO contexts */
+    int32_t product[CFPQ_TUNE_CLASSES];    /* CFPQ_BATCH_GROUPED (0, built-in): the class's queries
+                                              run in the grouped launch, whose products are gathers;
+                                              CFPQ_BATCH_ALONE (1): they are solved beside it,
+                                              concurrently, each by its own single-query loop on its
+                                              context's stream, with the context's product path (the
+                                              automatic path puts a product on the tensor cores,
+                                              with tile skipping, where the cost model finds it
+                                              cheaper). Same results either way */
 } cfpq_batch_tuning;
+#define CFPQ_BATCH_GROUPED 0
+#define CFPQ_BATCH_ALONE 1
 
 typedef struct {
     int32_t trials;        /* batched solves the tuner timed (the final confirmation included) */
@@ -413,7 +425,8 @@ int cfpq_batch_tuning_set(const cfpq_batch_tuning *t);
  * so the contexts end solved, with the results of the last run) under candidate
  * configurations, by coordinate descent from the built-in one: blocks per SM (1, 2, 4, 8,
  * within occupancy), then cpl (1, 2, 4, 8) for each size class present, heaviest class
- * first, then the schedule of each class that holds AUTO contexts. A candidate replaces
+ * first, then the schedule of each class that holds AUTO contexts, then, for each class of
+ * W > 32 words (heaviest first), solving its queries alone beside the launch. A candidate replaces
  * the current choice only if it is at least 3 % faster. Every step is timed with CUDA
  * events on `stream` (NULL: the first context's stream). The best configuration is
  * merged into the installed one (the classes present and blocks_per_sm), copied to

@@ -100,15 +100,19 @@ class ServerStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+BATCH_GROUPED, BATCH_ALONE = 0, 1
+
+
 class BatchTuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("cpl", ctypes.c_int32 * TUNE_CLASSES),
-                ("schedule", ctypes.c_int32 * TUNE_CLASSES)]
+                ("schedule", ctypes.c_int32 * TUNE_CLASSES), ("product", ctypes.c_int32 * TUNE_CLASSES)]
 
     def as_dict(self):
         """blocks_per_sm plus the non-built-in entries per size class."""
         return {"blocks_per_sm": self.blocks_per_sm,
                 "cpl": {c: self.cpl[c] for c in range(TUNE_CLASSES) if self.cpl[c]},
-                "schedule": {c: self.schedule[c] for c in range(TUNE_CLASSES) if self.schedule[c]}}
+                "schedule": {c: self.schedule[c] for c in range(TUNE_CLASSES) if self.schedule[c]},
+                "alone": sorted(c for c in range(TUNE_CLASSES) if self.product[c] == BATCH_ALONE)}
 
 
 class TensorPeaks(ctypes.Structure):

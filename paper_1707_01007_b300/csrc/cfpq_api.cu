@@ -1422,9 +1422,9 @@ extern "C" int cfpq_create(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edg
     return CFPQ_OK;
 }
 
-extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
-    if (!c || c->block) return CFPQ_ERR_INVALID;  // a row block is solved with the cfpq_block_* calls
-    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+// The asynchronous part of a solve: the matrix initialisation and the loop (a graph launch
+// or the host-driven loop) enqueued on s, the end event recorded.
+int cfpq::solve_begin(cfpq_ctx *c, cudaStream_t s) {
     c->solved = false;
     c->last_stream = s;
     c->stats.product_ms = c->stats.tensor_ms = c->stats.lengths_ms = 0.0;
@@ -1435,8 +1435,14 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
     rc = c->path == CFPQ_PATH_WORKLIST ? worklist_run(c, s) : run_loop(c, s);
     if (rc != CFPQ_OK) return rc;
     CK(cudaEventRecord(c->ev1, s));
+    return CFPQ_OK;
+}
+
+// The rest of a solve begun on s: the status (waits for the loop), the hand-over to the
+// worklist path where the loop asked for it, and the statistics.
+int cfpq::solve_end(cfpq_ctx *c, cudaStream_t s) {
     unsigned to_wl = 0;
-    rc = read_status(c, s, &to_wl);
+    int rc = read_status(c, s, &to_wl);
     if (rc == CFPQ_ERR_CUDA) return rc;
     c->switched = false;
     if (rc == CFPQ_OK && c->allow_switch) {
@@ -1463,6 +1469,14 @@ extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
     c->stats.gather_cpl = 0;
     c->solved = true;
     return rc;
+}
+
+extern "C" int cfpq_solve(cfpq_ctx *c, void *stream) {
+    if (!c || c->block) return CFPQ_ERR_INVALID;  // a row block is solved with the cfpq_block_* calls
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const int rc = solve_begin(c, s);
+    if (rc != CFPQ_OK) return rc;
+    return solve_end(c, s);
 }
 
 extern "C" int cfpq_block_start(cfpq_ctx *c, void *stream) {

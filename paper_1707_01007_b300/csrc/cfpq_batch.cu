@@ -475,6 +475,7 @@ static bool tuning_valid(const cfpq_batch_tuning &t) {
         const int v = t.cpl[c];
         if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8) return false;
         if (t.schedule[c] != CFPQ_SCHED_INPLACE && t.schedule[c] != CFPQ_SCHED_JACOBI) return false;
+        if (t.product[c] != CFPQ_BATCH_GROUPED && t.product[c] != CFPQ_BATCH_ALONE) return false;
     }
     return true;
 }
@@ -632,8 +633,55 @@ static int batch_buffers_for(int k, BatchBuffers **out) {
     return CFPQ_OK;
 }
 
-// One complete batched solve of ctxs under configuration t; *ms = device time of the launch.
+static int solve_grouped(cfpq_ctx *const *ctxs, int k, cudaStream_t s, const cfpq_batch_tuning &t, float *ms_out);
+
+// One complete batched solve of ctxs under configuration t; *ms = device time of the batch
+// (from its start on s until every query is solved). The queries of the size classes that
+// t solves alone are begun first, each on its context's stream after s; the grouped launch
+// takes the rest; s then waits for all of them.
 static int solve_batch_with(cfpq_ctx *const *ctxs, int k, cudaStream_t s, const cfpq_batch_tuning &t, float *ms_out) {
+    std::vector<cfpq_ctx *> grouped, alone;
+    for (int j = 0; j < k; j++)
+        (t.product[batch_size_class(ctxs[j]->W)] == CFPQ_BATCH_ALONE ? alone : grouped).push_back(ctxs[j]);
+    if (alone.empty()) return solve_grouped(ctxs, k, s, t, ms_out);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreateWithFlags(&e0, cudaEventDefault) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e1, cudaEventDefault) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return CFPQ_ERR_CUDA;
+    }
+    int rc = CFPQ_OK;
+    size_t begun = 0;
+    for (cfpq_ctx *c : alone) {
+        if (cudaStreamWaitEvent(c->stream, e0, 0) != cudaSuccess) { rc = CFPQ_ERR_CUDA; break; }
+        if ((rc = solve_begin(c, c->stream)) != CFPQ_OK) break;
+        begun++;
+    }
+    if (rc == CFPQ_OK && !grouped.empty()) rc = solve_grouped(grouped.data(), (int)grouped.size(), s, t, nullptr);
+    for (size_t j = 0; j < begun; j++)  // s waits for every solve begun (even after an error)
+        if (cudaEventRecord(alone[j]->ev1, alone[j]->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(s, alone[j]->ev1, 0) != cudaSuccess)
+            rc = CFPQ_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        rc = CFPQ_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc == CFPQ_ERR_CUDA) return rc;
+    int worst = rc;  // the grouped launch's status (OK, or a limit some of its queries hit)
+    for (size_t j = 0; j < begun; j++) {
+        const int r = solve_end(alone[j], alone[j]->stream);
+        if (r == CFPQ_ERR_CUDA) return r;
+        if (r != CFPQ_OK && worst == CFPQ_OK) worst = r;
+    }
+    if (worst == CFPQ_OK && ms_out) *ms_out = ms;
+    return worst;
+}
+
+// The grouped launch over ctxs; *ms = its device time.
+static int solve_grouped(cfpq_ctx *const *ctxs, int k, cudaStream_t s, const cfpq_batch_tuning &t, float *ms_out) {
     std::lock_guard<std::mutex> lock(g_bufs_mu);
     std::vector<BatchQuery> hb(k);
     bool any_jacobi = false;
@@ -805,6 +853,14 @@ extern "C" int cfpq_autotune_batch(cfpq_ctx *const *ctxs, int32_t k, void *strea
         cand.schedule[c] = cur.schedule[c] == CFPQ_SCHED_INPLACE ? CFPQ_SCHED_JACOBI : CFPQ_SCHED_INPLACE;
         if ((rc = consider(cand)) != CFPQ_OK) return rc;
     }
+    // classes of queries whose own tiles come close to filling the GPU (W > 32 words: n_pad >
+    // 1024) may be solved alone beside the launch, with tensor-core products where they pay
+    for (int c : classes) {
+        if (c < 6) continue;
+        cfpq_batch_tuning cand = cur;
+        cand.product[c] = CFPQ_BATCH_ALONE;
+        if ((rc = consider(cand)) != CFPQ_OK) return rc;
+    }
     // confirm (the contexts end with the chosen configuration's results and statistics)
     float best_ms = 0.f;
     if ((rc = timed(cur, &best_ms)) != CFPQ_OK) return rc;
@@ -813,6 +869,7 @@ extern "C" int cfpq_autotune_batch(cfpq_ctx *const *ctxs, int32_t k, void *strea
         g_tune.blocks_per_sm = cur.blocks_per_sm;
         for (int c : classes) {
             g_tune.cpl[c] = cur.cpl[c];
+            g_tune.product[c] = cur.product[c];
             if (has_auto[c]) g_tune.schedule[c] = cur.schedule[c];
         }
     }

@@ -128,6 +128,10 @@ int enqueue_all_transposes(cfpq_ctx *c, cudaStream_t s);
 // Statistics and status of a solve from a copy of its device state.
 int apply_status(cfpq_ctx *c, const DevState &st);
 int run_loop(cfpq_ctx *c, cudaStream_t s);
+// cfpq_solve in two parts: solve_begin enqueues the solve on s (no host synchronisation),
+// solve_end waits for it and finishes it (status, worklist hand-over, statistics).
+int solve_begin(cfpq_ctx *c, cudaStream_t s);
+int solve_end(cfpq_ctx *c, cudaStream_t s);
 uint32_t gather_chunks(uint32_t W, int *cpl);
 
 // tensor-core product path (cfpq_tensor.cu)

@@ -165,10 +165,16 @@ def test_batch_tuning_host_calls():
         t.schedule[7] = eng.SCHED_JACOBI
         eng.set_batch_tuning(t)
         got = eng.batch_tuning()
-        assert got.as_dict() == {"blocks_per_sm": 4, "cpl": {5: 2, 9: 8}, "schedule": {7: eng.SCHED_JACOBI}}
+        assert got.as_dict() == {"blocks_per_sm": 4, "cpl": {5: 2, 9: 8}, "schedule": {7: eng.SCHED_JACOBI},
+                                 "alone": []}
+        t.product[11] = eng.BATCH_ALONE
+        eng.set_batch_tuning(t)
+        got = eng.batch_tuning()
+        assert got.as_dict()["alone"] == [11]
         # every invalid field is rejected and leaves the installed configuration unchanged
         for field, idx, value in [("blocks_per_sm", None, 9), ("blocks_per_sm", None, -1), ("cpl", 3, 3),
-                                  ("cpl", 4, 16), ("schedule", 6, eng.SCHED_AUTO), ("schedule", 2, -1)]:
+                                  ("cpl", 4, 16), ("schedule", 6, eng.SCHED_AUTO), ("schedule", 2, -1),
+                                  ("product", 8, 2), ("product", 3, -1)]:
             bad = eng.batch_tuning_default()
             if idx is None:
                 setattr(bad, field, value)

@@ -138,3 +138,45 @@ def test_tuned_solve_rejects_invalid_configuration():
     t = eng.batch_tuning_default()
     t.cpl[3] = 3
     assert eng.solve_batch([q], tuning=t, check=False) == eng.ERR_INVALID
+
+
+def _mixed_dense_batch():
+    """Sparse hierarchy queries (n 64..1500) with block-diagonal closures of 2,048-8,192
+    nodes (communities of 512, S -> S S | t0), all created on the automatic path."""
+    out = []
+    for graph, text in synth.batch_queries(24, 64, 1500, 0.3, seed=31):
+        g = eng.Grammar(text, graph.labels)
+        out.append((graph, text, g, eng.Query(g, graph.n, graph.edges)))
+    for j, n in enumerate([2048, 3000, 4096, 6000, 8192]):
+        graph = synth.communities(n, max(1, n // 512), 2, seed=40 + j)
+        text = "S S S\nS t0\n"
+        g = eng.Grammar(text, graph.labels)
+        out.append((graph, text, g, eng.Query(g, graph.n, graph.edges)))
+    return out
+
+
+def test_classes_solved_alone_give_the_same_result():
+    # the large classes leave the grouped launch (each query on its context's stream, with
+    # the automatic product choice, tensor products included): same triples as grouped
+    batch = _mixed_dense_batch()
+    qs = [b[3] for b in batch]
+    eng.solve_batch(qs, tuning=eng.batch_tuning_default())
+    grouped = [{nm: q.get(nm) for nm in g.names} for _, _, g, q in batch]
+    t = eng.batch_tuning_default()
+    for c in range(6, eng.TUNE_CLASSES):
+        t.product[c] = eng.BATCH_ALONE
+    eng.solve_batch(qs, tuning=t)
+    assert sum(q.stats()["tensor_products"] for q in qs) > 0  # the dense classes took the tensor cores
+    for (graph, text, g, q), prev in zip(batch, grouped):
+        for nm in g.names:
+            assert np.array_equal(q.get(nm), prev[nm]), (graph.n, nm)
+    _check_oracle(batch)
+
+
+def test_autotune_solves_dense_large_classes_alone():
+    batch = _mixed_dense_batch()
+    qs = [b[3] for b in batch]
+    best, report = eng.autotune_batch(qs)
+    assert best.as_dict()["alone"], best.as_dict()
+    assert report["best_ms"] < report["default_ms"]
+    _check_oracle(batch)
