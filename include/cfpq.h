@@ -317,6 +317,37 @@ int cfpq_block_import(cfpq_ctx *ctx, const uint32_t *buf, size_t words, void *st
  * ITER_LIMIT, TIMEOUT, CUDA. */
 int cfpq_block_finish(cfpq_ctx *ctx, void *stream, int32_t *changed);
 
+/*
+ * Checkpoint and resume of the fixpoint loop. After k executions of Algorithm 1's loop
+ * (Section 4.2) the loop's whole state is T_k and the pairs the k-th execution added (the
+ * next execution's semi-naive delta), with their row bitmaps and counts. The closure is
+ * monotone with a unique least fixpoint (Theorem 2), so resuming from a saved state reaches
+ * the same result as an uninterrupted solve, after the same total number of executions
+ * under the Jacobi schedule. Only contexts on a matrix path without lengths, and not row
+ * blocks, have this state (UNSUPPORTED otherwise).
+ *   cfpq_state_size    bytes of a state image of this context (host memory)
+ *   cfpq_export_state  copies the state after a cfpq_solve or cfpq_resume that returned
+ *                      (OK, ITER_LIMIT or TIMEOUT) into buf (cap bytes); NOT_SOLVED before
+ *                      any solve, UNSUPPORTED if the worklist path finished the solve, BUFFER
+ *                      if cap is too small
+ *   cfpq_import_state  loads an image into a context created with the same grammar, n and
+ *                      edges (INVALID if the image does not fit it; the product path and the
+ *                      schedule may differ, as every choice reaches the same fixpoint); a
+ *                      cfpq_resume then continues the loop from it
+ *   cfpq_resume        continues the loop of an interrupted solve (ITER_LIMIT, TIMEOUT) or
+ *                      of an imported state without re-seeding: at most more_executions
+ *                      further executions (0: up to Theorem 3's bound, |V|^2 |N| + 1
+ *                      executions in all, whatever cap the context was created with), then as
+ *                      cfpq_solve (the same statuses; the relations are read the same way).
+ *                      NOT_SOLVED if there is nothing to resume
+ * The image holds a header and then, bit-packed as on the device, T, the delta plane, its
+ * row bitmap, T's row bitmap and T's word summary; it is tied to this library's layout.
+ */
+int cfpq_state_size(const cfpq_ctx *ctx, size_t *bytes);
+int cfpq_export_state(cfpq_ctx *ctx, void *buf, size_t cap);
+int cfpq_import_state(cfpq_ctx *ctx, const void *buf, size_t bytes);
+int cfpq_resume(cfpq_ctx *ctx, void *stream, int64_t more_executions);
+
 /* |R_A| without copying pairs (for the start symbol, the #results column of the tables of
  * Section 6, diagonal pairs included). Errors: as cfpq_get. */
 int cfpq_count(cfpq_ctx *ctx, int32_t A, size_t *count);

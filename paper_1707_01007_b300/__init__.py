@@ -185,6 +185,10 @@ SIGNATURES = {
     "cfpq_block_export": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _P(ctypes.c_size_t), _VP]),
     "cfpq_block_import": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _VP]),
     "cfpq_block_finish": (ctypes.c_int, [_VP, _VP, _P(ctypes.c_int32)]),
+    "cfpq_state_size": (ctypes.c_int, [_VP, _P(ctypes.c_size_t)]),
+    "cfpq_export_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    "cfpq_import_state": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    "cfpq_resume": (ctypes.c_int, [_VP, _VP, ctypes.c_int64]),
 }
 EXPORTS = sorted(SIGNATURES)
 
@@ -369,6 +373,27 @@ class Query:
         _check(_lib().cfpq_get_all_device(self._h, ctypes.c_void_p(dev_ptr) if dev_ptr else None, cap,
                                           ctypes.byref(c)), "cfpq_get_all_device")
         return int(c.value)
+
+    # checkpoint and resume of the loop (cfpq_export_state / cfpq_import_state / cfpq_resume)
+    def export_state(self) -> np.ndarray:
+        """The loop's state (T, the next execution's delta, bitmaps, counts) as a uint8 array."""
+        n = ctypes.c_size_t()
+        _check(_lib().cfpq_state_size(self._h, ctypes.byref(n)), "cfpq_state_size")
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(_lib().cfpq_export_state(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size), "cfpq_export_state")
+        return buf
+
+    def import_state(self, image: np.ndarray):
+        image = np.ascontiguousarray(image, dtype=np.uint8)
+        _check(_lib().cfpq_import_state(self._h, image.ctypes.data_as(ctypes.c_void_p), image.size),
+               "cfpq_import_state")
+
+    def resume(self, stream=None, more_executions: int = 0, check: bool = True) -> int:
+        code = _lib().cfpq_resume(self._h, _stream_handle(stream), int(more_executions))
+        self.status = code
+        if check:
+            _check(code, "cfpq_resume")
+        return code
 
     # sharded solve by row blocks (contexts created with row_begin / row_end): the calls of
     # cfpq_block_*; the exchange between them is the caller's (see shard.py)

@@ -1462,6 +1462,8 @@ int cfpq::solve_end(cfpq_ctx *c, cudaStream_t s) {
     // a loop that converged leaves both delta planes zero (each execution clears the delta it
     // read, the last one adds nothing); the worklist path and an interrupted loop do not
     c->clean = rc == CFPQ_OK && !c->switched && c->path != CFPQ_PATH_WORKLIST && c->n_groups > 0;
+    // an interrupted loop can go on from where it stopped (cfpq_resume)
+    c->resumable = (rc == CFPQ_ERR_ITER_LIMIT || rc == CFPQ_ERR_TIMEOUT) && !c->switched;
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
     c->stats.solve_ms = ms;

@@ -39,6 +39,7 @@ struct cfpq_ctx {
     void *d_tile_list = nullptr;      // tile skipping: live output tiles of one product (uint2 each; arena)
     bool dense_tensor = false;        // tensor products over every K step (no tile skipping)
     int tensor_kind = CFPQ_TENSOR_FP4;  // operand format of the tensor products (FP8 or FP4, resolved)
+    bool resumable = false;           // the device holds an interrupted or imported loop state (cfpq_resume)
     bool block = false;               // sharded solve: the products compute rows [row0, row1) only
     bool block_started = false;       // cfpq_block_start ran and the solve has not finished yet
     uint32_t row0 = 0, row1 = 0;      // the row block (row1 = n_pad for the last block)

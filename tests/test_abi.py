@@ -127,6 +127,10 @@ def test_lengths_options_checked_before_device_use():
     assert lib.cfpq_block_export(None, None, 0, None, None) == eng.ERR_INVALID
     assert lib.cfpq_block_import(None, None, 0, None) == eng.ERR_INVALID
     assert lib.cfpq_block_finish(None, None, None) == eng.ERR_INVALID
+    assert lib.cfpq_state_size(None, None) == eng.ERR_INVALID
+    assert lib.cfpq_export_state(None, None, 0) == eng.ERR_INVALID
+    assert lib.cfpq_import_state(None, None, 0) == eng.ERR_INVALID
+    assert lib.cfpq_resume(None, None, 0) == eng.ERR_INVALID
     assert lib.cfpq_get_path(None, 0, 0, 0, None, None, 0, None) == eng.ERR_INVALID
 
 
