@@ -545,6 +545,8 @@ def engine_arm(args):
             leg.step()
             ams = leg.time(max(2, min(args.steps, 5)))
             alternatives[name] = {"ms_per_step": ams, "value": world * ops_per_step / (ams / 1e3) / 1e9,
+                                  "step_ms": {"best": min(leg.step_ms), "median": float(np.median(leg.step_ms)),
+                                              "worst": max(leg.step_ms)},
                                   "iterations": [q.stats()["iterations"] for q in leg.qs],
                                   "tensor_products": sum(q.stats()["tensor_products"] for q in leg.qs),
                                   "gather_products": sum(q.stats()["gather_products"] for q in leg.qs),

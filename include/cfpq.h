@@ -19,7 +19,10 @@
  *     aborts the process; cfpq_strerror() names a code;
  *   - the library copies every input array during the call; the caller keeps ownership
  *     of everything it passes and of every output buffer;
- *   - all device memory belongs to a context and is released by cfpq_destroy();
+ *   - all device memory belongs to a context and is released by cfpq_destroy(); the
+ *     contexts of cfpq_create take it from a memory pool of the library (one per device),
+ *     which keeps what destroyed contexts released for the next ones until
+ *     cfpq_trim_memory() hands it back to the system;
  *   - a context is not thread-safe; distinct contexts may be used from distinct threads.
  *
  * Limits: 1 <= n <= CFPQ_MAX_NODES, 1 <= |N| <= CFPQ_MAX_NONTERM.
@@ -357,8 +360,18 @@ int cfpq_count(cfpq_ctx *ctx, int32_t A, size_t *count);
  * Errors: INVALID. */
 int cfpq_stats_get(const cfpq_ctx *ctx, cfpq_stats *out);
 
-/* Releases the context and its device memory; NULL is ignored. */
+/* Releases the context and its device memory; NULL is ignored. Waits for the device's
+ * outstanding work first (as cudaFree does), then returns the memory to the library's pool
+ * of the context's device, where the next cfpq_create reuses it without a new allocation. */
 void cfpq_destroy(cfpq_ctx *ctx);
+
+/* Hands the device memory that the library's pool on the current device holds unused (what
+ * destroyed contexts released) back to the system, keeping at most keep_bytes reserved
+ * (0: everything unused). Memory of live contexts is not touched. Not part of the paper's
+ * method: a memory-management call of this library. A pool that cannot allocate trims
+ * itself this way once before it reports CFPQ_ERR_NOMEM. Errors: UNSUPPORTED (the device
+ * has no memory pools), CUDA. */
+int cfpq_trim_memory(size_t keep_bytes);
 
 /* Static string naming a status code. */
 const char *cfpq_strerror(int code);

@@ -56,6 +56,17 @@ class Triple(ctypes.Structure):
     _fields_ = [("A", ctypes.c_int32), ("m", ctypes.c_uint32), ("n", ctypes.c_uint32)]
 
 
+def _triple_rows(k: int) -> np.ndarray:
+    """A host buffer for k cfpq_triple records as a (k, 3) uint32 array: the record is three
+    32-bit words, and A (a non-terminal id) and m, n (< CFPQ_MAX_NODES) are non-negative,
+    so the unsigned view reads every field exactly."""
+    return np.empty((max(k, 1), 3), dtype="<u4")
+
+
+def _triple_ptr(buf: np.ndarray):
+    return buf.ctypes.data_as(ctypes.POINTER(Triple))
+
+
 class Options(ctypes.Structure):
     _fields_ = [("schedule", ctypes.c_int32), ("path", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_iter", ctypes.c_int64), ("timeout_s", ctypes.c_double),
@@ -150,6 +161,7 @@ SIGNATURES = {
                                      _P(ctypes.c_int32), ctypes.c_size_t, _P(ctypes.c_size_t)]),
     "cfpq_stats_get": (ctypes.c_int, [_VP, _P(Stats)]),
     "cfpq_destroy": (None, [_VP]),
+    "cfpq_trim_memory": (ctypes.c_int, [ctypes.c_size_t]),
     "cfpq_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "cfpq_grammar_parse": (ctypes.c_int, [ctypes.c_char_p, _P(ctypes.c_char_p), ctypes.c_int32, _P(_VP),
                                           ctypes.c_char_p, ctypes.c_size_t]),
@@ -309,26 +321,28 @@ class Query:
         c = ctypes.c_size_t()
         _check(_lib().cfpq_get(self._h, a, None, 0, ctypes.byref(c)), "cfpq_get")
         k = int(c.value)
-        buf = np.zeros(max(k, 1), dtype=[("A", "<i4"), ("m", "<u4"), ("n", "<u4")])
-        _check(_lib().cfpq_get(self._h, a, buf.ctypes.data_as(ctypes.POINTER(Triple)), k, ctypes.byref(c)),
-               "cfpq_get")
-        buf = buf[:k]
-        return np.stack([buf["A"].astype(np.int64), buf["m"].astype(np.int64), buf["n"].astype(np.int64)], axis=1)
+        buf = _triple_rows(k)
+        _check(_lib().cfpq_get(self._h, a, _triple_ptr(buf), k, ctypes.byref(c)), "cfpq_get")
+        return buf[:k].astype(np.int64)
 
     def triples_all(self) -> np.ndarray:
         """Every relation as an (k, 3) int64 array of (A, m, n), sorted (``cfpq_get_all``)."""
         c = ctypes.c_size_t()
         _check(_lib().cfpq_get_all(self._h, None, 0, ctypes.byref(c)), "cfpq_get_all")
         k = int(c.value)
-        buf = np.zeros(max(k, 1), dtype=[("A", "<i4"), ("m", "<u4"), ("n", "<u4")])
-        _check(_lib().cfpq_get_all(self._h, buf.ctypes.data_as(ctypes.POINTER(Triple)), k, ctypes.byref(c)),
-               "cfpq_get_all")
-        buf = buf[:k]
-        return np.stack([buf["A"].astype(np.int64), buf["m"].astype(np.int64), buf["n"].astype(np.int64)], axis=1)
+        buf = _triple_rows(k)
+        _check(_lib().cfpq_get_all(self._h, _triple_ptr(buf), k, ctypes.byref(c)), "cfpq_get_all")
+        return buf[:k].astype(np.int64)
 
     def get(self, A) -> np.ndarray:
         """R_A as a sorted (k, 2) uint32 array of (m, n)."""
-        return self.triples(A)[:, 1:].astype(np.uint32)
+        a = self._aid(A)
+        c = ctypes.c_size_t()
+        _check(_lib().cfpq_get(self._h, a, None, 0, ctypes.byref(c)), "cfpq_get")
+        k = int(c.value)
+        buf = _triple_rows(k)
+        _check(_lib().cfpq_get(self._h, a, _triple_ptr(buf), k, ctypes.byref(c)), "cfpq_get")
+        return np.ascontiguousarray(buf[:k, 1:])
 
     def lengths(self, A):
         """Single-path semantics (``cfpq_get_lengths``): R_A as a sorted (k, 2) uint32 array of
@@ -337,13 +351,12 @@ class Query:
         c = ctypes.c_size_t()
         _check(_lib().cfpq_get_lengths(self._h, a, None, None, 0, ctypes.byref(c)), "cfpq_get_lengths")
         k = int(c.value)
-        buf = np.zeros(max(k, 1), dtype=[("A", "<i4"), ("m", "<u4"), ("n", "<u4")])
-        lens = np.zeros(max(k, 1), dtype=np.uint32)
-        _check(_lib().cfpq_get_lengths(self._h, a, buf.ctypes.data_as(ctypes.POINTER(Triple)),
+        buf = _triple_rows(k)
+        lens = np.empty(max(k, 1), dtype=np.uint32)
+        _check(_lib().cfpq_get_lengths(self._h, a, _triple_ptr(buf),
                                        lens.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), k, ctypes.byref(c)),
                "cfpq_get_lengths")
-        pairs = np.stack([buf["m"][:k], buf["n"][:k]], axis=1).astype(np.uint32)
-        return pairs, lens[:k]
+        return np.ascontiguousarray(buf[:k, 1:]), lens[:k]
 
     def path(self, A, m: int, n: int):
         """Single-path semantics (``cfpq_get_path``): one walk from m to n whose labels A
@@ -502,11 +515,10 @@ class Server:
         c = ctypes.c_size_t()
         _check(_lib().cfpq_server_result(self._h, ticket, A, None, 0, ctypes.byref(c)), "cfpq_server_result")
         k = int(c.value)
-        buf = np.zeros(max(k, 1), dtype=[("A", "<i4"), ("m", "<u4"), ("n", "<u4")])
-        _check(_lib().cfpq_server_result(self._h, ticket, A, buf.ctypes.data_as(ctypes.POINTER(Triple)), k,
-                                         ctypes.byref(c)), "cfpq_server_result")
-        buf = buf[:k]
-        return np.stack([buf["m"], buf["n"]], axis=1).astype(np.uint32)
+        buf = _triple_rows(k)
+        _check(_lib().cfpq_server_result(self._h, ticket, A, _triple_ptr(buf), k, ctypes.byref(c)),
+               "cfpq_server_result")
+        return np.ascontiguousarray(buf[:k, 1:])
 
     def release(self, ticket: int):
         _check(_lib().cfpq_server_release(self._h, ticket), "cfpq_server_release")
@@ -604,3 +616,9 @@ def measure_tensor_peaks() -> dict:
     p = TensorPeaks()
     _check(_lib().cfpq_measure_tensor_peaks(ctypes.byref(p)), "cfpq_measure_tensor_peaks")
     return p.as_dict()
+
+
+def trim_memory(keep_bytes: int = 0):
+    """Hands the device memory that destroyed queries left in the library's pool on the
+    current device back to the system, keeping at most keep_bytes (``cfpq_trim_memory``)."""
+    _check(_lib().cfpq_trim_memory(int(keep_bytes)), "cfpq_trim_memory")

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -943,17 +944,70 @@ static int build_graph(cfpq_ctx *c) {
     return CFPQ_OK;
 }
 
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+}  // namespace
+
+cudaMemPool_t library_pool(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pool[dev]) return g_pool[dev];
+    int supported = 0;
+    if (cudaDeviceGetAttribute(&supported, cudaDevAttrMemoryPoolsSupported, dev) != cudaSuccess || !supported) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    // freed memory stays in the pool across synchronisations (the default threshold, zero,
+    // would hand it back at every stream synchronisation)
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+    return pool;
+}
+
+cudaError_t ctx_alloc(cfpq_ctx *c, void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        cudaMemPoolTrimTo(c->pool, 0);
+        e = cudaMallocFromPoolAsync(p, bytes, c->pool, s);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+    }
+    return e;
+}
+
+void ctx_free(cfpq_ctx *c, void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
 void free_ctx_device(cfpq_ctx *c) {
+    // A context of cfpq_create may still have work in flight on a caller's stream or on its
+    // side streams: let it finish before its memory goes back to the pool (cudaFree used to
+    // synchronise the device in the same way). A server's contexts are retired only after
+    // their stream's work has completed.
+    if (!c->pooled) cudaDeviceSynchronize();
     tensor_release(c);
     worklist_release(c);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
     void *ptrs[] = {c->d_arena, c->d_triples, c->d_tc_work, c->d_lens};
-    for (void *p : ptrs)
-        if (p) {
-            if (c->pooled) cudaFreeAsync(p, c->stream);
-            else cudaFree(p);
-        }
+    for (void *p : ptrs) ctx_free(c, p, c->stream);
     for (auto e : c->prof_ev)
         if (e) cudaEventDestroy(e);
     c->prof_ev.clear();
@@ -1050,6 +1104,14 @@ int apply_status(cfpq_ctx *c, const DevState &st) {
     int rc = CFPQ_OK;
     if (st.error == kErrIterLimit) rc = CFPQ_ERR_ITER_LIMIT;
     else if (st.error == kErrTimeout) rc = CFPQ_ERR_TIMEOUT;
+    else if (st.error == kErrDevice) {
+        rc = CFPQ_ERR_CUDA;
+        if (getenv("CFPQ_VERBOSE"))
+            fprintf(stderr,
+                    "cfpq: a tensor product gave up: wait site %u, CTA %u, group %u, execution %u, %u tiles listed, "
+                    "%u tiles claimed\n",
+                    st.tc_diag[0], st.tc_diag[1] - 1u, st.tc_diag[2], st.tc_diag[3], st.tc_diag[4], st.tc_diag[5]);
+    }
     c->stats.status = rc;
     return rc;
 }
@@ -1203,10 +1265,18 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_tile_list, occ ? (size_t)(c->n_pad / 256) * (c->n_pad / 128) * 8 : 0}};
     size_t arena = 0;
     for (const Part &pt : parts) arena += (pt.bytes + 255) / 256 * 256;
+    if (!c->pool) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        c->pool = library_pool(dev);
+        if (!c->pool) return CFPQ_ERR_UNSUPPORTED;
+    }
     {
-        const cudaError_t e = c->pooled ? cudaMallocAsync(&c->d_arena, arena, c->stream) : cudaMalloc(&c->d_arena, arena);
-        if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); c->d_arena = nullptr; return CFPQ_ERR_NOMEM; }
-        if (e != cudaSuccess) { c->d_arena = nullptr; return CFPQ_ERR_CUDA; }
+        void *arena_p = nullptr;
+        const cudaError_t e = ctx_alloc(c, &arena_p, arena, c->stream);
+        if (e == cudaErrorMemoryAllocation) return CFPQ_ERR_NOMEM;
+        if (e != cudaSuccess) return CFPQ_ERR_CUDA;
+        c->d_arena = arena_p;
     }
     {
         char *p = static_cast<char *>(c->d_arena);
@@ -1283,6 +1353,9 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     c->hq = q;
     CK(cudaMemcpyAsync(c->d_q, &q, sizeof(q), cudaMemcpyHostToDevice, cs));
     if (c->path == CFPQ_PATH_WORKLIST) return worklist_setup(c, edges, n_edges);
+    // the set-up above ran on the context's stream, and a solve may run on any stream the
+    // caller names: finish it here (a server's contexts share the server's stream)
+    if (!c->pooled) CK(cudaStreamSynchronize(cs));
     return CFPQ_OK;
 }
 
@@ -1342,6 +1415,12 @@ int ctx_create_pooled(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *ed
     c->pooled = true;
     c->stream = pool_stream;
     c->own_stream = false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&c->pool, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return CFPQ_ERR_CUDA;
+    }
     const int rc = ctx_init(c, g, n, edges, n_edges, o);
     if (rc != CFPQ_OK) {
         free_ctx_device(c);
@@ -1599,19 +1678,12 @@ namespace cfpq {
 // Grows the context's device triples buffer to hold `total` triples.
 int ensure_triples(cfpq_ctx *c, size_t total, cudaStream_t s) {
     if (c->triples_cap >= total) return CFPQ_OK;
-    if (c->d_triples) {
-        if (c->pooled) cudaFreeAsync(c->d_triples, s);
-        else cudaFree(c->d_triples);
-    }
+    ctx_free(c, c->d_triples, s);
     c->d_triples = nullptr;
     c->triples_cap = 0;
-    const cudaError_t e = c->pooled ? cudaMallocAsync(&c->d_triples, total * sizeof(cfpq_triple), s)
-                                    : cudaMalloc(&c->d_triples, total * sizeof(cfpq_triple));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        c->d_triples = nullptr;
-        return CFPQ_ERR_NOMEM;
-    }
+    void *p = nullptr;
+    if (ctx_alloc(c, &p, total * sizeof(cfpq_triple), s) != cudaSuccess) return CFPQ_ERR_NOMEM;
+    c->d_triples = static_cast<cfpq_triple *>(p);
     c->triples_cap = total;
     return CFPQ_OK;
 }
@@ -1717,19 +1789,12 @@ extern "C" int cfpq_get_lengths(cfpq_ctx *c, int32_t A, cfpq_triple *buf, uint32
     if (total == 0) return CFPQ_OK;
     if ((rc = ensure_triples(c, total, s)) != CFPQ_OK) return rc;
     if (c->lens_cap < total) {
-        if (c->d_lens) {
-            if (c->pooled) cudaFreeAsync(c->d_lens, s);
-            else cudaFree(c->d_lens);
-        }
+        ctx_free(c, c->d_lens, s);
         c->d_lens = nullptr;
         c->lens_cap = 0;
-        const cudaError_t e = c->pooled ? cudaMallocAsync(&c->d_lens, total * sizeof(uint32_t), s)
-                                        : cudaMalloc(&c->d_lens, total * sizeof(uint32_t));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            c->d_lens = nullptr;
-            return CFPQ_ERR_NOMEM;
-        }
+        void *p = nullptr;
+        if (ctx_alloc(c, &p, total * sizeof(uint32_t), s) != cudaSuccess) return CFPQ_ERR_NOMEM;
+        c->d_lens = static_cast<uint32_t *>(p);
         c->lens_cap = total;
     }
     if ((rc = emit(c, A, c->d_triples, s)) != CFPQ_OK) return rc;
@@ -1785,4 +1850,19 @@ extern "C" void cfpq_destroy(cfpq_ctx *c) {
     if (!c) return;
     free_ctx_device(c);
     delete c;
+}
+
+extern "C" int cfpq_trim_memory(size_t keep_bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CFPQ_ERR_CUDA;
+    }
+    cudaMemPool_t pool = cfpq::library_pool(dev);
+    if (!pool) return CFPQ_ERR_UNSUPPORTED;
+    if (cudaMemPoolTrimTo(pool, keep_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return CFPQ_ERR_CUDA;
+    }
+    return CFPQ_OK;
 }

@@ -29,7 +29,10 @@ namespace cfpq {
 
 constexpr int kMaxNT = CFPQ_MAX_NONTERM;
 
-enum : uint32_t { kErrNone = 0, kErrIterLimit = 1, kErrTimeout = 2 };
+// kErrDevice: a tensor-core product gave up on a bounded wait, so some of its output tiles
+// are missing; the loop stops and the solve fails (CFPQ_ERR_CUDA) instead of converging on an
+// incomplete product
+enum : uint32_t { kErrNone = 0, kErrIterLimit = 1, kErrTimeout = 2, kErrDevice = 3 };
 
 // A loop execution that adds at most kSmallDelta pairs is "small"; after kSwitchAfter small
 // executions in a row, a loop that may switch hands the closure to the worklist path (a long
@@ -69,6 +72,8 @@ struct DevState {
     unsigned int occ_probe;             // AUTO: refresh tile occupancy this execution for the cost model
     unsigned long long block_records;   // sharded solve: records packed by the last export
     unsigned int block_bad;             // sharded solve: an imported record was out of range
+    unsigned int tc_diag[6];            // first tensor product that gave up: wait site, CTA + 1, group,
+                                        // execution, listed tiles, tiles claimed
 };
 
 struct Rule {
@@ -447,6 +452,7 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
         st->changed = 0u;
         st->iter = it + 1;
         unsigned cont = changed ? 1u : 0u;
+        if (ld_u32(&st->error) == kErrDevice) cont = 0;
         if (cont && q.allow_switch) {
             st->small_run = s_added <= kSmallDelta ? st->small_run + 1u : 0u;
             if (st->small_run >= kSwitchAfter) {

@@ -80,7 +80,8 @@ struct cfpq_ctx {
     // execution
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    bool pooled = false;                     // device memory from the stream-ordered pool of `stream`
+    bool pooled = false;                     // a server's context: runs on the server's stream
+    cudaMemPool_t pool = nullptr;            // every device buffer of the context comes from this pool
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaStream_t aux_stream = nullptr;       // capture the branches of the AUTO choice nodes
@@ -106,11 +107,19 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
              const cfpq_options &o);
 int validate_inputs(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
                     const cfpq_options *opt);
-// Creates a context whose device memory comes from the stream-ordered pool of `pool_stream`
-// and which runs on that stream (used by the server); inputs must be validated already.
+// Creates a context whose device memory comes from the device's default memory pool and
+// which runs on `pool_stream` (used by the server); inputs must be validated already.
 int ctx_create_pooled(const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge *edges, size_t n_edges,
                       const cfpq_options &o, cudaStream_t pool_stream, cfpq_ctx **out);
 void ctx_destroy(cfpq_ctx *c);
+// The library's memory pool on device `dev`: the contexts of cfpq_create allocate from it,
+// and memory they free stays reserved in it for the next context (cfpq_trim_memory returns
+// it to the system). Created on first use; nullptr if the device has no memory pools.
+cudaMemPool_t library_pool(int dev);
+// Stream-ordered allocation of `bytes` from the context's pool on stream s; when the pool is
+// out of memory it gives back what it holds unused and tries once more.
+cudaError_t ctx_alloc(cfpq_ctx *c, void **p, size_t bytes, cudaStream_t s);
+void ctx_free(cfpq_ctx *c, void *p, cudaStream_t s);
 int ensure_triples(cfpq_ctx *c, size_t total, cudaStream_t s);
 int extract_all_host(cfpq_ctx *c, std::vector<std::vector<cfpq_triple>> &out);
 // Bytes of device memory a context for this query holds (path GATHER unless tensor).

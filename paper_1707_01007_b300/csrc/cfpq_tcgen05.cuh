@@ -32,17 +32,17 @@ __device__ __forceinline__ bool mbar_try(unsigned long long *b, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false (and the CTA's error flag set) if the phase did not complete in time
-// or another role of the CTA already gave up.
+// Bounded wait: false if the phase did not complete in time (the CTA's error flag then holds
+// `site`, which names the wait that gave up) or another role of the CTA already gave up.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *b, uint32_t parity, volatile int *err,
-                                          unsigned long long limit_ns = WAIT_LIMIT_NS) {
+                                          unsigned long long limit_ns = WAIT_LIMIT_NS, int site = 1) {
     if (mbar_try(b, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
         if (mbar_try(b, parity)) return true;
         if (*err) return false;
         if (globaltimer_ns() - t0 > limit_ns) {
-            *err = 1;
+            *err = site;
             return false;
         }
     }

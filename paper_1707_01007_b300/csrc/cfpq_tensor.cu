@@ -87,7 +87,7 @@ struct __align__(1024) Smem {
     unsigned long long tile_full[2], tile_empty[2];  // tile skipping: claimed tile handed to the consumers
     uint32_t tile_q[2];
     uint32_t tmem_base;
-    int err;
+    int err;  // 0, or the wait site that gave up (100: the plan and the bitmaps disagree)
 };
 
 template <int KIND>
@@ -326,18 +326,22 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint64_t i = (uint64_t)blockIdx.x + (uint64_t)ord * gridDim.x;
             return i < ntile ? (uint32_t)i : kNoTile;
         }
-        if (!mbar_wait(&S.tile_empty[ord & 1u], ((ord >> 1) & 1u) ^ 1u, err)) return kNoTile;
+        if (!mbar_wait(&S.tile_empty[ord & 1u], ((ord >> 1) & 1u) ^ 1u, err, WAIT_LIMIT_NS, 1)) {
+            return kNoTile;
+        }
         const uint32_t i = atomicAdd(take, 1u);
         S.tile_q[ord & 1u] = i < ntile ? i : kNoTile;
         mbar_arrive(&S.tile_full[ord & 1u]);
         return i < ntile ? i : kNoTile;
     };
-    auto read_tile = [&](uint32_t ord) -> uint32_t {
+    auto read_tile = [&](uint32_t ord, uint32_t role) -> uint32_t {
         if (!list) {
             const uint64_t i = (uint64_t)blockIdx.x + (uint64_t)ord * gridDim.x;
             return i < ntile ? (uint32_t)i : kNoTile;
         }
-        if (!mbar_wait(&S.tile_full[ord & 1u], (ord >> 1) & 1u, err)) return kNoTile;
+        if (!mbar_wait(&S.tile_full[ord & 1u], (ord >> 1) & 1u, err, WAIT_LIMIT_NS, 2)) {
+            return kNoTile;
+        }
         const uint32_t i = S.tile_q[ord & 1u];
         mbar_arrive(&S.tile_empty[ord & 1u]);
         return i;
@@ -366,7 +370,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                             live &= live - 1;
                             const uint32_t s = issued;
                             const uint32_t slot = s % PST, ph = (s / PST) & 1u;
-                            if (!mbar_wait(&S.empty_p[slot], ph ^ 1u, err)) {
+                            if (!mbar_wait(&S.empty_p[slot], ph ^ 1u, err, WAIT_LIMIT_NS, 3)) {
                                 stop = true;
                                 break;
                             }
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
                 if (!stop && done != e.y) {  // the plan and the bitmaps disagree: give up cleanly
-                    *err = 1;
+                    *err = 100;
                     stop = true;
                 }
             }
@@ -400,16 +404,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t s = 0, tiles_done = 0;
             bool stop = false;
             for (uint32_t ord = 0; !stop; ord++) {
-                const uint32_t i = read_tile(ord);
+                const uint32_t i = read_tile(ord, 0u);
                 if (i == kNoTile) break;
                 const uint32_t steps = list ? list[i].y : dense_steps;
                 if (tiles_done > 0) {  // the epilogue has read the previous tile's accumulator
-                    if (!mbar_wait(&S.acc_empty, (tiles_done - 1) & 1u, err)) break;
+                    if (!mbar_wait(&S.acc_empty, (tiles_done - 1) & 1u, err, WAIT_LIMIT_NS, 4)) {
+                        break;
+                    }
                     tc_fence_after();
                 }
                 for (uint32_t u = 0; u < steps; u++, s++) {
                     const uint32_t slot = s % UST, ph = (s / UST) & 1u;
-                    if (!mbar_wait(&S.full_u[slot], ph, err)) {
+                    if (!mbar_wait(&S.full_u[slot], ph, err, WAIT_LIMIT_NS, 5)) {
                         stop = true;
                         break;
                     }
@@ -469,8 +475,26 @@ __global__ void __launch_bounds__(THREADS, 1)
         auto unpack_until = [&](uint32_t limit) -> bool {
             for (; sn < limit; sn += UNPACK_GROUPS) {
                 const uint32_t ps = sn % PST, pph = (sn / PST) & 1u;
-                if (!mbar_wait(&S.full_p[ps], pph, err)) return false;
-                if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err)) return false;
+                if constexpr (PST % UNPACK_GROUPS != 0) {
+                    // With an odd packed ring the groups take turns on each slot: this group's
+                    // waits on full_p[ps] skip every other phase, and a parity wait cannot tell
+                    // the phase of stage sn from the one two before it, which is complete while
+                    // the other group's stage sn - PST (TMA loads land in any order) may not
+                    // have landed yet. So first wait until the other group has consumed stage
+                    // sn - PST (phase sn / PST - 1 of empty_p[ps]; the phase before it is this
+                    // group's own, already passed): full_p[ps] is then at most one phase behind.
+                    if (sn >= (uint32_t)PST) {
+                        if (!mbar_wait(&S.empty_p[ps], ((sn / PST) - 1u) & 1u, err, WAIT_LIMIT_NS, 9)) {
+                            return false;
+                        }
+                    }
+                }
+                if (!mbar_wait(&S.full_p[ps], pph, err, WAIT_LIMIT_NS, 6)) {
+                    return false;
+                }
+                if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err, WAIT_LIMIT_NS, 7)) {
+                    return false;
+                }
                 tc_fence_after();
                 uint32_t pa[KW / 2], pb[KW];  // this lane's half row of A and the thread's row of B
                 if constexpr (KIND == 0) {
@@ -502,7 +526,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             return true;
         };
         uint32_t ord = 0;  // this CTA's ord-th tile (t is the thread's B row)
-        uint32_t i = read_tile(0);
+        uint32_t i = read_tile(0, 1u);
         uint32_t m0 = 0, n0 = 0;
         if (i != kNoTile) {
             const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
@@ -514,7 +538,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // the next tile's first stages (at most UST: their ring slots are freed by this
             // tile's own MMAs, which wait for nothing else) are unpacked before this tile's
             // epilogue, so that its MMAs can start as soon as the accumulator is handed back
-            const uint32_t i2 = fine ? read_tile(ord + 1) : kNoTile;
+            const uint32_t i2 = fine ? read_tile(ord + 1, 1u) : kNoTile;
             uint32_t m2 = 0, n2 = 0, s_end2 = s_end;
             if (i2 != kNoTile) {
                 const uint2 e2 = list ? list[i2] : make_uint2(i2, dense_steps);
@@ -522,7 +546,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 s_end2 = s_end + e2.y;
                 fine = unpack_until(min(s_end2, s_end + (uint32_t)UST));
             }
-            const bool ok = fine && !*err && mbar_wait(&S.acc_full, tiles_done & 1u, err);
+            const bool ok = fine && !*err && mbar_wait(&S.acc_full, tiles_done & 1u, err, WAIT_LIMIT_NS, 8);
             tc_fence_after();
             const uint32_t row = m0 + quad * 32 + lane;
             unsigned cnt = 0;
@@ -574,7 +598,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0 && S.err) atomicExch(&st->error, 3u);
+    if (threadIdx.x == 0 && S.err) {
+        atomicExch(&st->error, kErrDevice);
+        if (atomicCAS(&st->tc_diag[0], 0u, (unsigned)S.err) == 0u) {
+            st->tc_diag[1] = blockIdx.x + 1u;
+            st->tc_diag[2] = (unsigned)g;
+            st->tc_diag[3] = (unsigned)st->iter;
+            st->tc_diag[4] = ntile;
+            st->tc_diag[5] = list ? __ldcg(take) : 0u;
+        }
+    }
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");

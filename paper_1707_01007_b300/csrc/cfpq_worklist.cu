@@ -846,9 +846,8 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
                           {(void **)&ws->d_top, 8}};
     size_t total = 0;
     for (const Part &p : parts) total += (p.bytes + 255) / 256 * 256;
-    cudaError_t e = c->pooled ? cudaMallocAsync(&ws->arena, total, c->stream) : cudaMalloc(&ws->arena, total);
+    cudaError_t e = ctx_alloc(c, &ws->arena, total, c->stream);
     if (e != cudaSuccess) {
-        cudaGetLastError();
         delete ws;
         return e == cudaErrorMemoryAllocation ? CFPQ_ERR_NOMEM : CFPQ_ERR_CUDA;
     }
@@ -891,9 +890,10 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
     up(d.uniq, uniq.data(), uniq.size() * 4);
     up(d.pchain, pchain.data(), (size_t)n_nt * sizeof(PChain));
     up(d.lift, lift.data(), lift.size() * 4);
+    // the uploads ran on the context's stream; the worklist may run on another one
+    if (ok && !c->pooled && cudaStreamSynchronize(s) != cudaSuccess) ok = false;
     if (!ok) {
-        if (c->pooled) cudaFreeAsync(ws->arena, s);
-        else cudaFree(ws->arena);
+        ctx_free(c, ws->arena, s);
         delete ws;
         return CFPQ_ERR_CUDA;
     }
@@ -904,10 +904,7 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
 void worklist_release(cfpq_ctx *c) {
     WorklistState *ws = static_cast<WorklistState *>(c->h_wl);
     if (!ws) return;
-    if (ws->arena) {
-        if (c->pooled) cudaFreeAsync(ws->arena, c->stream);
-        else cudaFree(ws->arena);
-    }
+    ctx_free(c, ws->arena, c->stream);
     delete ws;
     c->h_wl = nullptr;
 }
