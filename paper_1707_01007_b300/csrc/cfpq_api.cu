@@ -80,8 +80,10 @@ __global__ void __launch_bounds__(256) k_scan_rows(const QDesc *qd, uint32_t *li
 }
 
 template <int CPL>
-__global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDesc *qd, const uint32_t *list, uint32_t cap) {
+__global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDesc *qd, const uint32_t *list, uint32_t cap,
+                                                                       int honor_skip) {
     const QDesc &q = *qd;
+    if (honor_skip && ld_u32(&q.st->skip)) return;  // an unrolled loop body past the loop's end
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -123,8 +125,9 @@ __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDe
 // one warp per flagged row (the lanes test 32 rows of the warp's share at once; four chunks of
 // 32 words in flight); the word summary of T follows, and where lengths are kept (TTsum set)
 // T^T and its summary too, their bits set one per lane per round.
-__global__ void __launch_bounds__(256) k_merge(const QDesc *qd) {
+__global__ void __launch_bounds__(256) k_merge(const QDesc *qd, int honor_skip) {
     const QDesc &q = *qd;
+    if (honor_skip && ld_u32(&q.st->skip)) return;
     const int lane = threadIdx.x & 31;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -176,29 +179,48 @@ __global__ void __launch_bounds__(256) k_merge(const QDesc *qd) {
     }
 }
 
-// Start of a solve on a context whose last solve converged: zeroes the rows of T that its row
-// bitmap flags (every other row of T, and both delta planes, are zero already), and their
-// summary words. One block per (non-terminal, row word of 32 rows); the k-th flagged row goes
-// to warp k % 4, which zeroes it with 16-byte stores (W is a multiple of 8, SW of 4).
-__global__ void __launch_bounds__(128) k_clear_t_rows(const QDesc *qd) {
+// Start of a solve (the matrix initialisation's first part): the loop state from the context's
+// template with the deadline armed, and every word of the three row bitmaps (T and both
+// deltas) zeroed; on a context whose last solve converged (clear_t), the rows of T that its
+// row bitmap flags are zeroed first, with their summary words (every other row of T, and both
+// delta planes, are zero already). One block per (non-terminal, row word); the k-th flagged
+// row of the word goes to warp k % 4, which zeroes it with 16-byte stores (W is a multiple of
+// 8, SW of 4); block 0 also writes the state.
+__global__ void __launch_bounds__(128) k_reset(const QDesc *qd, const DevState *tmpl, unsigned long long dt_ns,
+                                               int clear_t) {
     const QDesc &q = *qd;
-    const uint32_t rw = (q.n + 31u) / 32u;
-    const int a = (int)(blockIdx.x / rw);
-    const uint32_t wq = blockIdx.x % rw;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t rows = __ldcg(q.Trow + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
-    uint4 *T = reinterpret_cast<uint4 *>(q.T + (uint64_t)a * q.plane);
-    const uint32_t W4 = q.W / 4u, SW4 = q.SW / 4u;
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    for (int k = 0; rows; k++) {
-        const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
-        rows &= rows - 1;
-        if ((k & 3) != warp) continue;
-        for (uint32_t w = (uint32_t)lane; w < W4; w += 32u) T[i * W4 + w] = z;
-        if (q.Tsum) {
-            uint4 *sum = reinterpret_cast<uint4 *>(q.Tsum + ((uint64_t)a * q.n_pad + i) * q.SW);
-            for (uint32_t w = (uint32_t)lane; w < SW4; w += 32u) sum[w] = z;
+    if (blockIdx.x == 0) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(tmpl);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(q.st);
+        for (uint32_t w = threadIdx.x; w < (uint32_t)(sizeof(DevState) / 4); w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        if (threadIdx.x == 0 && dt_ns) q.st->deadline_ns = globaltimer_ns() + dt_ns;
+    }
+    const int a = (int)(blockIdx.x / q.W);
+    const uint32_t wq = blockIdx.x % q.W;
+    const uint64_t word = (uint64_t)a * q.W + wq;
+    if (clear_t && wq < (q.n + 31u) / 32u) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        uint32_t rows = __ldcg(q.Trow + word) & rows_in_word(q.n, wq);
+        uint4 *T = reinterpret_cast<uint4 *>(q.T + (uint64_t)a * q.plane);
+        const uint32_t W4 = q.W / 4u, SW4 = q.SW / 4u;
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (int k = 0; rows; k++) {
+            const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+            rows &= rows - 1;
+            if ((k & 3) != warp) continue;
+            for (uint32_t w = (uint32_t)lane; w < W4; w += 32u) T[i * W4 + w] = z;
+            if (q.Tsum) {
+                uint4 *sum = reinterpret_cast<uint4 *>(q.Tsum + ((uint64_t)a * q.n_pad + i) * q.SW);
+                for (uint32_t w = (uint32_t)lane; w < SW4; w += 32u) sum[w] = z;
+            }
         }
+        __syncthreads();  // every warp has read the word
+    }
+    if (threadIdx.x == 0) {
+        q.Trow[word] = 0u;
+        q.R0[word] = 0u;
+        q.R1[word] = 0u;
     }
 }
 
@@ -225,14 +247,18 @@ __device__ __forceinline__ void clear_delta_rows(const QDesc &q, uint32_t b, uin
     }
 }
 
-__global__ void __launch_bounds__(128) k_clear(const QDesc *qd) { clear_delta_rows(*qd, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(128) k_clear(const QDesc *qd, int honor_skip) {
+    if (honor_skip && ld_u32(&qd->st->skip)) return;
+    clear_delta_rows(*qd, blockIdx.x, gridDim.x);
+}
 
 // End of a loop execution on a path with gathers: blocks below scan_blocks list the next
 // execution's gather items (its delta rows and counts are final here), the others clear the
 // delta rows read in this execution (the two touch different planes).
 __global__ void __launch_bounds__(256) k_clear_scan(const QDesc *qd, uint32_t *list, uint32_t cap, uint32_t nch,
-                                                    uint32_t scan_blocks) {
+                                                    uint32_t scan_blocks, int honor_skip) {
     const QDesc &q = *qd;
+    if (honor_skip && ld_u32(&q.st->skip)) return;
     if (blockIdx.x < scan_blocks)
         scan_rows(q, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint32_t)((q.st->iter + 1ull) & 1ull), list,
                   cap, nch);
@@ -315,7 +341,10 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
         if (use) atomicOr(&s_any, 1u);
     }
     __syncthreads();
-    if (tid == 0) st->occ_probe = s_probe;
+    if (tid == 0) {
+        st->occ_probe = s_probe;
+        st->any_next = s_any | s_probe;
+    }
     if (tid == 0 && use_handles) cudaGraphSetConditional(handles[q.n_groups], s_any | s_probe);
 
     if (tid < q.n_nt) {
@@ -337,17 +366,45 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
     __syncthreads();
 }
 
-__global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *handles, int use_handles) {
-    choose_products(*qd, handles, use_handles);
+// The choice before the loop. nested (the graph's nested loops): the inner loop's handle and
+// skip follow the choice, as the tail sets them after every execution.
+__global__ void k_choose(const QDesc *qd, const cudaGraphConditionalHandle *handles, int use_handles, int nested) {
+    const QDesc &q = *qd;
+    choose_products(q, handles, use_handles);
+    if (nested && threadIdx.x == 0) {
+        const unsigned any = ld_u32(&q.st->any_next);
+        cudaGraphSetConditional(handles[q.n_groups + 1], any ? 0u : 1u);
+        q.st->skip = any ? 1u : 0u;
+    }
 }
 
 // End of a loop execution. choice != NULL (automatic path in a graph): the product choice for
 // the next execution is made here too, saving a launch per execution.
+// flags: kTailHonorSkip, the tail of an unrolled body's copy (nothing to do once skip is set);
+// kTailUnrolled, the body repeats the execution and the copies after this one skip once the
+// loop ends; kTailNested (AUTO, with choice), the body runs gather-only executions in an inner
+// loop on handle choice[n_groups + 1] and a mixed one under the IF on choice[n_groups]: both
+// handles and skip follow the next execution's product choice.
+enum : int { kTailHonorSkip = 1, kTailUnrolled = 2, kTailNested = 4 };
+
 __global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int use_handle,
-                       const cudaGraphConditionalHandle *choice) {
-    const unsigned cont = tail_query(*qd, threadIdx.x, blockDim.x, true);
-    if (cont && choice) choose_products(*qd, choice, 1);
-    if (threadIdx.x == 0 && use_handle) cudaGraphSetConditional(handle, cont);
+                       const cudaGraphConditionalHandle *choice, int flags) {
+    const QDesc &q = *qd;
+    if ((flags & kTailHonorSkip) && ld_u32(&q.st->skip)) return;
+    const unsigned cont = tail_query(q, threadIdx.x, blockDim.x, true);
+    if (cont && choice) choose_products(q, choice, 1);
+    if (threadIdx.x == 0) {
+        if (use_handle) cudaGraphSetConditional(handle, cont);
+        if (flags & kTailNested) {
+            const unsigned any = cont ? ld_u32(&q.st->any_next) : 0u;
+            const unsigned gather_only = cont && !any ? 1u : 0u;
+            cudaGraphSetConditional(choice[q.n_groups], any);  // no tensor branch after the loop's end
+            cudaGraphSetConditional(choice[q.n_groups + 1], gather_only);
+            q.st->skip = gather_only ? 0u : 1u;
+        } else if (flags & kTailUnrolled) {
+            q.st->skip = cont ? 0u : 1u;
+        }
+    }
 }
 
 
@@ -691,15 +748,15 @@ static uint32_t row_warp_blocks(uint64_t rows) { return (uint32_t)((rows * 32 + 
 // The gather products of one loop execution, for every group not on the tensor cores: a
 // persistent grid runs one warp per (group, row, column chunk) item that the list of this
 // execution holds (listed after the seed, then at the end of each execution for the next).
-static int enqueue_gathers(cfpq_ctx *c, cudaStream_t s) {
+static int enqueue_gathers(cfpq_ctx *c, cudaStream_t s, int honor_skip = 0) {
     int cpl;
     gather_chunks(c->W, &cpl);
     const uint32_t grid = (uint32_t)c->gather_grid;
     switch (cpl) {
-        case 1: k_gather_list<1><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
-        case 2: k_gather_list<2><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
-        case 4: k_gather_list<4><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
-        default: k_gather_list<8><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap); break;
+        case 1: k_gather_list<1><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, honor_skip); break;
+        case 2: k_gather_list<2><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, honor_skip); break;
+        case 4: k_gather_list<4><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, honor_skip); break;
+        default: k_gather_list<8><<<grid, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, honor_skip); break;
     }
     c->iter_launches += 1;
     CK(cudaGetLastError());
@@ -708,7 +765,8 @@ static int enqueue_gathers(cfpq_ctx *c, cudaStream_t s) {
 
 // Adds an IF node on handle h to the graph that stream s is capturing (after the capture's
 // current dependencies), makes it the capture's only dependency and returns its body.
-static int add_if(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *body) {
+static int add_cond(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                    cudaGraph_t *body) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t *deps = nullptr;
@@ -718,13 +776,17 @@ static int add_if(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *bod
     cudaGraphNodeParams p = {};
     p.type = cudaGraphNodeTypeConditional;
     p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.type = type;
     p.conditional.size = 1;
     cudaGraphNode_t node;
     CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &p));
     CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     *body = p.conditional.phGraph_out[0];
     return CFPQ_OK;
+}
+
+static int add_if(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *body) {
+    return add_cond(s, h, cudaGraphCondTypeIf, body);
 }
 
 static int begin_branch(cudaStream_t b, cudaGraph_t body) {
@@ -763,7 +825,8 @@ static int enqueue_auto_tensor_graph(cfpq_ctx *c, cudaStream_t s) {
 // the end of the execution. In profile mode, CUDA events bracket every tensor-product launch
 // (one pair per group) and the gather products of the execution (one pair).
 static int enqueue_products(cfpq_ctx *c, cudaStream_t s, int use_handle);
-static int enqueue_iteration_end(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle);
+static int enqueue_iteration_end(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle,
+                                 int tail_flags = 0);
 
 int enqueue_iteration(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
     c->iter_launches = 0;
@@ -778,7 +841,7 @@ static int enqueue_products(cfpq_ctx *c, cudaStream_t s, int use_handle) {
         // choose per group; in a graph the chosen tensor products run under conditional
         // nodes, otherwise every tensor launch is made and returns at once if not chosen
         if (!use_handle) {  // in the graph, the previous execution's tail (or the node before the loop) chose
-            k_choose<<<1, 64, 0, s>>>(c->d_q, nullptr, 0);
+            k_choose<<<1, 64, 0, s>>>(c->d_q, nullptr, 0, 0);
             c->iter_launches++;
         }
         if (use_handle) {
@@ -820,8 +883,10 @@ static int enqueue_products(cfpq_ctx *c, cudaStream_t s, int use_handle) {
     return CFPQ_OK;
 }
 
-static int enqueue_iteration_end(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle) {
+static int enqueue_iteration_end(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int use_handle,
+                                 int tail_flags) {
     const bool prof = c->profile && !use_handle;
+    const int honor = (tail_flags & kTailHonorSkip) ? 1 : 0;
     const uint32_t word_blocks = (uint32_t)((uint64_t)c->n_nt * ((c->n + 31) / 32));  // one per (A, row word)
     if (c->lengths) {  // before the merge: T still holds the previous execution's matrices
         if (prof) CK(cudaEventRecord(c->prof_ev[2 * c->n_groups + 2], s));
@@ -831,7 +896,7 @@ static int enqueue_iteration_end(cfpq_ctx *c, cudaStream_t s, cudaGraphCondition
     }
     if (c->schedule == CFPQ_SCHED_JACOBI) {
         const uint64_t blocks_needed = ((uint64_t)c->n_nt * c->n + 7) / 8;  // 8 warps per block
-        k_merge<<<(uint32_t)std::min<uint64_t>(blocks_needed, 4ull * (uint64_t)c->sms), 256, 0, s>>>(c->d_q);
+        k_merge<<<(uint32_t)std::min<uint64_t>(blocks_needed, 4ull * (uint64_t)c->sms), 256, 0, s>>>(c->d_q, honor);
         c->iter_launches++;
     }
     if (c->any_gather) {
@@ -839,11 +904,13 @@ static int enqueue_iteration_end(cfpq_ctx *c, cudaStream_t s, cudaGraphCondition
         const uint32_t nch = gather_chunks(c->W, &cpl);
         const uint32_t scan_blocks = (uint32_t)(((uint64_t)c->n_groups * ((c->n + 31) / 32) + 255) / 256);
         const uint32_t clear_blocks = std::min<uint32_t>(word_blocks, 2u * (uint32_t)c->sms);
-        k_clear_scan<<<scan_blocks + clear_blocks, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, nch, scan_blocks);
+        k_clear_scan<<<scan_blocks + clear_blocks, 256, 0, s>>>(c->d_q, c->d_list, c->list_cap, nch, scan_blocks,
+                                                               honor);
     } else {
-        k_clear<<<std::min<uint32_t>(word_blocks, 4u * (uint32_t)c->sms), 128, 0, s>>>(c->d_q);
+        k_clear<<<std::min<uint32_t>(word_blocks, 4u * (uint32_t)c->sms), 128, 0, s>>>(c->d_q, honor);
     }
-    k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle, (use_handle && c->auto_mixed) ? c->d_choice : nullptr);
+    k_tail<<<1, 1024, 0, s>>>(c->d_q, h, use_handle, (use_handle && c->auto_mixed) ? c->d_choice : nullptr,
+                              tail_flags);
     c->iter_launches += 2;
     CK(cudaGetLastError());
     return CFPQ_OK;
@@ -880,8 +947,60 @@ static int collect_profile(cfpq_ctx *c) {
     return CFPQ_OK;
 }
 
+// Executions per iteration of a graph loop whose executions are gather-only: the copies after
+// the one that ends the loop (or, on the automatic path, hands over to a tensor execution)
+// return at once, so the loop's count is unchanged and a while-node iteration is paid once per
+// kUnroll executions. The first copy always runs (the loop's condition admitted it), so every
+// iteration of the loop runs one tail, which sets the condition.
+constexpr int kUnroll = 4;
+
+// kUnroll copies of a gather-only execution captured on s (c->iter_launches counts one).
+static int capture_gather_executions(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int tail_flags) {
+    int64_t one = 0;
+    for (int u = 0; u < kUnroll; u++) {
+        c->iter_launches = 0;
+        const int honor = u > 0 ? 1 : 0;
+        int rc = enqueue_gathers(c, s, honor);
+        if (rc == CFPQ_OK) rc = enqueue_iteration_end(c, s, h, 1, tail_flags | (honor ? kTailHonorSkip : 0));
+        if (rc != CFPQ_OK) return rc;
+        if (u == 0) one = c->iter_launches;
+    }
+    c->iter_launches = one;
+    return CFPQ_OK;
+}
+
+// AUTO path, nested loops: one execution in which some group takes the tensor product (or the
+// occupancy counts are asked for), captured on s: occupancy, then per group an IF node on its
+// choice holding its transposes and tensor product (captured on aux2_stream), the gathers of
+// the other groups and the end of the execution.
+static int capture_mixed_execution(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
+    int rc = enqueue_tensor_occupancy(c, s);
+    for (int g = 0; g < c->n_groups && rc == CFPQ_OK; g++) {
+        cudaGraph_t body;
+        if ((rc = add_if(s, c->h_choice[g], &body)) != CFPQ_OK) break;
+        if ((rc = begin_branch(c->aux2_stream, body)) != CFPQ_OK) break;
+        int r2 = enqueue_tensor_transposes_gated(c, g, c->aux2_stream);
+        if (r2 == CFPQ_OK) r2 = enqueue_tensor_group(c, g, c->aux2_stream);
+        rc = end_branch(c->aux2_stream, r2);
+    }
+    if (rc == CFPQ_OK && c->any_gather) rc = enqueue_gathers(c, s, 0);
+    if (rc == CFPQ_OK) rc = enqueue_iteration_end(c, s, h, 1, kTailNested);
+    return rc;
+}
+
+// The loop of Algorithm 1 as one graph: a WHILE node on "the last execution changed T" whose
+// body is one of
+//   automatic path: WHILE (the next execution is gather-only) { kUnroll gather-only
+//                   executions }, then IF (the next one has a tensor product) { that
+//                   execution }, after a first choice node;
+//   gather-only contexts: kUnroll executions;
+//   otherwise (tensor products every execution, lengths): one execution.
 static int build_graph(cfpq_ctx *c) {
     if (c->graph_exec) return CFPQ_OK;
+    bool any_tensor = false;
+    for (int g = 0; g < c->n_groups; g++) any_tensor |= c->group_tensor[g] != 0;
+    const bool nested = c->auto_mixed && !c->lengths;
+    const bool unrolled = !c->auto_mixed && !any_tensor && c->any_gather && !c->lengths;
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
@@ -889,8 +1008,9 @@ static int build_graph(cfpq_ctx *c) {
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "handle", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
     cudaGraphNode_t first = nullptr;  // automatic path: the first execution's product choice
     if (c->auto_mixed) {
-        // one IF handle per production group, then "any group chose tensor", set by the
-        // choice before the loop and by every execution's tail for the next one
+        // one IF handle per production group, then "any group chose tensor" and (nested) the
+        // inner loop's "gather-only", set by the choice before the loop and by every
+        // execution's tail for the next one
         const int prc = tensor_prepare(c);
         if (prc != CFPQ_OK) { cudaGraphDestroy(g); return prc; }
         for (cudaStream_t *as : {&c->aux_stream, &c->aux2_stream})
@@ -899,18 +1019,20 @@ static int build_graph(cfpq_ctx *c) {
                 note_cuda_error(e, "aux stream", __FILE__, __LINE__);
                 return CFPQ_ERR_CUDA;
             }
-        c->h_choice.assign(c->n_groups + 1, 0);
-        for (int k = 0; k <= c->n_groups; k++) {
+        // (a handle that no conditional node uses makes the instantiation fail)
+        const int handles = c->n_groups + (nested ? 2 : 1);
+        c->h_choice.assign(c->n_groups + 2, 0);
+        for (int k = 0; k < handles; k++) {
             e = cudaGraphConditionalHandleCreate(&c->h_choice[k], g, 0, 0);
             if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "choice handle", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
         }
-        e = cudaMemcpy(c->d_choice, c->h_choice.data(), sizeof(cudaGraphConditionalHandle) * (c->n_groups + 1),
+        e = cudaMemcpy(c->d_choice, c->h_choice.data(), sizeof(cudaGraphConditionalHandle) * (c->n_groups + 2),
                        cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "choice copy", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
         const QDesc *qd = c->d_q;
         const cudaGraphConditionalHandle *hs = c->d_choice;
-        int use = 1;
-        void *args[] = {(void *)&qd, (void *)&hs, (void *)&use};
+        int use = 1, nest = nested ? 1 : 0;
+        void *args[] = {(void *)&qd, (void *)&hs, (void *)&use, (void *)&nest};
         cudaKernelNodeParams kp = {};
         kp.func = (void *)k_choose;
         kp.gridDim = dim3(1);
@@ -930,7 +1052,22 @@ static int build_graph(cfpq_ctx *c) {
     cudaGraph_t body = p.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "capture", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
-    const int rc = enqueue_iteration(c, c->stream, h, 1);
+    int rc = CFPQ_OK;
+    if (nested) {
+        cudaGraph_t inner = nullptr, mixed = nullptr;
+        rc = add_cond(c->stream, c->h_choice[c->n_groups + 1], cudaGraphCondTypeWhile, &inner);
+        if (rc == CFPQ_OK && (rc = begin_branch(c->aux_stream, inner)) == CFPQ_OK)
+            rc = end_branch(c->aux_stream, capture_gather_executions(c, c->aux_stream, h, kTailNested));
+        const int64_t per_execution = c->iter_launches;  // a gather-only execution's launches
+        if (rc == CFPQ_OK) rc = add_if(c->stream, c->h_choice[c->n_groups], &mixed);
+        if (rc == CFPQ_OK && (rc = begin_branch(c->aux_stream, mixed)) == CFPQ_OK)
+            rc = end_branch(c->aux_stream, capture_mixed_execution(c, c->aux_stream, h));
+        c->iter_launches = per_execution;
+    } else if (unrolled) {
+        rc = capture_gather_executions(c, c->stream, h, kTailUnrolled);
+    } else {
+        rc = enqueue_iteration(c, c->stream, h, 1);
+    }
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(c->stream, &captured);
     if (rc != CFPQ_OK || e != cudaSuccess) {
@@ -1026,37 +1163,24 @@ void arm_deadline(cfpq_ctx *c, cudaStream_t s) {
 // Clears the matrices and seeds them from the edges (Algorithm 1's initialisation).
 int enqueue_reset_and_seed(cfpq_ctx *c, cudaStream_t s) {
     const size_t planes = (size_t)c->n_nt * c->plane * sizeof(uint32_t);
-    const size_t rows = (size_t)c->n_nt * c->W * sizeof(uint32_t);
-    if (c->clean) {
-        // the last solve converged: only the non-empty rows of T hold bits
-        k_clear_t_rows<<<(uint32_t)((uint64_t)c->n_nt * ((c->n + 31) / 32)), 128, 0, s>>>(c->d_q);
-        CK(cudaGetLastError());
-    } else {
+    if (!c->clean) {
         CK(cudaMemsetAsync(c->d_T, 0, planes, s));
         CK(cudaMemsetAsync(c->d_X0, 0, planes, s));
         CK(cudaMemsetAsync(c->d_X1, 0, planes, s));
         CK(cudaMemsetAsync(c->d_Tsum, 0, (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t), s));
     }
-    c->clean = false;
-    CK(cudaMemsetAsync(c->d_R0, 0, rows, s));
-    CK(cudaMemsetAsync(c->d_R1, 0, rows, s));
-    CK(cudaMemsetAsync(c->d_Trow, 0, rows, s));
     if (c->lengths) {  // T^T and its word summary are built pair by pair from here on
         const size_t sum = (size_t)c->n_nt * c->n_pad * c->SW * sizeof(uint32_t);
         CK(cudaMemsetAsync(c->d_TTsum, 0, sum, s));
         CK(cudaMemsetAsync(c->d_TT, 0, planes, s));
     }
-    DevState st0;
-    memset(&st0, 0, sizeof(st0));
-    st0.max_iter = c->max_iter;
-    for (int a = 0; a < c->n_nt; a++) st0.dirty[a] = st0.occ_now[a] = 1u;
-    for (int g = 0; g < c->n_groups && g < kMaxNT; g++) st0.use_tensor[g] = c->group_tensor[g] ? 1u : 0u;
-    CK(cudaMemcpyAsync(c->d_state, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
-    c->fixed_launches = 1;
-    if (c->timeout_s > 0) {
-        arm_deadline(c, s);
-        c->fixed_launches++;
-    }
+    // the row bitmaps, the state and the deadline; on a converged context also the rows of T
+    // that still hold bits
+    const unsigned long long dt_ns = c->timeout_s > 0 ? (unsigned long long)(c->timeout_s * 1e9) : 0ull;
+    k_reset<<<(uint32_t)((uint64_t)c->n_nt * c->W), 128, 0, s>>>(c->d_q, c->d_state0, dt_ns, c->clean ? 1 : 0);
+    CK(cudaGetLastError());
+    c->clean = false;
+    c->fixed_launches = 2;  // k_reset and the seed
     const uint64_t work = std::max<uint64_t>(c->n_edges, (uint64_t)c->n_eps_rules * c->n);
     const uint32_t blocks = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(1, (work + 255) / 256), 148ull * 16);
     k_seed<<<blocks, 256, 0, s>>>(c->d_q);
@@ -1245,12 +1369,13 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         {(void **)&c->d_gstart, gstart.size() * sizeof(int32_t)}, {(void **)&c->d_unary, unary.size() * sizeof(int2)},
         {(void **)&c->d_nt_rules, (size_t)c->n_nt * sizeof(int2)},
         {(void **)&c->d_eps, eps.size() * sizeof(int32_t)}, {(void **)&c->d_edges, n_edges * sizeof(cfpq_edge)},
-        {(void **)&c->d_state, sizeof(DevState)}, {(void **)&c->d_q, sizeof(QDesc)},
+        {(void **)&c->d_state, sizeof(DevState)}, {(void **)&c->d_state0, sizeof(DevState)},
+        {(void **)&c->d_q, sizeof(QDesc)},
         {(void **)&c->d_counts, cells * sizeof(uint32_t)}, {(void **)&c->d_offsets, cells * sizeof(uint64_t)},
         {(void **)&c->d_block_sums, (kScanMaxBlocks + 1) * sizeof(unsigned long long)},
         {(void **)&c->d_nt_off, (size_t)(c->n_nt + 1) * sizeof(unsigned long long)},
         {(void **)&c->d_total, sizeof(unsigned long long)},
-        {(void **)&c->d_choice, sizeof(cudaGraphConditionalHandle) * (kMaxNT + 1)},
+        {(void **)&c->d_choice, sizeof(cudaGraphConditionalHandle) * (kMaxNT + 2)},
         {(void **)&c->d_list, (size_t)c->list_cap * sizeof(uint32_t)},
         {(void **)&c->d_colcnt, c->profile ? sizeof(uint32_t) * c->n_pad : 0},
         {(void **)&c->d_L, c->lengths ? (size_t)c->n_nt * c->n_pad * c->n_pad * sizeof(uint32_t) : 0},
@@ -1352,6 +1477,16 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     q.st = c->d_state;
     c->hq = q;
     CK(cudaMemcpyAsync(c->d_q, &q, sizeof(q), cudaMemcpyHostToDevice, cs));
+    {
+        // the state every solve starts from: no executions yet, every transpose and tile
+        // occupancy to be built, the groups' product kinds (the loop's tail plans the rest)
+        DevState st0;
+        memset(&st0, 0, sizeof(st0));
+        st0.max_iter = c->max_iter;
+        for (int a = 0; a < c->n_nt; a++) st0.dirty[a] = st0.occ_now[a] = 1u;
+        for (int g = 0; g < c->n_groups && g < kMaxNT; g++) st0.use_tensor[g] = c->group_tensor[g] ? 1u : 0u;
+        CK(cudaMemcpyAsync(c->d_state0, &st0, sizeof(st0), cudaMemcpyHostToDevice, cs));
+    }
     if (c->path == CFPQ_PATH_WORKLIST) return worklist_setup(c, edges, n_edges);
     // the set-up above ran on the context's stream, and a solve may run on any stream the
     // caller names: finish it here (a server's contexts share the server's stream)
@@ -1440,7 +1575,7 @@ void ctx_destroy(cfpq_ctx *c) {
 int run_loop(cfpq_ctx *c, cudaStream_t s) {
     if (c->n_groups == 0) {
         // no binary productions: one execution of the loop body finds nothing new
-        k_tail<<<1, 1024, 0, s>>>(c->d_q, 0, 0, nullptr);
+        k_tail<<<1, 1024, 0, s>>>(c->d_q, 0, 0, nullptr, 0);
         c->iter_launches = 1;
         CK(cudaGetLastError());
         return CFPQ_OK;
@@ -1623,7 +1758,7 @@ extern "C" int cfpq_block_finish(cfpq_ctx *c, void *stream, int32_t *changed) {
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     int rc;
     if (c->n_groups == 0) {
-        k_tail<<<1, 1024, 0, s>>>(c->d_q, 0, 0, nullptr);
+        k_tail<<<1, 1024, 0, s>>>(c->d_q, 0, 0, nullptr, 0);
         c->iter_launches = 1;
         CK(cudaGetLastError());
     } else if ((rc = enqueue_iteration_end(c, s, 0, 0)) != CFPQ_OK) {

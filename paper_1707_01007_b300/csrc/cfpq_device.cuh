@@ -72,6 +72,8 @@ struct DevState {
     unsigned int occ_probe;             // AUTO: refresh tile occupancy this execution for the cost model
     unsigned long long block_records;   // sharded solve: records packed by the last export
     unsigned int block_bad;             // sharded solve: an imported record was out of range
+    unsigned int skip;                  // graph loop: the remaining executions of this unrolled body do nothing
+    unsigned int any_next;              // AUTO: the next execution has a tensor product (or an occupancy probe)
     unsigned int tc_diag[6];            // first tensor product that gave up: wait site, CTA + 1, group,
                                         // execution, listed tiles, tiles claimed
 };

@@ -61,6 +61,7 @@ struct cfpq_ctx {
     int32_t *d_eps = nullptr;
     cfpq_edge *d_edges = nullptr;
     cfpq::DevState *d_state = nullptr;
+    cfpq::DevState *d_state0 = nullptr;      // the loop state every solve starts from (fixed at create)
     cfpq::QDesc *d_q = nullptr;
     cfpq::QDesc hq{};
     void *d_arena = nullptr;                 // every buffer below lives in this one allocation

@@ -202,6 +202,7 @@ extern "C" int cfpq_resume(cfpq_ctx *c, void *stream, int64_t more_executions) {
     CK(cudaStreamSynchronize(s));
     st.error = st.done = st.cont = st.changed = 0u;
     st.small_run = st.to_worklist = 0u;
+    st.skip = st.any_next = 0u;  // the graph loop's flags (the first execution of a loop iteration runs regardless)
     // 0: Theorem 3's bound on changing executions, |V|^2 |N|, plus the final one
     const double bound = (double)c->n * (double)c->n * (double)c->n_nt + 1.0;
     st.max_iter = more_executions > 0 ? st.iter + (uint64_t)more_executions
