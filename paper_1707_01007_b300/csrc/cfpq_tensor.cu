@@ -475,6 +475,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         auto unpack_until = [&](uint32_t limit) -> bool {
             for (; sn < limit; sn += UNPACK_GROUPS) {
                 const uint32_t ps = sn % PST, pph = (sn / PST) & 1u;
+                bool passed = true;
                 if constexpr (PST % UNPACK_GROUPS != 0) {
                     // With an odd packed ring the groups take turns on each slot: this group's
                     // waits on full_p[ps] skip every other phase, and a parity wait cannot tell
@@ -483,18 +484,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                     // have landed yet. So first wait until the other group has consumed stage
                     // sn - PST (phase sn / PST - 1 of empty_p[ps]; the phase before it is this
                     // group's own, already passed): full_p[ps] is then at most one phase behind.
-                    if (sn >= (uint32_t)PST) {
-                        if (!mbar_wait(&S.empty_p[ps], ((sn / PST) - 1u) & 1u, err, WAIT_LIMIT_NS, 9)) {
-                            return false;
-                        }
-                    }
+                    if (sn >= (uint32_t)PST) passed = mbar_wait(&S.empty_p[ps], ((sn / PST) - 1u) & 1u, err, WAIT_LIMIT_NS, 9);
                 }
-                if (!mbar_wait(&S.full_p[ps], pph, err, WAIT_LIMIT_NS, 6)) {
-                    return false;
-                }
-                if (!mbar_wait(&S.empty_u[us], uph ^ 1u, err, WAIT_LIMIT_NS, 7)) {
-                    return false;
-                }
+                passed = passed && mbar_wait(&S.full_p[ps], pph, err, WAIT_LIMIT_NS, 6);
+                passed = passed && mbar_wait(&S.empty_u[us], uph ^ 1u, err, WAIT_LIMIT_NS, 7);
+                // one warp-uniform outcome for the stage: the unpack below uses warp-collective tcgen05.st
+                if (!__all_sync(0xffffffffu, passed)) return false;
                 tc_fence_after();
                 uint32_t pa[KW / 2], pb[KW];  // this lane's half row of A and the thread's row of B
                 if constexpr (KIND == 0) {
@@ -526,7 +521,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             return true;
         };
         uint32_t ord = 0;  // this CTA's ord-th tile (t is the thread's B row)
-        uint32_t i = read_tile(0, 1u);
+        uint32_t i = __shfl_sync(0xffffffffu, read_tile(0, 1u), 0);  // warp-uniform
         uint32_t m0 = 0, n0 = 0;
         if (i != kNoTile) {
             const uint2 e = list ? list[i] : make_uint2(i, dense_steps);
@@ -538,7 +533,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // the next tile's first stages (at most UST: their ring slots are freed by this
             // tile's own MMAs, which wait for nothing else) are unpacked before this tile's
             // epilogue, so that its MMAs can start as soon as the accumulator is handed back
-            const uint32_t i2 = fine ? read_tile(ord + 1, 1u) : kNoTile;
+            const uint32_t i2 = __shfl_sync(0xffffffffu, fine ? read_tile(ord + 1, 1u) : kNoTile, 0);  // warp-uniform
             uint32_t m2 = 0, n2 = 0, s_end2 = s_end;
             if (i2 != kNoTile) {
                 const uint2 e2 = list ? list[i2] : make_uint2(i2, dense_steps);
@@ -546,7 +541,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 s_end2 = s_end + e2.y;
                 fine = unpack_until(min(s_end2, s_end + (uint32_t)UST));
             }
-            const bool ok = fine && !*err && mbar_wait(&S.acc_full, tiles_done & 1u, err, WAIT_LIMIT_NS, 8);
+            const bool ok =
+                __all_sync(0xffffffffu, fine && !*err && mbar_wait(&S.acc_full, tiles_done & 1u, err, WAIT_LIMIT_NS, 8));
             tc_fence_after();
             const uint32_t row = m0 + quad * 32 + lane;
             unsigned cnt = 0;
@@ -801,7 +797,7 @@ static bool encode_map(CUtensorMap *m, uint32_t *base, const cfpq_ctx *c, uint32
 }
 
 static int tensor_setup(cfpq_ctx *c) {
-    if (c->d_tc_work) return CFPQ_OK;
+    if (c->h_tc_work) return CFPQ_OK;  // once per context
     if (!c->d_TT) return CFPQ_ERR_UNSUPPORTED;
     TensorWork *w = new TensorWork();
     memset(w, 0, sizeof(*w));
