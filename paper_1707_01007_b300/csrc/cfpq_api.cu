@@ -305,7 +305,9 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
         const int kind = q.tensor_kind == CFPQ_TENSOR_FP8 ? 0 : 1;
         const float n = (float)q.n, W = (float)q.W, np = (float)q.n_pad;
         const float dense_rule_ns = 2.0f * np * np * np / tensor_ops_per_ns(kind);
-        const float transpose_ns = 2.0f * np * np / 8.0f / kTransposeBytesPerNs;
+        // a transpose reads T_C (n^2 / 8 bytes) and writes T_C^T: bit-packed for E4M3, as
+        // nibbles (n^2 / 2 bytes) for E2M1
+        const float transpose_ns = (np * np / 8.0f + (kind ? np * np / 2.0f : np * np / 8.0f)) / kTransposeBytesPerNs;
         const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
         float words = 0.0f, tensor_ns = kTensorLaunchNs;
         bool unknown = false;
@@ -1143,7 +1145,7 @@ void free_ctx_device(cfpq_ctx *c) {
     worklist_release(c);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     c->graph_exec = nullptr;
-    void *ptrs[] = {c->d_arena, c->d_triples, c->d_tc_work, c->d_lens};
+    void *ptrs[] = {c->d_arena, c->d_triples, c->d_tc_work, c->d_lens, c->d_TTn};
     for (void *p : ptrs) ctx_free(c, p, c->stream);
     for (auto e : c->prof_ev)
         if (e) cudaEventDestroy(e);

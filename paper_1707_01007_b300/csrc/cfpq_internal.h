@@ -73,6 +73,7 @@ struct cfpq_ctx {
     cfpq_triple *d_triples = nullptr;
     size_t triples_cap = 0;
     void *d_tc_work = nullptr;
+    uint8_t *d_TTn = nullptr;                // E2M1 products: T^T as nibbles (n_nt x n_pad rows of n_pad / 2 bytes)
     void *h_tc_work = nullptr;               // tensor path: tensor maps (host side)
     void *h_wl = nullptr;                    // worklist path state
     std::vector<int2> h_unary;               // (lhs, terminal) productions, host copy

@@ -70,18 +70,24 @@ struct Kind;
 template <>
 struct Kind<0> {
     static constexpr int KW = 4, PST = 8, SLICES = 1;  // packed words per row and stage, packed ring depth
+    static constexpr bool NIBBLE_B = false;            // B arrives bit-packed and is unpacked by the threads
 };
 template <>
 struct Kind<1> {
-    static constexpr int KW = 8, PST = 5, SLICES = 2;
+    // B arrives as E2M1 nibbles (T^T kept expanded, k_transpose_e2m1) straight into the MMA's
+    // shared-memory layout: a ring slot is the packed A stage plus the B tile, 6 slots (even, so
+    // each serves one unpack group)
+    static constexpr int KW = 8, PST = 6, SLICES = 2;
+    static constexpr bool NIBBLE_B = true;
 };
 
 template <int KIND>
 struct __align__(1024) Smem {
     static constexpr int KW = Kind<KIND>::KW, PST = Kind<KIND>::PST;
-    uint8_t b_tile[UST][B_TILE];
+    static constexpr bool NB = Kind<KIND>::NIBBLE_B;
+    uint8_t b_tile[NB ? PST : UST][B_TILE];   // unpacked B stages (nibble B: the ring's B tiles)
     uint32_t a_pack[PST][BM * KW];
-    uint32_t b_pack[PST][BN * KW];
+    uint32_t b_pack[NB ? 1 : PST][NB ? 4 : BN * KW];  // packed B stages (none with nibble B)
     unsigned long long full_p[PST], empty_p[PST], full_u[UST], empty_u[UST], acc_full, acc_empty;
     unsigned long long mma_done;  // the issuer's last commit: every MMA it issued has completed
     unsigned long long tile_full[2], tile_empty[2];  // tile skipping: claimed tile handed to the consumers
@@ -272,7 +278,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_tc_bool_gemm(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmTT, const QDesc *qd,
                    int g, const uint2 *list) {
     constexpr int KW = Kind<KIND>::KW, PST = Kind<KIND>::PST, SLICES = Kind<KIND>::SLICES;
-    constexpr uint32_t STAGE_BYTES = (uint32_t)(BM + BN) * KW * 4;  // packed bytes of one K stage
+    constexpr bool NB = Kind<KIND>::NIBBLE_B;
+    // bytes one K stage brings in: the packed rows of both operands, or (nibble B) the packed A
+    // rows and the B tile of E2M1 nibbles (256 rows x 128 bytes)
+    constexpr uint32_t STAGE_BYTES = NB ? (uint32_t)BM * KW * 4 + (uint32_t)B_TILE : (uint32_t)(BM + BN) * KW * 4;
     extern __shared__ uint8_t smem_raw[];
     Smem<KIND> &S =
         *reinterpret_cast<Smem<KIND> *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -291,7 +300,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) {
         for (int i = 0; i < PST; i++) {
             mbar_init(&S.full_p[i], 1);
-            mbar_init(&S.empty_p[i], GROUP_THREADS);
+            // a slot is free once the group has read its packed A (and, nibble B, once the MMAs
+            // that read its B tile have completed: one commit)
+            mbar_init(&S.empty_p[i], GROUP_THREADS + (NB ? 1 : 0));
         }
         for (int i = 0; i < UST; i++) {
             mbar_init(&S.full_u[i], GROUP_THREADS);
@@ -375,11 +386,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 break;
                             }
                             // K slice kb (for KIND 1 the first of the stage's two) starts at word 4 kb
+                            // of the packed rows, and at byte 64 kb of the nibble rows
                             mbar_expect_tx(&S.full_p[slot], STAGE_BYTES);
                             tma_load_2d(S.a_pack[slot], &tmT, &S.full_p[slot], (int)(kb * 4u),
                                         (int)((uint32_t)B * q.n_pad + m0));
-                            tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * 4u),
-                                        (int)((uint32_t)C * q.n_pad + n0));
+                            if constexpr (NB)
+                                tma_load_2d(S.b_tile[slot], &tmTT, &S.full_p[slot], (int)(kb * 64u),
+                                            (int)((uint32_t)C * q.n_pad + n0));
+                            else
+                                tma_load_2d(S.b_pack[slot], &tmTT, &S.full_p[slot], (int)(kb * 4u),
+                                            (int)((uint32_t)C * q.n_pad + n0));
                             issued = s + 1;
                             done++;
                         }
@@ -419,10 +435,19 @@ __global__ void __launch_bounds__(THREADS, 1)
                         stop = true;
                         break;
                     }
+                    // nibble B: the stage's B tile landed by TMA (the unpack group saw the same
+                    // phase before its arrival; the MMA thread waits on it itself, as the reader
+                    // of that tile)
+                    const uint32_t ps = s % PST;
+                    if (NB && !mbar_wait(&S.full_p[ps], (s / PST) & 1u, err, WAIT_LIMIT_NS, 10)) {
+                        stop = true;
+                        break;
+                    }
                     tc_fence_after();
-                    const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + slot * B_TILE;
+                    const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + (NB ? ps : slot) * B_TILE;
                     mma_stage<KIND>(tmem, at, bt, u == 0);
                     mma_commit(&S.empty_u[slot]);
+                    if (NB) mma_commit(&S.empty_p[ps]);  // the B tile may be overwritten once these MMAs completed
                 }
                 mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
                 tiles_done++;
@@ -499,17 +524,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                     pb[0] = y.x, pb[1] = y.y, pb[2] = y.z, pb[3] = y.w;
                 } else {
                     const uint4 x = reinterpret_cast<const uint4 *>(S.a_pack[ps])[2 * arow + half];
-                    const uint4 y0 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[2 * t];
-                    const uint4 y1 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[2 * t + 1];
                     pa[0] = x.x, pa[1] = x.y, pa[2] = x.z, pa[3] = x.w;
-                    pb[0] = y0.x, pb[1] = y0.y, pb[2] = y0.z, pb[3] = y0.w;
-                    pb[4] = y1.x, pb[5] = y1.y, pb[6] = y1.z, pb[7] = y1.w;
                 }
                 mbar_arrive(&S.empty_p[ps]);
                 unpack_half_row_tmem<KIND>(a_lane + us * A_COLS, pa);
-                unpack_row<KIND>(S.b_tile[us], off, pb);
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if constexpr (!NB) {
+                    unpack_row<KIND>(S.b_tile[us], off, pb);
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                } else {
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                }
                 tc_fence_before();
                 mbar_arrive(&S.full_u[us]);
                 us += UNPACK_GROUPS;
@@ -651,6 +676,37 @@ __global__ void __launch_bounds__(256) k_transpose(const QDesc *qd, int a, int g
     drow[1] = make_uint4(out[t][4], out[t][5], out[t][6], out[t][7]);
 }
 
+// T_a^T as E2M1 nibbles, the right operand of the E2M1 product (TMA loads its K stages straight
+// into the MMA's 128-byte-swizzled shared-memory layout). Row r of TTn[a] is n_pad / 2 bytes;
+// the 128 bytes of K stage st (K = 256 st .. 256 st + 255) are the 32 unpacked words
+// u = 0 .. 31, word u = spread4(word 8 st + u / 4 of row r of T_a^T, u % 4): the K permutation
+// with which the product unpacks its left operand, so both operands agree. One CTA per 256
+// rows x 256 columns of T_a, as k_transpose; each thread writes the 128 bytes of one stage of
+// one output row.
+__global__ void __launch_bounds__(256) k_transpose_e2m1(const QDesc *qd, int a, int gate, uint8_t *ttn) {
+    __shared__ uint32_t out[256][9];
+    const QDesc &q = *qd;
+    if (gate >= 0 && q.st->tt_now[a] != (unsigned)gate + 1u) return;
+    const uint32_t W = q.W;
+    const uint32_t r0 = blockIdx.y * 256, wc0 = blockIdx.x * 8;
+    const uint32_t *src = q.T + (uint64_t)a * q.plane;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint4 *row = reinterpret_cast<const uint4 *>(src + (uint64_t)(r0 + t) * W + wc0);
+    const uint4 lo = __ldcg(row), hi = __ldcg(row + 1);
+    const uint32_t in[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (int c = 0; c < 8; c++) out[c * 32 + lane][warp] = transpose32(in[c], lane);
+    __syncthreads();
+    // output row wc0 * 32 + t, K stage r0 / 256: 8 packed words -> 32 unpacked words
+    const uint64_t rb = (uint64_t)q.n_pad / 2u;  // bytes per nibble row
+    uint4 *drow = reinterpret_cast<uint4 *>(ttn + ((uint64_t)a * q.n_pad + wc0 * 32 + t) * rb + (r0 / 256u) * 128u);
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+        const uint32_t v = out[t][w];
+        drow[w] = make_uint4(spread4(v, 0), spread4(v, 1), spread4(v, 2), spread4(v, 3));
+    }
+}
+
 // Tile occupancy of T_a for tile skipping (one CTA per 256 rows x 256 columns, as k_transpose):
 // the CTA's 2 x 2 blocks of 128 rows x 128 columns give two (m-tile, K slice) bits of occA[a]
 // per m-tile and, ORed over the columns, the two (n-tile, K slice) bits of occB[a] (T_a^T's
@@ -784,6 +840,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// The E2M1 right operand: nibble rows of n_pad / 2 bytes, boxes of one K stage (128 bytes) x
+// box_rows rows, 128-byte swizzle (the MMA's K-major shared-memory layout).
+static bool encode_nibble_map(CUtensorMap *m, uint8_t *base, const cfpq_ctx *c, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)c->n_pad / 2, (cuuint64_t)c->n_nt * c->n_pad};
+    const cuuint64_t strides[1] = {(cuuint64_t)c->n_pad / 2};
+    const cuuint32_t box[2] = {128u, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 static bool encode_map(CUtensorMap *m, uint32_t *base, const cfpq_ctx *c, uint32_t box_words, uint32_t box_rows) {
     auto fn = encode_fn();
     if (!fn) return false;
@@ -799,12 +869,22 @@ static bool encode_map(CUtensorMap *m, uint32_t *base, const cfpq_ctx *c, uint32
 static int tensor_setup(cfpq_ctx *c) {
     if (c->h_tc_work) return CFPQ_OK;  // once per context
     if (!c->d_TT) return CFPQ_ERR_UNSUPPORTED;
+    if (c->tensor_kind != CFPQ_TENSOR_FP8 && !c->d_TTn) {
+        // the E2M1 products' right operand, made at the first tensor set-up of the context
+        // (contexts that never take a tensor product do not hold it)
+        void *p = nullptr;
+        const size_t bytes = (size_t)c->n_nt * c->n_pad * (c->n_pad / 2);
+        const cudaError_t e = ctx_alloc(c, &p, bytes, c->stream);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CFPQ_ERR_NOMEM : CFPQ_ERR_CUDA;
+        c->d_TTn = static_cast<uint8_t *>(p);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return CFPQ_ERR_CUDA;  // used on any stream
+    }
     TensorWork *w = new TensorWork();
     memset(w, 0, sizeof(*w));
     if (!encode_map(&w->tmT[0], c->d_T, c, tc::Kind<0>::KW, tc::BM) ||
         !encode_map(&w->tmTT[0], c->d_TT, c, tc::Kind<0>::KW, tc::BN) ||
         !encode_map(&w->tmT[1], c->d_T, c, tc::Kind<1>::KW, tc::BM) ||
-        !encode_map(&w->tmTT[1], c->d_TT, c, tc::Kind<1>::KW, tc::BN)) {
+        (c->d_TTn && !encode_nibble_map(&w->tmTT[1], c->d_TTn, c, tc::BN))) {
         delete w;
         return CFPQ_ERR_CUDA;
     }
@@ -825,9 +905,13 @@ void tensor_release(cfpq_ctx *c) {
     c->h_tc_work = nullptr;
 }
 
+// The right operand of a tensor product: T_a^T as nibbles for E2M1 products, bit-packed for E4M3.
 static void launch_transpose(cfpq_ctx *c, int a, cudaStream_t s, int64_t *launches, int gate = -1) {
     const dim3 grid(c->W / 8, c->n_pad / 256);
-    tc::k_transpose<<<grid, 256, 0, s>>>(c->d_q, a, gate);
+    if (c->tensor_kind != CFPQ_TENSOR_FP8)
+        tc::k_transpose_e2m1<<<grid, 256, 0, s>>>(c->d_q, a, gate, c->d_TTn);
+    else
+        tc::k_transpose<<<grid, 256, 0, s>>>(c->d_q, a, gate);
     (*launches)++;
 }
 
@@ -865,11 +949,11 @@ int enqueue_tensor_occupancy(cfpq_ctx *c, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 
-// T^T of every non-terminal that a production derives (the worklist's hand-over).
+// T^T (bit-packed) of every non-terminal that a production derives (the worklist's hand-over).
 int enqueue_all_transposes(cfpq_ctx *c, cudaStream_t s) {
-    int64_t ignored = 0;
+    const dim3 grid(c->W / 8, c->n_pad / 256);
     for (int a = 0; a < c->n_nt; a++)
-        if (c->nt_dynamic[a]) launch_transpose(c, a, s, &ignored);
+        if (c->nt_dynamic[a]) tc::k_transpose<<<grid, 256, 0, s>>>(c->d_q, a, -1);
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 

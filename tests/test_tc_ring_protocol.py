@@ -141,8 +141,8 @@ def run(seed, pst, ust, stages, fixed, groups=2):
     return None
 
 
-@pytest.mark.parametrize("pst,ust", [(5, 5), (8, 5), (4, 5), (3, 5), (5, 3)],
-                         ids=["e2m1", "e4m3", "even-4", "odd-3", "odd-5-ust-3"])
+@pytest.mark.parametrize("pst,ust", [(5, 5), (8, 5), (6, 5), (4, 5), (3, 5), (5, 3)],
+                         ids=["odd-5", "e4m3", "e2m1", "even-4", "odd-3", "odd-5-ust-3"])
 def test_ring_protocol_is_exact(pst, ust):
     for seed in range(400):
         err = run(seed, pst, ust, stages=70, fixed=True)
