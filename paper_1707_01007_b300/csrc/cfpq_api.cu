@@ -305,9 +305,10 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
         const int kind = q.tensor_kind == CFPQ_TENSOR_FP8 ? 0 : 1;
         const float n = (float)q.n, W = (float)q.W, np = (float)q.n_pad;
         const float dense_rule_ns = 2.0f * np * np * np / tensor_ops_per_ns(kind);
-        // a transpose reads T_C (n^2 / 8 bytes) and writes T_C^T: bit-packed for E4M3, as
-        // nibbles (n^2 / 2 bytes) for E2M1
-        const float transpose_ns = (np * np / 8.0f + (kind ? np * np / 2.0f : np * np / 8.0f)) / kTransposeBytesPerNs;
+        // a transpose reads T_C (n^2 / 8 bytes) and writes T_C^T: as nibbles (n^2 / 2 bytes)
+        // for dense E2M1 products (no tile occupancy), bit-packed otherwise
+        const bool nibble = kind && !q.occA;
+        const float transpose_ns = (np * np / 8.0f + (nibble ? np * np / 2.0f : np * np / 8.0f)) / kTransposeBytesPerNs;
         const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
         float words = 0.0f, tensor_ns = kTensorLaunchNs;
         bool unknown = false;

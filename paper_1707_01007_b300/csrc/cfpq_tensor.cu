@@ -64,7 +64,9 @@ static_assert(SFB_COL + 32 <= TMEM_COLS, "tensor memory budget");
 //           the bit-packed rows (4 words per row)
 //   KIND 1  E2M1 nibbles, kind::mxf4 with unit UE8M0 scale factors (K = 64 per MMA): a
 //           stage is two consecutive 128-bit K slices (8 words per row), half the unpacked
-//           bytes and half the MMA time per K of KIND 0
+//           bytes and half the MMA time per K of KIND 0; dense products, the right operand
+//           read as nibbles
+//   KIND 2  the same E2M1 MMAs with both operands bit-packed (tile skipping)
 template <int KIND>
 struct Kind;
 template <>
@@ -74,11 +76,18 @@ struct Kind<0> {
 };
 template <>
 struct Kind<1> {
-    // B arrives as E2M1 nibbles (T^T kept expanded, k_transpose_e2m1) straight into the MMA's
-    // shared-memory layout: a ring slot is the packed A stage plus the B tile, 6 slots (even, so
-    // each serves one unpack group)
+    // dense products: B arrives as E2M1 nibbles (T^T kept expanded, k_transpose_e2m1) straight
+    // into the MMA's shared-memory layout; a ring slot is the packed A stage plus the B tile,
+    // 6 slots (even, so each serves one unpack group)
     static constexpr int KW = 8, PST = 6, SLICES = 2;
     static constexpr bool NIBBLE_B = true;
+};
+template <>
+struct Kind<2> {
+    // tile skipping: B arrives bit-packed and is unpacked like A (short tiles: a transpose per
+    // changed operand and execution writes a quarter of the nibble operand's bytes)
+    static constexpr int KW = 8, PST = 5, SLICES = 2;
+    static constexpr bool NIBBLE_B = false;
 };
 
 template <int KIND>
@@ -100,7 +109,8 @@ template <int KIND>
 constexpr size_t smem_bytes() {
     return sizeof(Smem<KIND>) + 1024;
 }
-static_assert(smem_bytes<0>() <= 227 * 1024 && smem_bytes<1>() <= 227 * 1024, "shared memory per CTA");
+static_assert(smem_bytes<0>() <= 227 * 1024 && smem_bytes<1>() <= 227 * 1024 && smem_bytes<2>() <= 227 * 1024,
+              "shared memory per CTA");
 
 // Instruction descriptors (both operands K-major, M = 128, N = 256, F32 accumulator):
 // kind::f8f6f4 with A = B = E4M3 (bits 4-5: D is F32); kind::mxf4 block-scaled with
@@ -480,7 +490,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t *TA = q.T + (uint64_t)A * q.plane;
         uint32_t off[8];
         swizzled_row(t, off);
-        if constexpr (KIND == 1) {
+        if constexpr (KIND != 0) {
             // unit scale factors (UE8M0 127 = 2^0) for every K block of both operands: warps 2-5
             // (one per lane quadrant, all in group 0) write them before their first stage, whose
             // completion the MMA issuer waits for before its first MMA
@@ -525,6 +535,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 } else {
                     const uint4 x = reinterpret_cast<const uint4 *>(S.a_pack[ps])[2 * arow + half];
                     pa[0] = x.x, pa[1] = x.y, pa[2] = x.z, pa[3] = x.w;
+                    if constexpr (!NB) {
+                        const uint4 y0 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[2 * t];
+                        const uint4 y1 = reinterpret_cast<const uint4 *>(S.b_pack[ps])[2 * t + 1];
+                        pb[0] = y0.x, pb[1] = y0.y, pb[2] = y0.z, pb[3] = y0.w;
+                        pb[4] = y1.x, pb[5] = y1.y, pb[6] = y1.z, pb[7] = y1.w;
+                    }
                 }
                 mbar_arrive(&S.empty_p[ps]);
                 unpack_half_row_tmem<KIND>(a_lane + us * A_COLS, pa);
@@ -823,7 +839,7 @@ bool tensor_path_available() {
 }
 
 struct TensorWork {
-    CUtensorMap tmT[2], tmTT[2];  // per operand kind: boxes of Kind<KIND>::KW words
+    CUtensorMap tmT[3], tmTT[3];  // per operand kind: boxes of Kind<KIND>::KW words (tmTT[1]: nibbles)
     bool attr_set;
 };
 
@@ -866,12 +882,18 @@ static bool encode_map(CUtensorMap *m, uint32_t *base, const cfpq_ctx *c, uint32
            CUDA_SUCCESS;
 }
 
+// Dense E2M1 products read the right operand as nibbles (KIND 1); tile skipping (a plan list)
+// and E4M3 products read it bit-packed.
+static bool uses_nibble_operand(const cfpq_ctx *c) {
+    return c->tensor_kind != CFPQ_TENSOR_FP8 && c->dense_tensor;
+}
+
 static int tensor_setup(cfpq_ctx *c) {
     if (c->h_tc_work) return CFPQ_OK;  // once per context
     if (!c->d_TT) return CFPQ_ERR_UNSUPPORTED;
-    if (c->tensor_kind != CFPQ_TENSOR_FP8 && !c->d_TTn) {
-        // the E2M1 products' right operand, made at the first tensor set-up of the context
-        // (contexts that never take a tensor product do not hold it)
+    if (uses_nibble_operand(c) && !c->d_TTn) {
+        // the dense E2M1 products' right operand, made at the first tensor set-up of the
+        // context (contexts that never take a tensor product do not hold it)
         void *p = nullptr;
         const size_t bytes = (size_t)c->n_nt * c->n_pad * (c->n_pad / 2);
         const cudaError_t e = ctx_alloc(c, &p, bytes, c->stream);
@@ -884,14 +906,18 @@ static int tensor_setup(cfpq_ctx *c) {
     if (!encode_map(&w->tmT[0], c->d_T, c, tc::Kind<0>::KW, tc::BM) ||
         !encode_map(&w->tmTT[0], c->d_TT, c, tc::Kind<0>::KW, tc::BN) ||
         !encode_map(&w->tmT[1], c->d_T, c, tc::Kind<1>::KW, tc::BM) ||
-        (c->d_TTn && !encode_nibble_map(&w->tmTT[1], c->d_TTn, c, tc::BN))) {
+        (c->d_TTn && !encode_nibble_map(&w->tmTT[1], c->d_TTn, c, tc::BN)) ||
+        !encode_map(&w->tmT[2], c->d_T, c, tc::Kind<2>::KW, tc::BM) ||
+        !encode_map(&w->tmTT[2], c->d_TT, c, tc::Kind<2>::KW, tc::BN)) {
         delete w;
         return CFPQ_ERR_CUDA;
     }
     if (cudaFuncSetAttribute(tc::k_tc_bool_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tc::smem_bytes<0>()) != cudaSuccess ||
         cudaFuncSetAttribute(tc::k_tc_bool_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tc::smem_bytes<1>()) != cudaSuccess) {
+                             (int)tc::smem_bytes<1>()) != cudaSuccess ||
+        cudaFuncSetAttribute(tc::k_tc_bool_gemm<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tc::smem_bytes<2>()) != cudaSuccess) {
         delete w;
         return CFPQ_ERR_CUDA;
     }
@@ -905,10 +931,11 @@ void tensor_release(cfpq_ctx *c) {
     c->h_tc_work = nullptr;
 }
 
-// The right operand of a tensor product: T_a^T as nibbles for E2M1 products, bit-packed for E4M3.
+// The right operand of a tensor product: T_a^T as nibbles for dense E2M1 products, bit-packed
+// otherwise.
 static void launch_transpose(cfpq_ctx *c, int a, cudaStream_t s, int64_t *launches, int gate = -1) {
     const dim3 grid(c->W / 8, c->n_pad / 256);
-    if (c->tensor_kind != CFPQ_TENSOR_FP8)
+    if (uses_nibble_operand(c))
         tc::k_transpose_e2m1<<<grid, 256, 0, s>>>(c->d_q, a, gate, c->d_TTn);
     else
         tc::k_transpose<<<grid, 256, 0, s>>>(c->d_q, a, gate);
@@ -1016,8 +1043,10 @@ int enqueue_tensor_group(cfpq_ctx *c, int g, cudaStream_t s) {
     const uint32_t grid = std::min<uint32_t>(tiles, (uint32_t)std::max(1, sms));
     if (c->tensor_kind == CFPQ_TENSOR_FP8)
         launch_group<0>(c, w, g, s, tiles, grid);
-    else
+    else if (uses_nibble_operand(c))
         launch_group<1>(c, w, g, s, tiles, grid);
+    else
+        launch_group<2>(c, w, g, s, tiles, grid);
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
 }
 
