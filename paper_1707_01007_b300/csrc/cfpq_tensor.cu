@@ -720,13 +720,16 @@ __global__ void __launch_bounds__(256) k_transpose_e2m1(const QDesc *qd, int a, 
 #pragma unroll
     for (int c = 0; c < 8; c++) out[c * 32 + lane][warp] = transpose32(in[c], lane);
     __syncthreads();
-    // output row wc0 * 32 + t, K stage r0 / 256: 8 packed words -> 32 unpacked words
+    // output rows wc0 * 32 + 0 .. 255, K stage r0 / 256: each row's 8 packed words become its 128
+    // bytes (chunk k = the 4 unpacked words of packed word k); 8 consecutive threads write one
+    // row, so a warp's store covers 4 whole 128-byte lines
     const uint64_t rb = (uint64_t)q.n_pad / 2u;  // bytes per nibble row
-    uint4 *drow = reinterpret_cast<uint4 *>(ttn + ((uint64_t)a * q.n_pad + wc0 * 32 + t) * rb + (r0 / 256u) * 128u);
+    uint8_t *base = ttn + ((uint64_t)a * q.n_pad + wc0 * 32) * rb + (r0 / 256u) * 128u;
 #pragma unroll
-    for (int w = 0; w < 8; w++) {
-        const uint32_t v = out[t][w];
-        drow[w] = make_uint4(spread4(v, 0), spread4(v, 1), spread4(v, 2), spread4(v, 3));
+    for (int it = 0; it < 8; it++) {
+        const int c = it * 256 + t, r = c >> 3, k = c & 7;
+        const uint32_t v = out[r][k];
+        reinterpret_cast<uint4 *>(base + (uint64_t)r * rb)[k] = make_uint4(spread4(v, 0), spread4(v, 1), spread4(v, 2), spread4(v, 3));
     }
 }
 
