@@ -175,6 +175,10 @@ typedef struct {
                                  productions A -> B C of |{k : (i, k) in T_B, (k, j) in T_C}| */
     double tensor_live_ops;   /* Boolean ops the tensor-core products executed: 2 x 128 x 256 x 128
                                  per K step issued (equals dense_ops with dense_tensor = 1) */
+    double worklist_setup_ms; /* worklist path: wall time of building its tables (CSR adjacency of
+                                 the static relations, unique-successor and period power tables,
+                                 all on the device), at cfpq_create or at the first hand-over;
+                                 0 until then */
 } cfpq_stats;
 
 typedef struct cfpq_ctx cfpq_ctx;

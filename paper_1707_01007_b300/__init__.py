@@ -85,7 +85,7 @@ class Stats(ctypes.Structure):
                 ("worklist_items", ctypes.c_int64), ("schedule", ctypes.c_int32), ("gather_cpl", ctypes.c_int32),
                 ("useful_ops", ctypes.c_double), ("lengths_ms", ctypes.c_double),
                 ("lengths_launches", ctypes.c_int64), ("lengths_splits", ctypes.c_double),
-                ("tensor_live_ops", ctypes.c_double)]
+                ("tensor_live_ops", ctypes.c_double), ("worklist_setup_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1316,7 +1316,6 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
     }
     c->auto_mixed = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && tensor_path_available();
     c->allow_switch = c->path == CFPQ_PATH_AUTO && c->n_groups > 0 && c->schedule != CFPQ_SCHED_JACOBI;
-    if (c->allow_switch) c->h_edges.assign(edges, edges + n_edges);
     c->any_gather = c->n_groups > 0 && c->path != CFPQ_PATH_TENSOR && c->path != CFPQ_PATH_WORKLIST;
     {
         int dev = 0, sms = 0;
@@ -1490,7 +1489,7 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
         for (int g = 0; g < c->n_groups && g < kMaxNT; g++) st0.use_tensor[g] = c->group_tensor[g] ? 1u : 0u;
         CK(cudaMemcpyAsync(c->d_state0, &st0, sizeof(st0), cudaMemcpyHostToDevice, cs));
     }
-    if (c->path == CFPQ_PATH_WORKLIST) return worklist_setup(c, edges, n_edges);
+    if (c->path == CFPQ_PATH_WORKLIST) return worklist_setup(c, false);
     // the set-up above ran on the context's stream, and a solve may run on any stream the
     // caller names: finish it here (a server's contexts share the server's stream)
     if (!c->pooled) CK(cudaStreamSynchronize(cs));
@@ -1666,7 +1665,7 @@ int cfpq::solve_end(cfpq_ctx *c, cudaStream_t s) {
         // the loop stopped after a long run of tiny deltas: the worklist path finishes the
         // closure from the current delta (same least fixpoint)
         if (to_wl) {
-            if (!c->h_wl && (rc = worklist_setup(c, c->h_edges.data(), c->h_edges.size())) != CFPQ_OK) return rc;
+            if (!c->h_wl && (rc = worklist_setup(c, true)) != CFPQ_OK) return rc;
             const int64_t loops = c->stats.iterations;
             if ((rc = worklist_run(c, s, true)) != CFPQ_OK) return rc;
             CK(cudaEventRecord(c->ev1, s));

@@ -26,7 +26,6 @@ struct cfpq_ctx {
     bool any_gather = false;          // some group may take the gather product
     bool allow_switch = false;        // AUTO, not Jacobi: a long run of tiny deltas hands over to the worklist
     bool switched = false;            // the last solve finished on the worklist path
-    std::vector<cfpq_edge> h_edges;   // host copy of the edges (worklist set-up on a switch)
     uint32_t *d_list = nullptr;       // gather items of one loop execution (in the arena)
     uint32_t *d_colcnt = nullptr;     // profile mode: column counts of a left operand (n_pad)
     uint32_t list_cap = 0;
@@ -137,6 +136,7 @@ int enqueue_tensor_transposes_gated(cfpq_ctx *c, int g, cudaStream_t s);
 int enqueue_useful_work(cfpq_ctx *c, int g, cudaStream_t s);
 int tensor_prepare(cfpq_ctx *c);
 int enqueue_all_transposes(cfpq_ctx *c, cudaStream_t s);
+int enqueue_transpose_bits(cfpq_ctx *c, int a, cudaStream_t s);  // TT[a] = T[a]^T, bit-packed
 // Statistics and status of a solve from a copy of its device state.
 int apply_status(cfpq_ctx *c, const DevState &st);
 int run_loop(cfpq_ctx *c, cudaStream_t s);
@@ -163,7 +163,8 @@ int lengths_rules_ok(const cfpq_ctx *c);  // few enough productions for the deri
 int lengths_path(cfpq_ctx *c, int32_t A, uint32_t m, uint32_t n, uint32_t len, uint32_t *nodes, int32_t *labels);
 
 // worklist path (cfpq_worklist.cu)
-int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges);
+// seeded: T holds the seed already (a hand-over from the matrix loop); else it is seeded here
+int worklist_setup(cfpq_ctx *c, bool seeded);
 // from_delta: continue a closure the matrix loop started (stack = the current delta pairs,
 // T^T rebuilt from T); otherwise a full solve from the seeds.
 int worklist_run(cfpq_ctx *c, cudaStream_t s, bool from_delta = false);

@@ -987,11 +987,15 @@ int enqueue_tensor_occupancy(cfpq_ctx *c, cudaStream_t s) {
 }
 
 // T^T (bit-packed) of every non-terminal that a production derives (the worklist's hand-over).
-int enqueue_all_transposes(cfpq_ctx *c, cudaStream_t s) {
-    const dim3 grid(c->W / 8, c->n_pad / 256);
-    for (int a = 0; a < c->n_nt; a++)
-        if (c->nt_dynamic[a]) tc::k_transpose<<<grid, 256, 0, s>>>(c->d_q, a, -1);
+int enqueue_transpose_bits(cfpq_ctx *c, int a, cudaStream_t s) {
+    tc::k_transpose<<<dim3(c->W / 8, c->n_pad / 256), 256, 0, s>>>(c->d_q, a, -1);
     return cudaGetLastError() == cudaSuccess ? CFPQ_OK : CFPQ_ERR_CUDA;
+}
+
+int enqueue_all_transposes(cfpq_ctx *c, cudaStream_t s) {
+    for (int a = 0; a < c->n_nt; a++)
+        if (c->nt_dynamic[a] && enqueue_transpose_bits(c, a, s) != CFPQ_OK) return CFPQ_ERR_CUDA;
+    return CFPQ_OK;
 }
 
 // After the matrix initialisation: transposes of every right operand of a tensor group.

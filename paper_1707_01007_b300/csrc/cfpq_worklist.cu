@@ -11,7 +11,7 @@
 // (or, when it is the only new pair, handed to the next step in registers). When the stack
 // is empty, T is closed under every production: the same least fixpoint as the matrix loop.
 // Partners of non-terminals that no production derives (their relation is exactly the seed)
-// come from CSR adjacency built on the host; partners of the others from the bit matrices:
+// come from CSR adjacency built from T by set-up kernels; partners of the others from the bit matrices:
 // row j of T_C, and row i of T_B^T (T^T is kept for every derived non-terminal).
 //
 // Warp 0 of block 0 owns the stack. Batches of general pairs are joined by all 16 warps of
@@ -19,6 +19,7 @@
 // chains (which return to their non-terminal) are computed by binary lifting in rounds that
 // span up to 128 blocks of a cooperative launch.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <vector>
 
@@ -688,18 +689,157 @@ __global__ void k_worklist_init(const QDesc *qd, WLDesc w, unsigned long long *t
     }
 }
 
+// ------------------------------------------------------------------ set-up (device tables)
+//
+// A non-terminal that no production derives keeps exactly its seed, so its relation is read
+// from T (and from T^T, its bit transpose) once the seed is in place. Its two CSRs (by row
+// and by column), the unique-successor tables and the power tables of the period maps are
+// built here by kernels, each launch covering every static relation (grid y), in the places
+// the host laid out: CSR ci = 2 r + dir of the r-th static relation (dir 0: by row, from T;
+// 1: by column, from T^T) has its n + 1 offsets at csr_off + ci (n + 1) and its
+// unique-successor table at uniq + ci n; map m's power tables start at lift + m L n.
+struct CsrPlan {
+    const uint32_t *T, *TT;      // bit planes
+    uint64_t plane;              // words per plane
+    const int32_t *statics;      // [n_static] non-terminal of each static relation
+    uint32_t n, W;
+};
+
+__device__ __forceinline__ const uint32_t *csr_plane(const CsrPlan &p, uint32_t ci) {
+    const int32_t a = p.statics[ci >> 1];
+    return ((ci & 1u) ? p.TT : p.T) + (uint64_t)a * p.plane;
+}
+
+// Row popcounts: off[ci (n + 1) + i] = |row i| for i < n. One warp per row.
+__global__ void k_csr_count(CsrPlan p, uint32_t *csr_off) {
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= p.n) return;
+    const uint32_t *row = csr_plane(p, blockIdx.y) + warp * p.W;
+    uint32_t c = 0;
+    for (uint32_t w = lane; w < p.W; w += 32) c += (uint32_t)__popc(__ldcg(row + w));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) csr_off[(uint64_t)blockIdx.y * (p.n + 1) + warp] = c;
+}
+
+// The counts become offsets into the one column array shared by every CSR, in place: the
+// CSRs in order, each row's offset = the columns of every row before it (earlier CSRs
+// included), off[n] of each CSR = its end. One block of 1024 threads, each scanning a
+// contiguous run of rows; the 64-bit total goes to *total, which the host checks against the
+// 32-bit offset range before any column is written.
+__global__ void __launch_bounds__(1024) k_csr_scan(uint32_t *csr_off, uint32_t n, uint32_t n_csr,
+                                                   unsigned long long *total) {
+    __shared__ unsigned long long part[1024];
+    const uint32_t t = threadIdx.x;
+    const uint32_t per = (n + 1023u) / 1024u;
+    const uint32_t lo = min(n, t * per), hi = min(n, lo + per);
+    unsigned long long base = 0;
+    for (uint32_t ci = 0; ci < n_csr; ci++) {
+        uint32_t *off = csr_off + (uint64_t)ci * (n + 1);
+        unsigned long long sum = 0;
+        for (uint32_t i = lo; i < hi; i++) sum += off[i];
+        part[t] = sum;
+        __syncthreads();
+        for (uint32_t o = 1; o < 1024; o <<= 1) {
+            const unsigned long long v = t >= o ? part[t - o] : 0ull;
+            __syncthreads();
+            part[t] += v;
+            __syncthreads();
+        }
+        unsigned long long acc = base + part[t] - sum;
+        for (uint32_t i = lo; i < hi; i++) {
+            const uint32_t c = off[i];
+            off[i] = (uint32_t)acc;
+            acc += c;
+        }
+        base += part[1023];
+        if (t == 0) off[n] = (uint32_t)base;
+        __syncthreads();  // part is rewritten by the next CSR
+    }
+    if (t == 0) *total = base;
+}
+
+// The columns: row i's set bits in ascending order from col[off[i]]. One warp per row; each
+// 32-word chunk of the row is placed by a warp prefix sum of its words' popcounts. Then the
+// row's unique-successor entry: its only column, or kNone when it has none or several.
+__global__ void k_csr_fill(CsrPlan p, const uint32_t *csr_off, uint32_t *col, uint32_t *uniq) {
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= p.n) return;
+    const uint32_t ci = blockIdx.y;
+    const uint32_t *row = csr_plane(p, ci) + warp * p.W;
+    const uint32_t *off = csr_off + (uint64_t)ci * (p.n + 1);
+    const uint32_t start = off[warp];
+    uint32_t pos = start;
+    for (uint32_t w0 = 0; w0 < p.W; w0 += 32) {
+        uint32_t bits = (w0 + lane < p.W) ? __ldcg(row + w0 + lane) : 0u;
+        const uint32_t c = (uint32_t)__popc(bits);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        uint32_t q = pos + incl - c;
+        while (bits) {
+            col[q++] = (w0 + lane) * 32u + (uint32_t)(__ffs(bits) - 1);
+            bits &= bits - 1;
+        }
+        pos += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    if (lane == 0) uniq[(uint64_t)ci * p.n + warp] = pos - start == 1u ? col[start] : kNone;
+}
+
+// One period of a periodic chain (grid y): G (row) and H (column) start as the identity and go
+// through the unique-successor table of each of its P <= 2 steps, on the coordinate that step
+// moves; level 0 of the power tables of the maps that move (map index -1: identity, no table).
+struct PeriodSteps {
+    int32_t P, col0, col1, g_map, h_map, pad;
+    uint64_t m0, m1;  // the steps' tables in uniq
+};
+
+__global__ void k_period_maps(const uint32_t *uniq, const PeriodSteps *periods, uint32_t n, uint32_t *lift) {
+    const uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= n) return;
+    const PeriodSteps ps = periods[blockIdx.y];
+    uint32_t g = (uint32_t)y, h = (uint32_t)y;
+    for (int st = 0; st < ps.P; st++) {
+        const uint32_t *M = uniq + (st == 0 ? ps.m0 : ps.m1);
+        uint32_t &f = (st == 0 ? ps.col0 : ps.col1) ? h : g;
+        f = f == kNone ? kNone : M[f];
+    }
+    const uint64_t L = (uint64_t)kLiftLevels * n;
+    if (ps.g_map >= 0) lift[(uint64_t)ps.g_map * L + y] = g;
+    if (ps.h_map >= 0) lift[(uint64_t)ps.h_map * L + y] = h;
+}
+
+// Level lv of every map's power table (grid y: the map) from level lv - 1:
+// F^(2^lv) = F^(2^(lv-1)) o F^(2^(lv-1)).
+__global__ void k_lift_level(uint32_t *lift, uint32_t n, int lv) {
+    const uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= n) return;
+    const uint32_t *prev = lift + (uint64_t)blockIdx.y * kLiftLevels * n + (uint64_t)(lv - 1) * n;
+    const uint32_t v = prev[y];
+    lift[(uint64_t)blockIdx.y * kLiftLevels * n + (uint64_t)lv * n + y] = v == kNone ? kNone : prev[v];
+}
+
 // ------------------------------------------------------------------------------------ host
 
 struct WorklistState {
     WLDesc d;
     void *arena = nullptr;
+    void *cols = nullptr;  // the CSR columns of the static relations
     unsigned long long *d_top = nullptr;
     int blocks = 1;  // grid of the walk: periodic chains use up to kMaxPcBlocks blocks
 };
 
-int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
+int worklist_setup(cfpq_ctx *c, bool seeded) {
+    const auto t_begin = std::chrono::steady_clock::now();
     const int n_nt = c->n_nt;
-    const uint32_t n = c->n;
+    const uint32_t n = c->n, W = c->W;
+    cudaStream_t s = c->stream;
     std::vector<int32_t> is_static(n_nt, 1), needs_tt(n_nt, 0);
     for (const Rule &r : c->rules) is_static[r.lhs] = 0;
     // T^T is kept for every derived non-terminal: right-operand joins read T_p^T of a dynamic
@@ -718,48 +858,20 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
         occ_flat.insert(occ_flat.end(), occ[a].begin(), occ[a].end());
     }
     occ_start[n_nt] = (int32_t)occ_flat.size();
-    // CSR of static non-terminals (their relation is exactly the seed: edges and eps)
-    std::vector<std::vector<int32_t>> heads(c->n_term);
-    for (const int2 &u : c->h_unary) heads[u.y].push_back(u.x);
-    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> pairs(n_nt);
-    for (size_t e = 0; e < n_edges; e++)
-        for (int a : heads[edges[e].label])
-            if (is_static[a]) pairs[a].push_back({edges[e].src, edges[e].dst});
-    for (int a : c->h_eps)
-        if (is_static[a])
-            for (uint32_t m = 0; m < n; m++) pairs[a].push_back({m, m});
-    std::vector<uint64_t> out_base(n_nt, 0), in_base(n_nt, 0);
-    std::vector<uint32_t> csr_off, csr_col;
-    auto build = [&](std::vector<std::pair<uint32_t, uint32_t>> &pr, bool by_src) {
-        const uint64_t base = csr_off.size();
-        std::sort(pr.begin(), pr.end(), [&](const auto &x, const auto &y) {
-            return by_src ? (x.first != y.first ? x.first < y.first : x.second < y.second)
-                          : (x.second != y.second ? x.second < y.second : x.first < y.first);
-        });
-        pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
-        std::vector<uint32_t> off(n + 1, 0);
-        for (const auto &e : pr) off[(by_src ? e.first : e.second) + 1]++;
-        for (uint32_t i = 0; i < n; i++) off[i + 1] += off[i];
-        const uint32_t col0 = (uint32_t)csr_col.size();
-        for (uint32_t i = 0; i <= n; i++) csr_off.push_back(col0 + off[i]);
-        for (const auto &e : pr) csr_col.push_back(by_src ? e.second : e.first);
-        return base;
-    };
-    std::vector<uint64_t> uniq_out_base(n_nt, 0), uniq_in_base(n_nt, 0);
-    std::vector<uint32_t> uniq;
+    // layout of the tables of static non-terminals: two CSRs (n + 1 offsets each; the columns
+    // are counted on the device) and two unique-successor tables (n entries each)
+    std::vector<uint64_t> out_base(n_nt, 0), in_base(n_nt, 0), uniq_out_base(n_nt, 0), uniq_in_base(n_nt, 0);
+    std::vector<int> statics;
+    uint64_t n_off = 0, n_uniq = 0;
     for (int a = 0; a < n_nt; a++)
         if (is_static[a]) {
-            out_base[a] = build(pairs[a], true);
-            in_base[a] = build(pairs[a], false);
-            // unique successor tables from the two CSRs just built
-            for (int dir = 0; dir < 2; dir++) {
-                const uint64_t b = dir == 0 ? out_base[a] : in_base[a];
-                (dir == 0 ? uniq_out_base : uniq_in_base)[a] = uniq.size();
-                for (uint32_t key = 0; key < n; key++) {
-                    const uint32_t lo = csr_off[b + key], hi = csr_off[b + key + 1];
-                    uniq.push_back(hi - lo == 1 ? csr_col[lo] : 0xFFFFFFFFu);
-                }
-            }
+            statics.push_back(a);
+            out_base[a] = n_off;
+            in_base[a] = n_off + n + 1;
+            n_off += 2ull * (n + 1);
+            uniq_out_base[a] = n_uniq;
+            uniq_in_base[a] = n_uniq + n;
+            n_uniq += 2ull * n;
         }
     std::vector<int4> chain(n_nt, make_int4(0, 0, 0, 0));
     std::vector<uint64_t> chain_base(n_nt, 0);
@@ -772,11 +884,12 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
         chain[a] = make_int4(1, r.lhs, left ? 1 : 0, p);
         chain_base[a] = left ? uniq_out_base[p] : uniq_in_base[p];
     }
-    // periodic chains (a -> a or a -> a1 -> a through chain steps) and the power tables of
-    // their period maps G (row) and H (column)
+    // periodic chains (a -> a or a -> a1 -> a through chain steps): the steps of a period and
+    // the places of the power tables of its maps G (row) and H (column), where they move
     std::vector<PChain> pchain(n_nt);
     memset(pchain.data(), 0, sizeof(PChain) * n_nt);
-    std::vector<uint32_t> lift;
+    std::vector<PeriodSteps> periods;
+    int n_maps = 0;
     for (int a = 0; a < n_nt; a++) {
         if (!chain[a].x) continue;
         const int a1 = chain[a].y;
@@ -784,72 +897,78 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
         if (a1 == a) P = 1;
         else if (chain[a1].x && chain[a1].y == a) P = 2;
         if (P == 0) continue;
-        std::vector<uint32_t> G(n), H(n);
-        for (uint32_t x = 0; x < n; x++) G[x] = H[x] = x;
-        bool row_moves = false, col_moves = false;
-        for (int st = 0; st < P; st++) {
-            const int x = st == 0 ? a : a1;
-            const bool col = chain[x].z != 0;  // left operand: the column moves
-            const uint32_t *M = uniq.data() + chain_base[x];
-            std::vector<uint32_t> &F = col ? H : G;
-            (col ? col_moves : row_moves) = true;
-            for (uint32_t y = 0; y < n; y++) F[y] = F[y] == kNone ? kNone : M[F[y]];
-        }
+        PeriodSteps ps;
+        memset(&ps, 0, sizeof(ps));
+        ps.g_map = ps.h_map = -1;
+        ps.P = P;
+        ps.col0 = chain[a].z != 0 ? 1 : 0;  // left operand: the column moves
+        ps.m0 = chain_base[a];
+        ps.col1 = P == 2 && chain[a1].z != 0 ? 1 : 0;
+        ps.m1 = P == 2 ? chain_base[a1] : 0;
+        const bool row_moves = !ps.col0 || (P == 2 && !ps.col1);
+        const bool col_moves = ps.col0 || (P == 2 && ps.col1);
         PChain pc;
         memset(&pc, 0, sizeof(pc));
         pc.P = P;
         pc.a1 = a1;
-        pc.c0 = chain[a].z != 0 ? 1 : 0;
+        pc.c0 = ps.col0;
         pc.m0 = chain_base[a];
         pc.g_id = row_moves ? 0 : 1;
         pc.h_id = col_moves ? 0 : 1;
-        auto powers = [&](const std::vector<uint32_t> &F) {
-            const uint64_t base = lift.size();
-            lift.insert(lift.end(), F.begin(), F.end());
-            for (int k = 1; k < kLiftLevels; k++) {
-                const uint64_t prev = base + (uint64_t)(k - 1) * n;
-                for (uint32_t y = 0; y < n; y++) {
-                    const uint32_t v = lift[prev + y];
-                    lift.push_back(v == kNone ? kNone : lift[prev + v]);
-                }
-            }
-            return base;
-        };
-        pc.lg = row_moves ? powers(G) : 0;
-        pc.lh = col_moves ? powers(H) : 0;
+        if (row_moves) {
+            ps.g_map = n_maps++;
+            pc.lg = (uint64_t)ps.g_map * kLiftLevels * n;
+        }
+        if (col_moves) {
+            ps.h_map = n_maps++;
+            pc.lh = (uint64_t)ps.h_map * kLiftLevels * n;
+        }
         pchain[a] = pc;
+        periods.push_back(ps);
     }
-    // device arena
+    const uint64_t n_lift = (uint64_t)n_maps * kLiftLevels * n;
+    // device arena (the CSR columns follow once their number is known)
     const uint64_t cap_full = (uint64_t)n_nt * (uint64_t)n * (uint64_t)n;
     const uint64_t cap = std::max<uint64_t>(1024, std::min<uint64_t>(cap_full, 1ull << 27));
     struct Part { void **dst; size_t bytes; };
     WorklistState *ws = new WorklistState();
     WLDesc &d = ws->d;
     memset(&d, 0, sizeof(d));
+    unsigned long long *d_total = nullptr;
+    int32_t *d_statics = nullptr;
+    PeriodSteps *d_periods = nullptr;
     const Part parts[] = {{(void **)&d.occ, occ_flat.size() * sizeof(int2) + 8},
                           {(void **)&d.occ_start, occ_start.size() * 4},
                           {(void **)&d.is_static, (size_t)n_nt * 4},
                           {(void **)&d.out_base, (size_t)n_nt * 8},
                           {(void **)&d.in_base, (size_t)n_nt * 8},
-                          {(void **)&d.csr_off, csr_off.size() * 4 + 8},
-                          {(void **)&d.csr_col, csr_col.size() * 4 + 8},
+                          {(void **)&d.csr_off, n_off * 4 + 8},
                           {(void **)&d.needs_tt, (size_t)n_nt * 4},
                           {(void **)&d.chain, (size_t)n_nt * sizeof(int4)},
                           {(void **)&d.chain_base, (size_t)n_nt * 8},
-                          {(void **)&d.uniq, uniq.size() * 4 + 8},
+                          {(void **)&d.uniq, n_uniq * 4 + 8},
                           {(void **)&d.pchain, (size_t)n_nt * sizeof(PChain)},
-                          {(void **)&d.lift, lift.size() * 4 + 8},
+                          {(void **)&d.lift, n_lift * 4 + 8},
                           {(void **)&d.pcc, sizeof(PcCtl)},
                           {(void **)&d.stack, cap * 12},
                           {(void **)&d.items, 8},
                           {(void **)&d.overflow, 8},
-                          {(void **)&ws->d_top, 8}};
+                          {(void **)&ws->d_top, 8},
+                          {(void **)&d_total, 8},
+                          {(void **)&d_statics, statics.size() * 4 + 8},
+                          {(void **)&d_periods, periods.size() * sizeof(PeriodSteps) + 8}};
     size_t total = 0;
     for (const Part &p : parts) total += (p.bytes + 255) / 256 * 256;
-    cudaError_t e = ctx_alloc(c, &ws->arena, total, c->stream);
-    if (e != cudaSuccess) {
+    auto fail = [&](int rc) {
+        if (ws->arena) ctx_free(c, ws->arena, s);
+        if (ws->cols) ctx_free(c, ws->cols, s);
         delete ws;
-        return e == cudaErrorMemoryAllocation ? CFPQ_ERR_NOMEM : CFPQ_ERR_CUDA;
+        return rc;
+    };
+    cudaError_t e = ctx_alloc(c, &ws->arena, total, s);
+    if (e != cudaSuccess) {
+        ws->arena = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? CFPQ_ERR_NOMEM : CFPQ_ERR_CUDA);
     }
     char *ptr = static_cast<char *>(ws->arena);
     for (const Part &p : parts) {
@@ -857,8 +976,7 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
         ptr += (p.bytes + 255) / 256 * 256;
     }
     d.cap = cap;
-    bool any_periodic = false;
-    for (const PChain &pc : pchain) any_periodic |= pc.P > 0;
+    bool any_periodic = !periods.empty();
     if (any_periodic) {
         // every block of the grid must be resident at once (cooperative launch)
         int dev = 0, sms = 0, per_sm = 0, coop = 0;
@@ -871,7 +989,6 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
         }
         cudaGetLastError();
     }
-    cudaStream_t s = c->stream;
     bool ok = true;
     auto up = [&](const void *dst, const void *src, size_t bytes) {
         if (bytes && cudaMemcpyAsync(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
@@ -882,22 +999,61 @@ int worklist_setup(cfpq_ctx *c, const cfpq_edge *edges, size_t n_edges) {
     up(d.is_static, is_static.data(), (size_t)n_nt * 4);
     up(d.out_base, out_base.data(), (size_t)n_nt * 8);
     up(d.in_base, in_base.data(), (size_t)n_nt * 8);
-    up(d.csr_off, csr_off.data(), csr_off.size() * 4);
-    up(d.csr_col, csr_col.data(), csr_col.size() * 4);
     up(d.needs_tt, needs_tt.data(), (size_t)n_nt * 4);
     up(d.chain, chain.data(), (size_t)n_nt * sizeof(int4));
     up(d.chain_base, chain_base.data(), (size_t)n_nt * 8);
-    up(d.uniq, uniq.data(), uniq.size() * 4);
     up(d.pchain, pchain.data(), (size_t)n_nt * sizeof(PChain));
-    up(d.lift, lift.data(), lift.size() * 4);
-    // the uploads ran on the context's stream; the worklist may run on another one
-    if (ok && !c->pooled && cudaStreamSynchronize(s) != cudaSuccess) ok = false;
-    if (!ok) {
-        ctx_free(c, ws->arena, s);
-        delete ws;
-        return CFPQ_ERR_CUDA;
+    up(d_statics, statics.data(), statics.size() * 4);
+    up(d_periods, periods.data(), periods.size() * sizeof(PeriodSteps));
+    if (!ok) return fail(CFPQ_ERR_CUDA);
+    // the static relations: the seed, in T (a context handed over from the matrix loop holds
+    // it already: no production writes a static non-terminal), and its transpose in T^T
+    // (scratch here: the worklist keeps T^T of derived non-terminals only)
+    if (!seeded) {
+        const int rc = enqueue_reset_and_seed(c, s);
+        if (rc != CFPQ_OK) return fail(rc);
     }
+    const uint32_t n_csr = 2u * (uint32_t)statics.size();
+    unsigned long long n_col = 0;
+    CsrPlan plan;
+    plan.T = c->d_T;
+    plan.TT = c->d_TT;
+    plan.plane = c->plane;
+    plan.statics = d_statics;
+    plan.n = n;
+    plan.W = W;
+    const uint32_t row_blocks = (uint32_t)std::max<uint64_t>(1, ((uint64_t)n * 32 + 255) / 256);
+    const uint32_t key_blocks = (uint32_t)std::max<uint64_t>(1, ((uint64_t)n + 255) / 256);
+    if (n_csr) {
+        for (int a : statics)
+            if (enqueue_transpose_bits(c, a, s) != CFPQ_OK) return fail(CFPQ_ERR_CUDA);
+        k_csr_count<<<dim3(row_blocks, n_csr), 256, 0, s>>>(plan, const_cast<uint32_t *>(d.csr_off));
+        k_csr_scan<<<1, 1024, 0, s>>>(const_cast<uint32_t *>(d.csr_off), n, n_csr, d_total);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&n_col, d_total, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(CFPQ_ERR_CUDA);
+        if (n_col > 0xFFFFFFFFull) return fail(CFPQ_ERR_NOMEM);  // offsets are 32-bit
+    }
+    if ((e = ctx_alloc(c, &ws->cols, n_col * 4 + 8, s)) != cudaSuccess) {
+        ws->cols = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? CFPQ_ERR_NOMEM : CFPQ_ERR_CUDA);
+    }
+    d.csr_col = static_cast<uint32_t *>(ws->cols);
+    if (n_csr)
+        k_csr_fill<<<dim3(row_blocks, n_csr), 256, 0, s>>>(plan, d.csr_off, const_cast<uint32_t *>(d.csr_col),
+                                                           const_cast<uint32_t *>(d.uniq));
+    if (!periods.empty() && n_maps > 0) {  // every period moves a coordinate: n_maps >= 1
+        uint32_t *lift = const_cast<uint32_t *>(d.lift);
+        k_period_maps<<<dim3(key_blocks, (uint32_t)periods.size()), 256, 0, s>>>(d.uniq, d_periods, n, lift);
+        for (int lv = 1; lv < kLiftLevels; lv++) k_lift_level<<<dim3(key_blocks, (uint32_t)n_maps), 256, 0, s>>>(lift, n, lv);
+    }
+    // the worklist may run on another stream than the context's
+    if (cudaGetLastError() != cudaSuccess || (!c->pooled && cudaStreamSynchronize(s) != cudaSuccess))
+        return fail(CFPQ_ERR_CUDA);
     c->h_wl = ws;
+    c->stats.worklist_setup_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
     return CFPQ_OK;
 }
 
@@ -905,6 +1061,7 @@ void worklist_release(cfpq_ctx *c) {
     WorklistState *ws = static_cast<WorklistState *>(c->h_wl);
     if (!ws) return;
     ctx_free(c, ws->arena, c->stream);
+    if (ws->cols) ctx_free(c, ws->cols, c->stream);
     delete ws;
     c->h_wl = nullptr;
 }

@@ -107,3 +107,32 @@ def test_period_two_chain_on_one_coordinate():
     # (i, j) with i even and j = i + 2k, k >= 0
     assert q.count("S") == sum((n - 1 - i) // 2 + 1 for i in range(0, n, 2))
     parity(labelled_graph(401, e[:400] + [(i, 2, i) for i in range(0, 401, 2)], ["b", "c", "a"]), text)
+
+
+def test_static_relations_with_repeats_eps_and_empty():
+    # the static relations are the seeds as sets: repeated edges, two labels seeding the same
+    # pair of B, eps on B (the diagonal, which also meets the a-loops' pairs), and a static Z
+    # with no pair at all; n spans several 32-bit words with a ragged tail
+    n = 777
+    e = [(i, 0, i + 1) for i in range(n - 1)] * 2
+    e += [(i, 1, i + 1) for i in range(0, n - 1, 3)]
+    e += [(i, 2, i) for i in range(0, n, 5)] * 2
+    graph = labelled_graph(n, e, ["b", "c", "a", "z"])
+    parity(graph, "S S B\nS a\nB b\nB c\nB eps\nX S Z\nZ z\nY B S\n")
+
+
+@pytest.mark.parametrize("path", ["auto", "worklist"])
+def test_tables_rebuilt_per_context(path):
+    # two contexts one after the other: the second's tables come from its own seed, not from
+    # the memory the first left behind
+    p = eng.PATH_AUTO if path == "auto" else eng.PATH_WORKLIST
+    for (pp, qq) in ((40, 39), (33, 32)):
+        graph = synth.two_cycles(pp, qq)
+        g = eng.Grammar(synth.GRAMMAR_C3, graph.labels)
+        q = eng.Query(g, graph.n, graph.edges, path=p, timeout_s=300.0)
+        q.solve()
+        ref = oracle.hellings(graph, synth.GRAMMAR_C3)
+        for nm in g.names:
+            assert np.array_equal(q.get(nm), ref.pairs(nm)), (pp, nm)
+        assert q.stats()["worklist_items"] > 0  # the automatic path handed over to the worklist
+        q.close()
