@@ -56,11 +56,33 @@ class Triple(ctypes.Structure):
     _fields_ = [("A", ctypes.c_int32), ("m", ctypes.c_uint32), ("n", ctypes.c_uint32)]
 
 
+_PINNED = None  # torch, when its CUDA host allocator can stage results (False: plain numpy)
+
+
+def _host_words(rows: int, cols: int) -> np.ndarray:
+    """A (rows, cols) uint32 host array for results copied from the device. Page-locked memory
+    from torch's caching host allocator where CUDA is up: the device-to-host copy then runs at
+    the link's rate with no staging or page faults, and the block returns to the allocator's
+    cache when the array is dropped (the array keeps its tensor alive)."""
+    global _PINNED
+    if _PINNED is None:
+        try:
+            import torch
+
+            _PINNED = torch if torch.cuda.is_available() else False
+        except ImportError:
+            _PINNED = False
+    if _PINNED:
+        t = _PINNED.empty((rows, cols), dtype=_PINNED.int32, pin_memory=True)
+        return t.numpy().view("<u4")
+    return np.empty((rows, cols), dtype="<u4")
+
+
 def _triple_rows(k: int) -> np.ndarray:
     """A host buffer for k cfpq_triple records as a (k, 3) uint32 array: the record is three
     32-bit words, and A (a non-terminal id) and m, n (< CFPQ_MAX_NODES) are non-negative,
     so the unsigned view reads every field exactly."""
-    return np.empty((max(k, 1), 3), dtype="<u4")
+    return _host_words(max(k, 1), 3)
 
 
 def _triple_ptr(buf: np.ndarray):
@@ -316,23 +338,37 @@ class Query:
         return int(c.value)
 
     def triples(self, A) -> np.ndarray:
-        """R_A as an (k, 3) int64 array of (A, m, n) triples, sorted by (m, n)."""
+        """R_A as an (k, 3) uint32 array of (A, m, n) triples, sorted by (m, n)."""
         a = self._aid(A)
         c = ctypes.c_size_t()
         _check(_lib().cfpq_get(self._h, a, None, 0, ctypes.byref(c)), "cfpq_get")
         k = int(c.value)
         buf = _triple_rows(k)
         _check(_lib().cfpq_get(self._h, a, _triple_ptr(buf), k, ctypes.byref(c)), "cfpq_get")
-        return buf[:k].astype(np.int64)
+        return buf[:k]
 
     def triples_all(self) -> np.ndarray:
-        """Every relation as an (k, 3) int64 array of (A, m, n), sorted (``cfpq_get_all``)."""
+        """Every relation as an (k, 3) uint32 array of (A, m, n), sorted (``cfpq_get_all``).
+        The last solve's pair counters (seed pairs plus pairs the products added, each counted
+        when its bit was first set) size the buffer, so one call usually does; a buffer that
+        turns out too small takes the exact count from that call and a second one."""
         c = ctypes.c_size_t()
-        _check(_lib().cfpq_get_all(self._h, None, 0, ctypes.byref(c)), "cfpq_get_all")
+        st = Stats()
+        _check(_lib().cfpq_stats_get(self._h, ctypes.byref(st)), "cfpq_stats_get")
+        hint = max(0, int(st.seed_bits) + int(st.new_bits))
+        if hint > 0:
+            buf = _triple_rows(hint)
+            rc = _lib().cfpq_get_all(self._h, _triple_ptr(buf), hint, ctypes.byref(c))
+            if rc == OK:
+                return buf[:int(c.value)]
+            if rc != ERR_BUFFER:
+                _check(rc, "cfpq_get_all")
+        else:
+            _check(_lib().cfpq_get_all(self._h, None, 0, ctypes.byref(c)), "cfpq_get_all")
         k = int(c.value)
         buf = _triple_rows(k)
         _check(_lib().cfpq_get_all(self._h, _triple_ptr(buf), k, ctypes.byref(c)), "cfpq_get_all")
-        return buf[:k].astype(np.int64)
+        return buf[:k]
 
     def get(self, A) -> np.ndarray:
         """R_A as a sorted (k, 2) uint32 array of (m, n)."""
