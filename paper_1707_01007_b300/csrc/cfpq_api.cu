@@ -79,11 +79,10 @@ __global__ void __launch_bounds__(256) k_scan_rows(const QDesc *qd, uint32_t *li
     scan_rows(q, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint32_t)(q.st->iter & 1ull), list, cap, nch);
 }
 
+// The listed gathers of one loop execution over the warps of the grid (every thread of every
+// block calls it).
 template <int CPL>
-__global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDesc *qd, const uint32_t *list, uint32_t cap,
-                                                                       int honor_skip) {
-    const QDesc &q = *qd;
-    if (honor_skip && ld_u32(&q.st->skip)) return;  // an unrolled loop body past the loop's end
+__device__ __forceinline__ void gather_listed(const QDesc &q, const uint32_t *list, uint32_t cap) {
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -121,13 +120,19 @@ __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDe
     }
 }
 
+template <int CPL>
+__global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4) k_gather_list(const QDesc *qd, const uint32_t *list, uint32_t cap,
+                                                                       int honor_skip) {
+    const QDesc &q = *qd;
+    if (honor_skip && ld_u32(&q.st->skip)) return;  // an unrolled loop body past the loop's end
+    gather_listed<CPL>(q, list, cap);
+}
+
 // Jacobi schedule: T |= N over the rows N touched (T_{k+1} = T_k u T_k x T_k). Persistent grid,
 // one warp per flagged row (the lanes test 32 rows of the warp's share at once; four chunks of
 // 32 words in flight); the word summary of T follows, and where lengths are kept (TTsum set)
 // T^T and its summary too, their bits set one per lane per round.
-__global__ void __launch_bounds__(256) k_merge(const QDesc *qd, int honor_skip) {
-    const QDesc &q = *qd;
-    if (honor_skip && ld_u32(&q.st->skip)) return;
+__device__ __forceinline__ void merge_new_rows(const QDesc &q) {
     const int lane = threadIdx.x & 31;
     const uint64_t gwarp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t gwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -179,6 +184,12 @@ __global__ void __launch_bounds__(256) k_merge(const QDesc *qd, int honor_skip) 
     }
 }
 
+__global__ void __launch_bounds__(256) k_merge(const QDesc *qd, int honor_skip) {
+    const QDesc &q = *qd;
+    if (honor_skip && ld_u32(&q.st->skip)) return;
+    merge_new_rows(q);
+}
+
 // Start of a solve (the matrix initialisation's first part): the loop state from the context's
 // template with the deadline armed, and every word of the three row bitmaps (T and both
 // deltas) zeroed; on a context whose last solve converged (clear_t), the rows of T that its
@@ -228,15 +239,15 @@ __global__ void __launch_bounds__(128) k_reset(const QDesc *qd, const DevState *
 // word of 32 rows) units grid-stride (block b of nb); the k-th flagged row of a unit goes to
 // warp k % (warps per block), which zeroes it with 16-byte stores (W is a multiple of 8, so
 // every row is whole uint4s).
-__device__ __forceinline__ void clear_delta_rows(const QDesc &q, uint32_t b, uint32_t nb) {
+__device__ __forceinline__ void clear_delta_rows(const QDesc &q, uint32_t b, uint32_t nb, uint32_t parity) {
     const uint32_t rw = (q.n + 31u) / 32u;
-    const uint32_t parity = (uint32_t)(q.st->iter & 1ull);
     const uint32_t W4 = q.W / 4u;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    const uint32_t *DR = parity ? q.R1 : q.R0;
     for (uint32_t unit = b; unit < (uint32_t)q.n_nt * rw; unit += nb) {
         const int a = (int)(unit / rw);
         const uint32_t wq = unit % rw;
-        uint32_t rows = __ldcg((parity ? q.R1 : q.R0) + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
+        uint32_t rows = __ldcg(DR + (uint64_t)a * q.W + wq) & rows_in_word(q.n, wq);
         uint4 *D = reinterpret_cast<uint4 *>((parity ? q.X1 : q.X0) + (uint64_t)a * q.plane);
         for (int k = 0; rows; k++) {
             const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
@@ -247,9 +258,31 @@ __device__ __forceinline__ void clear_delta_rows(const QDesc &q, uint32_t b, uin
     }
 }
 
+// The same clear for one (non-terminal, row word) unit by one warp: it reads the unit's word
+// of the read row bitmap, zeroes that word (so the tail need not zero the bitmap), and zeroes
+// the flagged rows.
+__device__ __forceinline__ void clear_delta_unit_warp(const QDesc &q, uint64_t unit, uint32_t parity) {
+    const uint32_t rw = (q.n + 31u) / 32u;
+    const uint32_t W4 = q.W / 4u;
+    const int lane = threadIdx.x & 31;
+    const uint64_t a = unit / rw;
+    const uint32_t wq = (uint32_t)(unit % rw);
+    uint32_t *word = (parity ? q.R1 : q.R0) + a * q.W + wq;
+    const uint32_t v = __ldcg(word);
+    __syncwarp();
+    if (lane == 0 && v) *word = 0u;
+    uint32_t rows = v & rows_in_word(q.n, wq);
+    uint4 *D = reinterpret_cast<uint4 *>((parity ? q.X1 : q.X0) + a * q.plane);
+    while (rows) {
+        const uint64_t i = wq * 32u + (uint32_t)(__ffs(rows) - 1);
+        rows &= rows - 1;
+        for (uint32_t w = (uint32_t)lane; w < W4; w += 32u) D[i * W4 + w] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
 __global__ void __launch_bounds__(128) k_clear(const QDesc *qd, int honor_skip) {
     if (honor_skip && ld_u32(&qd->st->skip)) return;
-    clear_delta_rows(*qd, blockIdx.x, gridDim.x);
+    clear_delta_rows(*qd, blockIdx.x, gridDim.x, (uint32_t)(qd->st->iter & 1ull));
 }
 
 // End of a loop execution on a path with gathers: blocks below scan_blocks list the next
@@ -263,7 +296,7 @@ __global__ void __launch_bounds__(256) k_clear_scan(const QDesc *qd, uint32_t *l
         scan_rows(q, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint32_t)((q.st->iter + 1ull) & 1ull), list,
                   cap, nch);
     else
-        clear_delta_rows(q, blockIdx.x - scan_blocks, gridDim.x - scan_blocks);
+        clear_delta_rows(q, blockIdx.x - scan_blocks, gridDim.x - scan_blocks, (uint32_t)(q.st->iter & 1ull));
 }
 
 
@@ -410,6 +443,90 @@ __global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int u
     }
 }
 
+
+// Gather-only loop executions in one persistent launch (every block resident: a cooperative
+// launch of 256-thread blocks). Each execution runs the work of the launches it replaces in
+// phases separated by grid barriers: the listed gathers; (Jacobi) the merge T |= N, which the
+// next list reads through the row bitmap of T; then, at once, block 0's tail (the loop
+// condition and, with choice, the next execution's product choice) and, on the other blocks'
+// warps, the next execution's list and the clear of the delta rows read (each clear unit also
+// zeroing its word of the read row bitmap, which the tail zeroes otherwise). The tail reads only what the gathers (and the
+// merge) wrote, and writes nothing the clear or the list reads: the counts of the parity just
+// read, the iteration number (each block took the parity before the execution), the choice.
+// The launch ends when the loop ends or (choice) the next execution has a tensor product; on
+// the way out block 0 sets the graph's handles as k_tail does with the same flags
+// (kTailNested: the nested loops'; kTailUnrolled: the loop's alone).
+template <int CPL>
+__global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4)
+    k_gather_loop(const QDesc *qd, uint32_t *list, uint32_t cap, uint32_t nch, cudaGraphConditionalHandle handle,
+                  const cudaGraphConditionalHandle *choice, int flags) {
+    const QDesc &q = *qd;
+    DevState *st = q.st;
+    __shared__ unsigned long long s_target;
+    __shared__ unsigned s_go;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->loop_launches, 1u);
+    grid_sync_start(st, s_target);
+    const bool jacobi = q.schedule == CFPQ_SCHED_JACOBI;
+    // the clear and the list: warps of blocks 1 .. (block 0 runs the tail), the list's
+    // (group, row word) items 32 to a warp, then the clear's (non-terminal, row word) units one
+    // to a warp
+    const uint32_t rw = (q.n + 31u) / 32u;
+    const uint32_t first = gridDim.x > 1 ? 1u : 0u;
+    const uint64_t warps = (uint64_t)(gridDim.x - first) * (blockDim.x >> 5);
+    const uint64_t my_warp = (uint64_t)(blockIdx.x - first) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint64_t scan_warps = ((uint64_t)q.n_groups * rw + 31u) / 32u;  // 32 items each
+    const uint64_t clear_warps = (uint64_t)q.n_nt * rw;                   // one unit each
+    for (;;) {
+        const uint32_t par = (uint32_t)(ld_u64(&st->iter) & 1ull);  // this execution's parity
+        gather_listed<CPL>(q, list, cap);
+        if (!grid_sync(st, s_target)) break;
+        if (jacobi) {
+            merge_new_rows(q);
+            if (!grid_sync(st, s_target)) break;
+        }
+        if (blockIdx.x == 0) {
+            const unsigned cont = tail_query(q, threadIdx.x, blockDim.x, false);
+            if (cont && choice) choose_products(q, choice, 1);
+            if (threadIdx.x == 0) {
+                const unsigned any = (cont && choice) ? ld_u32(&st->any_next) : 0u;
+                const unsigned go = cont && !any ? 1u : 0u;
+                st->loop_execs += 1ull;
+                if (!go) {
+                    cudaGraphSetConditional(handle, cont);
+                    if (flags & kTailNested) {
+                        cudaGraphSetConditional(choice[q.n_groups], any);
+                        cudaGraphSetConditional(choice[q.n_groups + 1], 0u);
+                    }
+                    st->skip = 1u;
+                }
+                st->loop_go = go;  // read by every block after the barrier
+            }
+        }
+        if (blockIdx.x >= first)
+            for (uint64_t w = my_warp; w < scan_warps + clear_warps; w += warps) {
+                if (w < scan_warps)
+                    scan_rows(q, w * 32u + (threadIdx.x & 31u), par ^ 1u, list, cap, nch);
+                else
+                    clear_delta_unit_warp(q, w - scan_warps, par);
+            }
+        if (!grid_sync(st, s_target)) break;
+        if (threadIdx.x == 0) s_go = ld_u32(&st->loop_go) && ld_u32(&st->error) != kErrDevice;
+        __syncthreads();
+        if (!s_go) break;
+    }
+    // a barrier that gave up (kErrDevice): the loop stops here, so that no conditional node
+    // runs this launch again
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ld_u32(&st->error) == kErrDevice) {
+        cudaGraphSetConditional(handle, 0u);
+        if (flags & kTailNested) {
+            cudaGraphSetConditional(choice[q.n_groups], 0u);
+            cudaGraphSetConditional(choice[q.n_groups + 1], 0u);
+        }
+        st->skip = 1u;
+        st->cont = 0u;
+        st->done = 1u;
+    }
+}
 
 __global__ void k_arm_deadline(DevState *st, unsigned long long dt_ns) { st->deadline_ns = globaltimer_ns() + dt_ns; }
 
@@ -976,6 +1093,39 @@ static int capture_gather_executions(cfpq_ctx *c, cudaStream_t s, cudaGraphCondi
 // occupancy counts are asked for), captured on s: occupancy, then per group an IF node on its
 // choice holding its transposes and tensor product (captured on aux2_stream), the gathers of
 // the other groups and the end of the execution.
+// The gather-only executions as one persistent launch of k_gather_loop (a cooperative kernel
+// node), which runs them until the loop ends or the next one takes a tensor product.
+static int capture_gather_loop(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h, int tail_flags) {
+    int cpl;
+    const uint32_t nch = gather_chunks(c->W, &cpl);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cfg.gridDim = dim3((uint32_t)c->loop_grid);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    const QDesc *qd = c->d_q;
+    uint32_t *list = c->d_list;
+    const uint32_t cap = c->list_cap;
+    const cudaGraphConditionalHandle *choice = c->auto_mixed ? c->d_choice : nullptr;
+    cudaError_t e;
+    switch (cpl) {
+        case 1: e = cudaLaunchKernelEx(&cfg, k_gather_loop<1>, qd, list, cap, nch, h, choice, tail_flags); break;
+        case 2: e = cudaLaunchKernelEx(&cfg, k_gather_loop<2>, qd, list, cap, nch, h, choice, tail_flags); break;
+        case 4: e = cudaLaunchKernelEx(&cfg, k_gather_loop<4>, qd, list, cap, nch, h, choice, tail_flags); break;
+        default: e = cudaLaunchKernelEx(&cfg, k_gather_loop<8>, qd, list, cap, nch, h, choice, tail_flags); break;
+    }
+    if (e != cudaSuccess) {
+        note_cuda_error(e, "gather loop", __FILE__, __LINE__);
+        return CFPQ_ERR_CUDA;
+    }
+    return CFPQ_OK;
+}
+
 static int capture_mixed_execution(cfpq_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
     int rc = enqueue_tensor_occupancy(c, s);
     for (int g = 0; g < c->n_groups && rc == CFPQ_OK; g++) {
@@ -1056,18 +1206,28 @@ static int build_graph(cfpq_ctx *c) {
     e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "capture", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
     int rc = CFPQ_OK;
+    // gather-only executions in one persistent launch where the device can hold its grid;
+    // the launch count then comes from the device (loop_launches, loop_execs)
+    const bool persistent = c->loop_grid > 0 && !c->block;
     if (nested) {
         cudaGraph_t inner = nullptr, mixed = nullptr;
         rc = add_cond(c->stream, c->h_choice[c->n_groups + 1], cudaGraphCondTypeWhile, &inner);
         if (rc == CFPQ_OK && (rc = begin_branch(c->aux_stream, inner)) == CFPQ_OK)
-            rc = end_branch(c->aux_stream, capture_gather_executions(c, c->aux_stream, h, kTailNested));
+            rc = end_branch(c->aux_stream, persistent ? capture_gather_loop(c, c->aux_stream, h, kTailNested)
+                                                      : capture_gather_executions(c, c->aux_stream, h, kTailNested));
         const int64_t per_execution = c->iter_launches;  // a gather-only execution's launches
+        if (persistent) c->iter_launches = 0;             // the mixed execution's launches, counted next
         if (rc == CFPQ_OK) rc = add_if(c->stream, c->h_choice[c->n_groups], &mixed);
         if (rc == CFPQ_OK && (rc = begin_branch(c->aux_stream, mixed)) == CFPQ_OK)
             rc = end_branch(c->aux_stream, capture_mixed_execution(c, c->aux_stream, h));
-        c->iter_launches = per_execution;
+        if (!persistent) c->iter_launches = per_execution;  // else the mixed execution's launches
     } else if (unrolled) {
-        rc = capture_gather_executions(c, c->stream, h, kTailUnrolled);
+        if (persistent) {
+            rc = capture_gather_loop(c, c->stream, h, kTailUnrolled);
+            c->iter_launches = 0;  // every execution runs in the persistent launch
+        } else {
+            rc = capture_gather_executions(c, c->stream, h, kTailUnrolled);
+        }
     } else {
         rc = enqueue_iteration(c, c->stream, h, 1);
     }
@@ -1223,7 +1383,8 @@ int apply_status(cfpq_ctx *c, const DevState &st) {
     c->stats.gather_products = (int64_t)st.gather_products;
     c->stats.dense_ops = 2.0 * (double)c->n_pad * (double)c->n_pad * (double)c->n_pad * (double)st.tensor_products;
     c->stats.n_pad = c->n_pad;
-    c->stats.kernel_launches = c->fixed_launches + (int64_t)st.iter * c->iter_launches;
+    c->stats.kernel_launches = c->fixed_launches + ((int64_t)st.iter - (int64_t)st.loop_execs) * c->iter_launches +
+                               (int64_t)st.loop_launches;
     c->stats.product_bytes = 4.0 * (double)st.prof_words;
     c->stats.useful_ops = 2.0 * (double)st.useful_macs;
     c->stats.lengths_splits = (double)st.len_splits;
@@ -1337,6 +1498,15 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
                            : cpl == 4 ? (const void *)k_gather_list<4> : (const void *)k_gather_list<8>;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
             c->gather_grid = std::max(1, sms) * per_sm;
+            // the persistent loop of gather-only executions: every block resident at once
+            int coop = 0, loop_per_sm = 0;
+            const void *lf = cpl == 1 ? (const void *)k_gather_loop<1> : cpl == 2 ? (const void *)k_gather_loop<2>
+                           : cpl == 4 ? (const void *)k_gather_loop<4> : (const void *)k_gather_loop<8>;
+            c->loop_grid = 0;
+            if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&loop_per_sm, lf, 256, 0) == cudaSuccess && loop_per_sm > 0)
+                c->loop_grid = std::max(1, sms) * loop_per_sm;
+            cudaGetLastError();
         }
     }
 

@@ -76,6 +76,10 @@ struct DevState {
     unsigned int any_next;              // AUTO: the next execution has a tensor product (or an occupancy probe)
     unsigned int tc_diag[6];            // first tensor product that gave up: wait site, CTA + 1, group,
                                         // execution, listed tiles, tiles claimed
+    unsigned int loop_launches;         // persistent loop launches of this solve
+    unsigned int loop_go;               // persistent loop: the next execution runs in this launch
+    unsigned long long loop_execs;      // loop executions those launches ran
+    unsigned long long gbar;            // grid barriers of the persistent loop: block arrivals this solve
 };
 
 struct Rule {
@@ -134,6 +138,50 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// Grid barrier of a persistent launch whose blocks are all resident (a cooperative launch):
+// every thread of every block calls it. st->gbar counts the blocks' arrivals over the solve;
+// a launch's barriers complete at base + k gridDim.x (k = 1, 2, ...), and target (shared
+// memory, set by grid_sync_start) is the block's next one. The writes before the barrier are
+// visible to every block after it: each block's writes are ordered before its arrival (block
+// barrier, then a device-scope fence), and its loads after the release (a device-scope fence
+// after the count reached the target, then a block barrier). A block that waits longer than
+// kGridWaitNs, or sees kErrDevice, records kErrDevice and returns false. The limit is far
+// above any one loop phase (one execution's gathers at most); it bounds a wait on blocks that
+// never arrive.
+constexpr unsigned long long kGridWaitNs = 60ull * 1000 * 1000 * 1000;
+__device__ inline void grid_sync_start(DevState *st, unsigned long long &target) {
+    if (threadIdx.x == 0) {
+        // fewer than gridDim.x arrivals can precede this read: the first barrier needs every block
+        const unsigned long long c = ld_u64(&st->gbar);
+        target = c - c % gridDim.x + gridDim.x;
+    }
+    __syncthreads();
+}
+__device__ inline bool grid_sync(DevState *st, unsigned long long &target) {
+    __shared__ unsigned s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned ok = 1u;
+        const unsigned long long t = target;
+        __threadfence();
+        atomicAdd(&st->gbar, 1ull);
+        const unsigned long long t0 = globaltimer_ns();
+        for (unsigned spin = 0; ld_u64(&st->gbar) < t; spin++) {
+            if ((spin & 31u) == 31u &&
+                (ld_u32(&st->error) == kErrDevice || globaltimer_ns() - t0 > kGridWaitNs)) {
+                ok = 0u;
+                atomicExch(&st->error, kErrDevice);
+                break;
+            }
+        }
+        __threadfence();
+        target = t + gridDim.x;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0u;
 }
 
 // ------------------------------------------------------------------------------------

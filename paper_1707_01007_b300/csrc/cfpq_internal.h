@@ -49,6 +49,7 @@ struct cfpq_ctx {
     uint32_t *d_lens = nullptr;       // extraction: lengths of the emitted triples
     size_t lens_cap = 0;
     int gather_grid = 0;              // persistent grid of the listed gathers
+    int loop_grid = 0;                // cooperative grid of the persistent gather loop (0: not used)
     int sms = 148;                    // multiprocessors of the device (grid-stride kernels use a few blocks per SM)
     // device memory
     uint32_t *d_T = nullptr, *d_TT = nullptr, *d_X0 = nullptr, *d_X1 = nullptr;

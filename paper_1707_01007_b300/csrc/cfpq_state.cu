@@ -201,6 +201,8 @@ extern "C" int cfpq_resume(cfpq_ctx *c, void *stream, int64_t more_executions) {
     CK(cudaMemcpyAsync(&st, c->d_state, sizeof(st), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     st.error = st.done = st.cont = st.changed = 0u;
+    st.loop_go = 0u;
+    st.gbar = 0ull;
     st.small_run = st.to_worklist = 0u;
     st.skip = st.any_next = 0u;  // the graph loop's flags (the first execution of a loop iteration runs regardless)
     // 0: Theorem 3's bound on changing executions, |V|^2 |N|, plus the final one
