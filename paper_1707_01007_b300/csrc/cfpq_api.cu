@@ -43,10 +43,15 @@ __device__ __forceinline__ void scan_rows(const QDesc &q, uint64_t item, uint32_
         g = (int)(item / rw);
         wq = (uint32_t)(item % rw);
         const uint32_t *DR = par ? q.R1 : q.R0;
+        // the three loads of a production do not depend on one another, nor on the other
+        // productions': issued together, a few productions cost one round trip
+#pragma unroll 4
         for (int r = q.gstart[g]; r < q.gstart[g + 1]; r++) {
             const int B = q.rules[r].b, C = q.rules[r].c;
-            cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
-            if (__ldcg(&st->dcount[par][C]) != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
+            const uint32_t d = __ldcg(DR + (uint64_t)B * q.W + wq);
+            const unsigned long long dc = __ldcg(&st->dcount[par][C]);
+            const uint32_t t = __ldcg(q.Trow + (uint64_t)B * q.W + wq);
+            cand |= d | (dc != 0ull ? t : 0u);
         }
         cand &= rows_in_word(q.n, wq) & rows_of_block(q, wq);
     }
@@ -325,12 +330,43 @@ constexpr float kTransposeBytesPerNs = 3000.0f;
 
 // Every thread of one block (at least max(n_nt, n_groups) threads) calls this: thread g
 // costs group g from the device-side counts, thread a assigns the refresh of TT[A].
+// Live K steps of a production with tile skipping: the dot product of its operands' per-slice
+// tile counts, one warp per production (the first kLiveRules) and the lanes over the slices.
+// The counts are integers and the sums stay below 2^24, so the float sums are exact in any order.
+constexpr int kLiveRules = 256;
+__device__ __forceinline__ float live_steps_of(const QDesc &q, int B, int C, int lane) {
+    const uint32_t *mB = q.occCA + (uint64_t)B * q.KS, *nC = q.occCB + (uint64_t)C * q.KS;
+    float live = 0.0f;
+    for (uint32_t k = (uint32_t)lane; k < q.KS; k += 32u) live += (float)__ldcg(mB + k) * (float)__ldcg(nC + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) live += __shfl_xor_sync(0xffffffffu, live, o);
+    return live;
+}
+
 __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle *handles, int use_handles) {
     __shared__ unsigned s_use[kMaxNT], s_any, s_probe;
+    __shared__ float s_live[kLiveRules];
+    // the per-non-terminal counts and flags the costs read, loaded at once (nothing changes
+    // them while the choice runs)
+    __shared__ float s_dc[kMaxNT], s_tc[kMaxNT];
+    __shared__ unsigned s_dirty[kMaxNT], s_known[kMaxNT];
     DevState *st = q.st;
     const int tid = threadIdx.x;
-    const uint32_t p = (uint32_t)(st->iter & 1ull);
+    const uint32_t p = (uint32_t)(ld_u64(&st->iter) & 1ull);
     if (tid == 0) s_any = s_probe = 0u;
+    if (tid < q.n_nt) {
+        s_dc[tid] = (float)ld_u64(&st->dcount[p][tid]);
+        s_tc[tid] = (float)ld_u64(&st->tcount[tid]);
+        s_dirty[tid] = ld_u32(&st->dirty[tid]);
+        s_known[tid] = q.occKnown ? ld_u32(&q.occKnown[tid]) : 0u;
+    }
+    __syncthreads();
+    if (q.occA)
+        for (int r = tid >> 5; r < q.n_rules && r < kLiveRules; r += (int)(blockDim.x >> 5)) {
+            const int B = q.rules[r].b, C = q.rules[r].c;
+            const float live = (s_known[B] && s_known[C]) ? live_steps_of(q, B, C, tid & 31) : 0.0f;
+            if ((tid & 31) == 0) s_live[r] = live;
+        }
     __syncthreads();
     if (tid < q.n_groups) {
         const int g = tid;
@@ -347,14 +383,18 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
         bool unknown = false;
         for (int r = r0; r < r1; r++) {
             const int B = q.rules[r].b, C = q.rules[r].c;
-            const float dB = (float)st->dcount[p][B], dC = (float)st->dcount[p][C], tB = (float)st->tcount[B];
+            const float dB = s_dc[B], dC = s_dc[C], tB = s_tc[B];
             words += dB * W;
             if (dC > 0.0f) words += fminf(n, tB) * 2.0f * W + tB * fminf(1.0f, dC / n) * W;
-            const float extra = st->dirty[C] ? transpose_ns : 0.0f;
-            if (q.occA && q.occKnown[B] && q.occKnown[C]) {
+            const float extra = s_dirty[C] ? transpose_ns : 0.0f;
+            if (q.occA && s_known[B] && s_known[C]) {
                 float live = 0.0f;
-                const uint32_t *mB = q.occCA + (uint64_t)B * q.KS, *nC = q.occCB + (uint64_t)C * q.KS;
-                for (uint32_t k = 0; k < q.KS; k++) live += (float)__ldcg(mB + k) * (float)__ldcg(nC + k);
+                if (r < kLiveRules) {
+                    live = s_live[r];
+                } else {  // beyond the warps' productions: this thread alone
+                    const uint32_t *mB = q.occCA + (uint64_t)B * q.KS, *nC = q.occCB + (uint64_t)C * q.KS;
+                    for (uint32_t k = 0; k < q.KS; k++) live += (float)__ldcg(mB + k) * (float)__ldcg(nC + k);
+                }
                 tensor_ns += live * kStepOps / skip_ops_per_ns(kind) + extra;
             } else {
                 tensor_ns += dense_rule_ns + extra;
@@ -395,7 +435,7 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
                         owner = (unsigned)g + 1u;
                         break;
                     }
-        const unsigned now = (owner != 0u && st->dirty[a]) ? owner : 0u;
+        const unsigned now = (owner != 0u && s_dirty[a]) ? owner : 0u;
         st->tt_now[a] = now;
         if (now) st->dirty[a] = 0u;
     }
@@ -486,13 +526,16 @@ __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4)
         }
         if (blockIdx.x == 0) {
             const unsigned cont = tail_query(q, threadIdx.x, blockDim.x, false);
-            if (cont && choice) choose_products(q, choice, 1);
+            // the per-group handles matter only to a mixed execution: set on the way out
+            if (cont && choice) choose_products(q, choice, 0);
             if (threadIdx.x == 0) {
                 const unsigned any = (cont && choice) ? ld_u32(&st->any_next) : 0u;
                 const unsigned go = cont && !any ? 1u : 0u;
                 st->loop_execs += 1ull;
                 if (!go) {
                     cudaGraphSetConditional(handle, cont);
+                    if (any)
+                        for (int g = 0; g < q.n_groups; g++) cudaGraphSetConditional(choice[g], st->use_tensor[g]);
                     if (flags & kTailNested) {
                         cudaGraphSetConditional(choice[q.n_groups], any);
                         cudaGraphSetConditional(choice[q.n_groups + 1], 0u);

@@ -467,6 +467,17 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
     DevState *st = q.st;
     const unsigned long long it = ld_u64(&st->iter);
     const uint32_t old = (uint32_t)(it & 1ull);
+    // thread 0's inputs to the decision, loaded together (the products that set changed or
+    // error have finished; the others change only here)
+    unsigned changed0 = 0u, error0 = 0u, small0 = 0u;
+    unsigned long long max_iter0 = 0ull, deadline0 = 0ull;
+    if (tid == 0) {
+        changed0 = ld_u32(&st->changed);
+        error0 = ld_u32(&st->error);
+        small0 = ld_u32(&st->small_run);
+        max_iter0 = ld_u64(&st->max_iter);
+        deadline0 = ld_u64(&st->deadline_ns);
+    }
     if (zero_read_bitmap) {
         uint32_t *DR = old ? q.R1 : q.R0;
         for (uint64_t w = tid; w < (uint64_t)q.n_nt * q.W; w += nthreads) DR[w] = 0u;
@@ -498,23 +509,23 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
     }
     if (tid == 0) {
         st->list_len[old] = 0u;  // consumed; the next list of this parity is built one execution later
-        const unsigned changed = ld_u32(&st->changed);
         st->changed = 0u;
         st->iter = it + 1;
-        unsigned cont = changed ? 1u : 0u;
-        if (ld_u32(&st->error) == kErrDevice) cont = 0;
+        unsigned cont = changed0 ? 1u : 0u;
+        if (error0 == kErrDevice) cont = 0;
         if (cont && q.allow_switch) {
-            st->small_run = s_added <= kSmallDelta ? st->small_run + 1u : 0u;
-            if (st->small_run >= kSwitchAfter) {
+            const unsigned run = s_added <= kSmallDelta ? small0 + 1u : 0u;
+            st->small_run = run;
+            if (run >= kSwitchAfter) {
                 st->to_worklist = 1u;
                 cont = 0;
             }
         }
-        if (cont && it + 1 >= ld_u64(&st->max_iter)) {
+        if (cont && it + 1 >= max_iter0) {
             st->error = kErrIterLimit;
             cont = 0;
         }
-        const unsigned long long dl = ld_u64(&st->deadline_ns);
+        const unsigned long long dl = deadline0;
         if (cont && dl && globaltimer_ns() > dl) {
             st->error = kErrTimeout;
             cont = 0;
