@@ -839,6 +839,8 @@ def serve_measure(eng, count=2000, seeds=SERVE_ARRIVAL_SEEDS):
             srv.close()
             f_sum = serve.run_serial(queries, arr)
             runs.append({"seed": sd, "server": s_sum, "serial_fifo": f_sum, "server_launches": stats["launches"],
+                         "server_steps": stats["steps"],
+                         "server_host_ms": {k: stats[k] for k in ("admit_ms", "launch_ms", "retire_ms")},
                          "peak_hbm_bytes": stats["peak_used_bytes"], "budget_bytes": stats["budget_bytes"]})
 
         def spread(who, key):

@@ -565,6 +565,9 @@ typedef struct {
 typedef struct {
     int64_t queued, resident, completed, failed, launches, steps;
     uint64_t budget_bytes, used_bytes, peak_used_bytes;
+    double admit_ms;   /* host wall time of the steps' admissions (context creation, uploads) */
+    double launch_ms;  /* host wall time of the grouped launches, from issue to their results */
+    double retire_ms;  /* host wall time of the retirements (status, every R_A to the host, free) */
 } cfpq_server_stats;
 
 /* Fills *opt with the defaults. Errors: INVALID. */

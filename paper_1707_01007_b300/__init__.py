@@ -127,7 +127,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("launches", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("budget_bytes", ctypes.c_uint64), ("used_bytes", ctypes.c_uint64),
-                ("peak_used_bytes", ctypes.c_uint64)]
+                ("peak_used_bytes", ctypes.c_uint64), ("admit_ms", ctypes.c_double), ("launch_ms", ctypes.c_double),
+                ("retire_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

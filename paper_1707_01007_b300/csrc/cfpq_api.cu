@@ -1250,8 +1250,11 @@ static int build_graph(cfpq_ctx *c) {
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "capture", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
     int rc = CFPQ_OK;
     // gather-only executions in one persistent launch where the device can hold its grid;
-    // the launch count then comes from the device (loop_launches, loop_execs)
-    const bool persistent = c->loop_grid > 0 && !c->block;
+    // the launch count then comes from the device (loop_launches, loop_execs). Not for a
+    // server's contexts: a large query's loop runs beside the grouped launches of the small
+    // ones, and a persistent launch would hold every SM until that query converged, where the
+    // separate launches interleave with them
+    const bool persistent = c->loop_grid > 0 && !c->block && !c->pooled;
     if (nested) {
         cudaGraph_t inner = nullptr, mixed = nullptr;
         rc = add_cond(c->stream, c->h_choice[c->n_groups + 1], cudaGraphCondTypeWhile, &inner);
@@ -1541,14 +1544,18 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
                            : cpl == 4 ? (const void *)k_gather_list<4> : (const void *)k_gather_list<8>;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
             c->gather_grid = std::max(1, sms) * per_sm;
-            // the persistent loop of gather-only executions: every block resident at once
+            // the persistent loop of gather-only executions: every block resident at once. Small
+            // problems take fewer blocks (a barrier then gathers fewer arrivals): one per SM up to
+            // n = 4096, two up to 8192, else all that fit (measured on hierarchy queries, n = 512 ..
+            // 16384: one per SM is 7 % faster than three at n <= 2048, three 27 % faster than one
+            // at 16384)
             int coop = 0, loop_per_sm = 0;
             const void *lf = cpl == 1 ? (const void *)k_gather_loop<1> : cpl == 2 ? (const void *)k_gather_loop<2>
                            : cpl == 4 ? (const void *)k_gather_loop<4> : (const void *)k_gather_loop<8>;
             c->loop_grid = 0;
             if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&loop_per_sm, lf, 256, 0) == cudaSuccess && loop_per_sm > 0)
-                c->loop_grid = std::max(1, sms) * loop_per_sm;
+                c->loop_grid = std::max(1, sms) * std::min(loop_per_sm, n <= 4096u ? 1 : n <= 8192u ? 2 : loop_per_sm);
             cudaGetLastError();
         }
     }
@@ -2062,7 +2069,10 @@ namespace cfpq {
 
 // Counts every relation and returns the first triple of each non-terminal (n_nt + 1
 // entries, the last = total). One synchronisation.
-int count_all(cfpq_ctx *c, cudaStream_t s, std::vector<unsigned long long> &nt_off) {
+// The counts, the offsets of every (non-terminal, row) cell and the per-non-terminal offsets
+// (n_nt + 1 of them, copied to host memory h_nt_off when the stream reaches the copy; page-
+// locked memory keeps the copy asynchronous), without waiting.
+int count_all_enqueue(cfpq_ctx *c, cudaStream_t s, unsigned long long *h_nt_off) {
     const uint64_t cells = (uint64_t)c->n_nt * c->n_pad;
     const int nb = (int)((cells + kScanSeg - 1) / kScanSeg);
     k_count_all<<<row_warp_blocks(cells), 256, 0, s>>>(c->d_q, c->d_counts);
@@ -2071,8 +2081,14 @@ int count_all(cfpq_ctx *c, cudaStream_t s, std::vector<unsigned long long> &nt_o
     k_scan_apply<<<nb, 1024, 0, s>>>(c->d_counts, cells, c->d_block_sums, c->d_offsets);
     k_nt_offsets<<<1, 96, 0, s>>>(c->d_q, c->d_offsets, c->d_total, c->d_nt_off);
     CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h_nt_off, c->d_nt_off, (c->n_nt + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    return CFPQ_OK;
+}
+
+int count_all(cfpq_ctx *c, cudaStream_t s, std::vector<unsigned long long> &nt_off) {
     nt_off.assign(c->n_nt + 1, 0);
-    CK(cudaMemcpyAsync(nt_off.data(), c->d_nt_off, (c->n_nt + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    const int rc = count_all_enqueue(c, s, nt_off.data());
+    if (rc != CFPQ_OK) return rc;
     CK(cudaStreamSynchronize(s));
     return CFPQ_OK;
 }

@@ -123,6 +123,8 @@ cudaMemPool_t library_pool(int dev);
 cudaError_t ctx_alloc(cfpq_ctx *c, void **p, size_t bytes, cudaStream_t s);
 void ctx_free(cfpq_ctx *c, void *p, cudaStream_t s);
 int ensure_triples(cfpq_ctx *c, size_t total, cudaStream_t s);
+int count_all_enqueue(cfpq_ctx *c, cudaStream_t s, unsigned long long *h_nt_off);
+int emit_all(cfpq_ctx *c, cfpq_triple *out, cudaStream_t s);
 int extract_all_host(cfpq_ctx *c, std::vector<std::vector<cfpq_triple>> &out);
 // Bytes of device memory a context for this query holds (path GATHER unless tensor).
 size_t query_footprint(uint32_t n, int n_nt, size_t n_edges, int n_rules, bool tensor);

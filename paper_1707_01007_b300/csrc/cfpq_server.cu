@@ -21,6 +21,7 @@
 // Results are identical to solving each query alone: each query runs Algorithm 1 to its
 // own least fixpoint; other queries only share the launch.
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -77,8 +78,32 @@ struct cfpq_server {
     BatchBuffers bufs{};
     int bufs_cap = 0;
     int64_t launches = 0, steps = 0, completed = 0, failed = 0;
+    double admit_ms = 0.0, launch_ms = 0.0, retire_ms = 0.0;  // host wall time per phase of the steps
     std::vector<int64_t> just_finished;  // tickets finished since the last cfpq_server_completed
+    // page-locked staging of a step's retirements: loop states, per-non-terminal offsets, triples
+    DevState *h_state = nullptr;
+    unsigned long long *h_off = nullptr;
+    cfpq_triple *h_trip = nullptr;
+    size_t state_cap = 0, off_cap = 0, trip_cap = 0;
 };
+
+// Page-locked host array of at least `need` elements (grown by half again; the old one freed).
+template <class T>
+static bool host_reserve(T *&p, size_t &cap, size_t need) {
+    if (cap >= need) return true;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    const size_t n = std::max<size_t>(need, cap + cap / 2);
+    cap = 0;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&p), std::max<size_t>(n, 1) * sizeof(T), cudaHostAllocDefault) !=
+        cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    cap = n;
+    return true;
+}
 
 static int server_bufs(cfpq_server *s, int k) {
     if (k <= s->bufs_cap) return CFPQ_OK;
@@ -153,25 +178,70 @@ extern "C" int cfpq_server_submit(cfpq_server *s, const cfpq_grammar_cnf *g, uin
     return CFPQ_OK;
 }
 
-// Copies every R_A of a stopped query to the host and returns its device memory.
-static int retire(cfpq_server *s, Served *q) {
-    cfpq_ctx *c = q->ctx;
-    cudaStream_t st = q->solo ? s->solo_stream : s->stream;
-    int rc = read_status(c, st);
-    q->status = rc;
-    c->last_stream = st;
-    q->iterations = c->stats.iterations;
-    c->solved = true;
-    if (rc == CFPQ_ERR_CUDA) return rc;
-    if ((rc = extract_all_host(c, q->results)) != CFPQ_OK) return rc;
-    ctx_destroy(c);
-    q->ctx = nullptr;
-    s->used -= q->footprint;
-    q->state = (q->status == CFPQ_OK) ? CFPQ_QUERY_DONE : CFPQ_QUERY_FAILED;
-    s->state_of[q->ticket] = q->state;
-    s->finished[q->ticket] = q;
-    s->just_finished.push_back(q->ticket);
-    s->completed++;
+// Copies every R_A of the stopped queries qs (all on stream st) to the host and returns their
+// device memory. Two waits for the whole set: one for every query's loop state and relation
+// sizes (the counting kernels of all queries enqueued first), one for the triples of all of
+// them, emitted and copied into page-locked staging back to back. On an error nothing has
+// been freed yet (the caller keeps the queries).
+static int retire_batch(cfpq_server *s, const std::vector<Served *> &qs, cudaStream_t st) {
+    const size_t k = qs.size();
+    if (k == 0) return CFPQ_OK;
+    size_t n_off = 0;
+    for (Served *q : qs) n_off += (size_t)q->ctx->n_nt + 1;
+    if (!host_reserve(s->h_state, s->state_cap, k) || !host_reserve(s->h_off, s->off_cap, n_off)) return CFPQ_ERR_NOMEM;
+    std::vector<size_t> obase(k), tbase(k);
+    size_t o = 0;
+    for (size_t j = 0; j < k; j++) {
+        cfpq_ctx *c = qs[j]->ctx;
+        c->last_stream = st;
+        if (cudaMemcpyAsync(&s->h_state[j], c->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return CFPQ_ERR_CUDA;
+        obase[j] = o;
+        const int rc = count_all_enqueue(c, st, s->h_off + o);
+        if (rc != CFPQ_OK) return rc;
+        o += (size_t)c->n_nt + 1;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CFPQ_ERR_CUDA;
+    size_t total = 0;
+    for (size_t j = 0; j < k; j++) {
+        tbase[j] = total;
+        total += (size_t)s->h_off[obase[j] + (size_t)qs[j]->ctx->n_nt];
+    }
+    if (!host_reserve(s->h_trip, s->trip_cap, total)) return CFPQ_ERR_NOMEM;
+    for (size_t j = 0; j < k; j++) {
+        Served *q = qs[j];
+        cfpq_ctx *c = q->ctx;
+        const int rc = apply_status(c, s->h_state[j]);
+        q->status = rc;
+        q->iterations = c->stats.iterations;
+        c->solved = true;
+        if (rc == CFPQ_ERR_CUDA) return rc;
+        const size_t tj = (size_t)s->h_off[obase[j] + (size_t)c->n_nt];
+        if (tj == 0) continue;
+        int r2 = ensure_triples(c, tj, st);
+        if (r2 == CFPQ_OK) r2 = emit_all(c, c->d_triples, st);
+        if (r2 != CFPQ_OK) return r2;
+        if (cudaMemcpyAsync(s->h_trip + tbase[j], c->d_triples, tj * sizeof(cfpq_triple), cudaMemcpyDeviceToHost,
+                            st) != cudaSuccess)
+            return CFPQ_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CFPQ_ERR_CUDA;
+    for (size_t j = 0; j < k; j++) {
+        Served *q = qs[j];
+        cfpq_ctx *c = q->ctx;
+        const unsigned long long *off = s->h_off + obase[j];
+        const cfpq_triple *t = s->h_trip + tbase[j];
+        q->results.assign(c->n_nt, {});
+        for (int a = 0; a < c->n_nt; a++) q->results[a].assign(t + off[a], t + off[a + 1]);
+        ctx_destroy(c);
+        q->ctx = nullptr;
+        s->used -= q->footprint;
+        q->state = (q->status == CFPQ_OK) ? CFPQ_QUERY_DONE : CFPQ_QUERY_FAILED;
+        s->state_of[q->ticket] = q->state;
+        s->finished[q->ticket] = q;
+        s->just_finished.push_back(q->ticket);
+        s->completed++;
+    }
     return CFPQ_OK;
 }
 
@@ -179,6 +249,9 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
     if (!s) return CFPQ_ERR_INVALID;
     int done_now = 0;
     s->steps++;
+    using clk = std::chrono::steady_clock;
+    auto ms_since = [](clk::time_point t) { return std::chrono::duration<double, std::milli>(clk::now() - t).count(); };
+    clk::time_point t_phase = clk::now();
     // 1) admission by free HBM, in arrival order
     while (!s->waiting.empty() && (int)(s->resident.size() + s->solo.size()) < s->max_resident) {
         Pending &p = s->waiting.front();
@@ -251,7 +324,7 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
     }
     // large queries whose single-query loop has finished
     auto retire_solo = [&]() -> int {
-        std::vector<Served *> still;
+        std::vector<Served *> still, done;
         for (Served *q : s->solo) {
             const cudaError_t e = cudaEventQuery(q->ctx->ev1);
             if (e == cudaErrorNotReady) {
@@ -259,20 +332,28 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
                 continue;
             }
             if (e != cudaSuccess) return CFPQ_ERR_CUDA;
-            const int rc = retire(s, q);
-            if (rc != CFPQ_OK) return rc;
-            done_now++;
+            done.push_back(q);
         }
         s->solo.swap(still);
+        const int rc = retire_batch(s, done, s->solo_stream);
+        if (rc != CFPQ_OK) {  // nothing was freed: the queries stay where they were
+            s->solo.insert(s->solo.end(), done.begin(), done.end());
+            return rc;
+        }
+        done_now += (int)done.size();
         return CFPQ_OK;
     };
+    s->admit_ms += ms_since(t_phase);
+    t_phase = clk::now();
     int src = retire_solo();
+    s->retire_ms += ms_since(t_phase);
     if (src != CFPQ_OK) return src;
     if (s->resident.empty()) {
         if (n_completed) *n_completed = done_now;
         return CFPQ_OK;
     }
     // 2) one grouped launch over every resident query
+    t_phase = clk::now();
     const int k = (int)s->resident.size();
     int rc = server_bufs(s, k);
     if (rc != CFPQ_OK) return rc;
@@ -302,20 +383,24 @@ extern "C" int cfpq_server_step(cfpq_server *s, int32_t *n_completed) {
         return CFPQ_ERR_CUDA;
     if (err) return CFPQ_ERR_TIMEOUT;
     batch_record_profile(&s->bufs, s->stream);
+    s->launch_ms += ms_since(t_phase);
+    t_phase = clk::now();
     // 3) retire the queries that stopped
-    std::vector<Served *> keep;
+    std::vector<Served *> keep, stopped;
     for (int j = 0; j < k; j++) {
         Served *q = s->resident[j];
         q->init = 0;
-        if (active[j]) {
-            keep.push_back(q);
-            continue;
-        }
-        if ((rc = retire(s, q)) != CFPQ_OK) return rc;
-        done_now++;
+        (active[j] ? keep : stopped).push_back(q);
     }
     s->resident.swap(keep);
-    if ((rc = retire_solo()) != CFPQ_OK) return rc;
+    if ((rc = retire_batch(s, stopped, s->stream)) != CFPQ_OK) {  // nothing was freed
+        s->resident.insert(s->resident.end(), stopped.begin(), stopped.end());
+        return rc;
+    }
+    done_now += (int)stopped.size();
+    rc = retire_solo();
+    s->retire_ms += ms_since(t_phase);
+    if (rc != CFPQ_OK) return rc;
     if (n_completed) *n_completed = done_now;
     return CFPQ_OK;
 }
@@ -383,6 +468,9 @@ extern "C" int cfpq_server_stats_get(const cfpq_server *s, cfpq_server_stats *ou
     out->budget_bytes = s->budget;
     out->used_bytes = s->used;
     out->peak_used_bytes = s->peak_used;
+    out->admit_ms = s->admit_ms;
+    out->launch_ms = s->launch_ms;
+    out->retire_ms = s->retire_ms;
     return CFPQ_OK;
 }
 
@@ -405,5 +493,8 @@ extern "C" void cfpq_server_destroy(cfpq_server *s) {
         cudaStreamDestroy(s->stream);
     }
     if (s->solo_stream) cudaStreamDestroy(s->solo_stream);
+    if (s->h_state) cudaFreeHost(s->h_state);
+    if (s->h_off) cudaFreeHost(s->h_off);
+    if (s->h_trip) cudaFreeHost(s->h_trip);
     delete s;
 }
