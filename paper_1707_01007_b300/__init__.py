@@ -277,11 +277,18 @@ class Grammar:
             self._h = None
 
 
+_EDGE_DTYPE = np.dtype([("src", "<u4"), ("label", "<i4"), ("dst", "<u4")])
+
+
 def _edges_struct(edges):
-    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int64).reshape(-1, 3))
-    rec = np.empty(e.shape[0], dtype=[("src", "<u4"), ("label", "<i4"), ("dst", "<u4")])
-    rec["src"], rec["label"], rec["dst"] = e[:, 0], e[:, 1], e[:, 2]
-    return rec
+    """The edges as cfpq_edge records, in page-locked memory where CUDA is up (the library's
+    upload from it is a direct copy; see _host_words)."""
+    e = np.asarray(edges).reshape(-1, 3)
+    if e.size and int(e.max()) >= 1 << 32:  # would wrap into the 32-bit fields (the library checks the rest)
+        raise CfpqError(ERR_INVALID, "edge field out of range")
+    words = _host_words(e.shape[0], 3)
+    np.copyto(words, e, casting="unsafe")  # one pass; a negative label keeps its int32 bits
+    return words.view(_EDGE_DTYPE).reshape(-1)
 
 
 def _stream_handle(stream):
