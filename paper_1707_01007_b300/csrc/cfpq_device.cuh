@@ -148,9 +148,10 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // barrier, then a device-scope fence), and its loads after the release (a device-scope fence
 // after the count reached the target, then a block barrier). A block that waits longer than
 // kGridWaitNs, or sees kErrDevice, records kErrDevice and returns false. The limit is far
-// above any one loop phase (one execution's gathers at most); it bounds a wait on blocks that
-// never arrive.
-constexpr unsigned long long kGridWaitNs = 60ull * 1000 * 1000 * 1000;
+// above any one loop phase (one execution's gathers at most: a phase this long means a
+// closure that no timeout of the caller would let finish); it bounds a wait on blocks that
+// never arrive, which the cooperative launch rules out.
+constexpr unsigned long long kGridWaitNs = 300ull * 1000 * 1000 * 1000;
 __device__ inline void grid_sync_start(DevState *st, unsigned long long &target) {
     if (threadIdx.x == 0) {
         // fewer than gridDim.x arrivals can precede this read: the first barrier needs every block
