@@ -73,6 +73,20 @@ __device__ __forceinline__ int find_slot(const unsigned long long *off, int n, u
     return lo;
 }
 
+// The same search in a block's shared copy of the offsets.
+__device__ __forceinline__ int find_slot_shared(const unsigned long long *off, int n, unsigned long long x) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Rounds with at most this many queries take part read the round's tables (item offsets,
+// row offsets, query ids) from a shared-memory copy in every block.
+constexpr int kSlotCache = 1024;
+
 // Rebuilds the per-round tables over the queries that take part in round `round`: not
 // converged and still within their own round budget (one block of <= 1024 threads).
 __device__ void build_tables(BatchCtl *ctl, const BatchQuery *bq, int round) {
@@ -235,27 +249,53 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
     };
     mark(0, 0);
 
+    __shared__ unsigned long long s_poff[kSlotCache + 1], s_roff[kSlotCache + 1];
+    __shared__ int s_act[kSlotCache];
     for (int round = 0; round < ctl->max_rounds; round++) {
         const int na = min((int)ld_u32(&ctl->n_active), k);
         if (na <= 0) break;
         if (gtid == 0) ctl->rounds++;
+        // the round's tables (built by block 0 before the last barrier), once per block: each
+        // lane's search for its item's query then costs no global round trips
+        const bool cached = na <= kSlotCache;
+        if (cached) {
+            for (int i = threadIdx.x; i <= na; i += blockDim.x) {
+                s_poff[i] = __ldcg(ctl->prod_off + i);
+                s_roff[i] = __ldcg(ctl->row_off + i);
+                if (i < na) s_act[i] = __ldcg(ctl->act + i);
+            }
+            __syncthreads();
+        }
+        // query and offset within it of item `it` of a table (prod or row offsets)
+        auto slot_of = [&](bool rows_table, unsigned long long it, int &jj, unsigned long long &loc) {
+            if (cached) {
+                const unsigned long long *off = rows_table ? s_roff : s_poff;
+                const int sl = find_slot_shared(off, na, it);
+                jj = s_act[sl];
+                loc = it - off[sl];
+            } else {
+                const unsigned long long *off = rows_table ? ctl->row_off : ctl->prod_off;
+                const int sl = find_slot(off, na, it);
+                jj = __ldcg(ctl->act + sl);
+                loc = it - __ldcg(off + sl);
+            }
+        };
         // 3a) candidate rows, one lane per item (query, group, row word): the rows of the
         //     word that have a left delta row or (where the right operand has a delta) a
         //     non-empty left row become one product item per column chunk; the warp reserves
         //     its lanes' items with one atomic and each lane writes its own
-        const unsigned long long np = __ldcg(ctl->prod_off + na);
+        const unsigned long long np = cached ? s_poff[na] : __ldcg(ctl->prod_off + na);
         for (unsigned long long it0 = gwarp * 32ull; it0 < np; it0 += gwarps * 32ull) {
             const unsigned long long it = it0 + (unsigned)lane;
             uint32_t cand = 0, wq = 0, nch = 0;
             int j = 0, g = 0;
             if (it < np) {
-                const int s = find_slot(ctl->prod_off, na, it);
-                j = __ldcg(ctl->act + s);
+                unsigned long long loc = 0;
+                slot_of(false, it, j, loc);
                 if (j >= 0 && j < k) {
                     const BatchQuery &b = bq[j];
                     const QDesc &q = b.q;
                     const uint32_t rw = (q.n + 31u) / 32u;
-                    const unsigned long long loc = it - __ldcg(ctl->prod_off + s);
                     const unsigned long long g64 = loc / rw;
                     wq = (uint32_t)(loc % rw);
                     if (g64 < (unsigned long long)q.n_groups) {
@@ -263,10 +303,14 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
                         nch = b.nch;
                         const uint32_t parity = (uint32_t)(ld_u64(&q.st->iter) & 1ull);
                         const uint32_t *DR = parity ? q.R1 : q.R0;
+                        // a production's three loads are independent: issued together
+#pragma unroll 4
                         for (int ri = q.gstart[g]; ri < q.gstart[g + 1]; ri++) {
                             const int B = q.rules[ri].b, C = q.rules[ri].c;
-                            cand |= __ldcg(DR + (uint64_t)B * q.W + wq);
-                            if (ld_u64(&q.st->dcount[parity][C]) != 0) cand |= __ldcg(q.Trow + (uint64_t)B * q.W + wq);
+                            const uint32_t d = __ldcg(DR + (uint64_t)B * q.W + wq);
+                            const unsigned long long dc = ld_u64(&q.st->dcount[parity][C]);
+                            const uint32_t t = __ldcg(q.Trow + (uint64_t)B * q.W + wq);
+                            cand |= d | (dc != 0ull ? t : 0u);
                         }
                         cand &= rows_in_word(q.n, wq);
                     }
@@ -296,44 +340,21 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
             }
         }
         // the plane this round's products write (N) is the one the previous round read (its
-        // D): clear the rows its bitmap flags, then the bitmap. One lane per (query,
-        // non-terminal, row word) finds the rows; the warp clears them together.
-        const unsigned long long nr = __ldcg(ctl->row_off + na);
-        for (unsigned long long it0 = gwarp * 32ull; it0 < nr; it0 += gwarps * 32ull) {
-            const unsigned long long it = it0 + (unsigned)lane;
-            uint32_t rows = 0, wq = 0, W = 0;
-            uint32_t *plane = nullptr;
-            if (it < nr) {
-                const int s = find_slot(ctl->row_off, na, it);
-                const int j = __ldcg(ctl->act + s);
-                const unsigned long long loc = it - __ldcg(ctl->row_off + s);
-                if (j >= 0 && j < k && loc < bq[j].row_items) {
-                    const QDesc &q = bq[j].q;
-                    const uint32_t rw = (q.n + 31u) / 32u;
-                    const int a = (int)(loc / rw);
-                    wq = (uint32_t)(loc % rw);
-                    W = q.W;
-                    const uint32_t prev = (uint32_t)((ld_u64(&q.st->iter) + 1ull) & 1ull);
-                    uint32_t *bm = (prev ? q.R1 : q.R0) + (uint64_t)a * q.W + wq;
-                    const uint32_t word = __ldcg(bm);
-                    rows = word & rows_in_word(q.n, wq);
-                    plane = (prev ? q.X1 : q.X0) + (uint64_t)a * q.plane;
-                    if (word) *bm = 0u;
-                }
-            }
-            unsigned todo = __ballot_sync(0xffffffffu, rows != 0);
-            while (todo) {
-                const int src = __ffs(todo) - 1;
-                todo &= todo - 1;
-                uint32_t r = __shfl_sync(0xffffffffu, rows, src);
-                const uint32_t sw = __shfl_sync(0xffffffffu, W, src), swq = __shfl_sync(0xffffffffu, wq, src);
-                uint32_t *sp = reinterpret_cast<uint32_t *>(
-                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(plane), src));
-                while (r) {
-                    const uint64_t i = swq * 32u + (uint32_t)(__ffs(r) - 1);
-                    r &= r - 1;
-                    for (uint32_t w = lane; w < sw; w += 32) sp[i * sw + w] = 0u;
-                }
+        // D): its row bitmap is zeroed (one lane per (query, non-terminal, row word)). Its rows
+        // are not: the products write every chunk of a row they touch whole (gather_row_chunk
+        // with WRITE_CHUNK), a row is read again only where its bit is set, and a set bit means
+        // every chunk of the row was written in this round.
+        const unsigned long long nr = cached ? s_roff[na] : __ldcg(ctl->row_off + na);
+        for (unsigned long long it = gwarp * 32ull + (unsigned)lane; it < nr; it += gwarps * 32ull) {
+            int j = 0;
+            unsigned long long loc = 0;
+            slot_of(true, it, j, loc);
+            if (j >= 0 && j < k && loc < bq[j].row_items) {
+                const QDesc &q = bq[j].q;
+                const uint32_t rw = (q.n + 31u) / 32u;
+                const uint32_t prev = (uint32_t)((ld_u64(&q.st->iter) + 1ull) & 1ull);
+                uint32_t *bm = (prev ? q.R1 : q.R0) + (uint64_t)(loc / rw) * q.W + (uint32_t)(loc % rw);
+                if (__ldcg(bm)) *bm = 0u;
             }
         }
         if (!grid_barrier(ctl)) return;
@@ -349,10 +370,10 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
             if (g >= b.q.n_groups || i >= b.q.n || ch >= b.nch) continue;
             const uint32_t parity = (uint32_t)(ld_u64(&b.q.st->iter) & 1ull);
             switch (b.cpl) {
-                case 1: gather_row_chunk<1>(b.q, g, i, ch, lane, parity); break;
-                case 2: gather_row_chunk<2>(b.q, g, i, ch, lane, parity); break;
-                case 4: gather_row_chunk<4>(b.q, g, i, ch, lane, parity); break;
-                default: gather_row_chunk<8>(b.q, g, i, ch, lane, parity); break;
+                case 1: gather_row_chunk<1, true>(b.q, g, i, ch, lane, parity); break;
+                case 2: gather_row_chunk<2, true>(b.q, g, i, ch, lane, parity); break;
+                case 4: gather_row_chunk<4, true>(b.q, g, i, ch, lane, parity); break;
+                default: gather_row_chunk<8, true>(b.q, g, i, ch, lane, parity); break;
             }
         }
         if (!grid_barrier(ctl)) return;
@@ -360,16 +381,16 @@ __global__ void __launch_bounds__(256, 4) k_batch(BatchCtl *ctl, const BatchQuer
         // 4) Jacobi queries: T |= N over the rows N touched (one lane per (query, non-terminal,
         //    row word) finds them and sets the row bitmap of T; the warp merges them together)
         if (ctl->any_jacobi) {
-            const unsigned long long nr = __ldcg(ctl->row_off + na);
+            const unsigned long long nr = cached ? s_roff[na] : __ldcg(ctl->row_off + na);
             for (unsigned long long it0 = gwarp * 32ull; it0 < nr; it0 += gwarps * 32ull) {
                 const unsigned long long it = it0 + (unsigned)lane;
                 uint32_t rows = 0, wq = 0, W = 0;
                 uint32_t *tp = nullptr;
                 const uint32_t *np_ = nullptr;
                 if (it < nr) {
-                    const int s = find_slot(ctl->row_off, na, it);
-                    const int j = __ldcg(ctl->act + s);
-                    const unsigned long long loc = it - __ldcg(ctl->row_off + s);
+                    int j = 0;
+                    unsigned long long loc = 0;
+                    slot_of(true, it, j, loc);
                     if (j >= 0 && j < k && loc < bq[j].row_items && bq[j].q.schedule == CFPQ_SCHED_JACOBI) {
                         const QDesc &q = bq[j].q;
                         const uint32_t rw = (q.n + 31u) / 32u;

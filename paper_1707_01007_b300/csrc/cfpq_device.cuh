@@ -302,7 +302,11 @@ __device__ __forceinline__ void or_rows_for_bits(uint32_t (&acc)[CPL], uint32_t 
 // blk_new != NULL: the new pairs are added to blk_new[A] (the calling block's shared table,
 // which the caller flushes into the counts and flags once per block); NULL: straight into the
 // device-side counts and flags.
-template <int CPL>
+// WRITE_CHUNK: the chunk of row i of N_A is written whole (its new bits, zeros elsewhere)
+// instead of ORed into, so N need not be cleared first. Valid where every product is a gather
+// and every chunk of a listed row is listed (the grouped launch): a row whose delta bit is set
+// is then entirely this execution's, and no other row of N is read before it is rewritten.
+template <int CPL, bool WRITE_CHUNK = false>
 __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint32_t ch, int lane,
                                         uint32_t parity, unsigned long long *blk_new = nullptr) {
     const uint32_t W = q.W;
@@ -397,9 +401,10 @@ __device__ inline void gather_row_chunk(const QDesc &q, int g, uint32_t i, uint3
             if (nw) {
                 cnt += __popc(nw);
                 if (inplace) TA[col] = old | nw;
-                NA[col] = __ldcg(NA + col) | nw;
+                if (!WRITE_CHUNK) NA[col] = __ldcg(NA + col) | nw;
             }
         }
+        if (WRITE_CHUNK && col < W) NA[col] = nw;
         if (inplace && q.Tsum) {  // the 32 lanes' words form one word of the summary of T_A
             const unsigned sb = __ballot_sync(0xffffffffu, nw != 0u);
             if (lane == 0 && sb) atomicOr(&q.Tsum[((uint64_t)A * q.n_pad + i) * q.SW + ((base + 32u * c) >> 5)], sb);
