@@ -350,20 +350,29 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
     // them while the choice runs)
     __shared__ float s_dc[kMaxNT], s_tc[kMaxNT];
     __shared__ unsigned s_dirty[kMaxNT], s_known[kMaxNT];
+    // the productions' operands (the first kLiveRules) and the group starts, in the same round
+    // trip as the counts
+    __shared__ int2 s_bc[kLiveRules];
+    __shared__ int s_gstart[kMaxNT + 1];
     DevState *st = q.st;
     const int tid = threadIdx.x;
-    const uint32_t p = (uint32_t)(ld_u64(&st->iter) & 1ull);
+    const unsigned long long it = ld_u64(&st->iter);
     if (tid == 0) s_any = s_probe = 0u;
     if (tid < q.n_nt) {
-        s_dc[tid] = (float)ld_u64(&st->dcount[p][tid]);
+        // both parities' delta counts, loaded beside the iteration number (not after it)
+        const unsigned long long d0 = ld_u64(&st->dcount[0][tid]), d1 = ld_u64(&st->dcount[1][tid]);
         s_tc[tid] = (float)ld_u64(&st->tcount[tid]);
         s_dirty[tid] = ld_u32(&st->dirty[tid]);
         s_known[tid] = q.occKnown ? ld_u32(&q.occKnown[tid]) : 0u;
+        s_dc[tid] = (float)((it & 1ull) ? d1 : d0);
     }
+    for (int r = tid; r < q.n_rules && r < kLiveRules; r += (int)blockDim.x) s_bc[r] = make_int2(q.rules[r].b, q.rules[r].c);
+    for (int g = tid; g <= q.n_groups; g += (int)blockDim.x) s_gstart[g] = q.gstart[g];
     __syncthreads();
+    auto operands = [&](int r) { return r < kLiveRules ? s_bc[r] : make_int2(q.rules[r].b, q.rules[r].c); };
     if (q.occA)
         for (int r = tid >> 5; r < q.n_rules && r < kLiveRules; r += (int)(blockDim.x >> 5)) {
-            const int B = q.rules[r].b, C = q.rules[r].c;
+            const int B = s_bc[r].x, C = s_bc[r].y;
             const float live = (s_known[B] && s_known[C]) ? live_steps_of(q, B, C, tid & 31) : 0.0f;
             if ((tid & 31) == 0) s_live[r] = live;
         }
@@ -378,11 +387,12 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
         // for dense E2M1 products (no tile occupancy), bit-packed otherwise
         const bool nibble = kind && !q.occA;
         const float transpose_ns = (np * np / 8.0f + (nibble ? np * np / 2.0f : np * np / 8.0f)) / kTransposeBytesPerNs;
-        const int r0 = q.gstart[g], r1 = q.gstart[g + 1];
+        const int r0 = s_gstart[g], r1 = s_gstart[g + 1];
         float words = 0.0f, tensor_ns = kTensorLaunchNs;
         bool unknown = false;
         for (int r = r0; r < r1; r++) {
-            const int B = q.rules[r].b, C = q.rules[r].c;
+            const int2 bc = operands(r);
+            const int B = bc.x, C = bc.y;
             const float dB = s_dc[B], dC = s_dc[C], tB = s_tc[B];
             words += dB * W;
             if (dC > 0.0f) words += fminf(n, tB) * 2.0f * W + tB * fminf(1.0f, dC / n) * W;
@@ -408,7 +418,10 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
         const float pass_ns = 2.0f * (float)(r1 - r0) * np * np / 8.0f / kTransposeBytesPerNs;
         if (q.occA && unknown && !use && gather_ns > fmaxf(kProbeNs, 10.0f * pass_ns)) {
             // tile skipping might beat the gather here: the next occupancy pass gets these counts
-            for (int r = r0; r < r1; r++) st->occ_now[q.rules[r].b] = st->occ_now[q.rules[r].c] = 1u;
+            for (int r = r0; r < r1; r++) {
+                const int2 bc = operands(r);
+                st->occ_now[bc.x] = st->occ_now[bc.y] = 1u;
+            }
             atomicOr(&s_probe, 1u);
         }
         st->use_tensor[g] = use;
@@ -430,8 +443,8 @@ __device__ void choose_products(const QDesc &q, const cudaGraphConditionalHandle
         unsigned owner = 0u;
         for (int g = 0; g < q.n_groups && !owner; g++)
             if (s_use[g])
-                for (int r = q.gstart[g]; r < q.gstart[g + 1]; r++)
-                    if (q.rules[r].c == a) {
+                for (int r = s_gstart[g]; r < s_gstart[g + 1]; r++)
+                    if (operands(r).y == a) {
                         owner = (unsigned)g + 1u;
                         break;
                     }

@@ -494,7 +494,9 @@ __device__ inline unsigned tail_query(const QDesc &q, int tid, int nthreads, boo
     }
     __syncthreads();
     if (tid < q.n_nt) {
-        const unsigned long long add = ld_u64(&st->dcount[old ^ 1u][tid]);  // pairs added now
+        // pairs added now: both parities' counts are loaded (not one after the iteration number)
+        const unsigned long long d0 = ld_u64(&st->dcount[0][tid]), d1 = ld_u64(&st->dcount[1][tid]);
+        const unsigned long long add = old ? d0 : d1;
         if (add) atomicAdd(&s_added, add);
         st->dcount[old][tid] = 0ull;
     }
