@@ -97,3 +97,37 @@ def test_results_survive_the_next_extraction():
     assert np.array_equal(np.concatenate(per, axis=0), keep)
     assert ctypes.sizeof(eng.Triple) == 12
     q.close()
+
+
+def test_concurrent_solves_on_two_streams():
+    """Two contexts solved at the same time from two host threads on two streams: each
+    launches the persistent gather loop (a cooperative grid over the whole device), so the
+    launches share the GPU; both closures equal the oracle's."""
+    import threading
+
+    import torch
+
+    cases = []
+    for seed, text in ((21, synth.GRAMMAR_Q1), (22, synth.GRAMMAR_QSC)):
+        graph = synth.hierarchy(6000, 1800, seed=seed)
+        g = eng.Grammar(text, graph.labels)
+        cases.append((graph, text, g, eng.Query(g, graph.n, graph.edges, path=eng.PATH_GATHER, timeout_s=120.0)))
+    streams = [torch.cuda.Stream() for _ in cases]
+    errors = []
+
+    def work(q, s):
+        try:
+            for _ in range(4):
+                q.solve(s)
+        except Exception as e:  # reported below, on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(c[3], s)) for c, s in zip(cases, streams)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    for graph, text, g, q in cases:
+        assert np.array_equal(q.triples_all(), expected_triples(graph, text, g.names))
+        q.close()
