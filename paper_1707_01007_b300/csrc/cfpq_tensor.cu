@@ -42,21 +42,23 @@ namespace cfpq {
 namespace tc {
 
 constexpr int BM = 128, BN = 256;
-constexpr int UST = 5;                // unpacked ring depth
+// (the unpacked ring's depth is per kind: Kind<KIND>::UST)
 constexpr int B_TILE = BN * 128;      // bytes of one unpacked B stage: 256 rows x 128 bytes
 constexpr int UNPACK_GROUPS = 2;     // groups of 8 unpack warps; group g takes the K stages s = g mod 2
 constexpr int GROUP_THREADS = 256;   // one group: two warps per SM sub-partition
 constexpr int UNPACK_WARPS = 8 * UNPACK_GROUPS;
-static_assert(UNPACK_GROUPS < UST, "a group's ring slot advances by UNPACK_GROUPS with one wrap at most");
 constexpr uint32_t RASTER_N = 8;      // N tiles per rasterisation band
 constexpr int UNPACK_THREADS = 32 * UNPACK_WARPS;
 constexpr int THREADS = 64 + UNPACK_THREADS;
 constexpr uint32_t ACC_COLS = 256;                 // F32 accumulator, 128 lanes x 256 columns
 constexpr uint32_t A_COLS = 32;                    // one stage of A: 128 bytes per lane = 32 columns
-constexpr uint32_t SFA_COL = ACC_COLS + UST * A_COLS;  // FP4: scale factors of A (32 columns, all 2^0)
-constexpr uint32_t SFB_COL = SFA_COL + 32;             // FP4: scale factors of B (32 columns, all 2^0)
+// FP4 scale factors (32 columns each, all 2^0) after the accumulator and the UST A stages
+template <int UST>
+__host__ __device__ constexpr uint32_t sfa_col() { return ACC_COLS + UST * A_COLS; }
+template <int UST>
+__host__ __device__ constexpr uint32_t sfb_col() { return sfa_col<UST>() + 32; }
 constexpr uint32_t TMEM_COLS = 512;                // power of two
-static_assert(SFB_COL + 32 <= TMEM_COLS, "tensor memory budget");
+static_assert(sfb_col<6>() + 32 <= TMEM_COLS, "tensor memory budget");
 
 // Operand kinds. An unpacked K stage is 128 bytes per row either way (one 128-byte
 // swizzle row of a shared-memory tile, 32 tensor-memory columns) and feeds 4 MMAs.
@@ -73,14 +75,20 @@ template <>
 struct Kind<0> {
     static constexpr int KW = 4, PST = 8, SLICES = 1;  // packed words per row and stage, packed ring depth
     static constexpr bool NIBBLE_B = false;            // B arrives bit-packed and is unpacked by the threads
+    static constexpr int UST = 5;                      // unpacked ring depth
 };
 template <>
 struct Kind<1> {
     // dense products: B arrives as E2M1 nibbles (T^T kept expanded, k_transpose_e2m1) straight
     // into the MMA's shared-memory layout; a ring slot is the packed A stage plus the B tile,
     // 6 slots (even, so each serves one unpack group)
+    // The unpacked A ring has the packed ring's depth (256 + 6 x 32 + 64 tensor-memory columns:
+    // all 512), so stage s uses slot s % 6 in both, and one MMA commit per stage frees it in
+    // both: the commit follows the unpack's reads of the packed A (the MMAs waited for the
+    // unpack), and the loads of stage s + 6, which the unpack waits for, are issued only after it
     static constexpr int KW = 8, PST = 6, SLICES = 2;
     static constexpr bool NIBBLE_B = true;
+    static constexpr int UST = 6;
 };
 template <>
 struct Kind<2> {
@@ -88,11 +96,12 @@ struct Kind<2> {
     // changed operand and execution writes a quarter of the nibble operand's bytes)
     static constexpr int KW = 8, PST = 5, SLICES = 2;
     static constexpr bool NIBBLE_B = false;
+    static constexpr int UST = 5;
 };
 
 template <int KIND>
 struct __align__(1024) Smem {
-    static constexpr int KW = Kind<KIND>::KW, PST = Kind<KIND>::PST;
+    static constexpr int KW = Kind<KIND>::KW, PST = Kind<KIND>::PST, UST = Kind<KIND>::UST;
     static constexpr bool NB = Kind<KIND>::NIBBLE_B;
     uint8_t b_tile[NB ? PST : UST][B_TILE];   // unpacked B stages (nibble B: the ring's B tiles)
     uint32_t a_pack[PST][BM * KW];
@@ -150,7 +159,8 @@ __device__ __forceinline__ void mma_stage(uint32_t tmem, uint32_t at, uint32_t b
         if constexpr (KIND == 0)
             mma_f8_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), acc);
         else
-            mma_f4_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), tmem + SFA_COL, tmem + SFB_COL, acc);
+            mma_f4_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), tmem + sfa_col<Kind<KIND>::UST>(),
+                      tmem + sfb_col<Kind<KIND>::UST>(), acc);
     }
 }
 
@@ -291,8 +301,11 @@ template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_bool_gemm(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmTT, const QDesc *qd,
                    int g, const uint2 *list) {
-    constexpr int KW = Kind<KIND>::KW, PST = Kind<KIND>::PST, SLICES = Kind<KIND>::SLICES;
+    constexpr int KW = Kind<KIND>::KW, PST = Kind<KIND>::PST, SLICES = Kind<KIND>::SLICES, UST = Kind<KIND>::UST;
     constexpr bool NB = Kind<KIND>::NIBBLE_B;
+    static_assert(!NB || UST == PST, "nibble B: one commit frees both rings' slot");
+    static_assert(UNPACK_GROUPS < UST, "a group's ring slot advances by UNPACK_GROUPS with one wrap at most");
+    constexpr uint32_t SFA_COL = sfa_col<UST>(), SFB_COL = sfb_col<UST>();
     // N tiles per rasterisation band: 4 for dense nibble products; with a plan list, the plan's own
     // mapping (k_tile_plan numbers tiles with RASTER_N)
     const uint32_t RASTER = (NB && !list) ? 4u : RASTER_N;
@@ -319,7 +332,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&S.full_p[i], 1);
             // a slot is free once the group has read its packed A (and, nibble B, once the MMAs
             // that read its B tile have completed: one commit)
-            mbar_init(&S.empty_p[i], GROUP_THREADS + (NB ? 1 : 0));
+            mbar_init(&S.empty_p[i], NB ? 1 : GROUP_THREADS);  // nibble B: the MMAs' commit (it follows the unpack's reads)
         }
         for (int i = 0; i < UST; i++) {
             mbar_init(&S.full_u[i], GROUP_THREADS);
@@ -463,8 +476,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tc_fence_after();
                     const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + (NB ? ps : slot) * B_TILE;
                     mma_stage<KIND>(tmem, at, bt, u == 0);
-                    mma_commit(&S.empty_u[slot]);
-                    if (NB) mma_commit(&S.empty_p[ps]);  // the B tile may be overwritten once these MMAs completed
+                    if (NB) mma_commit(&S.empty_p[ps]);  // frees the stage in both rings
+                    else mma_commit(&S.empty_u[slot]);
                 }
                 mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
                 tiles_done++;
@@ -529,7 +542,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (sn >= (uint32_t)PST) passed = mbar_wait(&S.empty_p[ps], ((sn / PST) - 1u) & 1u, err, WAIT_LIMIT_NS, 9);
                 }
                 passed = passed && mbar_wait(&S.full_p[ps], pph, err, WAIT_LIMIT_NS, 6);
-                passed = passed && mbar_wait(&S.empty_u[us], uph ^ 1u, err, WAIT_LIMIT_NS, 7);
+                // nibble B: stage sn's loads were issued after stage sn - PST's MMAs completed,
+                // so the tensor-memory slot (sn % PST) is free once they landed
+                if constexpr (!NB) passed = passed && mbar_wait(&S.empty_u[us], uph ^ 1u, err, WAIT_LIMIT_NS, 7);
                 // one warp-uniform outcome for the stage: the unpack below uses warp-collective tcgen05.st
                 if (!__all_sync(0xffffffffu, passed)) return false;
                 tc_fence_after();
@@ -549,7 +564,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         pb[4] = y1.x, pb[5] = y1.y, pb[6] = y1.z, pb[7] = y1.w;
                     }
                 }
-                mbar_arrive(&S.empty_p[ps]);
+                if constexpr (!NB) mbar_arrive(&S.empty_p[ps]);
                 unpack_half_row_tmem<KIND>(a_lane + us * A_COLS, pa);
                 if constexpr (!NB) {
                     unpack_row<KIND>(S.b_tile[us], off, pb);
