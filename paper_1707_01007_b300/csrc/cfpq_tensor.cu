@@ -465,14 +465,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                         stop = true;
                         break;
                     }
-                    // nibble B: the stage's B tile landed by TMA (the unpack group saw the same
-                    // phase before its arrival; the MMA thread waits on it itself, as the reader
-                    // of that tile)
+                    // nibble B: the stage's B tile has landed. It lands by TMA on full_p[ps] with
+                    // the packed A, and the unpack group waited for that phase before its arrivals
+                    // on full_u[slot]: passing full_u orders the MMAs after the tile's bytes (a
+                    // second wait here, on full_p, cost about 7 % of the dense step)
                     const uint32_t ps = s % PST;
-                    if (NB && !mbar_wait(&S.full_p[ps], (s / PST) & 1u, err, WAIT_LIMIT_NS, 10)) {
-                        stop = true;
-                        break;
-                    }
                     tc_fence_after();
                     const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + (NB ? ps : slot) * B_TILE;
                     mma_stage<KIND>(tmem, at, bt, u == 0);
