@@ -166,7 +166,7 @@ def run_single_commit(seed, pst, ust, stages, groups=2):
     """The dense E2M1 kind's protocol (B landed by TMA in the packed slot beside the packed A):
     one MMA commit per stage on empty_p frees the stage's packed slot and, with ust == pst,
     its tensor-memory A slot; the unpack groups wait only for the stage's loads, and the MMA
-    thread for the unpacked stage and the stage's B. Returns None or the first violation
+    thread only for the unpacked stage (which implies the stage's B). Returns None or the first violation
     (a slot overwritten while an earlier stage's MMAs still read it, a wrong stage read)."""
     rng = random.Random(seed)
     full_p = [Barrier(1) for _ in range(pst)]
@@ -218,7 +218,9 @@ def run_single_commit(seed, pst, ust, stages, groups=2):
         s = mma["s"]
         if s >= stages:
             return False
-        if not full_u[s % ust].passed((s // ust) & 1) or not full_p[s % pst].passed((s // pst) & 1):
+        # only the unpacked stage's barrier: the unpack group waited for the stage's loads
+        # (the B tile lands with the packed A) before arriving on it
+        if not full_u[s % ust].passed((s // ust) & 1):
             return False
         if unpacked[s % ust] != s or packed[s % pst] != s:
             return f"MMA of stage {s} read A {unpacked[s % ust]} / B {packed[s % pst]}"
