@@ -153,13 +153,14 @@ __device__ __forceinline__ void mma_f4_ts(uint32_t tmem_d, uint32_t tmem_a, uint
 // The 4 MMAs of one unpacked stage (A at tensor-memory column at, B at shared address bt).
 template <int KIND>
 __device__ __forceinline__ void mma_stage(uint32_t tmem, uint32_t at, uint32_t bt, bool first) {
+    const uint64_t d0 = sdesc(bt);  // the K step kk starts 32 bytes further: + 2 in the address field
 #pragma unroll
     for (int kk = 0; kk < 4; kk++) {
         const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
         if constexpr (KIND == 0)
-            mma_f8_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), acc);
+            mma_f8_ts(tmem, at + kk * 8, d0 + (uint64_t)(2 * kk), acc);
         else
-            mma_f4_ts(tmem, at + kk * 8, sdesc(bt + kk * 32), tmem + sfa_col<Kind<KIND>::UST>(),
+            mma_f4_ts(tmem, at + kk * 8, d0 + (uint64_t)(2 * kk), tmem + sfa_col<Kind<KIND>::UST>(),
                       tmem + sfb_col<Kind<KIND>::UST>(), acc);
     }
 }
@@ -448,6 +449,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             // ---------------- MMA issuer
             const uint32_t b0 = sa(S.b_tile[0]);
             uint32_t s = 0, tiles_done = 0;
+            // running ring positions of stage s: slot = s % UST and its phase, ps = s % PST
+            uint32_t slot = 0, ph = 0, ps = 0;
             bool stop = false;
             for (uint32_t ord = 0; !stop; ord++) {
                 const uint32_t i = read_tile(ord, 0u);
@@ -460,7 +463,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                     tc_fence_after();
                 }
                 for (uint32_t u = 0; u < steps; u++, s++) {
-                    const uint32_t slot = s % UST, ph = (s / UST) & 1u;
                     if (!mbar_wait(&S.full_u[slot], ph, err, WAIT_LIMIT_NS, 5)) {
                         stop = true;
                         break;
@@ -469,12 +471,16 @@ __global__ void __launch_bounds__(THREADS, 1)
                     // the packed A, and the unpack group waited for that phase before its arrivals
                     // on full_u[slot]: passing full_u orders the MMAs after the tile's bytes (a
                     // second wait here, on full_p, cost about 7 % of the dense step)
-                    const uint32_t ps = s % PST;
                     tc_fence_after();
                     const uint32_t at = tmem + ACC_COLS + slot * A_COLS, bt = b0 + (NB ? ps : slot) * B_TILE;
                     mma_stage<KIND>(tmem, at, bt, u == 0);
                     if (NB) mma_commit(&S.empty_p[ps]);  // frees the stage in both rings
                     else mma_commit(&S.empty_u[slot]);
+                    if (++slot == (uint32_t)UST) {
+                        slot = 0;
+                        ph ^= 1u;
+                    }
+                    if (++ps == (uint32_t)PST) ps = 0;
                 }
                 mma_commit(&S.acc_full);  // arrives once every MMA issued above has completed
                 tiles_done++;
