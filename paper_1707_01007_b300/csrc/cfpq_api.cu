@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256) k_clear_scan(const QDesc *qd, uint32_t *l
 // if no group takes the tensor cores), so the next choice prices the live steps.
 // Measured rates (Boolean ops per ns) of dense products and of the work executed with tile
 // skipping, for E4M3 and E2M1 operands.
-__device__ __forceinline__ float tensor_ops_per_ns(int kind) { return kind ? 6.9e6f : 3.2e6f; }
+__device__ __forceinline__ float tensor_ops_per_ns(int kind) { return kind ? 7.6e6f : 3.2e6f; }
 __device__ __forceinline__ float skip_ops_per_ns(int kind) { return kind ? 3.2e6f : 2.2e6f; }
 constexpr float kStepOps = 2.0f * 128.0f * 256.0f * 128.0f;  // Boolean ops of one K slice of a tile
 constexpr float kTensorLaunchNs = 8000.0f;               // plan and product launches of a group
