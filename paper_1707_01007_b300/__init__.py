@@ -57,6 +57,7 @@ class Triple(ctypes.Structure):
 
 
 _PINNED = None  # torch, when its CUDA host allocator can stage results (False: plain numpy)
+_PINNED_MAX_BYTES = 1 << 30  # larger results go to ordinary memory (pinning gigabytes can fail)
 
 
 def _host_words(rows: int, cols: int) -> np.ndarray:
@@ -72,9 +73,12 @@ def _host_words(rows: int, cols: int) -> np.ndarray:
             _PINNED = torch if torch.cuda.is_available() else False
         except ImportError:
             _PINNED = False
-    if _PINNED:
-        t = _PINNED.empty((rows, cols), dtype=_PINNED.int32, pin_memory=True)
-        return t.numpy().view("<u4")
+    if _PINNED and rows * cols * 4 <= _PINNED_MAX_BYTES:
+        try:
+            t = _PINNED.empty((rows, cols), dtype=_PINNED.int32, pin_memory=True)
+            return t.numpy().view("<u4")
+        except RuntimeError:  # page-locked memory exhausted: ordinary memory works as well
+            pass
     return np.empty((rows, cols), dtype="<u4")
 
 
