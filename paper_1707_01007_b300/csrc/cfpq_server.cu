@@ -207,7 +207,9 @@ static int retire_batch(cfpq_server *s, const std::vector<Served *> &qs, cudaStr
         tbase[j] = total;
         total += (size_t)s->h_off[obase[j] + (size_t)qs[j]->ctx->n_nt];
     }
-    if (!host_reserve(s->h_trip, s->trip_cap, total)) return CFPQ_ERR_NOMEM;
+    // the triples' staging (page-locked); where it cannot grow, each query's triples go to
+    // ordinary host memory one query at a time
+    const bool staged = host_reserve(s->h_trip, s->trip_cap, total);
     for (size_t j = 0; j < k; j++) {
         Served *q = qs[j];
         cfpq_ctx *c = q->ctx;
@@ -217,6 +219,11 @@ static int retire_batch(cfpq_server *s, const std::vector<Served *> &qs, cudaStr
         c->solved = true;
         if (rc == CFPQ_ERR_CUDA) return rc;
         const size_t tj = (size_t)s->h_off[obase[j] + (size_t)c->n_nt];
+        if (!staged) {
+            const int r2 = extract_all_host(c, q->results);
+            if (r2 != CFPQ_OK) return r2;
+            continue;
+        }
         if (tj == 0) continue;
         int r2 = ensure_triples(c, tj, st);
         if (r2 == CFPQ_OK) r2 = emit_all(c, c->d_triples, st);
@@ -225,14 +232,16 @@ static int retire_batch(cfpq_server *s, const std::vector<Served *> &qs, cudaStr
                             st) != cudaSuccess)
             return CFPQ_ERR_CUDA;
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) return CFPQ_ERR_CUDA;
+    if (staged && cudaStreamSynchronize(st) != cudaSuccess) return CFPQ_ERR_CUDA;
     for (size_t j = 0; j < k; j++) {
         Served *q = qs[j];
         cfpq_ctx *c = q->ctx;
         const unsigned long long *off = s->h_off + obase[j];
-        const cfpq_triple *t = s->h_trip + tbase[j];
-        q->results.assign(c->n_nt, {});
-        for (int a = 0; a < c->n_nt; a++) q->results[a].assign(t + off[a], t + off[a + 1]);
+        if (staged) {
+            const cfpq_triple *t = s->h_trip + tbase[j];
+            q->results.assign(c->n_nt, {});
+            for (int a = 0; a < c->n_nt; a++) q->results[a].assign(t + off[a], t + off[a + 1]);
+        }
         ctx_destroy(c);
         q->ctx = nullptr;
         s->used -= q->footprint;
