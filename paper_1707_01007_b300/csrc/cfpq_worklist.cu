@@ -302,12 +302,18 @@ __device__ uint32_t general_join(const QDesc &q, const WLDesc &w, uint32_t ca, u
                 uint32_t bits = (w0 + lane < q.W) ? __ldcg(row + w0 + lane) : 0u;
                 if (!left && bits) {
                     // the derived pairs (x, k, cj) fill column cj of T_x: one word-wide OR
-                    // into T_x^T per 32 of them; the new ones are then set in T_x
+                    // into T_x^T per 32 of them; the ones not there yet are then set in T_x,
+                    // and a pair is new where its bit of T_x was clear. T_x decides, as for
+                    // every other way of setting a pair: a pair set at the same time through
+                    // T_x first (wl_set, then T_x^T) would otherwise count once on each side
                     const uint32_t old = atomicOr(dst_col + w0 + lane, bits);
                     bits &= ~old;
                     for (uint32_t nb = bits; nb; nb &= nb - 1) {
+                        const uint32_t bk = nb & (0u - nb);
                         const uint32_t k = (w0 + lane) * 32u + (uint32_t)(__ffs(nb) - 1);
-                        atomicOr(&q.T[(uint64_t)x * q.plane + (uint64_t)k * q.W + (cj >> 5)], 1u << (cj & 31));
+                        const uint32_t cbit = 1u << (cj & 31);
+                        if (atomicOr(&q.T[(uint64_t)x * q.plane + (uint64_t)k * q.W + (cj >> 5)], cbit) & cbit)
+                            bits &= ~bk;
                     }
                 }
                 if (left && bits) {
