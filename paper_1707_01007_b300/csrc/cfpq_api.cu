@@ -11,6 +11,7 @@
 
 #include "cfpq_device.cuh"
 #include "cfpq_internal.h"
+#include "cfpq_lengths.cuh"
 
 namespace cfpq {
 
@@ -499,7 +500,8 @@ __global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int u
 
 // Gather-only loop executions in one persistent launch (every block resident: a cooperative
 // launch of 256-thread blocks). Each execution runs the work of the launches it replaces in
-// phases separated by grid barriers: the listed gathers; (Jacobi) the merge T |= N, which the
+// phases separated by grid barriers: the listed gathers; (LEN) the lengths of the pairs they
+// added, read from T before the merge; (Jacobi) the merge T |= N, which the
 // next list reads through the row bitmap of T; then, at once, block 0's tail (the loop
 // condition and, with choice, the next execution's product choice) and, on the other blocks'
 // warps, the next execution's list and the clear of the delta rows read (each clear unit also
@@ -509,10 +511,10 @@ __global__ void k_tail(const QDesc *qd, cudaGraphConditionalHandle handle, int u
 // The launch ends when the loop ends or (choice) the next execution has a tensor product; on
 // the way out block 0 sets the graph's handles as k_tail does with the same flags
 // (kTailNested: the nested loops'; kTailUnrolled: the loop's alone).
-template <int CPL>
+template <int CPL, bool LEN>
 __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4)
     k_gather_loop(const QDesc *qd, uint32_t *list, uint32_t cap, uint32_t nch, cudaGraphConditionalHandle handle,
-                  const cudaGraphConditionalHandle *choice, int flags) {
+                  const cudaGraphConditionalHandle *choice, int flags, uint32_t *L, uint32_t *Wit, uint64_t lplane) {
     const QDesc &q = *qd;
     DevState *st = q.st;
     __shared__ unsigned long long s_target;
@@ -533,6 +535,10 @@ __global__ void __launch_bounds__(256, CPL >= 8 ? 3 : 4)
         const uint32_t par = (uint32_t)(ld_u64(&st->iter) & 1ull);  // this execution's parity
         gather_listed<CPL>(q, list, cap);
         if (!grid_sync(st, s_target)) break;
+        if constexpr (LEN) {  // the new pairs' lengths, from T before the merge (Section 5)
+            lengths_of_new_pairs(q, L, Wit, lplane);
+            if (!grid_sync(st, s_target)) break;
+        }
         if (jacobi) {
             merge_new_rows(q);
             if (!grid_sync(st, s_target)) break;
@@ -1168,12 +1174,23 @@ static int capture_gather_loop(cfpq_ctx *c, cudaStream_t s, cudaGraphConditional
     uint32_t *list = c->d_list;
     const uint32_t cap = c->list_cap;
     const cudaGraphConditionalHandle *choice = c->auto_mixed ? c->d_choice : nullptr;
+    uint32_t *L = c->d_L, *Wit = c->d_Wit;
+    const uint64_t lplane = c->lplane;
     cudaError_t e;
-    switch (cpl) {
-        case 1: e = cudaLaunchKernelEx(&cfg, k_gather_loop<1>, qd, list, cap, nch, h, choice, tail_flags); break;
-        case 2: e = cudaLaunchKernelEx(&cfg, k_gather_loop<2>, qd, list, cap, nch, h, choice, tail_flags); break;
-        case 4: e = cudaLaunchKernelEx(&cfg, k_gather_loop<4>, qd, list, cap, nch, h, choice, tail_flags); break;
-        default: e = cudaLaunchKernelEx(&cfg, k_gather_loop<8>, qd, list, cap, nch, h, choice, tail_flags); break;
+    if (c->lengths) {
+        switch (cpl) {
+            case 1: e = cudaLaunchKernelEx(&cfg, k_gather_loop<1, true>, qd, list, cap, nch, h, choice, tail_flags, L, Wit, lplane); break;
+            case 2: e = cudaLaunchKernelEx(&cfg, k_gather_loop<2, true>, qd, list, cap, nch, h, choice, tail_flags, L, Wit, lplane); break;
+            case 4: e = cudaLaunchKernelEx(&cfg, k_gather_loop<4, true>, qd, list, cap, nch, h, choice, tail_flags, L, Wit, lplane); break;
+            default: e = cudaLaunchKernelEx(&cfg, k_gather_loop<8, true>, qd, list, cap, nch, h, choice, tail_flags, L, Wit, lplane); break;
+        }
+    } else {
+        switch (cpl) {
+            case 1: e = cudaLaunchKernelEx(&cfg, k_gather_loop<1, false>, qd, list, cap, nch, h, choice, tail_flags, L, Wit, lplane); break;
+            case 2: e = cudaLaunchKernelEx(&cfg, k_gather_loop<2, false>, qd, list, cap, nch, h, choice, tail_flags, L, Wit, lplane); break;
+            case 4: e = cudaLaunchKernelEx(&cfg, k_gather_loop<4, false>, qd, list, cap, nch, h, choice, tail_flags, L, Wit, lplane); break;
+            default: e = cudaLaunchKernelEx(&cfg, k_gather_loop<8, false>, qd, list, cap, nch, h, choice, tail_flags, L, Wit, lplane); break;
+        }
     }
     if (e != cudaSuccess) {
         note_cuda_error(e, "gather loop", __FILE__, __LINE__);
@@ -1208,8 +1225,15 @@ static int build_graph(cfpq_ctx *c) {
     if (c->graph_exec) return CFPQ_OK;
     bool any_tensor = false;
     for (int g = 0; g < c->n_groups; g++) any_tensor |= c->group_tensor[g] != 0;
-    const bool nested = c->auto_mixed && !c->lengths;
-    const bool unrolled = !c->auto_mixed && !any_tensor && c->any_gather && !c->lengths;
+    // gather-only executions in one persistent launch where the device can hold its grid;
+    // the launch count then comes from the device (loop_launches, loop_execs). Not for a
+    // server's contexts: a large query's loop runs beside the grouped launches of the small
+    // ones, and a persistent launch would hold every SM until that query converged, where the
+    // separate launches interleave with them. Lengths need it for the nested and unrolled
+    // shapes (their unrolled copies would run the length kernel past the loop's end).
+    const bool persistent = c->loop_grid > 0 && !c->block && !c->pooled;
+    const bool nested = c->auto_mixed && (!c->lengths || persistent);
+    const bool unrolled = !c->auto_mixed && !any_tensor && c->any_gather && (!c->lengths || persistent);
     cudaGraph_t g = nullptr;
     CK(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
@@ -1262,12 +1286,6 @@ static int build_graph(cfpq_ctx *c) {
     e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(g); note_cuda_error(e, "capture", __FILE__, __LINE__); return CFPQ_ERR_CUDA; }
     int rc = CFPQ_OK;
-    // gather-only executions in one persistent launch where the device can hold its grid;
-    // the launch count then comes from the device (loop_launches, loop_execs). Not for a
-    // server's contexts: a large query's loop runs beside the grouped launches of the small
-    // ones, and a persistent launch would hold every SM until that query converged, where the
-    // separate launches interleave with them
-    const bool persistent = c->loop_grid > 0 && !c->block && !c->pooled;
     if (nested) {
         cudaGraph_t inner = nullptr, mixed = nullptr;
         rc = add_cond(c->stream, c->h_choice[c->n_groups + 1], cudaGraphCondTypeWhile, &inner);
@@ -1563,8 +1581,11 @@ int ctx_init(cfpq_ctx *c, const cfpq_grammar_cnf *g, uint32_t n, const cfpq_edge
             // 16384: one per SM is 7 % faster than three at n <= 2048, three 27 % faster than one
             // at 16384)
             int coop = 0, loop_per_sm = 0;
-            const void *lf = cpl == 1 ? (const void *)k_gather_loop<1> : cpl == 2 ? (const void *)k_gather_loop<2>
-                           : cpl == 4 ? (const void *)k_gather_loop<4> : (const void *)k_gather_loop<8>;
+            const void *lf = c->lengths
+                                 ? (cpl == 1 ? (const void *)k_gather_loop<1, true> : cpl == 2 ? (const void *)k_gather_loop<2, true>
+                                    : cpl == 4 ? (const void *)k_gather_loop<4, true> : (const void *)k_gather_loop<8, true>)
+                                 : (cpl == 1 ? (const void *)k_gather_loop<1, false> : cpl == 2 ? (const void *)k_gather_loop<2, false>
+                                    : cpl == 4 ? (const void *)k_gather_loop<4, false> : (const void *)k_gather_loop<8, false>);
             c->loop_grid = 0;
             if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&loop_per_sm, lf, 256, 0) == cudaSuccess && loop_per_sm > 0)
