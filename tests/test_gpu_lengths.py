@@ -319,3 +319,19 @@ def test_full_size_hierarchy_walks(text):
             m, n, l = int(pairs[t, 0]), int(pairs[t, 1]), int(lens[t])
             nodes, labels = q.path(nm, m, n)
             _check_walk(graph, cnf, a, m, n, l, nodes, labels, cyk_up_to=16)
+
+
+@pytest.mark.parametrize("path", [eng.PATH_GATHER, eng.PATH_AUTO])
+def test_graph_solve_runs_the_lengths_in_the_persistent_loop(path):
+    """Gather-only executions of a graph solve run in one persistent loop launch that also
+    computes the new pairs' lengths (between the gathers and the merge); the host-driven loop
+    launches the length kernel once per execution. Same lengths as the oracle either way, and
+    the graph solve runs far fewer kernels."""
+    graph = synth.hierarchy(2000, 600, seed=4)
+    _, qg = parity(graph, synth.GRAMMAR_Q1, path)
+    _, qh = parity(graph, synth.GRAMMAR_Q1, path, use_graph=False)
+    sg, sh = qg.stats(), qh.stats()
+    assert sg["iterations"] == sh["iterations"] > 4
+    assert sg["kernel_launches"] < sh["kernel_launches"] - 2 * sh["iterations"]
+    qg.close()
+    qh.close()
