@@ -1217,10 +1217,11 @@ static int capture_mixed_execution(cfpq_ctx *c, cudaStream_t s, cudaGraphConditi
 // The loop of Algorithm 1 as one graph: a WHILE node on "the last execution changed T" whose
 // body is one of
 //   automatic path: WHILE (the next execution is gather-only) { kUnroll gather-only
-//                   executions }, then IF (the next one has a tensor product) { that
-//                   execution }, after a first choice node;
-//   gather-only contexts: kUnroll executions;
-//   otherwise (tensor products every execution, lengths): one execution.
+//                   executions, or the persistent loop launch }, then IF (the next one has
+//                   a tensor product) { that execution }, after a first choice node;
+//   gather-only contexts: kUnroll executions (or the persistent loop launch);
+//   otherwise (tensor products every execution; lengths without the persistent loop):
+//   one execution.
 static int build_graph(cfpq_ctx *c) {
     if (c->graph_exec) return CFPQ_OK;
     bool any_tensor = false;
